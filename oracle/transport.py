@@ -1,0 +1,517 @@
+"""Plain FP64 CPU oracle for one time step of the 6-D spectral transport method.
+
+TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the bench's CPU
+baseline leg are the only callers; the CUDA library never calls this module and
+this module imports nothing from the library.
+
+What it computes (Bonazzola, Vasset & Peres 2011):
+  dF/dt = -L_sph F + CT,
+  L_sph = cos(Th) d_r + (1/r)[ sin(Th)cos(Ph) d_th + sin(Th)sin(Ph)/sin(th) d_ph
+                               - sin(Th) d_Th - sin(Th)sin(Ph) cot(th) d_Ph ]   (Eq. Liouvsph, Sect. 4.1)
+  CT = eta - kappa F + kappa_s (J - F),  J = (1/4pi) int F dOmega            (Eq. Transp, Sect. 2.2,
+                                                                           isotropic kernel Eq. sigman, B = 0)
+on the phase-space grid (r, th, ph, Th, Ph) with energy groups as independent
+slices. Every per-axis derivative follows the paper's coefficient-space route
+(Sect. 5.1): nodal values -> spectral coefficients -> derivative in coefficient
+space -> back to nodal values.
+
+Readings of the paper taken here (the paper is silent or garbled on these):
+  * State: nodal values; coefficients are formed per line when needed.
+  * r: Chebyshev-Gauss-Lobatto nodes r_i = (R1+R2)/2 - (R2-R1)/2 cos(pi i/(Nr-1)).
+  * th, Th: pole-free nodes pi (j+1/2)/N with a double-Fourier-sphere (DFS)
+    parity basis: on the doubled circle F(-th, ph, Th, Ph) = F(th, ph+pi, Th, Ph+pi)
+    and F(-Th, Ph) = F(Th, Ph+pi); both maps leave position and direction unchanged.
+  * ph, Ph: Fourier on 2 pi l/N. Nyquist modes of first derivatives are zeroed.
+  * Boundaries: Tau method (Sect. 5.1) on every stage derivative: for each
+    direction node the inflow node is r = R1 when cos(Th) > 0 and r = R2
+    otherwise; the top Chebyshev coefficient of dF/dt is replaced so that
+    dF/dt at the inflow node equals the (static, hence zero) rate of the
+    inflow data. Inflow data enter by setting F = g at the inflow nodes once
+    (``apply_inflow``).
+  * Time: classical RK4 (the paper's AB2 of Sect. 5.1 is replaced).
+  * Quadrature: Fejer's first rule in cos(th), cos(Th) (integral of the
+    polynomial interpolant); trapezoid in ph, Ph; Clenshaw-Curtis in r.
+  * Split variant: one streaming-only RK4 step, then a backward-Euler
+    collision step solved in closed form, then F = g again at inflow nodes
+    (model: the implicit first-order source step of App. B).
+  * Filter (off unless asked): sigma(k) = exp(-alpha (k/k_max)^order) per axis
+    in coefficient space.
+
+Layout: F[g][r][th][ph][Th][Ph] (numpy, float64, Ph fastest); coefficient
+fields kappa, eta, kappa_s are [g][r][th][ph]; inflow data g_R1 is
+[g][th][ph][NTh/2][Ph] (directions with cos Th > 0), g_R2 the other half.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+AX_R, AX_TH, AX_PH, AX_TTH, AX_TPH = 1, 2, 3, 4, 5   # axes of F (axis 0 = group)
+
+
+def _along(M, F, axis):
+    """Apply the matrix M (n_out x n_in) along one axis of F."""
+    return np.moveaxis(np.tensordot(M, F, axes=([1], [axis])), 0, axis)
+
+
+class Grid:
+    """Nodes and per-axis spectral machinery of one phase-space grid."""
+
+    def __init__(self, R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups=1):
+        if Nr < 3 or Nphi % 2 or NPhi % 2 or NTheta % 2:
+            raise ValueError("need Nr >= 3 and even N_phi, N_Phi, N_Theta")
+        self.R1, self.R2 = float(R1), float(R2)
+        self.Nr, self.Nt, self.Np, self.NT, self.NP = Nr, Ntheta, Nphi, NTheta, NPhi
+        self.G = groups
+        N = Nr - 1
+        i = np.arange(Nr)
+        self.xr = -np.cos(np.pi * i / N)                 # Chebyshev variable, ascending
+        self.r = 0.5 * (R1 + R2) + 0.5 * (R2 - R1) * self.xr
+        self.theta = np.pi * (np.arange(Ntheta) + 0.5) / Ntheta
+        self.phi = 2 * np.pi * np.arange(Nphi) / Nphi
+        self.Theta = np.pi * (np.arange(NTheta) + 0.5) / NTheta
+        self.Phi = 2 * np.pi * np.arange(NPhi) / NPhi
+        # Chebyshev transform pair on the Gauss-Lobatto nodes.
+        # V[i][k] = T_k(x_i);  x_i = cos(pi (N - i)/N).
+        k = np.arange(Nr)
+        self.cheb_V = np.cos(np.pi * np.outer(N - i, k) / N)
+        cbar = np.ones(Nr)
+        cbar[0] = cbar[-1] = 2.0
+        # c_k = 2/(N cbar_k) sum_i f_i T_k(x_i)/cbar_i   (discrete orthogonality)
+        self.cheb_S = (2.0 / N) * self.cheb_V.T / cbar[:, None] / cbar[None, :]
+        # derivative in coefficient space by the backward recurrence
+        # b_{k-1} = b_{k+1} + 2 k a_k, b_0 halved; columns = unit coefficient vectors
+        C = np.zeros((Nr, Nr))
+        for col in range(Nr):
+            a = np.zeros(Nr)
+            a[col] = 1.0
+            C[:, col] = self._cheb_deriv_coef(a)
+        self.cheb_C = C * (2.0 / (R2 - R1))              # d/dr = 2/(R2-R1) d/dx
+        self.shape = (groups, Nr, Ntheta, Nphi, NTheta, NPhi)
+
+    @property
+    def points(self):
+        return int(np.prod(self.shape))
+
+    @staticmethod
+    def _cheb_deriv_coef(a):
+        N = len(a) - 1
+        b = np.zeros(N + 2)
+        for kk in range(N, 0, -1):
+            b[kk - 1] = b[kk + 1] + 2 * kk * a[kk]
+        b[0] *= 0.5
+        return b[:N + 1]
+
+    # ------------------------------------------------------------------ r axis
+    def cheb_coeffs(self, F, axis=AX_R):
+        return _along(self.cheb_S, F, axis)
+
+    def cheb_values(self, c, axis=AX_R):
+        return _along(self.cheb_V, c, axis)
+
+    def d_r(self, F):
+        """d/dr: values -> Chebyshev coefficients -> recurrence -> values."""
+        c = self.cheb_coeffs(F)
+        c = _along(self.cheb_C, c, AX_R)
+        return self.cheb_values(c)
+
+    def d_r_T(self, mu):
+        """Transpose of d_r (explicit transposes of the three factors)."""
+        m = _along(self.cheb_V.T, mu, AX_R)
+        m = _along(self.cheb_C.T, m, AX_R)
+        return _along(self.cheb_S.T, m, AX_R)
+
+    # -------------------------------------------------------- Fourier machinery
+    @staticmethod
+    def _fourier_deriv(f, axis):
+        """Periodic spectral derivative along `axis` (period 2 pi, equispaced),
+        Nyquist mode zeroed."""
+        M = f.shape[axis]
+        c = np.fft.fft(f, axis=axis)
+        kk = np.fft.fftfreq(M, d=1.0 / M)
+        mult = 1j * kk
+        if M % 2 == 0:
+            mult[M // 2] = 0.0
+        shp = [1] * f.ndim
+        shp[axis] = M
+        return np.real(np.fft.ifft(c * mult.reshape(shp), axis=axis))
+
+    @staticmethod
+    def _fourier_filter(f, axis, sigma_of_k):
+        M = f.shape[axis]
+        c = np.fft.fft(f, axis=axis)
+        kk = np.abs(np.fft.fftfreq(M, d=1.0 / M))
+        shp = [1] * f.ndim
+        shp[axis] = M
+        return np.real(np.fft.ifft(c * sigma_of_k(kk).reshape(shp), axis=axis))
+
+    def _partner_th(self, F):
+        """F at the DFS partner of (th, ph, Th, Ph): (ph + pi, Ph + pi)."""
+        return np.roll(np.roll(F, -self.Np // 2, axis=AX_PH), -self.NP // 2, axis=AX_TPH)
+
+    def _partner_Th(self, F):
+        """F at the DFS partner of (Th, Ph): (Ph + pi)."""
+        return np.roll(F, -self.NP // 2, axis=AX_TPH)
+
+    def _extend(self, F, axis, partner):
+        """Doubled circle of 2N nodes: node n < N is th_n; node 2N-1-j carries
+        the reflected angle 2 pi - th_j whose value is F at the partner."""
+        return np.concatenate([F, np.flip(partner, axis=axis)], axis=axis)
+
+    def _restrict_T(self, mu, axis):
+        """Transpose of 'take the first N nodes of the doubled circle'."""
+        return np.concatenate([mu, np.zeros_like(mu)], axis=axis)
+
+    def _extend_T(self, e, axis, partner_T):
+        N = e.shape[axis] // 2
+        first = np.take(e, np.arange(N), axis=axis)
+        second = np.flip(np.take(e, np.arange(N, 2 * N), axis=axis), axis=axis)
+        return first + partner_T(second)
+
+    def d_th(self, F):
+        ext = self._extend(F, AX_TH, self._partner_th(F))
+        return np.take(self._fourier_deriv(ext, AX_TH), np.arange(self.Nt), axis=AX_TH)
+
+    def d_Th(self, F):
+        ext = self._extend(F, AX_TTH, self._partner_Th(F))
+        return np.take(self._fourier_deriv(ext, AX_TTH), np.arange(self.NT), axis=AX_TTH)
+
+    def d_ph(self, F):
+        return self._fourier_deriv(F, AX_PH)
+
+    def d_Ph(self, F):
+        return self._fourier_deriv(F, AX_TPH)
+
+    # Transposes: the Nyquist-zeroed periodic derivative is antisymmetric.
+    def d_ph_T(self, mu):
+        return -self._fourier_deriv(mu, AX_PH)
+
+    def d_Ph_T(self, mu):
+        return -self._fourier_deriv(mu, AX_TPH)
+
+    def _partner_th_inv(self, F):
+        return np.roll(np.roll(F, self.Np // 2, axis=AX_PH), self.NP // 2, axis=AX_TPH)
+
+    def _partner_Th_inv(self, F):
+        return np.roll(F, self.NP // 2, axis=AX_TPH)
+
+    def d_th_T(self, mu):
+        e = -self._fourier_deriv(self._restrict_T(mu, AX_TH), AX_TH)
+        return self._extend_T(e, AX_TH, self._partner_th_inv)
+
+    def d_Th_T(self, mu):
+        e = -self._fourier_deriv(self._restrict_T(mu, AX_TTH), AX_TTH)
+        return self._extend_T(e, AX_TTH, self._partner_Th_inv)
+
+    # ------------------------------------------------------ geometric factors
+    def coefficients(self):
+        """The five factors of Eq. (Liouvsph), broadcastable against F."""
+        r = self.r.reshape(1, -1, 1, 1, 1, 1)
+        th = self.theta.reshape(1, 1, -1, 1, 1, 1)
+        Th = self.Theta.reshape(1, 1, 1, 1, -1, 1)
+        Ph = self.Phi.reshape(1, 1, 1, 1, 1, -1)
+        a_r = np.cos(Th)
+        a_th = np.sin(Th) * np.cos(Ph) / r
+        a_ph = np.sin(Th) * np.sin(Ph) / (r * np.sin(th))
+        a_Th = -np.sin(Th) / r
+        a_Ph = -np.sin(Th) * np.sin(Ph) * np.cos(th) / (r * np.sin(th))
+        return a_r, a_th, a_ph, a_Th, a_Ph
+
+    def liouville(self, F):
+        """L_sph F (Eq. Liouvsph)."""
+        a_r, a_th, a_ph, a_Th, a_Ph = self.coefficients()
+        return (a_r * self.d_r(F) + a_th * self.d_th(F) + a_ph * self.d_ph(F)
+                + a_Th * self.d_Th(F) + a_Ph * self.d_Ph(F))
+
+    def liouville_T(self, mu):
+        """Transpose of liouville: sum_ax D_ax^T (a_ax mu)."""
+        a_r, a_th, a_ph, a_Th, a_Ph = self.coefficients()
+        return (self.d_r_T(a_r * mu) + self.d_th_T(a_th * mu) + self.d_ph_T(a_ph * mu)
+                + self.d_Th_T(a_Th * mu) + self.d_Ph_T(a_Ph * mu))
+
+    # ---------------------------------------------------------- quadratures
+    @staticmethod
+    def fejer_integral(g, axis):
+        """int_0^pi g(t) sin t dt from values at t_k = pi (k+1/2)/N: integrate
+        the interpolating polynomial in cos t exactly (Fejer's first rule)."""
+        N = g.shape[axis]
+        t = np.pi * (np.arange(N) + 0.5) / N
+        n = np.arange(N)
+        Tm = np.cos(np.outer(n, t))                       # T_n(cos t_k)
+        a = _along(Tm * (2.0 / N), g, axis)
+        a0 = np.take(a, [0], axis=axis) * 0.5
+        a = np.concatenate([a0, np.take(a, n[1:], axis=axis)], axis=axis)
+        In = np.zeros(N)
+        In[0::2] = 2.0 / (1.0 - n[0::2].astype(float) ** 2)
+        return np.tensordot(a, In, axes=([axis], [0]))
+
+    @staticmethod
+    def trapezoid_periodic(g, axis):
+        """int_0^{2 pi} g: 2 pi x the mean of the equispaced samples."""
+        return 2 * np.pi * np.mean(g, axis=axis)
+
+    def clenshaw_curtis_r(self, h, axis=AX_R):
+        """int_{R1}^{R2} h dr: integrate the Chebyshev interpolant exactly."""
+        c = _along(self.cheb_S, h, axis)
+        k = np.arange(self.Nr)
+        Ik = np.zeros(self.Nr)
+        Ik[0::2] = 2.0 / (1.0 - k[0::2].astype(float) ** 2)
+        return 0.5 * (self.R2 - self.R1) * np.tensordot(c, Ik, axes=([axis], [0]))
+
+    def sphere_integral(self, F):
+        """int F dOmega = int_0^pi sin Th dTh int_0^{2pi} dPh F  over the last two axes."""
+        return self.fejer_integral(self.trapezoid_periodic(F, -1), -1)
+
+    def scattering_mean(self, F):
+        """J = (1/4pi) int F dOmega, shape [g][r][th][ph]."""
+        return self.sphere_integral(F) / (4 * np.pi)
+
+    def quadrature_weights_direction(self):
+        """q[k][m] with J = sum q F: obtained by applying scattering_mean to
+        unit vectors (the functional's own coefficients)."""
+        q = np.zeros((self.NT, self.NP))
+        for kk in range(self.NT):
+            for m in range(self.NP):
+                e = np.zeros((self.NT, self.NP))
+                e[kk, m] = 1.0
+                q[kk, m] = self.sphere_integral(e) / (4 * np.pi)
+        return q
+
+    # ------------------------------------------------------------ boundaries
+    def inflow_mask(self):
+        """True at (r, Th) inflow nodes: r = R1 for cos Th > 0, r = R2 otherwise (Sect. 4.2)."""
+        m = np.zeros((self.Nr, self.NT), dtype=bool)
+        h = self.NT // 2
+        m[0, :h] = np.cos(self.Theta[:h]) > 0
+        m[-1, h:] = np.cos(self.Theta[h:]) < 0
+        return m
+
+    def apply_inflow(self, F, g_R1=None, g_R2=None):
+        F = F.copy()
+        h = self.NT // 2
+        F[:, 0, :, :, :h, :] = 0.0 if g_R1 is None else g_R1
+        F[:, -1, :, :, h:, :] = 0.0 if g_R2 is None else g_R2
+        return F
+
+    def _inflow_node_index(self):
+        return np.where(np.cos(self.Theta) > 0, 0, self.Nr - 1)
+
+    def tau(self, K, gdot=0.0):
+        """Tau boundary condition (Sect. 5.1): per r-line replace the top
+        Chebyshev coefficient of K so that K at the inflow node = gdot."""
+        c = self.cheb_coeffs(K)
+        out_c = c.copy()
+        N = self.Nr - 1
+        b_of_k = self._inflow_node_index()
+        for kk in range(self.NT):
+            b = b_of_k[kk]
+            Tb = self.cheb_V[b, :]                         # T_k(x_b)
+            cl = c[:, :, :, :, kk, :]                      # [g][k][th][ph][Ph]
+            val = np.tensordot(Tb, cl, axes=([0], [1]))    # K at x_b
+            out_c[:, N, :, :, kk, :] += (gdot - val) / Tb[N]
+        return self.cheb_values(out_c)
+
+    def tau_T(self, mu):
+        """Transpose of the linear part of tau."""
+        N = self.Nr - 1
+        m = _along(self.cheb_V.T, mu, AX_R)                # adjoint in coefficient space
+        b_of_k = self._inflow_node_index()
+        out = m.copy()
+        for kk in range(self.NT):
+            b = b_of_k[kk]
+            Tb = self.cheb_V[b, :]
+            top = m[:, N, :, :, kk, :] / Tb[N]             # [g][th][ph][Ph]
+            out[:, :, :, :, kk, :] -= Tb.reshape(1, -1, 1, 1, 1) * top[:, None]
+        return _along(self.cheb_S.T, out, AX_R)
+
+    # ---------------------------------------------------------- filter
+    def filter(self, F, alpha=36.0, order=16):
+        """Exponential filter sigma(k) = exp(-alpha (k/k_max)^order) applied
+        per axis in coefficient space (r, th, ph, Th, Ph)."""
+        N = self.Nr - 1
+        sig_r = np.exp(-alpha * (np.arange(self.Nr) / N) ** order)
+        c = self.cheb_coeffs(F)
+        F = self.cheb_values(c * sig_r.reshape(1, -1, 1, 1, 1, 1))
+        def circ(f, axis, kmax):
+            return self._fourier_filter(f, axis, lambda k: np.exp(-alpha * (k / kmax) ** order))
+        ext = self._extend(F, AX_TH, self._partner_th(F))
+        F = np.take(circ(ext, AX_TH, self.Nt), np.arange(self.Nt), axis=AX_TH)
+        F = circ(F, AX_PH, self.Np // 2)
+        ext = self._extend(F, AX_TTH, self._partner_Th(F))
+        F = np.take(circ(ext, AX_TTH, self.NT), np.arange(self.NT), axis=AX_TTH)
+        F = circ(F, AX_TPH, self.NP // 2)
+        return F
+
+    # ------------------------------------------------------------- moments
+    def moments(self, F):
+        """F0 = J, F1 = (1/4pi) int F omega dOmega (Cartesian components,
+        Eqs. omegax-omegaz and Fmom0), particle number N (Eq. Npho, with the
+        missing dTheta restored) and the radial fluxes J_R1, J_R2 (Eq. Flux)."""
+        th = self.theta.reshape(-1, 1, 1, 1)
+        ph = self.phi.reshape(1, -1, 1, 1)
+        Th = self.Theta.reshape(1, 1, -1, 1)
+        Ph = self.Phi.reshape(1, 1, 1, -1)
+        ox = (np.cos(Th) * np.sin(th) * np.cos(ph) + np.sin(Th) * np.cos(Ph) * np.cos(th) * np.cos(ph)
+              - np.sin(Th) * np.sin(Ph) * np.sin(ph))
+        oy = (np.cos(Th) * np.sin(th) * np.sin(ph) + np.sin(Th) * np.cos(Ph) * np.cos(th) * np.sin(ph)
+              + np.sin(Th) * np.sin(Ph) * np.cos(ph))
+        oz = np.cos(Th) * np.cos(th) - np.sin(Th) * np.cos(Ph) * np.sin(th)
+        F0 = self.scattering_mean(F)
+        F1 = np.stack([self.scattering_mean(F * o) for o in (ox, oy, oz)])
+        n_dir = self.sphere_integral(F)                                  # [g][r][th][ph]
+        n_pos = self.fejer_integral(self.trapezoid_periodic(n_dir, -1), -1)   # [g][r]
+        r2 = (self.r ** 2)[None, :]
+        Nnum = self.clenshaw_curtis_r(r2 * n_pos, axis=1)
+        cosTh = np.cos(self.Theta).reshape(1, 1, 1, -1, 1)
+        def flux(i, R):
+            f = self.sphere_integral(F[:, i] * cosTh)                    # [g][th][ph]
+            return R ** 2 * self.fejer_integral(self.trapezoid_periodic(f, -1), -1)
+        return F0, F1, Nnum, flux(0, self.R1), flux(-1, self.R2)
+
+    def outgoing_flux_weights(self):
+        """w such that J_R2 = sum over [th][ph][Th][Ph] of w * F(R2, ...):
+        the functional's coefficients, from unit vectors."""
+        Nt, Np, NT, NP = self.Nt, self.Np, self.NT, self.NP
+        w = np.zeros((Nt, Np, NT, NP))
+        # separable: R2^2 * q_th[j] * (2pi/Np) * q_Th[k] cos Th_k * (2pi/NP)
+        qt = np.array([self.fejer_integral(np.eye(Nt)[j], 0) for j in range(Nt)])
+        qT = np.array([self.fejer_integral(np.eye(NT)[k], 0) for k in range(NT)])
+        w = (self.R2 ** 2 * qt[:, None, None, None] * (2 * np.pi / Np)
+             * (qT * np.cos(self.Theta))[None, None, :, None] * (2 * np.pi / NP)
+             * np.ones((Nt, Np, NT, NP)))
+        return w
+
+
+class Problem:
+    """Grid + coefficient fields + boundary data + scheme options."""
+
+    def __init__(self, grid, kappa=None, eta=None, kappa_s=None, g_R1=None, g_R2=None,
+                 bc="tau", scheme="rk4", filter_on=False, filter_alpha=36.0, filter_order=16):
+        self.g = grid
+        z = np.zeros((grid.G, grid.Nr, grid.Nt, grid.Np))
+        self.kappa = z if kappa is None else np.asarray(kappa, dtype=np.float64)
+        self.eta = z if eta is None else np.asarray(eta, dtype=np.float64)
+        self.kappa_s = z if kappa_s is None else np.asarray(kappa_s, dtype=np.float64)
+        self.g_R1, self.g_R2 = g_R1, g_R2
+        self.bc, self.scheme = bc, scheme
+        self.filter_on, self.filter_alpha, self.filter_order = filter_on, filter_alpha, filter_order
+
+    def _c(self, a):
+        return a[..., None, None]
+
+    def collision(self, F):
+        J = self.g.scattering_mean(F)[..., None, None]
+        return self._c(self.eta) - self._c(self.kappa) * F + self._c(self.kappa_s) * (J - F)
+
+    def rhs(self, F, streaming_only=False):
+        """One stage derivative K = Tau(-L F + CT) (Eq. Transpfpsph)."""
+        K = -self.g.liouville(F)
+        if not streaming_only:
+            K = K + self.collision(F)
+        if self.bc == "tau":
+            K = self.g.tau(K)
+        return K
+
+    def apply_inflow(self, F):
+        return self.g.apply_inflow(F, self.g_R1, self.g_R2)
+
+    def rk4_step(self, F, dt, streaming_only=False, keep_stages=False):
+        """Classical RK4: U1 = F, U2 = F + dt/2 K1, U3 = F + dt/2 K2, U4 = F + dt K3,
+        F_new = F + dt/6 (K1 + 2 K2 + 2 K3 + K4)."""
+        U1 = F
+        K1 = self.rhs(U1, streaming_only)
+        U2 = F + 0.5 * dt * K1
+        K2 = self.rhs(U2, streaming_only)
+        U3 = F + 0.5 * dt * K2
+        K3 = self.rhs(U3, streaming_only)
+        U4 = F + dt * K3
+        K4 = self.rhs(U4, streaming_only)
+        Fn = F + (dt / 6.0) * (K1 + 2 * K2 + 2 * K3 + K4)
+        if keep_stages:
+            return Fn, (U1, U2, U3, U4)
+        return Fn
+
+    def implicit_collision(self, Fs, dt):
+        """Backward Euler for dF/dt = CT solved in closed form:
+        J+ = (J* + dt eta)/(1 + dt kappa),
+        F+ = (F* + dt (eta + kappa_s J+))/(1 + dt (kappa + kappa_s))."""
+        Js = self.g.scattering_mean(Fs)
+        Jp = (Js + dt * self.eta) / (1.0 + dt * self.kappa)
+        Fp = ((Fs + dt * self._c(self.eta + self.kappa_s * Jp))
+              / self._c(1.0 + dt * (self.kappa + self.kappa_s)))
+        return Fp
+
+    def step(self, F, dt):
+        if self.scheme == "rk4":
+            Fn = self.rk4_step(F, dt)
+        elif self.scheme == "split":
+            Fs = self.rk4_step(F, dt, streaming_only=True)
+            Fn = self.implicit_collision(Fs, dt)
+            if self.bc == "tau":
+                Fn = self.apply_inflow(Fn)
+        else:
+            raise ValueError(self.scheme)
+        if self.filter_on:
+            Fn = self.g.filter(Fn, self.filter_alpha, self.filter_order)
+        return Fn
+
+    def run(self, F, dt, nsteps):
+        for _ in range(nsteps):
+            F = self.step(F, dt)
+        return F
+
+    # ------------------------------------------------------------- adjoint
+    def _A_T(self, lam):
+        """Transpose of the linear stage operator U -> -L U - kappa U + kappa_s (J(U) - U)."""
+        q = self._q
+        s = np.sum(self._c(self.kappa_s) * lam, axis=(-2, -1), keepdims=True)
+        return (-self.g.liouville_T(lam) - self._c(self.kappa) * lam
+                + q * s - self._c(self.kappa_s) * lam)
+
+    def adjoint_step(self, F_n, lam, dt):
+        """Discrete adjoint of one RK4 step (plain RK4 scheme, filter off).
+
+        Given F_n and lam = dObj/dF_{n+1}, returns (lam_n, g_kappa, g_eta) where
+        lam_n = (dF_{n+1}/dF_n)^T lam and g_kappa, g_eta ([g][r][th][ph]) are the
+        contributions of this step to dObj/dkappa and dObj/deta."""
+        if self.scheme != "rk4" or self.filter_on:
+            raise NotImplementedError("adjoint covers the plain RK4 step")
+        self._q = self.g.quadrature_weights_direction()
+        _, U = self.rk4_step(F_n, dt, keep_stages=True)
+        w = np.array([1.0, 2.0, 2.0, 1.0]) * dt / 6.0
+        gk = np.zeros_like(self.kappa)
+        ge = np.zeros_like(self.eta)
+        lam_n = lam.copy()
+        Ubar_next = None
+        for s in (3, 2, 1, 0):
+            Kbar = w[s] * lam
+            if s == 3:
+                pass
+            elif s == 2:
+                Kbar = Kbar + dt * Ubar_next
+            else:
+                Kbar = Kbar + 0.5 * dt * Ubar_next
+            lt = self.g.tau_T(Kbar) if self.bc == "tau" else Kbar
+            ge += lt.sum(axis=(-2, -1))
+            gk -= (lt * U[s]).sum(axis=(-2, -1))
+            Ubar = self._A_T(lt)
+            lam_n = lam_n + Ubar
+            Ubar_next = Ubar
+        return lam_n, gk, ge
+
+
+def exact_free_streaming(grid, F0_of, t):
+    """Exact vacuum solution with zero inflow (rays are straight lines, Eq. Tra1):
+    F(t, x, omega) = F0(x - t omega, omega) if the segment {x - s omega, 0<=s<=t}
+    stays inside R1 <= |.| <= R2, else 0. F0_of(r, cosTheta) must be independent
+    of theta, phi, Phi. Returns [Nr][NTheta]."""
+    r = grid.r[:, None]
+    mu = np.cos(grid.Theta)[None, :]
+    rp2 = r ** 2 - 2 * r * t * mu + t ** 2
+    rp = np.sqrt(np.maximum(rp2, 0.0))
+    mup = (r * mu - t) / np.where(rp > 0, rp, 1.0)
+    # closest approach to the origin along the back-traced segment
+    s_star = r * mu                                    # parameter of closest approach
+    inside_seg = (s_star > 0) & (s_star < t)
+    dmin = np.where(inside_seg, r * np.sqrt(np.maximum(1 - mu ** 2, 0.0)), np.minimum(r, rp))
+    ok = (rp <= grid.R2 * (1 + 1e-14)) & (dmin >= grid.R1 * (1 - 1e-14))
+    return np.where(ok, F0_of(rp, mup), 0.0)

@@ -1,0 +1,491 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each pin compares the oracle with something other than itself: SymPy's symbolic
+derivatives of Cartesian polynomials (Eqs. Liouvsph, prop2, propf), numpy's
+Chebyshev-series routines, closed-form integrals, the closed-form RK4
+isotropisation solution, the exact free-streaming solution, the paper's own
+printed conservation figure (tests/golden/paper_values.txt) and central finite
+differences for the adjoint. ``test_planted_mistakes`` checks that plausible
+mistakes in the oracle make at least one pin fail.
+"""
+import math
+import os
+
+import numpy as np
+import numpy.polynomial.chebyshev as npcheb
+import pytest
+
+import analytic as A
+from oracle.transport import Grid, Problem, exact_free_streaming
+from paper_1104_5330_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
+
+
+def golden(key):
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()[:2]
+                if k == key:
+                    return float(v)
+    raise KeyError(key)
+
+
+# ---------------------------------------------------------------- pin helpers
+def pin_liouville(grid, cases=("x", "z", "wx", "wy*wz", "xy+wz", "x*wy-z^2", "cubic")):
+    """max relative error of L_h P against omega.grad P (SymPy) over cases."""
+    worst = 0.0
+    for name in cases:
+        P, adv = A.cartesian_case(name)
+        F = A.on_grid(P, grid)
+        E = A.on_grid(adv, grid)
+        err = np.abs(grid.liouville(F) - E).max() / max(1.0, np.abs(E).max())
+        worst = max(worst, err)
+    return worst
+
+
+def pin_axis_derivatives(grid):
+    P, _ = A.cartesian_case("cubic")
+    F = A.on_grid(P, grid)
+    errs = []
+    for f, d in zip([grid.d_r, grid.d_th, grid.d_ph, grid.d_Th, grid.d_Ph], A.spherical_derivatives(P)):
+        E = A.on_grid(d, grid)
+        errs.append(np.abs(f(F) - E).max() / max(1.0, np.abs(E).max()))
+    return max(errs)
+
+
+def pin_isotropisation(nsteps=12, dt=0.01, ks=0.7):
+    """F0 = (1 + 2 wx + wy + wz/2)^4 (Sect. 5.2, on the full sphere), scattering
+    only: the discrete solution is J + (F0 - J) R(-ks dt)^n with the RK4
+    polynomial R and J the exact sphere mean 1 + 2|a|^2 + |a|^4/5, |a|^2 = 21/4."""
+    g = Grid(0.2, 1.0, 5, 8, 12, 8, 12)
+    P, _ = A.cartesian_case("iso4")
+    F = A.on_grid(P, g)
+    pr = Problem(g, kappa_s=np.full((1, 5, 8, 12), ks), bc="none")
+    Fn = pr.run(F, dt, nsteps)
+    a2 = 21.0 / 4.0
+    J = 1 + 2 * a2 + a2 ** 2 / 5
+    z = -ks * dt
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    ex = J + (F - J) * R ** nsteps
+    N0 = g.moments(F)[2][0]
+    Nn = g.moments(Fn)[2][0]
+    return np.abs(Fn - ex).max() / np.abs(ex).max(), abs(Nn / N0 - 1.0)
+
+
+def pin_tau(grid):
+    """The Tau rule of Sect. 5.1 is fixed by two facts: tau(K) - K is a multiple
+    of T_{Nr-1} in r (checked with numpy's Chebyshev fit) and tau(K) vanishes at
+    the inflow node (r = R1 for cos Th > 0, r = R2 otherwise)."""
+    rng = np.random.default_rng(5)
+    K = rng.standard_normal(grid.shape)
+    T = grid.tau(K)
+    D = (T - K)[0]                      # [r][th][ph][Th][Ph]
+    lines = np.moveaxis(D, 0, -1).reshape(-1, grid.Nr)
+    coef = npcheb.chebfit(grid.xr, lines.T, grid.Nr - 1)    # [Nr][lines]
+    low = np.abs(coef[:-1]).max() / max(1.0, np.abs(coef[-1]).max())
+    h = grid.NT // 2
+    bnd = max(np.abs(T[0, 0, :, :, :h, :]).max(), np.abs(T[0, -1, :, :, h:, :]).max())
+    return max(low, bnd / np.abs(K).max())
+
+
+def pin_free_streaming(Nr, NT, T=0.1):
+    g = Grid(0.2, 1.0, Nr, 4, 4, NT, 4)
+    F0f = lambda rr, mu: np.exp(-((rr - 0.6) / 0.1) ** 2) * (1 + 0.5 * mu)
+    F = I.gaussian_shell(g.r, g.theta, g.phi, g.Theta, g.Phi)
+    pr = Problem(g)
+    F = pr.apply_inflow(F)
+    dt = I.dt_rule(0.2, 1.0, Nr)
+    n = int(round(T / dt))
+    Fn = pr.run(F, dt, n)
+    ex = exact_free_streaming(g, F0f, n * dt)
+    return np.abs(Fn[0, :, 0, 0, :, 0] - ex).max()
+
+
+def pin_conservation(grid):
+    """Sect. App. A: for data the grid resolves, N(dF/dt) + J_R2 - J_R1 = 0 with
+    scattering only (no Tau, so the balance is the divergence theorem)."""
+    F = I.seeded_smooth(grid.r, grid.theta, grid.phi, grid.Theta, grid.Phi, 7, grid.R1, grid.R2)[None]
+    ks = np.full((1, grid.Nr, grid.Nt, grid.Np), 0.5)
+    pr = Problem(grid, kappa_s=ks, bc="none")
+    K = pr.rhs(F)
+    _, _, NK, _, _ = grid.moments(K)
+    _, _, NF, J1, J2 = grid.moments(F)
+    return abs(NK[0] + J2[0] - J1[0]) / (abs(J1[0]) + abs(J2[0]) + abs(NF[0]))
+
+
+def pin_adjoint_fd(nsteps=4, seed=3):
+    g = Grid(0.2, 1.0, 9, 6, 8, 6, 8, groups=2)
+    kap, eta, ks = I.gradient_fields(g.r, g.theta, g.phi, 2, 1104, 0.2, 1.0)
+    F0 = np.stack([I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 1104 + k, 0.2, 1.0) for k in range(2)])
+    gR1, gR2 = I.inflow_from(F0, g.NT)
+    dt = I.dt_rule(0.2, 1.0, g.Nr)
+    w = g.outgoing_flux_weights()
+
+    def obj(k, e):
+        p = Problem(g, k, e, ks, gR1, gR2)
+        return np.sum(w * p.run(F0, dt, nsteps)[:, -1])
+
+    pr = Problem(g, kap, eta, ks, gR1, gR2)
+    Fs = [F0]
+    for _ in range(nsteps):
+        Fs.append(pr.rk4_step(Fs[-1], dt))
+    lam = np.zeros(g.shape)
+    lam[:, -1] = w
+    GK = np.zeros_like(kap)
+    GE = np.zeros_like(eta)
+    for i in range(nsteps - 1, -1, -1):
+        lam, gk, ge = pr.adjoint_step(Fs[i], lam, dt)
+        GK += gk
+        GE += ge
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for G_, which in ((GK, 0), (GE, 1)):
+        for _ in range(2):
+            v = I.seeded_smooth(g.r, g.theta, g.phi, None, None, int(rng.integers(1 << 30)),
+                                0.2, 1.0, with_direction=False)[None].repeat(2, 0)
+            eps = 1e-5 * np.linalg.norm(kap) / np.linalg.norm(v)
+            if which == 0:
+                fd = (obj(kap + eps * v, eta) - obj(kap - eps * v, eta)) / (2 * eps)
+            else:
+                fd = (obj(kap, eta + eps * v) - obj(kap, eta - eps * v)) / (2 * eps)
+            worst = max(worst, abs(fd - np.sum(G_ * v)) / max(abs(fd), 1e-30))
+    return worst
+
+
+# ---------------------------------------------------------------------- tests
+def test_chebyshev_transform_round_trip():
+    g = Grid(0.2, 1.0, 17, 4, 4, 4, 4)
+    assert np.abs(g.cheb_S @ g.cheb_V - np.eye(17)).max() < 1e-14
+    assert np.abs(g.cheb_V @ g.cheb_S - np.eye(17)).max() < 1e-14
+    # coefficients agree with numpy's Chebyshev interpolation of the same samples
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal(17)
+    c_np = npcheb.chebfit(g.xr, f, 16)
+    assert np.abs(g.cheb_S @ f - c_np).max() < 1e-12
+
+
+def test_radial_derivative_exact_on_polynomials():
+    g = Grid(0.2, 1.0, 9, 4, 4, 4, 4)
+    # p(r) of degree 8 = Nr - 1; derivative by numpy's polynomial class
+    p = np.polynomial.Polynomial([0.3, -1.2, 2.0, 0.7, -0.4, 1.1, -0.9, 0.5, 0.25])
+    F = np.broadcast_to(p(g.r)[None, :, None, None, None, None], g.shape)
+    E = p.deriv()(g.r)
+    err = np.abs(g.d_r(F)[0, :, 0, 0, 0, 0] - E).max() / np.abs(E).max()
+    assert err < 1e-13
+
+
+def test_axis_derivatives_exact_on_band_limited_data():
+    assert pin_axis_derivatives(Grid(0.2, 1.0, 9, 8, 8, 8, 8)) < 1e-13
+    assert pin_axis_derivatives(Grid(0.4, 1.3, 7, 6, 10, 8, 6)) < 1e-13
+
+
+def test_liouville_equals_omega_dot_grad():
+    """L_h P = omega . grad P (footnote to Eq. prop2; L x_i = omega_i, L omega_i = 0)."""
+    assert pin_liouville(Grid(0.2, 1.0, 9, 8, 8, 8, 8)) < 1e-12
+    assert pin_liouville(Grid(0.5, 2.0, 6, 6, 8, 10, 8)) < 1e-12
+
+
+def test_liouville_of_direction_only_function_vanishes():
+    """Eq. (propf): L F(omega) = 0, with the paper's test function (Sect. 5.2)."""
+    g = Grid(0.2, 1.0, 5, 8, 12, 8, 12)
+    P, _ = A.cartesian_case("iso4")
+    F = A.on_grid(P, g)
+    assert np.abs(g.liouville(F)).max() / np.abs(F).max() < 1e-12
+
+
+def test_isotropisation_closed_form_and_paper_conservation():
+    err, dN = pin_isotropisation()
+    assert err < 1e-13
+    # Sect. 5.2: relative particle-number error below 5e-15 in double precision
+    assert dN < golden("isotropisation_number_error_max")
+
+
+def test_quadratures_exact():
+    g = Grid(0.2, 1.0, 9, 8, 8, 8, 8)
+    # Fejer: int_0^pi cos^n t sin t dt = 2/(n+1) (n even), 0 (n odd), n <= N-1
+    for n in range(8):
+        val = Grid.fejer_integral(np.cos(g.Theta) ** n, 0)
+        ex = 2.0 / (n + 1) if n % 2 == 0 else 0.0
+        assert abs(val - ex) < 1e-14
+    # Clenshaw-Curtis: int_R1^R2 r^n dr, n <= Nr - 1
+    for n in range(9):
+        val = g.clenshaw_curtis_r(g.r ** n, axis=0)
+        assert abs(val - (1.0 ** (n + 1) - 0.2 ** (n + 1)) / (n + 1)) < 1e-14
+    # trapezoid exact for band-limited periodic data
+    assert abs(Grid.trapezoid_periodic(np.cos(g.Phi) ** 2, 0) - math.pi) < 1e-14
+
+
+def test_moments_two_moment_form():
+    """App. C, Eq. (Fmom0): F = F0 + 3 F1 . omega returns F0 and F1 exactly;
+    N (Eq. Npho) and the radial fluxes (Eq. Flux) of that F in closed form."""
+    g = Grid(0.2, 1.0, 7, 6, 8, 6, 8)
+    F0v, F1v = 0.8, np.array([0.3, -0.2, 0.45])
+    ox, oy, oz = I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi)
+    F = np.broadcast_to(F0v + 3 * (F1v[0] * ox + F1v[1] * oy + F1v[2] * oz), g.shape[2:])
+    F = np.ascontiguousarray(np.broadcast_to(F, g.shape))
+    m0, m1, N, J1, J2 = g.moments(F)
+    assert np.abs(m0 - F0v).max() < 1e-14
+    for c in range(3):
+        assert np.abs(m1[c] - F1v[c]).max() < 1e-14
+    assert abs(N[0] - F0v * 16 * math.pi ** 2 * (1.0 - 0.2 ** 3) / 3) < 1e-12
+    # F = F0 + 3 F1.omega integrates over the sphere with cos Th to (4 pi) F1.rhat;
+    # over all positions of a sphere, F1.rhat integrates to 0 for constant F1.
+    assert abs(J1[0]) < 1e-13 and abs(J2[0]) < 1e-13
+    Fc = np.ascontiguousarray(np.broadcast_to(1.0 + 0.6 * np.cos(g.Theta)[:, None], g.shape))
+    _, _, _, J1, J2 = g.moments(Fc)
+    for R, Jv in ((0.2, J1[0]), (1.0, J2[0])):
+        assert abs(Jv - R ** 2 * 4 * math.pi * 2 * math.pi * 0.6 * 2 / 3) < 1e-12
+
+
+def test_homogeneous_steady_state():
+    """F = eta/kappa = c everywhere, inflow c: dF/dt = 0 (Eq. Transp with J = F)."""
+    g = Grid(0.2, 1.0, 9, 6, 8, 6, 8, groups=2)
+    kap, _, ks = I.absorber_fields(g.r, g.theta, g.phi, groups=2)
+    c = 1.7
+    F = np.full(g.shape, c)
+    gR1, gR2 = I.inflow_from(F, g.NT)
+    pr = Problem(g, kap, c * kap, ks, gR1, gR2)
+    assert np.abs(pr.rhs(F)).max() < 1e-13 * c
+    assert np.abs(pr.run(F, 1e-3, 3) - c).max() < 1e-14 * c * 10
+
+
+def test_two_dimensional_reduction():
+    """For F(r, Th) the 5-D right-hand side reduces to Eq. (Sphersy):
+    dF/dt = -cos Th dF/dr + (sin Th / r) dF/dTh + eta - kappa F + kappa_s (J - F),
+    J = (1/2) int F(Th') sin Th' dTh'; derivatives from SymPy."""
+    import sympy as sp
+    g = Grid(0.3, 1.1, 8, 6, 8, 10, 8)
+    expr = (1 + A.r - 0.7 * A.r ** 3) * (0.5 + sp.cos(A.Th) - 0.3 * sp.cos(A.Th) ** 4)
+    F = A.on_grid(expr, g)
+    kap = np.full((1, 8, 6, 8), 1.3)
+    eta = np.full_like(kap, 0.4)
+    ks = np.full_like(kap, 0.6)
+    pr = Problem(g, kap, eta, ks, bc="none")
+    mu = sp.symbols("mu")
+    qint = sp.integrate((0.5 + mu - 0.3 * mu ** 4), (mu, -1, 1)) / 2
+    J = (1 + A.r - 0.7 * A.r ** 3) * qint
+    rhs = (-sp.cos(A.Th) * sp.diff(expr, A.r) + sp.sin(A.Th) / A.r * sp.diff(expr, A.Th)
+           + 0.4 - 1.3 * expr + 0.6 * (J - expr))
+    E = A.on_grid(rhs, g)
+    assert np.abs(pr.rhs(F) - E).max() / np.abs(E).max() < 1e-13
+
+
+def test_tau_rule():
+    assert pin_tau(Grid(0.2, 1.0, 9, 4, 4, 6, 4)) < 1e-11
+
+
+def test_inflow_values_held_by_tau():
+    g = Grid(0.2, 1.0, 9, 6, 8, 6, 8)
+    F = I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 11, 0.2, 1.0)[None]
+    gR1, gR2 = 0.5 * np.ones((1, 6, 8, 3, 8)), -0.25 * np.ones((1, 6, 8, 3, 8))
+    kap, eta, ks = I.absorber_fields(g.r, g.theta, g.phi)
+    pr = Problem(g, kap, eta, ks, gR1, gR2)
+    F = pr.apply_inflow(F)
+    Fn = pr.run(F, I.dt_rule(0.2, 1.0, 9), 3)
+    # Tau fixes dF/dt = 0 at the inflow nodes; the coefficient-form update is exact up to rounding
+    assert np.abs(Fn[:, 0, :, :, :3, :] - 0.5).max() < 1e-13
+    assert np.abs(Fn[:, -1, :, :, 3:, :] + 0.25).max() < 1e-13
+
+
+def test_free_streaming_converges_to_exact_solution():
+    """Vacuum, zero inflow: F(t, x, w) = F0(x - t w, w) (straight rays, Eq. Tra1);
+    the error falls spectrally with (N_r, N_Theta)."""
+    e1 = pin_free_streaming(17, 8)
+    e2 = pin_free_streaming(33, 16)
+    assert e1 < 0.05
+    assert e2 < 2e-6
+    assert e2 < 1e-3 * e1
+
+
+def test_number_balance_divergence_theorem():
+    assert pin_conservation(Grid(0.2, 1.0, 12, 8, 8, 8, 8)) < 1e-12
+
+
+def test_filter_single_modes():
+    """sigma(k) = exp(-36 (k/kmax)^16) multiplies each single mode; k = 0 unchanged."""
+    g = Grid(0.2, 1.0, 9, 8, 8, 8, 8)
+    sig = lambda q: math.exp(-36.0 * q ** 16)
+    for k in range(9):   # T_k(x_r)
+        F = np.broadcast_to(np.cos(k * np.arccos(g.xr))[None, :, None, None, None, None], g.shape)
+        out = g.filter(F)
+        assert np.abs(out - sig(k / 8) * F).max() < 1e-14
+    g = Grid(0.2, 1.0, 9, 8, 16, 8, 16)
+    # cos(k phi) and cos(k Phi) are regular on the sphere (DFS-consistent) only for even k
+    for k in (0, 2, 4, 6):
+        F = np.broadcast_to(np.cos(k * g.phi)[None, None, None, :, None, None], g.shape)
+        assert np.abs(g.filter(F) - sig(k / 8) * F).max() < 1e-14
+        F = np.broadcast_to(np.cos(k * g.Phi)[None, None, None, None, None, :], g.shape)
+        assert np.abs(g.filter(F) - sig(k / 8) * F).max() < 1e-14
+    for k in range(8):   # cos(k theta): mode k of the doubled theta circle
+        F = np.broadcast_to(np.cos(k * g.theta)[None, None, :, None, None, None], g.shape)
+        assert np.abs(g.filter(F) - sig(k / 8) * F).max() < 1e-14
+    for k in range(8):   # cos(k Theta) is DFS-even (F(-Th) = F(Th)): mode k of the doubled circle
+        F = np.broadcast_to(np.cos(k * g.Theta)[None, None, None, None, :, None], g.shape)
+        assert np.abs(g.filter(F) - sig(k / 8) * F).max() < 1e-14
+
+
+def test_implicit_collision_solves_backward_euler():
+    g = Grid(0.2, 1.0, 7, 6, 8, 6, 8)
+    kap, eta, ks = I.absorber_fields(g.r, g.theta, g.phi)
+    kap = kap * 40.0
+    F = I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 3, 0.2, 1.0)[None]
+    pr = Problem(g, kap, eta, ks, scheme="split")
+    dt = 0.05
+    Fp = pr.implicit_collision(F, dt)
+    res = Fp - F - dt * pr.collision(Fp)
+    assert np.abs(res).max() < 1e-14 * np.abs(F).max() * 10
+
+
+def test_adjoint_dot_products():
+    g = Grid(0.2, 1.0, 9, 6, 8, 6, 8, groups=2)
+    rng = np.random.default_rng(1)
+    F = rng.standard_normal(g.shape)
+    mu = rng.standard_normal(g.shape)
+    scale = np.abs(F).sum() * np.abs(mu).sum() / F.size
+    for fwd, bwd in ((g.liouville, g.liouville_T), (g.tau, g.tau_T), (g.d_th, g.d_th_T),
+                     (g.d_Th, g.d_Th_T), (g.d_r, g.d_r_T)):
+        assert abs(np.sum(fwd(F) * mu) - np.sum(F * bwd(mu))) < 1e-12 * scale
+    kap, eta, ks = I.gradient_fields(g.r, g.theta, g.phi, 2, 5, 0.2, 1.0)
+    pr = Problem(g, kap, eta, ks)
+    dt = I.dt_rule(0.2, 1.0, 9)
+    d = rng.standard_normal(g.shape)
+    lam_n, _, _ = pr.adjoint_step(F, mu, dt)
+    lhs = np.sum((pr.rk4_step(F + d, dt) - pr.rk4_step(F, dt)) * mu)
+    assert abs(lhs - np.sum(d * lam_n)) < 1e-11 * abs(lhs)
+
+
+def test_adjoint_matches_finite_differences():
+    assert pin_adjoint_fd() < 1e-6
+
+
+def test_time_step_rule_values():
+    """dt = 0.4 x the smallest radial Gauss-Lobatto spacing."""
+    assert abs(I.dt_rule(0.2, 1.0, 17) - 3.0744e-3) < 1e-7
+    assert abs(I.dt_rule(0.2, 1.0, 33) - 7.704e-4) < 1e-7
+    assert abs(I.dt_rule(0.2, 1.0, 65) - 1.927e-4) < 1e-7
+
+
+# --------------------------------------------------------- planted mistakes
+MUTANTS = {}
+
+
+def mutant(name):
+    def deco(f):
+        MUTANTS[name] = f
+        return f
+    return deco
+
+
+@mutant("sign of the d_Phi term")
+def _m1(mp):
+    orig = Grid.coefficients
+    mp.setattr(Grid, "coefficients", lambda self: (*orig(self)[:4], -orig(self)[4]))
+
+
+@mutant("d_phi term dropped")
+def _m2(mp):
+    orig = Grid.coefficients
+    mp.setattr(Grid, "coefficients", lambda self: (orig(self)[0], orig(self)[1], 0 * orig(self)[2],
+                                                     orig(self)[3], orig(self)[4]))
+
+
+@mutant("DFS partner without the Phi shift")
+def _m3(mp):
+    mp.setattr(Grid, "_partner_th", lambda self, F: np.roll(F, -self.Np // 2, axis=3))
+
+
+@mutant("Chebyshev recurrence without halving b_0")
+def _m4(mp):
+    def bad(a):
+        N = len(a) - 1
+        b = np.zeros(N + 2)
+        for kk in range(N, 0, -1):
+            b[kk - 1] = b[kk + 1] + 2 * kk * a[kk]
+        return b[:N + 1]
+    mp.setattr(Grid, "_cheb_deriv_coef", staticmethod(bad))
+
+
+@mutant("Fejer without halving a_0")
+def _m5(mp):
+    def bad(g, axis):
+        N = g.shape[axis]
+        t = np.pi * (np.arange(N) + 0.5) / N
+        n = np.arange(N)
+        a = np.moveaxis(np.tensordot(np.cos(np.outer(n, t)) * (2.0 / N), g, axes=([1], [axis])), 0, axis)
+        In = np.zeros(N)
+        In[0::2] = 2.0 / (1.0 - n[0::2] ** 2.0)
+        return np.tensordot(a, In, axes=([axis], [0]))
+    mp.setattr(Grid, "fejer_integral", staticmethod(bad))
+
+
+@mutant("inflow side swapped")
+def _m6(mp):
+    mp.setattr(Grid, "_inflow_node_index", lambda self: np.where(np.cos(self.Theta) > 0, self.Nr - 1, 0))
+
+
+@mutant("RK4 weight of K2 = 1")
+def _m7(mp):
+    def bad(self, F, dt, streaming_only=False, keep_stages=False):
+        K1 = self.rhs(F, streaming_only)
+        K2 = self.rhs(F + 0.5 * dt * K1, streaming_only)
+        K3 = self.rhs(F + 0.5 * dt * K2, streaming_only)
+        K4 = self.rhs(F + dt * K3, streaming_only)
+        Fn = F + (dt / 6.0) * (K1 + K2 + 2 * K3 + K4)
+        return (Fn, (F, F, F, F)) if keep_stages else Fn
+    mp.setattr(Problem, "rk4_step", bad)
+
+
+@mutant("scattering sign flipped")
+def _m8(mp):
+    def bad(self, F):
+        J = self.g.scattering_mean(F)[..., None, None]
+        return self._c(self.eta) - self._c(self.kappa) * F - self._c(self.kappa_s) * (J - F)
+    mp.setattr(Problem, "collision", bad)
+
+
+@mutant("transpose of d_r not transposed")
+def _m9(mp):
+    def bad(self, mu):
+        from oracle.transport import _along
+        m = _along(self.cheb_V.T, mu, 1)
+        m = _along(self.cheb_C, m, 1)
+        return _along(self.cheb_S.T, m, 1)
+    mp.setattr(Grid, "d_r_T", bad)
+
+
+@mutant("theta nodes without the half offset")
+def _m10(mp):
+    orig = Grid.__init__
+    def bad(self, *a, **k):
+        orig(self, *a, **k)
+        self.theta = np.pi * np.arange(self.Nt) / self.Nt + 1e-3
+    mp.setattr(Grid, "__init__", bad)
+
+
+def _all_pins_pass():
+    small = Grid(0.2, 1.0, 9, 8, 8, 8, 8)
+    checks = [
+        lambda: pin_liouville(small) < 1e-12,
+        lambda: pin_axis_derivatives(small) < 1e-13,
+        lambda: pin_isotropisation(nsteps=4)[0] < 1e-13,
+        lambda: pin_tau(Grid(0.2, 1.0, 9, 4, 4, 6, 4)) < 1e-11,
+        lambda: pin_free_streaming(17, 8, T=0.05) < 0.05,
+        lambda: pin_conservation(Grid(0.2, 1.0, 12, 8, 8, 8, 8)) < 1e-12,
+        lambda: pin_adjoint_fd(nsteps=2) < 1e-6,
+    ]
+    for c in checks:
+        try:
+            if not c():
+                return False
+        except Exception:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistakes(name, monkeypatch):
+    MUTANTS[name](monkeypatch)
+    assert not _all_pins_pass(), f"no pin caught: {name}"
