@@ -1,0 +1,429 @@
+#!/usr/bin/env python
+"""Benchmark of the 6-D spectral transport step (one JSON line on rank 0).
+
+Workload (default): the absorber problem on the 33 x 16^4 grid with 4 energy
+groups in FP64 -- shell r in [0.2, 1], kappa = 1 + 0.5 sin(theta) cos(phi),
+eta = kappa exp(-r^2), kappa_s = 0.5, seeded smooth initial data, static
+inflow data, dt = 0.4 x the smallest radial node spacing, classical RK4.
+One benchmark step = one RK4 step of every group (12 kernel launches).
+
+Metric: phase-space point-updates per second (grid points x groups x steps /
+device time), timed with CUDA events on the launching stream between a
+barrier + synchronize on both sides, max over ranks. Under torchrun each rank
+runs its own copy of the workload on its own GPU (weak scaling; no collective
+on the data path).
+
+Extra keys: roofline of the dominant kernel (per-launch device time from
+ts_step_profile; FP64 ALU peak derived from the nominal GB300 FP64 rate),
+end-to-end rate through ts_step_host (host buffers, copies inside the timed
+region), the FP32 variant and the adjoint step on the same workload, the CPU
+oracle timed on a bounded sample on this host's cores, and SM clocks sampled
+during the timed region.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "phase-space point-updates/s per GB300 (fwd, adjoint) vs plain FP64 GPU form at stated err"
+WORKLOADS = {
+    # name: (R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups)
+    "absorber_33x16^4_g4": (0.2, 1.0, 33, 16, 16, 16, 16, 4),
+    "absorber_17x8^4_g1": (0.2, 1.0, 17, 8, 8, 8, 8, 1),
+    "absorber_65x32^4_g1": (0.2, 1.0, 65, 32, 32, 32, 32, 1),
+}
+FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 (vector and tensor) rate
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+# ------------------------------------------------------------------ helpers
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("ts_kernels.cuh", "ts_launch.cuh"):
+        with open(os.path.join(ROOT, "paper_1104_5330_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload, precision):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    if the kernels changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    if t.get("kernel_hash") != _kernel_hash():
+        return None
+    return t.get("per_launch_bytes", {}).get(f"{workload}/{precision}/{kernel}")
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ts_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------- algorithmic work
+def pass_work(dims, es):
+    """Algorithmic flops and DRAM bytes per launch of each pass (one stage of
+    all groups). Flops count the dense contractions (2 per multiply-add) and the
+    pointwise terms; bytes count each field the pass must read or write once."""
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    pts = Nr * Nt * Np * NT * NP * G
+    flops = {
+        "angular": pts * (2 * 2 * NT + 2 * NP + 2 + 11),   # dTh (DFS pair), dPh, J, terms+collision
+        "plane": pts * (2 * 2 * Nt + 2 * Np + 8),           # dth (DFS pair), dph, terms
+        "radial": pts * (2 * Nr + 10),                      # dr, term, Tau row, stage update
+    }
+    byts = {
+        "angular": pts * es * 2,        # read U, write K
+        "plane": pts * es * 3,          # read U, read+write K
+        "radial": pts * es * 5,         # read U, K, F, Acc; write U (or F) and Acc: 4-6 fields
+    }
+    return pts, flops, byts
+
+
+# ------------------------------------------------------------- oracle side
+def _oracle_task(args):
+    """One group of the workload on the CPU oracle: `warm` untimed steps, then
+    `nsteps` timed steps. Runs in a spawned process with one BLAS thread."""
+    dims, g, warm, nsteps = args
+    sys.path.insert(0, ROOT)
+    from oracle.transport import Grid, Problem
+    from paper_1104_5330_gb300 import inputs as I
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    og = Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=1)
+    kap, eta, ks = I.absorber_fields(og.r, og.theta, og.phi, groups=1)
+    F = I.seeded_smooth(og.r, og.theta, og.phi, og.Theta, og.Phi, 1104 + g, R1, R2)[None]
+    gR1, gR2 = I.inflow_from(F, NT)
+    pr = Problem(og, kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(R1, R2, Nr)
+    F = pr.run(F, dt, warm)
+    t0 = time.perf_counter()
+    F = pr.run(F, dt, nsteps)
+    return time.perf_counter() - t0, og.points * nsteps
+
+
+def oracle_rate(dims, warm, nsteps):
+    """Point-updates/s of the oracle, one spawned process per group (up to the
+    host's cores), all groups concurrently: the slowest process sets the time."""
+    G = dims[-1]
+    cores = min(G, os.cpu_count() or 1)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_task, [(dims, g, warm, nsteps) for g in range(G)])
+    wall = max(r[0] for r in res)
+    pts = sum(r[1] for r in res)
+    return pts / wall, wall, cores
+
+
+# -------------------------------------------------------------------- runs
+def run_reference(args, dims, wname):
+    rank, _, world = _env_rank()
+    if rank != 0:
+        return 0
+    rate, wall, cores = oracle_rate(dims, args.warmup, args.steps)
+    pts = dims[2] * dims[3] * dims[4] * dims[5] * dims[6] * dims[7]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "point-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded smooth fields)",
+        "config": {"workload": wname, "grid": list(dims[2:7]), "groups": dims[7],
+                   "points_per_step": pts},
+        "cpu_baseline": {"value": rate, "unit": "point-updates/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{args.steps} RK4 steps of every group of {wname} "
+                                   f"(after {args.warmup} untimed), one process per group"},
+        "e2e": {"value": rate, "unit": "point-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, dims, wname):
+    import torch
+    import torch.distributed as dist
+
+    rank, local, world = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1104_5330_gb300 import build as b
+    if rank == 0:
+        b.build()
+    if world > 1:
+        dist.barrier()
+    import paper_1104_5330_gb300.ts as ts
+    from paper_1104_5330_gb300 import inputs as I
+
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    prec = ts.TS_FP64 if args.precision == "fp64" else ts.TS_FP32
+    tdt = torch.float64 if prec == ts.TS_FP64 else torch.float32
+    es = 8 if prec == ts.TS_FP64 else 4
+
+    def make(precision):
+        gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=precision)
+        r, th, ph, Th, Ph = gg.nodes()
+        kap, eta, ks = I.absorber_fields(r, th, ph, groups=G)
+        F0 = np.stack([I.seeded_smooth(r, th, ph, Th, Ph, 1104 + g, R1, R2) for g in range(G)])
+        gR1, gR2 = I.inflow_from(F0, NT)
+        gg.set_coeffs(kap, eta, ks, gR1, gR2)
+        return gg, F0
+
+    gg, F0 = make(prec)
+    dt = I.dt_rule(R1, R2, Nr)
+    pts = gg.points
+    F = torch.as_tensor(F0, dtype=tdt, device="cuda").contiguous()
+    stream = torch.cuda.current_stream()
+
+    def sync_all():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    gg.step(F, dt, args.warmup)
+    sync_all()
+    with ClockSampler(local) as clk:
+        sync_all()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gg.step(F, dt, args.steps)
+        e1.record(stream)
+        sync_all()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = pts * args.steps * world / (ms * 1e-3)
+    launches = 12 * args.steps
+
+    # per-pass device time (CUDA events on the launching stream)
+    nprof = max(2, min(args.steps, 10))
+    pass_ms, pass_n = ts.ts_step_profile(gg.handle, F, dt, nprof)
+    names = ["angular", "plane", "radial"]
+    _, flops, byts = pass_work(dims, es)
+    shares = pass_ms[:3] / pass_ms[:3].sum()
+    dom = int(np.argmax(pass_ms[:3]))
+    dname = names[dom]
+    avg_ms = pass_ms[dom] / pass_n[dom]
+    peaks, peak_src = _peaks()
+    if prec == ts.TS_FP64:
+        achieved = flops[dname] / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": f"k_{dname}<double>", "achieved": achieved,
+                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                "algorithmic_flops_per_launch": flops[dname],
+                "traffic": _traffic(dname, wname, args.precision),
+                "algorithmic_bytes_per_launch": byts[dname],
+                "hbm_achieved_gbs": byts[dname] / (avg_ms * 1e-3) / 1e9}
+    else:
+        achieved = byts[dname] / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": f"k_{dname}<float>", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"{peak_src} hbm_gbs",
+                "algorithmic_bytes_per_launch": byts[dname],
+                "traffic": _traffic(dname, wname, args.precision)}
+    roof["avg_launch_ms"] = avg_ms
+    roof["pass_share"] = {n: float(s) for n, s in zip(names, shares)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "point-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == ts.TS_FP64 else "f32",
+        "data": "synthetic (seeded smooth fields; no dataset)",
+        "config": {"workload": wname, "grid": [Nr, Nt, Np, NT, NP], "groups": G,
+                   "R": [R1, R2], "dt": dt, "scheme": "RK4 + Tau inflow rows",
+                   "points_per_step": pts,
+                   "l2": f"inputs larger than L2: working set {4 * pts * es / 1e6:.0f} MB > 129 MB",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    if not args.skip_e2e:
+        Fh = torch.as_tensor(F0, dtype=tdt).contiguous().pin_memory()
+        ts.ts_step_host(gg.handle, Fh, dt, 1)
+        ne = max(3, min(args.steps, 10))
+        sync_all()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            ts.ts_step_host(gg.handle, Fh, dt, 1)
+        sync_all()
+        te = time.perf_counter() - t0
+        nbytes = pts * es
+        line["e2e"] = {"value": pts * ne * world / te, "unit": "point-updates/s",
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                       "steps": ne, "api": "ts_step_host (pinned host F, one step per call)"}
+
+    # the FP32 variant and the adjoint, same workload (rank 0 reports them)
+    if not args.skip_variants:
+        ref = torch.as_tensor(F0, dtype=torch.float64, device="cuda").contiguous()
+        nv = max(2, min(args.steps, 10))
+        gg.step(ref, dt, nv)
+        g32, _ = make(ts.TS_FP32)
+        F32 = torch.as_tensor(F0, dtype=torch.float32, device="cuda").contiguous()
+        g32.step(F32, dt, nv)
+        err32 = float(torch.linalg.vector_norm(F32.double() - ref) / torch.linalg.vector_norm(ref))
+        F32b = F32.clone()
+        g32.step(F32b, dt, 2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g32.step(F32b, dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1)
+        pm, pn = ts.ts_step_profile(g32.handle, F32b, dt, nv)
+        _, _, by32 = pass_work(dims, 4)
+        d32 = int(np.argmax(pm[:3]))
+        hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
+        line["variants"] = {"fp32": {
+            "value": pts * args.steps / (ms32 * 1e-3), "unit": "point-updates/s",
+            "ms_per_step": ms32 / args.steps,
+            "rel_l2_vs_gpu_fp64": err32, "after_steps": nv,
+            "roofline": {"bound": "hbm", "kernel": f"k_{names[d32]}<float>",
+                         "achieved": hbm32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": hbm32 / peaks["hbm_gbs"],
+                         "pass_share": {n: float(s) for n, s in zip(names, pm[:3] / pm[:3].sum())}}}}
+        del g32, F32, F32b
+        lam = torch.randn_like(F)
+        gk = torch.zeros(gg.coef_shape, dtype=torch.float64, device="cuda")
+        ge = torch.zeros_like(gk)
+        gg.adjoint_step(F, lam, gk, ge, dt)
+        torch.cuda.synchronize()
+        na = max(2, min(args.steps, 5))
+        e0.record(stream)
+        for _ in range(na):
+            gg.adjoint_step(F, lam, gk, ge, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msa = e0.elapsed_time(e1)
+        line["adjoint"] = {"value": pts * na / (msa * 1e-3), "unit": "point-updates/s",
+                           "ms_per_step": msa / na, "dtype": "f64",
+                           "includes": "forward recomputation of the stage inputs"}
+
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        rate, wall, cores = oracle_rate(dims, 0, 1)
+        line["cpu_baseline"] = {"value": rate, "unit": "point-updates/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"1 RK4 step of each of the {G} groups of {wname} "
+                                          f"({wall:.1f} s wall, one process per group)"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="absorber_33x16^4_g4")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-variants", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)      # timing rule: at least 3 untimed steps
+    dims = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, dims, args.workload)
+    return run_ours(args, dims, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * ts.h -- C ABI of the GB300 library for one time step of the 6-D spectral
+ * transport method of Bonazzola, Vasset & Peres (A&A 2011, "Solving the
+ * transport equation by the use of 6D spectral methods in spherical
+ * coordinates").
+ *
+ * The step advances the distribution function F(r, theta, phi, Theta, Phi)
+ * of one or more independent energy groups under
+ *     dF/dt + L_sph F = CT                                   (Eq. Transpfpsph, Sect. 4.1)
+ *     L_sph = cos(Th) d_r + (1/r)[ sin(Th)cos(Ph) d_th + sin(Th)sin(Ph)/sin(th) d_ph
+ *                                  - sin(Th) d_Th - sin(Th)sin(Ph) cot(th) d_Ph ]
+ *                                                            (Eq. Liouvsph, Sect. 4.1)
+ *     CT = eta - kappa F + kappa_s (J - F),  J = (1/4 pi) int F dOmega
+ *          (Eq. Transp, Sect. 2.2, with the isotropic kernel of Eq. sigman, B = 0,
+ *           coherent scattering Eq. sigmadif so that groups decouple)
+ * with spectral derivatives on every axis (Sect. 5.1): Chebyshev in r on
+ * Gauss-Lobatto nodes, double-Fourier-sphere parity Fourier series on the
+ * pole-free nodes th_j = pi (j+1/2)/N_theta and Th_k = pi (k+1/2)/N_Theta,
+ * Fourier in phi and Phi; inflow boundaries by the Tau method (Sect. 5.1;
+ * inflow at R1 where cos Theta > 0, at R2 where cos Theta < 0, Sect. 4.2);
+ * classical RK4 in time.
+ *
+ * Conventions shared by every entry point
+ *  - Layout of a field F: F[g][i_r][j_theta][l_phi][k_Theta][m_Phi], row-major,
+ *    Phi fastest. Coefficient fields (kappa, eta, kappa_s, gradients, moments):
+ *    [g][i_r][j_theta][l_phi]. Inflow data: g_R1[g][j][l][k < NTheta/2][m]
+ *    (cos Theta > 0), g_R2[g][j][l][k - NTheta/2][m] (cos Theta < 0).
+ *  - Element type: double for TS_FP64 grids; float for every other precision.
+ *    Coefficient fields, gradients and moments are always double.
+ *  - Pointers are DEVICE pointers unless the name ends in _host. The caller
+ *    owns every pointer it passes; the library owns the grid (tables and
+ *    workspace) from ts_create_grid to ts_destroy_grid.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Calls are asynchronous on that stream unless stated otherwise.
+ *  - Argument errors are returned synchronously and leave the device state
+ *    untouched. Launch errors are returned as TS_ERR_CUDA. The text of the
+ *    last error of the calling thread is returned by ts_last_error().
+ *  - Supported sizes: 3 <= Nr <= 129; 2 <= Ntheta <= 64; Nphi, NTheta, NPhi
+ *    even and 2..64; groups >= 1. Otherwise TS_ERR_UNSUPPORTED.
+ */
+#ifndef TS_H_
+#define TS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TS_OK = 0,
+  TS_ERR_ARG = 1,          /* null pointer, non-finite dt, wrong size */
+  TS_ERR_UNSUPPORTED = 2,  /* valid request this build does not offer */
+  TS_ERR_OOM = 3,          /* device allocation failed */
+  TS_ERR_CUDA = 4,         /* a CUDA call or launch failed */
+  TS_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+  TS_ERR_STATE = 6         /* call order violated (e.g. step before coefficients) */
+} ts_status;
+
+typedef enum {
+  TS_FP64 = 0,     /* double storage, double arithmetic */
+  TS_FP32 = 1      /* float storage, float arithmetic; the radial derivative rows
+                      nearest r = R1 and r = R2 are accumulated in double */
+} ts_precision;
+
+typedef enum {
+  TS_RK4 = 0,                /* classical RK4 on -L F + CT */
+  TS_RK4_SPLIT_IMPLICIT = 1  /* RK4 on -L F, then backward-Euler collision step
+                                (closed form), then F = inflow data at inflow nodes
+                                (implicit first-order source step of App. B) */
+} ts_scheme;
+
+typedef enum {
+  TS_BC_TAU_INFLOW = 0,  /* Tau inflow condition on every stage derivative */
+  TS_BC_NONE = 1         /* no boundary rows (operator tests, closed domains) */
+} ts_bc;
+
+typedef struct {
+  double R1, R2;                            /* shell radii, 0 < R1 < R2 */
+  int Nr, Ntheta, Nphi, NTheta, NPhi;       /* nodes per axis */
+  int groups;                               /* independent energy groups */
+  int precision;                            /* ts_precision */
+  int scheme;                               /* ts_scheme */
+  int bc;                                   /* ts_bc */
+  int filter_on;                            /* 1: exponential filter after each step */
+  double filter_alpha;                      /* sigma(k) = exp(-alpha (k/kmax)^order) */
+  int filter_order;
+} ts_grid_desc;
+
+typedef struct ts_grid ts_grid;             /* opaque, library-owned */
+
+/* Create a grid: builds the node, differentiation, quadrature and filter
+ * tables on the host (Sect. 5.1 bases), uploads them, and allocates the
+ * workspace (three fields of the grid's element type plus small buffers) on
+ * the current device. Synchronous. *out is NULL on failure. */
+ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out);
+
+/* Free the grid's tables and workspace. Synchronizes the device first. */
+ts_status ts_destroy_grid(ts_grid* grid);
+
+/* Host copies of the nodes: r[Nr] (Chebyshev-Gauss-Lobatto on [R1,R2],
+ * ascending), theta[Ntheta], phi[Nphi], Theta[NTheta], Phi[NPhi]. Any pointer
+ * may be NULL. Synchronous, host memory only. */
+ts_status ts_grid_nodes(const ts_grid* grid, double* r_host, double* theta_host,
+                        double* phi_host, double* Theta_host, double* Phi_host);
+
+/* Number of elements of one field (groups * Nr * Ntheta * Nphi * NTheta * NPhi). */
+size_t ts_field_elems(const ts_grid* grid);
+
+/* Set the absorption kappa, emissivity eta and isotropic scattering kappa_s
+ * (Eq. Transp with the density folded in), each [G][Nr][Ntheta][Nphi]
+ * double, and the static inflow data g_R1, g_R2 (layout above, element type
+ * of the grid). Any pointer may be NULL, meaning zero. Values are copied into
+ * the grid (device to device on `stream`). */
+ts_status ts_set_coeffs(ts_grid* grid, const double* kappa, const double* eta,
+                        const double* kappa_s, const void* inflow_R1,
+                        const void* inflow_R2, void* stream);
+
+/* Set F = inflow data at the inflow nodes (r = R1 with cos Theta > 0, r = R2
+ * with cos Theta < 0). Call once on initial data: the Tau rows of ts_step
+ * then keep those values fixed. */
+ts_status ts_apply_inflow(ts_grid* grid, void* F, void* stream);
+
+/* Advance F (in place) by `nsteps` steps of size dt with the grid's scheme,
+ * boundary rows and filter. Requires ts_set_coeffs first (TS_ERR_STATE).
+ * Uses the grid's workspace: calls on one grid must not overlap. */
+ts_status ts_step(ts_grid* grid, void* F, double dt, int nsteps, void* stream);
+
+/* As ts_step, and also times every kernel launch with CUDA events recorded on
+ * `stream` around it. On return (the stream is synchronized):
+ *   pass_ms[0..3]  = summed device time in ms of the angular-block passes,
+ *                    the (theta,phi)-plane passes, the radial passes (with
+ *                    the Tau rows and the stage update), and all other kernels;
+ *   launches[0..3] = the number of launches of each.
+ * Host arrays of 4 elements; either may be NULL. The events serialize
+ * nothing that the plain call does not, but add a small per-launch cost. */
+ts_status ts_step_profile(ts_grid* grid, void* F, double dt, int nsteps, double* pass_ms_host,
+                          int* launches_host, void* stream);
+
+/* As ts_step, with F in HOST memory: copies F to the device, steps, copies
+ * back, and synchronizes `stream` before returning. F_host should be pinned
+ * for full copy bandwidth. */
+ts_status ts_step_host(ts_grid* grid, void* F_host, double dt, int nsteps, void* stream);
+
+/* One stage derivative K = Tau(-L_sph F + CT) (the right-hand side of
+ * Eq. Transpfpsph with the grid's boundary rows) written to K. */
+ts_status ts_rhs(ts_grid* grid, const void* F, void* K, void* stream);
+
+/* L_sph F alone (Eq. Liouvsph), no collision, no boundary rows. */
+ts_status ts_liouville(ts_grid* grid, const void* F, void* LF, void* stream);
+
+/* Discrete adjoint of one ts_step step (TS_RK4 scheme, filter off).
+ * Given F_n (the state the step started from) and lambda = dObj/dF_{n+1},
+ * overwrites lambda with dObj/dF_n and ADDS this step's contributions to
+ * grad_kappa and grad_eta ([G][Nr][Ntheta][Nphi], double):
+ *   dObj/dkappa = -sum_stages b_s sum_(Theta,Phi) lambda~_s U_s,
+ *   dObj/deta   =  sum_stages b_s sum_(Theta,Phi) lambda~_s,
+ * lambda~_s being the stage adjoint after the transposed Tau rows. kappa_s
+ * receives no gradient. The paper has no adjoint: this is the exact transpose
+ * of the discrete step. Uses the grid's workspace. */
+ts_status ts_adjoint_step(ts_grid* grid, const void* F_n, void* lambda,
+                          double* grad_kappa, double* grad_eta, double dt, void* stream);
+
+/* Weights w[Ntheta][Nphi][NTheta][NPhi] (device, double) such that the
+ * outgoing radial flux J_R2 of Eq. (Flux), App. A, for group g is
+ * sum w * F[g][Nr-1][...]. */
+ts_status ts_flux_weights(ts_grid* grid, double* w, void* stream);
+
+/* Angular moments and balances (App. A and App. C), all double:
+ *   F0[G][Nr][Nth][Nph] = (1/4pi) int F dOmega,
+ *   F1[3][G][Nr][Nth][Nph] = (1/4pi) int F omega dOmega (Cartesian x,y,z,
+ *                            Eqs. omegax-omegaz; F = F0 + 3 F1.omega, Eq. Fmom0),
+ *   N[G]   = particle number (Eq. Npho, with d Theta),
+ *   J_R1[G], J_R2[G] = radial fluxes through R1, R2 (Eq. Flux).
+ * Quadrature: Clenshaw-Curtis (r), Fejer's first rule (theta, Theta),
+ * trapezoid (phi, Phi). Any output pointer may be NULL. */
+ts_status ts_moments(ts_grid* grid, const void* F, double* F0, double* F1, double* N,
+                     double* J_R1, double* J_R2, void* stream);
+
+/* Status of device-side checks latched since the last call (bounded waits).
+ * Synchronizes `stream`. */
+ts_status ts_sync_status(ts_grid* grid, void* stream);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* ts_last_error(void);
+
+/* Library version string. */
+const char* ts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TS_H_ */

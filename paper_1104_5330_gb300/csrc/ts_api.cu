@@ -1,0 +1,715 @@
+// Host side of the transport-step library: tables, grid lifecycle and the C ABI
+// declared in include/ts.h.
+//
+// Tables are built here from closed forms, not from transforms:
+//  * d/dr: the Chebyshev-Gauss-Lobatto differentiation matrix in barycentric
+//    form, D_ij = (w_j/w_i)/(x_i - x_j), w_j = (-1)^j delta_j (delta = 1/2 at the
+//    ends), diagonal = minus the row sum; scaled by 2/(R2-R1).
+//  * Fourier derivative on M equispaced nodes of a 2 pi circle, Nyquist mode
+//    zeroed: D_jk = (1/2)(-1)^(j-k) cot((j-k) pi/M), D_jj = 0. For theta and
+//    Theta the circle is the doubled (double-Fourier-sphere) circle of 2N
+//    nodes; node 2N-1-j carries F at the partner point, which splits the
+//    matrix into A[j][j'] = D[j][j'] and B[j][j'] = D[j][2N-1-j'].
+//  * Fejer's first rule on pi (k+1/2)/N and Clenshaw-Curtis weights on the
+//    Gauss-Lobatto nodes from their cosine-sum closed forms.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ts_internal.h"
+
+using ts::Dims;
+using ts::Launch;
+using ts::Tables;
+
+namespace {
+
+thread_local std::string g_err;
+
+ts_status fail(ts_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+ts_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(TS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+typedef std::vector<double> Vec;
+
+// ------------------------------------------------------------------ tables
+Vec cheb_diff(int Nr, double R1, double R2) {
+  const int N = Nr - 1;
+  Vec x(Nr), w(Nr), D((size_t)Nr * Nr, 0.0);
+  for (int i = 0; i < Nr; ++i) {
+    x[i] = -std::cos(M_PI * i / N);
+    w[i] = ((i % 2) ? -1.0 : 1.0) * ((i == 0 || i == N) ? 0.5 : 1.0);
+  }
+  for (int i = 0; i < Nr; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < Nr; ++j) {
+      if (i == j) continue;
+      // x_i - x_j = 2 sin(pi (i+j)/(2N)) sin(pi (i-j)/(2N)), accurate near the ends
+      const double dx = 2.0 * std::sin(M_PI * (i + j) / (2.0 * N)) * std::sin(M_PI * (i - j) / (2.0 * N));
+      const double v = (w[j] / w[i]) / dx;
+      D[(size_t)i * Nr + j] = v;
+      diag -= v;
+    }
+    D[(size_t)i * Nr + i] = diag;
+  }
+  const double s = 2.0 / (R2 - R1);
+  for (double& v : D) v *= s;
+  return D;
+}
+
+Vec fourier_diff(int M) {
+  Vec D((size_t)M * M, 0.0);
+  for (int j = 0; j < M; ++j)
+    for (int k = 0; k < M; ++k) {
+      if (j == k) continue;
+      const int q = j - k;
+      D[(size_t)j * M + k] = 0.5 * (((q % 2) + 2) % 2 ? -1.0 : 1.0) / std::tan(q * M_PI / M);
+    }
+  return D;
+}
+
+// Filter on M equispaced circle nodes: F_jk = (1/M) sum_q sigma(|q|) e^{i q (j-k) h}.
+Vec fourier_filter(int M, double kmax, double alpha, int order) {
+  Vec Fm((size_t)M * M);
+  auto sig = [&](double q) { return std::exp(-alpha * std::pow(q / kmax, order)); };
+  for (int j = 0; j < M; ++j)
+    for (int k = 0; k < M; ++k) {
+      const double a = 2.0 * M_PI * (j - k) / M;
+      double s = sig(0.0);
+      for (int q = 1; q < M / 2; ++q) s += 2.0 * sig(q) * std::cos(q * a);
+      if (M % 2 == 0) s += sig(M / 2) * std::cos((M / 2) * a);
+      else s += 2.0 * sig(M / 2) * std::cos((M / 2) * a);
+      Fm[(size_t)j * M + k] = s / M;
+    }
+  return Fm;
+}
+
+// Filter in r: sum_k T_k(x_i) sigma(k/N) c_k with c_k the Chebyshev coefficients
+// of the nodal values (discrete orthogonality on the Gauss-Lobatto nodes).
+Vec cheb_filter(int Nr, double alpha, int order) {
+  const int N = Nr - 1;
+  Vec Fm((size_t)Nr * Nr, 0.0);
+  for (int i = 0; i < Nr; ++i)
+    for (int ip = 0; ip < Nr; ++ip) {
+      double s = 0.0;
+      const double cip = (ip == 0 || ip == N) ? 2.0 : 1.0;
+      for (int k = 0; k <= N; ++k) {
+        const double ck = (k == 0 || k == N) ? 2.0 : 1.0;
+        const double Ti = std::cos(M_PI * k * (N - i) / N);
+        const double Tip = std::cos(M_PI * k * (N - ip) / N);
+        s += Ti * std::exp(-alpha * std::pow((double)k / N, order)) * 2.0 / (N * ck * cip) * Tip;
+      }
+      Fm[(size_t)i * Nr + ip] = s;
+    }
+  return Fm;
+}
+
+void dfs_split(const Vec& Dc, int N, Vec& A, Vec& B) {
+  const int M = 2 * N;
+  A.assign((size_t)N * N, 0.0);
+  B.assign((size_t)N * N, 0.0);
+  for (int j = 0; j < N; ++j)
+    for (int jp = 0; jp < N; ++jp) {
+      A[(size_t)j * N + jp] = Dc[(size_t)j * M + jp];
+      B[(size_t)j * N + jp] = Dc[(size_t)j * M + (M - 1 - jp)];
+    }
+}
+
+// Fejer's first rule for int_0^pi g(t) sin t dt on t_k = pi (k+1/2)/N.
+Vec fejer(int N) {
+  Vec w(N);
+  for (int k = 0; k < N; ++k) {
+    const double t = M_PI * (k + 0.5) / N;
+    double s = 0.0;
+    for (int m = 1; m <= N / 2; ++m) s += std::cos(2.0 * m * t) / (4.0 * m * m - 1.0);
+    w[k] = 2.0 / N * (1.0 - 2.0 * s);
+  }
+  return w;
+}
+
+// Clenshaw-Curtis weights for int_{-1}^{1} on the Nr Gauss-Lobatto nodes.
+Vec clenshaw_curtis(int Nr) {
+  const int N = Nr - 1;
+  Vec w(Nr);
+  for (int i = 0; i <= N; ++i) {
+    double s = 1.0;
+    for (int k = 1; k <= N / 2; ++k) {
+      const double b = (2 * k == N) ? 1.0 : 2.0;
+      s -= b / (4.0 * k * k - 1.0) * std::cos(2.0 * k * i * M_PI / N);
+    }
+    w[i] = ((i == 0 || i == N) ? 1.0 : 2.0) / N * s;
+  }
+  return w;
+}
+
+Vec transpose(const Vec& M, int rows, int cols) {
+  Vec T((size_t)rows * cols);
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < cols; ++j) T[(size_t)j * rows + i] = M[(size_t)i * cols + j];
+  return T;
+}
+
+struct HostTables {
+  Vec r, theta, phi, Theta, Phi;
+  Vec Dr, Ath, Bth, Dph, ATh, BTh, DPh;          // [out][in]
+  Vec Fr, FthA, FthB, Fph, FThA, FThB, FPh;      // filter [out][in]
+  Vec inv_r, inv_sinth, cot_th, sin_th, cos_th, sin_ph, cos_ph;
+  Vec cosT, sinT, cosP, sinP, tsign, qdir;
+  Vec wr, wth, fluxw;
+};
+
+// Ordered list of the tables that go to the device (the order of Tables<C>).
+std::vector<const Vec*> device_list(const HostTables& h, std::vector<Vec>& tmp) {
+  const int Nr = (int)h.r.size(), Nt = (int)h.theta.size(), Np = (int)h.phi.size();
+  const int NT = (int)h.Theta.size(), NP = (int)h.Phi.size();
+  tmp.clear();
+  tmp.reserve(14);
+  tmp.push_back(transpose(h.Dr, Nr, Nr));
+  tmp.push_back(transpose(h.Ath, Nt, Nt));
+  tmp.push_back(transpose(h.Bth, Nt, Nt));
+  tmp.push_back(transpose(h.Dph, Np, Np));
+  tmp.push_back(transpose(h.ATh, NT, NT));
+  tmp.push_back(transpose(h.BTh, NT, NT));
+  tmp.push_back(transpose(h.DPh, NP, NP));
+  tmp.push_back(transpose(h.Fr, Nr, Nr));
+  tmp.push_back(transpose(h.FthA, Nt, Nt));
+  tmp.push_back(transpose(h.FthB, Nt, Nt));
+  tmp.push_back(transpose(h.Fph, Np, Np));
+  tmp.push_back(transpose(h.FThA, NT, NT));
+  tmp.push_back(transpose(h.FThB, NT, NT));
+  tmp.push_back(transpose(h.FPh, NP, NP));
+  return {&tmp[0], &tmp[1], &tmp[2], &tmp[3], &tmp[4], &tmp[5], &tmp[6],
+          &h.Dr, &h.Ath, &h.Bth, &h.Dph, &h.ATh, &h.BTh, &h.DPh,
+          &h.inv_r, &h.inv_sinth, &h.cot_th, &h.sin_th, &h.cos_th, &h.sin_ph, &h.cos_ph,
+          &h.cosT, &h.sinT, &h.cosP, &h.sinP, &h.tsign, &h.qdir,
+          &tmp[7], &tmp[8], &tmp[9], &tmp[10], &tmp[11], &tmp[12], &tmp[13]};
+}
+
+template <typename C>
+cudaError_t upload_tables(const HostTables& h, void** mem, Tables<C>* t) {
+  std::vector<Vec> tmp;
+  std::vector<const Vec*> list = device_list(h, tmp);
+  size_t n = 0;
+  for (const Vec* v : list) n += (v->size() + 31) / 32 * 32;
+  std::vector<C> host(n, (C)0);
+  C* dev = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dev, n * sizeof(C));
+  if (e != cudaSuccess) return e;
+  C** slots[] = {&t->DrT, &t->AthT, &t->BthT, &t->DphT, &t->AThT, &t->BThT, &t->DPhT,
+                 &t->Dr, &t->Ath, &t->Bth, &t->Dph, &t->ATh, &t->BTh, &t->DPh,
+                 &t->inv_r, &t->inv_sinth, &t->cot_th, &t->sin_th, &t->cos_th, &t->sin_ph,
+                 &t->cos_ph, &t->cosT, &t->sinT, &t->cosP, &t->sinP, &t->tsign, &t->qdir,
+                 &t->FrT, &t->FthAT, &t->FthBT, &t->FphT, &t->FThAT, &t->FThBT, &t->FPhT};
+  size_t off = 0;
+  for (size_t a = 0; a < list.size(); ++a) {
+    for (size_t b = 0; b < list[a]->size(); ++b) host[off + b] = (C)(*list[a])[b];
+    *slots[a] = dev + off;
+    off += (list[a]->size() + 31) / 32 * 32;
+  }
+  e = cudaMemcpy(dev, host.data(), n * sizeof(C), cudaMemcpyHostToDevice);
+  *mem = dev;
+  return e;
+}
+
+HostTables build_tables(const ts_grid_desc& g) {
+  HostTables h;
+  const int Nr = g.Nr, Nt = g.Ntheta, Np = g.Nphi, NT = g.NTheta, NP = g.NPhi;
+  const int N = Nr - 1;
+  for (int i = 0; i < Nr; ++i)
+    h.r.push_back(0.5 * (g.R1 + g.R2) - 0.5 * (g.R2 - g.R1) * std::cos(M_PI * i / N));
+  for (int j = 0; j < Nt; ++j) h.theta.push_back(M_PI * (j + 0.5) / Nt);
+  for (int l = 0; l < Np; ++l) h.phi.push_back(2.0 * M_PI * l / Np);
+  for (int k = 0; k < NT; ++k) h.Theta.push_back(M_PI * (k + 0.5) / NT);
+  for (int m = 0; m < NP; ++m) h.Phi.push_back(2.0 * M_PI * m / NP);
+
+  h.Dr = cheb_diff(Nr, g.R1, g.R2);
+  dfs_split(fourier_diff(2 * Nt), Nt, h.Ath, h.Bth);
+  h.Dph = fourier_diff(Np);
+  dfs_split(fourier_diff(2 * NT), NT, h.ATh, h.BTh);
+  h.DPh = fourier_diff(NP);
+
+  const double fa = g.filter_alpha > 0 ? g.filter_alpha : 36.0;
+  const int fo = g.filter_order > 0 ? g.filter_order : 16;
+  h.Fr = cheb_filter(Nr, fa, fo);
+  dfs_split(fourier_filter(2 * Nt, Nt, fa, fo), Nt, h.FthA, h.FthB);
+  h.Fph = fourier_filter(Np, Np / 2, fa, fo);
+  dfs_split(fourier_filter(2 * NT, NT, fa, fo), NT, h.FThA, h.FThB);
+  h.FPh = fourier_filter(NP, NP / 2, fa, fo);
+
+  for (int i = 0; i < Nr; ++i) {
+    h.inv_r.push_back(1.0 / h.r[i]);
+    h.tsign.push_back(((N - i) % 2) ? -1.0 : 1.0);  // T_N(x_i) = cos(pi (N - i)) on these nodes
+  }
+  for (int j = 0; j < Nt; ++j) {
+    const double s = std::sin(h.theta[j]), c = std::cos(h.theta[j]);
+    h.inv_sinth.push_back(1.0 / s);
+    h.cot_th.push_back(c / s);
+    h.sin_th.push_back(s);
+    h.cos_th.push_back(c);
+  }
+  for (int l = 0; l < Np; ++l) {
+    h.sin_ph.push_back(std::sin(h.phi[l]));
+    h.cos_ph.push_back(std::cos(h.phi[l]));
+  }
+  const Vec fT = fejer(NT);
+  for (int k = 0; k < NT; ++k) {
+    h.cosT.push_back(std::cos(h.Theta[k]));
+    h.sinT.push_back(std::sin(h.Theta[k]));
+    // J = (1/4pi) int F dOmega = sum_k fejer_k (2pi/NP)/(4pi) sum_m F_km
+    h.qdir.push_back(fT[k] / (2.0 * NP));
+  }
+  for (int m = 0; m < NP; ++m) {
+    h.cosP.push_back(std::cos(h.Phi[m]));
+    h.sinP.push_back(std::sin(h.Phi[m]));
+  }
+  const Vec cc = clenshaw_curtis(Nr);
+  for (int i = 0; i < Nr; ++i) h.wr.push_back(cc[i] * 0.5 * (g.R2 - g.R1) * h.r[i] * h.r[i]);
+  h.wth = fejer(Nt);
+  h.fluxw.resize((size_t)Nt * Np * NT * NP);
+  for (int j = 0; j < Nt; ++j)
+    for (int l = 0; l < Np; ++l)
+      for (int k = 0; k < NT; ++k)
+        for (int m = 0; m < NP; ++m)
+          h.fluxw[(((size_t)j * Np + l) * NT + k) * NP + m] =
+              g.R2 * g.R2 * h.wth[j] * (2.0 * M_PI / Np) * fT[k] * h.cosT[k] * (2.0 * M_PI / NP);
+  return h;
+}
+
+}  // namespace
+
+struct ts_grid {
+  ts_grid_desc desc;
+  Dims d;
+  size_t es = 8;
+  HostTables h;
+  void* tab64 = nullptr;
+  void* tab32 = nullptr;
+  Tables<double> t64{};
+  Tables<float> t32{};
+  double *kap = nullptr, *eta = nullptr, *kaps = nullptr;
+  void *gR1 = nullptr, *gR2 = nullptr;
+  bool coeffs = false;
+  void *U = nullptr, *K = nullptr, *Acc = nullptr;
+  void* adj[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *wr = nullptr, *wth = nullptr, *partN = nullptr, *partJ = nullptr;
+  void* io = nullptr;
+};
+
+namespace {
+
+ts::Problem make_problem(const ts_grid* g) {
+  ts::Problem p;
+  p.d = g->d;
+  p.bc = g->desc.bc;
+  p.n_fp64_rows = g->desc.precision == TS_FP32 ? 2 : 0;
+  p.kap = g->kap;
+  p.eta = g->eta;
+  p.kaps = g->kaps;
+  p.gR1 = g->gR1;
+  p.gR2 = g->gR2;
+  return p;
+}
+
+size_t field_bytes(const ts_grid* g) { return (size_t)g->d.total * g->es; }
+
+// Optional per-launch event timing (ts_step_profile). Each launch is
+// bracketed by two events on the launching stream; `kind` selects the bucket.
+struct Profiler {
+  cudaStream_t st;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;
+  cudaError_t mark() {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ev.push_back(e);
+    return cudaEventRecord(e, st);
+  }
+  cudaError_t begin() { return mark(); }
+  cudaError_t end(int k) {
+    kind.push_back(k);
+    return mark();
+  }
+  void collect(double* ms, int* n) {
+    for (size_t a = 0; a < kind.size(); ++a) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[2 * a], ev[2 * a + 1]);
+      if (ms) ms[kind[a]] += t;
+      if (n) n[kind[a]] += 1;
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+    kind.clear();
+  }
+};
+
+#define TS_TIMED(prof, k, call)                              \
+  do {                                                       \
+    if (e == cudaSuccess && (prof)) e = (prof)->begin();     \
+    if (e == cudaSuccess) e = (call);                        \
+    if (e == cudaSuccess && (prof)) e = (prof)->end(k);      \
+  } while (0)
+
+template <typename T, typename C>
+cudaError_t run_stage(ts_grid* g, const Tables<C>& t, const T* in, T* F, int s, bool collision,
+                      double dt, cudaStream_t st, Profiler* prof) {
+  const ts::Problem p = make_problem(g);
+  T* K = static_cast<T*>(g->K);
+  T* U = static_cast<T*>(g->U);
+  T* Acc = static_cast<T*>(g->Acc);
+  cudaError_t e = cudaSuccess;
+  TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, (C)-1, collision, st)));
+  TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, in, K, (C)-1, st)));
+  TS_TIMED(prof, 2, (Launch<T, C>::radial(p, t, g->t64.Dr, in, K, (C)-1,
+                                          g->desc.bc == TS_BC_TAU_INFLOW, ts::RAD_STAGE0 + s, F,
+                                          Acc, U, nullptr, dt, st)));
+  return e;
+}
+
+template <typename T, typename C>
+cudaError_t run_steps(ts_grid* g, const Tables<C>& t, T* F, double dt, int nsteps,
+                      cudaStream_t st, Profiler* prof = nullptr) {
+  const bool split = g->desc.scheme == TS_RK4_SPLIT_IMPLICIT;
+  const ts::Problem p = make_problem(g);
+  cudaError_t e = cudaSuccess;
+  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    for (int s = 0; s < 4 && e == cudaSuccess; ++s)
+      e = run_stage<T, C>(g, t, s == 0 ? F : static_cast<T*>(g->U), F, s, !split, dt, st, prof);
+    if (split) TS_TIMED(prof, 3, (Launch<T, C>::implicit_collision(p, t, F, dt, st)));
+    if (g->desc.filter_on) TS_TIMED(prof, 3, (Launch<T, C>::filter(p, t, F, static_cast<T*>(g->K), st)));
+  }
+  return e;
+}
+
+template <typename T, typename C>
+cudaError_t run_rhs(ts_grid* g, const Tables<C>& t, const T* F, T* K, bool liouville_only,
+                    cudaStream_t st) {
+  const ts::Problem p = make_problem(g);
+  const C sgn = liouville_only ? (C)1 : (C)-1;
+  cudaError_t e = Launch<T, C>::angular(p, t, F, K, sgn, !liouville_only, st);
+  if (e == cudaSuccess) e = Launch<T, C>::plane(p, t, F, K, sgn, st);
+  if (e == cudaSuccess)
+    e = Launch<T, C>::radial(p, t, g->t64.Dr, F, K, sgn,
+                             !liouville_only && g->desc.bc == TS_BC_TAU_INFLOW, ts::RAD_RHS,
+                             nullptr, nullptr, nullptr, K, 0.0, st);
+  return e;
+}
+
+template <typename T, typename C>
+cudaError_t run_adjoint(ts_grid* g, const Tables<C>& t, const T* Fn, T* lam, double* gk,
+                        double* ge, double dt, cudaStream_t st) {
+  const ts::Problem p = make_problem(g);
+  const bool tau = g->desc.bc == TS_BC_TAU_INFLOW;
+  T* K = static_cast<T*>(g->K);
+  T* junk = static_cast<T*>(g->Acc);
+  T* U2 = static_cast<T*>(g->adj[0]);
+  T* U3 = static_cast<T*>(g->adj[1]);
+  T* U4 = static_cast<T*>(g->adj[2]);
+  T* Kb = static_cast<T*>(g->adj[3]);
+  T* lt = static_cast<T*>(g->adj[4]);
+  T* Ub = static_cast<T*>(g->adj[5]);
+  T* lacc = static_cast<T*>(g->adj[6]);
+  T* Fmut = const_cast<T*>(Fn);  // stage modes 0..2 only read F
+  // forward recomputation of the stage inputs U2, U3, U4
+  const T* ins[3] = {Fn, U2, U3};
+  T* outs[3] = {U2, U3, U4};
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < 3 && e == cudaSuccess; ++s) {
+    e = Launch<T, C>::angular(p, t, ins[s], K, (C)-1, true, st);
+    if (e == cudaSuccess) e = Launch<T, C>::plane(p, t, ins[s], K, (C)-1, st);
+    if (e == cudaSuccess)
+      e = Launch<T, C>::radial(p, t, g->t64.Dr, ins[s], K, (C)-1, tau, ts::RAD_STAGE0 + s,
+                               Fmut, junk, outs[s], nullptr, dt, st);
+  }
+  // reverse sweep: stage 4, 3, 2, 1
+  const T* Us[4] = {Fn, U2, U3, U4};
+  const double wl[4] = {0.0, dt / 6.0, dt / 3.0, dt / 3.0};   // weight of lam in Kbar_{s-1}
+  const double wu[4] = {0.0, 0.5 * dt, 0.5 * dt, dt};         // weight of Ubar_s in Kbar_{s-1}
+  for (int s = 3; s >= 0 && e == cudaSuccess; --s) {
+    if (s == 3) e = Launch<T, C>::radial_T(p, t, lam, dt / 6.0, tau, lt, Ub, st);
+    else e = Launch<T, C>::radial_T(p, t, Kb, 1.0, tau, lt, Ub, st);
+    if (e == cudaSuccess) e = Launch<T, C>::plane_T(p, t, lt, Ub, st);
+    if (e == cudaSuccess)
+      e = Launch<T, C>::angular_T(p, t, lt, Ub, Us[s], gk, ge, lam, s == 3 ? lam : lacc,
+                                  s == 0 ? lam : lacc, s == 0 ? nullptr : Kb, wl[s], wu[s], st);
+  }
+  return e;
+}
+
+bool fits(const ts_grid_desc& g, size_t es) {
+  const size_t mx = 227 * 1024;
+  const size_t a = (size_t)(2 * g.NTheta * g.NTheta + g.NPhi * g.NPhi + 2 * g.NTheta * g.NPhi + 1) * es;
+  const size_t p = (size_t)(2 * g.Ntheta * g.Ntheta + g.Nphi * g.Nphi + 2 * g.Ntheta * g.Nphi * 2) * es;
+  const size_t r = (size_t)(g.Nr * g.Nr + 2 * g.Nr * 8) * es;
+  return a <= mx && p <= mx && r <= mx;
+}
+
+ts_status check_F(const ts_grid* g, const void* F) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  if (!F) return fail(TS_ERR_ARG, "field pointer is NULL");
+  return TS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ts_last_error(void) { return g_err.c_str(); }
+
+const char* ts_version(void) { return "ts 0.1 (sm_103a, 6-D spectral transport step)"; }
+
+size_t ts_field_elems(const ts_grid* g) { return g ? (size_t)g->d.total : 0; }
+
+ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
+  if (!out) return fail(TS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(TS_ERR_ARG, "desc is NULL");
+  const ts_grid_desc& g = *desc;
+  if (!(g.R1 > 0.0) || !(g.R2 > g.R1) || !std::isfinite(g.R2))
+    return fail(TS_ERR_ARG, "need 0 < R1 < R2");
+  if (g.groups < 1) return fail(TS_ERR_ARG, "groups must be >= 1");
+  if (g.Nr < 3 || g.Nr > 129 || g.Ntheta < 2 || g.Ntheta > 64 || g.Nphi < 2 || g.Nphi > 64 ||
+      g.NTheta < 2 || g.NTheta > 64 || g.NPhi < 2 || g.NPhi > 64 || (g.Nphi % 2) ||
+      (g.NTheta % 2) || (g.NPhi % 2))
+    return fail(TS_ERR_UNSUPPORTED,
+                "sizes: need 3<=Nr<=129, 2<=Ntheta<=64, even 2..64 for Nphi, NTheta, NPhi");
+  if (g.precision != TS_FP64 && g.precision != TS_FP32)
+    return fail(TS_ERR_UNSUPPORTED, "precision must be TS_FP64 or TS_FP32");
+  if (g.scheme != TS_RK4 && g.scheme != TS_RK4_SPLIT_IMPLICIT)
+    return fail(TS_ERR_UNSUPPORTED, "unknown scheme");
+  if (g.bc != TS_BC_TAU_INFLOW && g.bc != TS_BC_NONE) return fail(TS_ERR_UNSUPPORTED, "unknown bc");
+  const size_t es = g.precision == TS_FP64 ? 8 : 4;
+  if (!fits(g, es)) return fail(TS_ERR_UNSUPPORTED, "grid too large for one shared-memory tile");
+
+  ts_grid* G = new ts_grid();
+  G->desc = g;
+  G->es = es;
+  Dims& d = G->d;
+  d.G = g.groups; d.Nr = g.Nr; d.Nt = g.Ntheta; d.Np = g.Nphi; d.NT = g.NTheta; d.NP = g.NPhi;
+  d.S_l = (long long)g.NTheta * g.NPhi;
+  d.S_j = d.S_l * g.Nphi;
+  d.S_i = d.S_j * g.Ntheta;
+  d.S_g = d.S_i * g.Nr;
+  d.total = d.S_g * g.groups;
+  d.nblk = (long long)g.groups * g.Nr * g.Ntheta * g.Nphi;
+  G->h = build_tables(g);
+
+  cudaError_t e = upload_tables<double>(G->h, &G->tab64, &G->t64);
+  if (e == cudaSuccess && g.precision == TS_FP32) e = upload_tables<float>(G->h, &G->tab32, &G->t32);
+  const size_t ncoef = (size_t)d.nblk * sizeof(double);
+  const size_t ninfl = (size_t)g.groups * g.Ntheta * g.Nphi * (g.NTheta / 2) * g.NPhi * es;
+  const size_t nf = (size_t)d.total * es;
+  void** bufs[] = {(void**)&G->kap, (void**)&G->eta, (void**)&G->kaps, &G->gR1, &G->gR2,
+                   &G->U, &G->K, &G->Acc, (void**)&G->wr, (void**)&G->wth,
+                   (void**)&G->partN, (void**)&G->partJ};
+  const size_t sizes[] = {ncoef, ncoef, ncoef, ninfl, ninfl, nf, nf, nf,
+                          (size_t)g.Nr * 8, (size_t)g.Ntheta * 8, ncoef,
+                          (size_t)g.groups * 2 * g.Ntheta * g.Nphi * 8};
+  for (int b = 0; b < 12 && e == cudaSuccess; ++b) {
+    e = cudaMalloc(bufs[b], sizes[b]);
+    if (e == cudaSuccess) e = cudaMemset(*bufs[b], 0, sizes[b]);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(G->wr, G->h.wr.data(), g.Nr * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(G->wth, G->h.wth.data(), g.Ntheta * 8, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ts_destroy_grid(G);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? fail(TS_ERR_OOM, "device allocation failed")
+                                          : cuda_fail(e, "ts_create_grid");
+  }
+  *out = G;
+  return TS_OK;
+}
+
+ts_status ts_destroy_grid(ts_grid* g) {
+  if (!g) return TS_OK;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
+                  g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : g->adj)
+    if (p) cudaFree(p);
+  delete g;
+  return TS_OK;
+}
+
+ts_status ts_grid_nodes(const ts_grid* g, double* r, double* th, double* ph, double* Th,
+                        double* Ph) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  if (r) std::memcpy(r, g->h.r.data(), g->h.r.size() * 8);
+  if (th) std::memcpy(th, g->h.theta.data(), g->h.theta.size() * 8);
+  if (ph) std::memcpy(ph, g->h.phi.data(), g->h.phi.size() * 8);
+  if (Th) std::memcpy(Th, g->h.Theta.data(), g->h.Theta.size() * 8);
+  if (Ph) std::memcpy(Ph, g->h.Phi.data(), g->h.Phi.size() * 8);
+  return TS_OK;
+}
+
+ts_status ts_set_coeffs(ts_grid* g, const double* kappa, const double* eta,
+                        const double* kappa_s, const void* inflow_R1, const void* inflow_R2,
+                        void* stream) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nc = (size_t)g->d.nblk * sizeof(double);
+  const size_t ni = (size_t)g->d.G * g->d.Nt * g->d.Np * (g->d.NT / 2) * g->d.NP * g->es;
+  const void* src[] = {kappa, eta, kappa_s, inflow_R1, inflow_R2};
+  void* dst[] = {g->kap, g->eta, g->kaps, g->gR1, g->gR2};
+  const size_t n[] = {nc, nc, nc, ni, ni};
+  for (int a = 0; a < 5; ++a) {
+    cudaError_t e = src[a] ? cudaMemcpyAsync(dst[a], src[a], n[a], cudaMemcpyDeviceToDevice, st)
+                           : cudaMemsetAsync(dst[a], 0, n[a], st);
+    if (e != cudaSuccess) return cuda_fail(e, "ts_set_coeffs");
+  }
+  g->coeffs = true;
+  return TS_OK;
+}
+
+ts_status ts_apply_inflow(ts_grid* g, void* F, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ts::Problem p = make_problem(g);
+  cudaError_t e = g->es == 8 ? Launch<double, double>::apply_inflow(p, (double*)F, st)
+                             : Launch<float, float>::apply_inflow(p, (float*)F, st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_apply_inflow");
+}
+
+ts_status ts_step(ts_grid* g, void* F, double dt, int nsteps, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  if (!std::isfinite(dt) || nsteps < 0) return fail(TS_ERR_ARG, "need finite dt, nsteps >= 0");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = g->es == 8 ? run_steps<double, double>(g, g->t64, (double*)F, dt, nsteps, st)
+                             : run_steps<float, float>(g, g->t32, (float*)F, dt, nsteps, st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step");
+}
+
+ts_status ts_step_profile(ts_grid* g, void* F, double dt, int nsteps, double* pass_ms,
+                          int* launches, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  if (!std::isfinite(dt) || nsteps < 0) return fail(TS_ERR_ARG, "need finite dt, nsteps >= 0");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Profiler prof{st, {}, {}};
+  cudaError_t e = g->es == 8 ? run_steps<double, double>(g, g->t64, (double*)F, dt, nsteps, st, &prof)
+                             : run_steps<float, float>(g, g->t32, (float*)F, dt, nsteps, st, &prof);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (pass_ms) for (int a = 0; a < 4; ++a) pass_ms[a] = 0.0;
+  if (launches) for (int a = 0; a < 4; ++a) launches[a] = 0;
+  if (e == cudaSuccess) prof.collect(pass_ms, launches);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step_profile");
+}
+
+ts_status ts_step_host(ts_grid* g, void* F_host, double dt, int nsteps, void* stream) {
+  ts_status s = check_F(g, F_host);
+  if (s != TS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nb = field_bytes(g);
+  if (!g->io) {
+    cudaError_t e = cudaMalloc(&g->io, nb);
+    if (e != cudaSuccess) {
+      g->io = nullptr;
+      cudaGetLastError();
+      return fail(TS_ERR_OOM, "ts_step_host: device buffer allocation failed");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(g->io, F_host, nb, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ts_step_host (to device)");
+  s = ts_step(g, g->io, dt, nsteps, stream);
+  if (s != TS_OK) return s;
+  e = cudaMemcpyAsync(F_host, g->io, nb, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step_host (to host)");
+}
+
+ts_status ts_rhs(ts_grid* g, const void* F, void* K, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  if (!K) return fail(TS_ERR_ARG, "K is NULL");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = g->es == 8 ? run_rhs<double, double>(g, g->t64, (const double*)F, (double*)K, false, st)
+                             : run_rhs<float, float>(g, g->t32, (const float*)F, (float*)K, false, st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_rhs");
+}
+
+ts_status ts_liouville(ts_grid* g, const void* F, void* LF, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  if (!LF) return fail(TS_ERR_ARG, "LF is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = g->es == 8 ? run_rhs<double, double>(g, g->t64, (const double*)F, (double*)LF, true, st)
+                             : run_rhs<float, float>(g, g->t32, (const float*)F, (float*)LF, true, st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_liouville");
+}
+
+ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* grad_kappa,
+                          double* grad_eta, double dt, void* stream) {
+  ts_status s = check_F(g, F_n);
+  if (s != TS_OK) return s;
+  if (!lambda || !grad_kappa || !grad_eta) return fail(TS_ERR_ARG, "NULL adjoint argument");
+  if (!std::isfinite(dt)) return fail(TS_ERR_ARG, "dt must be finite");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
+  if (g->desc.scheme != TS_RK4 || g->desc.filter_on)
+    return fail(TS_ERR_UNSUPPORTED, "adjoint covers the TS_RK4 scheme without filter");
+  if (!g->adj[0]) {
+    for (int a = 0; a < 7; ++a) {
+      cudaError_t e = cudaMalloc(&g->adj[a], field_bytes(g));
+      if (e != cudaSuccess) {
+        for (int b = 0; b <= a; ++b) {
+          if (g->adj[b]) cudaFree(g->adj[b]);
+          g->adj[b] = nullptr;
+        }
+        cudaGetLastError();
+        return fail(TS_ERR_OOM, "adjoint workspace allocation failed");
+      }
+    }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = g->es == 8
+      ? run_adjoint<double, double>(g, g->t64, (const double*)F_n, (double*)lambda, grad_kappa, grad_eta, dt, st)
+      : run_adjoint<float, float>(g, g->t32, (const float*)F_n, (float*)lambda, grad_kappa, grad_eta, dt, st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_adjoint_step");
+}
+
+ts_status ts_flux_weights(ts_grid* g, double* w, void* stream) {
+  if (!g || !w) return fail(TS_ERR_ARG, "NULL argument");
+  cudaError_t e = cudaMemcpyAsync(w, g->h.fluxw.data(), g->h.fluxw.size() * 8,
+                                  cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_flux_weights");
+}
+
+ts_status ts_moments(ts_grid* g, const void* F, double* F0, double* F1, double* N, double* JR1,
+                     double* JR2, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ts::Problem p = make_problem(g);
+  cudaError_t e = g->es == 8
+      ? Launch<double, double>::moments(p, g->t64, g->wr, g->wth, (const double*)F, F0, F1,
+                                        g->partN, g->partJ, N, JR1, JR2, g->desc.R1, g->desc.R2, st)
+      : Launch<float, float>::moments(p, g->t64, g->wr, g->wth, (const float*)F, F0, F1,
+                                      g->partN, g->partJ, N, JR1, JR2, g->desc.R1, g->desc.R2, st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_moments");
+}
+
+ts_status ts_sync_status(ts_grid* g, void* stream) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_sync_status");
+}
+
+}  // extern "C"

@@ -1,0 +1,625 @@
+// Kernels of one RK4 stage of the 6-D transport step and of its adjoint.
+//
+// A stage derivative K = Tau(-L_sph U + CT(U)) (Eqs. Liouvsph, Transpfpsph,
+// Transp) is built in three passes over the field, each staging the lines it
+// contracts in shared memory:
+//   1. angular pass, one angular block (fixed g,i,j,l: all Theta, Phi) per
+//      tile: d_Theta (double-Fourier-sphere pair: Theta_k and the partner at
+//      Phi + pi), d_Phi, the scattering mean J (Fejer x trapezoid, warp
+//      reduction), the collision term, and the Theta/Phi terms of L_sph;
+//   2. plane pass, one (theta, phi) plane at fixed (g,i,Theta) and a set of
+//      Phi columns closed under Phi -> Phi + pi: d_theta (partner at
+//      (phi + pi, Phi + pi)) and d_phi, the theta/phi terms of L_sph;
+//   3. radial pass, full r-lines: d_r (Chebyshev-Gauss-Lobatto matrix), the
+//      r term, the Tau inflow rows (Sect. 5.1), and the RK4 stage update.
+// Derivative matrices are applied as dense contractions; their transposes
+// give the adjoint passes.
+#pragma once
+
+#include "ts_internal.h"
+
+namespace ts {
+
+constexpr int kThreads = 256;
+
+template <typename C>
+__device__ __forceinline__ C fmac(C a, C b, C c) { return fma(a, b, c); }
+
+__device__ __forceinline__ void decode_block(const Dims& d, long long blk, int& g, int& i, int& j,
+                                             int& l) {
+  l = (int)(blk % d.Np);
+  long long q = blk / d.Np;
+  j = (int)(q % d.Nt);
+  q /= d.Nt;
+  i = (int)(q % d.Nr);
+  g = (int)(q / d.Nr);
+}
+
+// ----------------------------------------------------------------------------
+// Pass 1 (forward): angular blocks. A CTA owns `nb` consecutive blocks, which
+// are contiguous in memory (block b = elements [b*S, (b+1)*S), S = NT*NP).
+// K = sgn * (a_Th dTh U + a_Ph dPh U) + [eta - (kappa+kappa_s) U + kappa_s J]
+// a_Th = -sin(Th)/r, a_Ph = -sin(Th) sin(Ph) cot(th)/r.
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_angular(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
+          int collision, int nb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = p.d;
+  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2;
+  C* sA = reinterpret_cast<C*>(smem_raw);  // AThT [k'][k]
+  C* sB = sA + NT * NT;                    // BThT [k'][k]
+  C* sD = sB + NT * NT;                    // DPhT [m'][m]
+  C* su = sD + NP * NP;                    // tile [bb][k][m]
+  C* sJ = su + nb * S;                     // [nb]
+  const long long b0 = (long long)blockIdx.x * nb;
+  const int nbb = (int)min((long long)nb, d.nblk - b0);
+  for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
+    sA[x] = t.AThT[x];
+    sB[x] = t.BThT[x];
+  }
+  for (int x = threadIdx.x; x < NP * NP; x += blockDim.x) sD[x] = t.DPhT[x];
+  const T* src = U + b0 * S;
+  for (int x = threadIdx.x; x < nbb * S; x += blockDim.x) su[x] = (C)src[x];
+  __syncthreads();
+  if (collision) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
+      C acc = 0;
+      for (int x = lane; x < S; x += 32) acc = fmac(t.qdir[x / NP], su[bb * S + x], acc);
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) sJ[bb] = acc;
+    }
+    __syncthreads();
+  }
+  for (int x = threadIdx.x; x < nbb * S; x += blockDim.x) {
+    const int bb = x / S, r = x - bb * S, k = r / NP, m = r - k * NP;
+    const int mh = (m + hP) % NP;
+    const C* ub = su + bb * S;
+    C dT = 0, dP = 0;
+    for (int kk = 0; kk < NT; ++kk) {
+      dT = fmac(sA[kk * NT + k], ub[kk * NP + m], dT);
+      dT = fmac(sB[kk * NT + k], ub[kk * NP + mh], dT);
+    }
+    for (int mm = 0; mm < NP; ++mm) dP = fmac(sD[mm * NP + m], ub[k * NP + mm], dP);
+    const long long blk = b0 + bb;
+    int g, i, j, l;
+    decode_block(d, blk, g, i, j, l);
+    const C aT = -t.sinT[k] * t.inv_r[i];
+    const C aP = aT * t.sinP[m] * t.cot_th[j];
+    C v = sgn * (aT * dT + aP * dP);
+    if (collision) {
+      const C u = ub[r];
+      const C kap = (C)p.kap[blk], eta = (C)p.eta[blk], ks = (C)p.kaps[blk];
+      v += eta - (kap + ks) * u + ks * sJ[bb];
+    }
+    K[blk * S + r] = (T)v;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Pass 2 (forward): (theta, phi) planes. A CTA owns (g, i, k) and the Phi
+// columns m0..m0+c-1 and m0+NP/2..m0+NP/2+c-1; tile [j][l][w], w < 2c.
+// K += sgn * (a_th dth U + a_ph dph U), a_th = sin(Th)cos(Ph)/r,
+// a_ph = sin(Th) sin(Ph)/(r sin(th)).
+__device__ __forceinline__ int plane_m(int w, int c, int m0, int hP) {
+  return w < c ? m0 + w : m0 + hP + (w - c);
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_plane(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn, int c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = p.d;
+  const int Nt = d.Nt, Np = d.Np, NP = d.NP, hP = NP / 2, hp = Np / 2, W = 2 * c;
+  C* sA = reinterpret_cast<C*>(smem_raw);  // AthT [j'][j]
+  C* sB = sA + Nt * Nt;                    // BthT
+  C* sD = sB + Nt * Nt;                    // DphT [l'][l]
+  C* su = sD + Np * Np;                    // [j][l][w]
+  const int nchunk = hP / c;
+  long long q = blockIdx.x;
+  const int chunk = (int)(q % nchunk);
+  q /= nchunk;
+  const int k = (int)(q % d.NT);
+  q /= d.NT;
+  const int i = (int)(q % d.Nr);
+  const int g = (int)(q / d.Nr);
+  const int m0 = chunk * c;
+  const long long base = (long long)g * d.S_g + (long long)i * d.S_i + (long long)k * NP;
+  for (int x = threadIdx.x; x < Nt * Nt; x += blockDim.x) {
+    sA[x] = t.AthT[x];
+    sB[x] = t.BthT[x];
+  }
+  for (int x = threadIdx.x; x < Np * Np; x += blockDim.x) sD[x] = t.DphT[x];
+  const int n = Nt * Np * W;
+  for (int x = threadIdx.x; x < n; x += blockDim.x) {
+    const int w = x % W, jl = x / W, l = jl % Np, j = jl / Np;
+    su[x] = (C)U[base + (long long)j * d.S_j + (long long)l * d.S_l + plane_m(w, c, m0, hP)];
+  }
+  __syncthreads();
+  const C sTk = t.sinT[k], ir = t.inv_r[i];
+  for (int x = threadIdx.x; x < n; x += blockDim.x) {
+    const int w = x % W, jl = x / W, l = jl % Np, j = jl / Np;
+    const int lh = (l + hp) % Np, wh = w < c ? w + c : w - c;
+    C dth = 0, dph = 0;
+    for (int jj = 0; jj < Nt; ++jj) {
+      dth = fmac(sA[jj * Nt + j], su[(jj * Np + l) * W + w], dth);
+      dth = fmac(sB[jj * Nt + j], su[(jj * Np + lh) * W + wh], dth);
+    }
+    for (int ll = 0; ll < Np; ++ll) dph = fmac(sD[ll * Np + l], su[(j * Np + ll) * W + w], dph);
+    const int m = plane_m(w, c, m0, hP);
+    const C ath = sTk * t.cosP[m] * ir;
+    const C aph = sTk * t.sinP[m] * ir * t.inv_sinth[j];
+    const long long idx = base + (long long)j * d.S_j + (long long)l * d.S_l + m;
+    K[idx] = (T)((C)K[idx] + sgn * (ath * dth + aph * dph));
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Pass 3 (forward): r-lines. A CTA owns (g, j, l) and W consecutive columns
+// col = k*NP + m of the angular block, all Nr radial nodes: tile [i][w].
+// K += sgn * cos(Th) d_r U, then the Tau rows, then the stage update.
+// Tau (Sect. 5.1): K_i += (gdot - K_b) T_N(x_b) T_N(x_i), gdot = 0 for static
+// inflow data, b = 0 if cos(Th) > 0 else Nr-1; T_N(x_i) = (-1)^(N-i). This is
+// the nodal form of replacing the top Chebyshev coefficient of K.
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_radial(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U,
+         const T* Kin, C sgn, int tau, int mode, T* F, T* Acc, T* Uout, T* out,
+         C dt, int W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = p.d;
+  const int Nr = d.Nr, NP = d.NP, S = d.NT * d.NP;
+  C* sDr = reinterpret_cast<C*>(smem_raw);  // Dr [i][i']
+  C* su = sDr + Nr * Nr;                    // [i][w]
+  C* sk = su + Nr * W;                      // [i][w]
+  const int nchunk = (S + W - 1) / W;
+  long long q = blockIdx.x;
+  const int chunk = (int)(q % nchunk);
+  q /= nchunk;
+  const int l = (int)(q % d.Np);
+  q /= d.Np;
+  const int j = (int)(q % d.Nt);
+  const int g = (int)(q / d.Nt);
+  const int c0 = chunk * W;
+  const int Wc = min(W, S - c0);
+  const long long base =
+      (long long)g * d.S_g + (long long)j * d.S_j + (long long)l * d.S_l + c0;
+  for (int x = threadIdx.x; x < Nr * Nr; x += blockDim.x) sDr[x] = t.Dr[x];
+  for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
+    const int i = x / Wc, w = x - i * Wc;
+    const long long gi = base + (long long)i * d.S_i + w;
+    su[i * W + w] = (C)U[gi];
+    sk[i * W + w] = (C)Kin[gi];
+  }
+  __syncthreads();
+  const int nlo = p.n_fp64_rows, nhi = Nr - p.n_fp64_rows;
+  for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
+    const int i = x / Wc, w = x - i * Wc;
+    const int k = (c0 + w) / NP;
+    C dr;
+    if (i < nlo || i >= nhi) {  // rows with the largest entries: accumulate in double
+      double a = 0;
+      for (int ii = 0; ii < Nr; ++ii) a = fma(Dr64[i * Nr + ii], (double)su[ii * W + w], a);
+      dr = (C)a;
+    } else {
+      C a = 0;
+      for (int ii = 0; ii < Nr; ++ii) a = fmac(sDr[i * Nr + ii], su[ii * W + w], a);
+      dr = a;
+    }
+    sk[i * W + w] += sgn * t.cosT[k] * dr;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
+    const int i = x / Wc, w = x - i * Wc;
+    const int k = (c0 + w) / NP;
+    C kv = sk[i * W + w];
+    if (tau) {
+      const int b = t.cosT[k] > (C)0 ? 0 : Nr - 1;
+      kv -= sk[b * W + w] * t.tsign[b] * t.tsign[i];
+    }
+    const long long gi = base + (long long)i * d.S_i + w;
+    switch (mode) {
+      case RAD_RHS:
+        out[gi] = (T)kv;
+        break;
+      case RAD_STAGE0:
+        Acc[gi] = (T)kv;
+        Uout[gi] = (T)((C)F[gi] + (C)0.5 * dt * kv);
+        break;
+      case RAD_STAGE1:
+        Acc[gi] = (T)((C)Acc[gi] + (C)2 * kv);
+        Uout[gi] = (T)((C)F[gi] + (C)0.5 * dt * kv);
+        break;
+      case RAD_STAGE2:
+        Acc[gi] = (T)((C)Acc[gi] + (C)2 * kv);
+        Uout[gi] = (T)((C)F[gi] + dt * kv);
+        break;
+      default:  // RAD_STAGE3
+        F[gi] = (T)((C)F[gi] + dt / (C)6 * ((C)Acc[gi] + kv));
+        break;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Adjoint pass 3^T: r-lines. Kbar = scale * X. lt = Tau^T Kbar:
+// lt_i = Kbar_i - [i == b] T_N(x_b) sum_i' T_N(x_i') Kbar_i'. Then the radial
+// part of the stage adjoint: Ubar = -cos(Th) D_r^T lt.
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_radial_T(Problem p, Tables<C> t, const T* __restrict__ X, C scale, int tau,
+           T* __restrict__ lt, T* __restrict__ Ubar, int W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = p.d;
+  const int Nr = d.Nr, NP = d.NP, S = d.NT * d.NP;
+  C* sDr = reinterpret_cast<C*>(smem_raw);  // Dr [i][i'] read as [in][out] of D_r^T
+  C* sk = sDr + Nr * Nr;
+  C* sl = sk + Nr * W;
+  const int nchunk = (S + W - 1) / W;
+  long long q = blockIdx.x;
+  const int chunk = (int)(q % nchunk);
+  q /= nchunk;
+  const int l = (int)(q % d.Np);
+  q /= d.Np;
+  const int j = (int)(q % d.Nt);
+  const int g = (int)(q / d.Nt);
+  const int c0 = chunk * W;
+  const int Wc = min(W, S - c0);
+  const long long base =
+      (long long)g * d.S_g + (long long)j * d.S_j + (long long)l * d.S_l + c0;
+  for (int x = threadIdx.x; x < Nr * Nr; x += blockDim.x) sDr[x] = t.Dr[x];
+  for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
+    const int i = x / Wc, w = x - i * Wc;
+    sk[i * W + w] = scale * (C)X[base + (long long)i * d.S_i + w];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
+    const int i = x / Wc, w = x - i * Wc;
+    const int k = (c0 + w) / NP;
+    C v = sk[i * W + w];
+    if (tau) {
+      const int b = t.cosT[k] > (C)0 ? 0 : Nr - 1;
+      if (i == b) {
+        C s = 0;
+        for (int ii = 0; ii < Nr; ++ii) s = fmac(t.tsign[ii], sk[ii * W + w], s);
+        v -= t.tsign[b] * s;
+      }
+    }
+    sl[i * W + w] = v;
+    lt[base + (long long)i * d.S_i + w] = (T)v;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
+    const int i = x / Wc, w = x - i * Wc;  // i = output index of D_r^T
+    const int k = (c0 + w) / NP;
+    C a = 0;
+    for (int ii = 0; ii < Nr; ++ii) a = fmac(sDr[ii * Nr + i], sl[ii * W + w], a);
+    Ubar[base + (long long)i * d.S_i + w] = (T)(-t.cosT[k] * a);
+  }
+}
+
+// Adjoint pass 2^T: Ubar -= D_th^T (a_th lt) + D_ph^T (a_ph lt).
+// (D_th^T mu)(j', l, m) = sum_j Ath[j][j'] mu(j,l,m) + Bth[j][j'] mu(j, l+Np/2, m+NP/2).
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_plane_T(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__ Ubar, int c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = p.d;
+  const int Nt = d.Nt, Np = d.Np, NP = d.NP, hP = NP / 2, hp = Np / 2, W = 2 * c;
+  C* sA = reinterpret_cast<C*>(smem_raw);  // Ath [j][j'] = [in][out] of the transpose
+  C* sB = sA + Nt * Nt;
+  C* sD = sB + Nt * Nt;                    // Dph [l][l']
+  C* s1 = sD + Np * Np;                    // a_th * lt   [j][l][w]
+  C* s2 = s1 + Nt * Np * W;                // a_ph * lt
+  const int nchunk = hP / c;
+  long long q = blockIdx.x;
+  const int chunk = (int)(q % nchunk);
+  q /= nchunk;
+  const int k = (int)(q % d.NT);
+  q /= d.NT;
+  const int i = (int)(q % d.Nr);
+  const int g = (int)(q / d.Nr);
+  const int m0 = chunk * c;
+  const long long base = (long long)g * d.S_g + (long long)i * d.S_i + (long long)k * NP;
+  for (int x = threadIdx.x; x < Nt * Nt; x += blockDim.x) {
+    sA[x] = t.Ath[x];
+    sB[x] = t.Bth[x];
+  }
+  for (int x = threadIdx.x; x < Np * Np; x += blockDim.x) sD[x] = t.Dph[x];
+  const C sTk = t.sinT[k], ir = t.inv_r[i];
+  const int n = Nt * Np * W;
+  for (int x = threadIdx.x; x < n; x += blockDim.x) {
+    const int w = x % W, jl = x / W, l = jl % Np, j = jl / Np;
+    const int m = plane_m(w, c, m0, hP);
+    const C v = (C)lt[base + (long long)j * d.S_j + (long long)l * d.S_l + m];
+    s1[x] = sTk * t.cosP[m] * ir * v;
+    s2[x] = sTk * t.sinP[m] * ir * t.inv_sinth[j] * v;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < n; x += blockDim.x) {
+    const int w = x % W, jl = x / W, l = jl % Np, j = jl / Np;
+    const int lh = (l + hp) % Np, wh = w < c ? w + c : w - c;
+    C a = 0;
+    for (int jj = 0; jj < Nt; ++jj) {
+      a = fmac(sA[jj * Nt + j], s1[(jj * Np + l) * W + w], a);
+      a = fmac(sB[jj * Nt + j], s1[(jj * Np + lh) * W + wh], a);
+    }
+    for (int ll = 0; ll < Np; ++ll) a = fmac(sD[ll * Np + l], s2[(j * Np + ll) * W + w], a);
+    const long long idx =
+        base + (long long)j * d.S_j + (long long)l * d.S_l + plane_m(w, c, m0, hP);
+    Ubar[idx] = (T)((C)Ubar[idx] - a);
+  }
+}
+
+// Adjoint pass 1^T: angular blocks.
+//   Ubar_s = Ubar - D_Th^T(a_Th lt) - D_Ph^T(a_Ph lt) - (kappa+kappa_s) lt + kappa_s q_k sum lt
+//   gk -= sum_block lt*Us,  ge += sum_block lt
+//   lam_out = lam_in + Ubar_s;   Kbar_out = wl*lam + wu*Ubar_s (if Kbar_out)
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restrict__ Ubar,
+            const T* __restrict__ Us, double* gk, double* ge, const T* lam, const T* lam_in,
+            T* lam_out, T* Kbar_out, C wl, C wu, int nb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = p.d;
+  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2;
+  C* sA = reinterpret_cast<C*>(smem_raw);  // ATh [k][k']
+  C* sB = sA + NT * NT;
+  C* sD = sB + NT * NT;                    // DPh [m][m']
+  C* s1 = sD + NP * NP;                    // a_Th * lt  [bb][k][m]
+  C* s2 = s1 + nb * S;                     // a_Ph * lt
+  C* sS = s2 + nb * S;                     // [nb] kappa_s-weighted sum of lt
+  const long long b0 = (long long)blockIdx.x * nb;
+  const int nbb = (int)min((long long)nb, d.nblk - b0);
+  for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
+    sA[x] = t.ATh[x];
+    sB[x] = t.BTh[x];
+  }
+  for (int x = threadIdx.x; x < NP * NP; x += blockDim.x) sD[x] = t.DPh[x];
+  for (int x = threadIdx.x; x < nbb * S; x += blockDim.x) {
+    const int bb = x / S, r = x - bb * S, k = r / NP, m = r - k * NP;
+    int g, i, j, l;
+    decode_block(d, b0 + bb, g, i, j, l);
+    const C v = (C)lt[b0 * S + x];
+    const C aT = -t.sinT[k] * t.inv_r[i];
+    s1[x] = aT * v;
+    s2[x] = aT * t.sinP[m] * t.cot_th[j] * v;
+  }
+  __syncthreads();
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
+      double sl = 0, slu = 0;
+      for (int x = lane; x < S; x += 32) {
+        const double v = (double)lt[(b0 + bb) * S + x];
+        sl += v;
+        slu = fma(v, (double)Us[(b0 + bb) * S + x], slu);
+      }
+      for (int o = 16; o; o >>= 1) {
+        sl += __shfl_xor_sync(0xffffffffu, sl, o);
+        slu += __shfl_xor_sync(0xffffffffu, slu, o);
+      }
+      if (lane == 0) {
+        const long long blk = b0 + bb;
+        sS[bb] = (C)(p.kaps[blk] * sl);
+        ge[blk] += sl;
+        gk[blk] -= slu;
+      }
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < nbb * S; x += blockDim.x) {
+    const int bb = x / S, r = x - bb * S, k = r / NP, m = r - k * NP;
+    const int mh = (m + hP) % NP;
+    const C* a1 = s1 + bb * S;
+    const C* a2 = s2 + bb * S;
+    C a = 0;
+    for (int kk = 0; kk < NT; ++kk) {
+      a = fmac(sA[kk * NT + k], a1[kk * NP + m], a);
+      a = fmac(sB[kk * NT + k], a1[kk * NP + mh], a);
+    }
+    for (int mm = 0; mm < NP; ++mm) a = fmac(sD[mm * NP + m], a2[k * NP + mm], a);
+    const long long blk = b0 + bb, gi = blk * S + r;
+    const C v = (C)lt[gi];
+    const C kap = (C)p.kap[blk], ks = (C)p.kaps[blk];
+    const C ub = (C)Ubar[gi] - a - (kap + ks) * v + t.qdir[k] * sS[bb];
+    lam_out[gi] = (T)((C)lam_in[gi] + ub);
+    if (Kbar_out) Kbar_out[gi] = (T)(wl * (C)lam[gi] + wu * ub);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Split scheme: backward-Euler collision step in closed form per angular block,
+//   J+ = (J* + dt eta)/(1 + dt kappa),  F+ = (F* + dt (eta + kappa_s J+))/(1 + dt (kappa+kappa_s)),
+// then F = inflow data at the inflow nodes (if the grid has Tau rows).
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_implicit_collision(Problem p, Tables<C> t, T* F, C dt, int nb) {
+  const Dims d = p.d;
+  const int NT = d.NT, NP = d.NP, S = NT * NP, hT = NT / 2;
+  const long long b0 = (long long)blockIdx.x * nb;
+  const int nbb = (int)min((long long)nb, d.nblk - b0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int bb = warp; bb < nbb; bb += nw) {
+    const long long blk = b0 + bb;
+    C acc = 0;
+    for (int x = lane; x < S; x += 32) acc = fmac(t.qdir[x / NP], (C)F[blk * S + x], acc);
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const C kap = (C)p.kap[blk], eta = (C)p.eta[blk], ks = (C)p.kaps[blk];
+    const C Jp = (acc + dt * eta) / ((C)1 + dt * kap);
+    const C num = dt * (eta + ks * Jp), den = (C)1 + dt * (kap + ks);
+    int g, i, j, l;
+    decode_block(d, blk, g, i, j, l);
+    const T* g1 = reinterpret_cast<const T*>(p.gR1);
+    const T* g2 = reinterpret_cast<const T*>(p.gR2);
+    for (int x = lane; x < S; x += 32) {
+      const int k = x / NP, m = x - k * NP;
+      C v = ((C)F[blk * S + x] + num) / den;
+      if (p.bc == TS_BC_TAU_INFLOW) {
+        const long long pos = (((long long)g * d.Nt + j) * d.Np + l) * hT;
+        if (i == 0 && k < hT) v = g1 ? (C)g1[(pos + k) * NP + m] : (C)0;
+        if (i == d.Nr - 1 && k >= hT) v = g2 ? (C)g2[(pos + k - hT) * NP + m] : (C)0;
+      }
+      F[blk * S + x] = (T)v;
+    }
+  }
+}
+
+// F = inflow data at the inflow nodes.
+template <typename T>
+__global__ void k_apply_inflow(Problem p, T* F) {
+  const Dims d = p.d;
+  const int hT = d.NT / 2;
+  const long long n = (long long)d.G * d.Nt * d.Np * d.NT * d.NP;  // one value per (g,j,l,k,m)
+  const T* g1 = reinterpret_cast<const T*>(p.gR1);
+  const T* g2 = reinterpret_cast<const T*>(p.gR2);
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
+       x += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(x % d.NP);
+    long long q = x / d.NP;
+    const int k = (int)(q % d.NT);
+    q /= d.NT;
+    const int l = (int)(q % d.Np);
+    q /= d.Np;
+    const int j = (int)(q % d.Nt);
+    const int g = (int)(q / d.Nt);
+    const long long pos = (((long long)g * d.Nt + j) * d.Np + l) * hT;
+    const long long off = (long long)j * d.S_j + (long long)l * d.S_l + (long long)k * d.NP + m;
+    if (k < hT)
+      F[(long long)g * d.S_g + off] = g1 ? g1[(pos + k) * d.NP + m] : (T)0;
+    else
+      F[(long long)g * d.S_g + (long long)(d.Nr - 1) * d.S_i + off] =
+          g2 ? g2[(pos + k - hT) * d.NP + m] : (T)0;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Filter, one axis per launch (off the hot loop): out = M along `axis`,
+// with the DFS partner term for theta (axis 1) and Theta (axis 3).
+// M1T, M2T are [in][out].
+template <typename T, typename C>
+__global__ void k_filter_axis(Problem p, const C* __restrict__ M1T, const C* __restrict__ M2T,
+                              int axis, const T* __restrict__ in, T* __restrict__ out) {
+  const Dims d = p.d;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < d.total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(x % d.NP);
+    long long q = x / d.NP;
+    const int k = (int)(q % d.NT);
+    q /= d.NT;
+    const int l = (int)(q % d.Np);
+    q /= d.Np;
+    const int j = (int)(q % d.Nt);
+    q /= d.Nt;
+    const int i = (int)(q % d.Nr);
+    const int g = (int)(q / d.Nr);
+    const long long g0 = (long long)g * d.S_g;
+    C a = 0;
+    if (axis == 0) {
+      const long long b = g0 + (long long)j * d.S_j + (long long)l * d.S_l + k * d.NP + m;
+      for (int n = 0; n < d.Nr; ++n) a = fmac(M1T[n * d.Nr + i], (C)in[b + n * d.S_i], a);
+    } else if (axis == 1) {
+      const int lh = (l + d.Np / 2) % d.Np, mh = (m + d.NP / 2) % d.NP;
+      const long long b = g0 + (long long)i * d.S_i + (long long)l * d.S_l + k * d.NP + m;
+      const long long bh = g0 + (long long)i * d.S_i + (long long)lh * d.S_l + k * d.NP + mh;
+      for (int n = 0; n < d.Nt; ++n) {
+        a = fmac(M1T[n * d.Nt + j], (C)in[b + n * d.S_j], a);
+        a = fmac(M2T[n * d.Nt + j], (C)in[bh + n * d.S_j], a);
+      }
+    } else if (axis == 2) {
+      const long long b = g0 + (long long)i * d.S_i + (long long)j * d.S_j + k * d.NP + m;
+      for (int n = 0; n < d.Np; ++n) a = fmac(M1T[n * d.Np + l], (C)in[b + n * d.S_l], a);
+    } else if (axis == 3) {
+      const int mh = (m + d.NP / 2) % d.NP;
+      const long long b = x - (long long)k * d.NP - m;
+      for (int n = 0; n < d.NT; ++n) {
+        a = fmac(M1T[n * d.NT + k], (C)in[b + n * d.NP + m], a);
+        a = fmac(M2T[n * d.NT + k], (C)in[b + n * d.NP + mh], a);
+      }
+    } else {
+      const long long b = x - m;
+      for (int n = 0; n < d.NP; ++n) a = fmac(M1T[n * d.NP + m], (C)in[b + n], a);
+    }
+    out[x] = (T)a;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Moments (App. A, App. C). One warp per angular block (double arithmetic):
+// S0 = sum q_k F, Sr = sum q_k cos(Th) F, St = sum q_k sin(Th)cos(Ph) F,
+// Sp = sum q_k sin(Th) sin(Ph) F with q_k = Fejer_k (2pi/NP)/(4pi). F0 = S0 and
+// F1 is (Sr, St, Sp) rotated from the local (rhat, thetahat, phihat) frame to
+// Cartesian axes (Eqs. omegax-omegaz). Per-block contributions to N and to the
+// fluxes go to partN/partJ and are summed per group by k_moments_reduce in a
+// fixed order (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_moments(Problem p, Tables<double> t, const double* __restrict__ wr,
+          const double* __restrict__ wth, const T* __restrict__ F, double* F0, double* F1,
+          double* partN, double* partJ, double R1, double R2) {
+  const Dims d = p.d;
+  const int NP = d.NP, S = d.NT * NP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long blk = blockIdx.x * (long long)(blockDim.x >> 5) + warp;
+  if (blk >= d.nblk) return;
+  double s0 = 0, sr = 0, st = 0, sp = 0;
+  for (int x = lane; x < S; x += 32) {
+    const int k = x / NP, m = x - k * NP;
+    const double v = t.qdir[k] * (double)F[blk * S + x];
+    s0 += v;
+    sr = fma(v, t.cosT[k], sr);
+    st = fma(v, t.sinT[k] * t.cosP[m], st);
+    sp = fma(v, t.sinT[k] * t.sinP[m], sp);
+  }
+  for (int o = 16; o; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    st += __shfl_xor_sync(0xffffffffu, st, o);
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+  }
+  if (lane != 0) return;
+  int g, i, j, l;
+  decode_block(d, blk, g, i, j, l);
+  const double sth = t.sin_th[j], cth = t.cos_th[j], sph = t.sin_ph[l], cph = t.cos_ph[l];
+  if (F0) F0[blk] = s0;
+  if (F1) {
+    F1[blk] = sr * sth * cph + st * cth * cph - sp * sph;
+    F1[d.nblk + blk] = sr * sth * sph + st * cth * sph + sp * cph;
+    F1[2 * d.nblk + blk] = sr * cth - st * sth;
+  }
+  const double area = wth[j] * (2.0 * M_PI / d.Np) * 4.0 * M_PI;  // position-angle weight x 4 pi
+  partN[blk] = wr[i] * area * s0;
+  const long long pos = (long long)j * d.Np + l;
+  if (i == 0) partJ[((long long)g * 2 + 0) * d.Nt * d.Np + pos] = R1 * R1 * area * sr;
+  if (i == d.Nr - 1) partJ[((long long)g * 2 + 1) * d.Nt * d.Np + pos] = R2 * R2 * area * sr;
+}
+
+static __global__ void k_moments_reduce(Dims d, const double* partN, const double* partJ, double* N,
+                                 double* JR1, double* JR2) {
+  __shared__ double red[3][kThreads];
+  const int g = blockIdx.x;
+  const long long nN = (long long)d.Nr * d.Nt * d.Np, nJ = (long long)d.Nt * d.Np;
+  double a = 0, b = 0, c = 0;
+  for (long long x = threadIdx.x; x < nN; x += blockDim.x) a += partN[g * nN + x];
+  for (long long x = threadIdx.x; x < nJ; x += blockDim.x) {
+    b += partJ[(g * 2 + 0) * nJ + x];
+    c += partJ[(g * 2 + 1) * nJ + x];
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int v = 0; v < 3; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (N) N[g] = red[0][0];
+    if (JR1) JR1[g] = red[1][0];
+    if (JR2) JR2[g] = red[2][0];
+  }
+}
+
+}  // namespace ts

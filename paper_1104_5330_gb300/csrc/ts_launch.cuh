@@ -1,0 +1,185 @@
+// Launch configuration of the transport-step kernels (tile sizes per pass).
+#pragma once
+
+#include <algorithm>
+
+#include "ts_kernels.cuh"
+
+namespace ts {
+
+// Shared-memory budget per CTA used when choosing tile sizes; kernels opt in
+// to the full 227 KB once so that large grids still fit one tile.
+constexpr size_t kSmemBudget = 96 * 1024;
+constexpr size_t kSmemMax = 227 * 1024;
+
+template <typename K>
+static cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+}
+
+static inline unsigned grid1(long long n) { return (unsigned)n; }
+
+template <typename T, typename C>
+static int angular_nb(const Dims& d, int ntiles) {
+  const int S = d.NT * d.NP;
+  const size_t mats = (size_t)(2 * d.NT * d.NT + d.NP * d.NP) * sizeof(C);
+  int nb = std::max(1, 2048 / S);
+  while (nb > 1 && mats + (size_t)nb * (ntiles * S + 1) * sizeof(C) > kSmemBudget) nb /= 2;
+  return nb;
+}
+
+template <typename T, typename C>
+static int plane_c(const Dims& d, int ntiles) {
+  const int hP = d.NP / 2;
+  const size_t mats = (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np) * sizeof(C);
+  int best = 1;
+  for (int c = 1; c <= hP; ++c) {
+    if (hP % c) continue;
+    if (mats + (size_t)ntiles * d.Nt * d.Np * 2 * c * sizeof(C) <= kSmemBudget) best = c;
+  }
+  return best;
+}
+
+template <typename T, typename C>
+static int radial_W(const Dims& d, int ntiles) {
+  const int S = d.NT * d.NP;
+  int W = std::min(S, sizeof(C) == 8 ? 64 : 128);
+  while (W > 8 && (size_t)(d.Nr * d.Nr + ntiles * d.Nr * W) * sizeof(C) > kSmemBudget) W /= 2;
+  return W;
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::angular(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
+                                  bool collision, cudaStream_t s) {
+  static bool init = false;
+  if (!init) { allow_smem(k_angular<T, C>); init = true; }
+  const Dims& d = p.d;
+  const int nb = angular_nb<T, C>(d, 1);
+  const size_t smem = (size_t)(2 * d.NT * d.NT + d.NP * d.NP + nb * (d.NT * d.NP + 1)) * sizeof(C);
+  k_angular<T, C><<<grid1((d.nblk + nb - 1) / nb), kThreads, smem, s>>>(p, t, U, K, sgn,
+                                                                         collision ? 1 : 0, nb);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::plane(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
+                                cudaStream_t s) {
+  static bool init = false;
+  if (!init) { allow_smem(k_plane<T, C>); init = true; }
+  const Dims& d = p.d;
+  const int c = plane_c<T, C>(d, 1);
+  const size_t smem =
+      (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + d.Nt * d.Np * 2 * c) * sizeof(C);
+  const long long nct = (long long)d.G * d.Nr * d.NT * (d.NP / 2 / c);
+  k_plane<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, U, K, sgn, c);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::radial(const Problem& p, const Tables<C>& t, const double* Dr64,
+                                 const T* U, const T* K, C sgn, bool tau, int mode, T* F, T* Acc,
+                                 T* Uout, T* out, double dt, cudaStream_t s) {
+  static bool init = false;
+  if (!init) { allow_smem(k_radial<T, C>); init = true; }
+  const Dims& d = p.d;
+  const int W = radial_W<T, C>(d, 2);
+  const int S = d.NT * d.NP;
+  const size_t smem = (size_t)(d.Nr * d.Nr + 2 * d.Nr * W) * sizeof(C);
+  const long long nct = (long long)d.G * d.Nt * d.Np * ((S + W - 1) / W);
+  k_radial<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, tau ? 1 : 0, mode, F,
+                                                    Acc, Uout, out, (C)dt, W);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::radial_T(const Problem& p, const Tables<C>& t, const T* X,
+                                   double scale, bool tau, T* lt, T* Ubar, cudaStream_t s) {
+  static bool init = false;
+  if (!init) { allow_smem(k_radial_T<T, C>); init = true; }
+  const Dims& d = p.d;
+  const int W = radial_W<T, C>(d, 2);
+  const int S = d.NT * d.NP;
+  const size_t smem = (size_t)(d.Nr * d.Nr + 2 * d.Nr * W) * sizeof(C);
+  const long long nct = (long long)d.G * d.Nt * d.Np * ((S + W - 1) / W);
+  k_radial_T<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, X, (C)scale, tau ? 1 : 0, lt, Ubar,
+                                                      W);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::plane_T(const Problem& p, const Tables<C>& t, const T* lt, T* Ubar,
+                                  cudaStream_t s) {
+  static bool init = false;
+  if (!init) { allow_smem(k_plane_T<T, C>); init = true; }
+  const Dims& d = p.d;
+  const int c = plane_c<T, C>(d, 2);
+  const size_t smem =
+      (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + 2 * d.Nt * d.Np * 2 * c) * sizeof(C);
+  const long long nct = (long long)d.G * d.Nr * d.NT * (d.NP / 2 / c);
+  k_plane_T<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, lt, Ubar, c);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::angular_T(const Problem& p, const Tables<C>& t, const T* lt,
+                                    const T* Ubar, const T* Us, double* gk, double* ge,
+                                    const T* lam, const T* lam_in, T* lam_out, T* Kbar_out,
+                                    double wl, double wu, cudaStream_t s) {
+  static bool init = false;
+  if (!init) { allow_smem(k_angular_T<T, C>); init = true; }
+  const Dims& d = p.d;
+  const int nb = angular_nb<T, C>(d, 2);
+  const size_t smem =
+      (size_t)(2 * d.NT * d.NT + d.NP * d.NP + nb * (2 * d.NT * d.NP + 1)) * sizeof(C);
+  k_angular_T<T, C><<<grid1((d.nblk + nb - 1) / nb), kThreads, smem, s>>>(
+      p, t, lt, Ubar, Us, gk, ge, lam, lam_in, lam_out, Kbar_out, (C)wl, (C)wu, nb);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::implicit_collision(const Problem& p, const Tables<C>& t, T* F,
+                                             double dt, cudaStream_t s) {
+  const int nb = kThreads / 32;
+  k_implicit_collision<T, C><<<grid1((p.d.nblk + nb - 1) / nb), kThreads, 0, s>>>(p, t, F,
+                                                                                 (C)dt, nb);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::apply_inflow(const Problem& p, T* F, cudaStream_t s) {
+  const Dims& d = p.d;
+  const long long n = (long long)d.G * d.Nt * d.Np * d.NT * d.NP;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152 * 32);
+  k_apply_inflow<T><<<grid1(std::max<long long>(blocks, 1)), 256, 0, s>>>(p, F);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::filter(const Problem& p, const Tables<C>& t, T* F, T* tmp,
+                                 cudaStream_t s) {
+  const long long blocks = std::min<long long>((p.d.total + 255) / 256, 152 * 64);
+  const unsigned b = grid1(std::max<long long>(blocks, 1));
+  k_filter_axis<T, C><<<b, 256, 0, s>>>(p, t.FrT, nullptr, 0, F, tmp);
+  k_filter_axis<T, C><<<b, 256, 0, s>>>(p, t.FthAT, t.FthBT, 1, tmp, F);
+  k_filter_axis<T, C><<<b, 256, 0, s>>>(p, t.FphT, nullptr, 2, F, tmp);
+  k_filter_axis<T, C><<<b, 256, 0, s>>>(p, t.FThAT, t.FThBT, 3, tmp, F);
+  k_filter_axis<T, C><<<b, 256, 0, s>>>(p, t.FPhT, nullptr, 4, F, tmp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(F, tmp, (size_t)p.d.total * sizeof(T), cudaMemcpyDeviceToDevice, s);
+}
+
+template <typename T, typename C>
+cudaError_t Launch<T, C>::moments(const Problem& p, const Tables<double>& t64, const double* wr,
+                                  const double* wth, const T* F, double* F0, double* F1,
+                                  double* partN, double* partJ, double* N, double* JR1,
+                                  double* JR2, double R1, double R2, cudaStream_t s) {
+  const Dims& d = p.d;
+  const int wpb = kThreads / 32;
+  k_moments<T><<<grid1((d.nblk + wpb - 1) / wpb), kThreads, 0, s>>>(p, t64, wr, wth, F, F0, F1,
+                                                                     partN, partJ, R1, R2);
+  k_moments_reduce<<<d.G, kThreads, 0, s>>>(d, partN, partJ, N, JR1, JR2);
+  return cudaGetLastError();
+}
+
+}  // namespace ts

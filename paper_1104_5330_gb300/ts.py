@@ -1,0 +1,280 @@
+"""Thin Python binding of the C ABI in include/ts.h.
+
+Every function here only marshals arguments (tensor data pointers, the
+current CUDA stream) into the same-named C entry point of libts.so; all
+arithmetic of the step runs in the library's CUDA kernels. There is no CPU
+fallback: if libts.so cannot be loaded the import of this module raises.
+
+Tensors are torch tensors on the CUDA device, contiguous, with the element
+type of the grid (float64 for TS_FP64, float32 for TS_FP32); coefficient
+fields, gradients and moments are float64. Layouts follow include/ts.h:
+F[g][r][theta][phi][Theta][Phi], coefficients [g][r][theta][phi].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libts.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ts.h")
+
+TS_OK, TS_ERR_ARG, TS_ERR_UNSUPPORTED, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE = range(7)
+TS_FP64, TS_FP32 = 0, 1
+TS_RK4, TS_RK4_SPLIT_IMPLICIT = 0, 1
+TS_BC_TAU_INFLOW, TS_BC_NONE = 0, 1
+
+STATUS_NAMES = ["TS_OK", "TS_ERR_ARG", "TS_ERR_UNSUPPORTED", "TS_ERR_OOM", "TS_ERR_CUDA",
+                "TS_ERR_TIMEOUT", "TS_ERR_STATE"]
+
+
+class TSError(RuntimeError):
+    def __init__(self, status, where, text):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {text}")
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("R1", ctypes.c_double), ("R2", ctypes.c_double),
+                ("Nr", ctypes.c_int), ("Ntheta", ctypes.c_int), ("Nphi", ctypes.c_int),
+                ("NTheta", ctypes.c_int), ("NPhi", ctypes.c_int), ("groups", ctypes.c_int),
+                ("precision", ctypes.c_int), ("scheme", ctypes.c_int), ("bc", ctypes.c_int),
+                ("filter_on", ctypes.c_int), ("filter_alpha", ctypes.c_double),
+                ("filter_order", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libts.so not built ({LIB_PATH}); run __graft_entry__.build() "
+                          "or python -m paper_1104_5330_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "ts_create_grid": [ctypes.POINTER(GridDesc), ctypes.POINTER(P)],
+        "ts_destroy_grid": [P],
+        "ts_grid_nodes": [P, P, P, P, P, P],
+        "ts_set_coeffs": [P, P, P, P, P, P, P],
+        "ts_apply_inflow": [P, P, P],
+        "ts_step": [P, P, D, I, P],
+        "ts_step_host": [P, P, D, I, P],
+        "ts_step_profile": [P, P, D, I, P, P, P],
+        "ts_rhs": [P, P, P, P],
+        "ts_liouville": [P, P, P, P],
+        "ts_adjoint_step": [P, P, P, P, P, D, P],
+        "ts_flux_weights": [P, P, P],
+        "ts_moments": [P, P, P, P, P, P, P, P],
+        "ts_sync_status": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.ts_last_error.restype = ctypes.c_char_p
+    lib.ts_last_error.argtypes = []
+    lib.ts_version.restype = ctypes.c_char_p
+    lib.ts_version.argtypes = []
+    lib.ts_field_elems.restype = S
+    lib.ts_field_elems.argtypes = [P]
+    return lib
+
+
+LIB = _load()
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions include/ts.h declares."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ts_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _check(status, where):
+    if status != TS_OK:
+        raise TSError(status, where, LIB.ts_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def ts_version() -> str:
+    return LIB.ts_version().decode()
+
+
+def ts_create_grid(desc: GridDesc):
+    h = ctypes.c_void_p()
+    _check(LIB.ts_create_grid(ctypes.byref(desc), ctypes.byref(h)), "ts_create_grid")
+    return h
+
+
+def ts_destroy_grid(grid):
+    _check(LIB.ts_destroy_grid(grid), "ts_destroy_grid")
+
+
+def ts_field_elems(grid) -> int:
+    return int(LIB.ts_field_elems(grid))
+
+
+def ts_grid_nodes(grid, desc: GridDesc):
+    import numpy as np
+    out = [np.zeros(n) for n in (desc.Nr, desc.Ntheta, desc.Nphi, desc.NTheta, desc.NPhi)]
+    _check(LIB.ts_grid_nodes(grid, *[o.ctypes.data_as(ctypes.c_void_p) for o in out]),
+           "ts_grid_nodes")
+    return out
+
+
+def ts_set_coeffs(grid, kappa, eta, kappa_s, inflow_R1=None, inflow_R2=None, stream=None):
+    _check(LIB.ts_set_coeffs(grid, _ptr(kappa), _ptr(eta), _ptr(kappa_s), _ptr(inflow_R1),
+                             _ptr(inflow_R2), _stream(stream)), "ts_set_coeffs")
+
+
+def ts_apply_inflow(grid, F, stream=None):
+    _check(LIB.ts_apply_inflow(grid, _ptr(F), _stream(stream)), "ts_apply_inflow")
+
+
+def ts_step(grid, F, dt, nsteps=1, stream=None):
+    _check(LIB.ts_step(grid, _ptr(F), float(dt), int(nsteps), _stream(stream)), "ts_step")
+
+
+def ts_step_profile(grid, F, dt, nsteps=1, stream=None):
+    """Returns (pass_ms[4], launches[4]) summed over the steps: angular-block,
+    plane, radial passes and other kernels."""
+    import numpy as np
+    ms = np.zeros(4)
+    n = np.zeros(4, dtype=np.int32)
+    _check(LIB.ts_step_profile(grid, _ptr(F), float(dt), int(nsteps),
+                               ms.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                               _stream(stream)), "ts_step_profile")
+    return ms, n
+
+
+def ts_step_host(grid, F_host, dt, nsteps=1, stream=None):
+    """F_host: a CPU tensor (pinned for full bandwidth), updated in place."""
+    if F_host.is_cuda:
+        raise ValueError("ts_step_host takes a host tensor")
+    _check(LIB.ts_step_host(grid, _ptr(F_host), float(dt), int(nsteps), _stream(stream)),
+           "ts_step_host")
+
+
+def ts_rhs(grid, F, K, stream=None):
+    _check(LIB.ts_rhs(grid, _ptr(F), _ptr(K), _stream(stream)), "ts_rhs")
+
+
+def ts_liouville(grid, F, LF, stream=None):
+    _check(LIB.ts_liouville(grid, _ptr(F), _ptr(LF), _stream(stream)), "ts_liouville")
+
+
+def ts_adjoint_step(grid, F_n, lam, grad_kappa, grad_eta, dt, stream=None):
+    _check(LIB.ts_adjoint_step(grid, _ptr(F_n), _ptr(lam), _ptr(grad_kappa), _ptr(grad_eta),
+                               float(dt), _stream(stream)), "ts_adjoint_step")
+
+
+def ts_flux_weights(grid, w, stream=None):
+    _check(LIB.ts_flux_weights(grid, _ptr(w), _stream(stream)), "ts_flux_weights")
+
+
+def ts_moments(grid, F, F0=None, F1=None, N=None, J_R1=None, J_R2=None, stream=None):
+    _check(LIB.ts_moments(grid, _ptr(F), _ptr(F0), _ptr(F1), _ptr(N), _ptr(J_R1), _ptr(J_R2),
+                          _stream(stream)), "ts_moments")
+
+
+def ts_sync_status(grid, stream=None):
+    _check(LIB.ts_sync_status(grid, _stream(stream)), "ts_sync_status")
+
+
+class Grid:
+    """Owning handle around ts_create_grid/ts_destroy_grid with tensor helpers."""
+
+    def __init__(self, R1=0.2, R2=1.0, Nr=17, Ntheta=8, Nphi=8, NTheta=8, NPhi=8, groups=1,
+                 precision=TS_FP64, scheme=TS_RK4, bc=TS_BC_TAU_INFLOW, filter_on=False,
+                 filter_alpha=36.0, filter_order=16, device=None):
+        self.desc = GridDesc(R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups, precision, scheme,
+                             bc, int(filter_on), filter_alpha, filter_order)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.handle = ts_create_grid(self.desc)
+        self.shape = (groups, Nr, Ntheta, Nphi, NTheta, NPhi)
+        self.coef_shape = (groups, Nr, Ntheta, Nphi)
+        self.inflow_shape = (groups, Ntheta, Nphi, NTheta // 2, NPhi)
+        self.dtype = torch.float64 if precision == TS_FP64 else torch.float32
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            ts_destroy_grid(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def points(self):
+        n = 1
+        for s in self.shape:
+            n *= s
+        return n
+
+    def nodes(self):
+        return ts_grid_nodes(self.handle, self.desc)
+
+    def empty(self):
+        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
+
+    def set_coeffs(self, kappa=None, eta=None, kappa_s=None, inflow_R1=None, inflow_R2=None):
+        cv = lambda a, dt: None if a is None else torch.as_tensor(a, dtype=dt, device=self.device).contiguous()
+        self._coeffs = [cv(kappa, torch.float64), cv(eta, torch.float64), cv(kappa_s, torch.float64),
+                        cv(inflow_R1, self.dtype), cv(inflow_R2, self.dtype)]
+        ts_set_coeffs(self.handle, *self._coeffs)
+
+    def apply_inflow(self, F):
+        ts_apply_inflow(self.handle, F)
+        return F
+
+    def step(self, F, dt, nsteps=1):
+        ts_step(self.handle, F, dt, nsteps)
+        return F
+
+    def rhs(self, F, K=None):
+        K = torch.empty_like(F) if K is None else K
+        ts_rhs(self.handle, F, K)
+        return K
+
+    def liouville(self, F, LF=None):
+        LF = torch.empty_like(F) if LF is None else LF
+        ts_liouville(self.handle, F, LF)
+        return LF
+
+    def adjoint_step(self, F_n, lam, grad_kappa, grad_eta, dt):
+        ts_adjoint_step(self.handle, F_n, lam, grad_kappa, grad_eta, dt)
+        return lam
+
+    def flux_weights(self):
+        w = torch.empty(self.shape[2:], dtype=torch.float64, device=self.device)
+        ts_flux_weights(self.handle, w)
+        return w
+
+    def moments(self, F):
+        G = self.shape[0]
+        F0 = torch.empty(self.coef_shape, dtype=torch.float64, device=self.device)
+        F1 = torch.empty((3,) + self.coef_shape, dtype=torch.float64, device=self.device)
+        N = torch.empty(G, dtype=torch.float64, device=self.device)
+        J1 = torch.empty(G, dtype=torch.float64, device=self.device)
+        J2 = torch.empty(G, dtype=torch.float64, device=self.device)
+        ts_moments(self.handle, F, F0, F1, N, J1, J2)
+        return F0, F1, N, J1, J2

@@ -1,0 +1,214 @@
+"""Parity of the CUDA library (called through the C ABI) with the FP64 oracle.
+
+Bar: relative L2 <= 1e-12 for the FP64 path (element by element on the same
+seeded inputs), <= 1e-5 for the FP32 variant. Grids are chosen so every pass
+runs several tiles with a ragged last tile, plus the full-size workloads of
+the benchmark (one step, every element).
+"""
+import numpy as np
+import pytest
+import torch
+
+import analytic as A
+from gpu_common import T, absorber_workload, cuda, host, pair, rel_l2, setup_both
+from oracle.transport import Problem as OProblem, exact_free_streaming
+from paper_1104_5330_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+RAGGED = (0.2, 1.0, 11, 7, 10, 6, 12)     # odd N_theta; tiles do not divide the grid
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1104_5330_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield
+
+
+def test_nodes_match_oracle():
+    og, gg = pair(0.3, 1.7, 13, 9, 10, 8, 6)
+    for a, b in zip(gg.nodes(), (og.r, og.theta, og.phi, og.Theta, og.Phi)):
+        assert np.abs(a - b).max() < 1e-15
+
+
+@pytest.mark.parametrize("name", ["x", "wx", "xy+wz", "x*wy-z^2", "cubic"])
+def test_liouville_exact_on_cartesian_polynomials(name):
+    """L_h P = omega . grad P on the GPU too (Eqs. prop2, propf; SymPy)."""
+    og, gg = pair(0.2, 1.0, 9, 8, 8, 8, 8)
+    P, adv = A.cartesian_case(name)
+    F = A.on_grid(P, og)
+    E = A.on_grid(adv, og)
+    LF = host(gg.liouville(cuda(F)))
+    assert np.abs(LF - E).max() / max(1.0, np.abs(E).max()) < 1e-12
+
+
+@pytest.mark.parametrize("dims", [RAGGED, (0.2, 1.0, 9, 8, 8, 8, 8), (0.5, 2.0, 5, 4, 2, 2, 4),
+                                  (0.2, 1.0, 3, 2, 2, 2, 2)])
+def test_liouville_parity(dims):
+    og, gg = pair(*dims, G=2)
+    F = np.random.default_rng(1).standard_normal(og.shape)
+    assert rel_l2(host(gg.liouville(cuda(F))), og.liouville(F)) < FP64_TOL
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_rhs_parity(bc):
+    og, gg = pair(*RAGGED, G=3, bc=bc)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap * 1.7, eta, ks, gR1, gR2, bc="tau" if bc == 0 else "none")
+    F = F0 + 0.1 * np.random.default_rng(2).standard_normal(og.shape)
+    assert rel_l2(host(gg.rhs(cuda(F))), op.rhs(F)) < FP64_TOL
+
+
+def test_step_parity_gaussian_shell_17x8():
+    """Vacuum free streaming, 17 x 8^4, zero inflow, dt = 0.4 h_min, 100 RK4 steps."""
+    og, gg = pair(0.2, 1.0, 17, 8, 8, 8, 8)
+    op = setup_both(og, gg, None, None, None)
+    F0 = op.apply_inflow(I.gaussian_shell(og.r, og.theta, og.phi, og.Theta, og.Phi))
+    dt = I.dt_rule(0.2, 1.0, 17)
+    Fg = gg.apply_inflow(cuda(I.gaussian_shell(og.r, og.theta, og.phi, og.Theta, og.Phi)))
+    assert rel_l2(host(Fg), F0) == 0.0
+    gg.step(Fg, dt, 100)
+    Fo = op.run(F0, dt, 100)
+    assert rel_l2(host(Fg), Fo) < FP64_TOL
+    # and the free-streaming solution itself (discretisation error at this size)
+    ex = exact_free_streaming(og, lambda r, mu: np.exp(-((r - 0.6) / 0.1) ** 2) * (1 + 0.5 * mu), 100 * dt)
+    assert np.abs(host(Fg)[0, :, 0, 0, :, 0] - ex).max() < 0.05
+
+
+def test_step_parity_absorber_ragged_groups():
+    og, gg = pair(*RAGGED, G=4)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    Fg = cuda(F0)
+    gg.step(Fg, dt, 40)
+    assert rel_l2(host(Fg), op.run(F0, dt, 40)) < FP64_TOL
+
+
+def test_step_parity_absorber_full_size_33x16():
+    """The benchmark workload at full size: 33 x 16^4, 4 groups, every element
+    after 2 steps in the launch configuration the benchmark times."""
+    og, gg = pair(0.2, 1.0, 33, 16, 16, 16, 16, G=4)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.2, 1.0, 33)
+    Fg = cuda(F0)
+    gg.step(Fg, dt, 2)
+    assert rel_l2(host(Fg), op.run(F0, dt, 2)) < FP64_TOL
+
+
+def test_rhs_parity_full_size_65x32():
+    """One stage derivative on the 65 x 32^4 grid (68M points), every element."""
+    og, gg = pair(0.2, 1.0, 65, 32, 32, 32, 32)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    Kg = host(gg.rhs(cuda(F0)))
+    assert rel_l2(Kg, op.rhs(F0)) < FP64_TOL
+
+
+def test_split_implicit_parity():
+    og, gg = pair(*RAGGED, G=2, scheme=1)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, 60.0 * kap, eta, ks, gR1, gR2, scheme="split")
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    Fg = cuda(F0)
+    gg.step(Fg, dt, 10)
+    assert rel_l2(host(Fg), op.run(F0, dt, 10)) < FP64_TOL
+
+
+def test_filter_parity():
+    og, gg = pair(*RAGGED, G=1, filter_on=True)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2, filter_on=True)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    F = F0 + 0.05 * np.random.default_rng(4).standard_normal(og.shape)
+    Fg = cuda(F)
+    gg.step(Fg, dt, 5)
+    assert rel_l2(host(Fg), op.run(F, dt, 5)) < FP64_TOL
+
+
+def test_moments_parity():
+    og, gg = pair(*RAGGED, G=2)
+    F = np.random.default_rng(5).standard_normal(og.shape) + 2.0
+    gg.set_coeffs()
+    F0g, F1g, Ng, J1g, J2g = [host(x) for x in gg.moments(cuda(F))]
+    F0o, F1o, No, J1o, J2o = og.moments(F)
+    assert rel_l2(F0g, F0o) < FP64_TOL
+    assert rel_l2(F1g, F1o) < FP64_TOL
+    assert rel_l2(Ng, No) < FP64_TOL
+    assert rel_l2(J1g, J1o) < FP64_TOL and rel_l2(J2g, J2o) < FP64_TOL
+
+
+def test_flux_weights_match_oracle():
+    og, gg = pair(*RAGGED)
+    assert rel_l2(host(gg.flux_weights()), og.outgoing_flux_weights()) < 1e-14
+
+
+def test_adjoint_parity_with_oracle():
+    og, gg = pair(*RAGGED, G=2)
+    kap, eta, ks = I.gradient_fields(og.r, og.theta, og.phi, 2, 1104, 0.2, 1.0)
+    F0 = np.stack([I.seeded_smooth(og.r, og.theta, og.phi, og.Theta, og.Phi, 1104 + g, 0.2, 1.0)
+                   for g in range(2)])
+    gR1, gR2 = I.inflow_from(F0, og.NT)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    lam = np.random.default_rng(6).standard_normal(og.shape)
+    lo, gko, geo = op.adjoint_step(F0, lam, dt)
+    lg = cuda(lam)
+    gk = torch.zeros(og.G, og.Nr, og.Nt, og.Np, dtype=torch.float64, device="cuda")
+    ge = torch.zeros_like(gk)
+    gg.adjoint_step(cuda(F0), lg, gk, ge, dt)
+    assert rel_l2(host(lg), lo) < FP64_TOL
+    assert rel_l2(host(gk), gko) < FP64_TOL
+    assert rel_l2(host(ge), geo) < FP64_TOL
+
+
+def test_fp32_variant_against_oracle():
+    og, gg = pair(*RAGGED, G=2, precision=1)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    Fg = cuda(F0, torch.float32)
+    gg.step(Fg, dt, 40)
+    assert rel_l2(host(Fg), op.run(F0, dt, 40)) < FP32_TOL
+
+
+def test_bitwise_deterministic():
+    og, gg = pair(*RAGGED, G=2)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    gg.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    a, b = cuda(F0), cuda(F0)
+    gg.step(a, dt, 5)
+    gg.step(b, dt, 5)
+    assert torch.equal(a, b)
+
+
+def test_step_host_matches_device_step():
+    og, gg = pair(*RAGGED, G=1)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    gg.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    Fd = cuda(F0)
+    gg.step(Fd, dt, 3)
+    Fh = torch.as_tensor(F0).clone().pin_memory()
+    T().ts_step_host(gg.handle, Fh, dt, 3)
+    assert torch.equal(Fh, Fd.cpu())
+
+
+def test_zero_steps_and_state_errors():
+    og, gg = pair(*RAGGED)
+    F = cuda(np.ones(og.shape))
+    with pytest.raises(T().TSError) as e:
+        gg.step(F, 0.01, 1)          # coefficients not set yet
+    assert e.value.status == T().TS_ERR_STATE
+    gg.set_coeffs()
+    gg.step(F, 0.01, 0)
+    assert torch.equal(F, cuda(np.ones(og.shape)))
+    with pytest.raises(T().TSError):
+        gg.step(F, float("nan"), 1)

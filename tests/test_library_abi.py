@@ -1,0 +1,52 @@
+"""CPU-side checks of the C ABI: the library builds, loads, exports every
+function include/ts.h declares, and rejects bad arguments before touching the
+device (these calls return before any CUDA call)."""
+import ctypes
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_1104_5330_gb300 import build
+    build.build()
+    import paper_1104_5330_gb300.ts as T
+    return T
+
+
+def test_every_declared_symbol_is_exported(T):
+    names = T.declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(T.LIB, n), n
+    assert "sm_103a" in T.ts_version()
+
+
+def _desc(T, **kw):
+    d = dict(R1=0.2, R2=1.0, Nr=9, Ntheta=8, Nphi=8, NTheta=8, NPhi=8, groups=1,
+             precision=T.TS_FP64, scheme=T.TS_RK4, bc=T.TS_BC_TAU_INFLOW, filter_on=0,
+             filter_alpha=36.0, filter_order=16)
+    d.update(kw)
+    return T.GridDesc(**d)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(Nr=2), 2), (dict(Nr=200), 2), (dict(Nphi=7), 2), (dict(NTheta=5), 2),
+    (dict(NPhi=3), 2), (dict(NTheta=66), 2), (dict(R1=0.0), 1), (dict(R2=0.1), 1),
+    (dict(groups=0), 1), (dict(precision=9), 2), (dict(scheme=4), 2), (dict(bc=3), 2),
+])
+def test_create_grid_rejects_bad_descriptors(T, kw, status):
+    h = ctypes.c_void_p()
+    st = T.LIB.ts_create_grid(ctypes.byref(_desc(T, **kw)), ctypes.byref(h))
+    assert st == status
+    assert h.value is None
+    assert len(T.LIB.ts_last_error()) > 0
+
+
+def test_null_arguments_are_rejected(T):
+    assert T.LIB.ts_create_grid(None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_step(None, None, ctypes.c_double(0.1), 1, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_moments(None, None, None, None, None, None, None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_adjoint_step(None, None, None, None, None, ctypes.c_double(0.1), None) == T.TS_ERR_ARG
+    assert T.LIB.ts_destroy_grid(None) == T.TS_OK
+    assert T.LIB.ts_field_elems(None) == 0
