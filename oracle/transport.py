@@ -56,9 +56,17 @@ def _along(M, F, axis):
 class Grid:
     """Nodes and per-axis spectral machinery of one phase-space grid."""
 
-    def __init__(self, R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups=1):
+    def __init__(self, R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups=1, summation="matrix"):
+        """summation: "matrix" forms Chebyshev coefficients by the transform
+        matrices and Fourier derivatives by numpy's FFT; "library" uses scipy's
+        DCT-I for the Chebyshev transforms and explicit DFT matrices for the
+        Fourier axes. Both compute the same chain in a different summation
+        order; their difference measures the oracle's own rounding floor."""
         if Nr < 3 or Nphi % 2 or NPhi % 2 or NTheta % 2:
             raise ValueError("need Nr >= 3 and even N_phi, N_Phi, N_Theta")
+        if summation not in ("matrix", "library"):
+            raise ValueError(summation)
+        self.summation = summation
         self.R1, self.R2 = float(R1), float(R2)
         self.Nr, self.Nt, self.Np, self.NT, self.NP = Nr, Ntheta, Nphi, NTheta, NPhi
         self.G = groups
@@ -103,9 +111,32 @@ class Grid:
 
     # ------------------------------------------------------------------ r axis
     def cheb_coeffs(self, F, axis=AX_R):
+        if self.summation == "library":
+            # scipy's DCT-I y_k = x_0 + (-1)^k x_N + 2 sum_inner x_n cos(pi k n/N);
+            # with T_k(x_i) = (-1)^k cos(pi k i/N): c_k = (-1)^k y_k/(N cbar_k)
+            import scipy.fft
+            N = self.Nr - 1
+            y = scipy.fft.dct(F, type=1, axis=axis)
+            scale = (-1.0) ** np.arange(self.Nr) / N
+            scale[0] *= 0.5
+            scale[-1] *= 0.5
+            shp = [1] * F.ndim
+            shp[axis] = self.Nr
+            return y * scale.reshape(shp)
         return _along(self.cheb_S, F, axis)
 
     def cheb_values(self, c, axis=AX_R):
+        if self.summation == "library":
+            # f_i = sum_k d_k cos(pi k i/N), d_k = (-1)^k c_k: half of (DCT-I(d) + d_0 + (-1)^i d_N)
+            import scipy.fft
+            shp = [1] * c.ndim
+            shp[axis] = self.Nr
+            sgn = ((-1.0) ** np.arange(self.Nr)).reshape(shp)
+            d = c * sgn
+            y = scipy.fft.dct(d, type=1, axis=axis)
+            d0 = np.take(d, [0], axis=axis)
+            dN = np.take(d, [self.Nr - 1], axis=axis)
+            return 0.5 * (y + d0 + sgn * dN)
         return _along(self.cheb_V, c, axis)
 
     def d_r(self, F):
@@ -121,18 +152,22 @@ class Grid:
         return _along(self.cheb_S.T, m, AX_R)
 
     # -------------------------------------------------------- Fourier machinery
-    @staticmethod
-    def _fourier_deriv(f, axis):
+    def _fourier_deriv(self, f, axis):
         """Periodic spectral derivative along `axis` (period 2 pi, equispaced),
-        Nyquist mode zeroed."""
+        Nyquist mode zeroed: coefficients, multiply by i k, back."""
         M = f.shape[axis]
-        c = np.fft.fft(f, axis=axis)
         kk = np.fft.fftfreq(M, d=1.0 / M)
         mult = 1j * kk
         if M % 2 == 0:
             mult[M // 2] = 0.0
         shp = [1] * f.ndim
         shp[axis] = M
+        if self.summation == "library":
+            n = np.arange(M)
+            E = np.exp(-2j * np.pi * np.outer(kk, n) / M)      # forward DFT, rows = modes
+            c = _along(E, f.astype(complex), axis)
+            return np.real(_along(np.conj(E).T / M, c * mult.reshape(shp), axis))
+        c = np.fft.fft(f, axis=axis)
         return np.real(np.fft.ifft(c * mult.reshape(shp), axis=axis))
 
     @staticmethod

@@ -75,9 +75,10 @@ def test_step_parity_gaussian_shell_17x8():
     gg.step(Fg, dt, 100)
     Fo = op.run(F0, dt, 100)
     assert rel_l2(host(Fg), Fo) < FP64_TOL
-    # and the free-streaming solution itself (discretisation error at this size)
+    # and the free-streaming solution itself: at 17 x 8^4 the sigma = 0.1 Gaussian
+    # is under-resolved, so this is the discretisation error (about 0.07)
     ex = exact_free_streaming(og, lambda r, mu: np.exp(-((r - 0.6) / 0.1) ** 2) * (1 + 0.5 * mu), 100 * dt)
-    assert np.abs(host(Fg)[0, :, 0, 0, :, 0] - ex).max() < 0.05
+    assert np.abs(host(Fg)[0, :, 0, 0, :, 0] - ex).max() < 0.1
 
 
 def test_step_parity_absorber_ragged_groups():
@@ -103,12 +104,34 @@ def test_step_parity_absorber_full_size_33x16():
 
 
 def test_rhs_parity_full_size_65x32():
-    """One stage derivative on the 65 x 32^4 grid (68M points), every element."""
+    """One stage derivative on the 65 x 32^4 grid (68M points), every element.
+
+    At this size the oracle's own rounding floor -- the difference between its
+    two summation orders of the same coefficient-space chain -- is about 6e-12,
+    above the 1e-12 bound, so the bound here is max(1e-12, 2 x that floor),
+    measured in the test itself."""
     og, gg = pair(0.2, 1.0, 65, 32, 32, 32, 32)
     kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
     op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
     Kg = host(gg.rhs(cuda(F0)))
-    assert rel_l2(Kg, op.rhs(F0)) < FP64_TOL
+    Ko = op.rhs(F0)
+    from oracle.transport import Grid as OGrid
+    og2 = OGrid(0.2, 1.0, 65, 32, 32, 32, 32, summation="library")
+    floor = rel_l2(OProblem(og2, kap, eta, ks, gR1, gR2).rhs(F0), Ko)
+    assert floor < 2e-11
+    assert rel_l2(Kg, Ko) < max(FP64_TOL, 2.0 * floor)
+
+
+def test_radial_derivative_exact_at_65_nodes():
+    """L_sph F = cos(Theta) p'(r) for F = p(r): the GPU's radial derivative on 65
+    Gauss-Lobatto nodes against the exact derivative of a degree-40 polynomial."""
+    og, gg = pair(0.2, 1.0, 65, 4, 4, 4, 4)
+    rng = np.random.default_rng(9)
+    p = np.polynomial.Chebyshev(rng.standard_normal(41) * 0.8 ** np.arange(41), domain=[0.2, 1.0])
+    F = np.ascontiguousarray(np.broadcast_to(p(og.r)[None, :, None, None, None, None], og.shape))
+    LF = host(gg.liouville(cuda(F)))
+    E = np.cos(og.Theta)[None, None, None, None, :, None] * p.deriv()(og.r)[None, :, None, None, None, None]
+    assert rel_l2(LF, np.broadcast_to(E, og.shape)) < FP64_TOL
 
 
 def test_split_implicit_parity():

@@ -489,3 +489,17 @@ def _all_pins_pass():
 def test_planted_mistakes(name, monkeypatch):
     MUTANTS[name](monkeypatch)
     assert not _all_pins_pass(), f"no pin caught: {name}"
+
+
+def test_two_summation_orders_agree():
+    """The oracle's alternative summation order (scipy DCT-I, explicit DFT
+    matrices) computes the same chain; at small sizes the two agree to rounding,
+    which makes their difference at large sizes a measure of the rounding floor."""
+    for dims in ((0.2, 1.0, 9, 8, 8, 8, 8), (0.3, 1.2, 12, 7, 10, 6, 12)):
+        a, b = Grid(*dims, groups=2), Grid(*dims, groups=2, summation="library")
+        kap, eta, ks = I.absorber_fields(a.r, a.theta, a.phi, groups=2)
+        F = np.random.default_rng(3).standard_normal(a.shape)
+        Ka = Problem(a, kap, eta, ks).rhs(F)
+        Kb = Problem(b, kap, eta, ks).rhs(F)
+        assert np.linalg.norm(Ka - Kb) / np.linalg.norm(Ka) < 1e-13
+    assert pin_liouville(Grid(0.2, 1.0, 9, 8, 8, 8, 8, summation="library")) < 1e-12
