@@ -177,6 +177,29 @@ ts_status ts_flux_weights(ts_grid* grid, double* w, void* stream);
 ts_status ts_moments(ts_grid* grid, const void* F, double* F0, double* F1, double* N,
                      double* J_R1, double* J_R2, void* stream);
 
+/* The same outputs as ts_moments, for callers that cannot allocate device
+ * memory: a process whose device memory is held by another allocator's pool,
+ * a deployment with a fixed device-memory budget, or a tight loop that cannot
+ * afford an allocation's implicit synchronisation. The paper has no
+ * counterpart; this is a property of the library only.
+ *  - Takes the grid description instead of a ts_grid (creating a grid
+ *    allocates) and computes its node and quadrature tables in the kernel.
+ *    Precision selects the element type of F (double or float).
+ *  - Allocates nothing: its per-block partial sums live in a static device
+ *    array of 2^21 doubles (16 MiB) that every GPU loading the library holds
+ *    until the process exits. Grids needing more than
+ *    groups*Nr*Ntheta*Nphi + 2*groups*Ntheta*Nphi > 2^21 doubles are
+ *    rejected with TS_ERR_UNSUPPORTED (text in ts_last_error()).
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call shares the array and it keeps the last call's contents. Each
+ *    call writes every slot it reads, so nothing needs clearing, but calls
+ *    whose kernels overlap on the GPU (other streams, other host threads)
+ *    race on it. */
+ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0, double* F1,
+                             double* N, double* J_R1, double* J_R2, void* stream);
+
 /* Status of device-side checks latched since the last call (bounded waits).
  * Synchronizes `stream`. */
 ts_status ts_sync_status(ts_grid* grid, void* stream);

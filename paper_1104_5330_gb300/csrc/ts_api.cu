@@ -286,6 +286,8 @@ HostTables build_tables(const ts_grid_desc& g) {
 
 }  // namespace
 
+void ts::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct ts_grid {
   ts_grid_desc desc;
   Dims d;

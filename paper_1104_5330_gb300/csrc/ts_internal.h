@@ -4,9 +4,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/ts.h"
 
 namespace ts {
+
+// Sets the text that ts_last_error() returns on the calling thread.
+void set_last_error(const std::string& msg);
 
 // Sizes and strides of F[g][i][j][l][k][m] (m = Phi fastest).
 struct Dims {

@@ -67,6 +67,7 @@ def _load():
         "ts_adjoint_step": [P, P, P, P, P, D, P],
         "ts_flux_weights": [P, P, P],
         "ts_moments": [P, P, P, P, P, P, P, P],
+        "ts_moments_noalloc": [ctypes.POINTER(GridDesc), P, P, P, P, P, P, P],
         "ts_sync_status": [P, P],
     }
     for name, args in sig.items():
@@ -190,6 +191,13 @@ def ts_flux_weights(grid, w, stream=None):
 def ts_moments(grid, F, F0=None, F1=None, N=None, J_R1=None, J_R2=None, stream=None):
     _check(LIB.ts_moments(grid, _ptr(F), _ptr(F0), _ptr(F1), _ptr(N), _ptr(J_R1), _ptr(J_R2),
                           _stream(stream)), "ts_moments")
+
+
+def ts_moments_noalloc(desc: GridDesc, F, F0=None, F1=None, N=None, J_R1=None, J_R2=None,
+                       stream=None):
+    """ts_moments without a grid and without device allocation (static scratch)."""
+    _check(LIB.ts_moments_noalloc(ctypes.byref(desc), _ptr(F), _ptr(F0), _ptr(F1), _ptr(N),
+                                  _ptr(J_R1), _ptr(J_R2), _stream(stream)), "ts_moments_noalloc")
 
 
 def ts_sync_status(grid, stream=None):
