@@ -1,0 +1,108 @@
+"""Gradients of the outgoing flux through R2 (Eq. Flux) after n steps with
+respect to the absorption kappa and the emissivity eta, via the library's
+discrete adjoint behind torch.autograd with sqrt(N) checkpointing: against the
+oracle's discrete adjoint (1e-12) and against central finite differences of the
+GPU forward (1e-6)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import T, cuda, host, pair, rel_l2
+from oracle.transport import Problem as OProblem
+from paper_1104_5330_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1104_5330_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+def _workload(og, seed=1104):
+    G = og.G
+    kap, eta, ks = I.gradient_fields(og.r, og.theta, og.phi, G, seed, og.R1, og.R2)
+    F0 = np.stack([I.seeded_smooth(og.r, og.theta, og.phi, og.Theta, og.Phi, seed + g, og.R1, og.R2)
+                   for g in range(G)])
+    gR1, gR2 = I.inflow_from(F0, og.NT)
+    return kap, eta, ks, F0, gR1, gR2
+
+
+def _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, n, segment=None):
+    from paper_1104_5330_gb300.autograd import outgoing_flux, transport_steps
+    k = cuda(kap).requires_grad_()
+    e = cuda(eta).requires_grad_()
+    F = transport_steps(gg, cuda(F0), k, e, cuda(ks), dt, n, cuda(gR1), cuda(gR2), segment)
+    J = outgoing_flux(gg, F).sum()
+    J.backward()
+    return float(J), k.grad, e.grad, F
+
+
+def test_gradients_match_oracle_adjoint():
+    og, gg = pair(0.2, 1.0, 11, 7, 10, 6, 12, G=2)
+    kap, eta, ks, F0, gR1, gR2 = _workload(og)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    n = 7
+    _, gk, ge, _ = _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, n)
+    op = OProblem(og, kap, eta, ks, gR1, gR2)
+    Fs = [F0]
+    for _ in range(n):
+        Fs.append(op.rk4_step(Fs[-1], dt))
+    lam = np.zeros(og.shape)
+    lam[:, -1] = og.outgoing_flux_weights()
+    GK, GE = np.zeros_like(kap), np.zeros_like(eta)
+    for i in range(n - 1, -1, -1):
+        lam, a, b = op.adjoint_step(Fs[i], lam, dt)
+        GK += a
+        GE += b
+    assert rel_l2(host(gk), GK) < 1e-12
+    assert rel_l2(host(ge), GE) < 1e-12
+
+
+def test_checkpointing_does_not_change_gradients():
+    og, gg = pair(0.2, 1.0, 11, 7, 10, 6, 12, G=1)
+    kap, eta, ks, F0, gR1, gR2 = _workload(og)
+    dt = I.dt_rule(0.2, 1.0, og.Nr)
+    J1, k1, e1, F1 = _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, 10, segment=10)
+    J2, k2, e2, F2 = _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, 10, segment=None)   # ceil(sqrt(10)) = 4
+    J3, k3, e3, F3 = _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, 10, segment=1)
+    assert J1 == J2 == J3
+    assert torch.equal(k1, k2) and torch.equal(k1, k3)
+    assert torch.equal(e1, e2) and torch.equal(e1, e3)
+
+
+@pytest.mark.parametrize("dims,G,n", [((0.2, 1.0, 11, 7, 10, 6, 12), 2, 20),
+                                      ((0.2, 1.0, 33, 16, 16, 16, 16), 8, 200)])
+def test_gradients_match_central_differences(dims, G, n):
+    """The gradient workload: kappa in [0.5, 5] and eta from seeded smooth fields;
+    the 33 x 16^4 x 8-group case is the full-size gradient workload (200 steps)."""
+    og, gg = pair(*dims, G=G)
+    kap, eta, ks, F0, gR1, gR2 = _workload(og)
+    dt = I.dt_rule(dims[0], dims[1], dims[2])
+    _, gk, ge, _ = _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, n)
+    gk, ge = host(gk), host(ge)
+    from paper_1104_5330_gb300.autograd import outgoing_flux
+
+    def J(k, e):
+        gg.set_coeffs(k, e, ks, gR1, gR2)
+        F = cuda(F0)
+        gg.step(F, dt, n)
+        return float(outgoing_flux(gg, F).sum())
+
+    rng = np.random.default_rng(17)
+    for which, grad in (("kappa", gk), ("eta", ge)):
+        for _ in range(2):
+            v = I.seeded_smooth(og.r, og.theta, og.phi, None, None, int(rng.integers(1 << 30)),
+                                og.R1, og.R2, with_direction=False)
+            v = np.broadcast_to(v, kap.shape)
+            base = kap if which == "kappa" else eta
+            eps = 1e-5 * np.linalg.norm(base) / np.linalg.norm(v)
+            if which == "kappa":
+                fd = (J(kap + eps * v, eta) - J(kap - eps * v, eta)) / (2 * eps)
+            else:
+                fd = (J(kap, eta + eps * v) - J(kap, eta - eps * v)) / (2 * eps)
+            ad = float(np.sum(grad * v))
+            assert abs(fd - ad) <= 1e-6 * abs(fd), (which, fd, ad)
