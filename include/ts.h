@@ -59,8 +59,15 @@ typedef enum {
 
 typedef enum {
   TS_FP64 = 0,     /* double storage, double arithmetic */
-  TS_FP32 = 1      /* float storage, float arithmetic; the radial derivative rows
-                      nearest r = R1 and r = R2 are accumulated in double */
+  TS_FP32 = 1,     /* float storage, float arithmetic */
+  TS_FP32_R64 = 2, /* float storage and angular arithmetic; the two radial
+                      derivative rows nearest each of r = R1 and r = R2 (the rows
+                      with the largest entries) accumulated in double, and the
+                      split scheme's implicit collision step in double */
+  TS_TF32X3 = 3    /* float storage; the radial derivative on the tensor cores
+                      (tcgen05, operands split into TF32 hi + lo, three products
+                      hi*hi + hi*lo + lo*hi accumulated in FP32) for N_r <= 81,
+                      angular passes as TS_FP32 */
 } ts_precision;
 
 typedef enum {
@@ -199,6 +206,51 @@ ts_status ts_moments(ts_grid* grid, const void* F, double* F0, double* F1, doubl
  *    race on it. */
 ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0, double* F1,
                              double* N, double* J_R1, double* J_R2, void* stream);
+
+/* ---------------------------------------------------------------- tuning
+ * Time the candidate tile shapes of the three forward passes of this grid
+ * (angular blocks per CTA, Phi column pairs per plane tile, columns per radial
+ * tile) with CUDA events and keep the fastest for later calls on this grid.
+ * Results are cached per (precision, Nr, Ntheta, Nphi, NTheta, NPhi) for the
+ * process and, if the environment variable TS_AUTOTUNE_CACHE names a file,
+ * appended to / read from that file. Overwrites the grid's workspace.
+ * Synchronous. Tile shapes change no result bit: every element is computed by
+ * the same arithmetic in any tile. (No counterpart in the paper.) */
+ts_status ts_autotune(ts_grid* grid, void* stream);
+
+/* The tile shapes the grid's forward passes use (after ts_autotune, or the
+ * built-in choice). Host ints; any pointer may be NULL. */
+ts_status ts_tile_shape(const ts_grid* grid, int* angular_blocks, int* plane_pairs,
+                        int* radial_columns);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent problems of uneven sizes (each with its own grid
+ * description, energy groups, scheme and coefficients; one precision for the
+ * whole batch) stepped together. Each pass of a stage is one persistent
+ * launch whose CTAs take tiles of every problem from an atomic work queue; a
+ * step is captured once into a CUDA graph and replayed. Results are bit-for-bit
+ * those of ts_step on each problem's grid. (The paper steps one problem at a
+ * time; batching is a property of this library.) */
+typedef struct ts_batch ts_batch;
+
+/* Create grids for descs[0..n-1] (as ts_create_grid) and, if autotune != 0,
+ * run ts_autotune on each. Synchronous. */
+ts_status ts_batch_create(const ts_grid_desc* descs, int n, int autotune, ts_batch** out);
+
+/* Destroy the batch and its grids. Synchronizes the device. */
+ts_status ts_batch_destroy(ts_batch* batch);
+
+/* Borrow problem `problem`'s grid (owned by the batch) for ts_set_coeffs,
+ * ts_grid_nodes, ts_apply_inflow, ts_moments, ts_step. */
+ts_status ts_batch_grid(ts_batch* batch, int problem, ts_grid** grid);
+
+/* Advance every problem by nsteps steps: F_host_array[q] is the DEVICE
+ * pointer of problem q's field and dt_host[q] its time step (host arrays of n
+ * entries). Every problem needs ts_set_coeffs first (TS_ERR_STATE). Work runs
+ * on the batch's own stream, ordered after prior work on `stream` and before
+ * later work on `stream`. */
+ts_status ts_batch_step(ts_batch* batch, void* const* F_host_array, const double* dt_host,
+                        int nsteps, void* stream);
 
 /* Status of device-side checks latched since the last call (bounded waits).
  * Synchronizes `stream`. */

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -39,7 +40,8 @@ ts_status cuda_fail(cudaError_t e, const char* where) {
   return fail(TS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-typedef std::vector<double> Vec;
+using ts::Vec;
+using ts::HostTables;
 
 // ------------------------------------------------------------------ tables
 Vec cheb_diff(int Nr, double R1, double R2) {
@@ -158,14 +160,6 @@ Vec transpose(const Vec& M, int rows, int cols) {
   return T;
 }
 
-struct HostTables {
-  Vec r, theta, phi, Theta, Phi;
-  Vec Dr, Ath, Bth, Dph, ATh, BTh, DPh;          // [out][in]
-  Vec Fr, FthA, FthB, Fph, FThA, FThB, FPh;      // filter [out][in]
-  Vec inv_r, inv_sinth, cot_th, sin_th, cos_th, sin_ph, cos_ph;
-  Vec cosT, sinT, cosP, sinP, tsign, qdir;
-  Vec wr, wth, fluxw;
-};
 
 // Ordered list of the tables that go to the device (the order of Tables<C>).
 std::vector<const Vec*> device_list(const HostTables& h, std::vector<Vec>& tmp) {
@@ -191,7 +185,78 @@ std::vector<const Vec*> device_list(const HostTables& h, std::vector<Vec>& tmp) 
           &h.Dr, &h.Ath, &h.Bth, &h.Dph, &h.ATh, &h.BTh, &h.DPh,
           &h.inv_r, &h.inv_sinth, &h.cot_th, &h.sin_th, &h.cos_th, &h.sin_ph, &h.cos_ph,
           &h.cosT, &h.sinT, &h.cosP, &h.sinP, &h.tsign, &h.qdir,
-          &tmp[7], &tmp[8], &tmp[9], &tmp[10], &tmp[11], &tmp[12], &tmp[13]};
+          &tmp[7], &tmp[8], &tmp[9], &tmp[10], &tmp[11], &tmp[12], &tmp[13],
+          &h.PthT, &h.QthT, &h.PThT, &h.QThT, &h.EpT, &h.OpT, &h.DrMc, &h.DrMr,
+          &h.TcBhi, &h.TcBlo};
+}
+
+// Even/odd forms of the derivative matrices (see Tables in ts_internal.h).
+// DFS pair: for F at a node and G at its partner, A F + B G = P (F+G) + Q (F-G)
+// and at the partner A G + B F = P (F+G) - Q (F-G), P = (A+B)/2, Q = (A-B)/2.
+// TF32 rounding, to nearest with ties away from zero on the 13 dropped bits.
+float tf32_round(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  b = (b + 0x1000u) & 0xFFFFE000u;
+  float y;
+  std::memcpy(&y, &b, 4);
+  return y;
+}
+
+// D_r as the tensor cores' B operand: B[n = i][k = i'] = D_r[i][i'] split into
+// TF32 hi + lo, zero-padded to (N_r up to 16) x (N_r up to 8), stored as 8-row
+// x 4-column core matrices, core (n/8, k/4) at float offset ((n/8) KC + k/4) 32.
+void tc_tables(HostTables& h) {
+  const int Nr = (int)h.r.size(), Kpad = (Nr + 7) / 8 * 8, Npad = (Nr + 15) / 16 * 16;
+  const int KC = Kpad / 4;
+  h.TcBhi.assign((size_t)Npad * Kpad, 0.0);
+  h.TcBlo.assign((size_t)Npad * Kpad, 0.0);
+  for (int n = 0; n < Nr; ++n)
+    for (int k = 0; k < Nr; ++k) {
+      const double v = h.Dr[(size_t)n * Nr + k];
+      const float hi = tf32_round((float)v);
+      const float lo = tf32_round((float)(v - (double)hi));
+      const size_t o = (size_t)((n / 8) * KC + k / 4) * 32 + (n % 8) * 4 + (k % 4);
+      h.TcBhi[o] = hi;
+      h.TcBlo[o] = lo;
+    }
+}
+
+void even_odd_tables(HostTables& h) {
+  auto pq = [](const Vec& A, const Vec& B, int N, Vec& PT, Vec& QT) {
+    PT.assign((size_t)N * N, 0.0);
+    QT.assign((size_t)N * N, 0.0);
+    for (int o = 0; o < N; ++o)
+      for (int i = 0; i < N; ++i) {
+        PT[(size_t)i * N + o] = 0.5 * (A[(size_t)o * N + i] + B[(size_t)o * N + i]);
+        QT[(size_t)i * N + o] = 0.5 * (A[(size_t)o * N + i] - B[(size_t)o * N + i]);
+      }
+  };
+  pq(h.Ath, h.Bth, (int)h.theta.size(), h.PthT, h.QthT);
+  pq(h.ATh, h.BTh, (int)h.Theta.size(), h.PThT, h.QThT);
+  // radial: D[N-i][N-i'] = -D[i][i'] on the symmetric Gauss-Lobatto nodes, so the
+  // pair (i, N-i) needs only E = u_i' + u_{N-i'} and O = u_i' - u_{N-i'}:
+  //   D u (i)   = 1/2 (sum_i' Op[i][i'] O_i' + sum_i' Ep[i][i'] E_i' + 2 D[i][M] u_M)
+  //   D u (N-i) = 1/2 (sum_i' Op[i][i'] O_i' - sum_i' Ep[i][i'] E_i' - 2 D[i][M] u_M)
+  //   D u (M)   = sum_i' D[M][i'] O_i'                    (middle node M = N/2, odd Nr)
+  const int Nr = (int)h.r.size(), N = Nr - 1, hh = Nr / 2;
+  h.EpT.assign((size_t)hh * hh, 0.0);
+  h.OpT.assign((size_t)hh * hh, 0.0);
+  h.DrMc.assign(hh, 0.0);
+  h.DrMr.assign(hh, 0.0);
+  for (int i = 0; i < hh; ++i)
+    for (int ip = 0; ip < hh; ++ip) {
+      const double a = h.Dr[(size_t)i * Nr + ip], b = h.Dr[(size_t)i * Nr + (N - ip)];
+      h.EpT[(size_t)ip * hh + i] = a + b;
+      h.OpT[(size_t)ip * hh + i] = a - b;
+    }
+  if (Nr % 2) {
+    const int M = N / 2;
+    for (int i = 0; i < hh; ++i) {
+      h.DrMc[i] = h.Dr[(size_t)i * Nr + M];
+      h.DrMr[i] = h.Dr[(size_t)M * Nr + i];
+    }
+  }
 }
 
 template <typename C>
@@ -208,7 +273,9 @@ cudaError_t upload_tables(const HostTables& h, void** mem, Tables<C>* t) {
                  &t->Dr, &t->Ath, &t->Bth, &t->Dph, &t->ATh, &t->BTh, &t->DPh,
                  &t->inv_r, &t->inv_sinth, &t->cot_th, &t->sin_th, &t->cos_th, &t->sin_ph,
                  &t->cos_ph, &t->cosT, &t->sinT, &t->cosP, &t->sinP, &t->tsign, &t->qdir,
-                 &t->FrT, &t->FthAT, &t->FthBT, &t->FphT, &t->FThAT, &t->FThBT, &t->FPhT};
+                 &t->FrT, &t->FthAT, &t->FthBT, &t->FphT, &t->FThAT, &t->FThBT, &t->FPhT,
+                 &t->PthT, &t->QthT, &t->PThT, &t->QThT, &t->EpT, &t->OpT, &t->DrMc, &t->DrMr,
+                 &t->TcBhi, &t->TcBlo};
   size_t off = 0;
   for (size_t a = 0; a < list.size(); ++a) {
     for (size_t b = 0; b < list[a]->size(); ++b) host[off + b] = (C)(*list[a])[b];
@@ -274,6 +341,8 @@ HostTables build_tables(const ts_grid_desc& g) {
   const Vec cc = clenshaw_curtis(Nr);
   for (int i = 0; i < Nr; ++i) h.wr.push_back(cc[i] * 0.5 * (g.R2 - g.R1) * h.r[i] * h.r[i]);
   h.wth = fejer(Nt);
+  even_odd_tables(h);
+  tc_tables(h);
   h.fluxw.resize((size_t)Nt * Np * NT * NP);
   for (int j = 0; j < Nt; ++j)
     for (int l = 0; l < Np; ++l)
@@ -287,41 +356,34 @@ HostTables build_tables(const ts_grid_desc& g) {
 }  // namespace
 
 void ts::set_last_error(const std::string& msg) { g_err = msg; }
-
-struct ts_grid {
-  ts_grid_desc desc;
-  Dims d;
-  size_t es = 8;
-  HostTables h;
-  void* tab64 = nullptr;
-  void* tab32 = nullptr;
-  Tables<double> t64{};
-  Tables<float> t32{};
-  double *kap = nullptr, *eta = nullptr, *kaps = nullptr;
-  void *gR1 = nullptr, *gR2 = nullptr;
-  bool coeffs = false;
-  void *U = nullptr, *K = nullptr, *Acc = nullptr;
-  void* adj[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double *wr = nullptr, *wth = nullptr, *partN = nullptr, *partJ = nullptr;
-  void* io = nullptr;
-};
+ts_status ts::fail_status(ts_status s, const std::string& msg) { return fail(s, msg); }
+ts_status ts::cuda_status(cudaError_t e, const char* where) { return cuda_fail(e, where); }
 
 namespace {
 
 ts::Problem make_problem(const ts_grid* g) {
   ts::Problem p;
   p.d = g->d;
+  p.tp = g->tp;
   p.bc = g->desc.bc;
-  p.n_fp64_rows = g->desc.precision == TS_FP32 ? 2 : 0;
+  p.n_fp64_rows = g->desc.precision == TS_FP32_R64 ? 2 : 0;
   p.kap = g->kap;
   p.eta = g->eta;
   p.kaps = g->kaps;
   p.gR1 = g->gR1;
   p.gR2 = g->gR2;
+  p.tc = g->desc.precision == TS_TF32X3 && ts::tc_supported(g->d.Nr);
+  p.err = g->err;
   return p;
 }
 
 size_t field_bytes(const ts_grid* g) { return (size_t)g->d.total * g->es; }
+
+}  // namespace
+
+ts::Problem ts::problem_of(const ts_grid* g) { return make_problem(g); }
+
+namespace {
 
 // Optional per-launch event timing (ts_step_profile). Each launch is
 // bracketed by two events on the launching stream; `kind` selects the bucket.
@@ -484,8 +546,9 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
       (g.NTheta % 2) || (g.NPhi % 2))
     return fail(TS_ERR_UNSUPPORTED,
                 "sizes: need 3<=Nr<=129, 2<=Ntheta<=64, even 2..64 for Nphi, NTheta, NPhi");
-  if (g.precision != TS_FP64 && g.precision != TS_FP32)
-    return fail(TS_ERR_UNSUPPORTED, "precision must be TS_FP64 or TS_FP32");
+  if (g.precision != TS_FP64 && g.precision != TS_FP32 && g.precision != TS_FP32_R64 &&
+      g.precision != TS_TF32X3)
+    return fail(TS_ERR_UNSUPPORTED, "unknown precision");
   if (g.scheme != TS_RK4 && g.scheme != TS_RK4_SPLIT_IMPLICIT)
     return fail(TS_ERR_UNSUPPORTED, "unknown scheme");
   if (g.bc != TS_BC_TAU_INFLOW && g.bc != TS_BC_NONE) return fail(TS_ERR_UNSUPPORTED, "unknown bc");
@@ -504,19 +567,23 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   d.total = d.S_g * g.groups;
   d.nblk = (long long)g.groups * g.Nr * g.Ntheta * g.Nphi;
   G->h = build_tables(g);
+  {
+    const char* gen = std::getenv("TS_GENERIC_PASSES");  // 1: plain passes only (testing)
+    G->tp.rb = (gen && gen[0] == '1') ? 0 : ts::rb_mask(d, (int)es, g.precision == TS_FP32_R64 ? 2 : 0);
+  }
 
   cudaError_t e = upload_tables<double>(G->h, &G->tab64, &G->t64);
-  if (e == cudaSuccess && g.precision == TS_FP32) e = upload_tables<float>(G->h, &G->tab32, &G->t32);
+  if (e == cudaSuccess && g.precision != TS_FP64) e = upload_tables<float>(G->h, &G->tab32, &G->t32);
   const size_t ncoef = (size_t)d.nblk * sizeof(double);
   const size_t ninfl = (size_t)g.groups * g.Ntheta * g.Nphi * (g.NTheta / 2) * g.NPhi * es;
   const size_t nf = (size_t)d.total * es;
   void** bufs[] = {(void**)&G->kap, (void**)&G->eta, (void**)&G->kaps, &G->gR1, &G->gR2,
                    &G->U, &G->K, &G->Acc, (void**)&G->wr, (void**)&G->wth,
-                   (void**)&G->partN, (void**)&G->partJ};
+                   (void**)&G->partN, (void**)&G->partJ, (void**)&G->err};
   const size_t sizes[] = {ncoef, ncoef, ncoef, ninfl, ninfl, nf, nf, nf,
                           (size_t)g.Nr * 8, (size_t)g.Ntheta * 8, ncoef,
-                          (size_t)g.groups * 2 * g.Ntheta * g.Nphi * 8};
-  for (int b = 0; b < 12 && e == cudaSuccess; ++b) {
+                          (size_t)g.groups * 2 * g.Ntheta * g.Nphi * 8, sizeof(int)};
+  for (int b = 0; b < 13 && e == cudaSuccess; ++b) {
     e = cudaMalloc(bufs[b], sizes[b]);
     if (e == cudaSuccess) e = cudaMemset(*bufs[b], 0, sizes[b]);
   }
@@ -537,7 +604,7 @@ ts_status ts_destroy_grid(ts_grid* g) {
   if (!g) return TS_OK;
   cudaDeviceSynchronize();
   void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
-                  g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io};
+                  g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : g->adj)
@@ -711,7 +778,16 @@ ts_status ts_moments(ts_grid* g, const void* F, double* F0, double* F1, double* 
 ts_status ts_sync_status(ts_grid* g, void* stream) {
   if (!g) return fail(TS_ERR_ARG, "grid is NULL");
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_sync_status");
+  if (e != cudaSuccess) return cuda_fail(e, "ts_sync_status");
+  int flag = 0;
+  e = cudaMemcpy(&flag, g->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "ts_sync_status");
+  if (flag) {
+    const int zero = 0;
+    cudaMemcpy(g->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    return fail(TS_ERR_TIMEOUT, "a bounded device-side wait ran out; results of that call are invalid");
+  }
+  return TS_OK;
 }
 
 }  // extern "C"

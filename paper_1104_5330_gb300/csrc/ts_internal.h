@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ts.h"
 
@@ -34,11 +35,45 @@ struct Tables {
   C *inv_r, *inv_sinth, *cot_th, *sin_th, *cos_th, *sin_ph, *cos_ph;
   C *cosT, *sinT, *cosP, *sinP, *tsign, *qdir;
   C *FrT, *FthAT, *FthBT, *FphT, *FThAT, *FThBT, *FPhT;  // filter matrices, transposed
+  // Even/odd forms used by the register-blocked passes:
+  //  DFS axes: P = (A + B)/2 acts on F + F(partner), Q = (A - B)/2 on F - F(partner),
+  //  stored [in][out]; radial: the centro-antisymmetric D_r folded onto h = Nr/2
+  //  output pairs (i, N-i): EpT[i'][i] = D[i][i'] + D[i][N-i'], OpT[i'][i] =
+  //  D[i][i'] - D[i][N-i'], DrMc[i] = D[i][N/2], DrMr[i'] = D[N/2][i'] (odd Nr).
+  C *PthT, *QthT, *PThT, *QThT, *EpT, *OpT, *DrMc, *DrMr;
+  // D_r split into TF32 high and low halves in the tensor-core operand layout
+  // (N_r padded to 16 rows x N_r padded to 8 columns, 8 x 4 core matrices).
+  C *TcBhi, *TcBlo;
 };
+
+// Tile shapes of the passes; 0 selects the built-in heuristic.
+//   nb: angular blocks per CTA; c: Phi column pairs per plane tile; W: columns
+//   per radial tile. The *T fields are the same for the adjoint passes.
+struct TileParams {
+  int nb = 0, c = 0, W = 0, nbT = 0, cT = 0, WT = 0;
+  // Bit mask of forward passes that use the register-blocked even/odd form
+  // (1 angular, 2 plane, 4 radial); set from the grid's sizes.
+  int rb = 0;
+};
+
+// Output rows per thread of the register-blocked plane and radial passes.
+constexpr int kRBPlane = 2;
+constexpr int kRBRad = 2;
+
+// Which forward passes of a grid can use the register-blocked even/odd form.
+inline int rb_mask(const Dims& d, int elem_bytes, int n64) {
+  const int rbA = elem_bytes == 4 ? 4 : 2;
+  int m = 0;
+  if (d.NT % rbA == 0 && d.NP % 8 == 0) m |= 1;
+  if (d.Nt % kRBPlane == 0 && d.Np % 2 == 0 && d.NP % 8 == 0) m |= 2;
+  if (d.Nr >= 9 && (d.Nr / 2) % kRBRad == 0 && (d.NT * d.NP) % 4 == 0 && n64 <= 2) m |= 4;
+  return m;
+}
 
 // Everything a kernel launch needs about the problem.
 struct Problem {
   Dims d;
+  TileParams tp;
   int bc;            // ts_bc
   int n_fp64_rows;   // radial rows at each end accumulated in double (float grids)
   const double* kap; // [G][Nr][Nt][Np]
@@ -46,7 +81,16 @@ struct Problem {
   const double* kaps;
   const void* gR1;   // inflow data, element type of the grid
   const void* gR2;
+  int tc;            // 1: radial pass on the tensor cores (split TF32, float grids)
+  int* err;          // device flag set by a bounded wait that ran out
 };
+
+// Radial pass on the tensor cores (float grids; defined with the float kernels).
+cudaError_t launch_radial_tc(const Problem& p, const Tables<float>& t, const float* U,
+                             const float* K, float sgn, bool tau, int mode, float* F, float* Acc,
+                             float* Uout, float* out, double dt, cudaStream_t s);
+// Whether the tensor-core radial pass handles N_r (its tile must fit shared memory).
+inline bool tc_supported(int Nr) { return Nr >= 3 && Nr <= 81; }
 
 // Output mode of the radial pass (the last pass of a stage).
 enum RadialMode {
@@ -90,4 +134,46 @@ struct Launch {
                              double* JR2, double R1, double R2, cudaStream_t s);
 };
 
+typedef std::vector<double> Vec;
+
+// Host copies of the per-axis tables (derivative matrices [out][in]).
+struct HostTables {
+  Vec r, theta, phi, Theta, Phi;
+  Vec Dr, Ath, Bth, Dph, ATh, BTh, DPh;          // [out][in]
+  Vec Fr, FthA, FthB, Fph, FThA, FThB, FPh;      // filter [out][in]
+  Vec inv_r, inv_sinth, cot_th, sin_th, cos_th, sin_ph, cos_ph;
+  Vec cosT, sinT, cosP, sinP, tsign, qdir;
+  Vec wr, wth, fluxw;
+  Vec PthT, QthT, PThT, QThT, EpT, OpT, DrMc, DrMr;   // even/odd forms (see Tables)
+  Vec TcBhi, TcBlo;                                   // tensor-core operand of D_r
+};
+
+ts_status fail_status(ts_status s, const std::string& msg);
+ts_status cuda_status(cudaError_t e, const char* where);
+
+}  // namespace ts
+
+// The grid behind the opaque ts_grid handle of include/ts.h.
+struct ts_grid {
+  ts_grid_desc desc;
+  ts::Dims d;
+  size_t es = 8;
+  ts::HostTables h;
+  void* tab64 = nullptr;
+  void* tab32 = nullptr;
+  ts::Tables<double> t64{};
+  ts::Tables<float> t32{};
+  double *kap = nullptr, *eta = nullptr, *kaps = nullptr;
+  void *gR1 = nullptr, *gR2 = nullptr;
+  bool coeffs = false;
+  void *U = nullptr, *K = nullptr, *Acc = nullptr;
+  void* adj[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double *wr = nullptr, *wth = nullptr, *partN = nullptr, *partJ = nullptr;
+  int* err = nullptr;    // device flag: a bounded device-side wait ran out
+  void* io = nullptr;
+  ts::TileParams tp{};   // tile shapes (0 = built-in heuristic); set by ts_autotune
+};
+
+namespace ts {
+Problem problem_of(const ts_grid* g);
 }  // namespace ts

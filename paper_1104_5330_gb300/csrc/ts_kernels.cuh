@@ -41,9 +41,9 @@ __device__ __forceinline__ void decode_block(const Dims& d, long long blk, int& 
 // K = sgn * (a_Th dTh U + a_Ph dPh U) + [eta - (kappa+kappa_s) U + kappa_s J]
 // a_Th = -sin(Th)/r, a_Ph = -sin(Th) sin(Ph) cot(th)/r.
 template <typename T, typename C>
-__global__ void __launch_bounds__(kThreads)
-k_angular(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
-          int collision, int nb) {
+__device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& t,
+                                             const T* __restrict__ U, T* __restrict__ K, C sgn,
+                                             int collision, int nb, long long tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
   const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2;
@@ -52,7 +52,7 @@ k_angular(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C 
   C* sD = sB + NT * NT;                    // DPhT [m'][m]
   C* su = sD + NP * NP;                    // tile [bb][k][m]
   C* sJ = su + nb * S;                     // [nb]
-  const long long b0 = (long long)blockIdx.x * nb;
+  const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
     sA[x] = t.AThT[x];
@@ -107,8 +107,9 @@ __device__ __forceinline__ int plane_m(int w, int c, int m0, int hP) {
 }
 
 template <typename T, typename C>
-__global__ void __launch_bounds__(kThreads)
-k_plane(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn, int c) {
+__device__ __forceinline__ void plane_tile(const Problem& p, const Tables<C>& t,
+                                           const T* __restrict__ U, T* __restrict__ K, C sgn,
+                                           int c, long long tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
   const int Nt = d.Nt, Np = d.Np, NP = d.NP, hP = NP / 2, hp = Np / 2, W = 2 * c;
@@ -117,7 +118,7 @@ k_plane(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sg
   C* sD = sB + Nt * Nt;                    // DphT [l'][l]
   C* su = sD + Np * Np;                    // [j][l][w]
   const int nchunk = hP / c;
-  long long q = blockIdx.x;
+  long long q = tile;
   const int chunk = (int)(q % nchunk);
   q /= nchunk;
   const int k = (int)(q % d.NT);
@@ -163,10 +164,11 @@ k_plane(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sg
 // inflow data, b = 0 if cos(Th) > 0 else Nr-1; T_N(x_i) = (-1)^(N-i). This is
 // the nodal form of replacing the top Chebyshev coefficient of K.
 template <typename T, typename C>
-__global__ void __launch_bounds__(kThreads)
-k_radial(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U,
-         const T* Kin, C sgn, int tau, int mode, T* F, T* Acc, T* Uout, T* out,
-         C dt, int W) {
+__device__ __forceinline__ void radial_tile(const Problem& p, const Tables<C>& t,
+                                            const double* __restrict__ Dr64, const T* U,
+                                            const T* Kin, C sgn, int tau, int mode, T* F,
+                                            T* Acc, T* Uout, T* out, C dt, int W,
+                                            long long tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
   const int Nr = d.Nr, NP = d.NP, S = d.NT * d.NP;
@@ -174,7 +176,7 @@ k_radial(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U,
   C* su = sDr + Nr * Nr;                    // [i][w]
   C* sk = su + Nr * W;                      // [i][w]
   const int nchunk = (S + W - 1) / W;
-  long long q = blockIdx.x;
+  long long q = tile;
   const int chunk = (int)(q % nchunk);
   q /= nchunk;
   const int l = (int)(q % d.Np);
@@ -434,36 +436,45 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
 //   J+ = (J* + dt eta)/(1 + dt kappa),  F+ = (F* + dt (eta + kappa_s J+))/(1 + dt (kappa+kappa_s)),
 // then F = inflow data at the inflow nodes (if the grid has Tau rows).
 template <typename T, typename C>
-__global__ void __launch_bounds__(kThreads)
-k_implicit_collision(Problem p, Tables<C> t, T* F, C dt, int nb) {
+__device__ __forceinline__ void implicit_collision_tile(const Problem& p, const Tables<C>& t,
+                                                        T* F, double dt, int nb,
+                                                        long long tile) {
+  // Computed in double for every storage type: the stiff collision update
+  // (dt kappa up to 1e2) is kept in FP64 on the GPU.
   const Dims d = p.d;
   const int NT = d.NT, NP = d.NP, S = NT * NP, hT = NT / 2;
-  const long long b0 = (long long)blockIdx.x * nb;
+  const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int bb = warp; bb < nbb; bb += nw) {
     const long long blk = b0 + bb;
-    C acc = 0;
-    for (int x = lane; x < S; x += 32) acc = fmac(t.qdir[x / NP], (C)F[blk * S + x], acc);
+    double acc = 0;
+    for (int x = lane; x < S; x += 32) acc = fma((double)t.qdir[x / NP], (double)F[blk * S + x], acc);
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    const C kap = (C)p.kap[blk], eta = (C)p.eta[blk], ks = (C)p.kaps[blk];
-    const C Jp = (acc + dt * eta) / ((C)1 + dt * kap);
-    const C num = dt * (eta + ks * Jp), den = (C)1 + dt * (kap + ks);
+    const double kap = p.kap[blk], eta = p.eta[blk], ks = p.kaps[blk];
+    const double Jp = (acc + dt * eta) / (1.0 + dt * kap);
+    const double num = dt * (eta + ks * Jp), den = 1.0 + dt * (kap + ks);
     int g, i, j, l;
     decode_block(d, blk, g, i, j, l);
     const T* g1 = reinterpret_cast<const T*>(p.gR1);
     const T* g2 = reinterpret_cast<const T*>(p.gR2);
     for (int x = lane; x < S; x += 32) {
       const int k = x / NP, m = x - k * NP;
-      C v = ((C)F[blk * S + x] + num) / den;
+      double v = ((double)F[blk * S + x] + num) / den;
       if (p.bc == TS_BC_TAU_INFLOW) {
         const long long pos = (((long long)g * d.Nt + j) * d.Np + l) * hT;
-        if (i == 0 && k < hT) v = g1 ? (C)g1[(pos + k) * NP + m] : (C)0;
-        if (i == d.Nr - 1 && k >= hT) v = g2 ? (C)g2[(pos + k - hT) * NP + m] : (C)0;
+        if (i == 0 && k < hT) v = g1 ? (double)g1[(pos + k) * NP + m] : 0.0;
+        if (i == d.Nr - 1 && k >= hT) v = g2 ? (double)g2[(pos + k - hT) * NP + m] : 0.0;
       }
       F[blk * S + x] = (T)v;
     }
   }
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_implicit_collision(Problem p, Tables<C> t, T* F, double dt, int nb) {
+  implicit_collision_tile<T, C>(p, t, F, dt, nb, blockIdx.x);
 }
 
 // F = inflow data at the inflow nodes.

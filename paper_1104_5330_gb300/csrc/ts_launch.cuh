@@ -3,7 +3,7 @@
 
 #include <algorithm>
 
-#include "ts_kernels.cuh"
+#include "ts_kernels_rb.cuh"
 
 namespace ts {
 
@@ -12,38 +12,76 @@ namespace ts {
 constexpr size_t kSmemBudget = 96 * 1024;
 constexpr size_t kSmemMax = 227 * 1024;
 
+// Opt a kernel in to the largest dynamic shared memory the SM allows next to
+// the kernel's own static shared memory.
 template <typename K>
 static cudaError_t allow_smem(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(kSmemMax - a.sharedSizeBytes));
 }
 
 static inline unsigned grid1(long long n) { return (unsigned)n; }
 
+// Shared memory of one tile of each forward pass (rb: register-blocked form).
+template <typename C>
+size_t smem_angular(const Dims& d, int nb, bool rb) {
+  const size_t S = (size_t)d.NT * d.NP, mats = 2 * d.NT * d.NT + d.NP * d.NP;
+  return (mats + nb * S + (rb ? 4 * nb : nb)) * sizeof(C);
+}
+template <typename C>
+size_t smem_plane(const Dims& d, int c, bool rb) {
+  (void)rb;
+  return (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + d.Nt * d.Np * 2 * c) * sizeof(C);
+}
+template <typename C>
+size_t smem_radial(const Dims& d, int W, bool rb) {
+  if (!rb) return (size_t)(d.Nr * d.Nr + 2 * d.Nr * W) * sizeof(C);
+  const int hh = d.Nr / 2;
+  return (size_t)(2 * ((hh * hh + 3) & ~3) + 2 * ((hh + 3) & ~3) + 2 * d.Nr * W) * sizeof(C);
+}
+
+// Built-in tile shapes: fill 256 threads with work while staying in the budget.
 template <typename T, typename C>
-static int angular_nb(const Dims& d, int ntiles) {
+static int angular_nb(const Dims& d, int ntiles, bool rb = false) {
   const int S = d.NT * d.NP;
+  int nb;
+  if (rb && ntiles == 1) {
+    const int per = (d.NT / (sizeof(C) == 4 ? 4 : 2)) * (d.NP / 8);  // threads' units per block
+    nb = std::max(1, (512 + per - 1) / per);
+  } else {
+    nb = std::max(1, 2048 / S);
+  }
   const size_t mats = (size_t)(2 * d.NT * d.NT + d.NP * d.NP) * sizeof(C);
-  int nb = std::max(1, 2048 / S);
-  while (nb > 1 && mats + (size_t)nb * (ntiles * S + 1) * sizeof(C) > kSmemBudget) nb /= 2;
+  while (nb > 1 && mats + (size_t)nb * (ntiles * S + 4) * sizeof(C) > kSmemBudget) nb /= 2;
   return nb;
 }
 
 template <typename T, typename C>
-static int plane_c(const Dims& d, int ntiles) {
+static int plane_c(const Dims& d, int ntiles, bool rb = false) {
   const int hP = d.NP / 2;
   const size_t mats = (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np) * sizeof(C);
-  int best = 1;
+  int best = rb ? 4 : 1;
   for (int c = 1; c <= hP; ++c) {
-    if (hP % c) continue;
+    if (hP % c || (rb && c % 4)) continue;
     if (mats + (size_t)ntiles * d.Nt * d.Np * 2 * c * sizeof(C) <= kSmemBudget) best = c;
   }
   return best;
 }
 
 template <typename T, typename C>
-static int radial_W(const Dims& d, int ntiles) {
+static int radial_W(const Dims& d, int ntiles, bool rb = false) {
   const int S = d.NT * d.NP;
-  int W = std::min(S, sizeof(C) == 8 ? 64 : 128);
+  int W;
+  if (rb) {
+    const int hh = d.Nr / 2;
+    W = std::max(4, std::min(S, (4 * 256 * kRBRad / std::max(1, hh)) & ~3));
+    while (W > 4 && smem_radial<C>(d, W, true) > kSmemBudget) W = (W / 2) & ~3;
+    return std::max(4, W);
+  }
+  W = std::min(S, sizeof(C) == 8 ? 64 : 128);
   while (W > 8 && (size_t)(d.Nr * d.Nr + ntiles * d.Nr * W) * sizeof(C) > kSmemBudget) W /= 2;
   return W;
 }
@@ -52,10 +90,15 @@ template <typename T, typename C>
 cudaError_t Launch<T, C>::angular(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                                   bool collision, cudaStream_t s) {
   static bool init = false;
-  if (!init) { allow_smem(k_angular<T, C>); init = true; }
+  if (!init) {
+    const cudaError_t ea = allow_smem(k_angular<T, C>);
+    if (ea != cudaSuccess) return ea;
+    init = true;
+  }
   const Dims& d = p.d;
-  const int nb = angular_nb<T, C>(d, 1);
-  const size_t smem = (size_t)(2 * d.NT * d.NT + d.NP * d.NP + nb * (d.NT * d.NP + 1)) * sizeof(C);
+  const bool rb = p.tp.rb & 1;
+  const int nb = p.tp.nb > 0 ? p.tp.nb : angular_nb<T, C>(d, 1, rb);
+  const size_t smem = smem_angular<C>(d, nb, rb);
   k_angular<T, C><<<grid1((d.nblk + nb - 1) / nb), kThreads, smem, s>>>(p, t, U, K, sgn,
                                                                          collision ? 1 : 0, nb);
   return cudaGetLastError();
@@ -65,11 +108,15 @@ template <typename T, typename C>
 cudaError_t Launch<T, C>::plane(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                                 cudaStream_t s) {
   static bool init = false;
-  if (!init) { allow_smem(k_plane<T, C>); init = true; }
+  if (!init) {
+    const cudaError_t ea = allow_smem(k_plane<T, C>);
+    if (ea != cudaSuccess) return ea;
+    init = true;
+  }
   const Dims& d = p.d;
-  const int c = plane_c<T, C>(d, 1);
-  const size_t smem =
-      (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + d.Nt * d.Np * 2 * c) * sizeof(C);
+  const bool rb = p.tp.rb & 2;
+  const int c = p.tp.c > 0 ? p.tp.c : plane_c<T, C>(d, 1, rb);
+  const size_t smem = smem_plane<C>(d, c, rb);
   const long long nct = (long long)d.G * d.Nr * d.NT * (d.NP / 2 / c);
   k_plane<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, U, K, sgn, c);
   return cudaGetLastError();
@@ -80,11 +127,20 @@ cudaError_t Launch<T, C>::radial(const Problem& p, const Tables<C>& t, const dou
                                  const T* U, const T* K, C sgn, bool tau, int mode, T* F, T* Acc,
                                  T* Uout, T* out, double dt, cudaStream_t s) {
   static bool init = false;
-  if (!init) { allow_smem(k_radial<T, C>); init = true; }
+  if (!init) {
+    const cudaError_t ea = allow_smem(k_radial<T, C>);
+    if (ea != cudaSuccess) return ea;
+    init = true;
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (p.tc)
+      return launch_radial_tc(p, t, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, s);
+  }
   const Dims& d = p.d;
-  const int W = radial_W<T, C>(d, 2);
+  const bool rb = p.tp.rb & 4;
+  const int W = p.tp.W > 0 ? p.tp.W : radial_W<T, C>(d, 2, rb);
   const int S = d.NT * d.NP;
-  const size_t smem = (size_t)(d.Nr * d.Nr + 2 * d.Nr * W) * sizeof(C);
+  const size_t smem = smem_radial<C>(d, W, rb);
   const long long nct = (long long)d.G * d.Nt * d.Np * ((S + W - 1) / W);
   k_radial<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, tau ? 1 : 0, mode, F,
                                                     Acc, Uout, out, (C)dt, W);
@@ -95,9 +151,13 @@ template <typename T, typename C>
 cudaError_t Launch<T, C>::radial_T(const Problem& p, const Tables<C>& t, const T* X,
                                    double scale, bool tau, T* lt, T* Ubar, cudaStream_t s) {
   static bool init = false;
-  if (!init) { allow_smem(k_radial_T<T, C>); init = true; }
+  if (!init) {
+    const cudaError_t ea = allow_smem(k_radial_T<T, C>);
+    if (ea != cudaSuccess) return ea;
+    init = true;
+  }
   const Dims& d = p.d;
-  const int W = radial_W<T, C>(d, 2);
+  const int W = p.tp.WT > 0 ? p.tp.WT : radial_W<T, C>(d, 2);
   const int S = d.NT * d.NP;
   const size_t smem = (size_t)(d.Nr * d.Nr + 2 * d.Nr * W) * sizeof(C);
   const long long nct = (long long)d.G * d.Nt * d.Np * ((S + W - 1) / W);
@@ -110,9 +170,13 @@ template <typename T, typename C>
 cudaError_t Launch<T, C>::plane_T(const Problem& p, const Tables<C>& t, const T* lt, T* Ubar,
                                   cudaStream_t s) {
   static bool init = false;
-  if (!init) { allow_smem(k_plane_T<T, C>); init = true; }
+  if (!init) {
+    const cudaError_t ea = allow_smem(k_plane_T<T, C>);
+    if (ea != cudaSuccess) return ea;
+    init = true;
+  }
   const Dims& d = p.d;
-  const int c = plane_c<T, C>(d, 2);
+  const int c = p.tp.cT > 0 ? p.tp.cT : plane_c<T, C>(d, 2);
   const size_t smem =
       (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + 2 * d.Nt * d.Np * 2 * c) * sizeof(C);
   const long long nct = (long long)d.G * d.Nr * d.NT * (d.NP / 2 / c);
@@ -126,9 +190,13 @@ cudaError_t Launch<T, C>::angular_T(const Problem& p, const Tables<C>& t, const 
                                     const T* lam, const T* lam_in, T* lam_out, T* Kbar_out,
                                     double wl, double wu, cudaStream_t s) {
   static bool init = false;
-  if (!init) { allow_smem(k_angular_T<T, C>); init = true; }
+  if (!init) {
+    const cudaError_t ea = allow_smem(k_angular_T<T, C>);
+    if (ea != cudaSuccess) return ea;
+    init = true;
+  }
   const Dims& d = p.d;
-  const int nb = angular_nb<T, C>(d, 2);
+  const int nb = p.tp.nbT > 0 ? p.tp.nbT : angular_nb<T, C>(d, 2);
   const size_t smem =
       (size_t)(2 * d.NT * d.NT + d.NP * d.NP + nb * (2 * d.NT * d.NP + 1)) * sizeof(C);
   k_angular_T<T, C><<<grid1((d.nblk + nb - 1) / nb), kThreads, smem, s>>>(
@@ -140,8 +208,8 @@ template <typename T, typename C>
 cudaError_t Launch<T, C>::implicit_collision(const Problem& p, const Tables<C>& t, T* F,
                                              double dt, cudaStream_t s) {
   const int nb = kThreads / 32;
-  k_implicit_collision<T, C><<<grid1((p.d.nblk + nb - 1) / nb), kThreads, 0, s>>>(p, t, F,
-                                                                                 (C)dt, nb);
+  k_implicit_collision<T, C><<<grid1((p.d.nblk + nb - 1) / nb), kThreads, 0, s>>>(p, t, F, dt,
+                                                                                 nb);
   return cudaGetLastError();
 }
 

@@ -195,8 +195,8 @@ ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0
       d.NTheta < 2 || d.NTheta > 64 || d.NPhi < 2 || d.NPhi > 64 || (d.Nphi % 2) ||
       (d.NTheta % 2) || (d.NPhi % 2))
     return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: unsupported grid sizes");
-  if (d.precision != TS_FP64 && d.precision != TS_FP32)
-    return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: precision must be TS_FP64 or TS_FP32");
+  if (d.precision != TS_FP64 && d.precision != TS_FP32 && d.precision != TS_FP32_R64)
+    return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: unknown precision");
   Sizes z{d.groups, d.Nr, d.Ntheta, d.Nphi, d.NTheta, d.NPhi, d.R1, d.R2,
           (long long)d.groups * d.Nr * d.Ntheta * d.Nphi};
   const long long need = z.nblk + 2LL * d.groups * d.Ntheta * d.Nphi;

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libts.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ts.h")
 
 TS_OK, TS_ERR_ARG, TS_ERR_UNSUPPORTED, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE = range(7)
-TS_FP64, TS_FP32 = 0, 1
+TS_FP64, TS_FP32, TS_FP32_R64 = 0, 1, 2
 TS_RK4, TS_RK4_SPLIT_IMPLICIT = 0, 1
 TS_BC_TAU_INFLOW, TS_BC_NONE = 0, 1
 
@@ -68,6 +68,12 @@ def _load():
         "ts_flux_weights": [P, P, P],
         "ts_moments": [P, P, P, P, P, P, P, P],
         "ts_moments_noalloc": [ctypes.POINTER(GridDesc), P, P, P, P, P, P, P],
+        "ts_autotune": [P, P],
+        "ts_tile_shape": [P, P, P, P],
+        "ts_batch_create": [ctypes.POINTER(GridDesc), I, I, ctypes.POINTER(P)],
+        "ts_batch_destroy": [P],
+        "ts_batch_grid": [P, I, ctypes.POINTER(P)],
+        "ts_batch_step": [P, P, P, I, P],
         "ts_sync_status": [P, P],
     }
     for name, args in sig.items():
@@ -200,6 +206,41 @@ def ts_moments_noalloc(desc: GridDesc, F, F0=None, F1=None, N=None, J_R1=None, J
                                   _ptr(J_R1), _ptr(J_R2), _stream(stream)), "ts_moments_noalloc")
 
 
+def ts_autotune(grid, stream=None):
+    _check(LIB.ts_autotune(grid, _stream(stream)), "ts_autotune")
+
+
+def ts_tile_shape(grid):
+    v = [ctypes.c_int(), ctypes.c_int(), ctypes.c_int()]
+    _check(LIB.ts_tile_shape(grid, *[ctypes.byref(x) for x in v]), "ts_tile_shape")
+    return tuple(x.value for x in v)
+
+
+def ts_batch_create(descs, autotune=True):
+    arr = (GridDesc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _check(LIB.ts_batch_create(arr, len(descs), int(bool(autotune)), ctypes.byref(h)),
+           "ts_batch_create")
+    return h
+
+
+def ts_batch_destroy(batch):
+    _check(LIB.ts_batch_destroy(batch), "ts_batch_destroy")
+
+
+def ts_batch_grid(batch, problem):
+    h = ctypes.c_void_p()
+    _check(LIB.ts_batch_grid(batch, int(problem), ctypes.byref(h)), "ts_batch_grid")
+    return h
+
+
+def ts_batch_step(batch, fields, dts, nsteps=1, stream=None):
+    n = len(fields)
+    ptrs = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
+    dt = (ctypes.c_double * n)(*[float(x) for x in dts])
+    _check(LIB.ts_batch_step(batch, ptrs, dt, int(nsteps), _stream(stream)), "ts_batch_step")
+
+
 def ts_sync_status(grid, stream=None):
     _check(LIB.ts_sync_status(grid, _stream(stream)), "ts_sync_status")
 
@@ -215,14 +256,35 @@ class Grid:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             self.handle = ts_create_grid(self.desc)
-        self.shape = (groups, Nr, Ntheta, Nphi, NTheta, NPhi)
-        self.coef_shape = (groups, Nr, Ntheta, Nphi)
-        self.inflow_shape = (groups, Ntheta, Nphi, NTheta // 2, NPhi)
-        self.dtype = torch.float64 if precision == TS_FP64 else torch.float32
+        self._owns = True
+        self._shapes()
+
+    def _shapes(self):
+        d = self.desc
+        self.shape = (d.groups, d.Nr, d.Ntheta, d.Nphi, d.NTheta, d.NPhi)
+        self.coef_shape = (d.groups, d.Nr, d.Ntheta, d.Nphi)
+        self.inflow_shape = (d.groups, d.Ntheta, d.Nphi, d.NTheta // 2, d.NPhi)
+        self.dtype = torch.float64 if d.precision == TS_FP64 else torch.float32
+
+    @classmethod
+    def borrowed(cls, handle, desc, device=None):
+        """A view of a grid owned elsewhere (a batch's problem); never destroyed here."""
+        g = cls.__new__(cls)
+        g.desc = desc
+        g.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        g.handle = handle
+        g._owns = False
+        g._shapes()
+        return g
+
+    def autotune(self):
+        ts_autotune(self.handle)
+        return ts_tile_shape(self.handle)
 
     def close(self):
         if getattr(self, "handle", None) is not None:
-            ts_destroy_grid(self.handle)
+            if getattr(self, "_owns", True):
+                ts_destroy_grid(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -286,3 +348,35 @@ class Grid:
         J2 = torch.empty(G, dtype=torch.float64, device=self.device)
         ts_moments(self.handle, F, F0, F1, N, J1, J2)
         return F0, F1, N, J1, J2
+
+
+class Batch:
+    """Owning handle around ts_batch_create/ts_batch_destroy; `grids[q]` are
+    borrowed views of the per-problem grids (set_coeffs, nodes, moments...)."""
+
+    def __init__(self, descs, autotune=True):
+        self.descs = list(descs)
+        self.handle = ts_batch_create(self.descs, autotune)
+        self.grids = [Grid.borrowed(ts_batch_grid(self.handle, q), d)
+                      for q, d in enumerate(self.descs)]
+
+    def step(self, fields, dts, nsteps=1):
+        ts_batch_step(self.handle, fields, dts, nsteps)
+        return fields
+
+    @property
+    def points(self):
+        return sum(g.points for g in self.grids)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            for g in self.grids:
+                g.handle = None
+            ts_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,154 @@
+"""Batched steps of uneven problems (one persistent launch per pass over every
+problem's tiles, graph-captured) and the tile-shape autotuner.
+
+Bars: the batched step is bit-for-bit the single-problem step on each
+problem's grid; FP64 batches match the oracle to 1e-12 and FP32 split-scheme
+batches to 1e-5; autotuned tile shapes change no result bit."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import T, cuda, host, rel_l2
+from oracle.transport import Grid as OGrid, Problem as OProblem
+from paper_1104_5330_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1104_5330_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+# uneven shapes drawn from the batch workload's ranges (N_r in {17,33,65},
+# angular N in {8,16,24}), kept small enough for the oracle
+SPECS = [
+    (17, 8, 16, 8, 8, 2, 37.0),
+    (33, 8, 8, 16, 8, 1, 0.4),
+    (17, 16, 8, 8, 16, 3, 91.0),
+    (17, 8, 8, 8, 8, 1, 5.0),
+    (33, 8, 8, 8, 16, 2, 12.0),
+]
+
+
+def _descs(precision, scheme, specs=SPECS):
+    ts = T()
+    return [ts.GridDesc(0.2, 1.0, Nr, Nt, Np, NT, NP, G, precision, scheme, 0, 0, 36.0, 16)
+            for (Nr, Nt, Np, NT, NP, G, s) in specs]
+
+
+def _fields(og, spec, seed):
+    Nr, Nt, Np, NT, NP, G, s = spec
+    kap, eta, ks = I.absorber_fields(og.r, og.theta, og.phi, groups=G)
+    F0 = np.stack([I.seeded_smooth(og.r, og.theta, og.phi, og.Theta, og.Phi, seed + g, 0.2, 1.0)
+                   for g in range(G)])
+    gR1, gR2 = I.inflow_from(F0, NT)
+    return s * kap, s * eta, ks, F0, gR1, gR2
+
+
+def _setup(batch, specs, dtype):
+    ogs, data, Fs, dts = [], [], [], []
+    for q, spec in enumerate(specs):
+        og = OGrid(0.2, 1.0, *spec[:5], groups=spec[5])
+        kap, eta, ks, F0, gR1, gR2 = _fields(og, spec, 1104 + 31 * q)
+        batch.grids[q].set_coeffs(kap, eta, ks, gR1, gR2)
+        ogs.append(og)
+        data.append((kap, eta, ks, F0, gR1, gR2))
+        Fs.append(cuda(F0, dtype))
+        dts.append(I.dt_rule(0.2, 1.0, spec[0]))
+    return ogs, data, Fs, dts
+
+
+@pytest.mark.parametrize("precision,scheme", [(1, 1), (2, 1), (0, 0)])
+def test_batch_is_bitwise_the_single_problem_step(precision, scheme):
+    ts = T()
+    b = ts.Batch(_descs(precision, scheme), autotune=True)
+    dtype = torch.float64 if precision == 0 else torch.float32
+    _, _, Fs, dts = _setup(b, SPECS, dtype)
+    ref = [F.clone() for F in Fs]
+    b.step(Fs, dts, 3)
+    torch.cuda.synchronize()
+    for q, g in enumerate(b.grids):
+        g.step(ref[q], dts[q], 3)
+    torch.cuda.synchronize()
+    for q in range(len(SPECS)):
+        assert torch.equal(Fs[q], ref[q]), q
+    b.close()
+
+
+def test_batch_fp64_matches_oracle():
+    ts = T()
+    b = ts.Batch(_descs(0, 0), autotune=False)
+    ogs, data, Fs, dts = _setup(b, SPECS, torch.float64)
+    b.step(Fs, dts, 4)
+    torch.cuda.synchronize()
+    for q, og in enumerate(ogs):
+        kap, eta, ks, F0, gR1, gR2 = data[q]
+        ref = OProblem(og, kap, eta, ks, gR1, gR2).run(F0, dts[q], 4)
+        assert rel_l2(host(Fs[q]), ref) < 1e-12, q
+    b.close()
+
+
+def test_batch_fp32_r64_split_implicit_matches_oracle():
+    """FP32 storage and angular contractions, FP64 radial rows near the ends,
+    split scheme with the FP64 implicit collision step, kappa up to ~90."""
+    ts = T()
+    b = ts.Batch(_descs(2, 1), autotune=True)
+    ogs, data, Fs, dts = _setup(b, SPECS, torch.float32)
+    b.step(Fs, dts, 10)
+    torch.cuda.synchronize()
+    for q, og in enumerate(ogs):
+        kap, eta, ks, F0, gR1, gR2 = data[q]
+        ref = OProblem(og, kap, eta, ks, gR1, gR2, scheme="split").run(F0, dts[q], 10)
+        assert rel_l2(host(Fs[q]), ref) < 1e-5, q
+    b.close()
+
+
+def test_batch_reuses_its_graph_with_new_fields_and_steps():
+    ts = T()
+    b = ts.Batch(_descs(1, 1, SPECS[:3]), autotune=False)
+    _, _, Fs, dts = _setup(b, SPECS[:3], torch.float32)
+    F2 = [F.clone() for F in Fs]
+    ref = [F.clone() for F in Fs]
+    b.step(Fs, dts, 2)
+    b.step(Fs, dts, 3)          # same fields: graph and item table reused
+    b.step(F2, dts, 5)          # new pointers: item table re-uploaded
+    for q, g in enumerate(b.grids):
+        g.step(ref[q], dts[q], 5)
+    torch.cuda.synchronize()
+    for q in range(3):
+        assert torch.equal(Fs[q], ref[q]) and torch.equal(F2[q], ref[q])
+    b.close()
+
+
+def test_autotune_changes_no_result_bits():
+    ts = T()
+    g = ts.Grid(0.2, 1.0, 17, 8, 16, 16, 8, groups=2, precision=1)
+    og = OGrid(0.2, 1.0, 17, 8, 16, 16, 8, groups=2)
+    kap, eta, ks, F0, gR1, gR2 = _fields(og, (17, 8, 16, 16, 8, 2, 1.0), 5)
+    g.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.2, 1.0, 17)
+    a = cuda(F0, torch.float32)
+    g.step(a, dt, 3)
+    before = ts.ts_tile_shape(g.handle)
+    after = g.autotune()
+    bb = cuda(F0, torch.float32)
+    g.step(bb, dt, 3)
+    assert all(x > 0 for x in before + after)
+    assert torch.equal(a, bb)
+
+
+def test_batch_errors():
+    ts = T()
+    with pytest.raises(ts.TSError):
+        ts.Batch([ts.GridDesc(0.2, 1.0, 17, 8, 8, 8, 8, 1, 0, 0, 0, 0, 36.0, 16),
+                  ts.GridDesc(0.2, 1.0, 17, 8, 8, 8, 8, 1, 1, 0, 0, 0, 36.0, 16)])
+    b = ts.Batch(_descs(0, 0, SPECS[:2]), autotune=False)
+    F = [torch.zeros(g.shape, dtype=torch.float64, device="cuda") for g in b.grids]
+    with pytest.raises(ts.TSError) as e:
+        b.step(F, [1e-3, 1e-3], 1)      # coefficients not set
+    assert e.value.status == ts.TS_ERR_STATE
+    b.close()

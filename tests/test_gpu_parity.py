@@ -235,3 +235,51 @@ def test_zero_steps_and_state_errors():
     assert torch.equal(F, cuda(np.ones(og.shape)))
     with pytest.raises(T().TSError):
         gg.step(F, float("nan"), 1)
+
+
+# Ragged grids that qualify for the register-blocked even/odd passes
+# (NT, NP multiples of 4 and 8, even Nt and Np, even Nr/2); tiles do not divide them.
+RB_GRIDS = [(0.2, 1.0, 13, 6, 10, 12, 8), (0.3, 1.1, 21, 8, 6, 8, 24), (0.2, 1.0, 9, 4, 2, 4, 8)]
+
+
+@pytest.mark.parametrize("dims", RB_GRIDS)
+def test_register_blocked_passes_parity(dims):
+    og, gg = pair(*dims, G=3)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    F = F0 + 0.1 * np.random.default_rng(12).standard_normal(og.shape)
+    assert rel_l2(host(gg.rhs(cuda(F))), op.rhs(F)) < FP64_TOL
+    assert rel_l2(host(gg.liouville(cuda(F))), og.liouville(F)) < FP64_TOL
+    dt = I.dt_rule(dims[0], dims[1], dims[2])
+    Fg = cuda(F0)
+    gg.step(Fg, dt, 12)
+    assert rel_l2(host(Fg), op.run(F0, dt, 12)) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-6), (2, 1e-6)])
+def test_register_blocked_agrees_with_generic_passes(precision, tol, monkeypatch):
+    dims = RB_GRIDS[0]
+    og, fast = pair(*dims, G=2, precision=precision)
+    monkeypatch.setenv("TS_GENERIC_PASSES", "1")
+    _, plain = pair(*dims, G=2, precision=precision)
+    monkeypatch.delenv("TS_GENERIC_PASSES")
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    for g in (fast, plain):
+        g.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(dims[0], dims[1], dims[2])
+    dtype = torch.float64 if precision == 0 else torch.float32
+    a, b = cuda(F0, dtype), cuda(F0, dtype)
+    fast.step(a, dt, 5)
+    plain.step(b, dt, 5)
+    assert rel_l2(host(a), host(b)) < tol
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp32_variants_against_oracle_on_register_blocked_grid(precision):
+    og, gg = pair(*RB_GRIDS[1], G=2, precision=precision)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(0.3, 1.1, og.Nr)
+    Fg = cuda(F0, torch.float32)
+    gg.step(Fg, dt, 40)
+    assert rel_l2(host(Fg), op.run(F0, dt, 40)) < FP32_TOL
