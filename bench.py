@@ -55,6 +55,23 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 # ------------------------------------------------------------------ helpers
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: every rank runs its own replica of the workload
+    (weak scaling), so the job takes as long as its slowest rank."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def _env_rank():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -147,16 +164,31 @@ class ClockSampler:
 
 
 # -------------------------------------------------------- algorithmic work
+def even_odd_passes(dims, es):
+    """Which passes run in the register-blocked even/odd form (the library's rule)."""
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    rbA = 4 if es == 4 else 2
+    return {"angular": NT % rbA == 0 and NP % 8 == 0,
+            "plane": Nt % 2 == 0 and Np % 2 == 0 and NP % 8 == 0,
+            "radial": Nr >= 9 and (Nr // 2) % 2 == 0 and (NT * NP) % 4 == 0}
+
+
 def pass_work(dims, es):
     """Algorithmic flops and DRAM bytes per launch of each pass (one stage of
-    all groups). Flops count the dense contractions (2 per multiply-add) and the
-    pointwise terms; bytes count each field the pass must read or write once."""
+    all groups). Flops count the contractions the pass performs (2 per
+    multiply-add; the even/odd forms need half the multiply-adds of a dense
+    DFS or Chebyshev product) and the pointwise terms; bytes count each field
+    the pass must read or write once."""
     R1, R2, Nr, Nt, Np, NT, NP, G = dims
     pts = Nr * Nt * Np * NT * NP * G
+    eo = even_odd_passes(dims, es)
     flops = {
-        "angular": pts * (2 * 2 * NT + 2 * NP + 2 + 11),   # dTh (DFS pair), dPh, J, terms+collision
-        "plane": pts * (2 * 2 * Nt + 2 * Np + 8),           # dth (DFS pair), dph, terms
-        "radial": pts * (2 * Nr + 10),                      # dr, term, Tau row, stage update
+        # dTh on the DFS pair, dPh, J, coefficients and collision
+        "angular": pts * ((2 * NT + 1 if eo["angular"] else 4 * NT) + 2 * NP + 2 + 11),
+        # dth on the DFS pair, dph, coefficients
+        "plane": pts * ((2 * Nt + 1 if eo["plane"] else 4 * Nt) + 2 * Np + 8),
+        # dr (centro-antisymmetric halves), r term, Tau row, stage update
+        "radial": pts * ((Nr + 1 if eo["radial"] else 2 * Nr) + 10),
     }
     byts = {
         "angular": pts * es * 2,        # read U, write K
@@ -326,12 +358,8 @@ def run_ours(args, dims, wname):
         gg.step(F, dt, args.steps)
         e1.record(stream)
         sync_all()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = pts * args.steps * world / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    value = job_rate(pts * args.steps, world, ms)
     launches = 12 * args.steps
 
     # per-pass device time (CUDA events on the launching stream)
@@ -400,31 +428,39 @@ def run_ours(args, dims, wname):
         ref = torch.as_tensor(F0, dtype=torch.float64, device="cuda").contiguous()
         nv = max(2, min(args.steps, 10))
         gg.step(ref, dt, nv)
-        g32, _ = make(ts.TS_FP32)
-        F32 = torch.as_tensor(F0, dtype=torch.float32, device="cuda").contiguous()
-        g32.step(F32, dt, nv)
-        err32 = float(torch.linalg.vector_norm(F32.double() - ref) / torch.linalg.vector_norm(ref))
-        F32b = F32.clone()
-        g32.step(F32b, dt, 2)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        g32.step(F32b, dt, args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1)
-        pm, pn = ts.ts_step_profile(g32.handle, F32b, dt, nv)
-        _, _, by32 = pass_work(dims, 4)
-        d32 = int(np.argmax(pm[:3]))
-        hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
-        line["variants"] = {"fp32": {
-            "value": pts * args.steps / (ms32 * 1e-3), "unit": "point-updates/s",
-            "ms_per_step": ms32 / args.steps,
-            "rel_l2_vs_gpu_fp64": err32, "after_steps": nv,
-            "roofline": {"bound": "hbm", "kernel": f"k_{names[d32]}<float>",
-                         "achieved": hbm32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": hbm32 / peaks["hbm_gbs"],
-                         "pass_share": {n: float(s) for n, s in zip(names, pm[:3] / pm[:3].sum())}}}}
-        del g32, F32, F32b
+        line["variants"] = {}
+        kname = {"radial": "k_radial_tc"}
+        for vname, vprec in (("fp32", ts.TS_FP32), ("fp32_r64", ts.TS_FP32_R64),
+                             ("tf32x3_tensorcore_radial", ts.TS_TF32X3)):
+            g32, _ = make(vprec)
+            F32 = torch.as_tensor(F0, dtype=torch.float32, device="cuda").contiguous()
+            g32.step(F32, dt, nv)
+            err32 = float(torch.linalg.vector_norm(F32.double() - ref) / torch.linalg.vector_norm(ref))
+            F32b = F32.clone()
+            g32.step(F32b, dt, 2)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            g32.step(F32b, dt, args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.ts_sync_status(g32.handle)
+            ms32 = e0.elapsed_time(e1)
+            pm, pn = ts.ts_step_profile(g32.handle, F32b, dt, nv)
+            _, _, by32 = pass_work(dims, 4)
+            d32 = int(np.argmax(pm[:3]))
+            hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
+            kn = (kname.get(names[d32], f"k_{names[d32]}") if vprec == ts.TS_TF32X3
+                  else f"k_{names[d32]}") + "<float>"
+            line["variants"][vname] = {
+                "value": pts * args.steps / (ms32 * 1e-3), "unit": "point-updates/s",
+                "ms_per_step": ms32 / args.steps, "dtype": "f32",
+                "rel_l2_vs_gpu_fp64": err32, "after_steps": nv,
+                "roofline": {"bound": "hbm", "kernel": kn,
+                             "achieved": hbm32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": hbm32 / peaks["hbm_gbs"],
+                             "pass_share": {n: float(s) for n, s in zip(names, pm[:3] / pm[:3].sum())},
+                             "pass_ms_per_launch": {n: float(pm[a] / pn[a]) for a, n in enumerate(names)}}}
+            del g32, F32, F32b
         lam = torch.randn_like(F)
         gk = torch.zeros(gg.coef_shape, dtype=torch.float64, device="cuda")
         ge = torch.zeros_like(gk)

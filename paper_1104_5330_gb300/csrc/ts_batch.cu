@@ -166,8 +166,8 @@ cudaError_t tune_grid(ts_grid* g, const Tables<C>& t, cudaStream_t st, TileParam
   // angular: nb
   if (e == cudaSuccess) e = timeit(0, best, &tbest);
   for (int nb = 1; nb <= 64 && e == cudaSuccess; nb *= 2) {
-    if (nb * d.NT * d.NP > 16384 || smem_angular<C>(d, nb, rbA) > kSmemMax || nb == best.nb)
-      continue;
+    const size_t sm = rbA ? smem_angular_pp<C>(d, nb) : smem_angular<C>(d, nb, false);
+    if (nb * d.NT * d.NP > 16384 || sm > kSmemMax || nb == best.nb) continue;
     TileParams c = best;
     c.nb = nb;
     float ms;
@@ -177,8 +177,8 @@ cudaError_t tune_grid(ts_grid* g, const Tables<C>& t, cudaStream_t st, TileParam
   // plane: c (divisors of NP/2; multiples of 4 for the register-blocked form)
   if (e == cudaSuccess) e = timeit(1, best, &tbest);
   for (int c = 1; c <= d.NP / 2 && e == cudaSuccess; ++c) {
-    if ((d.NP / 2) % c || (rbP && c % 4) || smem_plane<C>(d, c, rbP) > kSmemMax || c == best.c)
-      continue;
+    const size_t sm = rbP ? smem_plane_pp<C>(d, c) : smem_plane<C>(d, c, false);
+    if ((d.NP / 2) % c || (rbP && c % 4) || sm > kSmemMax || c == best.c) continue;
     TileParams cand = best;
     cand.c = c;
     float ms;
@@ -188,7 +188,8 @@ cudaError_t tune_grid(ts_grid* g, const Tables<C>& t, cudaStream_t st, TileParam
   // radial: W
   if (e == cudaSuccess) e = timeit(2, best, &tbest);
   for (int W = 16; W <= 512 && e == cudaSuccess; W *= 2) {
-    if (W > d.NT * d.NP || smem_radial<C>(d, W, rbR) > kSmemMax || W == best.W) continue;
+    const size_t sm = rbR ? smem_radial_pp<C>(d, W) : smem_radial<C>(d, W, false);
+    if (W > d.NT * d.NP || sm > kSmemMax || W == best.W) continue;
     TileParams cand = best;
     cand.W = W;
     float ms;

@@ -1,4 +1,5 @@
-// Register-blocked forms of the three forward passes.
+// Register-blocked forms of the three forward passes, and their persistent,
+// double-buffered launches.
 //
 // Each pass is a batch of small matrix products (the per-axis derivative
 // matrices against the staged lines). Here every thread owns an RB x 4 block of
@@ -10,10 +11,21 @@
 //  * r: the Gauss-Lobatto differentiation matrix is centro-antisymmetric, so
 //    the outputs at i and N-i come from E = u_i' + u_{N-i'} and
 //    O = u_i' - u_{N-i'} against half-size matrices -- half the multiply-adds.
+// The sums and differences are formed once per tile in shared memory.
+//
+// Every pass is split into a staging step (the tile's input lines into shared
+// memory) and a compute step. The single-tile form stages synchronously (used
+// by the batched kernels); the persistent kernels k_*_pp keep the derivative
+// matrices in shared memory for all their tiles and stage tile t + gridDim.x
+// with asynchronous 16-byte copies (cp.async) into a second buffer while tile
+// t is computed.
+//
 // Requirements (checked on the host): NT, Nt multiples of RB, NP a multiple
 // of 8, plane columns per half (c) a multiple of 4, Nr/2 a multiple of RB.
 // Results equal the generic passes up to rounding.
 #pragma once
+
+#include <stdint.h>
 
 #include "ts_kernels.cuh"
 
@@ -49,44 +61,88 @@ __device__ __forceinline__ void ldr(const C* p, C (&v)[RB]) {
   for (int r = 0; r < RB; ++r) v[r] = p[r];
 }
 
+// Four consecutive elements global -> shared: plain (convert T -> C) or as
+// asynchronous 16-byte copies (T == C), completed by cp.async.wait_group.
+template <bool ASYNC, typename T, typename C>
+__device__ __forceinline__ void copy4(C* dst, const T* src) {
+  if constexpr (ASYNC) {
+    static_assert(sizeof(T) == sizeof(C), "async staging copies raw elements");
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+#pragma unroll
+    for (int h = 0; h < (int)sizeof(T) * 4 / 16; ++h)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                   :: "r"(d + 16 * h), "l"(reinterpret_cast<const char*>(src) + 16 * h)
+                   : "memory");
+  } else {
+    T v[4];
+    ld4<T>(src, v);
+    C w[4] = {(C)v[0], (C)v[1], (C)v[2], (C)v[3]};
+    st4<C>(dst, w);
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // RB for the angular pass (rows of Theta per thread); kRBPlane, kRBRad in ts_internal.h.
 template <typename C> struct RBAng { static constexpr int v = sizeof(C) == 4 ? 4 : 2; };
 
-// ----------------------------------------------------------------------------
+// ============================================================================
 // Angular pass. Thread: RB Theta rows k0.. x 4 column pairs (m, m + NP/2) of one block.
-template <typename T, typename C>
-__device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C>& t,
-                                                const T* __restrict__ U, T* __restrict__ K,
-                                                C sgn, int collision, int nb, long long tile) {
-  constexpr int RB = RBAng<C>::v, CB = 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Dims d = p.d;
-  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2;
-  C* sP = reinterpret_cast<C*>(smem_raw);  // PThT [k'][k]
-  C* sQ = sP + NT * NT;                    // QThT [k'][k]
-  C* sD = sQ + NT * NT;                    // DPhT [m'][m]
-  C* su = sD + NP * NP;                    // [bb][k][m]
-  C* sc = su + nb * S;                     // J, kappa, eta, kappa_s per block
-  const long long b0 = tile * nb;
-  const int nbb = (int)min((long long)nb, d.nblk - b0);
+// Shared layout: [PThT | QThT | DPhT | tile buffer(s) nb*S | sums/diffs nb*S | 4 nb]
+template <typename C>
+__device__ __forceinline__ void angular_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
+                                                C* sD) {
+  const int NT = d.NT, NP = d.NP;
   for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
     sP[x] = t.PThT[x];
     sQ[x] = t.QThT[x];
   }
   for (int x = threadIdx.x; x < NP * NP; x += blockDim.x) sD[x] = t.DPhT[x];
+}
+
+template <bool ASYNC, typename T, typename C>
+__device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int nb, long long tile,
+                                                C* su) {
+  const int S = d.NT * d.NP;
+  const long long b0 = tile * nb;
+  const int nbb = (int)min((long long)nb, d.nblk - b0);
   const T* src = U + b0 * S;
-  for (int x = 4 * threadIdx.x; x < nbb * S; x += 4 * blockDim.x) {
-    T v[4];
-    ld4<T>(src + x, v);
-    C w[4] = {(C)v[0], (C)v[1], (C)v[2], (C)v[3]};
-    st4<C>(su + x, w);
-  }
+  for (int x = 4 * threadIdx.x; x < nbb * S; x += 4 * blockDim.x) copy4<ASYNC, T, C>(su + x, src + x);
+}
+
+// Compute one staged tile. Entry: su complete and visible to all threads; sSD
+// and sc free. Exit: all outputs written (sSD/sc may still be read until the
+// caller's next barrier).
+template <typename T, typename C>
+__device__ __forceinline__ void angular_rb_body(const Problem& p, const Tables<C>& t,
+                                                const C* su, C* sSD, C* sc, const C* sP,
+                                                const C* sQ, const C* sD, T* __restrict__ K,
+                                                C sgn, int collision, int nb, long long tile) {
+  constexpr int RB = RBAng<C>::v, CB = 4;
+  const Dims& d = p.d;
+  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2;
+  const long long b0 = tile * nb;
+  const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // one conversion per block
     sc[nb + x] = (C)p.kap[b0 + x];
     sc[2 * nb + x] = (C)p.eta[b0 + x];
     sc[3 * nb + x] = (C)p.kaps[b0 + x];
   }
-  __syncthreads();
+  // F + F(partner) and F - F(partner) once per pair (the partner of Phi_m is Phi_{m+NP/2})
+  for (int x = threadIdx.x; x < nbb * NT * (hP / 4); x += blockDim.x) {
+    const int p4 = (x % (hP / 4)) * 4, rest = x / (hP / 4), kk = rest % NT, bb = rest / NT;
+    C a[4], b[4], s[4], df[4];
+    ld4<C>(su + bb * S + kk * NP + p4, a);
+    ld4<C>(su + bb * S + kk * NP + p4 + hP, b);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      s[c] = a[c] + b[c];
+      df[c] = a[c] - b[c];
+    }
+    st4<C>(sSD + bb * S + kk * hP + p4, s);
+    st4<C>(sSD + bb * S + NT * hP + kk * hP + p4, df);
+  }
   if (collision) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
@@ -95,32 +151,33 @@ __device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C
       for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) sc[bb] = acc;
     }
-    __syncthreads();
   }
+  __syncthreads();
   const int KR = NT / RB, PC = hP / CB;
   const int units = nbb * KR * PC;
   for (int unit = threadIdx.x; unit < units; unit += blockDim.x) {
     const int pc = unit % PC, rest = unit / PC, kr = rest % KR, bb = rest / KR;
     const int p0 = pc * CB, k0 = kr * RB;
     const C* ub = su + bb * S;
+    const C* us = sSD + bb * S;
+    const C* ud = us + NT * hP;
     C ps[RB][CB], qd[RB][CB], da[RB][CB], db[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int c = 0; c < CB; ++c) ps[r][c] = qd[r][c] = da[r][c] = db[r][c] = 0;
     for (int kk = 0; kk < NT; ++kk) {
-      C a[CB], b[CB], P[RB], Q[RB];
-      ld4<C>(ub + kk * NP + p0, a);
-      ld4<C>(ub + kk * NP + p0 + hP, b);
+      C sv[CB], dv[CB], P[RB], Q[RB];
+      ld4<C>(us + kk * hP + p0, sv);
+      ld4<C>(ud + kk * hP + p0, dv);
       ldr<C, RB>(sP + kk * NT + k0, P);
       ldr<C, RB>(sQ + kk * NT + k0, Q);
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
-        const C sv = a[c] + b[c], dv = a[c] - b[c];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-          ps[r][c] = fmac(P[r], sv, ps[r][c]);
-          qd[r][c] = fmac(Q[r], dv, qd[r][c]);
+          ps[r][c] = fmac(P[r], sv[c], ps[r][c]);
+          qd[r][c] = fmac(Q[r], dv[c], qd[r][c]);
         }
       }
     }
@@ -169,43 +226,122 @@ __device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C
   }
 }
 
-// ----------------------------------------------------------------------------
+template <typename T, typename C>
+__device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C>& t,
+                                                const T* __restrict__ U, T* __restrict__ K,
+                                                C sgn, int collision, int nb, long long tile) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims& d = p.d;
+  const int NT = d.NT, NP = d.NP, S = NT * NP;
+  C* sP = reinterpret_cast<C*>(smem_raw);
+  C* sQ = sP + NT * NT;
+  C* sD = sQ + NT * NT;
+  C* su = sD + NP * NP;
+  C* sSD = su + nb * S;
+  C* sc = sSD + nb * S;
+  angular_rb_mats<C>(t, d, sP, sQ, sD);
+  angular_rb_load<false, T, C>(d, U, nb, tile, su);
+  __syncthreads();
+  angular_rb_body<T, C>(p, t, su, sSD, sc, sP, sQ, sD, K, sgn, collision, nb, tile);
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
+             int collision, int nb, long long ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims& d = p.d;
+  const int NT = d.NT, NP = d.NP, S = NT * NP;
+  C* sP = reinterpret_cast<C*>(smem_raw);
+  C* sQ = sP + NT * NT;
+  C* sD = sQ + NT * NT;
+  C* sbuf[2] = {sD + NP * NP, sD + NP * NP + nb * S};
+  C* sSD = sbuf[1] + nb * S;
+  C* sc = sSD + nb * S;
+  angular_rb_mats<C>(t, d, sP, sQ, sD);
+  long long tile = blockIdx.x;
+  if (tile < ntiles) angular_rb_load<true, T, C>(d, U, nb, tile, sbuf[0]);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    if (next < ntiles) angular_rb_load<true, T, C>(d, U, nb, next, sbuf[(it + 1) & 1]);
+    cp_async_commit();
+    cp_async_wait1();  // this tile's copies (every group but the newest) have landed
+    __syncthreads();
+    angular_rb_body<T, C>(p, t, sbuf[it & 1], sSD, sc, sP, sQ, sD, K, sgn, collision, nb, tile);
+    __syncthreads();   // buffer and scratch free before they are refilled
+  }
+  cp_async_wait0();
+}
+
+// ============================================================================
 // Plane pass. Thread: RB theta rows j0.. x 4 columns w0.. at phi l < Np/2, and the
 // partner outputs (l + Np/2, w0^..) of the same E/O pair.
-template <typename T, typename C>
-__device__ __forceinline__ void plane_tile_rb(const Problem& p, const Tables<C>& t,
-                                              const T* __restrict__ U, T* __restrict__ K, C sgn,
-                                              int c, long long tile) {
-  constexpr int RB = kRBPlane, CB = 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Dims d = p.d;
-  const int Nt = d.Nt, Np = d.Np, NP = d.NP, hP = NP / 2, hp = Np / 2, W = 2 * c;
-  C* sP = reinterpret_cast<C*>(smem_raw);  // PthT [j'][j]
-  C* sQ = sP + Nt * Nt;
-  C* sD = sQ + Nt * Nt;                    // DphT [l'][l]
-  C* su = sD + Np * Np + ((Np * Np) & 3 ? 4 - ((Np * Np) & 3) : 0);  // [j][l][w], 16B aligned
-  const int nchunk = hP / c;
+// Shared layout: [PthT | QthT | DphT | tile buffer(s) Nt*Np*W | sums, diffs Nt*Np*W]
+__device__ __forceinline__ void plane_tile_coords(const Dims& d, int c, long long tile, int& k,
+                                                  int& i, int& g, int& m0) {
+  const int nchunk = d.NP / 2 / c;
   long long q = tile;
   const int chunk = (int)(q % nchunk);
   q /= nchunk;
-  const int k = (int)(q % d.NT);
+  k = (int)(q % d.NT);
   q /= d.NT;
-  const int i = (int)(q % d.Nr);
-  const int g = (int)(q / d.Nr);
-  const int m0 = chunk * c;
-  const long long base = (long long)g * d.S_g + (long long)i * d.S_i + (long long)k * NP;
+  i = (int)(q % d.Nr);
+  g = (int)(q / d.Nr);
+  m0 = chunk * c;
+}
+
+template <typename C>
+__device__ __forceinline__ void plane_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
+                                              C* sD) {
+  const int Nt = d.Nt, Np = d.Np;
   for (int x = threadIdx.x; x < Nt * Nt; x += blockDim.x) {
     sP[x] = t.PthT[x];
     sQ[x] = t.QthT[x];
   }
   for (int x = threadIdx.x; x < Np * Np; x += blockDim.x) sD[x] = t.DphT[x];
-  const int nq = Nt * Np * (W / 4);
+}
+
+template <bool ASYNC, typename T, typename C>
+__device__ __forceinline__ void plane_rb_load(const Dims& d, const T* U, int c, long long tile,
+                                              C* su) {
+  int k, i, g, m0;
+  plane_tile_coords(d, c, tile, k, i, g, m0);
+  const int Np = d.Np, hP = d.NP / 2, W = 2 * c;
+  const long long base = (long long)g * d.S_g + (long long)i * d.S_i + (long long)k * d.NP;
+  const int nq = d.Nt * Np * (W / 4);
   for (int x = threadIdx.x; x < nq; x += blockDim.x) {
     const int w4 = (x % (W / 4)) * 4, jl = x / (W / 4), l = jl % Np, j = jl / Np;
-    T v[4];
-    ld4<T>(U + base + (long long)j * d.S_j + (long long)l * d.S_l + plane_m(w4, c, m0, hP), v);
-    C w[4] = {(C)v[0], (C)v[1], (C)v[2], (C)v[3]};
-    st4<C>(su + jl * W + w4, w);
+    copy4<ASYNC, T, C>(su + jl * W + w4,
+                       U + base + (long long)j * d.S_j + (long long)l * d.S_l + plane_m(w4, c, m0, hP));
+  }
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>& t, const C* su,
+                                              C* sSm, const C* sP, const C* sQ, const C* sD,
+                                              T* __restrict__ K, C sgn, int c, long long tile) {
+  constexpr int RB = kRBPlane, CB = 4;
+  const Dims& d = p.d;
+  const int Nt = d.Nt, Np = d.Np, hP = d.NP / 2, hp = Np / 2, W = 2 * c;
+  C* sDf = sSm + Nt * hp * W;
+  int k, i, g, m0;
+  plane_tile_coords(d, c, tile, k, i, g, m0);
+  const long long base = (long long)g * d.S_g + (long long)i * d.S_i + (long long)k * d.NP;
+  // sums and differences with the partner (phi + pi, Phi + pi) once per pair
+  for (int x = threadIdx.x; x < Nt * hp * (W / 4); x += blockDim.x) {
+    const int w4 = (x % (W / 4)) * 4, jl = x / (W / 4), l = jl % hp, jj = jl / hp;
+    const int w4h = w4 < c ? w4 + c : w4 - c;
+    C a[4], b[4], s[4], df[4];
+    ld4<C>(su + (jj * Np + l) * W + w4, a);
+    ld4<C>(su + (jj * Np + l + hp) * W + w4h, b);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      s[cc] = a[cc] + b[cc];
+      df[cc] = a[cc] - b[cc];
+    }
+    st4<C>(sSm + jl * W + w4, s);
+    st4<C>(sDf + jl * W + w4, df);
   }
   __syncthreads();
   const C sTk = t.sinT[k], ir = t.inv_r[i];
@@ -221,18 +357,17 @@ __device__ __forceinline__ void plane_tile_rb(const Problem& p, const Tables<C>&
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) ps[r][cc] = qd[r][cc] = da[r][cc] = db[r][cc] = 0;
     for (int jj = 0; jj < Nt; ++jj) {
-      C a[CB], b[CB], P[RB], Q[RB];
-      ld4<C>(su + (jj * Np + l) * W + w0, a);
-      ld4<C>(su + (jj * Np + lh) * W + w0h, b);
+      C sv[CB], dv[CB], P[RB], Q[RB];
+      ld4<C>(sSm + (jj * hp + l) * W + w0, sv);
+      ld4<C>(sDf + (jj * hp + l) * W + w0, dv);
       ldr<C, RB>(sP + jj * Nt + j0, P);
       ldr<C, RB>(sQ + jj * Nt + j0, Q);
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
-        const C sv = a[cc] + b[cc], dv = a[cc] - b[cc];
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-          ps[r][cc] = fmac(P[r], sv, ps[r][cc]);
-          qd[r][cc] = fmac(Q[r], dv, qd[r][cc]);
+          ps[r][cc] = fmac(P[r], sv[cc], ps[r][cc]);
+          qd[r][cc] = fmac(Q[r], dv[cc], qd[r][cc]);
         }
       }
     }
@@ -273,27 +408,60 @@ __device__ __forceinline__ void plane_tile_rb(const Problem& p, const Tables<C>&
   }
 }
 
-// ----------------------------------------------------------------------------
+template <typename T, typename C>
+__device__ __forceinline__ void plane_tile_rb(const Problem& p, const Tables<C>& t,
+                                              const T* __restrict__ U, T* __restrict__ K, C sgn,
+                                              int c, long long tile) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims& d = p.d;
+  const int Nt = d.Nt, Np = d.Np, W = 2 * c;
+  C* sP = reinterpret_cast<C*>(smem_raw);  // PthT [j'][j]
+  C* sQ = sP + Nt * Nt;
+  C* sD = sQ + Nt * Nt;                    // DphT [l'][l]
+  C* su = sD + Np * Np;                    // [j][l][w] (Np even: 16-byte aligned)
+  C* sSm = su + Nt * Np * W;
+  plane_rb_mats<C>(t, d, sP, sQ, sD);
+  plane_rb_load<false, T, C>(d, U, c, tile, su);
+  __syncthreads();
+  plane_rb_body<T, C>(p, t, su, sSm, sP, sQ, sD, K, sgn, c, tile);
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_plane_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn, int c,
+           long long ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims& d = p.d;
+  const int Nt = d.Nt, Np = d.Np, W = 2 * c, TS = Nt * Np * W;
+  C* sP = reinterpret_cast<C*>(smem_raw);
+  C* sQ = sP + Nt * Nt;
+  C* sD = sQ + Nt * Nt;
+  C* sbuf[2] = {sD + Np * Np, sD + Np * Np + TS};
+  C* sSm = sbuf[1] + TS;
+  plane_rb_mats<C>(t, d, sP, sQ, sD);
+  long long tile = blockIdx.x;
+  if (tile < ntiles) plane_rb_load<true, T, C>(d, U, c, tile, sbuf[0]);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    if (next < ntiles) plane_rb_load<true, T, C>(d, U, c, next, sbuf[(it + 1) & 1]);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    plane_rb_body<T, C>(p, t, sbuf[it & 1], sSm, sP, sQ, sD, K, sgn, c, tile);
+    __syncthreads();
+  }
+  cp_async_wait0();
+}
+
+// ============================================================================
 // Radial pass. Thread: RB output pairs (i, N-i) x 4 columns; the middle node
 // (odd Nr) by separate units; rows 0..n64-1 and N-n64+1..N (n64 = p.n_fp64_rows)
 // in double from the full matrix. Then the Tau rows and the stage update.
-template <typename T, typename C>
-__device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>& t,
-                                               const double* __restrict__ Dr64, const T* U,
-                                               const T* Kin, C sgn, int tau, int mode, T* F,
-                                               T* Acc, T* Uout, T* out, C dt, int W,
-                                               long long tile) {
-  constexpr int RB = kRBRad, CB = 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Dims d = p.d;
-  const int Nr = d.Nr, N = Nr - 1, hh = Nr / 2, NP = d.NP, S = d.NT * d.NP;
-  const int hh4 = (hh * hh + 3) & ~3, h4 = (hh + 3) & ~3;
-  C* sE = reinterpret_cast<C*>(smem_raw);  // EpT [i'][i]
-  C* sO = sE + hh4;                        // OpT [i'][i]
-  C* sMc = sO + hh4;                       // D[i][M]
-  C* sMr = sMc + h4;                       // D[M][i']
-  C* su = sMr + h4;                        // [i][w]
-  C* sk = su + Nr * W;                     // [i][w]
+// Shared layout: [EpT | OpT | DrMc | DrMr | (u, K) buffer(s) 2 Nr W | E, O 2 hh W]
+__device__ __forceinline__ void radial_tile_coords(const Dims& d, int W, long long tile,
+                                                   long long& base, int& c0, int& Wc) {
+  const int S = d.NT * d.NP;
   const int nchunk = (S + W - 1) / W;
   long long q = tile;
   const int chunk = (int)(q % nchunk);
@@ -302,10 +470,15 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
   q /= d.Np;
   const int j = (int)(q % d.Nt);
   const int g = (int)(q / d.Nt);
-  const int c0 = chunk * W;
-  const int Wc = min(W, S - c0);
-  const long long base =
-      (long long)g * d.S_g + (long long)j * d.S_j + (long long)l * d.S_l + c0;
+  c0 = chunk * W;
+  Wc = min(W, S - c0);
+  base = (long long)g * d.S_g + (long long)j * d.S_j + (long long)l * d.S_l + c0;
+}
+
+template <typename C>
+__device__ __forceinline__ void radial_rb_mats(const Tables<C>& t, int Nr, C* sE, C* sO, C* sMc,
+                                               C* sMr) {
+  const int hh = Nr / 2;
   for (int x = threadIdx.x; x < hh * hh; x += blockDim.x) {
     sE[x] = t.EpT[x];
     sO[x] = t.OpT[x];
@@ -314,17 +487,50 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
     sMc[x] = t.DrMc[x];
     sMr[x] = t.DrMr[x];
   }
+}
+
+template <bool ASYNC, typename T, typename C>
+__device__ __forceinline__ void radial_rb_load(const Dims& d, const T* U, const T* Kin, int W,
+                                               long long tile, C* su, C* sk) {
+  long long base;
+  int c0, Wc;
+  radial_tile_coords(d, W, tile, base, c0, Wc);
   const int W4 = Wc / 4;
-  for (int x = threadIdx.x; x < Nr * W4; x += blockDim.x) {
+  for (int x = threadIdx.x; x < d.Nr * W4; x += blockDim.x) {
     const int ii = x / W4, w = (x - ii * W4) * 4;
     const long long gi = base + (long long)ii * d.S_i + w;
-    T a[4], b[4];
-    ld4<T>(U + gi, a);
-    ld4<T>(Kin + gi, b);
-    C ca[4] = {(C)a[0], (C)a[1], (C)a[2], (C)a[3]};
-    C cb[4] = {(C)b[0], (C)b[1], (C)b[2], (C)b[3]};
-    st4<C>(su + ii * W + w, ca);
-    st4<C>(sk + ii * W + w, cb);
+    copy4<ASYNC, T, C>(su + ii * W + w, U + gi);
+    copy4<ASYNC, T, C>(sk + ii * W + w, Kin + gi);
+  }
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>& t,
+                                               const double* __restrict__ Dr64, const C* su,
+                                               C* sk, C* sEv, const C* sE, const C* sO,
+                                               const C* sMc, const C* sMr, C sgn, int tau,
+                                               int mode, T* F, T* Acc, T* Uout, T* out, C dt,
+                                               int W, long long tile) {
+  constexpr int RB = kRBRad, CB = 4;
+  const Dims& d = p.d;
+  const int Nr = d.Nr, N = Nr - 1, hh = Nr / 2, NP = d.NP;
+  C* sOd = sEv + hh * W;
+  long long base;
+  int c0, Wc;
+  radial_tile_coords(d, W, tile, base, c0, Wc);
+  const int W4 = Wc / 4;
+  for (int x = threadIdx.x; x < hh * W4; x += blockDim.x) {   // even/odd parts once per pair
+    const int ii = x / W4, w = (x - ii * W4) * 4;
+    C a[4], b[4], e[4], o[4];
+    ld4<C>(su + ii * W + w, a);
+    ld4<C>(su + (N - ii) * W + w, b);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      e[cc] = a[cc] + b[cc];
+      o[cc] = a[cc] - b[cc];
+    }
+    st4<C>(sEv + ii * W + w, e);
+    st4<C>(sOd + ii * W + w, o);
   }
   __syncthreads();
   const int n64 = p.n_fp64_rows;
@@ -340,18 +546,17 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) ae[r][cc] = ao[r][cc] = 0;
       for (int ii = 0; ii < hh; ++ii) {
-        C a[CB], b[CB], E[RB], O[RB];
-        ld4<C>(su + ii * W + w0, a);
-        ld4<C>(su + (N - ii) * W + w0, b);
+        C ev[CB], ov[CB], E[RB], O[RB];
+        ld4<C>(sEv + ii * W + w0, ev);
+        ld4<C>(sOd + ii * W + w0, ov);
         ldr<C, RB>(sE + ii * hh + i0, E);
         ldr<C, RB>(sO + ii * hh + i0, O);
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) {
-          const C ev = a[cc] + b[cc], ov = a[cc] - b[cc];
 #pragma unroll
           for (int r = 0; r < RB; ++r) {
-            ae[r][cc] = fmac(E[r], ev, ae[r][cc]);
-            ao[r][cc] = fmac(O[r], ov, ao[r][cc]);
+            ae[r][cc] = fmac(E[r], ev[cc], ae[r][cc]);
+            ao[r][cc] = fmac(O[r], ov[cc], ao[r][cc]);
           }
         }
       }
@@ -378,12 +583,11 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
       const int w0 = (unit - IR * W4) * CB;
       C am[CB] = {0, 0, 0, 0};
       for (int ii = 0; ii < hh; ++ii) {
-        C a[CB], b[CB];
-        ld4<C>(su + ii * W + w0, a);
-        ld4<C>(su + (N - ii) * W + w0, b);
+        C ov[CB];
+        ld4<C>(sOd + ii * W + w0, ov);
         const C mr = sMr[ii];
 #pragma unroll
-        for (int cc = 0; cc < CB; ++cc) am[cc] = fmac(mr, a[cc] - b[cc], am[cc]);
+        for (int cc = 0; cc < CB; ++cc) am[cc] = fmac(mr, ov[cc], am[cc]);
       }
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc)
@@ -446,9 +650,66 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
   }
 }
 
+template <typename T, typename C>
+__device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>& t,
+                                               const double* __restrict__ Dr64, const T* U,
+                                               const T* Kin, C sgn, int tau, int mode, T* F,
+                                               T* Acc, T* Uout, T* out, C dt, int W,
+                                               long long tile) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Nr = p.d.Nr, hh = Nr / 2;
+  const int hh4 = (hh * hh + 3) & ~3, h4 = (hh + 3) & ~3;
+  C* sE = reinterpret_cast<C*>(smem_raw);
+  C* sO = sE + hh4;
+  C* sMc = sO + hh4;
+  C* sMr = sMc + h4;
+  C* su = sMr + h4;
+  C* sk = su + Nr * W;
+  C* sEv = sk + Nr * W;
+  radial_rb_mats<C>(t, Nr, sE, sO, sMc, sMr);
+  radial_rb_load<false, T, C>(p.d, U, Kin, W, tile, su, sk);
+  __syncthreads();
+  radial_rb_body<T, C>(p, t, Dr64, su, sk, sEv, sE, sO, sMc, sMr, sgn, tau, mode, F, Acc, Uout,
+                       out, dt, W, tile);
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_radial_pp(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U, const T* Kin,
+            C sgn, int tau, int mode, T* F, T* Acc, T* Uout, T* out, C dt, int W,
+            long long ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Nr = p.d.Nr, hh = Nr / 2;
+  const int hh4 = (hh * hh + 3) & ~3, h4 = (hh + 3) & ~3;
+  C* sE = reinterpret_cast<C*>(smem_raw);
+  C* sO = sE + hh4;
+  C* sMc = sO + hh4;
+  C* sMr = sMc + h4;
+  C* sbuf[2] = {sMr + h4, sMr + h4 + 2 * Nr * W};   // each: u [Nr][W] then K [Nr][W]
+  C* sEv = sbuf[1] + 2 * Nr * W;
+  radial_rb_mats<C>(t, Nr, sE, sO, sMc, sMr);
+  long long tile = blockIdx.x;
+  if (tile < ntiles) radial_rb_load<true, T, C>(p.d, U, Kin, W, tile, sbuf[0], sbuf[0] + Nr * W);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    C* nb_ = sbuf[(it + 1) & 1];
+    if (next < ntiles) radial_rb_load<true, T, C>(p.d, U, Kin, W, next, nb_, nb_ + Nr * W);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    C* cb = sbuf[it & 1];
+    radial_rb_body<T, C>(p, t, Dr64, cb, cb + Nr * W, sEv, sE, sO, sMc, sMr, sgn, tau, mode, F,
+                         Acc, Uout, out, dt, W, tile);
+    __syncthreads();
+  }
+  cp_async_wait0();
+}
+
 // ----------------------------------------------------------------------------
 // Pass dispatch (register-blocked form where the grid allows it) and the
-// single-problem kernels: one tile per CTA.
+// single-problem one-tile-per-CTA kernels (generic form, or rb without a
+// persistent launch).
 template <typename T, typename C>
 __device__ __forceinline__ void angular_tile_any(const Problem& p, const Tables<C>& t,
                                                  const T* U, T* K, C sgn, int collision, int nb,

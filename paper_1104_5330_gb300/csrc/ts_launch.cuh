@@ -26,24 +26,57 @@ static cudaError_t allow_smem(K kernel) {
 static inline unsigned grid1(long long n) { return (unsigned)n; }
 
 // Shared memory of one tile of each forward pass (rb: register-blocked form).
+// The register-blocked forms also hold the even/odd sums and differences.
 template <typename C>
 size_t smem_angular(const Dims& d, int nb, bool rb) {
   const size_t S = (size_t)d.NT * d.NP, mats = 2 * d.NT * d.NT + d.NP * d.NP;
-  return (mats + nb * S + (rb ? 4 * nb : nb)) * sizeof(C);
+  return (mats + (rb ? 2 : 1) * nb * S + (rb ? 4 * nb : nb)) * sizeof(C);
 }
 template <typename C>
 size_t smem_plane(const Dims& d, int c, bool rb) {
-  (void)rb;
-  return (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + d.Nt * d.Np * 2 * c) * sizeof(C);
+  return (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + (rb ? 2 : 1) * d.Nt * d.Np * 2 * c) * sizeof(C);
 }
 template <typename C>
 size_t smem_radial(const Dims& d, int W, bool rb) {
   if (!rb) return (size_t)(d.Nr * d.Nr + 2 * d.Nr * W) * sizeof(C);
   const int hh = d.Nr / 2;
-  return (size_t)(2 * ((hh * hh + 3) & ~3) + 2 * ((hh + 3) & ~3) + 2 * d.Nr * W) * sizeof(C);
+  return (size_t)(2 * ((hh * hh + 3) & ~3) + 2 * ((hh + 3) & ~3) + 2 * d.Nr * W + 2 * hh * W) *
+         sizeof(C);
 }
 
-// Built-in tile shapes: fill 256 threads with work while staying in the budget.
+// Persistent double-buffered forms: two staging buffers per CTA.
+template <typename C>
+size_t smem_angular_pp(const Dims& d, int nb) {
+  return smem_angular<C>(d, nb, true) + (size_t)nb * d.NT * d.NP * sizeof(C);
+}
+template <typename C>
+size_t smem_plane_pp(const Dims& d, int c) {
+  return smem_plane<C>(d, c, true) + (size_t)d.Nt * d.Np * 2 * c * sizeof(C);
+}
+template <typename C>
+size_t smem_radial_pp(const Dims& d, int W) {
+  return smem_radial<C>(d, W, true) + (size_t)2 * d.Nr * W * sizeof(C);
+}
+
+// CTAs of a persistent kernel: as many as fit on the GPU at this shared-memory size.
+template <typename K>
+static int persistent_ctas(K kernel, size_t smem, long long ntiles) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  return (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)occ * nsm));
+}
+
+// Built-in tile shapes: fill 256 threads with work while staying in the budget
+// (with room for the second staging buffer of the persistent forms).
 template <typename T, typename C>
 static int angular_nb(const Dims& d, int ntiles, bool rb = false) {
   const int S = d.NT * d.NP;
@@ -55,7 +88,8 @@ static int angular_nb(const Dims& d, int ntiles, bool rb = false) {
     nb = std::max(1, 2048 / S);
   }
   const size_t mats = (size_t)(2 * d.NT * d.NT + d.NP * d.NP) * sizeof(C);
-  while (nb > 1 && mats + (size_t)nb * (ntiles * S + 4) * sizeof(C) > kSmemBudget) nb /= 2;
+  const int per_block = (rb && ntiles == 1) ? 3 : ntiles;   // tiles of S values per block
+  while (nb > 1 && mats + (size_t)nb * (per_block * S + 4) * sizeof(C) > kSmemBudget) nb /= 2;
   return nb;
 }
 
@@ -64,9 +98,10 @@ static int plane_c(const Dims& d, int ntiles, bool rb = false) {
   const int hP = d.NP / 2;
   const size_t mats = (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np) * sizeof(C);
   int best = rb ? 4 : 1;
+  const int tiles = rb ? 3 * ntiles : ntiles;
   for (int c = 1; c <= hP; ++c) {
     if (hP % c || (rb && c % 4)) continue;
-    if (mats + (size_t)ntiles * d.Nt * d.Np * 2 * c * sizeof(C) <= kSmemBudget) best = c;
+    if (mats + (size_t)tiles * d.Nt * d.Np * 2 * c * sizeof(C) <= kSmemBudget) best = c;
   }
   return best;
 }
@@ -78,7 +113,7 @@ static int radial_W(const Dims& d, int ntiles, bool rb = false) {
   if (rb) {
     const int hh = d.Nr / 2;
     W = std::max(4, std::min(S, (4 * 256 * kRBRad / std::max(1, hh)) & ~3));
-    while (W > 4 && smem_radial<C>(d, W, true) > kSmemBudget) W = (W / 2) & ~3;
+    while (W > 4 && smem_radial_pp<C>(d, W) > kSmemBudget) W = (W / 2) & ~3;
     return std::max(4, W);
   }
   W = std::min(S, sizeof(C) == 8 ? 64 : 128);
@@ -91,16 +126,24 @@ cudaError_t Launch<T, C>::angular(const Problem& p, const Tables<C>& t, const T*
                                   bool collision, cudaStream_t s) {
   static bool init = false;
   if (!init) {
-    const cudaError_t ea = allow_smem(k_angular<T, C>);
+    cudaError_t ea = allow_smem(k_angular<T, C>);
+    if (ea == cudaSuccess) ea = allow_smem(k_angular_pp<T, C>);
     if (ea != cudaSuccess) return ea;
     init = true;
   }
   const Dims& d = p.d;
   const bool rb = p.tp.rb & 1;
   const int nb = p.tp.nb > 0 ? p.tp.nb : angular_nb<T, C>(d, 1, rb);
+  const long long ntiles = (d.nblk + nb - 1) / nb;
+  if (rb) {
+    const size_t smem = smem_angular_pp<C>(d, nb);
+    const int ctas = persistent_ctas(k_angular_pp<T, C>, smem, ntiles);
+    k_angular_pp<T, C><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, collision ? 1 : 0, nb,
+                                                    ntiles);
+    return cudaGetLastError();
+  }
   const size_t smem = smem_angular<C>(d, nb, rb);
-  k_angular<T, C><<<grid1((d.nblk + nb - 1) / nb), kThreads, smem, s>>>(p, t, U, K, sgn,
-                                                                         collision ? 1 : 0, nb);
+  k_angular<T, C><<<grid1(ntiles), kThreads, smem, s>>>(p, t, U, K, sgn, collision ? 1 : 0, nb);
   return cudaGetLastError();
 }
 
@@ -109,15 +152,22 @@ cudaError_t Launch<T, C>::plane(const Problem& p, const Tables<C>& t, const T* U
                                 cudaStream_t s) {
   static bool init = false;
   if (!init) {
-    const cudaError_t ea = allow_smem(k_plane<T, C>);
+    cudaError_t ea = allow_smem(k_plane<T, C>);
+    if (ea == cudaSuccess) ea = allow_smem(k_plane_pp<T, C>);
     if (ea != cudaSuccess) return ea;
     init = true;
   }
   const Dims& d = p.d;
   const bool rb = p.tp.rb & 2;
   const int c = p.tp.c > 0 ? p.tp.c : plane_c<T, C>(d, 1, rb);
-  const size_t smem = smem_plane<C>(d, c, rb);
   const long long nct = (long long)d.G * d.Nr * d.NT * (d.NP / 2 / c);
+  if (rb) {
+    const size_t smem = smem_plane_pp<C>(d, c);
+    const int ctas = persistent_ctas(k_plane_pp<T, C>, smem, nct);
+    k_plane_pp<T, C><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, c, nct);
+    return cudaGetLastError();
+  }
+  const size_t smem = smem_plane<C>(d, c, rb);
   k_plane<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, U, K, sgn, c);
   return cudaGetLastError();
 }
@@ -128,7 +178,8 @@ cudaError_t Launch<T, C>::radial(const Problem& p, const Tables<C>& t, const dou
                                  T* Uout, T* out, double dt, cudaStream_t s) {
   static bool init = false;
   if (!init) {
-    const cudaError_t ea = allow_smem(k_radial<T, C>);
+    cudaError_t ea = allow_smem(k_radial<T, C>);
+    if (ea == cudaSuccess) ea = allow_smem(k_radial_pp<T, C>);
     if (ea != cudaSuccess) return ea;
     init = true;
   }
@@ -140,8 +191,15 @@ cudaError_t Launch<T, C>::radial(const Problem& p, const Tables<C>& t, const dou
   const bool rb = p.tp.rb & 4;
   const int W = p.tp.W > 0 ? p.tp.W : radial_W<T, C>(d, 2, rb);
   const int S = d.NT * d.NP;
-  const size_t smem = smem_radial<C>(d, W, rb);
   const long long nct = (long long)d.G * d.Nt * d.Np * ((S + W - 1) / W);
+  if (rb) {
+    const size_t smem = smem_radial_pp<C>(d, W);
+    const int ctas = persistent_ctas(k_radial_pp<T, C>, smem, nct);
+    k_radial_pp<T, C><<<ctas, kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, tau ? 1 : 0, mode, F,
+                                                   Acc, Uout, out, (C)dt, W, nct);
+    return cudaGetLastError();
+  }
+  const size_t smem = smem_radial<C>(d, W, rb);
   k_radial<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, tau ? 1 : 0, mode, F,
                                                     Acc, Uout, out, (C)dt, W);
   return cudaGetLastError();

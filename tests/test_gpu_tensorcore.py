@@ -1,0 +1,67 @@
+"""The split-TF32 tensor-core radial pass (TS_TF32X3: tcgen05.mma with a TMEM
+accumulator, operands x = hi + lo in TF32, products hi*hi + hi*lo + lo*hi in
+FP32). Bar: the FP32 bound (1e-5 relative L2) against the FP64 oracle, and
+agreement with the FP32 SIMT passes."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import T, absorber_workload, cuda, host, pair, rel_l2, setup_both
+from paper_1104_5330_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+# 128-column tiles: whole (256 = 2 tiles), ragged (96 < 128, 192 = 1.5 tiles)
+GRIDS = [(0.2, 1.0, 33, 8, 8, 16, 16), (0.2, 1.0, 17, 6, 4, 8, 12), (0.3, 1.2, 65, 4, 6, 16, 12),
+         (0.2, 1.0, 9, 4, 4, 8, 8)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1104_5330_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    yield
+
+
+@pytest.mark.parametrize("dims", GRIDS)
+def test_tensor_core_rhs_and_steps_against_oracle(dims):
+    og, gg = pair(*dims, G=2, precision=3)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    F = F0 + 0.1 * np.random.default_rng(3).standard_normal(og.shape)
+    K = host(gg.rhs(cuda(F, torch.float32)))
+    T().ts_sync_status(gg.handle)
+    assert rel_l2(K, op.rhs(F)) < 1e-5
+    dt = I.dt_rule(dims[0], dims[1], dims[2])
+    Fg = cuda(F0, torch.float32)
+    gg.step(Fg, dt, 20)
+    T().ts_sync_status(gg.handle)
+    assert rel_l2(host(Fg), op.run(F0, dt, 20)) < 1e-5
+
+
+def test_tensor_core_radial_derivative_on_polynomial():
+    """cos(Theta) p'(r) for F = p(r) at 65 nodes through the tensor cores."""
+    og, gg = pair(0.2, 1.0, 65, 4, 4, 16, 8, precision=3)
+    gg.set_coeffs()
+    rng = np.random.default_rng(9)
+    p = np.polynomial.Chebyshev(rng.standard_normal(30) * 0.8 ** np.arange(30), domain=[0.2, 1.0])
+    F = np.ascontiguousarray(np.broadcast_to(p(og.r)[None, :, None, None, None, None], og.shape))
+    LF = host(gg.liouville(cuda(F, torch.float32)))
+    E = np.cos(og.Theta)[None, None, None, None, :, None] * p.deriv()(og.r)[None, :, None, None, None, None]
+    assert rel_l2(LF, np.broadcast_to(E, og.shape)) < 1e-5
+
+
+def test_tensor_core_agrees_with_simt_fp32():
+    dims = GRIDS[0]
+    og, tc = pair(*dims, G=3, precision=3)
+    _, simt = pair(*dims, G=3, precision=1)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    for g in (tc, simt):
+        g.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(dims[0], dims[1], dims[2])
+    a, b = cuda(F0, torch.float32), cuda(F0, torch.float32)
+    tc.step(a, dt, 10)
+    simt.step(b, dt, 10)
+    T().ts_sync_status(tc.handle)
+    assert rel_l2(host(a), host(b)) < 2e-6
