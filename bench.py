@@ -49,7 +49,10 @@ WORKLOADS = {
     "absorber_17x8^4_g1": (0.2, 1.0, 17, 8, 8, 8, 8, 1),
     "absorber_65x32^4_g1": (0.2, 1.0, 65, 32, 32, 32, 32, 1),
 }
-FP64_NOMINAL_TFLOPS = 1.25     # GB300 nominal FP64 (vector and tensor) rate
+PRECISIONS = {"fp64": "TS_FP64", "fp32": "TS_FP32", "fp32_r64": "TS_FP32_R64",
+              "tf32x3": "TS_TF32X3"}
+FP64_FMA_PER_SM_CLK = 2        # GB300: 2 FP64 FMA lanes per SM (1/64 of the 128 FP32 lanes)
+FP32_FMA_PER_SM_CLK = 128
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -87,7 +90,7 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for f in ("ts_kernels.cuh", "ts_launch.cuh"):
+    for f in ("ts_kernels.cuh", "ts_kernels_rb.cuh", "ts_launch.cuh", "ts_tc.cuh"):
         with open(os.path.join(ROOT, "paper_1104_5330_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -325,7 +328,7 @@ def run_ours(args, dims, wname):
     from paper_1104_5330_gb300 import inputs as I
 
     R1, R2, Nr, Nt, Np, NT, NP, G = dims
-    prec = ts.TS_FP64 if args.precision == "fp64" else ts.TS_FP32
+    prec = getattr(ts, PRECISIONS[args.precision])
     tdt = torch.float64 if prec == ts.TS_FP64 else torch.float32
     es = 8 if prec == ts.TS_FP64 else 4
 
@@ -372,20 +375,31 @@ def run_ours(args, dims, wname):
     dname = names[dom]
     avg_ms = pass_ms[dom] / pass_n[dom]
     peaks, peak_src = _peaks()
+    # the register-blocked even/odd passes launch as persistent k_<pass>_pp kernels
+    kfam = f"k_{dname}_pp" if even_odd_passes(dims, es)[dname] else f"k_{dname}"
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    smax = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = sms * 2 * FP64_FMA_PER_SM_CLK * smax * 1e6 / 1e12
     if prec == ts.TS_FP64:
         achieved = flops[dname] / (avg_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": f"k_{dname}<double>", "achieved": achieved,
-                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
-                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+        roof = {"bound": "alu", "kernel": f"{kfam}<double>", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "peak_source": f"derived: {sms} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 flop "
+                               f"x {smax:.0f} MHz",
+                "measured_dfma_loop_tflops": ts.ts_probe_fma_rate(ts.TS_FP64),
                 "algorithmic_flops_per_launch": flops[dname],
                 "traffic": _traffic(dname, wname, args.precision),
                 "algorithmic_bytes_per_launch": byts[dname],
                 "hbm_achieved_gbs": byts[dname] / (avg_ms * 1e-3) / 1e9}
     else:
         achieved = byts[dname] / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": f"k_{dname}<float>", "achieved": achieved,
+        if prec == ts.TS_TF32X3 and dname == "radial":
+            kfam = "k_radial_tc"
+        roof = {"bound": "hbm", "kernel": f"{kfam}<float>", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": f"{peak_src} hbm_gbs",
+                "fp32_alu_tflops": flops[dname] / (avg_ms * 1e-3) / 1e12,
+                "fp32_alu_peak_tflops": sms * 2 * FP32_FMA_PER_SM_CLK * smax * 1e6 / 1e12,
                 "algorithmic_bytes_per_launch": byts[dname],
                 "traffic": _traffic(dname, wname, args.precision)}
     roof["avg_launch_ms"] = avg_ms
@@ -446,11 +460,12 @@ def run_ours(args, dims, wname):
             ts.ts_sync_status(g32.handle)
             ms32 = e0.elapsed_time(e1)
             pm, pn = ts.ts_step_profile(g32.handle, F32b, dt, nv)
-            _, _, by32 = pass_work(dims, 4)
+            _, fl32, by32 = pass_work(dims, 4)
             d32 = int(np.argmax(pm[:3]))
             hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
-            kn = (kname.get(names[d32], f"k_{names[d32]}") if vprec == ts.TS_TF32X3
-                  else f"k_{names[d32]}") + "<float>"
+            alu32 = fl32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e12
+            kf = f"k_{names[d32]}_pp" if even_odd_passes(dims, 4)[names[d32]] else f"k_{names[d32]}"
+            kn = (kname.get(names[d32], kf) if vprec == ts.TS_TF32X3 else kf) + "<float>"
             line["variants"][vname] = {
                 "value": pts * args.steps / (ms32 * 1e-3), "unit": "point-updates/s",
                 "ms_per_step": ms32 / args.steps, "dtype": "f32",
@@ -458,6 +473,8 @@ def run_ours(args, dims, wname):
                 "roofline": {"bound": "hbm", "kernel": kn,
                              "achieved": hbm32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": hbm32 / peaks["hbm_gbs"],
+                             "fp32_alu_tflops": alu32,
+                             "fp32_alu_peak_tflops": sms * 2 * FP32_FMA_PER_SM_CLK * smax * 1e6 / 1e12,
                              "pass_share": {n: float(s) for n, s in zip(names, pm[:3] / pm[:3].sum())},
                              "pass_ms_per_launch": {n: float(pm[a] / pn[a]) for a, n in enumerate(names)}}}
             del g32, F32, F32b
@@ -481,10 +498,10 @@ def run_ours(args, dims, wname):
         line["batch"] = run_batch(args, stream)
 
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
-        rate, wall, cores = oracle_rate(dims, 0, 1)
+        rate, wall, cores = oracle_rate(dims, 0, 3)
         line["cpu_baseline"] = {"value": rate, "unit": "point-updates/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": f"1 RK4 step of each of the {G} groups of {wname} "
+                                "sample": f"3 RK4 steps of each of the {G} groups of {wname} "
                                           f"({wall:.1f} s wall, one process per group)"}
     if world > 1:
         dist.barrier()
@@ -500,7 +517,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default="fp64")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="absorber_33x16^4_g4")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-variants", action="store_true")

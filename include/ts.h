@@ -252,6 +252,15 @@ ts_status ts_batch_grid(ts_batch* batch, int problem, ts_grid** grid);
 ts_status ts_batch_step(ts_batch* batch, void* const* F_host_array, const double* dt_host,
                         int nsteps, void* stream);
 
+/* Measured fused multiply-add rate of the current device in TFLOP/s (2 flops
+ * per FMA), for precision TS_FP64 or TS_FP32 (else TS_ERR_UNSUPPORTED): a loop
+ * of 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, best
+ * of three timed launches after one warm-up, CUDA events on `stream`.
+ * Allocates and frees a small device buffer and synchronizes `stream`. The
+ * paper has no counterpart: this is the measured denominator of the roofline of
+ * the FP64 passes, which are bound by the FP64 arithmetic units. */
+ts_status ts_probe_fma_rate(int precision, double* tflops, void* stream);
+
 /* Status of device-side checks latched since the last call (bounded waits).
  * Synchronizes `stream`. */
 ts_status ts_sync_status(ts_grid* grid, void* stream);

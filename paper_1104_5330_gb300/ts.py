@@ -75,6 +75,7 @@ def _load():
         "ts_batch_grid": [P, I, ctypes.POINTER(P)],
         "ts_batch_step": [P, P, P, I, P],
         "ts_sync_status": [P, P],
+        "ts_probe_fma_rate": [I, ctypes.POINTER(D), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -120,6 +121,13 @@ def _stream(stream):
 
 def ts_version() -> str:
     return LIB.ts_version().decode()
+
+
+def ts_probe_fma_rate(precision: int, stream=None) -> float:
+    """Measured FMA rate (TFLOP/s) of the current device for TS_FP64 or TS_FP32."""
+    out = ctypes.c_double()
+    _check(LIB.ts_probe_fma_rate(precision, ctypes.byref(out), _stream(stream)), "ts_probe_fma_rate")
+    return out.value
 
 
 def ts_create_grid(desc: GridDesc):
