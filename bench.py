@@ -173,7 +173,13 @@ def even_odd_passes(dims, es):
     rbA = 4 if es == 4 else 2
     return {"angular": NT % rbA == 0 and NP % 8 == 0,
             "plane": Nt % 2 == 0 and Np % 2 == 0 and NP % 8 == 0,
-            "radial": Nr >= 9 and (Nr // 2) % 2 == 0 and (NT * NP) % 4 == 0}
+            "radial": Nr >= 9 and (Nr // 2) % rbA == 0 and (NT * NP) % 4 == 0}
+
+
+def eo_kernel(name):
+    """Kernel of the register-blocked even/odd form of a pass: persistent
+    k_angular_pp / k_plane_pp, one tile per CTA k_radial_eo."""
+    return "k_radial_eo" if name == "radial" else f"k_{name}_pp"
 
 
 def pass_work(dims, es):
@@ -375,8 +381,7 @@ def run_ours(args, dims, wname):
     dname = names[dom]
     avg_ms = pass_ms[dom] / pass_n[dom]
     peaks, peak_src = _peaks()
-    # the register-blocked even/odd passes launch as persistent k_<pass>_pp kernels
-    kfam = f"k_{dname}_pp" if even_odd_passes(dims, es)[dname] else f"k_{dname}"
+    kfam = eo_kernel(dname) if even_odd_passes(dims, es)[dname] else f"k_{dname}"
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     smax = peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = sms * 2 * FP64_FMA_PER_SM_CLK * smax * 1e6 / 1e12
@@ -464,7 +469,7 @@ def run_ours(args, dims, wname):
             d32 = int(np.argmax(pm[:3]))
             hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
             alu32 = fl32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e12
-            kf = f"k_{names[d32]}_pp" if even_odd_passes(dims, 4)[names[d32]] else f"k_{names[d32]}"
+            kf = eo_kernel(names[d32]) if even_odd_passes(dims, 4)[names[d32]] else f"k_{names[d32]}"
             kn = (kname.get(names[d32], kf) if vprec == ts.TS_TF32X3 else kf) + "<float>"
             line["variants"][vname] = {
                 "value": pts * args.steps / (ms32 * 1e-3), "unit": "point-updates/s",

@@ -214,8 +214,10 @@ ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0
  * Results are cached per (precision, Nr, Ntheta, Nphi, NTheta, NPhi) for the
  * process and, if the environment variable TS_AUTOTUNE_CACHE names a file,
  * appended to / read from that file. Overwrites the grid's workspace.
- * Synchronous. Tile shapes change no result bit: every element is computed by
- * the same arithmetic in any tile. (No counterpart in the paper.) */
+ * Synchronous. Tile shapes change results at most at the rounding level: every
+ * element is computed by the same operations in any tile, but some shapes
+ * select a form of a pass compiled for the grid's sizes. (No counterpart in the
+ * paper.) */
 ts_status ts_autotune(ts_grid* grid, void* stream);
 
 /* The tile shapes the grid's forward passes use (after ts_autotune, or the
@@ -228,9 +230,11 @@ ts_status ts_tile_shape(const ts_grid* grid, int* angular_blocks, int* plane_pai
  * description, energy groups, scheme and coefficients; one precision for the
  * whole batch) stepped together. Each pass of a stage is one persistent
  * launch whose CTAs take tiles of every problem from an atomic work queue; a
- * step is captured once into a CUDA graph and replayed. Results are bit-for-bit
- * those of ts_step on each problem's grid. (The paper steps one problem at a
- * time; batching is a property of this library.) */
+ * step is captured once into a CUDA graph and replayed. Results equal those
+ * of ts_step on each problem's grid to rounding (the same operations; the
+ * batched kernel runs the run-time-size form of each pass), and replaying the
+ * graph reproduces them bit for bit. (The paper steps one problem at a time;
+ * batching is a property of this library.) */
 typedef struct ts_batch ts_batch;
 
 /* Create grids for descs[0..n-1] (as ts_create_grid) and, if autotune != 0,

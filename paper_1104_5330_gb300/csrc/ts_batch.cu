@@ -4,9 +4,9 @@
 // Each pass of a stage is ONE persistent launch over the tiles of every
 // problem: CTAs (as many as fit on the GPU) take tile numbers from an atomic
 // work queue, find the owning problem by binary search over the per-problem
-// tile offsets, and run the same tile function as the single-problem kernels,
-// so a batched step gives bit-for-bit the results of stepping each problem on
-// its own. One step (a counter reset and 12 or 13 persistent launches) is
+// tile offsets, and run the run-time-size form of the single-problem tile
+// functions, so a batched step performs the operations of stepping each
+// problem on its own (results agree to rounding). One step (a counter reset and 12 or 13 persistent launches) is
 // captured once into a CUDA graph and replayed for every step.
 //
 // The autotuner times the candidate tile shapes of the three forward passes of
@@ -188,7 +188,7 @@ cudaError_t tune_grid(ts_grid* g, const Tables<C>& t, cudaStream_t st, TileParam
   // radial: W
   if (e == cudaSuccess) e = timeit(2, best, &tbest);
   for (int W = 16; W <= 512 && e == cudaSuccess; W *= 2) {
-    const size_t sm = rbR ? smem_radial_pp<C>(d, W) : smem_radial<C>(d, W, false);
+    const size_t sm = smem_radial<C>(d, W, rbR);
     if (W > d.NT * d.NP || sm > kSmemMax || W == best.W) continue;
     TileParams cand = best;
     cand.W = W;

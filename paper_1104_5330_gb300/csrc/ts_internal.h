@@ -56,17 +56,19 @@ struct TileParams {
   int rb = 0;
 };
 
-// Output rows per thread of the register-blocked plane and radial passes.
+// Output rows per thread of the register-blocked passes: angular and radial 4
+// in float, 2 in double; plane 2.
 constexpr int kRBPlane = 2;
-constexpr int kRBRad = 2;
+__host__ __device__ constexpr int rb_ang(int elem_bytes) { return elem_bytes == 4 ? 4 : 2; }
+__host__ __device__ constexpr int rb_rad(int elem_bytes) { return elem_bytes == 4 ? 4 : 2; }
 
 // Which forward passes of a grid can use the register-blocked even/odd form.
 inline int rb_mask(const Dims& d, int elem_bytes, int n64) {
-  const int rbA = elem_bytes == 4 ? 4 : 2;
   int m = 0;
-  if (d.NT % rbA == 0 && d.NP % 8 == 0) m |= 1;
+  if (d.NT % rb_ang(elem_bytes) == 0 && d.NP % 8 == 0) m |= 1;
   if (d.Nt % kRBPlane == 0 && d.Np % 2 == 0 && d.NP % 8 == 0) m |= 2;
-  if (d.Nr >= 9 && (d.Nr / 2) % kRBRad == 0 && (d.NT * d.NP) % 4 == 0 && n64 <= 2) m |= 4;
+  if (d.Nr >= 9 && (d.Nr / 2) % rb_rad(elem_bytes) == 0 && (d.NT * d.NP) % 4 == 0 && n64 <= 2)
+    m |= 4;
   return m;
 }
 

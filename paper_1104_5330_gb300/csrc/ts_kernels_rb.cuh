@@ -1,5 +1,5 @@
-// Register-blocked forms of the three forward passes, and their persistent,
-// double-buffered launches.
+// Register-blocked forms of the three forward passes, and their persistent
+// launches.
 //
 // Each pass is a batch of small matrix products (the per-axis derivative
 // matrices against the staged lines). Here every thread owns an RB x 4 block of
@@ -14,11 +14,15 @@
 // The sums and differences are formed once per tile in shared memory.
 //
 // Every pass is split into a staging step (the tile's input lines into shared
-// memory) and a compute step. The single-tile form stages synchronously (used
-// by the batched kernels); the persistent kernels k_*_pp keep the derivative
-// matrices in shared memory for all their tiles and stage tile t + gridDim.x
-// with asynchronous 16-byte copies (cp.async) into a second buffer while tile
-// t is computed.
+// memory), a preparation step (sums/differences, transposed copy) and a
+// compute step. The single-tile form stages synchronously (used by the batched
+// kernels); the persistent kernels k_*_pp keep the derivative matrices in
+// shared memory for all their tiles and stage the next tile with asynchronous
+// 16-byte copies (cp.async) while the current one is computed.
+//
+// The line lengths are template parameters (0 = read from the grid at run
+// time): with them fixed, the contraction loops unroll completely and the
+// index arithmetic folds into immediate offsets.
 //
 // Requirements (checked on the host): NT, Nt multiples of RB, NP a multiple
 // of 8, plane columns per half (c) a multiple of 4, Nr/2 a multiple of RB.
@@ -55,11 +59,29 @@ __device__ __forceinline__ void st4<double>(double* p, const double (&v)[4]) {
   reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
+
+// RB consecutive elements from an address aligned to RB elements (vector loads
+// where RB elements make 8 or 16 bytes).
 template <typename C, int RB>
-__device__ __forceinline__ void ldr(const C* p, C (&v)[RB]) {
+__device__ __forceinline__ void ldv(const C* p, C (&v)[RB]) {
+  if constexpr (sizeof(C) == 4 && RB == 4) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else if constexpr (sizeof(C) == 4 && RB == 2) {
+    const float2 a = *reinterpret_cast<const float2*>(p);
+    v[0] = a.x; v[1] = a.y;
+  } else if constexpr (sizeof(C) == 8 && RB == 2) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    v[0] = a.x; v[1] = a.y;
+  } else {
 #pragma unroll
-  for (int r = 0; r < RB; ++r) v[r] = p[r];
+    for (int r = 0; r < RB; ++r) v[r] = p[r];
+  }
 }
+
+// Compile-time line length if given, else the run-time one.
+template <int CT>
+__device__ __forceinline__ int ctsz(int rt) { return CT ? CT : rt; }
 
 // Four consecutive elements global -> shared: plain (convert T -> C) or as
 // asynchronous 16-byte copies (T == C), completed by cp.async.wait_group.
@@ -84,12 +106,35 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// RB for the angular pass (rows of Theta per thread); kRBPlane, kRBRad in ts_internal.h.
-template <typename C> struct RBAng { static constexpr int v = sizeof(C) == 4 ? 4 : 2; };
+// RB per pass (rows per thread): 4 in float, 2 in double for the angular and
+// radial passes (rb_ang / rb_rad in ts_internal.h), kRBPlane for the plane pass.
+template <typename C> struct RBAng { static constexpr int v = rb_ang((int)sizeof(C)); };
+template <typename C> struct RBRad { static constexpr int v = rb_rad((int)sizeof(C)); };
+
+// Row pitch of the transposed angular block (16 bytes of padding: the
+// transposing stores of a warp then cover all banks once).
+template <typename C>
+__host__ __device__ constexpr int ang_utp(int NT) { return NT + 16 / (int)sizeof(C); }
+
+// Line lengths with compiled-in forms of the single-problem kernels (0: the
+// run-time form, which the batched kernel always uses). The two forms perform
+// the same operations; results agree to rounding, not bit for bit.
+__host__ __device__ inline int ang_spec(const Dims& d) {
+  if (d.NT != d.NP) return 0;
+  return (d.NT == 16 || d.NT == 24 || d.NT == 32) ? d.NT : 0;
+}
+__host__ __device__ inline int plane_spec(const Dims& d, int c) {
+  const bool sq = d.Nt == d.Np && d.Np == d.NT && d.NT == d.NP && 2 * c == d.NP;
+  return (sq && (d.NP == 8 || d.NP == 16 || d.NP == 24 || d.NP == 32)) ? d.NP : 0;
+}
+__host__ __device__ inline int rad_spec(const Dims& d) {
+  return (d.Nr == 17 || d.Nr == 33 || d.Nr == 65) ? d.Nr : 0;
+}
 
 // ============================================================================
 // Angular pass. Thread: RB Theta rows k0.. x 4 column pairs (m, m + NP/2) of one block.
-// Shared layout: [PThT | QThT | DPhT | tile buffer(s) nb*S | sums/diffs nb*S | 4 nb]
+// Shared layout: [PThT | QThT | DPhT | tile nb*S | sums/diffs nb*S |
+//                 transposed tile nb*NP*UTP | 6 nb per-block scalars]
 template <typename C>
 __device__ __forceinline__ void angular_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
                                                 C* sD) {
@@ -111,27 +156,34 @@ __device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int n
   for (int x = 4 * threadIdx.x; x < nbb * S; x += 4 * blockDim.x) copy4<ASYNC, T, C>(su + x, src + x);
 }
 
-// Compute one staged tile. Entry: su complete and visible to all threads; sSD
-// and sc free. Exit: all outputs written (sSD/sc may still be read until the
-// caller's next barrier).
-template <typename T, typename C>
-__device__ __forceinline__ void angular_rb_body(const Problem& p, const Tables<C>& t,
-                                                const C* su, C* sSD, C* sc, const C* sP,
-                                                const C* sQ, const C* sD, T* __restrict__ K,
-                                                C sgn, int collision, int nb, long long tile) {
-  constexpr int RB = RBAng<C>::v, CB = 4;
+// Preparation of a staged tile: coefficients, J, the sums and differences of
+// every Phi pair, and the transposed copy uT[m][k] (for the Phi contraction
+// and the pointwise terms). Entry: su complete and visible. Exit (after the
+// caller's barrier): su is no longer read.
+template <int NT_, int NP_, typename T, typename C>
+__device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C>& t,
+                                                const C* su, C* sSD, C* uT, C* sc, int collision,
+                                                int nb, long long tile) {
   const Dims& d = p.d;
-  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2;
+  const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2;
+  const int UTP = ang_utp<C>(NT), H4 = hP / 4;
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
-  for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // one conversion per block
+  for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // once per block
     sc[nb + x] = (C)p.kap[b0 + x];
     sc[2 * nb + x] = (C)p.eta[b0 + x];
     sc[3 * nb + x] = (C)p.kaps[b0 + x];
+    int g, i, j, l;
+    decode_block(d, b0 + x, g, i, j, l);
+    sc[4 * nb + x] = t.inv_r[i];
+    sc[5 * nb + x] = t.cot_th[j];
   }
-  // F + F(partner) and F - F(partner) once per pair (the partner of Phi_m is Phi_{m+NP/2})
-  for (int x = threadIdx.x; x < nbb * NT * (hP / 4); x += blockDim.x) {
-    const int p4 = (x % (hP / 4)) * 4, rest = x / (hP / 4), kk = rest % NT, bb = rest / NT;
+  // When one warp covers exactly one block here, J comes out of this loop by
+  // a warp reduction; otherwise from a separate pass over the block.
+  const bool warp_J = NT * H4 == 32;
+  // lanes run over k fastest: the transposing stores of a warp hit distinct banks
+  for (int x = threadIdx.x; x < nbb * H4 * NT; x += blockDim.x) {
+    const int kk = x % NT, rest = x / NT, p4 = (rest % H4) * 4, bb = rest / H4;
     C a[4], b[4], s[4], df[4];
     ld4<C>(su + bb * S + kk * NP + p4, a);
     ld4<C>(su + bb * S + kk * NP + p4 + hP, b);
@@ -142,8 +194,19 @@ __device__ __forceinline__ void angular_rb_body(const Problem& p, const Tables<C
     }
     st4<C>(sSD + bb * S + kk * hP + p4, s);
     st4<C>(sSD + bb * S + NT * hP + kk * hP + p4, df);
+    C* ut = uT + bb * NP * UTP;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      ut[(p4 + c) * UTP + kk] = a[c];
+      ut[(p4 + hP + c) * UTP + kk] = b[c];
+    }
+    if (collision && warp_J) {
+      C acc = t.qdir[kk] * ((s[0] + s[1]) + (s[2] + s[3]));
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if ((threadIdx.x & 31) == 0) sc[bb] = acc;
+    }
   }
-  if (collision) {
+  if (collision && !warp_J) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
       C acc = 0;
@@ -152,26 +215,41 @@ __device__ __forceinline__ void angular_rb_body(const Problem& p, const Tables<C
       if (lane == 0) sc[bb] = acc;
     }
   }
-  __syncthreads();
+}
+
+// Compute a prepared tile and write K. Reads sSD, uT, sc and the matrices.
+template <int NT_, int NP_, typename T, typename C>
+__device__ __forceinline__ void angular_rb_compute(const Problem& p, const Tables<C>& t,
+                                                   const C* sSD, const C* uT, const C* sc,
+                                                   const C* sP, const C* sQ, const C* sD,
+                                                   T* __restrict__ K, C sgn, int collision,
+                                                   int nb, long long tile) {
+  constexpr int RB = RBAng<C>::v, CB = 4;
+  const Dims& d = p.d;
+  const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2;
+  const int UTP = ang_utp<C>(NT);
+  const long long b0 = tile * nb;
+  const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int KR = NT / RB, PC = hP / CB;
   const int units = nbb * KR * PC;
   for (int unit = threadIdx.x; unit < units; unit += blockDim.x) {
     const int pc = unit % PC, rest = unit / PC, kr = rest % KR, bb = rest / KR;
     const int p0 = pc * CB, k0 = kr * RB;
-    const C* ub = su + bb * S;
     const C* us = sSD + bb * S;
     const C* ud = us + NT * hP;
+    const C* ut = uT + bb * NP * UTP;
     C ps[RB][CB], qd[RB][CB], da[RB][CB], db[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int c = 0; c < CB; ++c) ps[r][c] = qd[r][c] = da[r][c] = db[r][c] = 0;
+#pragma unroll
     for (int kk = 0; kk < NT; ++kk) {
       C sv[CB], dv[CB], P[RB], Q[RB];
       ld4<C>(us + kk * hP + p0, sv);
       ld4<C>(ud + kk * hP + p0, dv);
-      ldr<C, RB>(sP + kk * NT + k0, P);
-      ldr<C, RB>(sQ + kk * NT + k0, Q);
+      ldv<C, RB>(sP + kk * NT + k0, P);
+      ldv<C, RB>(sQ + kk * NT + k0, Q);
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
 #pragma unroll
@@ -181,52 +259,55 @@ __device__ __forceinline__ void angular_rb_body(const Problem& p, const Tables<C
         }
       }
     }
+#pragma unroll
     for (int mm = 0; mm < NP; ++mm) {
-      C A4[CB], B4[CB];
+      C A4[CB], B4[CB], uv[RB];
       ld4<C>(sD + mm * NP + p0, A4);
       ld4<C>(sD + mm * NP + p0 + hP, B4);
+      ldv<C, RB>(ut + mm * UTP + k0, uv);
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
-        const C uv = ub[(k0 + r) * NP + mm];
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
-          da[r][c] = fmac(A4[c], uv, da[r][c]);
-          db[r][c] = fmac(B4[c], uv, db[r][c]);
+          da[r][c] = fmac(A4[c], uv[r], da[r][c]);
+          db[r][c] = fmac(B4[c], uv[r], db[r][c]);
         }
       }
     }
     const long long blk = b0 + bb;
-    int g, i, j, l;
-    decode_block(d, blk, g, i, j, l);
-    const C ir = t.inv_r[i], ct = t.cot_th[j];
+    const C ir = sc[4 * nb + bb], ct = sc[5 * nb + bb];
     const C J = sc[bb], kap = sc[nb + bb], eta = sc[2 * nb + bb], ks = sc[3 * nb + bb];
+    const C src = eta + ks * J, kks = kap + ks;
+    C s1[CB], s2[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      s1[c] = t.sinP[p0 + c] * ct;
+      s2[c] = t.sinP[p0 + c + hP] * ct;
+    }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const int k = k0 + r;
-      const C aT = -t.sinT[k] * ir;
-      C v1[CB], v2[CB], u1[CB], u2[CB];
-      ld4<C>(ub + k * NP + p0, u1);
-      ld4<C>(ub + k * NP + p0 + hP, u2);
+      const C aT = sgn * -t.sinT[k] * ir;
+      T o1[CB], o2[CB];
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
-        const int m = p0 + c;
-        v1[c] = sgn * aT * (ps[r][c] + qd[r][c] + t.sinP[m] * ct * da[r][c]);
-        v2[c] = sgn * aT * (ps[r][c] - qd[r][c] + t.sinP[m + hP] * ct * db[r][c]);
+        C v1 = aT * (ps[r][c] + qd[r][c] + s1[c] * da[r][c]);
+        C v2 = aT * (ps[r][c] - qd[r][c] + s2[c] * db[r][c]);
         if (collision) {
-          v1[c] += eta - (kap + ks) * u1[c] + ks * J;
-          v2[c] += eta - (kap + ks) * u2[c] + ks * J;
+          v1 += src - kks * ut[(p0 + c) * UTP + k];
+          v2 += src - kks * ut[(p0 + c + hP) * UTP + k];
         }
+        o1[c] = (T)v1;
+        o2[c] = (T)v2;
       }
       T* out = K + blk * S + k * NP + p0;
-      T o1[CB] = {(T)v1[0], (T)v1[1], (T)v1[2], (T)v1[3]};
-      T o2[CB] = {(T)v2[0], (T)v2[1], (T)v2[2], (T)v2[3]};
       st4<T>(out, o1);
       st4<T>(out + hP, o2);
     }
   }
 }
 
-template <typename T, typename C>
+template <int NT_, int NP_, typename T, typename C>
 __device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C>& t,
                                                 const T* __restrict__ U, T* __restrict__ K,
                                                 C sgn, int collision, int nb, long long tile) {
@@ -238,38 +319,46 @@ __device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C
   C* sD = sQ + NT * NT;
   C* su = sD + NP * NP;
   C* sSD = su + nb * S;
-  C* sc = sSD + nb * S;
+  C* uT = sSD + nb * S;
+  C* sc = uT + nb * NP * ang_utp<C>(NT);
   angular_rb_mats<C>(t, d, sP, sQ, sD);
   angular_rb_load<false, T, C>(d, U, nb, tile, su);
   __syncthreads();
-  angular_rb_body<T, C>(p, t, su, sSD, sc, sP, sQ, sD, K, sgn, collision, nb, tile);
+  angular_rb_prep<NT_, NP_, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+  __syncthreads();
+  angular_rb_compute<NT_, NP_, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb, tile);
 }
 
-template <typename T, typename C>
-__global__ void __launch_bounds__(kThreads)
+// Persistent: the next tile is copied into the staging buffer as soon as the
+// current one has been prepared, and lands while the current one is computed.
+template <typename T, typename C, int NT_, int NP_>
+__global__ void __launch_bounds__(kThreads, 2)
 k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
              int collision, int nb, long long ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims& d = p.d;
-  const int NT = d.NT, NP = d.NP, S = NT * NP;
+  const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP;
   C* sP = reinterpret_cast<C*>(smem_raw);
   C* sQ = sP + NT * NT;
   C* sD = sQ + NT * NT;
-  C* sbuf[2] = {sD + NP * NP, sD + NP * NP + nb * S};
-  C* sSD = sbuf[1] + nb * S;
-  C* sc = sSD + nb * S;
+  C* su = sD + NP * NP;
+  C* sSD = su + nb * S;
+  C* uT = sSD + nb * S;
+  C* sc = uT + nb * NP * ang_utp<C>(NT);
   angular_rb_mats<C>(t, d, sP, sQ, sD);
   long long tile = blockIdx.x;
-  if (tile < ntiles) angular_rb_load<true, T, C>(d, U, nb, tile, sbuf[0]);
+  if (tile < ntiles) angular_rb_load<true, T, C>(d, U, nb, tile, su);
   cp_async_commit();
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+  for (; tile < ntiles; tile += gridDim.x) {
+    cp_async_wait0();
+    __syncthreads();   // this tile staged; the previous tile's compute is done
+    angular_rb_prep<NT_, NP_, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+    __syncthreads();   // staging buffer free
     const long long next = tile + gridDim.x;
-    if (next < ntiles) angular_rb_load<true, T, C>(d, U, nb, next, sbuf[(it + 1) & 1]);
+    if (next < ntiles) angular_rb_load<true, T, C>(d, U, nb, next, su);
     cp_async_commit();
-    cp_async_wait1();  // this tile's copies (every group but the newest) have landed
-    __syncthreads();
-    angular_rb_body<T, C>(p, t, sbuf[it & 1], sSD, sc, sP, sQ, sD, K, sgn, collision, nb, tile);
-    __syncthreads();   // buffer and scratch free before they are refilled
+    angular_rb_compute<NT_, NP_, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb,
+                                       tile);
   }
   cp_async_wait0();
 }
@@ -317,13 +406,16 @@ __device__ __forceinline__ void plane_rb_load(const Dims& d, const T* U, int c, 
   }
 }
 
-template <typename T, typename C>
+// N_ > 0: square grid (N_ nodes on every angular axis) with c = N_/2, i.e. a
+// tile holds whole Phi rows; 0: sizes and c from the grid at run time.
+template <int N_, typename T, typename C>
 __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>& t, const C* su,
                                               C* sSm, const C* sP, const C* sQ, const C* sD,
-                                              T* __restrict__ K, C sgn, int c, long long tile) {
+                                              T* __restrict__ K, C sgn, int c_rt, long long tile) {
   constexpr int RB = kRBPlane, CB = 4;
   const Dims& d = p.d;
-  const int Nt = d.Nt, Np = d.Np, hP = d.NP / 2, hp = Np / 2, W = 2 * c;
+  const int Nt = ctsz<N_>(d.Nt), Np = ctsz<N_>(d.Np), hP = ctsz<N_>(d.NP) / 2, hp = Np / 2;
+  const int c = N_ ? N_ / 2 : c_rt, W = 2 * c;
   C* sDf = sSm + Nt * hp * W;
   int k, i, g, m0;
   plane_tile_coords(d, c, tile, k, i, g, m0);
@@ -344,7 +436,7 @@ __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>&
     st4<C>(sDf + jl * W + w4, df);
   }
   __syncthreads();
-  const C sTk = t.sinT[k], ir = t.inv_r[i];
+  const C sTk = t.sinT[k] * t.inv_r[i];
   const int JR = Nt / RB, WQ = W / CB;
   const int units = JR * hp * WQ;
   for (int unit = threadIdx.x; unit < units; unit += blockDim.x) {
@@ -356,12 +448,13 @@ __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>&
     for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) ps[r][cc] = qd[r][cc] = da[r][cc] = db[r][cc] = 0;
+#pragma unroll
     for (int jj = 0; jj < Nt; ++jj) {
       C sv[CB], dv[CB], P[RB], Q[RB];
       ld4<C>(sSm + (jj * hp + l) * W + w0, sv);
       ld4<C>(sDf + (jj * hp + l) * W + w0, dv);
-      ldr<C, RB>(sP + jj * Nt + j0, P);
-      ldr<C, RB>(sQ + jj * Nt + j0, Q);
+      ldv<C, RB>(sP + jj * Nt + j0, P);
+      ldv<C, RB>(sQ + jj * Nt + j0, Q);
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
 #pragma unroll
@@ -371,6 +464,7 @@ __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>&
         }
       }
     }
+#pragma unroll
     for (int ll = 0; ll < Np; ++ll) {
       const C Dl = sD[ll * Np + l], Dh = sD[ll * Np + lh];
 #pragma unroll
@@ -386,6 +480,14 @@ __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>&
       }
     }
     const int mA = plane_m(w0, c, m0, hP), mB = plane_m(w0h, c, m0, hP);
+    C cA[CB], sA[CB], cB[CB], sB[CB];
+#pragma unroll
+    for (int cc = 0; cc < CB; ++cc) {
+      cA[cc] = sgn * sTk * t.cosP[mA + cc];
+      sA[cc] = sgn * sTk * t.sinP[mA + cc];
+      cB[cc] = sgn * sTk * t.cosP[mB + cc];
+      sB[cc] = sgn * sTk * t.sinP[mB + cc];
+    }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const int j = j0 + r;
@@ -397,10 +499,8 @@ __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>&
       ld4<T>(pb, kb);
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
-        const C athA = sTk * t.cosP[mA + cc] * ir, aphA = sTk * t.sinP[mA + cc] * ir * isn;
-        const C athB = sTk * t.cosP[mB + cc] * ir, aphB = sTk * t.sinP[mB + cc] * ir * isn;
-        ka[cc] = (T)((C)ka[cc] + sgn * (athA * (ps[r][cc] + qd[r][cc]) + aphA * da[r][cc]));
-        kb[cc] = (T)((C)kb[cc] + sgn * (athB * (ps[r][cc] - qd[r][cc]) + aphB * db[r][cc]));
+        ka[cc] = (T)((C)ka[cc] + cA[cc] * (ps[r][cc] + qd[r][cc]) + sA[cc] * isn * da[r][cc]);
+        kb[cc] = (T)((C)kb[cc] + cB[cc] * (ps[r][cc] - qd[r][cc]) + sB[cc] * isn * db[r][cc]);
       }
       st4<T>(pa, ka);
       st4<T>(pb, kb);
@@ -408,7 +508,7 @@ __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>&
   }
 }
 
-template <typename T, typename C>
+template <int N_, typename T, typename C>
 __device__ __forceinline__ void plane_tile_rb(const Problem& p, const Tables<C>& t,
                                               const T* __restrict__ U, T* __restrict__ K, C sgn,
                                               int c, long long tile) {
@@ -423,42 +523,51 @@ __device__ __forceinline__ void plane_tile_rb(const Problem& p, const Tables<C>&
   plane_rb_mats<C>(t, d, sP, sQ, sD);
   plane_rb_load<false, T, C>(d, U, c, tile, su);
   __syncthreads();
-  plane_rb_body<T, C>(p, t, su, sSm, sP, sQ, sD, K, sgn, c, tile);
+  plane_rb_body<N_, T, C>(p, t, su, sSm, sP, sQ, sD, K, sgn, c, tile);
 }
 
-template <typename T, typename C>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, typename C, int N_>
+__global__ void __launch_bounds__(kThreads, 2)
 k_plane_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn, int c,
            long long ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims& d = p.d;
-  const int Nt = d.Nt, Np = d.Np, W = 2 * c, TS = Nt * Np * W;
+  const int Nt = ctsz<N_>(d.Nt), Np = ctsz<N_>(d.Np), W = 2 * c, TS = Nt * Np * W;
   C* sP = reinterpret_cast<C*>(smem_raw);
   C* sQ = sP + Nt * Nt;
   C* sD = sQ + Nt * Nt;
-  C* sbuf[2] = {sD + Np * Np, sD + Np * Np + TS};
-  C* sSm = sbuf[1] + TS;
+  C* buf0 = sD + Np * Np;
+  C* sSm = buf0 + 2 * TS;
   plane_rb_mats<C>(t, d, sP, sQ, sD);
   long long tile = blockIdx.x;
-  if (tile < ntiles) plane_rb_load<true, T, C>(d, U, c, tile, sbuf[0]);
+  if (tile < ntiles) plane_rb_load<true, T, C>(d, U, c, tile, buf0);
   cp_async_commit();
   for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
     const long long next = tile + gridDim.x;
-    if (next < ntiles) plane_rb_load<true, T, C>(d, U, c, next, sbuf[(it + 1) & 1]);
+    C* cur = buf0 + (it & 1) * TS;
+    C* nxt = buf0 + ((it + 1) & 1) * TS;
+    if (next < ntiles) plane_rb_load<true, T, C>(d, U, c, next, nxt);
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
-    plane_rb_body<T, C>(p, t, sbuf[it & 1], sSm, sP, sQ, sD, K, sgn, c, tile);
+    plane_rb_body<N_, T, C>(p, t, cur, sSm, sP, sQ, sD, K, sgn, c, tile);
     __syncthreads();
   }
   cp_async_wait0();
 }
 
 // ============================================================================
-// Radial pass. Thread: RB output pairs (i, N-i) x 4 columns; the middle node
-// (odd Nr) by separate units; rows 0..n64-1 and N-n64+1..N (n64 = p.n_fp64_rows)
-// in double from the full matrix. Then the Tau rows and the stage update.
-// Shared layout: [EpT | OpT | DrMc | DrMr | (u, K) buffer(s) 2 Nr W | E, O 2 hh W]
+// Radial pass. Thread: RB output pairs (i, N-i) x 4 columns of one tile of W
+// (Theta, Phi) columns at fixed (g, theta, phi). The even/odd parts of U are
+// formed straight from global memory into shared memory; each thread then
+// contracts them, adds the result to its rows of K (read from global memory),
+// publishes rows 0 and N (the Tau rows read them), and after one barrier
+// applies the Tau rows and the RK4 stage update to its own rows. The middle
+// node (odd Nr) is handled by the threads of the rows nearest to it; rows
+// 0..n64-1 and N-n64+1..N (n64 = p.n_fp64_rows) are accumulated in double from
+// the full matrix.
+// Shared layout: [EpT | OpT | DrMc | DrMr | E hh*W | O hh*W | middle W |
+//                 K rows 0, N 2W | double rows 4W]
 __device__ __forceinline__ void radial_tile_coords(const Dims& d, int W, long long tile,
                                                    long long& base, int& c0, int& Wc) {
   const int S = d.NT * d.NP;
@@ -489,68 +598,120 @@ __device__ __forceinline__ void radial_rb_mats(const Tables<C>& t, int Nr, C* sE
   }
 }
 
-template <bool ASYNC, typename T, typename C>
-__device__ __forceinline__ void radial_rb_load(const Dims& d, const T* U, const T* Kin, int W,
-                                               long long tile, C* su, C* sk) {
-  long long base;
-  int c0, Wc;
-  radial_tile_coords(d, W, tile, base, c0, Wc);
-  const int W4 = Wc / 4;
-  for (int x = threadIdx.x; x < d.Nr * W4; x += blockDim.x) {
-    const int ii = x / W4, w = (x - ii * W4) * 4;
-    const long long gi = base + (long long)ii * d.S_i + w;
-    copy4<ASYNC, T, C>(su + ii * W + w, U + gi);
-    copy4<ASYNC, T, C>(sk + ii * W + w, Kin + gi);
+// Stage update of one row segment (4 columns at gi) with the finished K values kv.
+template <typename T, typename C>
+__device__ __forceinline__ void radial_store(int mode, long long gi, const C (&kv)[4], T* F,
+                                             T* Acc, T* Uout, T* out, C dt) {
+  T o[4];
+  if (mode == RAD_RHS) {
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) o[cc] = (T)kv[cc];
+    st4<T>(out + gi, o);
+  } else if (mode == RAD_STAGE3) {
+    T f[4], ac[4];
+    ld4<T>(F + gi, f);
+    ld4<T>(Acc + gi, ac);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) o[cc] = (T)((C)f[cc] + dt / (C)6 * ((C)ac[cc] + kv[cc]));
+    st4<T>(F + gi, o);
+  } else {
+    T f[4], ac[4];
+    ld4<T>(F + gi, f);
+    const C cu = mode == RAD_STAGE2 ? dt : (C)0.5 * dt;
+    if (mode != RAD_STAGE0) ld4<T>(Acc + gi, ac);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      o[cc] = (T)((C)f[cc] + cu * kv[cc]);
+      ac[cc] = mode == RAD_STAGE0 ? (T)kv[cc] : (T)((C)ac[cc] + (C)2 * kv[cc]);
+    }
+    st4<T>(Acc + gi, ac);
+    st4<T>(Uout + gi, o);
   }
 }
 
-template <typename T, typename C>
+template <int Nr_, typename T, typename C>
 __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>& t,
-                                               const double* __restrict__ Dr64, const C* su,
-                                               C* sk, C* sEv, const C* sE, const C* sO,
-                                               const C* sMc, const C* sMr, C sgn, int tau,
-                                               int mode, T* F, T* Acc, T* Uout, T* out, C dt,
-                                               int W, long long tile) {
-  constexpr int RB = kRBRad, CB = 4;
+                                               const double* __restrict__ Dr64,
+                                               const T* __restrict__ U,
+                                               const T* __restrict__ Kin, C* sEv, const C* sE,
+                                               const C* sO, const C* sMc, const C* sMr, C sgn,
+                                               int tau, int mode, T* F, T* Acc, T* Uout, T* out,
+                                               C dt, int W, long long tile) {
+  constexpr int RB = RBRad<C>::v, CB = 4;
   const Dims& d = p.d;
-  const int Nr = d.Nr, N = Nr - 1, hh = Nr / 2, NP = d.NP;
+  const int Nr = ctsz<Nr_>(d.Nr), N = Nr - 1, hh = Nr / 2, NP = d.NP;
+  const bool odd = Nr & 1;
+  const long long Si = d.S_i;
   C* sOd = sEv + hh * W;
+  C* sMid = sOd + hh * W;
+  C* sBnd = sMid + W;
+  C* sR = sBnd + 2 * W;
   long long base;
   int c0, Wc;
   radial_tile_coords(d, W, tile, base, c0, Wc);
   const int W4 = Wc / 4;
+  const int n64 = p.n_fp64_rows;
+  const T* Ub = U + base;
   for (int x = threadIdx.x; x < hh * W4; x += blockDim.x) {   // even/odd parts once per pair
     const int ii = x / W4, w = (x - ii * W4) * 4;
-    C a[4], b[4], e[4], o[4];
-    ld4<C>(su + ii * W + w, a);
-    ld4<C>(su + (N - ii) * W + w, b);
+    T a[4], b[4];
+    ld4<T>(Ub + ii * Si + w, a);
+    ld4<T>(Ub + (N - ii) * Si + w, b);
+    C e[4], o[4];
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
-      e[cc] = a[cc] + b[cc];
-      o[cc] = a[cc] - b[cc];
+      e[cc] = (C)a[cc] + (C)b[cc];
+      o[cc] = (C)a[cc] - (C)b[cc];
     }
     st4<C>(sEv + ii * W + w, e);
     st4<C>(sOd + ii * W + w, o);
   }
+  if (odd) {
+    for (int x = threadIdx.x; x < W4; x += blockDim.x) {
+      T a[4];
+      ld4<T>(Ub + (N / 2) * Si + 4 * x, a);
+      C m[4] = {(C)a[0], (C)a[1], (C)a[2], (C)a[3]};
+      st4<C>(sMid + 4 * x, m);
+    }
+  }
+  for (int v = threadIdx.x; v < 2 * n64 * W4; v += blockDim.x) {  // rows nearest the ends
+    const int w0 = (v % W4) * 4, rr = v / W4;
+    const int i = rr < n64 ? rr : N - (rr - n64);
+    double a[4] = {0, 0, 0, 0};
+    for (int ii = 0; ii < Nr; ++ii) {
+      const double dv = Dr64[i * Nr + ii];
+      T u[4];
+      ld4<T>(Ub + ii * Si + w0, u);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) a[cc] = fma(dv, (double)u[cc], a[cc]);
+    }
+    C r4[4] = {(C)a[0], (C)a[1], (C)a[2], (C)a[3]};
+    st4<C>(sR + rr * W + w0, r4);
+  }
   __syncthreads();
-  const int n64 = p.n_fp64_rows;
-  const int IR = hh / RB;
-  const int units = IR * W4 + ((Nr & 1) ? W4 : 0) + 2 * n64 * W4;
-  for (int unit = threadIdx.x; unit < units; unit += blockDim.x) {
-    if (unit < IR * W4) {
-      const int wq = unit % W4, ir = unit / W4;
-      const int w0 = wq * CB, i0 = ir * RB;
+  const int IR = hh / RB, units = IR * W4;
+  const int rounds = (units + (int)blockDim.x - 1) / (int)blockDim.x;
+  for (int rd = 0; rd < rounds; ++rd) {   // uniform trip count: every thread meets the barrier
+    const int unit = rd * (int)blockDim.x + (int)threadIdx.x;
+    const bool act = unit < units;
+    const int wq = act ? unit % W4 : 0, ir = act ? unit / W4 : 0;
+    const int w0 = wq * CB, i0 = ir * RB;
+    const bool mid = odd && ir == IR - 1;
+    C klo[RB][CB], khi[RB][CB], kmid[CB];
+    C cT = 0, ckf = 0;
+    if (act) {
       C ae[RB][CB], ao[RB][CB];
 #pragma unroll
       for (int r = 0; r < RB; ++r)
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) ae[r][cc] = ao[r][cc] = 0;
+#pragma unroll 8
       for (int ii = 0; ii < hh; ++ii) {
         C ev[CB], ov[CB], E[RB], O[RB];
         ld4<C>(sEv + ii * W + w0, ev);
         ld4<C>(sOd + ii * W + w0, ov);
-        ldr<C, RB>(sE + ii * hh + i0, E);
-        ldr<C, RB>(sO + ii * hh + i0, O);
+        ldv<C, RB>(sE + ii * hh + i0, E);
+        ldv<C, RB>(sO + ii * hh + i0, O);
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) {
 #pragma unroll
@@ -560,97 +721,90 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
           }
         }
       }
-      if (Nr & 1) {
+      cT = t.cosT[(c0 + w0) / NP];   // 4 | w0, 8 | NP: the 4 columns share one Theta row
+      ckf = sgn * cT;
+      if (odd) {
         C um[CB];
-        ld4<C>(su + (N / 2) * W + w0, um);
+        ld4<C>(sMid + w0, um);
 #pragma unroll
         for (int r = 0; r < RB; ++r)
 #pragma unroll
           for (int cc = 0; cc < CB; ++cc) ae[r][cc] = fmac((C)2 * sMc[i0 + r], um[cc], ae[r][cc]);
       }
+      if (mid) {
+        C am[CB] = {0, 0, 0, 0};
+#pragma unroll
+        for (int ii = 0; ii < hh; ++ii) {
+          C ov[CB];
+          ld4<C>(sOd + ii * W + w0, ov);
+          const C mr = sMr[ii];
+#pragma unroll
+          for (int cc = 0; cc < CB; ++cc) am[cc] = fmac(mr, ov[cc], am[cc]);
+        }
+        T km[CB];
+        ld4<T>(Kin + base + (N / 2) * Si + w0, km);
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) kmid[cc] = (C)km[cc] + ckf * am[cc];
+      }
+      const C ck = ckf * (C)0.5;
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         const int i = i0 + r;
-        if (i < n64) continue;  // those rows are done in double below
+        T k1[CB], k2[CB];
+        ld4<T>(Kin + base + i * Si + w0, k1);
+        ld4<T>(Kin + base + (N - i) * Si + w0, k2);
+        if (i < n64) {
 #pragma unroll
-        for (int cc = 0; cc < CB; ++cc) {
-          const C ck = sgn * t.cosT[(c0 + w0 + cc) / NP] * (C)0.5;
-          sk[i * W + w0 + cc] += ck * (ao[r][cc] + ae[r][cc]);
-          sk[(N - i) * W + w0 + cc] += ck * (ao[r][cc] - ae[r][cc]);
+          for (int cc = 0; cc < CB; ++cc) {
+            klo[r][cc] = (C)k1[cc] + ckf * sR[i * W + w0 + cc];
+            khi[r][cc] = (C)k2[cc] + ckf * sR[(n64 + i) * W + w0 + cc];
+          }
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < CB; ++cc) {
+            klo[r][cc] = (C)k1[cc] + ck * (ao[r][cc] + ae[r][cc]);
+            khi[r][cc] = (C)k2[cc] + ck * (ao[r][cc] - ae[r][cc]);
+          }
         }
       }
-    } else if (unit < IR * W4 + ((Nr & 1) ? W4 : 0)) {
-      const int w0 = (unit - IR * W4) * CB;
-      C am[CB] = {0, 0, 0, 0};
-      for (int ii = 0; ii < hh; ++ii) {
-        C ov[CB];
-        ld4<C>(sOd + ii * W + w0, ov);
-        const C mr = sMr[ii];
-#pragma unroll
-        for (int cc = 0; cc < CB; ++cc) am[cc] = fmac(mr, ov[cc], am[cc]);
-      }
-#pragma unroll
-      for (int cc = 0; cc < CB; ++cc)
-        sk[(N / 2) * W + w0 + cc] += sgn * t.cosT[(c0 + w0 + cc) / NP] * am[cc];
-    } else {
-      // rows nearest the ends, accumulated in double from the full matrix
-      const int v = unit - IR * W4 - ((Nr & 1) ? W4 : 0);
-      const int w0 = (v % W4) * CB, rr = v / W4;
-      const int i = rr < n64 ? rr : N - (rr - n64);
-      double a[CB] = {0, 0, 0, 0};
-      for (int ii = 0; ii < Nr; ++ii) {
-        const double dv = Dr64[i * Nr + ii];
-#pragma unroll
-        for (int cc = 0; cc < CB; ++cc) a[cc] = fma(dv, (double)su[ii * W + w0 + cc], a[cc]);
-      }
-#pragma unroll
-      for (int cc = 0; cc < CB; ++cc)
-        sk[i * W + w0 + cc] += sgn * t.cosT[(c0 + w0 + cc) / NP] * (C)a[cc];
-    }
-  }
-  __syncthreads();
-  for (int x = threadIdx.x; x < Nr * W4; x += blockDim.x) {
-    const int i = x / W4, w = (x - i * W4) * 4;
-    const long long gi = base + (long long)i * d.S_i + w;
-    C kv[4];
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      kv[cc] = sk[i * W + w + cc];
-      if (tau) {
-        const int k = (c0 + w + cc) / NP;
-        const int b = t.cosT[k] > (C)0 ? 0 : Nr - 1;
-        kv[cc] -= sk[b * W + w + cc] * t.tsign[b] * t.tsign[i];
+      if (i0 == 0) {   // rows 0 and N of these columns: the Tau rows read them
+        st4<C>(sBnd + w0, klo[0]);
+        st4<C>(sBnd + W + w0, khi[0]);
       }
     }
-    T o[4];
-    if (mode == RAD_RHS) {
+    __syncthreads();
+    if (act) {
+      C kb[CB];
+      const int b = cT > (C)0 ? 0 : N;   // inflow node: cos(Theta) > 0 at R1
+      if (tau) ld4<C>(sBnd + (b ? W : 0) + w0, kb);
+      const C tb = t.tsign[b];
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) o[cc] = (T)kv[cc];
-      st4<T>(out + gi, o);
-    } else if (mode == RAD_STAGE3) {
-      T f[4], ac[4];
-      ld4<T>(F + gi, f);
-      ld4<T>(Acc + gi, ac);
+      for (int r = 0; r < RB; ++r) {
+        const int i = i0 + r;
+        if (tau) {
+          const C s1 = tb * t.tsign[i], s2 = tb * t.tsign[N - i];
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) o[cc] = (T)((C)f[cc] + dt / (C)6 * ((C)ac[cc] + kv[cc]));
-      st4<T>(F + gi, o);
-    } else {
-      T f[4], ac[4];
-      ld4<T>(F + gi, f);
-      const C cu = mode == RAD_STAGE2 ? dt : (C)0.5 * dt;
-      if (mode != RAD_STAGE0) ld4<T>(Acc + gi, ac);
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        o[cc] = (T)((C)f[cc] + cu * kv[cc]);
-        ac[cc] = mode == RAD_STAGE0 ? (T)kv[cc] : (T)((C)ac[cc] + (C)2 * kv[cc]);
+          for (int cc = 0; cc < CB; ++cc) {
+            klo[r][cc] -= kb[cc] * s1;
+            khi[r][cc] -= kb[cc] * s2;
+          }
+        }
+        radial_store<T, C>(mode, base + i * Si + w0, klo[r], F, Acc, Uout, out, dt);
+        radial_store<T, C>(mode, base + (N - i) * Si + w0, khi[r], F, Acc, Uout, out, dt);
       }
-      st4<T>(Acc + gi, ac);
-      st4<T>(Uout + gi, o);
+      if (mid) {
+        if (tau) {
+          const C s = tb * t.tsign[N / 2];
+#pragma unroll
+          for (int cc = 0; cc < CB; ++cc) kmid[cc] -= kb[cc] * s;
+        }
+        radial_store<T, C>(mode, base + (N / 2) * Si + w0, kmid, F, Acc, Uout, out, dt);
+      }
     }
   }
 }
 
-template <typename T, typename C>
+template <int Nr_, typename T, typename C>
 __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>& t,
                                                const double* __restrict__ Dr64, const T* U,
                                                const T* Kin, C sgn, int tau, int mode, T* F,
@@ -663,47 +817,28 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
   C* sO = sE + hh4;
   C* sMc = sO + hh4;
   C* sMr = sMc + h4;
-  C* su = sMr + h4;
-  C* sk = su + Nr * W;
-  C* sEv = sk + Nr * W;
+  C* sEv = sMr + h4;
   radial_rb_mats<C>(t, Nr, sE, sO, sMc, sMr);
-  radial_rb_load<false, T, C>(p.d, U, Kin, W, tile, su, sk);
-  __syncthreads();
-  radial_rb_body<T, C>(p, t, Dr64, su, sk, sEv, sE, sO, sMc, sMr, sgn, tau, mode, F, Acc, Uout,
-                       out, dt, W, tile);
+  radial_rb_body<Nr_, T, C>(p, t, Dr64, U, Kin, sEv, sE, sO, sMc, sMr, sgn, tau, mode, F, Acc,
+                            Uout, out, dt, W, tile);
 }
 
-template <typename T, typename C>
-__global__ void __launch_bounds__(kThreads)
-k_radial_pp(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U, const T* Kin,
-            C sgn, int tau, int mode, T* F, T* Acc, T* Uout, T* out, C dt, int W,
-            long long ntiles) {
+// One tile per CTA with the radial line length fixed at compile time.
+template <typename T, typename C, int Nr_>
+__global__ void __launch_bounds__(kThreads, 2)
+k_radial_eo(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U, const T* Kin,
+            C sgn, int tau, int mode, T* F, T* Acc, T* Uout, T* out, C dt, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int Nr = p.d.Nr, hh = Nr / 2;
+  const int Nr = ctsz<Nr_>(p.d.Nr), hh = Nr / 2;
   const int hh4 = (hh * hh + 3) & ~3, h4 = (hh + 3) & ~3;
   C* sE = reinterpret_cast<C*>(smem_raw);
   C* sO = sE + hh4;
   C* sMc = sO + hh4;
   C* sMr = sMc + h4;
-  C* sbuf[2] = {sMr + h4, sMr + h4 + 2 * Nr * W};   // each: u [Nr][W] then K [Nr][W]
-  C* sEv = sbuf[1] + 2 * Nr * W;
+  C* sEv = sMr + h4;
   radial_rb_mats<C>(t, Nr, sE, sO, sMc, sMr);
-  long long tile = blockIdx.x;
-  if (tile < ntiles) radial_rb_load<true, T, C>(p.d, U, Kin, W, tile, sbuf[0], sbuf[0] + Nr * W);
-  cp_async_commit();
-  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
-    const long long next = tile + gridDim.x;
-    C* nb_ = sbuf[(it + 1) & 1];
-    if (next < ntiles) radial_rb_load<true, T, C>(p.d, U, Kin, W, next, nb_, nb_ + Nr * W);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
-    C* cb = sbuf[it & 1];
-    radial_rb_body<T, C>(p, t, Dr64, cb, cb + Nr * W, sEv, sE, sO, sMc, sMr, sgn, tau, mode, F,
-                         Acc, Uout, out, dt, W, tile);
-    __syncthreads();
-  }
-  cp_async_wait0();
+  radial_rb_body<Nr_, T, C>(p, t, Dr64, U, Kin, sEv, sE, sO, sMc, sMr, sgn, tau, mode, F, Acc,
+                            Uout, out, dt, W, blockIdx.x);
 }
 
 // ----------------------------------------------------------------------------
@@ -714,14 +849,14 @@ template <typename T, typename C>
 __device__ __forceinline__ void angular_tile_any(const Problem& p, const Tables<C>& t,
                                                  const T* U, T* K, C sgn, int collision, int nb,
                                                  long long tile) {
-  if (p.tp.rb & 1) angular_tile_rb<T, C>(p, t, U, K, sgn, collision, nb, tile);
+  if (p.tp.rb & 1) angular_tile_rb<0, 0, T, C>(p, t, U, K, sgn, collision, nb, tile);
   else angular_tile<T, C>(p, t, U, K, sgn, collision, nb, tile);
 }
 
 template <typename T, typename C>
 __device__ __forceinline__ void plane_tile_any(const Problem& p, const Tables<C>& t, const T* U,
                                                T* K, C sgn, int c, long long tile) {
-  if (p.tp.rb & 2) plane_tile_rb<T, C>(p, t, U, K, sgn, c, tile);
+  if (p.tp.rb & 2) plane_tile_rb<0, T, C>(p, t, U, K, sgn, c, tile);
   else plane_tile<T, C>(p, t, U, K, sgn, c, tile);
 }
 
@@ -731,7 +866,7 @@ __device__ __forceinline__ void radial_tile_any(const Problem& p, const Tables<C
                                                 C sgn, int tau, int mode, T* F, T* Acc, T* Uout,
                                                 T* out, C dt, int W, long long tile) {
   if (p.tp.rb & 4)
-    radial_tile_rb<T, C>(p, t, Dr64, U, Kin, sgn, tau, mode, F, Acc, Uout, out, dt, W, tile);
+    radial_tile_rb<0, T, C>(p, t, Dr64, U, Kin, sgn, tau, mode, F, Acc, Uout, out, dt, W, tile);
   else
     radial_tile<T, C>(p, t, Dr64, U, Kin, sgn, tau, mode, F, Acc, Uout, out, dt, W, tile);
 }

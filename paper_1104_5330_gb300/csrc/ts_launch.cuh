@@ -26,11 +26,13 @@ static cudaError_t allow_smem(K kernel) {
 static inline unsigned grid1(long long n) { return (unsigned)n; }
 
 // Shared memory of one tile of each forward pass (rb: register-blocked form).
-// The register-blocked forms also hold the even/odd sums and differences.
+// The register-blocked forms also hold the even/odd sums and differences, and
+// the angular one a transposed copy of its blocks.
 template <typename C>
 size_t smem_angular(const Dims& d, int nb, bool rb) {
   const size_t S = (size_t)d.NT * d.NP, mats = 2 * d.NT * d.NT + d.NP * d.NP;
-  return (mats + (rb ? 2 : 1) * nb * S + (rb ? 4 * nb : nb)) * sizeof(C);
+  if (!rb) return (mats + nb * S + nb) * sizeof(C);
+  return (mats + nb * (2 * S + (size_t)d.NP * ang_utp<C>(d.NT)) + 6 * nb) * sizeof(C);
 }
 template <typename C>
 size_t smem_plane(const Dims& d, int c, bool rb) {
@@ -39,23 +41,20 @@ size_t smem_plane(const Dims& d, int c, bool rb) {
 template <typename C>
 size_t smem_radial(const Dims& d, int W, bool rb) {
   if (!rb) return (size_t)(d.Nr * d.Nr + 2 * d.Nr * W) * sizeof(C);
-  const int hh = d.Nr / 2;
-  return (size_t)(2 * ((hh * hh + 3) & ~3) + 2 * ((hh + 3) & ~3) + 2 * d.Nr * W + 2 * hh * W) *
-         sizeof(C);
+  const int hh = d.Nr / 2;   // E, O, middle row, K rows 0 and N, up to 4 double-precision rows
+  return (size_t)(2 * ((hh * hh + 3) & ~3) + 2 * ((hh + 3) & ~3) + (2 * hh + 7) * W) * sizeof(C);
 }
 
-// Persistent double-buffered forms: two staging buffers per CTA.
+// Persistent forms. The angular one stages the next tile into its single
+// staging buffer once the current tile is prepared; the plane one keeps two
+// staging buffers.
 template <typename C>
 size_t smem_angular_pp(const Dims& d, int nb) {
-  return smem_angular<C>(d, nb, true) + (size_t)nb * d.NT * d.NP * sizeof(C);
+  return smem_angular<C>(d, nb, true);
 }
 template <typename C>
 size_t smem_plane_pp(const Dims& d, int c) {
   return smem_plane<C>(d, c, true) + (size_t)d.Nt * d.Np * 2 * c * sizeof(C);
-}
-template <typename C>
-size_t smem_radial_pp(const Dims& d, int W) {
-  return smem_radial<C>(d, W, true) + (size_t)2 * d.Nr * W * sizeof(C);
 }
 
 // CTAs of a persistent kernel: as many as fit on the GPU at this shared-memory size.
@@ -75,21 +74,23 @@ static int persistent_ctas(K kernel, size_t smem, long long ntiles) {
   return (int)std::max<long long>(1, std::min<long long>(ntiles, (long long)occ * nsm));
 }
 
+// Two CTAs of the persistent kernels share an SM when each stays below this.
+constexpr size_t kSmemHalf = 112 * 1024;
+
 // Built-in tile shapes: fill 256 threads with work while staying in the budget
-// (with room for the second staging buffer of the persistent forms).
+// (two CTAs per SM for the persistent register-blocked forms).
 template <typename T, typename C>
 static int angular_nb(const Dims& d, int ntiles, bool rb = false) {
   const int S = d.NT * d.NP;
-  int nb;
   if (rb && ntiles == 1) {
-    const int per = (d.NT / (sizeof(C) == 4 ? 4 : 2)) * (d.NP / 8);  // threads' units per block
-    nb = std::max(1, (512 + per - 1) / per);
-  } else {
-    nb = std::max(1, 2048 / S);
+    const int per = (d.NT / rb_ang((int)sizeof(C))) * (d.NP / 8);  // threads' units per block
+    int nb = std::max(1, (kThreads + per - 1) / per);
+    while (nb > 1 && smem_angular<C>(d, nb, true) > kSmemHalf) --nb;
+    return nb;
   }
+  int nb = std::max(1, 2048 / S);
   const size_t mats = (size_t)(2 * d.NT * d.NT + d.NP * d.NP) * sizeof(C);
-  const int per_block = (rb && ntiles == 1) ? 3 : ntiles;   // tiles of S values per block
-  while (nb > 1 && mats + (size_t)nb * (per_block * S + 4) * sizeof(C) > kSmemBudget) nb /= 2;
+  while (nb > 1 && mats + (size_t)nb * (ntiles * S + 4) * sizeof(C) > kSmemBudget) nb /= 2;
   return nb;
 }
 
@@ -110,10 +111,10 @@ template <typename T, typename C>
 static int radial_W(const Dims& d, int ntiles, bool rb = false) {
   const int S = d.NT * d.NP;
   int W;
-  if (rb) {
+  if (rb) {   // about one unit (RB row pairs x 4 columns) per thread
     const int hh = d.Nr / 2;
-    W = std::max(4, std::min(S, (4 * 256 * kRBRad / std::max(1, hh)) & ~3));
-    while (W > 4 && smem_radial_pp<C>(d, W) > kSmemBudget) W = (W / 2) & ~3;
+    W = std::max(4, std::min(S, (4 * kThreads * rb_rad((int)sizeof(C)) / std::max(1, hh)) & ~3));
+    while (W > 4 && smem_radial<C>(d, W, true) > kSmemHalf) W = (W / 2) & ~3;
     return std::max(4, W);
   }
   W = std::min(S, sizeof(C) == 8 ? 64 : 128);
@@ -121,52 +122,86 @@ static int radial_W(const Dims& d, int ntiles, bool rb = false) {
   return W;
 }
 
+// Launches with the line lengths fixed at compile time for the common grids
+// (16, 24, 32 angular nodes -- also 8, and whole Phi rows per tile, in the
+// plane pass; 17, 33, 65 radial nodes), and the run-time form (template
+// argument 0) for every other size.
+
+template <typename T, typename C, int A, int B>
+static cudaError_t angular_pp(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
+                              int collision, int nb, long long ntiles, cudaStream_t s) {
+  static const cudaError_t e = allow_smem(k_angular_pp<T, C, A, B>);  // once per kernel
+  if (e != cudaSuccess) return e;
+  const size_t smem = smem_angular_pp<C>(p.d, nb);
+  const int ctas = persistent_ctas(k_angular_pp<T, C, A, B>, smem, ntiles);
+  k_angular_pp<T, C, A, B><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, collision, nb, ntiles);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C, int N>
+static cudaError_t plane_pp(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn, int c,
+                            long long ntiles, cudaStream_t s) {
+  static const cudaError_t e = allow_smem(k_plane_pp<T, C, N>);  // once per kernel
+  if (e != cudaSuccess) return e;
+  const size_t smem = smem_plane_pp<C>(p.d, c);
+  const int ctas = persistent_ctas(k_plane_pp<T, C, N>, smem, ntiles);
+  k_plane_pp<T, C, N><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, c, ntiles);
+  return cudaGetLastError();
+}
+
+template <typename T, typename C, int R>
+static cudaError_t radial_eo(const Problem& p, const Tables<C>& t, const double* Dr64,
+                             const T* U, const T* K, C sgn, int tau, int mode, T* F, T* Acc,
+                             T* Uout, T* out, C dt, int W, long long ntiles, cudaStream_t s) {
+  static const cudaError_t e = allow_smem(k_radial_eo<T, C, R>);  // once per kernel
+  if (e != cudaSuccess) return e;
+  const size_t smem = smem_radial<C>(p.d, W, true);
+  k_radial_eo<T, C, R><<<grid1(ntiles), kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, tau, mode, F,
+                                                             Acc, Uout, out, dt, W);
+  return cudaGetLastError();
+}
+
 template <typename T, typename C>
 cudaError_t Launch<T, C>::angular(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                                   bool collision, cudaStream_t s) {
-  static bool init = false;
-  if (!init) {
-    cudaError_t ea = allow_smem(k_angular<T, C>);
-    if (ea == cudaSuccess) ea = allow_smem(k_angular_pp<T, C>);
-    if (ea != cudaSuccess) return ea;
-    init = true;
-  }
   const Dims& d = p.d;
   const bool rb = p.tp.rb & 1;
   const int nb = p.tp.nb > 0 ? p.tp.nb : angular_nb<T, C>(d, 1, rb);
   const long long ntiles = (d.nblk + nb - 1) / nb;
+  const int col = collision ? 1 : 0;
   if (rb) {
-    const size_t smem = smem_angular_pp<C>(d, nb);
-    const int ctas = persistent_ctas(k_angular_pp<T, C>, smem, ntiles);
-    k_angular_pp<T, C><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, collision ? 1 : 0, nb,
-                                                    ntiles);
-    return cudaGetLastError();
+    switch (ang_spec(d)) {
+      case 16: return angular_pp<T, C, 16, 16>(p, t, U, K, sgn, col, nb, ntiles, s);
+      case 24: return angular_pp<T, C, 24, 24>(p, t, U, K, sgn, col, nb, ntiles, s);
+      case 32: return angular_pp<T, C, 32, 32>(p, t, U, K, sgn, col, nb, ntiles, s);
+      default: return angular_pp<T, C, 0, 0>(p, t, U, K, sgn, col, nb, ntiles, s);
+    }
   }
+  static const cudaError_t e = allow_smem(k_angular<T, C>);  // once per kernel
+  if (e != cudaSuccess) return e;
   const size_t smem = smem_angular<C>(d, nb, rb);
-  k_angular<T, C><<<grid1(ntiles), kThreads, smem, s>>>(p, t, U, K, sgn, collision ? 1 : 0, nb);
+  k_angular<T, C><<<grid1(ntiles), kThreads, smem, s>>>(p, t, U, K, sgn, col, nb);
   return cudaGetLastError();
 }
 
 template <typename T, typename C>
 cudaError_t Launch<T, C>::plane(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                                 cudaStream_t s) {
-  static bool init = false;
-  if (!init) {
-    cudaError_t ea = allow_smem(k_plane<T, C>);
-    if (ea == cudaSuccess) ea = allow_smem(k_plane_pp<T, C>);
-    if (ea != cudaSuccess) return ea;
-    init = true;
-  }
   const Dims& d = p.d;
   const bool rb = p.tp.rb & 2;
   const int c = p.tp.c > 0 ? p.tp.c : plane_c<T, C>(d, 1, rb);
   const long long nct = (long long)d.G * d.Nr * d.NT * (d.NP / 2 / c);
   if (rb) {
-    const size_t smem = smem_plane_pp<C>(d, c);
-    const int ctas = persistent_ctas(k_plane_pp<T, C>, smem, nct);
-    k_plane_pp<T, C><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, c, nct);
-    return cudaGetLastError();
+    switch (plane_spec(d, c)) {
+      case 8: return plane_pp<T, C, 8>(p, t, U, K, sgn, c, nct, s);
+      case 16: return plane_pp<T, C, 16>(p, t, U, K, sgn, c, nct, s);
+      case 24: return plane_pp<T, C, 24>(p, t, U, K, sgn, c, nct, s);
+      case 32: return plane_pp<T, C, 32>(p, t, U, K, sgn, c, nct, s);
+      default: return plane_pp<T, C, 0>(p, t, U, K, sgn, c, nct, s);
+    }
   }
+  static const cudaError_t e = allow_smem(k_plane<T, C>);  // once per kernel
+  if (e != cudaSuccess) return e;
   const size_t smem = smem_plane<C>(d, c, rb);
   k_plane<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, U, K, sgn, c);
   return cudaGetLastError();
@@ -176,13 +211,6 @@ template <typename T, typename C>
 cudaError_t Launch<T, C>::radial(const Problem& p, const Tables<C>& t, const double* Dr64,
                                  const T* U, const T* K, C sgn, bool tau, int mode, T* F, T* Acc,
                                  T* Uout, T* out, double dt, cudaStream_t s) {
-  static bool init = false;
-  if (!init) {
-    cudaError_t ea = allow_smem(k_radial<T, C>);
-    if (ea == cudaSuccess) ea = allow_smem(k_radial_pp<T, C>);
-    if (ea != cudaSuccess) return ea;
-    init = true;
-  }
   if constexpr (sizeof(T) == 4) {
     if (p.tc)
       return launch_radial_tc(p, t, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, s);
@@ -192,16 +220,20 @@ cudaError_t Launch<T, C>::radial(const Problem& p, const Tables<C>& t, const dou
   const int W = p.tp.W > 0 ? p.tp.W : radial_W<T, C>(d, 2, rb);
   const int S = d.NT * d.NP;
   const long long nct = (long long)d.G * d.Nt * d.Np * ((S + W - 1) / W);
+  const int ta = tau ? 1 : 0;
   if (rb) {
-    const size_t smem = smem_radial_pp<C>(d, W);
-    const int ctas = persistent_ctas(k_radial_pp<T, C>, smem, nct);
-    k_radial_pp<T, C><<<ctas, kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, tau ? 1 : 0, mode, F,
-                                                   Acc, Uout, out, (C)dt, W, nct);
-    return cudaGetLastError();
+    switch (rad_spec(d)) {
+      case 17: return radial_eo<T, C, 17>(p, t, Dr64, U, K, sgn, ta, mode, F, Acc, Uout, out, (C)dt, W, nct, s);
+      case 33: return radial_eo<T, C, 33>(p, t, Dr64, U, K, sgn, ta, mode, F, Acc, Uout, out, (C)dt, W, nct, s);
+      case 65: return radial_eo<T, C, 65>(p, t, Dr64, U, K, sgn, ta, mode, F, Acc, Uout, out, (C)dt, W, nct, s);
+      default: return radial_eo<T, C, 0>(p, t, Dr64, U, K, sgn, ta, mode, F, Acc, Uout, out, (C)dt, W, nct, s);
+    }
   }
+  static const cudaError_t e = allow_smem(k_radial<T, C>);  // once per kernel
+  if (e != cudaSuccess) return e;
   const size_t smem = smem_radial<C>(d, W, rb);
-  k_radial<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, tau ? 1 : 0, mode, F,
-                                                    Acc, Uout, out, (C)dt, W);
+  k_radial<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, Dr64, U, K, sgn, ta, mode, F, Acc, Uout,
+                                                    out, (C)dt, W);
   return cudaGetLastError();
 }
 
