@@ -102,6 +102,11 @@ __device__ __forceinline__ void copy4(C* dst, const T* src) {
     st4<C>(dst, w);
   }
 }
+// Ask for the 16 bytes at p to be brought into L2 (no register, no wait).
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T* p) {
+  asm volatile("prefetch.global.L2 [%0];" :: "l"(p));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -157,9 +162,9 @@ __device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int n
 }
 
 // Preparation of a staged tile: coefficients, J, the sums and differences of
-// every Phi pair, and the transposed copy uT[m][k] (for the Phi contraction
-// and the pointwise terms). Entry: su complete and visible. Exit (after the
-// caller's barrier): su is no longer read.
+// every Phi pair (for the Theta contraction and the pointwise terms), and the
+// transposed copy uT[m][k] (for the Phi contraction). Entry: su complete and
+// visible. Exit (after the caller's barrier): su is no longer read.
 template <int NT_, int NP_, typename T, typename C>
 __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C>& t,
                                                 const C* su, C* sSD, C* uT, C* sc, int collision,
@@ -288,14 +293,19 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
     for (int r = 0; r < RB; ++r) {
       const int k = k0 + r;
       const C aT = sgn * -t.sinT[k] * ir;
+      C sv[CB], dv[CB];   // F at (k, m) and (k, m + NP/2) from the pair's sum and difference
+      if (collision) {
+        ld4<C>(us + k * hP + p0, sv);
+        ld4<C>(ud + k * hP + p0, dv);
+      }
       T o1[CB], o2[CB];
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
         C v1 = aT * (ps[r][c] + qd[r][c] + s1[c] * da[r][c]);
         C v2 = aT * (ps[r][c] - qd[r][c] + s2[c] * db[r][c]);
         if (collision) {
-          v1 += src - kks * ut[(p0 + c) * UTP + k];
-          v2 += src - kks * ut[(p0 + c + hP) * UTP + k];
+          v1 += src - kks * (C)0.5 * (sv[c] + dv[c]);
+          v2 += src - kks * (C)0.5 * (sv[c] - dv[c]);
         }
         o1[c] = (T)v1;
         o2[c] = (T)v2;
@@ -556,6 +566,186 @@ k_plane_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C
   cp_async_wait0();
 }
 
+// ----------------------------------------------------------------------------
+// Plane pass on a square grid (N nodes on every angular axis), whole Phi rows
+// per tile: a tile is (g, i) and KT consecutive Theta values, i.e. columns
+// w = kl*N + m (KT*N of them, contiguous in memory for every (theta, phi)).
+// Thread: RB theta rows x one phi pair (l, l + N/2) x 4 columns m0.. and the
+// 4 partner columns m0 + N/2.. of one Theta value. It owns both DFS pairs
+// that these columns form -- (l, m) with (l+N/2, m+N/2) and (l, m+N/2) with
+// (l+N/2, m) -- so each staged value it loads feeds twice the multiply-adds of
+// the general form. Sums/differences use a row pitch of KT*N + 8 so that the
+// 8 lanes of a 16-byte load phase hit distinct banks.
+// Shared layout: [PthT | QthT | DphT | 2 tiles N*N*KT*N | sums, diffs 2*N*(N/2)*(KT*N+8)]
+template <int N, int KT>
+struct PlaneSq {
+  static constexpr int W = KT * N, hp = N / 2, H4 = hp / 4, SP = W + 8, TS = N * N * W;
+  static constexpr int RB = kRBPlane, JR = N / RB;
+  static constexpr int units = JR * hp * KT * H4;
+};
+
+template <int N, int KT, typename C>
+size_t smem_plane_sq() {
+  using S = PlaneSq<N, KT>;
+  return (size_t)(3 * N * N + 2 * S::TS + 2 * N * S::hp * S::SP) * sizeof(C);
+}
+
+template <int N, int KT, typename T, typename C>
+__device__ __forceinline__ void plane_sq_load(const Dims& d, const T* U, long long tile, C* su) {
+  using S = PlaneSq<N, KT>;
+  const long long q = tile / (N / KT);
+  const int k0 = (int)(tile - q * (N / KT)) * KT;
+  const long long base = q * d.S_i + (long long)k0 * N;   // q = g*Nr + i
+  for (int x = threadIdx.x; x < N * N * (S::W / 4); x += blockDim.x) {
+    const int w4 = (x % (S::W / 4)) * 4, jl = x / (S::W / 4);
+    copy4<true, T, C>(su + jl * S::W + w4, U + base + (long long)jl * d.S_l + w4);
+  }
+}
+
+template <int N, int KT, typename T, typename C>
+__device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>& t, const C* su,
+                                              C* sSm, const C* sP, const C* sQ, const C* sD,
+                                              T* __restrict__ K, C sgn, long long tile) {
+  using S = PlaneSq<N, KT>;
+  constexpr int RB = S::RB, CB = 4, W = S::W, hp = S::hp, SP = S::SP;
+  const Dims& d = p.d;
+  C* sDf = sSm + N * hp * SP;
+  const long long q = tile / (N / KT);
+  const int k0 = (int)(tile - q * (N / KT)) * KT;
+  const int i = (int)(q % d.Nr);
+  const long long base = q * d.S_i + (long long)k0 * N;
+  // sums and differences with the partner (phi + pi, Phi + pi) once per pair
+  for (int x = threadIdx.x; x < N * hp * (W / 4); x += blockDim.x) {
+    const int w4 = (x % (W / 4)) * 4, jl = x / (W / 4), l = jl % hp, jj = jl / hp;
+    const int m4 = w4 % N, w4h = w4 - m4 + (m4 + hp) % N;
+    C a[4], b[4], s[4], df[4];
+    ld4<C>(su + (jj * N + l) * W + w4, a);
+    ld4<C>(su + (jj * N + l + hp) * W + w4h, b);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      s[cc] = a[cc] + b[cc];
+      df[cc] = a[cc] - b[cc];
+    }
+    st4<C>(sSm + (jj * hp + l) * SP + w4, s);
+    st4<C>(sDf + (jj * hp + l) * SP + w4, df);
+  }
+  __syncthreads();
+  const C ir = t.inv_r[i];
+  for (int unit = threadIdx.x; unit < S::units; unit += blockDim.x) {
+    const int mq = unit % S::H4, r1 = unit / S::H4, kl = r1 % KT, r2 = r1 / KT;
+    const int l = r2 % hp, jr = r2 / hp;
+    const int m0 = mq * CB, j0 = jr * RB;
+    const int wA = kl * N + m0, wB = wA + hp;      // columns m0.. and m0 + N/2..
+    C psA[RB][CB], qdA[RB][CB], psB[RB][CB], qdB[RB][CB];
+    C daA[RB][CB], daB[RB][CB], dbA[RB][CB], dbB[RB][CB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int cc = 0; cc < CB; ++cc)
+        psA[r][cc] = qdA[r][cc] = psB[r][cc] = qdB[r][cc] = daA[r][cc] = daB[r][cc] =
+            dbA[r][cc] = dbB[r][cc] = 0;
+#pragma unroll 8
+    for (int jj = 0; jj < N; ++jj) {
+      C sa[CB], da_[CB], sb[CB], db_[CB], P[RB], Q[RB];
+      ld4<C>(sSm + (jj * hp + l) * SP + wA, sa);
+      ld4<C>(sDf + (jj * hp + l) * SP + wA, da_);
+      ld4<C>(sSm + (jj * hp + l) * SP + wB, sb);
+      ld4<C>(sDf + (jj * hp + l) * SP + wB, db_);
+      ldv<C, RB>(sP + jj * N + j0, P);
+      ldv<C, RB>(sQ + jj * N + j0, Q);
+#pragma unroll
+      for (int cc = 0; cc < CB; ++cc) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          psA[r][cc] = fmac(P[r], sa[cc], psA[r][cc]);
+          qdA[r][cc] = fmac(Q[r], da_[cc], qdA[r][cc]);
+          psB[r][cc] = fmac(P[r], sb[cc], psB[r][cc]);
+          qdB[r][cc] = fmac(Q[r], db_[cc], qdB[r][cc]);
+        }
+      }
+    }
+#pragma unroll 8
+    for (int ll = 0; ll < N; ++ll) {
+      const C Dl = sD[ll * N + l], Dh = sD[ll * N + l + hp];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        C a[CB], b[CB];
+        ld4<C>(su + ((j0 + r) * N + ll) * W + wA, a);
+        ld4<C>(su + ((j0 + r) * N + ll) * W + wB, b);
+#pragma unroll
+        for (int cc = 0; cc < CB; ++cc) {
+          daA[r][cc] = fmac(Dl, a[cc], daA[r][cc]);
+          daB[r][cc] = fmac(Dl, b[cc], daB[r][cc]);
+          dbA[r][cc] = fmac(Dh, a[cc], dbA[r][cc]);
+          dbB[r][cc] = fmac(Dh, b[cc], dbB[r][cc]);
+        }
+      }
+    }
+    const C sTk = sgn * t.sinT[k0 + kl] * ir;
+    C cA[CB], sA[CB], cB[CB], sB[CB];
+#pragma unroll
+    for (int cc = 0; cc < CB; ++cc) {
+      cA[cc] = sTk * t.cosP[m0 + cc];
+      sA[cc] = sTk * t.sinP[m0 + cc];
+      cB[cc] = sTk * t.cosP[m0 + hp + cc];
+      sB[cc] = sTk * t.sinP[m0 + hp + cc];
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int j = j0 + r;
+      const C isn = t.inv_sinth[j];
+      T* p0 = K + base + (long long)j * d.S_j + (long long)l * d.S_l + kl * N + m0;
+      T* p1 = p0 + (long long)hp * d.S_l;      // phi partner row l + N/2
+      T k0a[CB], k0b[CB], k1a[CB], k1b[CB];
+      ld4<T>(p0, k0a);
+      ld4<T>(p0 + hp, k0b);
+      ld4<T>(p1, k1a);
+      ld4<T>(p1 + hp, k1b);
+#pragma unroll
+      for (int cc = 0; cc < CB; ++cc) {
+        k0a[cc] = (T)((C)k0a[cc] + cA[cc] * (psA[r][cc] + qdA[r][cc]) + sA[cc] * isn * daA[r][cc]);
+        k0b[cc] = (T)((C)k0b[cc] + cB[cc] * (psB[r][cc] + qdB[r][cc]) + sB[cc] * isn * daB[r][cc]);
+        k1a[cc] = (T)((C)k1a[cc] + cA[cc] * (psB[r][cc] - qdB[r][cc]) + sA[cc] * isn * dbA[r][cc]);
+        k1b[cc] = (T)((C)k1b[cc] + cB[cc] * (psA[r][cc] - qdA[r][cc]) + sB[cc] * isn * dbB[r][cc]);
+      }
+      st4<T>(p0, k0a);
+      st4<T>(p0 + hp, k0b);
+      st4<T>(p1, k1a);
+      st4<T>(p1 + hp, k1b);
+    }
+  }
+}
+
+template <typename T, typename C, int N, int KT>
+__global__ void __launch_bounds__(kThreads, 2)
+k_plane_sq(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
+           long long ntiles) {
+  using S = PlaneSq<N, KT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims& d = p.d;
+  C* sP = reinterpret_cast<C*>(smem_raw);
+  C* sQ = sP + N * N;
+  C* sD = sQ + N * N;
+  C* buf0 = sD + N * N;
+  C* sSm = buf0 + 2 * S::TS;
+  plane_rb_mats<C>(t, d, sP, sQ, sD);
+  long long tile = blockIdx.x;
+  if (tile < ntiles) plane_sq_load<N, KT, T, C>(d, U, tile, buf0);
+  cp_async_commit();
+  for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+    const long long next = tile + gridDim.x;
+    C* cur = buf0 + (it & 1) * S::TS;
+    C* nxt = buf0 + ((it + 1) & 1) * S::TS;
+    if (next < ntiles) plane_sq_load<N, KT, T, C>(d, U, next, nxt);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    plane_sq_body<N, KT, T, C>(p, t, cur, sSm, sP, sQ, sD, K, sgn, tile);
+    __syncthreads();
+  }
+  cp_async_wait0();
+}
+
 // ============================================================================
 // Radial pass. Thread: RB output pairs (i, N-i) x 4 columns of one tile of W
 // (Theta, Phi) columns at fixed (g, theta, phi). The even/odd parts of U are
@@ -700,6 +890,23 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
     C klo[RB][CB], khi[RB][CB], kmid[CB];
     C cT = 0, ckf = 0;
     if (act) {
+      // this thread's K rows, and the F / Acc rows of its stage update, are
+      // requested before the contraction so that their latency overlaps it
+      T k1[RB][CB], k2[RB][CB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        const long long g1 = base + (i0 + r) * Si + w0, g2 = base + (N - i0 - r) * Si + w0;
+        ld4<T>(Kin + g1, k1[r]);
+        ld4<T>(Kin + g2, k2[r]);
+        if (mode != RAD_RHS) {
+          prefetch_l2(F + g1);
+          prefetch_l2(F + g2);
+          if (mode != RAD_STAGE0) {
+            prefetch_l2(Acc + g1);
+            prefetch_l2(Acc + g2);
+          }
+        }
+      }
       C ae[RB][CB], ao[RB][CB];
 #pragma unroll
       for (int r = 0; r < RB; ++r)
@@ -750,20 +957,17 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
         const int i = i0 + r;
-        T k1[CB], k2[CB];
-        ld4<T>(Kin + base + i * Si + w0, k1);
-        ld4<T>(Kin + base + (N - i) * Si + w0, k2);
         if (i < n64) {
 #pragma unroll
           for (int cc = 0; cc < CB; ++cc) {
-            klo[r][cc] = (C)k1[cc] + ckf * sR[i * W + w0 + cc];
-            khi[r][cc] = (C)k2[cc] + ckf * sR[(n64 + i) * W + w0 + cc];
+            klo[r][cc] = (C)k1[r][cc] + ckf * sR[i * W + w0 + cc];
+            khi[r][cc] = (C)k2[r][cc] + ckf * sR[(n64 + i) * W + w0 + cc];
           }
         } else {
 #pragma unroll
           for (int cc = 0; cc < CB; ++cc) {
-            klo[r][cc] = (C)k1[cc] + ck * (ao[r][cc] + ae[r][cc]);
-            khi[r][cc] = (C)k2[cc] + ck * (ao[r][cc] - ae[r][cc]);
+            klo[r][cc] = (C)k1[r][cc] + ck * (ao[r][cc] + ae[r][cc]);
+            khi[r][cc] = (C)k2[r][cc] + ck * (ao[r][cc] - ae[r][cc]);
           }
         }
       }

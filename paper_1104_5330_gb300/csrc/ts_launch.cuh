@@ -161,6 +161,18 @@ static cudaError_t radial_eo(const Problem& p, const Tables<C>& t, const double*
   return cudaGetLastError();
 }
 
+template <typename T, typename C, int N, int KT>
+static cudaError_t plane_sq(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
+                            cudaStream_t s) {
+  static const cudaError_t e = allow_smem(k_plane_sq<T, C, N, KT>);  // once per kernel
+  if (e != cudaSuccess) return e;
+  const size_t smem = smem_plane_sq<N, KT, C>();
+  const long long ntiles = (long long)p.d.G * p.d.Nr * (N / KT);
+  const int ctas = persistent_ctas(k_plane_sq<T, C, N, KT>, smem, ntiles);
+  k_plane_sq<T, C, N, KT><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, ntiles);
+  return cudaGetLastError();
+}
+
 template <typename T, typename C>
 cudaError_t Launch<T, C>::angular(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                                   bool collision, cudaStream_t s) {
@@ -194,7 +206,9 @@ cudaError_t Launch<T, C>::plane(const Problem& p, const Tables<C>& t, const T* U
   if (rb) {
     switch (plane_spec(d, c)) {
       case 8: return plane_pp<T, C, 8>(p, t, U, K, sgn, c, nct, s);
-      case 16: return plane_pp<T, C, 16>(p, t, U, K, sgn, c, nct, s);
+      case 16:
+        if constexpr (sizeof(C) == 4) return plane_sq<T, C, 16, 2>(p, t, U, K, sgn, s);
+        else return plane_pp<T, C, 16>(p, t, U, K, sgn, c, nct, s);
       case 24: return plane_pp<T, C, 24>(p, t, U, K, sgn, c, nct, s);
       case 32: return plane_pp<T, C, 32>(p, t, U, K, sgn, c, nct, s);
       default: return plane_pp<T, C, 0>(p, t, U, K, sgn, c, nct, s);
