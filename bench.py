@@ -50,7 +50,7 @@ WORKLOADS = {
     "absorber_65x32^4_g1": (0.2, 1.0, 65, 32, 32, 32, 32, 1),
 }
 PRECISIONS = {"fp64": "TS_FP64", "fp32": "TS_FP32", "fp32_r64": "TS_FP32_R64",
-              "tf32x3": "TS_TF32X3"}
+              "tf32x3": "TS_TF32X3", "bf16x3": "TS_BF16X3"}
 FP64_FMA_PER_SM_CLK = 2        # GB300: 2 FP64 FMA lanes per SM (1/64 of the 128 FP32 lanes)
 FP32_FMA_PER_SM_CLK = 128
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -398,7 +398,7 @@ def run_ours(args, dims, wname):
                 "hbm_achieved_gbs": byts[dname] / (avg_ms * 1e-3) / 1e9}
     else:
         achieved = byts[dname] / (avg_ms * 1e-3) / 1e9
-        if prec == ts.TS_TF32X3 and dname == "radial":
+        if prec in (ts.TS_TF32X3, ts.TS_BF16X3) and dname == "radial":
             kfam = "k_radial_tc"
         roof = {"bound": "hbm", "kernel": f"{kfam}<float>", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
@@ -450,7 +450,8 @@ def run_ours(args, dims, wname):
         line["variants"] = {}
         kname = {"radial": "k_radial_tc"}
         for vname, vprec in (("fp32", ts.TS_FP32), ("fp32_r64", ts.TS_FP32_R64),
-                             ("tf32x3_tensorcore_radial", ts.TS_TF32X3)):
+                             ("tf32x3_tensorcore_radial", ts.TS_TF32X3),
+                             ("bf16x3_tensorcore_radial", ts.TS_BF16X3)):
             g32, _ = make(vprec)
             F32 = torch.as_tensor(F0, dtype=torch.float32, device="cuda").contiguous()
             g32.step(F32, dt, nv)
@@ -470,7 +471,8 @@ def run_ours(args, dims, wname):
             hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
             alu32 = fl32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e12
             kf = eo_kernel(names[d32]) if even_odd_passes(dims, 4)[names[d32]] else f"k_{names[d32]}"
-            kn = (kname.get(names[d32], kf) if vprec == ts.TS_TF32X3 else kf) + "<float>"
+            kn = (kname.get(names[d32], kf) if vprec in (ts.TS_TF32X3, ts.TS_BF16X3) else kf)
+            kn += "<float>"
             line["variants"][vname] = {
                 "value": pts * args.steps / (ms32 * 1e-3), "unit": "point-updates/s",
                 "ms_per_step": ms32 / args.steps, "dtype": "f32",

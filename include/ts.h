@@ -64,10 +64,14 @@ typedef enum {
                       derivative rows nearest each of r = R1 and r = R2 (the rows
                       with the largest entries) accumulated in double, and the
                       split scheme's implicit collision step in double */
-  TS_TF32X3 = 3    /* float storage; the radial derivative on the tensor cores
+  TS_TF32X3 = 3,   /* float storage; the radial derivative on the tensor cores
                       (tcgen05, operands split into TF32 hi + lo, three products
                       hi*hi + hi*lo + lo*hi accumulated in FP32) for N_r <= 81,
                       angular passes as TS_FP32 */
+  TS_BF16X3 = 4    /* float storage; the radial derivative on the tensor cores
+                      with operands split into three bf16 terms b0 + b1 + b2 and
+                      the six products of total order <= 2 accumulated in FP32,
+                      for N_r <= 81; angular passes as TS_FP32 */
 } ts_precision;
 
 typedef enum {

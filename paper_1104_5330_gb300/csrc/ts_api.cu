@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
@@ -222,6 +223,42 @@ void tc_tables(HostTables& h) {
     }
 }
 
+// bf16 rounding to nearest, ties to even (finite inputs).
+uint16_t bf16_rne(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
+}
+float bf16_value(uint16_t h) {
+  const uint32_t b = (uint32_t)h << 16;
+  float y;
+  std::memcpy(&y, &b, 4);
+  return y;
+}
+
+// D_r as three bf16 terms (each the rounding of what the previous ones leave),
+// the tensor cores' B operand of the BF16x3 radial pass: zero-padded to (N_r up
+// to 16) x (N_r up to 16), 8-row x 8-element core matrices, core (n/8, k/8) at
+// element offset ((n/8) KC + k/8) 64, KC = Kpad/8; the terms one after another.
+std::vector<uint16_t> tc_tables_bf16(const HostTables& h) {
+  const int Nr = (int)h.r.size(), Kpad = (Nr + 15) / 16 * 16, Npad = (Nr + 15) / 16 * 16;
+  const int KC = Kpad / 8;
+  const size_t T = (size_t)Npad * Kpad;
+  std::vector<uint16_t> out(3 * T, 0);
+  for (int n = 0; n < Nr; ++n)
+    for (int k = 0; k < Nr; ++k) {
+      double v = h.Dr[(size_t)n * Nr + k];
+      const size_t o = (size_t)((n / 8) * KC + k / 8) * 64 + (n % 8) * 8 + (k % 8);
+      for (int term = 0; term < 3; ++term) {
+        const uint16_t b = bf16_rne((float)v);
+        out[term * T + o] = b;
+        v -= (double)bf16_value(b);
+      }
+    }
+  return out;
+}
+
 void even_odd_tables(HostTables& h) {
   auto pq = [](const Vec& A, const Vec& B, int N, Vec& PT, Vec& QT) {
     PT.assign((size_t)N * N, 0.0);
@@ -372,7 +409,11 @@ ts::Problem make_problem(const ts_grid* g) {
   p.kaps = g->kaps;
   p.gR1 = g->gR1;
   p.gR2 = g->gR2;
-  p.tc = g->desc.precision == TS_TF32X3 && ts::tc_supported(g->d.Nr);
+  p.tc = !ts::tc_supported(g->d.Nr)             ? ts::TC_NONE
+         : g->desc.precision == TS_TF32X3 ? ts::TC_TF32X3
+         : g->desc.precision == TS_BF16X3 ? ts::TC_BF16X3
+                                          : ts::TC_NONE;
+  p.tcb16 = g->tcb16;
   p.err = g->err;
   return p;
 }
@@ -547,7 +588,7 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
     return fail(TS_ERR_UNSUPPORTED,
                 "sizes: need 3<=Nr<=129, 2<=Ntheta<=64, even 2..64 for Nphi, NTheta, NPhi");
   if (g.precision != TS_FP64 && g.precision != TS_FP32 && g.precision != TS_FP32_R64 &&
-      g.precision != TS_TF32X3)
+      g.precision != TS_TF32X3 && g.precision != TS_BF16X3)
     return fail(TS_ERR_UNSUPPORTED, "unknown precision");
   if (g.scheme != TS_RK4 && g.scheme != TS_RK4_SPLIT_IMPLICIT)
     return fail(TS_ERR_UNSUPPORTED, "unknown scheme");
@@ -574,6 +615,12 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
 
   cudaError_t e = upload_tables<double>(G->h, &G->tab64, &G->t64);
   if (e == cudaSuccess && g.precision != TS_FP64) e = upload_tables<float>(G->h, &G->tab32, &G->t32);
+  if (e == cudaSuccess && g.precision == TS_BF16X3) {
+    const std::vector<uint16_t> b16 = tc_tables_bf16(G->h);
+    e = cudaMalloc(&G->tcb16, b16.size() * sizeof(uint16_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(G->tcb16, b16.data(), b16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  }
   const size_t ncoef = (size_t)d.nblk * sizeof(double);
   const size_t ninfl = (size_t)g.groups * g.Ntheta * g.Nphi * (g.NTheta / 2) * g.NPhi * es;
   const size_t nf = (size_t)d.total * es;
@@ -604,7 +651,7 @@ ts_status ts_destroy_grid(ts_grid* g) {
   if (!g) return TS_OK;
   cudaDeviceSynchronize();
   void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
-                  g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err};
+                  g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err, g->tcb16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : g->adj)

@@ -83,9 +83,13 @@ struct Problem {
   const double* kaps;
   const void* gR1;   // inflow data, element type of the grid
   const void* gR2;
-  int tc;            // 1: radial pass on the tensor cores (split TF32, float grids)
+  int tc;            // TcKind: radial pass on the tensor cores (float grids)
+  const void* tcb16; // BF16x3: the three bf16 terms of D_r in the MMA's B layout
   int* err;          // device flag set by a bounded wait that ran out
 };
+
+// Operand forms of the tensor-core radial pass.
+enum TcKind { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2 };
 
 // Radial pass on the tensor cores (float grids; defined with the float kernels).
 cudaError_t launch_radial_tc(const Problem& p, const Tables<float>& t, const float* U,
@@ -174,6 +178,7 @@ struct ts_grid {
   int* err = nullptr;    // device flag: a bounded device-side wait ran out
   void* io = nullptr;
   ts::TileParams tp{};   // tile shapes (0 = built-in heuristic); set by ts_autotune
+  void* tcb16 = nullptr; // TS_BF16X3: bf16 terms of D_r (tensor-core B operand)
 };
 
 namespace ts {

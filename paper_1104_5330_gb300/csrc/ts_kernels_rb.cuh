@@ -120,6 +120,12 @@ template <typename C> struct RBRad { static constexpr int v = rb_rad((int)sizeof
 // transposing stores of a warp then cover all banks once).
 template <typename C>
 __host__ __device__ constexpr int ang_utp(int NT) { return NT + 16 / (int)sizeof(C); }
+// Per-block strides of the angular sums/differences and transposed copy: 8
+// elements of padding put the blocks that one 16-byte load phase touches on
+// distinct banks.
+__host__ __device__ constexpr int ang_ss(int NT, int NP) { return NT * NP + 8; }
+template <typename C>
+__host__ __device__ constexpr int ang_us(int NT, int NP) { return NP * ang_utp<C>(NT) + 8; }
 
 // Line lengths with compiled-in forms of the single-problem kernels (0: the
 // run-time form, which the batched kernel always uses). The two forms perform
@@ -138,8 +144,8 @@ __host__ __device__ inline int rad_spec(const Dims& d) {
 
 // ============================================================================
 // Angular pass. Thread: RB Theta rows k0.. x 4 column pairs (m, m + NP/2) of one block.
-// Shared layout: [PThT | QThT | DPhT | tile nb*S | sums/diffs nb*S |
-//                 transposed tile nb*NP*UTP | 6 nb per-block scalars]
+// Shared layout: [PThT | QThT | DPhT | tile nb*S | sums/diffs nb*(S+8) |
+//                 transposed tile nb*(NP*UTP+8) | 6 nb per-block scalars]
 template <typename C>
 __device__ __forceinline__ void angular_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
                                                 C* sD) {
@@ -171,7 +177,7 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
                                                 int nb, long long tile) {
   const Dims& d = p.d;
   const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2;
-  const int UTP = ang_utp<C>(NT), H4 = hP / 4;
+  const int UTP = ang_utp<C>(NT), H4 = hP / 4, SS = ang_ss(NT, NP), US = ang_us<C>(NT, NP);
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // once per block
@@ -197,9 +203,9 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
       s[c] = a[c] + b[c];
       df[c] = a[c] - b[c];
     }
-    st4<C>(sSD + bb * S + kk * hP + p4, s);
-    st4<C>(sSD + bb * S + NT * hP + kk * hP + p4, df);
-    C* ut = uT + bb * NP * UTP;
+    st4<C>(sSD + bb * SS + kk * hP + p4, s);
+    st4<C>(sSD + bb * SS + NT * hP + kk * hP + p4, df);
+    C* ut = uT + bb * US;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       ut[(p4 + c) * UTP + kk] = a[c];
@@ -232,17 +238,20 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
   constexpr int RB = RBAng<C>::v, CB = 4;
   const Dims& d = p.d;
   const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2;
-  const int UTP = ang_utp<C>(NT);
+  const int UTP = ang_utp<C>(NT), SS = ang_ss(NT, NP), US = ang_us<C>(NT, NP);
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int KR = NT / RB, PC = hP / CB;
-  const int units = nbb * KR * PC;
+  // unit = (pc, 4 blocks, kr, block group): a 16-byte load phase spans 4 blocks
+  const int units = ((nbb + 3) / 4) * 4 * KR * PC;
   for (int unit = threadIdx.x; unit < units; unit += blockDim.x) {
-    const int pc = unit % PC, rest = unit / PC, kr = rest % KR, bb = rest / KR;
+    const int pc = unit % PC, r1 = unit / PC, b4 = r1 % 4, r2 = r1 / 4, kr = r2 % KR;
+    const int bb = (r2 / KR) * 4 + b4;
+    if (bb >= nbb) continue;
     const int p0 = pc * CB, k0 = kr * RB;
-    const C* us = sSD + bb * S;
+    const C* us = sSD + bb * SS;
     const C* ud = us + NT * hP;
-    const C* ut = uT + bb * NP * UTP;
+    const C* ut = uT + bb * US;
     C ps[RB][CB], qd[RB][CB], da[RB][CB], db[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
@@ -329,8 +338,8 @@ __device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C
   C* sD = sQ + NT * NT;
   C* su = sD + NP * NP;
   C* sSD = su + nb * S;
-  C* uT = sSD + nb * S;
-  C* sc = uT + nb * NP * ang_utp<C>(NT);
+  C* uT = sSD + nb * ang_ss(NT, NP);
+  C* sc = uT + nb * ang_us<C>(NT, NP);
   angular_rb_mats<C>(t, d, sP, sQ, sD);
   angular_rb_load<false, T, C>(d, U, nb, tile, su);
   __syncthreads();
@@ -353,8 +362,8 @@ k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K,
   C* sD = sQ + NT * NT;
   C* su = sD + NP * NP;
   C* sSD = su + nb * S;
-  C* uT = sSD + nb * S;
-  C* sc = uT + nb * NP * ang_utp<C>(NT);
+  C* uT = sSD + nb * ang_ss(NT, NP);
+  C* sc = uT + nb * ang_us<C>(NT, NP);
   angular_rb_mats<C>(t, d, sP, sQ, sD);
   long long tile = blockIdx.x;
   if (tile < ntiles) angular_rb_load<true, T, C>(d, U, nb, tile, su);

@@ -32,7 +32,8 @@ template <typename C>
 size_t smem_angular(const Dims& d, int nb, bool rb) {
   const size_t S = (size_t)d.NT * d.NP, mats = 2 * d.NT * d.NT + d.NP * d.NP;
   if (!rb) return (mats + nb * S + nb) * sizeof(C);
-  return (mats + nb * (2 * S + (size_t)d.NP * ang_utp<C>(d.NT)) + 6 * nb) * sizeof(C);
+  return (mats + nb * (S + (size_t)ang_ss(d.NT, d.NP) + ang_us<C>(d.NT, d.NP)) + 6 * nb) *
+         sizeof(C);
 }
 template <typename C>
 size_t smem_plane(const Dims& d, int c, bool rb) {
@@ -75,7 +76,7 @@ static int persistent_ctas(K kernel, size_t smem, long long ntiles) {
 }
 
 // Two CTAs of the persistent kernels share an SM when each stays below this.
-constexpr size_t kSmemHalf = 112 * 1024;
+constexpr size_t kSmemHalf = 113 * 1024;   // 228 KB per SM, 1 KB reserved per CTA
 
 // Built-in tile shapes: fill 256 threads with work while staying in the budget
 // (two CTAs per SM for the persistent register-blocked forms).

@@ -1,24 +1,30 @@
-// Radial pass on the 5th-generation tensor cores (tcgen05), split-TF32.
+// Radial pass on the 5th-generation tensor cores (tcgen05), split operands.
 //
 // One CTA (4 warps) owns 128 consecutive (Theta, Phi) columns of one (g,
 // theta, phi) position and all N_r radial nodes. The radial derivative of
 // those 128 r-lines is one matrix product
 //     D[w][i] = sum_i' u[i'][w] Dr[i][i']        (M = 128 columns, N = N_r padded
-//                                                 to 16, K = N_r padded to 8)
-// issued by one thread as tcgen05.mma kind::tf32 with the accumulator in
-// tensor memory (TMEM lane = column w). Operands are split into TF32 high and
-// low parts, x = hi + lo, and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
-// accumulated in FP32 (the lo*lo term, 2^-22 relative, is dropped). The
-// matrix halves are prepared on the host in the canonical no-swizzle K-major
-// layout (8-row x 16-byte core matrices) and copied into shared memory by the
-// bulk-copy (TMA) engine; the data tile is split and laid out by the threads.
-// After the MMAs complete, every thread reads its column's N_r results from
-// TMEM (tcgen05.ld) and applies the r term, the Tau rows and the RK4 stage
-// update for its own r-line. Every wait is bounded: if it runs out, the kernel
+//                                                 to 16, K = N_r padded to the
+//                                                 MMA's K step)
+// issued by one thread as tcgen05.mma with the accumulator in tensor memory
+// (TMEM lane = column w). Two operand forms, both accumulated in FP32:
+//  * TF32x3 (kind::tf32): x = hi + lo, hi = TF32(x), lo = TF32(x - hi);
+//    D = A_hi B_hi + A_hi B_lo + A_lo B_hi (lo*lo, 2^-22 relative, dropped);
+//  * BF16x3 (kind::f16 with bf16 operands): x = b0 + b1 + b2, each bf16 the
+//    rounding of what the previous terms leave; the six products of total
+//    order <= 2 (b0c0, b0c1, b1c0, b0c2, b1c1, b2c0), smallest first.
+// The matrix terms are prepared on the host in the canonical no-swizzle
+// K-major layout (8-row x 16-byte core matrices) and copied into shared
+// memory by the bulk-copy (TMA) engine; the data tile is split and laid out
+// by the threads. After the MMAs complete, every thread reads its column's N_r
+// results from TMEM (tcgen05.ld) and applies the r term, the Tau rows and the
+// RK4 stage update for its own r-line, loading each group of rows it updates
+// before storing any of them. Every wait is bounded: if it runs out, the kernel
 // sets the grid's error flag (ts_sync_status reports TS_ERR_TIMEOUT), waits a
 // bounded time for its own operations in flight, frees its TMEM and returns.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "ts_kernels_rb.cuh"
@@ -63,63 +69,107 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                // base offset 0, swizzle none
 }
 
-// Instruction descriptor of kind::tf32: D f32, A and B tf32, both K-major.
+// Instruction descriptors: D f32, A and B K-major; kind::tf32 with tf32
+// operands (format 2), kind::f16 with bf16 operands (format 1).
 __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
-
-__device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-      :: "r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if constexpr (KIND == TC_TF32X3)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        :: "r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        :: "r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+// Operand form: element bytes, operand terms, elements per 16-byte core
+// column, K of one MMA.
+template <int KIND>
+struct TcForm {
+  static constexpr int EB = KIND == TC_TF32X3 ? 4 : 2;
+  static constexpr int NTERM = KIND == TC_TF32X3 ? 2 : 3;
+  static constexpr int KE = 16 / EB;
+  static constexpr int KSTEP = 32 / EB;
+};
 
 struct TcShape {
   int Kpad, Npad, KC, tmem_cols;
-  size_t offA, offAlo, offB, offBlo, offOut, offBar, bytes;
+  size_t offA, offB, offOut, offBar, bytes, a_bytes, b_bytes;
 };
 
+template <int KIND>
 __host__ __device__ inline TcShape tc_shape(int Nr) {
+  using Fm = TcForm<KIND>;
   TcShape s;
-  s.Kpad = (Nr + 7) / 8 * 8;
+  s.Kpad = (Nr + Fm::KSTEP - 1) / Fm::KSTEP * Fm::KSTEP;
   s.Npad = (Nr + 15) / 16 * 16;
-  s.KC = s.Kpad / 4;
+  s.KC = s.Kpad / Fm::KE;
   int c = 32;
   while (c < s.Npad) c *= 2;
   s.tmem_cols = c;
-  const size_t a = (size_t)128 * s.Kpad * 4, b = (size_t)s.Npad * s.Kpad * 4;
-  s.offA = 0;
-  s.offAlo = a;
-  s.offB = 2 * a;
-  s.offBlo = 2 * a + b;
-  s.offOut = 2 * a + 2 * b;                                  // [Nr][128] results
+  s.a_bytes = (size_t)128 * s.Kpad * Fm::EB;
+  s.b_bytes = (size_t)s.Npad * s.Kpad * Fm::EB;
+  s.offA = 0;                                                 // NTERM data terms
+  s.offB = Fm::NTERM * s.a_bytes;                             // NTERM matrix terms
+  s.offOut = s.offB + Fm::NTERM * s.b_bytes;                  // [Nr][128] results
   s.offBar = s.offOut + (size_t)Nr * 128 * 4;
   s.offBar = (s.offBar + 15) / 16 * 16;
-  s.bytes = s.offBar + 32;                                   // 2 mbarriers + TMEM slot
+  s.bytes = s.offBar + 32;                                    // 2 mbarriers + TMEM slot
   return s;
 }
 
 // Byte offset of element (row, k) in a K-major no-swizzle operand with KC
-// 16-byte core columns: core (row/8, k/4) at ((row/8) KC + k/4) 128.
+// 16-byte core columns of KE elements: core (row/8, k/KE) at ((row/8) KC + k/KE) 128.
+template <int KE, int EB>
 __device__ __forceinline__ uint32_t core_off(int row, int k, int KC) {
-  return (uint32_t)((((row >> 3) * KC + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+  return (uint32_t)((((row >> 3) * KC + k / KE) << 7) + ((row & 7) << 4) + (k % KE) * EB);
 }
 
+// Split one value into the operand terms, written at byte offset o of each
+// term's tile (term stride a_bytes).
+template <int KIND>
+__device__ __forceinline__ void split_store(float v, unsigned char* sA, uint32_t o, size_t stride) {
+  if constexpr (KIND == TC_TF32X3) {
+    const uint32_t hi = tf32_rna(v);
+    const uint32_t lo = tf32_rna(v - __uint_as_float(hi));
+    *reinterpret_cast<uint32_t*>(sA + o) = hi;
+    *reinterpret_cast<uint32_t*>(sA + stride + o) = lo;
+  } else {
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(b0);
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+    *reinterpret_cast<__nv_bfloat16*>(sA + o) = b0;
+    *reinterpret_cast<__nv_bfloat16*>(sA + stride + o) = b1;
+    *reinterpret_cast<__nv_bfloat16*>(sA + 2 * stride + o) = b2;
+  }
+}
+
+template <int KIND>
 __global__ void __launch_bounds__(128, 1)
-k_radial_tc(Problem p, Tables<float> t, const float* __restrict__ BhiG,
-            const float* __restrict__ BloG, const float* U, const float* Kin, float sgn,
-            int tau, int mode, float* F, float* Acc, float* Uout, float* out, float dt) {
+k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const float* U,
+            const float* Kin, float sgn, int tau, int mode, float* F, float* Acc, float* Uout,
+            float* out, float dt) {
+  using Fm = TcForm<KIND>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const Dims d = p.d;
   const int Nr = d.Nr, NP = d.NP, S = d.NT * d.NP;
-  const TcShape sh = tc_shape(Nr);
+  const TcShape sh = tc_shape<KIND>(Nr);
   unsigned char* sA = smem_raw + sh.offA;
-  unsigned char* sAl = smem_raw + sh.offAlo;
   unsigned char* sB = smem_raw + sh.offB;
-  unsigned char* sBl = smem_raw + sh.offBlo;
   float* sOut = reinterpret_cast<float*>(smem_raw + sh.offOut);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sh.offBar);   // [0] copy, [1] mma
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + sh.offBar + 16);
@@ -138,39 +188,32 @@ k_radial_tc(Problem p, Tables<float> t, const float* __restrict__ BhiG,
   const long long base = (long long)g * d.S_g + (long long)j * d.S_j + (long long)l * d.S_l + c0;
 
   const uint32_t bar0 = smem_u32(&bar[0]), bar1 = smem_u32(&bar[1]);
-  const uint32_t bbytes = (uint32_t)(sh.Npad * sh.Kpad * 4);
+  const uint32_t bbytes = (uint32_t)(Fm::NTERM * sh.b_bytes);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar0) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (tid == 0) {  // matrix halves: bulk copies, completion counted in bytes on bar0
+  if (tid == 0) {  // matrix terms (contiguous in global memory): one bulk copy on bar0
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar0), "r"(2 * bbytes) : "memory");
+                 :: "r"(bar0), "r"(bbytes) : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        :: "r"(smem_u32(sB)), "l"(BhiG), "r"(bbytes), "r"(bar0) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        :: "r"(smem_u32(sBl)), "l"(BloG), "r"(bbytes), "r"(bar0) : "memory");
+        :: "r"(smem_u32(sB)), "l"(Bterms), "r"(bbytes), "r"(bar0) : "memory");
   }
   if (warp == 0) {  // TMEM accumulator: tmem_cols fp32 columns x 128 lanes
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  :: "r"(smem_u32(tslot)), "r"(sh.tmem_cols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // data tile -> A operand (rows = columns w, K = radial node), split hi/lo;
-  // columns beyond the tile and nodes beyond N_r are zero
+  // data tile -> A operand terms (rows = columns w, K = radial node); columns
+  // beyond the tile and nodes beyond N_r are zero
   for (int x = tid; x < sh.Kpad * 128; x += 128) {
     const int k = x >> 7, w = x & 127;
     float v = 0.f;
     if (k < Nr && w < Wc) v = U[base + (long long)k * d.S_i + w];
-    const uint32_t hi = tf32_rna(v);
-    const uint32_t lo = tf32_rna(v - __uint_as_float(hi));
-    const uint32_t o = core_off(w, k, sh.KC);
-    *reinterpret_cast<uint32_t*>(sA + o) = hi;
-    *reinterpret_cast<uint32_t*>(sAl + o) = lo;
+    split_store<KIND>(v, sA, core_off<Fm::KE, Fm::EB>(w, k, sh.KC), sh.a_bytes);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -181,15 +224,29 @@ k_radial_tc(Problem p, Tables<float> t, const float* __restrict__ BhiG,
   if (tid == 0) {
     ok = mbar_wait(bar0, 0);
     if (ok) {
-      const uint32_t idesc = umma_idesc_tf32(128, sh.Npad);
-      const uint32_t lbo = 128, sboA = (uint32_t)sh.KC * 128, sboB = sboA;
-      const uint32_t aH = smem_u32(sA), aL = smem_u32(sAl), bH = smem_u32(sB), bL = smem_u32(sBl);
-      for (int ks = 0; ks < sh.Kpad / 8; ++ks) {
+      const uint32_t idesc = KIND == TC_TF32X3 ? umma_idesc_tf32(128, sh.Npad)
+                                               : umma_idesc_bf16(128, sh.Npad);
+      const uint32_t lbo = 128, sbo = (uint32_t)sh.KC * 128;
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const uint32_t as = (uint32_t)sh.a_bytes, bs = (uint32_t)sh.b_bytes;
+      for (int ks = 0; ks < sh.Kpad / Fm::KSTEP; ++ks) {
         const uint32_t off = (uint32_t)ks * 256;  // two 16-byte core columns of K
-        umma_tf32(tmem, umma_desc(aH + off, lbo, sboA), umma_desc(bH + off, lbo, sboB), idesc,
-                  ks > 0);
-        umma_tf32(tmem, umma_desc(aH + off, lbo, sboA), umma_desc(bL + off, lbo, sboB), idesc, 1);
-        umma_tf32(tmem, umma_desc(aL + off, lbo, sboA), umma_desc(bH + off, lbo, sboB), idesc, 1);
+        auto mma = [&](int ta, int tb, uint32_t acc) {
+          umma<KIND>(tmem, umma_desc(a0 + ta * as + off, lbo, sbo),
+                     umma_desc(b0 + tb * bs + off, lbo, sbo), idesc, acc);
+        };
+        if constexpr (KIND == TC_TF32X3) {
+          mma(1, 0, ks > 0);
+          mma(0, 1, 1);
+          mma(0, 0, 1);
+        } else {
+          mma(2, 0, ks > 0);
+          mma(1, 1, 1);
+          mma(0, 2, 1);
+          mma(1, 0, 1);
+          mma(0, 1, 1);
+          mma(0, 0, 1);
+        }
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -229,7 +286,8 @@ k_radial_tc(Problem p, Tables<float> t, const float* __restrict__ BhiG,
                  :: "r"(tmem), "r"(sh.tmem_cols) : "memory");
   }
   if (!all_done) return;
-  // epilogue on this thread's r-line: r term, Tau rows, stage update
+  // epilogue on this thread's r-line: r term, Tau rows, stage update; rows in
+  // groups of RG whose loads are all issued before any of their stores
   const int w = tid;
   if (w >= Wc) return;
   const int k = (c0 + w) / NP;
@@ -237,29 +295,46 @@ k_radial_tc(Problem p, Tables<float> t, const float* __restrict__ BhiG,
   const int b = t.cosT[k] > 0.f ? 0 : Nr - 1;
   const float kb = Kin[base + (long long)b * d.S_i + w] + ck * sOut[b * 128 + w];
   const float tb = t.tsign[b];
-  for (int i = 0; i < Nr; ++i) {
-    const long long gi = base + (long long)i * d.S_i + w;
-    float kv = Kin[gi] + ck * sOut[i * 128 + w];
-    if (tau) kv -= kb * tb * t.tsign[i];
-    switch (mode) {
-      case RAD_RHS:
-        out[gi] = kv;
-        break;
-      case RAD_STAGE0:
-        Acc[gi] = kv;
-        Uout[gi] = F[gi] + 0.5f * dt * kv;
-        break;
-      case RAD_STAGE1:
-        Acc[gi] = Acc[gi] + 2.f * kv;
-        Uout[gi] = F[gi] + 0.5f * dt * kv;
-        break;
-      case RAD_STAGE2:
-        Acc[gi] = Acc[gi] + 2.f * kv;
-        Uout[gi] = F[gi] + dt * kv;
-        break;
-      default:
-        F[gi] = F[gi] + dt / 6.f * (Acc[gi] + kv);
-        break;
+  constexpr int RG = 8;
+  for (int i0 = 0; i0 < Nr; i0 += RG) {
+    float kv[RG], f[RG], ac[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      const int i = i0 + r;
+      if (i < Nr) {
+        const long long gi = base + (long long)i * d.S_i + w;
+        kv[r] = Kin[gi];
+        if (mode != RAD_RHS) f[r] = F[gi];
+        if (mode != RAD_RHS && mode != RAD_STAGE0) ac[r] = Acc[gi];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      const int i = i0 + r;
+      if (i >= Nr) break;
+      const long long gi = base + (long long)i * d.S_i + w;
+      float v = kv[r] + ck * sOut[i * 128 + w];
+      if (tau) v -= kb * tb * t.tsign[i];
+      switch (mode) {
+        case RAD_RHS:
+          out[gi] = v;
+          break;
+        case RAD_STAGE0:
+          Acc[gi] = v;
+          Uout[gi] = f[r] + 0.5f * dt * v;
+          break;
+        case RAD_STAGE1:
+          Acc[gi] = ac[r] + 2.f * v;
+          Uout[gi] = f[r] + 0.5f * dt * v;
+          break;
+        case RAD_STAGE2:
+          Acc[gi] = ac[r] + 2.f * v;
+          Uout[gi] = f[r] + dt * v;
+          break;
+        default:
+          F[gi] = f[r] + dt / 6.f * (ac[r] + v);
+          break;
+      }
     }
   }
 }

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "libts.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "ts.h")
 
 TS_OK, TS_ERR_ARG, TS_ERR_UNSUPPORTED, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE = range(7)
-TS_FP64, TS_FP32, TS_FP32_R64, TS_TF32X3 = 0, 1, 2, 3
+TS_FP64, TS_FP32, TS_FP32_R64, TS_TF32X3, TS_BF16X3 = 0, 1, 2, 3, 4
 TS_RK4, TS_RK4_SPLIT_IMPLICIT = 0, 1
 TS_BC_TAU_INFLOW, TS_BC_NONE = 0, 1
 

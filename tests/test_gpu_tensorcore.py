@@ -1,7 +1,8 @@
-"""The split-TF32 tensor-core radial pass (TS_TF32X3: tcgen05.mma with a TMEM
-accumulator, operands x = hi + lo in TF32, products hi*hi + hi*lo + lo*hi in
-FP32). Bar: the FP32 bound (1e-5 relative L2) against the FP64 oracle, and
-agreement with the FP32 SIMT passes."""
+"""The tensor-core radial passes (tcgen05.mma with a TMEM accumulator):
+TS_TF32X3 (operands x = hi + lo in TF32, products hi*hi + hi*lo + lo*hi) and
+TS_BF16X3 (operands x = b0 + b1 + b2 in bf16, the six products of total order
+<= 2), both accumulated in FP32. Bar: the FP32 bound (1e-5 relative L2)
+against the FP64 oracle, and agreement with the FP32 SIMT passes."""
 import numpy as np
 import pytest
 import torch
@@ -24,9 +25,13 @@ def _lib():
     yield
 
 
+TC = [3, 4]   # TS_TF32X3, TS_BF16X3
+
+
+@pytest.mark.parametrize("prec", TC)
 @pytest.mark.parametrize("dims", GRIDS)
-def test_tensor_core_rhs_and_steps_against_oracle(dims):
-    og, gg = pair(*dims, G=2, precision=3)
+def test_tensor_core_rhs_and_steps_against_oracle(dims, prec):
+    og, gg = pair(*dims, G=2, precision=prec)
     kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
     op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
     F = F0 + 0.1 * np.random.default_rng(3).standard_normal(og.shape)
@@ -40,9 +45,10 @@ def test_tensor_core_rhs_and_steps_against_oracle(dims):
     assert rel_l2(host(Fg), op.run(F0, dt, 20)) < 1e-5
 
 
-def test_tensor_core_radial_derivative_on_polynomial():
+@pytest.mark.parametrize("prec", TC)
+def test_tensor_core_radial_derivative_on_polynomial(prec):
     """cos(Theta) p'(r) for F = p(r) at 65 nodes through the tensor cores."""
-    og, gg = pair(0.2, 1.0, 65, 4, 4, 16, 8, precision=3)
+    og, gg = pair(0.2, 1.0, 65, 4, 4, 16, 8, precision=prec)
     gg.set_coeffs()
     rng = np.random.default_rng(9)
     p = np.polynomial.Chebyshev(rng.standard_normal(30) * 0.8 ** np.arange(30), domain=[0.2, 1.0])
@@ -52,9 +58,10 @@ def test_tensor_core_radial_derivative_on_polynomial():
     assert rel_l2(LF, np.broadcast_to(E, og.shape)) < 1e-5
 
 
-def test_tensor_core_agrees_with_simt_fp32():
+@pytest.mark.parametrize("prec", TC)
+def test_tensor_core_agrees_with_simt_fp32(prec):
     dims = GRIDS[0]
-    og, tc = pair(*dims, G=3, precision=3)
+    og, tc = pair(*dims, G=3, precision=prec)
     _, simt = pair(*dims, G=3, precision=1)
     kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
     for g in (tc, simt):
