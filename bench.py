@@ -268,6 +268,56 @@ def run_reference(args, dims, wname):
     return 0
 
 
+def run_differentiation(args, stream):
+    """Differentiable stepping on the gradient workload (33 x 16^4, 8 groups,
+    FP64, kappa in [0.5, 5]): n forward steps keeping ceil(sqrt(n)) checkpoints,
+    then the objective's backward pass (segment recomputation + adjoint steps)
+    for the gradients of the outgoing flux at R2 w.r.t. kappa, eta and F0."""
+    import torch
+    import paper_1104_5330_gb300.ts as ts
+    from paper_1104_5330_gb300 import inputs as I
+    from paper_1104_5330_gb300.autograd import outgoing_flux, transport_steps
+    R1, R2, Nr, Nt, Np, NT, NP, G = 0.2, 1.0, 33, 16, 16, 16, 16, 8
+    n = args.diff_steps
+    gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=ts.TS_FP64)
+    r, th, ph, Th, Ph = gg.nodes()
+    kap, eta, ks = I.gradient_fields(r, th, ph, G, 1104, R1, R2)
+    F0 = np.stack([I.seeded_smooth(r, th, ph, Th, Ph, 1104 + g, R1, R2) for g in range(G)])
+    gR1, gR2 = I.inflow_from(F0, NT)
+    dev = "cuda"
+    tk = torch.tensor(kap, device=dev, requires_grad=True)
+    te = torch.tensor(eta, device=dev, requires_grad=True)
+    tks = torch.tensor(ks, device=dev)
+    g1, g2 = torch.tensor(gR1, device=dev), torch.tensor(gR2, device=dev)
+    F = torch.tensor(F0, device=dev, requires_grad=True)
+    dt = I.dt_rule(R1, R2, Nr)
+    # warm-up: one short differentiable run
+    out = transport_steps(gg, F, tk, te, tks, dt, 2, g1, g2)
+    outgoing_flux(gg, out).sum().backward()
+    torch.cuda.synchronize()
+    tk.grad = te.grad = F.grad = None
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    out = transport_steps(gg, F, tk, te, tks, dt, n, g1, g2)
+    J = outgoing_flux(gg, out).sum()
+    e[1].record(stream)
+    J.backward()
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    ts.ts_sync_status(gg.handle)
+    fwd_ms, bwd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    pts = gg.points
+    finite = bool(torch.isfinite(tk.grad).all() and torch.isfinite(te.grad).all())
+    return {"workload": "gradient_33x16^4_g8", "steps": n,
+            "checkpoint_segment": int(np.ceil(np.sqrt(n))),
+            "value": pts * n / ((fwd_ms + bwd_ms) * 1e-3), "unit": "point-updates/s",
+            "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "backward_point_updates_per_s": pts * n / (bwd_ms * 1e-3),
+            "dtype": "f64", "objective": "outgoing flux at R2, all groups",
+            "grad_norms": {"kappa": float(tk.grad.norm()), "eta": float(te.grad.norm())},
+            "finite": finite}
+
+
 def run_batch(args, stream):
     """The uneven batch: 64 seeded problems (N_r in {17,33,65}, angular N in
     {8,16,24} per axis, 1..24 groups, kappa scale U[0.1,100]); FP32 storage and
@@ -503,6 +553,8 @@ def run_ours(args, dims, wname):
 
     if not args.skip_batch:
         line["batch"] = run_batch(args, stream)
+    if not args.skip_diff and args.diff_steps > 0:
+        line["differentiation"] = run_differentiation(args, stream)
 
     if rank == 0 and world == 1 and not args.skip_cpu_baseline:
         rate, wall, cores = oracle_rate(dims, 0, 3)
@@ -531,6 +583,8 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--skip-diff", action="store_true")
+    ap.add_argument("--diff-steps", type=int, default=200)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)      # timing rule: at least 3 untimed steps
     dims = WORKLOADS[args.workload]

@@ -188,7 +188,8 @@ std::vector<const Vec*> device_list(const HostTables& h, std::vector<Vec>& tmp) 
           &h.cosT, &h.sinT, &h.cosP, &h.sinP, &h.tsign, &h.qdir,
           &tmp[7], &tmp[8], &tmp[9], &tmp[10], &tmp[11], &tmp[12], &tmp[13],
           &h.PthT, &h.QthT, &h.PThT, &h.QThT, &h.EpT, &h.OpT, &h.DrMc, &h.DrMr,
-          &h.TcBhi, &h.TcBlo};
+          &h.TcBhi, &h.TcBlo,
+          &h.PthA, &h.QthA, &h.PThA, &h.QThA, &h.EpTa, &h.OpTa, &h.DrMca, &h.DrMra};
 }
 
 // Even/odd forms of the derivative matrices (see Tables in ts_internal.h).
@@ -294,6 +295,35 @@ void even_odd_tables(HostTables& h) {
       h.DrMr[i] = h.Dr[(size_t)M * Nr + i];
     }
   }
+  // the transposes: DFS halves read [in][out] = [j][j'] of A^T, i.e. A itself
+  auto pqa = [](const Vec& A, const Vec& B, int N, Vec& PA, Vec& QA) {
+    PA.assign((size_t)N * N, 0.0);
+    QA.assign((size_t)N * N, 0.0);
+    for (size_t x = 0; x < (size_t)N * N; ++x) {
+      PA[x] = 0.5 * (A[x] + B[x]);
+      QA[x] = 0.5 * (A[x] - B[x]);
+    }
+  };
+  pqa(h.Ath, h.Bth, (int)h.theta.size(), h.PthA, h.QthA);
+  pqa(h.ATh, h.BTh, (int)h.Theta.size(), h.PThA, h.QThA);
+  // M = D_r^T, M[i][i'] = D[i'][i]: the same folding as above
+  h.EpTa.assign((size_t)hh * hh, 0.0);
+  h.OpTa.assign((size_t)hh * hh, 0.0);
+  h.DrMca.assign(hh, 0.0);
+  h.DrMra.assign(hh, 0.0);
+  for (int i = 0; i < hh; ++i)
+    for (int ip = 0; ip < hh; ++ip) {
+      const double a = h.Dr[(size_t)ip * Nr + i], b = h.Dr[(size_t)(N - ip) * Nr + i];
+      h.EpTa[(size_t)ip * hh + i] = a + b;
+      h.OpTa[(size_t)ip * hh + i] = a - b;
+    }
+  if (Nr % 2) {
+    const int M = N / 2;
+    for (int i = 0; i < hh; ++i) {
+      h.DrMca[i] = h.Dr[(size_t)M * Nr + i];
+      h.DrMra[i] = h.Dr[(size_t)i * Nr + M];
+    }
+  }
 }
 
 template <typename C>
@@ -312,7 +342,9 @@ cudaError_t upload_tables(const HostTables& h, void** mem, Tables<C>* t) {
                  &t->cos_ph, &t->cosT, &t->sinT, &t->cosP, &t->sinP, &t->tsign, &t->qdir,
                  &t->FrT, &t->FthAT, &t->FthBT, &t->FphT, &t->FThAT, &t->FThBT, &t->FPhT,
                  &t->PthT, &t->QthT, &t->PThT, &t->QThT, &t->EpT, &t->OpT, &t->DrMc, &t->DrMr,
-                 &t->TcBhi, &t->TcBlo};
+                 &t->TcBhi, &t->TcBlo,
+                 &t->PthA, &t->QthA, &t->PThA, &t->QThA, &t->EpTa, &t->OpTa, &t->DrMca,
+                 &t->DrMra};
   size_t off = 0;
   for (size_t a = 0; a < list.size(); ++a) {
     for (size_t b = 0; b < list[a]->size(); ++b) host[off + b] = (C)(*list[a])[b];

@@ -41,6 +41,10 @@ struct Tables {
   //  output pairs (i, N-i): EpT[i'][i] = D[i][i'] + D[i][N-i'], OpT[i'][i] =
   //  D[i][i'] - D[i][N-i'], DrMc[i] = D[i][N/2], DrMr[i'] = D[N/2][i'] (odd Nr).
   C *PthT, *QthT, *PThT, *QThT, *EpT, *OpT, *DrMc, *DrMr;
+  // The same for the transposed matrices (adjoint passes): PthA[j][j'] =
+  // (A+B)[j][j']/2, QthA = (A-B)/2 ([in][out] of the transpose), Theta alike;
+  // EpTa, OpTa, DrMca, DrMra from D_r^T (also centro-antisymmetric).
+  C *PthA, *QthA, *PThA, *QThA, *EpTa, *OpTa, *DrMca, *DrMra;
   // D_r split into TF32 high and low halves in the tensor-core operand layout
   // (N_r padded to 16 rows x N_r padded to 8 columns, 8 x 4 core matrices).
   C *TcBhi, *TcBlo;
@@ -151,6 +155,7 @@ struct HostTables {
   Vec cosT, sinT, cosP, sinP, tsign, qdir;
   Vec wr, wth, fluxw;
   Vec PthT, QthT, PThT, QThT, EpT, OpT, DrMc, DrMr;   // even/odd forms (see Tables)
+  Vec PthA, QthA, PThA, QThA, EpTa, OpTa, DrMca, DrMra;  // even/odd forms of the transposes
   Vec TcBhi, TcBlo;                                   // tensor-core operand of D_r
 };
 

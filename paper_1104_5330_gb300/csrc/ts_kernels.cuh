@@ -247,17 +247,23 @@ __device__ __forceinline__ void radial_tile(const Problem& p, const Tables<C>& t
 // ----------------------------------------------------------------------------
 // Adjoint pass 3^T: r-lines. Kbar = scale * X. lt = Tau^T Kbar:
 // lt_i = Kbar_i - [i == b] T_N(x_b) sum_i' T_N(x_i') Kbar_i'. Then the radial
-// part of the stage adjoint: Ubar = -cos(Th) D_r^T lt.
+// part of the stage adjoint: Ubar = -cos(Th) D_r^T lt, with D_r^T (also
+// centro-antisymmetric) applied to the even/odd parts of lt: one thread per
+// output pair (i, N-i) and column, half the multiply-adds of the dense product.
 template <typename T, typename C>
 __global__ void __launch_bounds__(kThreads)
 k_radial_T(Problem p, Tables<C> t, const T* __restrict__ X, C scale, int tau,
            T* __restrict__ lt, T* __restrict__ Ubar, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
-  const int Nr = d.Nr, NP = d.NP, S = d.NT * d.NP;
-  C* sDr = reinterpret_cast<C*>(smem_raw);  // Dr [i][i'] read as [in][out] of D_r^T
-  C* sk = sDr + Nr * Nr;
-  C* sl = sk + Nr * W;
+  const int Nr = d.Nr, N = Nr - 1, hh = Nr / 2, NP = d.NP, S = d.NT * d.NP;
+  C* sE = reinterpret_cast<C*>(smem_raw);  // EpTa [i'][i]
+  C* sO = sE + hh * hh;                    // OpTa [i'][i]
+  C* sMc = sO + hh * hh;
+  C* sMr = sMc + hh;
+  C* sk = sMr + hh;                        // Kbar, then lt  [i][w]
+  C* sEv = sk + Nr * W;                    // lt_i' + lt_{N-i'}
+  C* sOd = sEv + hh * W;                   // lt_i' - lt_{N-i'}
   const int nchunk = (S + W - 1) / W;
   long long q = blockIdx.x;
   const int chunk = (int)(q % nchunk);
@@ -270,50 +276,78 @@ k_radial_T(Problem p, Tables<C> t, const T* __restrict__ X, C scale, int tau,
   const int Wc = min(W, S - c0);
   const long long base =
       (long long)g * d.S_g + (long long)j * d.S_j + (long long)l * d.S_l + c0;
-  for (int x = threadIdx.x; x < Nr * Nr; x += blockDim.x) sDr[x] = t.Dr[x];
+  for (int x = threadIdx.x; x < hh * hh; x += blockDim.x) {
+    sE[x] = t.EpTa[x];
+    sO[x] = t.OpTa[x];
+  }
+  for (int x = threadIdx.x; x < hh; x += blockDim.x) {
+    sMc[x] = t.DrMca[x];
+    sMr[x] = t.DrMra[x];
+  }
   for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
     const int i = x / Wc, w = x - i * Wc;
     sk[i * W + w] = scale * (C)X[base + (long long)i * d.S_i + w];
   }
   __syncthreads();
+  if (tau) {
+    for (int w = threadIdx.x; w < Wc; w += blockDim.x) {
+      const int b = t.cosT[(c0 + w) / NP] > (C)0 ? 0 : N;
+      C s = 0;
+      for (int ii = 0; ii < Nr; ++ii) s = fmac(t.tsign[ii], sk[ii * W + w], s);
+      sk[b * W + w] -= t.tsign[b] * s;
+    }
+    __syncthreads();
+  }
   for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
     const int i = x / Wc, w = x - i * Wc;
-    const int k = (c0 + w) / NP;
-    C v = sk[i * W + w];
-    if (tau) {
-      const int b = t.cosT[k] > (C)0 ? 0 : Nr - 1;
-      if (i == b) {
-        C s = 0;
-        for (int ii = 0; ii < Nr; ++ii) s = fmac(t.tsign[ii], sk[ii * W + w], s);
-        v -= t.tsign[b] * s;
-      }
-    }
-    sl[i * W + w] = v;
+    const C v = sk[i * W + w];
     lt[base + (long long)i * d.S_i + w] = (T)v;
+    if (i < hh) {
+      const C u = sk[(N - i) * W + w];
+      sEv[i * W + w] = v + u;
+      sOd[i * W + w] = v - u;
+    }
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < Nr * Wc; x += blockDim.x) {
-    const int i = x / Wc, w = x - i * Wc;  // i = output index of D_r^T
-    const int k = (c0 + w) / NP;
-    C a = 0;
-    for (int ii = 0; ii < Nr; ++ii) a = fmac(sDr[ii * Nr + i], sl[ii * W + w], a);
-    Ubar[base + (long long)i * d.S_i + w] = (T)(-t.cosT[k] * a);
+  const bool odd = Nr & 1;
+  const int npair = hh + (odd ? 1 : 0);
+  for (int x = threadIdx.x; x < npair * Wc; x += blockDim.x) {
+    const int i = x / Wc, w = x - i * Wc;
+    const C ck = -t.cosT[(c0 + w) / NP];
+    if (i < hh) {
+      C ae = 0, ao = 0;
+      for (int ip = 0; ip < hh; ++ip) {
+        ae = fmac(sE[ip * hh + i], sEv[ip * W + w], ae);
+        ao = fmac(sO[ip * hh + i], sOd[ip * W + w], ao);
+      }
+      if (odd) ae = fmac((C)2 * sMc[i], sk[(N / 2) * W + w], ae);
+      Ubar[base + (long long)i * d.S_i + w] = (T)(ck * (C)0.5 * (ao + ae));
+      Ubar[base + (long long)(N - i) * d.S_i + w] = (T)(ck * (C)0.5 * (ao - ae));
+    } else {  // middle node
+      C am = 0;
+      for (int ip = 0; ip < hh; ++ip) am = fmac(sMr[ip], sOd[ip * W + w], am);
+      Ubar[base + (long long)(N / 2) * d.S_i + w] = (T)(ck * am);
+    }
   }
 }
 
 // Adjoint pass 2^T: Ubar -= D_th^T (a_th lt) + D_ph^T (a_ph lt).
-// (D_th^T mu)(j', l, m) = sum_j Ath[j][j'] mu(j,l,m) + Bth[j][j'] mu(j, l+Np/2, m+NP/2).
+// (D_th^T mu)(j', l, m) = sum_j Ath[j][j'] mu(j,l,m) + Bth[j][j'] mu(j, l+Np/2, m+NP/2):
+// the output and its DFS partner (j', l+Np/2, m+NP/2) come from the sum and
+// difference of mu with its partner through (A+B)/2 and (A-B)/2 -- one thread
+// per output pair.
 template <typename T, typename C>
 __global__ void __launch_bounds__(kThreads)
 k_plane_T(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__ Ubar, int c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
   const int Nt = d.Nt, Np = d.Np, NP = d.NP, hP = NP / 2, hp = Np / 2, W = 2 * c;
-  C* sA = reinterpret_cast<C*>(smem_raw);  // Ath [j][j'] = [in][out] of the transpose
-  C* sB = sA + Nt * Nt;
-  C* sD = sB + Nt * Nt;                    // Dph [l][l']
-  C* s1 = sD + Np * Np;                    // a_th * lt   [j][l][w]
-  C* s2 = s1 + Nt * Np * W;                // a_ph * lt
+  C* sP = reinterpret_cast<C*>(smem_raw);  // PthA [j][j']
+  C* sQ = sP + Nt * Nt;
+  C* sD = sQ + Nt * Nt;                    // Dph [l][l']
+  C* sS = sD + Np * Np;                    // a_th lt + partner   [j][l < Np/2][w]
+  C* sDf = sS + Nt * hp * W;               // a_th lt - partner
+  C* s2 = sDf + Nt * hp * W;               // a_ph * lt            [j][l][w]
   const int nchunk = hP / c;
   long long q = blockIdx.x;
   const int chunk = (int)(q % nchunk);
@@ -325,32 +359,46 @@ k_plane_T(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__ Ubar
   const int m0 = chunk * c;
   const long long base = (long long)g * d.S_g + (long long)i * d.S_i + (long long)k * NP;
   for (int x = threadIdx.x; x < Nt * Nt; x += blockDim.x) {
-    sA[x] = t.Ath[x];
-    sB[x] = t.Bth[x];
+    sP[x] = t.PthA[x];
+    sQ[x] = t.QthA[x];
   }
   for (int x = threadIdx.x; x < Np * Np; x += blockDim.x) sD[x] = t.Dph[x];
-  const C sTk = t.sinT[k], ir = t.inv_r[i];
-  const int n = Nt * Np * W;
-  for (int x = threadIdx.x; x < n; x += blockDim.x) {
-    const int w = x % W, jl = x / W, l = jl % Np, j = jl / Np;
-    const int m = plane_m(w, c, m0, hP);
-    const C v = (C)lt[base + (long long)j * d.S_j + (long long)l * d.S_l + m];
-    s1[x] = sTk * t.cosP[m] * ir * v;
-    s2[x] = sTk * t.sinP[m] * ir * t.inv_sinth[j] * v;
+  const C sTk = t.sinT[k] * t.inv_r[i];
+  const int n2 = Nt * hp * W;
+  for (int x = threadIdx.x; x < n2; x += blockDim.x) {   // (j, l < Np/2, w) and its partner
+    const int w = x % W, jl = x / W, l = jl % hp, j = jl / hp;
+    const int wh = w < c ? w + c : w - c;
+    const int m = plane_m(w, c, m0, hP), mh = plane_m(wh, c, m0, hP);
+    const C v1 = (C)lt[base + (long long)j * d.S_j + (long long)l * d.S_l + m];
+    const C v2 = (C)lt[base + (long long)j * d.S_j + (long long)(l + hp) * d.S_l + mh];
+    const C a1 = sTk * t.cosP[m] * v1, a2 = sTk * t.cosP[mh] * v2;
+    sS[x] = a1 + a2;
+    sDf[x] = a1 - a2;
+    const C isn = t.inv_sinth[j];
+    s2[(j * Np + l) * W + w] = sTk * t.sinP[m] * isn * v1;
+    s2[(j * Np + l + hp) * W + wh] = sTk * t.sinP[mh] * isn * v2;
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < n; x += blockDim.x) {
-    const int w = x % W, jl = x / W, l = jl % Np, j = jl / Np;
-    const int lh = (l + hp) % Np, wh = w < c ? w + c : w - c;
-    C a = 0;
+  for (int x = threadIdx.x; x < n2; x += blockDim.x) {   // output pair (j, l, w), (j, l+hp, wh)
+    const int w = x % W, jl = x / W, l = jl % hp, j = jl / hp;
+    const int wh = w < c ? w + c : w - c;
+    C ps = 0, qd = 0;
     for (int jj = 0; jj < Nt; ++jj) {
-      a = fmac(sA[jj * Nt + j], s1[(jj * Np + l) * W + w], a);
-      a = fmac(sB[jj * Nt + j], s1[(jj * Np + lh) * W + wh], a);
+      const int o = (jj * hp + l) * W + w;
+      ps = fmac(sP[jj * Nt + j], sS[o], ps);
+      qd = fmac(sQ[jj * Nt + j], sDf[o], qd);
     }
-    for (int ll = 0; ll < Np; ++ll) a = fmac(sD[ll * Np + l], s2[(j * Np + ll) * W + w], a);
-    const long long idx =
+    C f1 = 0, f2 = 0;
+    for (int ll = 0; ll < Np; ++ll) {
+      f1 = fmac(sD[ll * Np + l], s2[(j * Np + ll) * W + w], f1);
+      f2 = fmac(sD[ll * Np + l + hp], s2[(j * Np + ll) * W + wh], f2);
+    }
+    const long long i1 =
         base + (long long)j * d.S_j + (long long)l * d.S_l + plane_m(w, c, m0, hP);
-    Ubar[idx] = (T)((C)Ubar[idx] - a);
+    const long long i2 =
+        base + (long long)j * d.S_j + (long long)(l + hp) * d.S_l + plane_m(wh, c, m0, hP);
+    Ubar[i1] = (T)((C)Ubar[i1] - (ps + qd) - f1);
+    Ubar[i2] = (T)((C)Ubar[i2] - (ps - qd) - f2);
   }
 }
 
@@ -358,6 +406,8 @@ k_plane_T(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__ Ubar
 //   Ubar_s = Ubar - D_Th^T(a_Th lt) - D_Ph^T(a_Ph lt) - (kappa+kappa_s) lt + kappa_s q_k sum lt
 //   gk -= sum_block lt*Us,  ge += sum_block lt
 //   lam_out = lam_in + Ubar_s;   Kbar_out = wl*lam + wu*Ubar_s (if Kbar_out)
+// D_Th^T on the DFS pair (k, m), (k, m+NP/2) through the sum and difference as
+// in the plane pass; one thread per output pair.
 template <typename T, typename C>
 __global__ void __launch_bounds__(kThreads)
 k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restrict__ Ubar,
@@ -365,28 +415,33 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
             T* lam_out, T* Kbar_out, C wl, C wu, int nb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
-  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2;
-  C* sA = reinterpret_cast<C*>(smem_raw);  // ATh [k][k']
-  C* sB = sA + NT * NT;
-  C* sD = sB + NT * NT;                    // DPh [m][m']
-  C* s1 = sD + NP * NP;                    // a_Th * lt  [bb][k][m]
-  C* s2 = s1 + nb * S;                     // a_Ph * lt
-  C* sS = s2 + nb * S;                     // [nb] kappa_s-weighted sum of lt
+  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2, hS = NT * hP;
+  C* sP = reinterpret_cast<C*>(smem_raw);  // PThA [k][k']
+  C* sQ = sP + NT * NT;
+  C* sD = sQ + NT * NT;                    // DPh [m][m']
+  C* sS = sD + NP * NP;                    // a_Th lt + partner  [bb][k][m < NP/2]
+  C* sDf = sS + nb * hS;                   // a_Th lt - partner
+  C* s2 = sDf + nb * hS;                   // a_Ph * lt          [bb][k][m]
+  C* sSum = s2 + nb * S;                   // [nb] kappa_s-weighted sum of lt
   const long long b0 = (long long)blockIdx.x * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
-    sA[x] = t.ATh[x];
-    sB[x] = t.BTh[x];
+    sP[x] = t.PThA[x];
+    sQ[x] = t.QThA[x];
   }
   for (int x = threadIdx.x; x < NP * NP; x += blockDim.x) sD[x] = t.DPh[x];
-  for (int x = threadIdx.x; x < nbb * S; x += blockDim.x) {
-    const int bb = x / S, r = x - bb * S, k = r / NP, m = r - k * NP;
+  for (int x = threadIdx.x; x < nbb * hS; x += blockDim.x) {   // (bb, k, m < NP/2) and partner
+    const int bb = x / hS, r = x - bb * hS, k = r / hP, m = r - k * hP;
     int g, i, j, l;
     decode_block(d, b0 + bb, g, i, j, l);
-    const C v = (C)lt[b0 * S + x];
+    const long long gi = (b0 + bb) * S + k * NP + m;
+    const C v1 = (C)lt[gi], v2 = (C)lt[gi + hP];
     const C aT = -t.sinT[k] * t.inv_r[i];
-    s1[x] = aT * v;
-    s2[x] = aT * t.sinP[m] * t.cot_th[j] * v;
+    sS[x] = aT * (v1 + v2);
+    sDf[x] = aT * (v1 - v2);
+    const C ct = aT * t.cot_th[j];
+    s2[bb * S + k * NP + m] = ct * t.sinP[m] * v1;
+    s2[bb * S + k * NP + m + hP] = ct * t.sinP[m + hP] * v2;
   }
   __syncthreads();
   {
@@ -404,30 +459,39 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
       }
       if (lane == 0) {
         const long long blk = b0 + bb;
-        sS[bb] = (C)(p.kaps[blk] * sl);
+        sSum[bb] = (C)(p.kaps[blk] * sl);
         ge[blk] += sl;
         gk[blk] -= slu;
       }
     }
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < nbb * S; x += blockDim.x) {
-    const int bb = x / S, r = x - bb * S, k = r / NP, m = r - k * NP;
-    const int mh = (m + hP) % NP;
-    const C* a1 = s1 + bb * S;
-    const C* a2 = s2 + bb * S;
-    C a = 0;
+  for (int x = threadIdx.x; x < nbb * hS; x += blockDim.x) {   // output pair (k, m), (k, m+hP)
+    const int bb = x / hS, r = x - bb * hS, k = r / hP, m = r - k * hP;
+    const C* a1 = sS + bb * hS;
+    const C* d1 = sDf + bb * hS;
+    const C* a2 = s2 + bb * S + k * NP;
+    C ps = 0, qd = 0;
     for (int kk = 0; kk < NT; ++kk) {
-      a = fmac(sA[kk * NT + k], a1[kk * NP + m], a);
-      a = fmac(sB[kk * NT + k], a1[kk * NP + mh], a);
+      ps = fmac(sP[kk * NT + k], a1[kk * hP + m], ps);
+      qd = fmac(sQ[kk * NT + k], d1[kk * hP + m], qd);
     }
-    for (int mm = 0; mm < NP; ++mm) a = fmac(sD[mm * NP + m], a2[k * NP + mm], a);
-    const long long blk = b0 + bb, gi = blk * S + r;
-    const C v = (C)lt[gi];
+    C f1 = 0, f2 = 0;
+    for (int mm = 0; mm < NP; ++mm) {
+      f1 = fmac(sD[mm * NP + m], a2[mm], f1);
+      f2 = fmac(sD[mm * NP + m + hP], a2[mm], f2);
+    }
+    const long long blk = b0 + bb, gi = blk * S + k * NP + m;
     const C kap = (C)p.kap[blk], ks = (C)p.kaps[blk];
-    const C ub = (C)Ubar[gi] - a - (kap + ks) * v + t.qdir[k] * sS[bb];
-    lam_out[gi] = (T)((C)lam_in[gi] + ub);
-    if (Kbar_out) Kbar_out[gi] = (T)(wl * (C)lam[gi] + wu * ub);
+    const C qs = t.qdir[k] * sSum[bb];
+    const C ub1 = (C)Ubar[gi] - (ps + qd) - f1 - (kap + ks) * (C)lt[gi] + qs;
+    const C ub2 = (C)Ubar[gi + hP] - (ps - qd) - f2 - (kap + ks) * (C)lt[gi + hP] + qs;
+    lam_out[gi] = (T)((C)lam_in[gi] + ub1);
+    lam_out[gi + hP] = (T)((C)lam_in[gi + hP] + ub2);
+    if (Kbar_out) {
+      Kbar_out[gi] = (T)(wl * (C)lam[gi] + wu * ub1);
+      Kbar_out[gi + hP] = (T)(wl * (C)lam[gi + hP] + wu * ub2);
+    }
   }
 }
 

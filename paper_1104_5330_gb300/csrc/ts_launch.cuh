@@ -100,10 +100,11 @@ static int plane_c(const Dims& d, int ntiles, bool rb = false) {
   const int hP = d.NP / 2;
   const size_t mats = (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np) * sizeof(C);
   int best = rb ? 4 : 1;
-  const int tiles = rb ? 3 * ntiles : ntiles;
+  const int tiles = rb ? 3 * ntiles : ntiles;   // rb: two staging buffers + sums/diffs
+  const size_t budget = rb ? kSmemHalf : kSmemBudget;
   for (int c = 1; c <= hP; ++c) {
     if (hP % c || (rb && c % 4)) continue;
-    if (mats + (size_t)tiles * d.Nt * d.Np * 2 * c * sizeof(C) <= kSmemBudget) best = c;
+    if (mats + (size_t)tiles * d.Nt * d.Np * 2 * c * sizeof(C) <= budget) best = c;
   }
   return best;
 }

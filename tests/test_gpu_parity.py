@@ -172,8 +172,14 @@ def test_flux_weights_match_oracle():
     assert rel_l2(host(gg.flux_weights()), og.outgoing_flux_weights()) < 1e-14
 
 
-def test_adjoint_parity_with_oracle():
-    og, gg = pair(*RAGGED, G=2)
+# odd and even N_r (with and without a middle node of the even/odd radial
+# adjoint), ragged tiles, and the 16^4 angular grid of the full-size workload
+ADJ_GRIDS = [RAGGED, (0.2, 1.0, 10, 6, 4, 8, 6), (0.2, 1.0, 9, 16, 16, 16, 16)]
+
+
+@pytest.mark.parametrize("dims", ADJ_GRIDS)
+def test_adjoint_parity_with_oracle(dims):
+    og, gg = pair(*dims, G=2)
     kap, eta, ks = I.gradient_fields(og.r, og.theta, og.phi, 2, 1104, 0.2, 1.0)
     F0 = np.stack([I.seeded_smooth(og.r, og.theta, og.phi, og.Theta, og.Phi, 1104 + g, 0.2, 1.0)
                    for g in range(2)])
