@@ -530,6 +530,7 @@ def run_ours(args, dims, wname):
                 "roofline": {"bound": "hbm", "kernel": kn,
                              "achieved": hbm32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": hbm32 / peaks["hbm_gbs"],
+                             "traffic": _traffic(names[d32], wname, vname),
                              "fp32_alu_tflops": alu32,
                              "fp32_alu_peak_tflops": sms * 2 * FP32_FMA_PER_SM_CLK * smax * 1e6 / 1e12,
                              "pass_share": {n: float(s) for n, s in zip(names, pm[:3] / pm[:3].sum())},
