@@ -192,8 +192,8 @@ def pass_work(dims, es):
     pts = Nr * Nt * Np * NT * NP * G
     eo = even_odd_passes(dims, es)
     flops = {
-        # dTh on the DFS pair, dPh, J, coefficients and collision
-        "angular": pts * ((2 * NT + 1 if eo["angular"] else 4 * NT) + 2 * NP + 2 + 11),
+        # dTh and dPh on the DFS pair halves (even/odd) or dense, J, coefficients, collision
+        "angular": pts * ((2 * NT + 1 + NP + 1 if eo["angular"] else 4 * NT + 2 * NP) + 2 + 11),
         # dth on the DFS pair, dph, coefficients
         "plane": pts * ((2 * Nt + 1 if eo["plane"] else 4 * Nt) + 2 * Np + 8),
         # dr (centro-antisymmetric halves), r term, Tau row, stage update

@@ -189,7 +189,8 @@ std::vector<const Vec*> device_list(const HostTables& h, std::vector<Vec>& tmp) 
           &tmp[7], &tmp[8], &tmp[9], &tmp[10], &tmp[11], &tmp[12], &tmp[13],
           &h.PthT, &h.QthT, &h.PThT, &h.QThT, &h.EpT, &h.OpT, &h.DrMc, &h.DrMr,
           &h.TcBhi, &h.TcBlo,
-          &h.PthA, &h.QthA, &h.PThA, &h.QThA, &h.EpTa, &h.OpTa, &h.DrMca, &h.DrMra};
+          &h.PthA, &h.QthA, &h.PThA, &h.QThA, &h.EpTa, &h.OpTa, &h.DrMca, &h.DrMra,
+          &h.MsPhT, &h.MdPhT, &h.MsphT, &h.MdphT};
 }
 
 // Even/odd forms of the derivative matrices (see Tables in ts_internal.h).
@@ -324,6 +325,21 @@ void even_odd_tables(HostTables& h) {
       h.DrMra[i] = h.Dr[(size_t)i * Nr + M];
     }
   }
+  // Fourier derivative on DFS pair halves (D circulant, so D[p+N/2][q+N/2] = D[p][q]):
+  // MsT[p'][p] = D[p][p'] + D[p][p'+N/2], MdT[p'][p] = D[p][p'] - D[p][p'+N/2]
+  auto halves = [](const Vec& D, int N, Vec& MsT, Vec& MdT) {
+    const int h = N / 2;
+    MsT.assign((size_t)h * h, 0.0);
+    MdT.assign((size_t)h * h, 0.0);
+    for (int p = 0; p < h; ++p)
+      for (int q = 0; q < h; ++q) {
+        const double a = D[(size_t)p * N + q], b = D[(size_t)p * N + q + h];
+        MsT[(size_t)q * h + p] = a + b;
+        MdT[(size_t)q * h + p] = a - b;
+      }
+  };
+  halves(h.DPh, (int)h.Phi.size(), h.MsPhT, h.MdPhT);
+  halves(h.Dph, (int)h.phi.size(), h.MsphT, h.MdphT);
 }
 
 template <typename C>
@@ -344,7 +360,7 @@ cudaError_t upload_tables(const HostTables& h, void** mem, Tables<C>* t) {
                  &t->PthT, &t->QthT, &t->PThT, &t->QThT, &t->EpT, &t->OpT, &t->DrMc, &t->DrMr,
                  &t->TcBhi, &t->TcBlo,
                  &t->PthA, &t->QthA, &t->PThA, &t->QThA, &t->EpTa, &t->OpTa, &t->DrMca,
-                 &t->DrMra};
+                 &t->DrMra, &t->MsPhT, &t->MdPhT, &t->MsphT, &t->MdphT};
   size_t off = 0;
   for (size_t a = 0; a < list.size(); ++a) {
     for (size_t b = 0; b < list[a]->size(); ++b) host[off + b] = (C)(*list[a])[b];

@@ -45,6 +45,13 @@ struct Tables {
   // (A+B)[j][j']/2, QthA = (A-B)/2 ([in][out] of the transpose), Theta alike;
   // EpTa, OpTa, DrMca, DrMra from D_r^T (also centro-antisymmetric).
   C *PthA, *QthA, *PThA, *QThA, *EpTa, *OpTa, *DrMca, *DrMra;
+  // Fourier derivative on the halves of a DFS pair: for s(p) = u(p) + u(p+N/2),
+  // d(p) = u(p) - u(p+N/2), p < N/2, the circulant D gives
+  //   (D u)(p) = (Ms s + Md d)(p) / 2,  (D u)(p + N/2) = (Ms s - Md d)(p) / 2,
+  // Ms[p][p'] = D[p][p'] + D[p][p'+N/2], Md[p][p'] = D[p][p'] - D[p][p'+N/2]:
+  // half the multiply-adds of D. Stored [p'][p] (MsPhT, MdPhT for Phi; MsphT,
+  // MdphT for phi).
+  C *MsPhT, *MdPhT, *MsphT, *MdphT;
   // D_r split into TF32 high and low halves in the tensor-core operand layout
   // (N_r padded to 16 rows x N_r padded to 8 columns, 8 x 4 core matrices).
   C *TcBhi, *TcBlo;
@@ -156,6 +163,7 @@ struct HostTables {
   Vec wr, wth, fluxw;
   Vec PthT, QthT, PThT, QThT, EpT, OpT, DrMc, DrMr;   // even/odd forms (see Tables)
   Vec PthA, QthA, PThA, QThA, EpTa, OpTa, DrMca, DrMra;  // even/odd forms of the transposes
+  Vec MsPhT, MdPhT, MsphT, MdphT;                     // pair-half Fourier derivatives
   Vec TcBhi, TcBlo;                                   // tensor-core operand of D_r
 };
 

@@ -144,17 +144,24 @@ __host__ __device__ inline int rad_spec(const Dims& d) {
 
 // ============================================================================
 // Angular pass. Thread: RB Theta rows k0.. x 4 column pairs (m, m + NP/2) of one block.
-// Shared layout: [PThT | QThT | DPhT | tile nb*S | sums/diffs nb*(S+8) |
-//                 transposed tile nb*(NP*UTP+8) | 6 nb per-block scalars]
+// Both contractions work on the pair halves s = F(m) + F(m+NP/2), d = F(m) -
+// F(m+NP/2): Theta through P, Q (DFS partner), Phi through Ms, Md (the
+// circulant Fourier derivative on the halves) -- each half the multiply-adds
+// of the dense product.
+// Shared layout: [PThT | QThT | MsPhT | MdPhT | tile nb*S | halves nb*(S+8) |
+//                 transposed halves nb*(NP*UTP+8) | 6 nb per-block scalars]
 template <typename C>
 __device__ __forceinline__ void angular_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
                                                 C* sD) {
-  const int NT = d.NT, NP = d.NP;
+  const int NT = d.NT, hP = d.NP / 2;
   for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
     sP[x] = t.PThT[x];
     sQ[x] = t.QThT[x];
   }
-  for (int x = threadIdx.x; x < NP * NP; x += blockDim.x) sD[x] = t.DPhT[x];
+  for (int x = threadIdx.x; x < hP * hP; x += blockDim.x) {
+    sD[x] = t.MsPhT[x];
+    sD[hP * hP + x] = t.MdPhT[x];
+  }
 }
 
 template <bool ASYNC, typename T, typename C>
@@ -168,9 +175,10 @@ __device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int n
 }
 
 // Preparation of a staged tile: coefficients, J, the sums and differences of
-// every Phi pair (for the Theta contraction and the pointwise terms), and the
-// transposed copy uT[m][k] (for the Phi contraction). Entry: su complete and
-// visible. Exit (after the caller's barrier): su is no longer read.
+// every Phi pair s[k][p], d[k][p] (for the Theta contraction and the pointwise
+// terms), and their transposed copies uT[p][k] = s, uT[NP/2 + p][k] = d (for the
+// Phi contraction). Entry: su complete and visible. Exit (after the caller's
+// barrier): su is no longer read.
 template <int NT_, int NP_, typename T, typename C>
 __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C>& t,
                                                 const C* su, C* sSD, C* uT, C* sc, int collision,
@@ -208,8 +216,8 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
     C* ut = uT + bb * US;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      ut[(p4 + c) * UTP + kk] = a[c];
-      ut[(p4 + hP + c) * UTP + kk] = b[c];
+      ut[(p4 + c) * UTP + kk] = s[c];
+      ut[(p4 + hP + c) * UTP + kk] = df[c];
     }
     if (collision && warp_J) {
       C acc = t.qdir[kk] * ((s[0] + s[1]) + (s[2] + s[3]));
@@ -252,11 +260,11 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
     const C* us = sSD + bb * SS;
     const C* ud = us + NT * hP;
     const C* ut = uT + bb * US;
-    C ps[RB][CB], qd[RB][CB], da[RB][CB], db[RB][CB];
+    C ps[RB][CB], qd[RB][CB], fs[RB][CB], fd[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int c = 0; c < CB; ++c) ps[r][c] = qd[r][c] = da[r][c] = db[r][c] = 0;
+      for (int c = 0; c < CB; ++c) ps[r][c] = qd[r][c] = fs[r][c] = fd[r][c] = 0;
 #pragma unroll
     for (int kk = 0; kk < NT; ++kk) {
       C sv[CB], dv[CB], P[RB], Q[RB];
@@ -273,18 +281,21 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
         }
       }
     }
+    const C* sMs = sD;
+    const C* sMd = sD + hP * hP;
 #pragma unroll
-    for (int mm = 0; mm < NP; ++mm) {
-      C A4[CB], B4[CB], uv[RB];
-      ld4<C>(sD + mm * NP + p0, A4);
-      ld4<C>(sD + mm * NP + p0 + hP, B4);
-      ldv<C, RB>(ut + mm * UTP + k0, uv);
+    for (int pp = 0; pp < hP; ++pp) {
+      C A4[CB], B4[CB], sv[RB], dv[RB];
+      ld4<C>(sMs + pp * hP + p0, A4);
+      ld4<C>(sMd + pp * hP + p0, B4);
+      ldv<C, RB>(ut + pp * UTP + k0, sv);
+      ldv<C, RB>(ut + (hP + pp) * UTP + k0, dv);
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
-          da[r][c] = fmac(A4[c], uv[r], da[r][c]);
-          db[r][c] = fmac(B4[c], uv[r], db[r][c]);
+          fs[r][c] = fmac(A4[c], sv[r], fs[r][c]);
+          fd[r][c] = fmac(B4[c], dv[r], fd[r][c]);
         }
       }
     }
@@ -292,11 +303,11 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
     const C ir = sc[4 * nb + bb], ct = sc[5 * nb + bb];
     const C J = sc[bb], kap = sc[nb + bb], eta = sc[2 * nb + bb], ks = sc[3 * nb + bb];
     const C src = eta + ks * J, kks = kap + ks;
-    C s1[CB], s2[CB];
+    C s1[CB], s2[CB];   // a_Phi / a_Theta at m and m + NP/2, with the 1/2 of the halves
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
-      s1[c] = t.sinP[p0 + c] * ct;
-      s2[c] = t.sinP[p0 + c + hP] * ct;
+      s1[c] = (C)0.5 * t.sinP[p0 + c] * ct;
+      s2[c] = (C)0.5 * t.sinP[p0 + c + hP] * ct;
     }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
@@ -310,8 +321,8 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
       T o1[CB], o2[CB];
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
-        C v1 = aT * (ps[r][c] + qd[r][c] + s1[c] * da[r][c]);
-        C v2 = aT * (ps[r][c] - qd[r][c] + s2[c] * db[r][c]);
+        C v1 = aT * (ps[r][c] + qd[r][c] + s1[c] * (fs[r][c] + fd[r][c]));
+        C v2 = aT * (ps[r][c] - qd[r][c] + s2[c] * (fs[r][c] - fd[r][c]));
         if (collision) {
           v1 += src - kks * (C)0.5 * (sv[c] + dv[c]);
           v2 += src - kks * (C)0.5 * (sv[c] - dv[c]);
