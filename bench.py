@@ -176,10 +176,20 @@ def even_odd_passes(dims, es):
             "radial": Nr >= 9 and (Nr // 2) % rbA == 0 and (NT * NP) % 4 == 0}
 
 
-def eo_kernel(name):
+def plane_square(dims):
+    """The library's square-grid plane pass (16 nodes on every angular axis)."""
+    return dims[3] == dims[4] == dims[5] == dims[6] == 16
+
+
+def eo_kernel(name, dims):
     """Kernel of the register-blocked even/odd form of a pass: persistent
-    k_angular_pp / k_plane_pp, one tile per CTA k_radial_eo."""
-    return "k_radial_eo" if name == "radial" else f"k_{name}_pp"
+    k_angular_pp / k_plane_pp (k_plane_sq on square grids), one tile per CTA
+    k_radial_eo."""
+    if name == "radial":
+        return "k_radial_eo"
+    if name == "plane" and plane_square(dims):
+        return "k_plane_sq"
+    return f"k_{name}_pp"
 
 
 def pass_work(dims, es):
@@ -195,7 +205,8 @@ def pass_work(dims, es):
         # dTh and dPh on the DFS pair halves (even/odd) or dense, J, coefficients, collision
         "angular": pts * ((2 * NT + 1 + NP + 1 if eo["angular"] else 4 * NT + 2 * NP) + 2 + 11),
         # dth on the DFS pair, dph, coefficients
-        "plane": pts * ((2 * Nt + 1 if eo["plane"] else 4 * Nt) + 2 * Np + 8),
+        "plane": pts * ((2 * Nt + 1 if eo["plane"] else 4 * Nt) +
+                        (Np + 1 if eo["plane"] and plane_square(dims) else 2 * Np) + 8),
         # dr (centro-antisymmetric halves), r term, Tau row, stage update
         "radial": pts * ((Nr + 1 if eo["radial"] else 2 * Nr) + 10),
     }
@@ -431,7 +442,7 @@ def run_ours(args, dims, wname):
     dname = names[dom]
     avg_ms = pass_ms[dom] / pass_n[dom]
     peaks, peak_src = _peaks()
-    kfam = eo_kernel(dname) if even_odd_passes(dims, es)[dname] else f"k_{dname}"
+    kfam = eo_kernel(dname, dims) if even_odd_passes(dims, es)[dname] else f"k_{dname}"
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     smax = peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = sms * 2 * FP64_FMA_PER_SM_CLK * smax * 1e6 / 1e12
@@ -520,7 +531,8 @@ def run_ours(args, dims, wname):
             d32 = int(np.argmax(pm[:3]))
             hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
             alu32 = fl32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e12
-            kf = eo_kernel(names[d32]) if even_odd_passes(dims, 4)[names[d32]] else f"k_{names[d32]}"
+            kf = (eo_kernel(names[d32], dims) if even_odd_passes(dims, 4)[names[d32]]
+                  else f"k_{names[d32]}")
             kn = (kname.get(names[d32], kf) if vprec in (ts.TS_TF32X3, ts.TS_BF16X3) else kf)
             kn += "<float>"
             line["variants"][vname] = {

@@ -591,28 +591,48 @@ k_plane_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C
 // per tile: a tile is (g, i) and KT consecutive Theta values, i.e. columns
 // w = kl*N + m (KT*N of them, contiguous in memory for every (theta, phi)).
 // Thread: RB theta rows x one phi pair (l, l + N/2) x 4 columns m0.. and the
-// 4 partner columns m0 + N/2.. of one Theta value. It owns both DFS pairs
-// that these columns form -- (l, m) with (l+N/2, m+N/2) and (l, m+N/2) with
-// (l+N/2, m) -- so each staged value it loads feeds twice the multiply-adds of
-// the general form. Sums/differences use a row pitch of KT*N + 8 so that the
-// 8 lanes of a 16-byte load phase hit distinct banks.
-// Shared layout: [PthT | QthT | DphT | 2 tiles N*N*KT*N | sums, diffs 2*N*(N/2)*(KT*N+8)]
-template <int N, int KT>
+// 4 partner columns m0 + N/2.. of one Theta value (RB = 2 in float, 1 in
+// double). It owns both DFS pairs that these columns form -- (l, m) with
+// (l+N/2, m+N/2) and (l, m+N/2) with (l+N/2, m) -- so each staged value it loads
+// feeds twice the multiply-adds of the general form, and it owns both halves
+// of the phi pair at each column, so the phi derivative acts on the pair halves
+// sigma = u(l) + u(l+N/2), delta = u(l) - u(l+N/2) through Ms, Md (half the
+// multiply-adds of the dense Fourier derivative). The staged tile is turned
+// into sigma (rows l < N/2) and delta (rows l + N/2) in place once the theta
+// sums are formed. Sums/differences use a row pitch of KT*N + 32 bytes so that
+// the lanes of a 16-byte load phase hit distinct banks.
+// Shared layout: [PthT | QthT | MsphT, MdphT | 2 tiles N*N*KT*N | theta sums, diffs]
+template <int N, int KT, typename C>
 struct PlaneSq {
-  static constexpr int W = KT * N, hp = N / 2, H4 = hp / 4, SP = W + 8, TS = N * N * W;
-  static constexpr int RB = kRBPlane, JR = N / RB;
+  static constexpr int W = KT * N, hp = N / 2, H4 = hp / 4, SP = W + 32 / (int)sizeof(C);
+  static constexpr int TS = N * N * W;
+  static constexpr int RB = sizeof(C) == 4 ? 2 : 1, JR = N / RB;
   static constexpr int units = JR * hp * KT * H4;
 };
 
 template <int N, int KT, typename C>
 size_t smem_plane_sq() {
-  using S = PlaneSq<N, KT>;
+  using S = PlaneSq<N, KT, C>;
   return (size_t)(3 * N * N + 2 * S::TS + 2 * N * S::hp * S::SP) * sizeof(C);
+}
+
+template <typename C>
+__device__ __forceinline__ void plane_sq_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
+                                              C* sD) {
+  const int Nt = d.Nt, hp = d.Np / 2;
+  for (int x = threadIdx.x; x < Nt * Nt; x += blockDim.x) {
+    sP[x] = t.PthT[x];
+    sQ[x] = t.QthT[x];
+  }
+  for (int x = threadIdx.x; x < hp * hp; x += blockDim.x) {
+    sD[x] = t.MsphT[x];
+    sD[hp * hp + x] = t.MdphT[x];
+  }
 }
 
 template <int N, int KT, typename T, typename C>
 __device__ __forceinline__ void plane_sq_load(const Dims& d, const T* U, long long tile, C* su) {
-  using S = PlaneSq<N, KT>;
+  using S = PlaneSq<N, KT, C>;
   const long long q = tile / (N / KT);
   const int k0 = (int)(tile - q * (N / KT)) * KT;
   const long long base = q * d.S_i + (long long)k0 * N;   // q = g*Nr + i
@@ -623,31 +643,52 @@ __device__ __forceinline__ void plane_sq_load(const Dims& d, const T* U, long lo
 }
 
 template <int N, int KT, typename T, typename C>
-__device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>& t, const C* su,
+__device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>& t, C* su,
                                               C* sSm, const C* sP, const C* sQ, const C* sD,
                                               T* __restrict__ K, C sgn, long long tile) {
-  using S = PlaneSq<N, KT>;
-  constexpr int RB = S::RB, CB = 4, W = S::W, hp = S::hp, SP = S::SP;
+  using S = PlaneSq<N, KT, C>;
+  constexpr int RB = S::RB, CB = 4, W = S::W, hp = S::hp, SP = S::SP, H4 = S::H4;
   const Dims& d = p.d;
   C* sDf = sSm + N * hp * SP;
   const long long q = tile / (N / KT);
   const int k0 = (int)(tile - q * (N / KT)) * KT;
   const int i = (int)(q % d.Nr);
   const long long base = q * d.S_i + (long long)k0 * N;
-  // sums and differences with the partner (phi + pi, Phi + pi) once per pair
-  for (int x = threadIdx.x; x < N * hp * (W / 4); x += blockDim.x) {
-    const int w4 = (x % (W / 4)) * 4, jl = x / (W / 4), l = jl % hp, jj = jl / hp;
-    const int m4 = w4 % N, w4h = w4 - m4 + (m4 + hp) % N;
-    C a[4], b[4], s[4], df[4];
-    ld4<C>(su + (jj * N + l) * W + w4, a);
-    ld4<C>(su + (jj * N + l + hp) * W + w4h, b);
+  // per (theta row, phi pair, 4 columns m4.. and m4 + N/2..): the theta sums and
+  // differences with the DFS partner (phi + pi, Phi + pi), then the phi pair
+  // halves sigma, delta written over the four staged rows this thread read
+  for (int x = threadIdx.x; x < N * hp * KT * H4; x += blockDim.x) {
+    const int mq = x % H4, r1 = x / H4, kl = r1 % KT, r2 = r1 / KT, l = r2 % hp, jj = r2 / hp;
+    const int wA = kl * N + mq * 4, wB = wA + hp;
+    C* rl = su + (jj * N + l) * W;
+    C* rh = su + (jj * N + l + hp) * W;
+    C a0[4], a1[4], b0[4], b1[4], t0[4], t1[4], t2[4], t3[4];
+    ld4<C>(rl + wA, a0);
+    ld4<C>(rl + wB, a1);
+    ld4<C>(rh + wA, b0);
+    ld4<C>(rh + wB, b1);
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
-      s[cc] = a[cc] + b[cc];
-      df[cc] = a[cc] - b[cc];
+      t0[cc] = a0[cc] + b1[cc];   // theta pair (l, m) with (l + N/2, m + N/2)
+      t1[cc] = a0[cc] - b1[cc];
+      t2[cc] = a1[cc] + b0[cc];   // theta pair (l, m + N/2) with (l + N/2, m)
+      t3[cc] = a1[cc] - b0[cc];
     }
-    st4<C>(sSm + (jj * hp + l) * SP + w4, s);
-    st4<C>(sDf + (jj * hp + l) * SP + w4, df);
+    st4<C>(sSm + (jj * hp + l) * SP + wA, t0);
+    st4<C>(sDf + (jj * hp + l) * SP + wA, t1);
+    st4<C>(sSm + (jj * hp + l) * SP + wB, t2);
+    st4<C>(sDf + (jj * hp + l) * SP + wB, t3);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      t0[cc] = a0[cc] + b0[cc];   // phi pair halves at column m
+      t1[cc] = a0[cc] - b0[cc];
+      t2[cc] = a1[cc] + b1[cc];   // and at column m + N/2
+      t3[cc] = a1[cc] - b1[cc];
+    }
+    st4<C>(rl + wA, t0);
+    st4<C>(rh + wA, t1);
+    st4<C>(rl + wB, t2);
+    st4<C>(rh + wB, t3);
   }
   __syncthreads();
   const C ir = t.inv_r[i];
@@ -657,13 +698,13 @@ __device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>&
     const int m0 = mq * CB, j0 = jr * RB;
     const int wA = kl * N + m0, wB = wA + hp;      // columns m0.. and m0 + N/2..
     C psA[RB][CB], qdA[RB][CB], psB[RB][CB], qdB[RB][CB];
-    C daA[RB][CB], daB[RB][CB], dbA[RB][CB], dbB[RB][CB];
+    C fsA[RB][CB], fdA[RB][CB], fsB[RB][CB], fdB[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc)
-        psA[r][cc] = qdA[r][cc] = psB[r][cc] = qdB[r][cc] = daA[r][cc] = daB[r][cc] =
-            dbA[r][cc] = dbB[r][cc] = 0;
+        psA[r][cc] = qdA[r][cc] = psB[r][cc] = qdB[r][cc] = fsA[r][cc] = fdA[r][cc] =
+            fsB[r][cc] = fdB[r][cc] = 0;
 #pragma unroll 8
     for (int jj = 0; jj < N; ++jj) {
       C sa[CB], da_[CB], sb[CB], db_[CB], P[RB], Q[RB];
@@ -684,31 +725,33 @@ __device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>&
         }
       }
     }
-#pragma unroll 8
-    for (int ll = 0; ll < N; ++ll) {
-      const C Dl = sD[ll * N + l], Dh = sD[ll * N + l + hp];
+#pragma unroll
+    for (int ll = 0; ll < hp; ++ll) {
+      const C Ms = sD[ll * hp + l], Md = sD[hp * hp + ll * hp + l];
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
-        C a[CB], b[CB];
-        ld4<C>(su + ((j0 + r) * N + ll) * W + wA, a);
-        ld4<C>(su + ((j0 + r) * N + ll) * W + wB, b);
+        C sa[CB], da_[CB], sb[CB], db_[CB];
+        ld4<C>(su + ((j0 + r) * N + ll) * W + wA, sa);
+        ld4<C>(su + ((j0 + r) * N + ll + hp) * W + wA, da_);
+        ld4<C>(su + ((j0 + r) * N + ll) * W + wB, sb);
+        ld4<C>(su + ((j0 + r) * N + ll + hp) * W + wB, db_);
 #pragma unroll
         for (int cc = 0; cc < CB; ++cc) {
-          daA[r][cc] = fmac(Dl, a[cc], daA[r][cc]);
-          daB[r][cc] = fmac(Dl, b[cc], daB[r][cc]);
-          dbA[r][cc] = fmac(Dh, a[cc], dbA[r][cc]);
-          dbB[r][cc] = fmac(Dh, b[cc], dbB[r][cc]);
+          fsA[r][cc] = fmac(Ms, sa[cc], fsA[r][cc]);
+          fdA[r][cc] = fmac(Md, da_[cc], fdA[r][cc]);
+          fsB[r][cc] = fmac(Ms, sb[cc], fsB[r][cc]);
+          fdB[r][cc] = fmac(Md, db_[cc], fdB[r][cc]);
         }
       }
     }
     const C sTk = sgn * t.sinT[k0 + kl] * ir;
-    C cA[CB], sA[CB], cB[CB], sB[CB];
+    C cA[CB], sA[CB], cB[CB], sB[CB];   // a_phi carries the 1/2 of the phi pair halves
 #pragma unroll
     for (int cc = 0; cc < CB; ++cc) {
       cA[cc] = sTk * t.cosP[m0 + cc];
-      sA[cc] = sTk * t.sinP[m0 + cc];
+      sA[cc] = (C)0.5 * sTk * t.sinP[m0 + cc];
       cB[cc] = sTk * t.cosP[m0 + hp + cc];
-      sB[cc] = sTk * t.sinP[m0 + hp + cc];
+      sB[cc] = (C)0.5 * sTk * t.sinP[m0 + hp + cc];
     }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
@@ -723,10 +766,14 @@ __device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>&
       ld4<T>(p1 + hp, k1b);
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
-        k0a[cc] = (T)((C)k0a[cc] + cA[cc] * (psA[r][cc] + qdA[r][cc]) + sA[cc] * isn * daA[r][cc]);
-        k0b[cc] = (T)((C)k0b[cc] + cB[cc] * (psB[r][cc] + qdB[r][cc]) + sB[cc] * isn * daB[r][cc]);
-        k1a[cc] = (T)((C)k1a[cc] + cA[cc] * (psB[r][cc] - qdB[r][cc]) + sA[cc] * isn * dbA[r][cc]);
-        k1b[cc] = (T)((C)k1b[cc] + cB[cc] * (psA[r][cc] - qdA[r][cc]) + sB[cc] * isn * dbB[r][cc]);
+        k0a[cc] = (T)((C)k0a[cc] + cA[cc] * (psA[r][cc] + qdA[r][cc]) +
+                      sA[cc] * isn * (fsA[r][cc] + fdA[r][cc]));
+        k0b[cc] = (T)((C)k0b[cc] + cB[cc] * (psB[r][cc] + qdB[r][cc]) +
+                      sB[cc] * isn * (fsB[r][cc] + fdB[r][cc]));
+        k1a[cc] = (T)((C)k1a[cc] + cA[cc] * (psB[r][cc] - qdB[r][cc]) +
+                      sA[cc] * isn * (fsA[r][cc] - fdA[r][cc]));
+        k1b[cc] = (T)((C)k1b[cc] + cB[cc] * (psA[r][cc] - qdA[r][cc]) +
+                      sB[cc] * isn * (fsB[r][cc] - fdB[r][cc]));
       }
       st4<T>(p0, k0a);
       st4<T>(p0 + hp, k0b);
@@ -740,7 +787,7 @@ template <typename T, typename C, int N, int KT>
 __global__ void __launch_bounds__(kThreads, 2)
 k_plane_sq(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
            long long ntiles) {
-  using S = PlaneSq<N, KT>;
+  using S = PlaneSq<N, KT, C>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims& d = p.d;
   C* sP = reinterpret_cast<C*>(smem_raw);
@@ -748,7 +795,7 @@ k_plane_sq(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C
   C* sD = sQ + N * N;
   C* buf0 = sD + N * N;
   C* sSm = buf0 + 2 * S::TS;
-  plane_rb_mats<C>(t, d, sP, sQ, sD);
+  plane_sq_mats<C>(t, d, sP, sQ, sD);
   long long tile = blockIdx.x;
   if (tile < ntiles) plane_sq_load<N, KT, T, C>(d, U, tile, buf0);
   cp_async_commit();

@@ -209,8 +209,9 @@ cudaError_t Launch<T, C>::plane(const Problem& p, const Tables<C>& t, const T* U
     switch (plane_spec(d, c)) {
       case 8: return plane_pp<T, C, 8>(p, t, U, K, sgn, c, nct, s);
       case 16:
+        // two Theta values per tile in float (RB 2), one in double (RB 1): 256 units
         if constexpr (sizeof(C) == 4) return plane_sq<T, C, 16, 2>(p, t, U, K, sgn, s);
-        else return plane_pp<T, C, 16>(p, t, U, K, sgn, c, nct, s);
+        else return plane_sq<T, C, 16, 1>(p, t, U, K, sgn, s);
       case 24: return plane_pp<T, C, 24>(p, t, U, K, sgn, c, nct, s);
       case 32: return plane_pp<T, C, 32>(p, t, U, K, sgn, c, nct, s);
       default: return plane_pp<T, C, 0>(p, t, U, K, sgn, c, nct, s);
