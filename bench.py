@@ -203,7 +203,9 @@ def pass_work(dims, es):
     eo = even_odd_passes(dims, es)
     flops = {
         # dTh and dPh on the DFS pair halves (even/odd) or dense, J, coefficients, collision
-        "angular": pts * ((2 * NT + 1 + NP + 1 if eo["angular"] else 4 * NT + 2 * NP) + 2 + 11),
+        # (even/odd: Theta folded twice -- DFS pair and Theta -> pi - Theta -- and Phi
+        # on the pair halves: N_Theta/2 + N_Phi/2 multiply-adds per point)
+        "angular": pts * ((NT + 3 + NP + 1 if eo["angular"] else 4 * NT + 2 * NP) + 2 + 11),
         # dth on the DFS pair, dph, coefficients
         "plane": pts * ((2 * Nt + 1 if eo["plane"] else 4 * Nt) +
                         (Np + 1 if eo["plane"] and plane_square(dims) else 2 * Np) + 8),

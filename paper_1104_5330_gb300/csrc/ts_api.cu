@@ -190,7 +190,8 @@ std::vector<const Vec*> device_list(const HostTables& h, std::vector<Vec>& tmp) 
           &h.PthT, &h.QthT, &h.PThT, &h.QThT, &h.EpT, &h.OpT, &h.DrMc, &h.DrMr,
           &h.TcBhi, &h.TcBlo,
           &h.PthA, &h.QthA, &h.PThA, &h.QThA, &h.EpTa, &h.OpTa, &h.DrMca, &h.DrMra,
-          &h.MsPhT, &h.MdPhT, &h.MsphT, &h.MdphT};
+          &h.MsPhT, &h.MdPhT, &h.MsphT, &h.MdphT,
+          &h.PeThT, &h.PoThT, &h.QeThT, &h.QoThT, &h.PethT, &h.PothT, &h.QethT, &h.QothT};
 }
 
 // Even/odd forms of the derivative matrices (see Tables in ts_internal.h).
@@ -340,6 +341,24 @@ void even_odd_tables(HostTables& h) {
   };
   halves(h.DPh, (int)h.Phi.size(), h.MsPhT, h.MdPhT);
   halves(h.Dph, (int)h.phi.size(), h.MsphT, h.MdphT);
+  // P and Q (from their transposed [in][out] forms) folded over k -> n-1-k:
+  // FeT[k'][k] = P[k][k'] + P[k][n-1-k'], FoT[k'][k] = P[k][k'] - P[k][n-1-k']
+  auto fold = [](const Vec& PT, int n, Vec& FeT, Vec& FoT) {
+    const int h = n / 2;
+    FeT.assign((size_t)h * h, 0.0);
+    FoT.assign((size_t)h * h, 0.0);
+    for (int k = 0; k < h; ++k)
+      for (int kp = 0; kp < h; ++kp) {
+        const double a = PT[(size_t)kp * n + k], b = PT[(size_t)(n - 1 - kp) * n + k];
+        FeT[(size_t)kp * h + k] = a + b;
+        FoT[(size_t)kp * h + k] = a - b;
+      }
+  };
+  const int nT = (int)h.Theta.size(), nt = (int)h.theta.size();
+  fold(h.PThT, nT, h.PeThT, h.PoThT);
+  fold(h.QThT, nT, h.QeThT, h.QoThT);
+  fold(h.PthT, nt, h.PethT, h.PothT);
+  fold(h.QthT, nt, h.QethT, h.QothT);
 }
 
 template <typename C>
@@ -360,7 +379,9 @@ cudaError_t upload_tables(const HostTables& h, void** mem, Tables<C>* t) {
                  &t->PthT, &t->QthT, &t->PThT, &t->QThT, &t->EpT, &t->OpT, &t->DrMc, &t->DrMr,
                  &t->TcBhi, &t->TcBlo,
                  &t->PthA, &t->QthA, &t->PThA, &t->QThA, &t->EpTa, &t->OpTa, &t->DrMca,
-                 &t->DrMra, &t->MsPhT, &t->MdPhT, &t->MsphT, &t->MdphT};
+                 &t->DrMra, &t->MsPhT, &t->MdPhT, &t->MsphT, &t->MdphT,
+                 &t->PeThT, &t->PoThT, &t->QeThT, &t->QoThT, &t->PethT, &t->PothT,
+                 &t->QethT, &t->QothT};
   size_t off = 0;
   for (size_t a = 0; a < list.size(); ++a) {
     for (size_t b = 0; b < list[a]->size(); ++b) host[off + b] = (C)(*list[a])[b];

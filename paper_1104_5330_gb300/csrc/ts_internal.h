@@ -52,6 +52,11 @@ struct Tables {
   // half the multiply-adds of D. Stored [p'][p] (MsPhT, MdPhT for Phi; MsphT,
   // MdphT for phi).
   C *MsPhT, *MdPhT, *MsphT, *MdphT;
+  // P and Q of the DFS Theta (and theta) circles are centro-antisymmetric (the
+  // nodes are symmetric about pi/2 and the derivative is odd): folded onto
+  // n/2 output pairs (k, n-1-k) like D_r, PeT[k'][k] = P[k][k'] + P[k][n-1-k'],
+  // PoT[k'][k] = P[k][k'] - P[k][n-1-k'] (k, k' < n/2), Q alike.
+  C *PeThT, *PoThT, *QeThT, *QoThT, *PethT, *PothT, *QethT, *QothT;
   // D_r split into TF32 high and low halves in the tensor-core operand layout
   // (N_r padded to 16 rows x N_r padded to 8 columns, 8 x 4 core matrices).
   C *TcBhi, *TcBlo;
@@ -67,16 +72,17 @@ struct TileParams {
   int rb = 0;
 };
 
-// Output rows per thread of the register-blocked passes: angular and radial 4
-// in float, 2 in double; plane 2.
+// Output rows per thread of the register-blocked passes: angular 2 in float and
+// 1 in double (each with its Theta mirror rows), radial 4 in float and 2 in
+// double, plane 2.
 constexpr int kRBPlane = 2;
-__host__ __device__ constexpr int rb_ang(int elem_bytes) { return elem_bytes == 4 ? 4 : 2; }
+__host__ __device__ constexpr int rb_ang(int elem_bytes) { return elem_bytes == 4 ? 2 : 1; }
 __host__ __device__ constexpr int rb_rad(int elem_bytes) { return elem_bytes == 4 ? 4 : 2; }
 
 // Which forward passes of a grid can use the register-blocked even/odd form.
 inline int rb_mask(const Dims& d, int elem_bytes, int n64) {
   int m = 0;
-  if (d.NT % rb_ang(elem_bytes) == 0 && d.NP % 8 == 0) m |= 1;
+  if (d.NT % (2 * rb_ang(elem_bytes)) == 0 && d.NP % 8 == 0) m |= 1;
   if (d.Nt % kRBPlane == 0 && d.Np % 2 == 0 && d.NP % 8 == 0) m |= 2;
   if (d.Nr >= 9 && (d.Nr / 2) % rb_rad(elem_bytes) == 0 && (d.NT * d.NP) % 4 == 0 && n64 <= 2)
     m |= 4;
@@ -164,6 +170,7 @@ struct HostTables {
   Vec PthT, QthT, PThT, QThT, EpT, OpT, DrMc, DrMr;   // even/odd forms (see Tables)
   Vec PthA, QthA, PThA, QThA, EpTa, OpTa, DrMca, DrMra;  // even/odd forms of the transposes
   Vec MsPhT, MdPhT, MsphT, MdphT;                     // pair-half Fourier derivatives
+  Vec PeThT, PoThT, QeThT, QoThT, PethT, PothT, QethT, QothT;   // folded P, Q
   Vec TcBhi, TcBlo;                                   // tensor-core operand of D_r
 };
 

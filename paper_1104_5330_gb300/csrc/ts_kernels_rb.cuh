@@ -143,20 +143,27 @@ __host__ __device__ inline int rad_spec(const Dims& d) {
 }
 
 // ============================================================================
-// Angular pass. Thread: RB Theta rows k0.. x 4 column pairs (m, m + NP/2) of one block.
-// Both contractions work on the pair halves s = F(m) + F(m+NP/2), d = F(m) -
-// F(m+NP/2): Theta through P, Q (DFS partner), Phi through Ms, Md (the
-// circulant Fourier derivative on the halves) -- each half the multiply-adds
-// of the dense product.
-// Shared layout: [PThT | QThT | MsPhT | MdPhT | tile nb*S | halves nb*(S+8) |
-//                 transposed halves nb*(NP*UTP+8) | 6 nb per-block scalars]
+// Angular pass. Thread: RB Theta rows k0.. and their mirror rows NT-1-k0-.. x 4
+// column pairs (m, m + NP/2) of one block. Both contractions work on the pair
+// halves s = F(m) + F(m+NP/2), d = F(m) - F(m+NP/2):
+//  * Theta through P, Q (DFS partner). P and Q are centro-antisymmetric (the
+//    Theta nodes are symmetric about pi/2 and the derivative is odd), so rows k
+//    and NT-1-k come from the Theta-even/odd parts e = h(k') + h(NT-1-k'),
+//    o = h(k') - h(NT-1-k') of each half h (k' < NT/2) through the folded
+//    matrices Pe, Po, Qe, Qo: a quarter of the dense multiply-adds;
+//  * Phi through Ms, Md (the circulant Fourier derivative on the halves): half.
+// Shared layout: [PeT | PoT | QeT | QoT (NT/2 x NT/2 each) | MsPhT | MdPhT |
+//                 tile nb*S | folded halves nb*(S+8) | transposed halves
+//                 nb*(NP*UTP+8) | 6 nb per-block scalars]
 template <typename C>
 __device__ __forceinline__ void angular_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
                                                 C* sD) {
-  const int NT = d.NT, hP = d.NP / 2;
-  for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
-    sP[x] = t.PThT[x];
-    sQ[x] = t.QThT[x];
+  const int hT = d.NT / 2, hP = d.NP / 2;
+  for (int x = threadIdx.x; x < hT * hT; x += blockDim.x) {
+    sP[x] = t.PeThT[x];
+    sP[hT * hT + x] = t.PoThT[x];
+    sQ[x] = t.QeThT[x];
+    sQ[hT * hT + x] = t.QoThT[x];
   }
   for (int x = threadIdx.x; x < hP * hP; x += blockDim.x) {
     sD[x] = t.MsPhT[x];
@@ -174,18 +181,19 @@ __device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int n
   for (int x = 4 * threadIdx.x; x < nbb * S; x += 4 * blockDim.x) copy4<ASYNC, T, C>(su + x, src + x);
 }
 
-// Preparation of a staged tile: coefficients, J, the sums and differences of
-// every Phi pair s[k][p], d[k][p] (for the Theta contraction and the pointwise
-// terms), and their transposed copies uT[p][k] = s, uT[NP/2 + p][k] = d (for the
-// Phi contraction). Entry: su complete and visible. Exit (after the caller's
-// barrier): su is no longer read.
+// Preparation of a staged tile: coefficients, J, the folded halves
+// [se | so | de | do] ([k' < NT/2][p < NP/2] each) for the Theta contraction and
+// the pointwise terms, and the transposed halves uT[p][k] = s, uT[NP/2 + p][k] =
+// d for the Phi contraction. Entry: su complete and visible. Exit (after the
+// caller's barrier): su is no longer read.
 template <int NT_, int NP_, typename T, typename C>
 __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C>& t,
                                                 const C* su, C* sSD, C* uT, C* sc, int collision,
                                                 int nb, long long tile) {
   const Dims& d = p.d;
-  const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2;
+  const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2, hT = NT / 2;
   const int UTP = ang_utp<C>(NT), H4 = hP / 4, SS = ang_ss(NT, NP), US = ang_us<C>(NT, NP);
+  const int Q4 = hT * hP;   // one folded half
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // once per block
@@ -197,32 +205,60 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
     sc[4 * nb + x] = t.inv_r[i];
     sc[5 * nb + x] = t.cot_th[j];
   }
-  // When one warp covers exactly one block here, J comes out of this loop by
-  // a warp reduction; otherwise from a separate pass over the block.
-  const bool warp_J = NT * H4 == 32;
+  // When the threads of one block form an aligned power-of-two group of at
+  // most a warp, J comes out of this loop by a segmented warp reduction;
+  // otherwise from a separate pass over the block.
+  const int tpb = hT * H4;
+  const bool warp_J = tpb <= 32 && (tpb & (tpb - 1)) == 0;
+  // With the warp reduction the trip count is rounded up to whole warps
+  // (blockDim.x is a multiple of 32), so every lane of a warp takes part in
+  // every shuffle; lanes past the tile contribute zero and store nothing.
+  const int nx = nbb * tpb, nxw = warp_J ? (nx + 31) / 32 * 32 : nx;
   // lanes run over k fastest: the transposing stores of a warp hit distinct banks
-  for (int x = threadIdx.x; x < nbb * H4 * NT; x += blockDim.x) {
-    const int kk = x % NT, rest = x / NT, p4 = (rest % H4) * 4, bb = rest / H4;
-    C a[4], b[4], s[4], df[4];
-    ld4<C>(su + bb * S + kk * NP + p4, a);
-    ld4<C>(su + bb * S + kk * NP + p4 + hP, b);
+  for (int x = threadIdx.x; x < nxw; x += blockDim.x) {
+    const bool act = x < nx;
+    const int kk = x % hT, rest = x / hT, p4 = (rest % H4) * 4, bb = rest / H4;
+    const int km = NT - 1 - kk;
+    C a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0}, b2[4] = {0, 0, 0, 0};
+    if (act) {
+      ld4<C>(su + bb * S + kk * NP + p4, a);
+      ld4<C>(su + bb * S + kk * NP + p4 + hP, b);
+      ld4<C>(su + bb * S + km * NP + p4, a2);
+      ld4<C>(su + bb * S + km * NP + p4 + hP, b2);
+    }
+    C s[4], df[4], s2[4], d2[4], e1[4], o1[4], e2[4], o2[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       s[c] = a[c] + b[c];
       df[c] = a[c] - b[c];
+      s2[c] = a2[c] + b2[c];
+      d2[c] = a2[c] - b2[c];
+      e1[c] = s[c] + s2[c];
+      o1[c] = s[c] - s2[c];
+      e2[c] = df[c] + d2[c];
+      o2[c] = df[c] - d2[c];
     }
-    st4<C>(sSD + bb * SS + kk * hP + p4, s);
-    st4<C>(sSD + bb * SS + NT * hP + kk * hP + p4, df);
-    C* ut = uT + bb * US;
+    if (act) {
+      C* q = sSD + bb * SS + kk * hP + p4;
+      st4<C>(q, e1);
+      st4<C>(q + Q4, o1);
+      st4<C>(q + 2 * Q4, e2);
+      st4<C>(q + 3 * Q4, o2);
+      C* ut = uT + bb * US;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      ut[(p4 + c) * UTP + kk] = s[c];
-      ut[(p4 + hP + c) * UTP + kk] = df[c];
+      for (int c = 0; c < 4; ++c) {
+        ut[(p4 + c) * UTP + kk] = s[c];
+        ut[(p4 + c) * UTP + km] = s2[c];
+        ut[(p4 + hP + c) * UTP + kk] = df[c];
+        ut[(p4 + hP + c) * UTP + km] = d2[c];
+      }
     }
-    if (collision && warp_J) {
-      C acc = t.qdir[kk] * ((s[0] + s[1]) + (s[2] + s[3]));
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if ((threadIdx.x & 31) == 0) sc[bb] = acc;
+    if (collision && warp_J) {   // warp-uniform: the trip count covers whole warps
+      C acc = act ? t.qdir[kk] * ((s[0] + s[1]) + (s[2] + s[3])) +
+                        t.qdir[km] * ((s2[0] + s2[1]) + (s2[2] + s2[3]))
+                  : (C)0;
+      for (int o = tpb >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (act && (x % tpb) == 0) sc[bb] = acc;
     }
   }
   if (collision && !warp_J) {
@@ -245,57 +281,75 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
                                                    int nb, long long tile) {
   constexpr int RB = RBAng<C>::v, CB = 4;
   const Dims& d = p.d;
-  const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2;
+  const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2, hT = NT / 2;
   const int UTP = ang_utp<C>(NT), SS = ang_ss(NT, NP), US = ang_us<C>(NT, NP);
+  const int Q4 = hT * hP;
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
-  const int KR = NT / RB, PC = hP / CB;
+  const int KR = hT / RB, PC = hP / CB;
   // unit = (pc, 4 blocks, kr, block group): a 16-byte load phase spans 4 blocks
   const int units = ((nbb + 3) / 4) * 4 * KR * PC;
+  const C* sPe = sP;
+  const C* sPo = sP + hT * hT;
+  const C* sQe = sQ;
+  const C* sQo = sQ + hT * hT;
+  const C* sMs = sD;
+  const C* sMd = sD + hP * hP;
   for (int unit = threadIdx.x; unit < units; unit += blockDim.x) {
     const int pc = unit % PC, r1 = unit / PC, b4 = r1 % 4, r2 = r1 / 4, kr = r2 % KR;
     const int bb = (r2 / KR) * 4 + b4;
     if (bb >= nbb) continue;
-    const int p0 = pc * CB, k0 = kr * RB;
-    const C* us = sSD + bb * SS;
-    const C* ud = us + NT * hP;
+    const int p0 = pc * CB, k0 = kr * RB, k1 = NT - RB - k0;   // mirror rows k1.. (reversed)
+    const C* qb = sSD + bb * SS;
     const C* ut = uT + bb * US;
-    C ps[RB][CB], qd[RB][CB], fs[RB][CB], fd[RB][CB];
+    C aE[RB][CB], aO[RB][CB], bE[RB][CB], bO[RB][CB];
+    C fs[RB][CB], fd[RB][CB], gs[RB][CB], gd[RB][CB];
 #pragma unroll
     for (int r = 0; r < RB; ++r)
 #pragma unroll
-      for (int c = 0; c < CB; ++c) ps[r][c] = qd[r][c] = fs[r][c] = fd[r][c] = 0;
+      for (int c = 0; c < CB; ++c)
+        aE[r][c] = aO[r][c] = bE[r][c] = bO[r][c] = fs[r][c] = fd[r][c] = gs[r][c] =
+            gd[r][c] = 0;
 #pragma unroll
-    for (int kk = 0; kk < NT; ++kk) {
-      C sv[CB], dv[CB], P[RB], Q[RB];
-      ld4<C>(us + kk * hP + p0, sv);
-      ld4<C>(ud + kk * hP + p0, dv);
-      ldv<C, RB>(sP + kk * NT + k0, P);
-      ldv<C, RB>(sQ + kk * NT + k0, Q);
+    for (int kk = 0; kk < hT; ++kk) {
+      C ev[CB], ov[CB], ew[CB], ow[CB], Pe[RB], Po[RB], Qe[RB], Qo[RB];
+      const C* qk = qb + kk * hP + p0;
+      ld4<C>(qk, ev);
+      ld4<C>(qk + Q4, ov);
+      ld4<C>(qk + 2 * Q4, ew);
+      ld4<C>(qk + 3 * Q4, ow);
+      ldv<C, RB>(sPe + kk * hT + k0, Pe);
+      ldv<C, RB>(sPo + kk * hT + k0, Po);
+      ldv<C, RB>(sQe + kk * hT + k0, Qe);
+      ldv<C, RB>(sQo + kk * hT + k0, Qo);
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
 #pragma unroll
         for (int r = 0; r < RB; ++r) {
-          ps[r][c] = fmac(P[r], sv[c], ps[r][c]);
-          qd[r][c] = fmac(Q[r], dv[c], qd[r][c]);
+          aE[r][c] = fmac(Pe[r], ev[c], aE[r][c]);
+          aO[r][c] = fmac(Po[r], ov[c], aO[r][c]);
+          bE[r][c] = fmac(Qe[r], ew[c], bE[r][c]);
+          bO[r][c] = fmac(Qo[r], ow[c], bO[r][c]);
         }
       }
     }
-    const C* sMs = sD;
-    const C* sMd = sD + hP * hP;
 #pragma unroll
     for (int pp = 0; pp < hP; ++pp) {
-      C A4[CB], B4[CB], sv[RB], dv[RB];
+      C A4[CB], B4[CB], sv[RB], dv[RB], sw[RB], dw[RB];
       ld4<C>(sMs + pp * hP + p0, A4);
       ld4<C>(sMd + pp * hP + p0, B4);
       ldv<C, RB>(ut + pp * UTP + k0, sv);
       ldv<C, RB>(ut + (hP + pp) * UTP + k0, dv);
+      ldv<C, RB>(ut + pp * UTP + k1, sw);
+      ldv<C, RB>(ut + (hP + pp) * UTP + k1, dw);
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
           fs[r][c] = fmac(A4[c], sv[r], fs[r][c]);
           fd[r][c] = fmac(B4[c], dv[r], fd[r][c]);
+          gs[r][c] = fmac(A4[c], sw[r], gs[r][c]);
+          gd[r][c] = fmac(B4[c], dw[r], gd[r][c]);
         }
       }
     }
@@ -309,30 +363,53 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
       s1[c] = (C)0.5 * t.sinP[p0 + c] * ct;
       s2[c] = (C)0.5 * t.sinP[p0 + c + hP] * ct;
     }
+    // row k = k0 + r (side 0) and its mirror NT-1-k = k1 + RB-1-r (side 1)
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const int k = k0 + r;
-      const C aT = sgn * -t.sinT[k] * ir;
-      C sv[CB], dv[CB];   // F at (k, m) and (k, m + NP/2) from the pair's sum and difference
-      if (collision) {
-        ld4<C>(us + k * hP + p0, sv);
-        ld4<C>(ud + k * hP + p0, dv);
-      }
-      T o1[CB], o2[CB];
+    for (int side = 0; side < 2; ++side) {
 #pragma unroll
-      for (int c = 0; c < CB; ++c) {
-        C v1 = aT * (ps[r][c] + qd[r][c] + s1[c] * (fs[r][c] + fd[r][c]));
-        C v2 = aT * (ps[r][c] - qd[r][c] + s2[c] * (fs[r][c] - fd[r][c]));
-        if (collision) {
-          v1 += src - kks * (C)0.5 * (sv[c] + dv[c]);
-          v2 += src - kks * (C)0.5 * (sv[c] - dv[c]);
+      for (int r = 0; r < RB; ++r) {
+        const int k = side ? NT - 1 - k0 - r : k0 + r;
+        const int rm = side ? RB - 1 - r : r;   // index of row k in the mirror loads
+        const C sg = side ? (C)-1 : (C)1;
+        const C aT = sgn * -t.sinT[k] * ir;
+        C ps[CB], qd[CB], fa[CB], fb[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          ps[c] = (C)0.5 * (aO[r][c] + sg * aE[r][c]);
+          qd[c] = (C)0.5 * (bO[r][c] + sg * bE[r][c]);
+          fa[c] = side ? gs[rm][c] : fs[r][c];
+          fb[c] = side ? gd[rm][c] : fd[r][c];
         }
-        o1[c] = (T)v1;
-        o2[c] = (T)v2;
+        C sv[CB], dv[CB];   // F at (k, m), (k, m + NP/2) from the folded halves
+        if (collision) {
+          C e1[CB], o1[CB], e2[CB], o2[CB];
+          const int kk = k0 + r;
+          ld4<C>(qb + kk * hP + p0, e1);
+          ld4<C>(qb + Q4 + kk * hP + p0, o1);
+          ld4<C>(qb + 2 * Q4 + kk * hP + p0, e2);
+          ld4<C>(qb + 3 * Q4 + kk * hP + p0, o2);
+#pragma unroll
+          for (int c = 0; c < CB; ++c) {
+            sv[c] = (C)0.5 * (e1[c] + sg * o1[c]);
+            dv[c] = (C)0.5 * (e2[c] + sg * o2[c]);
+          }
+        }
+        T o1v[CB], o2v[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          C v1 = aT * (ps[c] + qd[c] + s1[c] * (fa[c] + fb[c]));
+          C v2 = aT * (ps[c] - qd[c] + s2[c] * (fa[c] - fb[c]));
+          if (collision) {
+            v1 += src - kks * (C)0.5 * (sv[c] + dv[c]);
+            v2 += src - kks * (C)0.5 * (sv[c] - dv[c]);
+          }
+          o1v[c] = (T)v1;
+          o2v[c] = (T)v2;
+        }
+        T* out = K + blk * S + k * NP + p0;
+        st4<T>(out, o1v);
+        st4<T>(out + hP, o2v);
       }
-      T* out = K + blk * S + k * NP + p0;
-      st4<T>(out, o1);
-      st4<T>(out + hP, o2);
     }
   }
 }

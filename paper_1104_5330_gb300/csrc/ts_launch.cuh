@@ -84,7 +84,8 @@ template <typename T, typename C>
 static int angular_nb(const Dims& d, int ntiles, bool rb = false) {
   const int S = d.NT * d.NP;
   if (rb && ntiles == 1) {
-    const int per = (d.NT / rb_ang((int)sizeof(C))) * (d.NP / 8);  // threads' units per block
+    // threads' units per block: RB rows with their mirrors, 4 column pairs
+    const int per = (d.NT / 2 / rb_ang((int)sizeof(C))) * (d.NP / 8);
     int nb = std::max(1, (kThreads + per - 1) / per);
     while (nb > 1 && smem_angular<C>(d, nb, true) > kSmemHalf) --nb;
     return nb;
