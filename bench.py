@@ -207,8 +207,9 @@ def pass_work(dims, es):
         # on the pair halves: N_Theta/2 + N_Phi/2 multiply-adds per point)
         "angular": pts * ((NT + 3 + NP + 1 if eo["angular"] else 4 * NT + 2 * NP) + 2 + 11),
         # dth on the DFS pair, dph, coefficients
-        "plane": pts * ((2 * Nt + 1 if eo["plane"] else 4 * Nt) +
-                        (Np + 1 if eo["plane"] and plane_square(dims) else 2 * Np) + 8),
+        # (square grids: theta folded twice, phi on the pair halves)
+        "plane": pts * ((Nt + 3 + Np + 1) if eo["plane"] and plane_square(dims) else
+                        ((2 * Nt + 1 if eo["plane"] else 4 * Nt) + 2 * Np)) + pts * 8,
         # dr (centro-antisymmetric halves), r term, Tau row, stage update
         "radial": pts * ((Nr + 1 if eo["radial"] else 2 * Nr) + 10),
     }

@@ -667,39 +667,57 @@ k_plane_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C
 // Plane pass on a square grid (N nodes on every angular axis), whole Phi rows
 // per tile: a tile is (g, i) and KT consecutive Theta values, i.e. columns
 // w = kl*N + m (KT*N of them, contiguous in memory for every (theta, phi)).
-// Thread: RB theta rows x one phi pair (l, l + N/2) x 4 columns m0.. and the
-// 4 partner columns m0 + N/2.. of one Theta value (RB = 2 in float, 1 in
-// double). It owns both DFS pairs that these columns form -- (l, m) with
-// (l+N/2, m+N/2) and (l, m+N/2) with (l+N/2, m) -- so each staged value it loads
-// feeds twice the multiply-adds of the general form, and it owns both halves
-// of the phi pair at each column, so the phi derivative acts on the pair halves
-// sigma = u(l) + u(l+N/2), delta = u(l) - u(l+N/2) through Ms, Md (half the
-// multiply-adds of the dense Fourier derivative). The staged tile is turned
-// into sigma (rows l < N/2) and delta (rows l + N/2) in place once the theta
-// sums are formed. Sums/differences use a row pitch of KT*N + 32 bytes so that
-// the lanes of a 16-byte load phase hit distinct banks.
-// Shared layout: [PthT | QthT | MsphT, MdphT | 2 tiles N*N*KT*N | theta sums, diffs]
+// Thread: one theta row j < N/2 and its mirror N-1-j x one phi pair (l, l+N/2)
+// x CB columns m0.. and the CB partner columns m0 + N/2.. of one Theta value
+// (CB = 4 in float, 2 in double). Folding:
+//  * theta through the DFS pairs it owns -- (l, m) with (l+N/2, m+N/2) and
+//    (l, m+N/2) with (l+N/2, m) -- and, since P and Q are centro-antisymmetric,
+//    through the theta-even/odd parts of the pair sums and differences
+//    (folded matrices Pe, Po, Qe, Qo): a quarter of the dense multiply-adds;
+//  * phi on the phi pair halves sigma = u(l) + u(l+N/2), delta = u(l) -
+//    u(l+N/2) through Ms, Md: half.
+// The staged tile is turned into sigma (rows l < N/2) and delta (rows
+// l + N/2) in place once the theta sums are formed. The folded sums use a row
+// pitch of KT*N + 32 bytes so that the lanes of a load phase hit distinct banks.
+// Shared layout: [PeT, PoT | QeT, QoT | MsphT, MdphT | 2 tiles N*N*KT*N |
+//                 folded theta sums se, so, de, do: 4 x (N/2)*(N/2)*(KT*N+pad)]
 template <int N, int KT, typename C>
 struct PlaneSq {
-  static constexpr int W = KT * N, hp = N / 2, H4 = hp / 4, SP = W + 32 / (int)sizeof(C);
-  static constexpr int TS = N * N * W;
-  static constexpr int RB = sizeof(C) == 4 ? 2 : 1, JR = N / RB;
-  static constexpr int units = JR * hp * KT * H4;
+  static constexpr int W = KT * N, hp = N / 2, SP = W + 32 / (int)sizeof(C);
+  static constexpr int TS = N * N * W, CB = sizeof(C) == 4 ? 4 : 2, HC = hp / CB;
+  static constexpr int QS = hp * hp * SP;   // one folded sum array [j' < N/2][l < N/2][w]
+  static constexpr int units = hp * hp * KT * HC;
 };
 
 template <int N, int KT, typename C>
 size_t smem_plane_sq() {
   using S = PlaneSq<N, KT, C>;
-  return (size_t)(3 * N * N + 2 * S::TS + 2 * N * S::hp * S::SP) * sizeof(C);
+  return (size_t)(3 * N * N + 2 * S::TS + 4 * S::QS) * sizeof(C);
+}
+
+template <typename C, int NV>
+__device__ __forceinline__ void stv(C* p, const C (&v)[NV]) {
+  if constexpr (NV == 4) {
+    st4<C>(p, v);
+  } else if constexpr (sizeof(C) == 8 && NV == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else if constexpr (sizeof(C) == 4 && NV == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int r = 0; r < NV; ++r) p[r] = v[r];
+  }
 }
 
 template <typename C>
 __device__ __forceinline__ void plane_sq_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
                                               C* sD) {
-  const int Nt = d.Nt, hp = d.Np / 2;
-  for (int x = threadIdx.x; x < Nt * Nt; x += blockDim.x) {
-    sP[x] = t.PthT[x];
-    sQ[x] = t.QthT[x];
+  const int ht = d.Nt / 2, hp = d.Np / 2;
+  for (int x = threadIdx.x; x < ht * ht; x += blockDim.x) {
+    sP[x] = t.PethT[x];
+    sP[ht * ht + x] = t.PothT[x];
+    sQ[x] = t.QethT[x];
+    sQ[ht * ht + x] = t.QothT[x];
   }
   for (int x = threadIdx.x; x < hp * hp; x += blockDim.x) {
     sD[x] = t.MsphT[x];
@@ -721,141 +739,178 @@ __device__ __forceinline__ void plane_sq_load(const Dims& d, const T* U, long lo
 
 template <int N, int KT, typename T, typename C>
 __device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>& t, C* su,
-                                              C* sSm, const C* sP, const C* sQ, const C* sD,
+                                              C* sF, const C* sP, const C* sQ, const C* sD,
                                               T* __restrict__ K, C sgn, long long tile) {
   using S = PlaneSq<N, KT, C>;
-  constexpr int RB = S::RB, CB = 4, W = S::W, hp = S::hp, SP = S::SP, H4 = S::H4;
+  constexpr int CB = S::CB, W = S::W, hp = S::hp, SP = S::SP, HC = S::HC, QS = S::QS;
   const Dims& d = p.d;
-  C* sDf = sSm + N * hp * SP;
   const long long q = tile / (N / KT);
   const int k0 = (int)(tile - q * (N / KT)) * KT;
   const int i = (int)(q % d.Nr);
   const long long base = q * d.S_i + (long long)k0 * N;
-  // per (theta row, phi pair, 4 columns m4.. and m4 + N/2..): the theta sums and
-  // differences with the DFS partner (phi + pi, Phi + pi), then the phi pair
-  // halves sigma, delta written over the four staged rows this thread read
-  for (int x = threadIdx.x; x < N * hp * KT * H4; x += blockDim.x) {
-    const int mq = x % H4, r1 = x / H4, kl = r1 % KT, r2 = r1 / KT, l = r2 % hp, jj = r2 / hp;
-    const int wA = kl * N + mq * 4, wB = wA + hp;
-    C* rl = su + (jj * N + l) * W;
-    C* rh = su + (jj * N + l + hp) * W;
-    C a0[4], a1[4], b0[4], b1[4], t0[4], t1[4], t2[4], t3[4];
-    ld4<C>(rl + wA, a0);
-    ld4<C>(rl + wB, a1);
-    ld4<C>(rh + wA, b0);
-    ld4<C>(rh + wB, b1);
+  // Per (theta row j < N/2 with its mirror, phi pair, CB columns m.. and
+  // m + N/2..): the DFS sums/differences of both rows folded over the theta
+  // mirror into sF, then the phi pair halves written over the eight staged
+  // row segments this thread read.
+  for (int x = threadIdx.x; x < S::units; x += blockDim.x) {
+    const int mq = x % HC, r1 = x / HC, kl = r1 % KT, r2 = r1 / KT, l = r2 % hp, jj = r2 / hp;
+    const int wA = kl * N + mq * CB, wB = wA + hp;
+    C a0[2][CB], a1[2][CB], b0[2][CB], b1[2][CB];   // [row jj / mirror][cols]
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      t0[cc] = a0[cc] + b1[cc];   // theta pair (l, m) with (l + N/2, m + N/2)
-      t1[cc] = a0[cc] - b1[cc];
-      t2[cc] = a1[cc] + b0[cc];   // theta pair (l, m + N/2) with (l + N/2, m)
-      t3[cc] = a1[cc] - b0[cc];
+    for (int side = 0; side < 2; ++side) {
+      const int j = side ? N - 1 - jj : jj;
+      ldv<C, CB>(su + (j * N + l) * W + wA, a0[side]);
+      ldv<C, CB>(su + (j * N + l) * W + wB, a1[side]);
+      ldv<C, CB>(su + (j * N + l + hp) * W + wA, b0[side]);
+      ldv<C, CB>(su + (j * N + l + hp) * W + wB, b1[side]);
     }
-    st4<C>(sSm + (jj * hp + l) * SP + wA, t0);
-    st4<C>(sDf + (jj * hp + l) * SP + wA, t1);
-    st4<C>(sSm + (jj * hp + l) * SP + wB, t2);
-    st4<C>(sDf + (jj * hp + l) * SP + wB, t3);
+    C se[2][CB], so[2][CB], de[2][CB], dO[2][CB];   // [column A / B]
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      t0[cc] = a0[cc] + b0[cc];   // phi pair halves at column m
-      t1[cc] = a0[cc] - b0[cc];
-      t2[cc] = a1[cc] + b1[cc];   // and at column m + N/2
-      t3[cc] = a1[cc] - b1[cc];
+    for (int c = 0; c < CB; ++c) {
+      // DFS pairs (l, m)~(l+N/2, m+N/2) at column A and (l, m+N/2)~(l+N/2, m) at B
+      const C sA0 = a0[0][c] + b1[0][c], dA0 = a0[0][c] - b1[0][c];
+      const C sA1 = a0[1][c] + b1[1][c], dA1 = a0[1][c] - b1[1][c];
+      const C sB0 = a1[0][c] + b0[0][c], dB0 = a1[0][c] - b0[0][c];
+      const C sB1 = a1[1][c] + b0[1][c], dB1 = a1[1][c] - b0[1][c];
+      se[0][c] = sA0 + sA1;
+      so[0][c] = sA0 - sA1;
+      de[0][c] = dA0 + dA1;
+      dO[0][c] = dA0 - dA1;
+      se[1][c] = sB0 + sB1;
+      so[1][c] = sB0 - sB1;
+      de[1][c] = dB0 + dB1;
+      dO[1][c] = dB0 - dB1;
     }
-    st4<C>(rl + wA, t0);
-    st4<C>(rh + wA, t1);
-    st4<C>(rl + wB, t2);
-    st4<C>(rh + wB, t3);
+    C* f = sF + (jj * hp + l) * SP;
+    stv<C, CB>(f + wA, se[0]);
+    stv<C, CB>(f + QS + wA, so[0]);
+    stv<C, CB>(f + 2 * QS + wA, de[0]);
+    stv<C, CB>(f + 3 * QS + wA, dO[0]);
+    stv<C, CB>(f + wB, se[1]);
+    stv<C, CB>(f + QS + wB, so[1]);
+    stv<C, CB>(f + 2 * QS + wB, de[1]);
+    stv<C, CB>(f + 3 * QS + wB, dO[1]);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int j = side ? N - 1 - jj : jj;
+      C sg0[CB], dl0[CB], sg1[CB], dl1[CB];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        sg0[c] = a0[side][c] + b0[side][c];   // phi pair halves at column A
+        dl0[c] = a0[side][c] - b0[side][c];
+        sg1[c] = a1[side][c] + b1[side][c];   // and at column B
+        dl1[c] = a1[side][c] - b1[side][c];
+      }
+      stv<C, CB>(su + (j * N + l) * W + wA, sg0);
+      stv<C, CB>(su + (j * N + l + hp) * W + wA, dl0);
+      stv<C, CB>(su + (j * N + l) * W + wB, sg1);
+      stv<C, CB>(su + (j * N + l + hp) * W + wB, dl1);
+    }
   }
   __syncthreads();
   const C ir = t.inv_r[i];
+  const C* sPe = sP;
+  const C* sPo = sP + hp * hp;
+  const C* sQe = sQ;
+  const C* sQo = sQ + hp * hp;
   for (int unit = threadIdx.x; unit < S::units; unit += blockDim.x) {
-    const int mq = unit % S::H4, r1 = unit / S::H4, kl = r1 % KT, r2 = r1 / KT;
-    const int l = r2 % hp, jr = r2 / hp;
-    const int m0 = mq * CB, j0 = jr * RB;
+    const int mq = unit % HC, r1 = unit / HC, kl = r1 % KT, r2 = r1 / KT;
+    const int l = r2 % hp, j0 = r2 / hp, j1 = N - 1 - j0;
+    const int m0 = mq * CB;
     const int wA = kl * N + m0, wB = wA + hp;      // columns m0.. and m0 + N/2..
-    C psA[RB][CB], qdA[RB][CB], psB[RB][CB], qdB[RB][CB];
-    C fsA[RB][CB], fdA[RB][CB], fsB[RB][CB], fdB[RB][CB];
+    // theta: [column A / B][even / odd of P / Q]
+    C aEA[CB], aOA[CB], bEA[CB], bOA[CB], aEB[CB], aOB[CB], bEB[CB], bOB[CB];
+    // phi: [row j0 / mirror j1][column A / B]
+    C fs[2][2][CB], fd[2][2][CB];
 #pragma unroll
-    for (int r = 0; r < RB; ++r)
+    for (int c = 0; c < CB; ++c) {
+      aEA[c] = aOA[c] = bEA[c] = bOA[c] = aEB[c] = aOB[c] = bEB[c] = bOB[c] = 0;
 #pragma unroll
-      for (int cc = 0; cc < CB; ++cc)
-        psA[r][cc] = qdA[r][cc] = psB[r][cc] = qdB[r][cc] = fsA[r][cc] = fdA[r][cc] =
-            fsB[r][cc] = fdB[r][cc] = 0;
-#pragma unroll 8
-    for (int jj = 0; jj < N; ++jj) {
-      C sa[CB], da_[CB], sb[CB], db_[CB], P[RB], Q[RB];
-      ld4<C>(sSm + (jj * hp + l) * SP + wA, sa);
-      ld4<C>(sDf + (jj * hp + l) * SP + wA, da_);
-      ld4<C>(sSm + (jj * hp + l) * SP + wB, sb);
-      ld4<C>(sDf + (jj * hp + l) * SP + wB, db_);
-      ldv<C, RB>(sP + jj * N + j0, P);
-      ldv<C, RB>(sQ + jj * N + j0, Q);
+      for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
-      for (int cc = 0; cc < CB; ++cc) {
+        for (int ab = 0; ab < 2; ++ab) fs[s2][ab][c] = fd[s2][ab][c] = 0;
+    }
 #pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          psA[r][cc] = fmac(P[r], sa[cc], psA[r][cc]);
-          qdA[r][cc] = fmac(Q[r], da_[cc], qdA[r][cc]);
-          psB[r][cc] = fmac(P[r], sb[cc], psB[r][cc]);
-          qdB[r][cc] = fmac(Q[r], db_[cc], qdB[r][cc]);
-        }
+    for (int jj = 0; jj < hp; ++jj) {
+      const C* f = sF + (jj * hp + l) * SP;
+      C v[8][CB];
+      ldv<C, CB>(f + wA, v[0]);
+      ldv<C, CB>(f + QS + wA, v[1]);
+      ldv<C, CB>(f + 2 * QS + wA, v[2]);
+      ldv<C, CB>(f + 3 * QS + wA, v[3]);
+      ldv<C, CB>(f + wB, v[4]);
+      ldv<C, CB>(f + QS + wB, v[5]);
+      ldv<C, CB>(f + 2 * QS + wB, v[6]);
+      ldv<C, CB>(f + 3 * QS + wB, v[7]);
+      const C Pe = sPe[jj * hp + j0], Po = sPo[jj * hp + j0];
+      const C Qe = sQe[jj * hp + j0], Qo = sQo[jj * hp + j0];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        aEA[c] = fmac(Pe, v[0][c], aEA[c]);
+        aOA[c] = fmac(Po, v[1][c], aOA[c]);
+        bEA[c] = fmac(Qe, v[2][c], bEA[c]);
+        bOA[c] = fmac(Qo, v[3][c], bOA[c]);
+        aEB[c] = fmac(Pe, v[4][c], aEB[c]);
+        aOB[c] = fmac(Po, v[5][c], aOB[c]);
+        bEB[c] = fmac(Qe, v[6][c], bEB[c]);
+        bOB[c] = fmac(Qo, v[7][c], bOB[c]);
       }
     }
 #pragma unroll
     for (int ll = 0; ll < hp; ++ll) {
       const C Ms = sD[ll * hp + l], Md = sD[hp * hp + ll * hp + l];
 #pragma unroll
-      for (int r = 0; r < RB; ++r) {
+      for (int s2 = 0; s2 < 2; ++s2) {
+        const int j = s2 ? j1 : j0;
         C sa[CB], da_[CB], sb[CB], db_[CB];
-        ld4<C>(su + ((j0 + r) * N + ll) * W + wA, sa);
-        ld4<C>(su + ((j0 + r) * N + ll + hp) * W + wA, da_);
-        ld4<C>(su + ((j0 + r) * N + ll) * W + wB, sb);
-        ld4<C>(su + ((j0 + r) * N + ll + hp) * W + wB, db_);
+        ldv<C, CB>(su + (j * N + ll) * W + wA, sa);
+        ldv<C, CB>(su + (j * N + ll + hp) * W + wA, da_);
+        ldv<C, CB>(su + (j * N + ll) * W + wB, sb);
+        ldv<C, CB>(su + (j * N + ll + hp) * W + wB, db_);
 #pragma unroll
-        for (int cc = 0; cc < CB; ++cc) {
-          fsA[r][cc] = fmac(Ms, sa[cc], fsA[r][cc]);
-          fdA[r][cc] = fmac(Md, da_[cc], fdA[r][cc]);
-          fsB[r][cc] = fmac(Ms, sb[cc], fsB[r][cc]);
-          fdB[r][cc] = fmac(Md, db_[cc], fdB[r][cc]);
+        for (int c = 0; c < CB; ++c) {
+          fs[s2][0][c] = fmac(Ms, sa[c], fs[s2][0][c]);
+          fd[s2][0][c] = fmac(Md, da_[c], fd[s2][0][c]);
+          fs[s2][1][c] = fmac(Ms, sb[c], fs[s2][1][c]);
+          fd[s2][1][c] = fmac(Md, db_[c], fd[s2][1][c]);
         }
       }
     }
     const C sTk = sgn * t.sinT[k0 + kl] * ir;
     C cA[CB], sA[CB], cB[CB], sB[CB];   // a_phi carries the 1/2 of the phi pair halves
 #pragma unroll
-    for (int cc = 0; cc < CB; ++cc) {
-      cA[cc] = sTk * t.cosP[m0 + cc];
-      sA[cc] = (C)0.5 * sTk * t.sinP[m0 + cc];
-      cB[cc] = sTk * t.cosP[m0 + hp + cc];
-      sB[cc] = (C)0.5 * sTk * t.sinP[m0 + hp + cc];
+    for (int c = 0; c < CB; ++c) {
+      cA[c] = (C)0.5 * sTk * t.cosP[m0 + c];   // and a_theta the 1/2 of the theta folding
+      sA[c] = (C)0.5 * sTk * t.sinP[m0 + c];
+      cB[c] = (C)0.5 * sTk * t.cosP[m0 + hp + c];
+      sB[c] = (C)0.5 * sTk * t.sinP[m0 + hp + c];
     }
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const int j = j0 + r;
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int j = s2 ? j1 : j0;
+      const C sg = s2 ? (C)-1 : (C)1;
       const C isn = t.inv_sinth[j];
       T* p0 = K + base + (long long)j * d.S_j + (long long)l * d.S_l + kl * N + m0;
       T* p1 = p0 + (long long)hp * d.S_l;      // phi partner row l + N/2
       T k0a[CB], k0b[CB], k1a[CB], k1b[CB];
-      ld4<T>(p0, k0a);
-      ld4<T>(p0 + hp, k0b);
-      ld4<T>(p1, k1a);
-      ld4<T>(p1 + hp, k1b);
+      ldv<T, CB>(p0, k0a);
+      ldv<T, CB>(p0 + hp, k0b);
+      ldv<T, CB>(p1, k1a);
+      ldv<T, CB>(p1 + hp, k1b);
 #pragma unroll
-      for (int cc = 0; cc < CB; ++cc) {
-        k0a[cc] = (T)((C)k0a[cc] + cA[cc] * (psA[r][cc] + qdA[r][cc]) +
-                      sA[cc] * isn * (fsA[r][cc] + fdA[r][cc]));
-        k0b[cc] = (T)((C)k0b[cc] + cB[cc] * (psB[r][cc] + qdB[r][cc]) +
-                      sB[cc] * isn * (fsB[r][cc] + fdB[r][cc]));
-        k1a[cc] = (T)((C)k1a[cc] + cA[cc] * (psB[r][cc] - qdB[r][cc]) +
-                      sA[cc] * isn * (fsA[r][cc] - fdA[r][cc]));
-        k1b[cc] = (T)((C)k1b[cc] + cB[cc] * (psA[r][cc] - qdA[r][cc]) +
-                      sB[cc] * isn * (fsB[r][cc] - fdB[r][cc]));
+      for (int c = 0; c < CB; ++c) {
+        const C psA = aOA[c] + sg * aEA[c], qdA = bOA[c] + sg * bEA[c];   // x 2
+        const C psB = aOB[c] + sg * aEB[c], qdB = bOB[c] + sg * bEB[c];
+        const C fA = fs[s2][0][c], gA = fd[s2][0][c], fB = fs[s2][1][c], gB = fd[s2][1][c];
+        k0a[c] = (T)((C)k0a[c] + cA[c] * (psA + qdA) + sA[c] * isn * (fA + gA));
+        k0b[c] = (T)((C)k0b[c] + cB[c] * (psB + qdB) + sB[c] * isn * (fB + gB));
+        k1a[c] = (T)((C)k1a[c] + cA[c] * (psB - qdB) + sA[c] * isn * (fA - gA));
+        k1b[c] = (T)((C)k1b[c] + cB[c] * (psA - qdA) + sB[c] * isn * (fB - gB));
       }
-      st4<T>(p0, k0a);
-      st4<T>(p0 + hp, k0b);
-      st4<T>(p1, k1a);
-      st4<T>(p1 + hp, k1b);
+      stv<T, CB>(p0, k0a);
+      stv<T, CB>(p0 + hp, k0b);
+      stv<T, CB>(p1, k1a);
+      stv<T, CB>(p1 + hp, k1b);
     }
   }
 }
@@ -871,7 +926,7 @@ k_plane_sq(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C
   C* sQ = sP + N * N;
   C* sD = sQ + N * N;
   C* buf0 = sD + N * N;
-  C* sSm = buf0 + 2 * S::TS;
+  C* sF = buf0 + 2 * S::TS;
   plane_sq_mats<C>(t, d, sP, sQ, sD);
   long long tile = blockIdx.x;
   if (tile < ntiles) plane_sq_load<N, KT, T, C>(d, U, tile, buf0);
@@ -884,7 +939,7 @@ k_plane_sq(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
-    plane_sq_body<N, KT, T, C>(p, t, cur, sSm, sP, sQ, sD, K, sgn, tile);
+    plane_sq_body<N, KT, T, C>(p, t, cur, sF, sP, sQ, sD, K, sgn, tile);
     __syncthreads();
   }
   cp_async_wait0();
