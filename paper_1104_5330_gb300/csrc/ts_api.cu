@@ -191,7 +191,9 @@ std::vector<const Vec*> device_list(const HostTables& h, std::vector<Vec>& tmp) 
           &h.TcBhi, &h.TcBlo,
           &h.PthA, &h.QthA, &h.PThA, &h.QThA, &h.EpTa, &h.OpTa, &h.DrMca, &h.DrMra,
           &h.MsPhT, &h.MdPhT, &h.MsphT, &h.MdphT,
-          &h.PeThT, &h.PoThT, &h.QeThT, &h.QoThT, &h.PethT, &h.PothT, &h.QethT, &h.QothT};
+          &h.PeThT, &h.PoThT, &h.QeThT, &h.QoThT, &h.PethT, &h.PothT, &h.QethT, &h.QothT,
+          &h.PeThA, &h.PoThA, &h.QeThA, &h.QoThA, &h.PethA, &h.PothA, &h.QethA, &h.QothA,
+          &h.MsPhA, &h.MdPhA, &h.MsphA, &h.MdphA};
 }
 
 // Even/odd forms of the derivative matrices (see Tables in ts_internal.h).
@@ -359,6 +361,14 @@ void even_odd_tables(HostTables& h) {
   fold(h.QThT, nT, h.QeThT, h.QoThT);
   fold(h.PthT, nt, h.PethT, h.PothT);
   fold(h.QthT, nt, h.QethT, h.QothT);
+  // the adjoint's operators: P^T, Q^T are read [in][out] as PthA, PThA (= P, Q)
+  fold(h.PThA, nT, h.PeThA, h.PoThA);
+  fold(h.QThA, nT, h.QeThA, h.QoThA);
+  fold(h.PthA, nt, h.PethA, h.PothA);
+  fold(h.QthA, nt, h.QethA, h.QothA);
+  const int nP = (int)h.Phi.size(), np = (int)h.phi.size();
+  halves(transpose(h.DPh, nP, nP), nP, h.MsPhA, h.MdPhA);
+  halves(transpose(h.Dph, np, np), np, h.MsphA, h.MdphA);
 }
 
 template <typename C>
@@ -381,7 +391,9 @@ cudaError_t upload_tables(const HostTables& h, void** mem, Tables<C>* t) {
                  &t->PthA, &t->QthA, &t->PThA, &t->QThA, &t->EpTa, &t->OpTa, &t->DrMca,
                  &t->DrMra, &t->MsPhT, &t->MdPhT, &t->MsphT, &t->MdphT,
                  &t->PeThT, &t->PoThT, &t->QeThT, &t->QoThT, &t->PethT, &t->PothT,
-                 &t->QethT, &t->QothT};
+                 &t->QethT, &t->QothT,
+                 &t->PeThA, &t->PoThA, &t->QeThA, &t->QoThA, &t->PethA, &t->PothA,
+                 &t->QethA, &t->QothA, &t->MsPhA, &t->MdPhA, &t->MsphA, &t->MdphA};
   size_t off = 0;
   for (size_t a = 0; a < list.size(); ++a) {
     for (size_t b = 0; b < list[a]->size(); ++b) host[off + b] = (C)(*list[a])[b];

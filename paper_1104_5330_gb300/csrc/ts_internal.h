@@ -57,6 +57,10 @@ struct Tables {
   // n/2 output pairs (k, n-1-k) like D_r, PeT[k'][k] = P[k][k'] + P[k][n-1-k'],
   // PoT[k'][k] = P[k][k'] - P[k][n-1-k'] (k, k' < n/2), Q alike.
   C *PeThT, *PoThT, *QeThT, *QoThT, *PethT, *PothT, *QethT, *QothT;
+  // The same foldings of the transposed operators (adjoint passes): P^T, Q^T
+  // folded over k -> n-1-k, and D^T (circulant too) on the pair halves.
+  C *PeThA, *PoThA, *QeThA, *QoThA, *PethA, *PothA, *QethA, *QothA;
+  C *MsPhA, *MdPhA, *MsphA, *MdphA;
   // D_r split into TF32 high and low halves in the tensor-core operand layout
   // (N_r padded to 16 rows x N_r padded to 8 columns, 8 x 4 core matrices).
   C *TcBhi, *TcBlo;
@@ -171,6 +175,8 @@ struct HostTables {
   Vec PthA, QthA, PThA, QThA, EpTa, OpTa, DrMca, DrMra;  // even/odd forms of the transposes
   Vec MsPhT, MdPhT, MsphT, MdphT;                     // pair-half Fourier derivatives
   Vec PeThT, PoThT, QeThT, QoThT, PethT, PothT, QethT, QothT;   // folded P, Q
+  Vec PeThA, PoThA, QeThA, QoThA, PethA, PothA, QethA, QothA;   // folded P^T, Q^T
+  Vec MsPhA, MdPhA, MsphA, MdphA;                                // D^T on pair halves
   Vec TcBhi, TcBlo;                                   // tensor-core operand of D_r
 };
 

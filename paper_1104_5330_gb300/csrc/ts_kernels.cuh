@@ -402,12 +402,154 @@ k_plane_T(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__ Ubar
   }
 }
 
+// Adjoint pass 2^T with the theta folding (even N_theta): D_th^T through the
+// two DFS pairs that the columns w and w^ = w +- c form at (l, l + Np/2), and
+// over j -> Nt-1-j (P^T, Q^T centro-antisymmetric) through the theta-even/odd
+// parts of the pair sums and differences; D_ph^T (circulant) on the phi pair
+// halves at each column. One thread per (j < Nt/2, l < Np/2, w < c): the 8
+// outputs at rows j, Nt-1-j x phi l, l + Np/2 x columns w, w^.
+template <typename T, typename C>
+__global__ void __launch_bounds__(kThreads)
+k_plane_T_fold(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__ Ubar, int c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Dims d = p.d;
+  const int Nt = d.Nt, Np = d.Np, NP = d.NP, hP = NP / 2, hp = Np / 2, ht = Nt / 2, W = 2 * c;
+  const int FQ = ht * hp * W;               // one folded theta-sum array [jj][l][w]
+  const int HQ = Nt * hp * W;               // one phi-half array [j][l'][w]
+  C* sPe = reinterpret_cast<C*>(smem_raw);  // folded P^T, Q^T [jj][j] (Nt/2 x Nt/2 each)
+  C* sPo = sPe + ht * ht;
+  C* sQe = sPo + ht * ht;
+  C* sQo = sQe + ht * ht;
+  C* sMs = sQo + ht * ht;                   // D_ph^T on pair halves [l'][l]
+  C* sMd = sMs + hp * hp;
+  C* sF = sMd + hp * hp;                    // [ES | OS | ED | OD] of a_th lt
+  C* sH = sF + 4 * FQ;                      // [sigma | delta] of a_ph lt
+  const int nchunk = hP / c;
+  long long q = blockIdx.x;
+  const int chunk = (int)(q % nchunk);
+  q /= nchunk;
+  const int k = (int)(q % d.NT);
+  q /= d.NT;
+  const int i = (int)(q % d.Nr);
+  const int g = (int)(q / d.Nr);
+  const int m0 = chunk * c;
+  const long long base = (long long)g * d.S_g + (long long)i * d.S_i + (long long)k * NP;
+  for (int x = threadIdx.x; x < ht * ht; x += blockDim.x) {
+    sPe[x] = t.PethA[x];
+    sPo[x] = t.PothA[x];
+    sQe[x] = t.QethA[x];
+    sQo[x] = t.QothA[x];
+  }
+  for (int x = threadIdx.x; x < hp * hp; x += blockDim.x) {
+    sMs[x] = t.MsphA[x];
+    sMd[x] = t.MdphA[x];
+  }
+  const C sTk = t.sinT[k] * t.inv_r[i];
+  const int nq = ht * hp * c;
+  for (int x = threadIdx.x; x < nq; x += blockDim.x) {   // (jj, l, w < c) and partners
+    const int w = x % c, jl = x / c, l = jl % hp, jj = jl / hp;
+    const int wh = w + c;
+    const int mA = plane_m(w, c, m0, hP), mB = plane_m(wh, c, m0, hP);
+    const C cA = sTk * t.cosP[mA], cB = sTk * t.cosP[mB];
+    C sAv[2], dAv[2], sBv[2], dBv[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int j = side ? Nt - 1 - jj : jj;
+      const long long r0 = base + (long long)j * d.S_j + (long long)l * d.S_l;
+      const long long r1 = r0 + (long long)hp * d.S_l;
+      const C u0A = (C)lt[r0 + mA], u0B = (C)lt[r0 + mB];   // (l, w), (l, w^)
+      const C u1A = (C)lt[r1 + mA], u1B = (C)lt[r1 + mB];   // (l+hp, w), (l+hp, w^)
+      sAv[side] = cA * u0A + cB * u1B;   // DFS pair (l, w) ~ (l+hp, w^)
+      dAv[side] = cA * u0A - cB * u1B;
+      sBv[side] = cB * u0B + cA * u1A;   // DFS pair (l, w^) ~ (l+hp, w)
+      dBv[side] = cB * u0B - cA * u1A;
+      const C isn = t.inv_sinth[j];
+      const C pA = sTk * t.sinP[mA] * isn, pB = sTk * t.sinP[mB] * isn;
+      C* h = sH + (j * hp + l) * W;
+      h[w] = pA * (u0A + u1A);          // phi pair halves at column w
+      h[HQ + w] = pA * (u0A - u1A);
+      h[wh] = pB * (u0B + u1B);         // and at column w^
+      h[HQ + wh] = pB * (u0B - u1B);
+    }
+    C* f = sF + (jj * hp + l) * W;
+    f[w] = sAv[0] + sAv[1];
+    f[FQ + w] = sAv[0] - sAv[1];
+    f[2 * FQ + w] = dAv[0] + dAv[1];
+    f[3 * FQ + w] = dAv[0] - dAv[1];
+    f[wh] = sBv[0] + sBv[1];
+    f[FQ + wh] = sBv[0] - sBv[1];
+    f[2 * FQ + wh] = dBv[0] + dBv[1];
+    f[3 * FQ + wh] = dBv[0] - dBv[1];
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < nq; x += blockDim.x) {
+    const int w = x % c, jl = x / c, l = jl % hp, j0 = jl / hp;
+    const int wh = w + c;
+    C th[2][4];   // [column w / w^][aE, aO, bE, bO]
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) th[a][b] = 0;
+    for (int jj = 0; jj < ht; ++jj) {
+      const C* f = sF + (jj * hp + l) * W;
+      const int o = jj * ht + j0;
+      const C pe = sPe[o], po = sPo[o], qe = sQe[o], qo = sQo[o];
+      th[0][0] = fmac(pe, f[w], th[0][0]);
+      th[0][1] = fmac(po, f[FQ + w], th[0][1]);
+      th[0][2] = fmac(qe, f[2 * FQ + w], th[0][2]);
+      th[0][3] = fmac(qo, f[3 * FQ + w], th[0][3]);
+      th[1][0] = fmac(pe, f[wh], th[1][0]);
+      th[1][1] = fmac(po, f[FQ + wh], th[1][1]);
+      th[1][2] = fmac(qe, f[2 * FQ + wh], th[1][2]);
+      th[1][3] = fmac(qo, f[3 * FQ + wh], th[1][3]);
+    }
+    C ph[2][2][2];   // [row j0 / mirror][column w / w^][sigma, delta sums]
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b) ph[a][b][0] = ph[a][b][1] = 0;
+    for (int ll = 0; ll < hp; ++ll) {
+      const C ms = sMs[ll * hp + l], md = sMd[ll * hp + l];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int j = side ? Nt - 1 - j0 : j0;
+        const C* h = sH + (j * hp + ll) * W;
+        ph[side][0][0] = fmac(ms, h[w], ph[side][0][0]);
+        ph[side][0][1] = fmac(md, h[HQ + w], ph[side][0][1]);
+        ph[side][1][0] = fmac(ms, h[wh], ph[side][1][0]);
+        ph[side][1][1] = fmac(md, h[HQ + wh], ph[side][1][1]);
+      }
+    }
+    const int mA = plane_m(w, c, m0, hP), mB = plane_m(wh, c, m0, hP);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int j = side ? Nt - 1 - j0 : j0;
+      const C sg = side ? (C)-1 : (C)1;
+      const C psA = (C)0.5 * (th[0][1] + sg * th[0][0]), qdA = (C)0.5 * (th[0][3] + sg * th[0][2]);
+      const C psB = (C)0.5 * (th[1][1] + sg * th[1][0]), qdB = (C)0.5 * (th[1][3] + sg * th[1][2]);
+      const C fwA = (C)0.5 * (ph[side][0][0] + ph[side][0][1]);   // phi at (l, w)
+      const C fwB = (C)0.5 * (ph[side][0][0] - ph[side][0][1]);   // phi at (l+hp, w)
+      const C fhA = (C)0.5 * (ph[side][1][0] + ph[side][1][1]);   // phi at (l, w^)
+      const C fhB = (C)0.5 * (ph[side][1][0] - ph[side][1][1]);   // phi at (l+hp, w^)
+      const long long r0 = base + (long long)j * d.S_j + (long long)l * d.S_l;
+      const long long r1 = r0 + (long long)hp * d.S_l;
+      Ubar[r0 + mA] = (T)((C)Ubar[r0 + mA] - (psA + qdA) - fwA);   // (l, w)
+      Ubar[r1 + mB] = (T)((C)Ubar[r1 + mB] - (psA - qdA) - fhB);   // (l+hp, w^)
+      Ubar[r0 + mB] = (T)((C)Ubar[r0 + mB] - (psB + qdB) - fhA);   // (l, w^)
+      Ubar[r1 + mA] = (T)((C)Ubar[r1 + mA] - (psB - qdB) - fwB);   // (l+hp, w)
+    }
+  }
+}
+
 // Adjoint pass 1^T: angular blocks.
 //   Ubar_s = Ubar - D_Th^T(a_Th lt) - D_Ph^T(a_Ph lt) - (kappa+kappa_s) lt + kappa_s q_k sum lt
 //   gk -= sum_block lt*Us,  ge += sum_block lt
 //   lam_out = lam_in + Ubar_s;   Kbar_out = wl*lam + wu*Ubar_s (if Kbar_out)
-// D_Th^T on the DFS pair (k, m), (k, m+NP/2) through the sum and difference as
-// in the plane pass; one thread per output pair.
+// The transposed derivatives are folded as in the forward pass: D_Th^T on the
+// DFS pair (k, m), (k, m+NP/2) through the pair sum and difference, and over
+// k -> NT-1-k (P^T and Q^T are centro-antisymmetric) through their Theta-even/
+// odd parts; D_Ph^T (circulant) on the pair halves. One thread per 2 x 2 output
+// quadruple (k, NT-1-k) x (m, m+NP/2).
 template <typename T, typename C>
 __global__ void __launch_bounds__(kThreads)
 k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restrict__ Ubar,
@@ -415,33 +557,52 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
             T* lam_out, T* Kbar_out, C wl, C wu, int nb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
-  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2, hS = NT * hP;
-  C* sP = reinterpret_cast<C*>(smem_raw);  // PThA [k][k']
-  C* sQ = sP + NT * NT;
-  C* sD = sQ + NT * NT;                    // DPh [m][m']
-  C* sS = sD + NP * NP;                    // a_Th lt + partner  [bb][k][m < NP/2]
-  C* sDf = sS + nb * hS;                   // a_Th lt - partner
-  C* s2 = sDf + nb * hS;                   // a_Ph * lt          [bb][k][m]
-  C* sSum = s2 + nb * S;                   // [nb] kappa_s-weighted sum of lt
+  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2, hT = NT / 2;
+  const int Q4 = hT * hP, hS = NT * hP;
+  C* sPe = reinterpret_cast<C*>(smem_raw);  // folded P^T, Q^T [kk][k] (NT/2 x NT/2 each)
+  C* sPo = sPe + hT * hT;
+  C* sQe = sPo + hT * hT;
+  C* sQo = sQe + hT * hT;
+  C* sMs = sQo + hT * hT;                   // D_Ph^T on pair halves [p'][p] (NP/2 x NP/2)
+  C* sMd = sMs + hP * hP;
+  C* s1 = sMd + hP * hP;                    // a_Th lt folded: [bb][ES | OS | ED | OD][kk][p]
+  C* s2 = s1 + nb * S;                      // a_Ph lt pair halves: [bb][sigma | delta][k][p]
+  C* sSum = s2 + nb * S;                    // [nb] kappa_s-weighted sum of lt
   const long long b0 = (long long)blockIdx.x * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
-  for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
-    sP[x] = t.PThA[x];
-    sQ[x] = t.QThA[x];
+  for (int x = threadIdx.x; x < hT * hT; x += blockDim.x) {
+    sPe[x] = t.PeThA[x];
+    sPo[x] = t.PoThA[x];
+    sQe[x] = t.QeThA[x];
+    sQo[x] = t.QoThA[x];
   }
-  for (int x = threadIdx.x; x < NP * NP; x += blockDim.x) sD[x] = t.DPh[x];
-  for (int x = threadIdx.x; x < nbb * hS; x += blockDim.x) {   // (bb, k, m < NP/2) and partner
-    const int bb = x / hS, r = x - bb * hS, k = r / hP, m = r - k * hP;
+  for (int x = threadIdx.x; x < hP * hP; x += blockDim.x) {
+    sMs[x] = t.MsPhA[x];
+    sMd[x] = t.MdPhA[x];
+  }
+  for (int x = threadIdx.x; x < nbb * Q4; x += blockDim.x) {   // (bb, kk < NT/2, p < NP/2)
+    const int bb = x / Q4, r = x - bb * Q4, kk = r / hP, m = r - kk * hP, km = NT - 1 - kk;
     int g, i, j, l;
     decode_block(d, b0 + bb, g, i, j, l);
-    const long long gi = (b0 + bb) * S + k * NP + m;
-    const C v1 = (C)lt[gi], v2 = (C)lt[gi + hP];
-    const C aT = -t.sinT[k] * t.inv_r[i];
-    sS[x] = aT * (v1 + v2);
-    sDf[x] = aT * (v1 - v2);
-    const C ct = aT * t.cot_th[j];
-    s2[bb * S + k * NP + m] = ct * t.sinP[m] * v1;
-    s2[bb * S + k * NP + m + hP] = ct * t.sinP[m + hP] * v2;
+    const C ir = t.inv_r[i], ct = t.cot_th[j];
+    const long long gb = (b0 + bb) * S;
+    C sv[2], dv[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int k = side ? km : kk;
+      const C v1 = (C)lt[gb + k * NP + m], v2 = (C)lt[gb + k * NP + m + hP];
+      const C aT = -t.sinT[k] * ir;
+      sv[side] = aT * (v1 + v2);
+      dv[side] = aT * (v1 - v2);
+      const C n1 = aT * ct * t.sinP[m] * v1, n2 = aT * ct * t.sinP[m + hP] * v2;
+      s2[bb * S + k * hP + m] = n1 + n2;
+      s2[bb * S + hS + k * hP + m] = n1 - n2;
+    }
+    C* f = s1 + bb * S + kk * hP + m;
+    f[0] = sv[0] + sv[1];
+    f[Q4] = sv[0] - sv[1];
+    f[2 * Q4] = dv[0] + dv[1];
+    f[3 * Q4] = dv[0] - dv[1];
   }
   __syncthreads();
   {
@@ -466,31 +627,44 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
     }
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < nbb * hS; x += blockDim.x) {   // output pair (k, m), (k, m+hP)
-    const int bb = x / hS, r = x - bb * hS, k = r / hP, m = r - k * hP;
-    const C* a1 = sS + bb * hS;
-    const C* d1 = sDf + bb * hS;
-    const C* a2 = s2 + bb * S + k * NP;
-    C ps = 0, qd = 0;
-    for (int kk = 0; kk < NT; ++kk) {
-      ps = fmac(sP[kk * NT + k], a1[kk * hP + m], ps);
-      qd = fmac(sQ[kk * NT + k], d1[kk * hP + m], qd);
+  for (int x = threadIdx.x; x < nbb * Q4; x += blockDim.x) {   // quadruple (k, NT-1-k) x (m, m+hP)
+    const int bb = x / Q4, r = x - bb * Q4, k = r / hP, m = r - k * hP, km = NT - 1 - k;
+    const C* f = s1 + bb * S;
+    C aE = 0, aO = 0, bE = 0, bO = 0;
+    for (int kk = 0; kk < hT; ++kk) {
+      const int o = kk * hP + m, w = kk * hT + k;
+      aE = fmac(sPe[w], f[o], aE);
+      aO = fmac(sPo[w], f[Q4 + o], aO);
+      bE = fmac(sQe[w], f[2 * Q4 + o], bE);
+      bO = fmac(sQo[w], f[3 * Q4 + o], bO);
     }
-    C f1 = 0, f2 = 0;
-    for (int mm = 0; mm < NP; ++mm) {
-      f1 = fmac(sD[mm * NP + m], a2[mm], f1);
-      f2 = fmac(sD[mm * NP + m + hP], a2[mm], f2);
+    const C* g2 = s2 + bb * S;
+    C fs[2] = {0, 0}, fd[2] = {0, 0};
+    for (int pp = 0; pp < hP; ++pp) {
+      const C ms = sMs[pp * hP + m], md = sMd[pp * hP + m];
+      fs[0] = fmac(ms, g2[k * hP + pp], fs[0]);
+      fd[0] = fmac(md, g2[hS + k * hP + pp], fd[0]);
+      fs[1] = fmac(ms, g2[km * hP + pp], fs[1]);
+      fd[1] = fmac(md, g2[hS + km * hP + pp], fd[1]);
     }
-    const long long blk = b0 + bb, gi = blk * S + k * NP + m;
+    const long long blk = b0 + bb;
     const C kap = (C)p.kap[blk], ks = (C)p.kaps[blk];
-    const C qs = t.qdir[k] * sSum[bb];
-    const C ub1 = (C)Ubar[gi] - (ps + qd) - f1 - (kap + ks) * (C)lt[gi] + qs;
-    const C ub2 = (C)Ubar[gi + hP] - (ps - qd) - f2 - (kap + ks) * (C)lt[gi + hP] + qs;
-    lam_out[gi] = (T)((C)lam_in[gi] + ub1);
-    lam_out[gi + hP] = (T)((C)lam_in[gi + hP] + ub2);
-    if (Kbar_out) {
-      Kbar_out[gi] = (T)(wl * (C)lam[gi] + wu * ub1);
-      Kbar_out[gi + hP] = (T)(wl * (C)lam[gi + hP] + wu * ub2);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int kr = side ? km : k;
+      const C sg = side ? (C)-1 : (C)1;
+      const C ps = (C)0.5 * (aO + sg * aE), qd = (C)0.5 * (bO + sg * bE);
+      const C f1 = (C)0.5 * (fs[side] + fd[side]), f2 = (C)0.5 * (fs[side] - fd[side]);
+      const long long gi = blk * S + kr * NP + m;
+      const C qs = t.qdir[kr] * sSum[bb];
+      const C ub1 = (C)Ubar[gi] - (ps + qd) - f1 - (kap + ks) * (C)lt[gi] + qs;
+      const C ub2 = (C)Ubar[gi + hP] - (ps - qd) - f2 - (kap + ks) * (C)lt[gi + hP] + qs;
+      lam_out[gi] = (T)((C)lam_in[gi] + ub1);
+      lam_out[gi + hP] = (T)((C)lam_in[gi + hP] + ub2);
+      if (Kbar_out) {
+        Kbar_out[gi] = (T)(wl * (C)lam[gi] + wu * ub1);
+        Kbar_out[gi + hP] = (T)(wl * (C)lam[gi + hP] + wu * ub2);
+      }
     }
   }
 }

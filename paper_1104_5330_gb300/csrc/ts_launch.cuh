@@ -279,7 +279,8 @@ cudaError_t Launch<T, C>::plane_T(const Problem& p, const Tables<C>& t, const T*
                                   cudaStream_t s) {
   static bool init = false;
   if (!init) {
-    const cudaError_t ea = allow_smem(k_plane_T<T, C>);
+    cudaError_t ea = allow_smem(k_plane_T<T, C>);
+    if (ea == cudaSuccess) ea = allow_smem(k_plane_T_fold<T, C>);
     if (ea != cudaSuccess) return ea;
     init = true;
   }
@@ -288,7 +289,10 @@ cudaError_t Launch<T, C>::plane_T(const Problem& p, const Tables<C>& t, const T*
   const size_t smem =
       (size_t)(2 * d.Nt * d.Nt + d.Np * d.Np + 2 * d.Nt * d.Np * 2 * c) * sizeof(C);
   const long long nct = (long long)d.G * d.Nr * d.NT * (d.NP / 2 / c);
-  k_plane_T<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, lt, Ubar, c);
+  if (d.Nt % 2 == 0)   // theta folding needs the mirror of every row
+    k_plane_T_fold<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, lt, Ubar, c);
+  else
+    k_plane_T<T, C><<<grid1(nct), kThreads, smem, s>>>(p, t, lt, Ubar, c);
   return cudaGetLastError();
 }
 
