@@ -107,7 +107,7 @@ struct TcForm {
 
 struct TcShape {
   int Kpad, Npad, KC, tmem_cols;
-  size_t offA, offB, offOut, offBar, bytes, a_bytes, b_bytes;
+  size_t offA, offB, offBar, bytes, a_bytes, b_bytes;
 };
 
 template <int KIND>
@@ -124,8 +124,7 @@ __host__ __device__ inline TcShape tc_shape(int Nr) {
   s.b_bytes = (size_t)s.Npad * s.Kpad * Fm::EB;
   s.offA = 0;                                                 // NTERM data terms
   s.offB = Fm::NTERM * s.a_bytes;                             // NTERM matrix terms
-  s.offOut = s.offB + Fm::NTERM * s.b_bytes;                  // [Nr][128] results
-  s.offBar = s.offOut + (size_t)Nr * 128 * 4;
+  s.offBar = s.offB + Fm::NTERM * s.b_bytes;
   s.offBar = (s.offBar + 15) / 16 * 16;
   s.bytes = s.offBar + 32;                                    // 2 mbarriers + TMEM slot
   return s;
@@ -138,24 +137,54 @@ __device__ __forceinline__ uint32_t core_off(int row, int k, int KC) {
   return (uint32_t)((((row >> 3) * KC + k / KE) << 7) + ((row & 7) << 4) + (k % KE) * EB);
 }
 
-// Split one value into the operand terms, written at byte offset o of each
-// term's tile (term stride a_bytes).
+// Split one core row (KE consecutive K elements of one operand row, 16 bytes
+// per term) into the operand terms and store each term with one 16-byte store
+// at byte offset o of its tile (term stride a_bytes): a load phase of 8 lanes
+// writes one whole 128-byte core matrix.
 template <int KIND>
-__device__ __forceinline__ void split_store(float v, unsigned char* sA, uint32_t o, size_t stride) {
+__device__ __forceinline__ void split_store_row(const float (&v)[TcForm<KIND>::KE],
+                                                unsigned char* sA, uint32_t o, size_t stride) {
   if constexpr (KIND == TC_TF32X3) {
-    const uint32_t hi = tf32_rna(v);
-    const uint32_t lo = tf32_rna(v - __uint_as_float(hi));
-    *reinterpret_cast<uint32_t*>(sA + o) = hi;
-    *reinterpret_cast<uint32_t*>(sA + stride + o) = lo;
+    uint4 hi, lo;
+    uint32_t* h = reinterpret_cast<uint32_t*>(&hi);
+    uint32_t* w = reinterpret_cast<uint32_t*>(&lo);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = tf32_rna(v[e]);
+      w[e] = tf32_rna(v[e] - __uint_as_float(h[e]));
+    }
+    *reinterpret_cast<uint4*>(sA + o) = hi;
+    *reinterpret_cast<uint4*>(sA + stride + o) = lo;
   } else {
-    const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(b0);
-    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-    const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
-    *reinterpret_cast<__nv_bfloat16*>(sA + o) = b0;
-    *reinterpret_cast<__nv_bfloat16*>(sA + stride + o) = b1;
-    *reinterpret_cast<__nv_bfloat16*>(sA + 2 * stride + o) = b2;
+    uint4 t0, t1, t2;
+    __nv_bfloat16* b0 = reinterpret_cast<__nv_bfloat16*>(&t0);
+    __nv_bfloat16* b1 = reinterpret_cast<__nv_bfloat16*>(&t1);
+    __nv_bfloat16* b2 = reinterpret_cast<__nv_bfloat16*>(&t2);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      b0[e] = __float2bfloat16_rn(v[e]);
+      const float r1 = v[e] - __bfloat162float(b0[e]);
+      b1[e] = __float2bfloat16_rn(r1);
+      b2[e] = __float2bfloat16_rn(r1 - __bfloat162float(b1[e]));
+    }
+    *reinterpret_cast<uint4*>(sA + o) = t0;
+    *reinterpret_cast<uint4*>(sA + stride + o) = t1;
+    *reinterpret_cast<uint4*>(sA + 2 * stride + o) = t2;
   }
+}
+
+// 16 consecutive TMEM columns of this warp's 32 lanes (one per thread).
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
 template <int KIND>
@@ -170,7 +199,6 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
   const TcShape sh = tc_shape<KIND>(Nr);
   unsigned char* sA = smem_raw + sh.offA;
   unsigned char* sB = smem_raw + sh.offB;
-  float* sOut = reinterpret_cast<float*>(smem_raw + sh.offOut);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + sh.offBar);   // [0] copy, [1] mma
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem_raw + sh.offBar + 16);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -207,13 +235,18 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
                  :: "r"(smem_u32(tslot)), "r"(sh.tmem_cols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // data tile -> A operand terms (rows = columns w, K = radial node); columns
-  // beyond the tile and nodes beyond N_r are zero
-  for (int x = tid; x < sh.Kpad * 128; x += 128) {
-    const int k = x >> 7, w = x & 127;
-    float v = 0.f;
-    if (k < Nr && w < Wc) v = U[base + (long long)k * d.S_i + w];
-    split_store<KIND>(v, sA, core_off<Fm::KE, Fm::EB>(w, k, sh.KC), sh.a_bytes);
+  // data tile -> A operand terms (rows = columns w, K = radial node), one core
+  // row (KE nodes of one column) per thread and step; columns beyond the tile
+  // and nodes beyond N_r are zero
+  for (int x = tid; x < sh.KC * 128; x += 128) {
+    const int kq = x >> 7, w = x & 127;
+    float v[Fm::KE];
+#pragma unroll
+    for (int e = 0; e < Fm::KE; ++e) {
+      const int kk = kq * Fm::KE + e;
+      v[e] = (kk < Nr && w < Wc) ? U[base + (long long)kk * d.S_i + w] : 0.f;
+    }
+    split_store_row<KIND>(v, sA, core_off<Fm::KE, Fm::EB>(w, kq * Fm::KE, sh.KC), sh.a_bytes);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -262,20 +295,65 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
     mbar_wait(bar0, 0);  // let our own copies land before the CTA exits
     if (ok) mbar_wait(bar1, 0);
   } else {
-    // TMEM -> registers -> shared: this thread's column w = tid (TMEM lane)
+    // epilogue on this thread's r-line (column w = TMEM lane): r term, Tau rows,
+    // stage update, reading the products from TMEM 16 rows at a time (the
+    // loads of a warp are issued by all its lanes); the loads of each 16-row
+    // group are all issued before any of its stores
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c = 0; c < sh.Npad; c += 16) {
-      uint32_t r[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-            "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(lane_base + (uint32_t)c));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int w = tid;
+    const bool act = w < Wc;
+    const int k = act ? (c0 + w) / NP : 0;
+    const float ck = sgn * t.cosT[k];
+    const int b = t.cosT[k] > 0.f ? 0 : Nr - 1;
+    float dv[16];
+    tmem_ld16(lane_base + (uint32_t)((Nr - 1) / 16 * 16), dv);   // group holding row N
+    const float dN = dv[(Nr - 1) % 16];
+    tmem_ld16(lane_base, dv);                                    // group holding row 0
+    const float db = b == 0 ? dv[0] : dN;
+    const float kb = act ? Kin[base + (long long)b * d.S_i + w] + ck * db : 0.f;
+    const float tb = t.tsign[b];
+    for (int c = 0; c < Nr; c += 16) {
+      if (c > 0) tmem_ld16(lane_base + (uint32_t)c, dv);
+      if (!act) continue;
+      float kv[16], f[16], ac[16];
 #pragma unroll
-      for (int e = 0; e < 16; ++e)
-        if (c + e < Nr) sOut[(c + e) * 128 + tid] = __uint_as_float(r[e]);
+      for (int e = 0; e < 16; ++e) {
+        const int i = c + e;
+        if (i < Nr) {
+          const long long gi = base + (long long)i * d.S_i + w;
+          kv[e] = Kin[gi];
+          if (mode != RAD_RHS) f[e] = F[gi];
+          if (mode != RAD_RHS && mode != RAD_STAGE0) ac[e] = Acc[gi];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int i = c + e;
+        if (i >= Nr) break;
+        const long long gi = base + (long long)i * d.S_i + w;
+        float v = kv[e] + ck * dv[e];
+        if (tau) v -= kb * tb * t.tsign[i];
+        switch (mode) {
+          case RAD_RHS:
+            out[gi] = v;
+            break;
+          case RAD_STAGE0:
+            Acc[gi] = v;
+            Uout[gi] = f[e] + 0.5f * dt * v;
+            break;
+          case RAD_STAGE1:
+            Acc[gi] = ac[e] + 2.f * v;
+            Uout[gi] = f[e] + 0.5f * dt * v;
+            break;
+          case RAD_STAGE2:
+            Acc[gi] = ac[e] + 2.f * v;
+            Uout[gi] = f[e] + dt * v;
+            break;
+          default:
+            F[gi] = f[e] + dt / 6.f * (ac[e] + v);
+            break;
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -284,58 +362,6 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                  :: "r"(tmem), "r"(sh.tmem_cols) : "memory");
-  }
-  if (!all_done) return;
-  // epilogue on this thread's r-line: r term, Tau rows, stage update; rows in
-  // groups of RG whose loads are all issued before any of their stores
-  const int w = tid;
-  if (w >= Wc) return;
-  const int k = (c0 + w) / NP;
-  const float ck = sgn * t.cosT[k];
-  const int b = t.cosT[k] > 0.f ? 0 : Nr - 1;
-  const float kb = Kin[base + (long long)b * d.S_i + w] + ck * sOut[b * 128 + w];
-  const float tb = t.tsign[b];
-  constexpr int RG = 8;
-  for (int i0 = 0; i0 < Nr; i0 += RG) {
-    float kv[RG], f[RG], ac[RG];
-#pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      const int i = i0 + r;
-      if (i < Nr) {
-        const long long gi = base + (long long)i * d.S_i + w;
-        kv[r] = Kin[gi];
-        if (mode != RAD_RHS) f[r] = F[gi];
-        if (mode != RAD_RHS && mode != RAD_STAGE0) ac[r] = Acc[gi];
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      const int i = i0 + r;
-      if (i >= Nr) break;
-      const long long gi = base + (long long)i * d.S_i + w;
-      float v = kv[r] + ck * sOut[i * 128 + w];
-      if (tau) v -= kb * tb * t.tsign[i];
-      switch (mode) {
-        case RAD_RHS:
-          out[gi] = v;
-          break;
-        case RAD_STAGE0:
-          Acc[gi] = v;
-          Uout[gi] = f[r] + 0.5f * dt * v;
-          break;
-        case RAD_STAGE1:
-          Acc[gi] = ac[r] + 2.f * v;
-          Uout[gi] = f[r] + 0.5f * dt * v;
-          break;
-        case RAD_STAGE2:
-          Acc[gi] = ac[r] + 2.f * v;
-          Uout[gi] = f[r] + dt * v;
-          break;
-        default:
-          F[gi] = f[r] + dt / 6.f * (ac[r] + v);
-          break;
-      }
-    }
   }
 }
 

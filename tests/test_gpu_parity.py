@@ -289,3 +289,32 @@ def test_fp32_variants_against_oracle_on_register_blocked_grid(precision):
     Fg = cuda(F0, torch.float32)
     gg.step(Fg, dt, 40)
     assert rel_l2(host(Fg), op.run(F0, dt, 40)) < FP32_TOL
+
+
+def test_precision_variants_full_size_65x32_200_steps():
+    """The precision workload: 65 x 32^4 (68M points), one group, absorber
+    coefficients, 200 steps of every reduced-precision form against the GPU's
+    FP64 form (itself pinned to the oracle above): relative L2 <= 1e-5."""
+    ts = T()
+    dims = (0.2, 1.0, 65, 32, 32, 32, 32)
+    g64 = ts.Grid(*dims, groups=1, precision=ts.TS_FP64)
+    r, th, ph, Th, Ph = g64.nodes()
+    kap, eta, ks = I.absorber_fields(r, th, ph, groups=1)
+    F0 = I.seeded_smooth(r, th, ph, Th, Ph, 1104, 0.2, 1.0)[None]
+    gR1, gR2 = I.inflow_from(F0, 32)
+    dt = I.dt_rule(0.2, 1.0, 65)
+    g64.set_coeffs(kap, eta, ks, gR1, gR2)
+    ref = cuda(F0, torch.float64)
+    g64.step(ref, dt, 200)
+    ts.ts_sync_status(g64.handle)
+    ref_h = host(ref)
+    assert np.all(np.isfinite(ref_h))
+    del g64, ref
+    for prec in (ts.TS_FP32, ts.TS_FP32_R64, ts.TS_TF32X3, ts.TS_BF16X3):
+        g = ts.Grid(*dims, groups=1, precision=prec)
+        g.set_coeffs(kap, eta, ks, gR1, gR2)
+        F = cuda(F0, torch.float32)
+        g.step(F, dt, 200)
+        ts.ts_sync_status(g.handle)
+        assert rel_l2(host(F), ref_h) < FP32_TOL, prec
+        del g, F
