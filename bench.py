@@ -14,11 +14,14 @@ runs its own copy of the workload on its own GPU (weak scaling; no collective
 on the data path).
 
 Extra keys: roofline of the dominant kernel (per-launch device time from
-ts_step_profile; FP64 ALU peak derived from the nominal GB300 FP64 rate),
-end-to-end rate through ts_step_host (host buffers, copies inside the timed
-region), the FP32 variant and the adjoint step on the same workload, the CPU
-oracle timed on a bounded sample on this host's cores, and SM clocks sampled
-during the timed region.
+ts_step_profile; FP64 ALU peak derived from the SM count, the FP64 lanes per SM
+and the clock, with a measured DFMA-loop rate beside it), end-to-end rate
+through ts_step_host (host buffers, copies inside the timed region), the
+reduced-precision variants (FP32, FP32 + FP64 radial rows, tensor-core TF32x3
+and BF16x3) and the adjoint step on the same workload, the 64-problem batch,
+the differentiation workload (33 x 16^4, 8 groups, 200 steps with sqrt(N)
+checkpoints), the CPU oracle timed on a bounded sample on this host's cores,
+and SM clocks sampled during the timed region.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 project) on the host cores instead.
@@ -173,7 +176,7 @@ def even_odd_passes(dims, es):
     rbA = 4 if es == 4 else 2
     return {"angular": NT % rbA == 0 and NP % 8 == 0,
             "plane": Nt % 2 == 0 and Np % 2 == 0 and NP % 8 == 0,
-            "radial": Nr >= 9 and (Nr // 2) % rbA == 0 and (NT * NP) % 4 == 0}
+            "radial": Nr >= 9 and (Nr // 2) % 2 == 0 and (NT * NP) % 4 == 0}
 
 
 def plane_square(dims):

@@ -77,11 +77,10 @@ struct TileParams {
 };
 
 // Output rows per thread of the register-blocked passes: angular 2 in float and
-// 1 in double (each with its Theta mirror rows), radial 4 in float and 2 in
-// double, plane 2.
+// 1 in double (each with its Theta mirror rows), radial 2 (row pairs), plane 2.
 constexpr int kRBPlane = 2;
 __host__ __device__ constexpr int rb_ang(int elem_bytes) { return elem_bytes == 4 ? 2 : 1; }
-__host__ __device__ constexpr int rb_rad(int elem_bytes) { return elem_bytes == 4 ? 4 : 2; }
+__host__ __device__ constexpr int rb_rad(int elem_bytes) { return elem_bytes == 4 ? 2 : 2; }
 
 // Which forward passes of a grid can use the register-blocked even/odd form.
 inline int rb_mask(const Dims& d, int elem_bytes, int n64) {

@@ -1227,8 +1227,9 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
 }
 
 // One tile per CTA with the radial line length fixed at compile time.
+// Three CTAs per SM in float (its RB = 2 blocks fit 85 registers), two in double.
 template <typename T, typename C, int Nr_>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, sizeof(C) == 4 ? 3 : 2)
 k_radial_eo(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U, const T* Kin,
             C sgn, int tau, int mode, T* F, T* Acc, T* Uout, T* out, C dt, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

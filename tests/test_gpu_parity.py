@@ -318,3 +318,37 @@ def test_precision_variants_full_size_65x32_200_steps():
         ts.ts_sync_status(g.handle)
         assert rel_l2(host(F), ref_h) < FP32_TOL, prec
         del g, F
+
+
+# the largest line lengths the library accepts on each axis (N_r = 129, 64 nodes
+# on the angular axes) with the other axes small, and the smallest grid
+EXTREME = [(0.2, 1.0, 129, 4, 4, 4, 4), (0.2, 1.0, 9, 64, 64, 4, 4),
+           (0.2, 1.0, 9, 4, 4, 64, 64), (0.2, 1.0, 3, 2, 2, 2, 2)]
+
+
+@pytest.mark.parametrize("dims", EXTREME)
+def test_extreme_sizes_rhs_and_steps(dims):
+    """Stage derivative and 3 steps at the size limits, FP64 against the oracle
+    (bound: max(1e-12, 2 x the oracle's own rounding floor, measured here)) and
+    FP32 against the oracle (1e-5)."""
+    og, gg = pair(*dims, G=2)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    Ko = op.rhs(F0)
+    from oracle.transport import Grid as OGrid
+    og2 = OGrid(*dims, groups=2, summation="library")
+    floor = rel_l2(OProblem(og2, kap, eta, ks, gR1, gR2).rhs(F0), Ko)
+    tol = max(FP64_TOL, 2.0 * floor)
+    assert rel_l2(host(gg.rhs(cuda(F0))), Ko) < tol
+    # the radial step-size rule ignores the angular terms, which at 64 nodes near
+    # the poles need a far smaller step for a stable RK4 run: take 1e-5
+    dt = 1e-5
+    Fg = cuda(F0)
+    gg.step(Fg, dt, 3)
+    Fo = op.run(F0, dt, 3)
+    assert rel_l2(host(Fg), Fo) < tol
+    _, g32 = pair(*dims, G=2, precision=1)
+    g32.set_coeffs(kap, eta, ks, gR1, gR2)
+    F32 = cuda(F0, torch.float32)
+    g32.step(F32, dt, 3)
+    assert rel_l2(host(F32), Fo) < FP32_TOL
