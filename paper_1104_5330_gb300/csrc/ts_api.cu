@@ -359,6 +359,9 @@ void even_odd_tables(HostTables& h) {
   const int nT = (int)h.Theta.size(), nt = (int)h.theta.size();
   fold(h.PThT, nT, h.PeThT, h.PoThT);
   fold(h.QThT, nT, h.QeThT, h.QoThT);
+  // the angular pass takes the 1/2 of the Theta folding from its tables
+  for (Vec* v : {&h.PeThT, &h.PoThT, &h.QeThT, &h.QoThT})
+    for (double& x : *v) x *= 0.5;
   fold(h.PthT, nt, h.PethT, h.PothT);
   fold(h.QthT, nt, h.QethT, h.QothT);
   // the adjoint's operators: P^T, Q^T are read [in][out] as PthA, PThA (= P, Q)

@@ -375,12 +375,13 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
         C ps[CB], qd[CB], fa[CB], fb[CB];
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
-          ps[c] = (C)0.5 * (aO[r][c] + sg * aE[r][c]);
-          qd[c] = (C)0.5 * (bO[r][c] + sg * bE[r][c]);
+          // the folded tables carry the 1/2 of the Theta folding
+          ps[c] = aO[r][c] + sg * aE[r][c];
+          qd[c] = bO[r][c] + sg * bE[r][c];
           fa[c] = side ? gs[rm][c] : fs[r][c];
           fb[c] = side ? gd[rm][c] : fd[r][c];
         }
-        C sv[CB], dv[CB];   // F at (k, m), (k, m + NP/2) from the folded halves
+        C sv[CB], dv[CB];   // 2 F-halves at (k, m) from the folded halves: e + sg o
         if (collision) {
           C e1[CB], o1[CB], e2[CB], o2[CB];
           const int kk = k0 + r;
@@ -390,18 +391,19 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
           ld4<C>(qb + 3 * Q4 + kk * hP + p0, o2);
 #pragma unroll
           for (int c = 0; c < CB; ++c) {
-            sv[c] = (C)0.5 * (e1[c] + sg * o1[c]);
-            dv[c] = (C)0.5 * (e2[c] + sg * o2[c]);
+            sv[c] = e1[c] + sg * o1[c];
+            dv[c] = e2[c] + sg * o2[c];
           }
         }
+        const C kq = (C)0.25 * kks;   // F(k, m) = (sv + dv) / 4, F(k, m + NP/2) = (sv - dv) / 4
         T o1v[CB], o2v[CB];
 #pragma unroll
         for (int c = 0; c < CB; ++c) {
           C v1 = aT * (ps[c] + qd[c] + s1[c] * (fa[c] + fb[c]));
           C v2 = aT * (ps[c] - qd[c] + s2[c] * (fa[c] - fb[c]));
           if (collision) {
-            v1 += src - kks * (C)0.5 * (sv[c] + dv[c]);
-            v2 += src - kks * (C)0.5 * (sv[c] - dv[c]);
+            v1 += src - kq * (sv[c] + dv[c]);
+            v2 += src - kq * (sv[c] - dv[c]);
           }
           o1v[c] = (T)v1;
           o2v[c] = (T)v2;
