@@ -1068,15 +1068,19 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
   for (int v = threadIdx.x; v < 2 * n64 * W4; v += blockDim.x) {  // rows nearest the ends
     const int w0 = (v % W4) * 4, rr = v / W4;
     const int i = rr < n64 ? rr : N - (rr - n64);
-    double a[4] = {0, 0, 0, 0};
+    double a[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};   // even / odd ii: 8 chains
+#pragma unroll 8
     for (int ii = 0; ii < Nr; ++ii) {
       const double dv = Dr64[i * Nr + ii];
       T u[4];
       ld4<T>(Ub + ii * Si + w0, u);
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) a[cc] = fma(dv, (double)u[cc], a[cc]);
+      for (int cc = 0; cc < 4; ++cc) {
+        if (ii & 1) a2[cc] = fma(dv, (double)u[cc], a2[cc]);
+        else a[cc] = fma(dv, (double)u[cc], a[cc]);
+      }
     }
-    C r4[4] = {(C)a[0], (C)a[1], (C)a[2], (C)a[3]};
+    C r4[4] = {(C)(a[0] + a2[0]), (C)(a[1] + a2[1]), (C)(a[2] + a2[2]), (C)(a[3] + a2[3])};
     st4<C>(sR + rr * W + w0, r4);
   }
   __syncthreads();

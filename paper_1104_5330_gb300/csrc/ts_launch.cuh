@@ -235,7 +235,12 @@ cudaError_t Launch<T, C>::radial(const Problem& p, const Tables<C>& t, const dou
   }
   const Dims& d = p.d;
   const bool rb = p.tp.rb & 4;
-  const int W = p.tp.W > 0 ? p.tp.W : radial_W<T, C>(d, 2, rb);
+  int W = p.tp.W > 0 ? p.tp.W : radial_W<T, C>(d, 2, rb);
+  // the double-precision end rows are computed by 4 threads per 4 columns before
+  // the tile's barrier: twice the columns keep every thread of the CTA busy there
+  if (rb && p.n_fp64_rows > 0 && p.tp.W <= 0 && 2 * W <= d.NT * d.NP &&
+      smem_radial<C>(d, 2 * W, true) <= kSmemHalf)
+    W *= 2;
   const int S = d.NT * d.NP;
   const long long nct = (long long)d.G * d.Nt * d.Np * ((S + W - 1) / W);
   const int ta = tau ? 1 : 0;
