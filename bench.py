@@ -257,6 +257,7 @@ def oracle_rate(dims, warm, nsteps):
         res = pool.map(_oracle_task, [(dims, g, warm, nsteps) for g in range(G)])
     wall = max(r[0] for r in res)
     pts = sum(r[1] for r in res)
+    oracle_rate.single = statistics.median(r[1] / r[0] for r in res)   # one process alone
     return pts / wall, wall, cores
 
 
@@ -579,6 +580,7 @@ def run_ours(args, dims, wname):
         rate, wall, cores = oracle_rate(dims, 0, 3)
         line["cpu_baseline"] = {"value": rate, "unit": "point-updates/s", "cores": cores,
                                 "kind": "oracle",
+                                "single_thread_value": oracle_rate.single,
                                 "sample": f"3 RK4 steps of each of the {G} groups of {wname} "
                                           f"({wall:.1f} s wall, one process per group)"}
     if world > 1:
