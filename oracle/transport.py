@@ -8,8 +8,10 @@ What it computes (Bonazzola, Vasset & Peres 2011):
   dF/dt = -L_sph F + CT,
   L_sph = cos(Th) d_r + (1/r)[ sin(Th)cos(Ph) d_th + sin(Th)sin(Ph)/sin(th) d_ph
                                - sin(Th) d_Th - sin(Th)sin(Ph) cot(th) d_Ph ]   (Eq. Liouvsph, Sect. 4.1)
-  CT = eta - kappa F + kappa_s (J - F),  J = (1/4pi) int F dOmega            (Eq. Transp, Sect. 2.2,
-                                                                           isotropic kernel Eq. sigman, B = 0)
+  CT = eta - kappa F + kappa_s (J + b omega.H - F),                         (Eq. Transp, Sect. 2.2)
+  J = (1/4pi) int F dOmega, H = (1/4pi) int omega F dOmega, from the linearly
+  anisotropic kernel A (1 + b omega.omega') with kappa_s = 4 pi A (Eqs. sigmadif,
+  sigmatot, crossnun, crossnup); b = 0 is isotropic scattering
 on the phase-space grid (r, th, ph, Th, Ph) with energy groups as independent
 slices. Every per-axis derivative follows the paper's coefficient-space route
 (Sect. 5.1): nodal values -> spectral coefficients -> derivative in coefficient
@@ -377,10 +379,10 @@ class Grid:
         return F
 
     # ------------------------------------------------------------- moments
-    def moments(self, F):
-        """F0 = J, F1 = (1/4pi) int F omega dOmega (Cartesian components,
-        Eqs. omegax-omegaz and Fmom0), particle number N (Eq. Npho, with the
-        missing dTheta restored) and the radial fluxes J_R1, J_R2 (Eq. Flux)."""
+    def direction_cartesian(self):
+        """Cartesian components (ox, oy, oz) of the momentum direction omega at
+        every (th, ph, Th, Ph) node, Eqs. omegax-omegaz: omega = cos Th e_r +
+        sin Th cos Ph e_th + sin Th sin Ph e_ph. Shapes [th][ph][Th][Ph]."""
         th = self.theta.reshape(-1, 1, 1, 1)
         ph = self.phi.reshape(1, -1, 1, 1)
         Th = self.Theta.reshape(1, 1, -1, 1)
@@ -390,8 +392,19 @@ class Grid:
         oy = (np.cos(Th) * np.sin(th) * np.sin(ph) + np.sin(Th) * np.cos(Ph) * np.cos(th) * np.sin(ph)
               + np.sin(Th) * np.sin(Ph) * np.cos(ph))
         oz = np.cos(Th) * np.cos(th) - np.sin(Th) * np.cos(Ph) * np.sin(th)
+        shape = (self.Nt, self.Np, self.NT, self.NP)
+        return tuple(np.ascontiguousarray(np.broadcast_to(o, shape)) for o in (ox, oy, oz))
+
+    def first_moment(self, F):
+        """H = (1/4pi) int F omega dOmega, Cartesian components, [3][g][r][th][ph]."""
+        return np.stack([self.scattering_mean(F * o) for o in self.direction_cartesian()])
+
+    def moments(self, F):
+        """F0 = J, F1 = (1/4pi) int F omega dOmega (Cartesian components,
+        Eqs. omegax-omegaz and Fmom0), particle number N (Eq. Npho, with the
+        missing dTheta restored) and the radial fluxes J_R1, J_R2 (Eq. Flux)."""
         F0 = self.scattering_mean(F)
-        F1 = np.stack([self.scattering_mean(F * o) for o in (ox, oy, oz)])
+        F1 = self.first_moment(F)
         n_dir = self.sphere_integral(F)                                  # [g][r][th][ph]
         n_pos = self.fejer_integral(self.trapezoid_periodic(n_dir, -1), -1)   # [g][r]
         r2 = (self.r ** 2)[None, :]
@@ -420,12 +433,18 @@ class Problem:
     """Grid + coefficient fields + boundary data + scheme options."""
 
     def __init__(self, grid, kappa=None, eta=None, kappa_s=None, g_R1=None, g_R2=None,
-                 bc="tau", scheme="rk4", filter_on=False, filter_alpha=36.0, filter_order=16):
+                 bc="tau", scheme="rk4", filter_on=False, filter_alpha=36.0, filter_order=16,
+                 scatter_b=None):
+        """scatter_b: the ratio b = B/A of the linearly anisotropic scattering
+        kernel A (1 + b omega.omega') (Eqs. sigmadif, crossnun, crossnup), a
+        [g][r][th][ph] field or a scalar; None or 0 is isotropic scattering."""
         self.g = grid
         z = np.zeros((grid.G, grid.Nr, grid.Nt, grid.Np))
         self.kappa = z if kappa is None else np.asarray(kappa, dtype=np.float64)
         self.eta = z if eta is None else np.asarray(eta, dtype=np.float64)
         self.kappa_s = z if kappa_s is None else np.asarray(kappa_s, dtype=np.float64)
+        self.scatter_b = z if scatter_b is None else np.broadcast_to(
+            np.asarray(scatter_b, dtype=np.float64), z.shape)
         self.g_R1, self.g_R2 = g_R1, g_R2
         self.bc, self.scheme = bc, scheme
         self.filter_on, self.filter_alpha, self.filter_order = filter_on, filter_alpha, filter_order
@@ -434,8 +453,16 @@ class Problem:
         return a[..., None, None]
 
     def collision(self, F):
+        """CT = eta - kappa F - sigma_t F + int sigma_d(omega.omega') F(omega') dOmega'
+        with sigma_d = A (1 + b omega.omega') and kappa_s = sigma_t = 4 pi A:
+        CT = eta - kappa F + kappa_s (J + b omega.H - F), H the first moment."""
         J = self.g.scattering_mean(F)[..., None, None]
-        return self._c(self.eta) - self._c(self.kappa) * F + self._c(self.kappa_s) * (J - F)
+        CT = self._c(self.eta) - self._c(self.kappa) * F + self._c(self.kappa_s) * (J - F)
+        if np.any(self.scatter_b != 0):
+            H = self.g.first_moment(F)
+            wH = sum(o * h[..., None, None] for o, h in zip(self.g.direction_cartesian(), H))
+            CT = CT + self._c(self.kappa_s * self.scatter_b) * wH
+        return CT
 
     def rhs(self, F, streaming_only=False):
         """One stage derivative K = Tau(-L F + CT) (Eq. Transpfpsph)."""
@@ -466,14 +493,26 @@ class Problem:
         return Fn
 
     def implicit_collision(self, Fs, dt):
-        """Backward Euler for dF/dt = CT solved in closed form:
-        J+ = (J* + dt eta)/(1 + dt kappa),
-        F+ = (F* + dt (eta + kappa_s J+))/(1 + dt (kappa + kappa_s))."""
-        Js = self.g.scattering_mean(Fs)
-        Jp = (Js + dt * self.eta) / (1.0 + dt * self.kappa)
-        Fp = ((Fs + dt * self._c(self.eta + self.kappa_s * Jp))
-              / self._c(1.0 + dt * (self.kappa + self.kappa_s)))
-        return Fp
+        """Backward Euler F+ = F* + dt CT(F+), solved exactly. CT couples the
+        directions only through the moments l_a(F) = (1/4pi) int phi_a F dOmega
+        of phi = (1, ox, oy, oz) with weights c = (1, b, b, b):
+          (1 + dt (kappa + kappa_s)) F+ = F* + dt eta + dt kappa_s sum_a c_a phi_a L_a,
+        L_a = l_a(F+). Applying l_b gives, per position, the 4 x 4 system
+          (1 + dt (kappa + kappa_s)) L_b - dt kappa_s sum_a c_a G_ba L_a = l_b(F* + dt eta),
+        G_ba = l_b(phi_a) (the quadrature's own Gram matrix); then F+ from L.
+        Isotropic case (b = 0): J+ = (J* + dt eta)/(1 + dt kappa)."""
+        g = self.g
+        phi = (np.ones_like(g.direction_cartesian()[0]),) + g.direction_cartesian()
+        Gm = np.stack([np.stack([g.scattering_mean(pb * pa) for pa in phi], -1) for pb in phi], -2)
+        rhs_F = Fs + dt * self._c(self.eta)
+        rhs = np.stack([g.scattering_mean(rhs_F * pb) for pb in phi], -1)      # [g][r][th][ph][4]
+        den = 1.0 + dt * (self.kappa + self.kappa_s)
+        c = np.stack([np.ones_like(self.scatter_b)] + [self.scatter_b] * 3, -1)  # [g][r][th][ph][4]
+        M = (den[..., None, None] * np.eye(4)
+             - dt * self.kappa_s[..., None, None] * Gm[None, None] * c[..., None, :])
+        L = np.linalg.solve(M, rhs[..., None])[..., 0]
+        src = sum(phi[a] * (c[..., a] * L[..., a])[..., None, None] for a in range(4))
+        return (rhs_F + dt * self._c(self.kappa_s) * src) / self._c(den)
 
     def step(self, F, dt):
         if self.scheme == "rk4":
@@ -496,11 +535,19 @@ class Problem:
 
     # ------------------------------------------------------------- adjoint
     def _A_T(self, lam):
-        """Transpose of the linear stage operator U -> -L U - kappa U + kappa_s (J(U) - U)."""
+        """Transpose of the linear stage operator
+        U -> -L U - kappa U + kappa_s (J(U) + b omega.H(U) - U), with J(U) = sum q U
+        and H(U) = sum q omega U: the scattering part transposes to
+        q (sum kappa_s lam) + q omega . (sum kappa_s b omega lam)."""
         q = self._q
         s = np.sum(self._c(self.kappa_s) * lam, axis=(-2, -1), keepdims=True)
-        return (-self.g.liouville_T(lam) - self._c(self.kappa) * lam
-                + q * s - self._c(self.kappa_s) * lam)
+        out = (-self.g.liouville_T(lam) - self._c(self.kappa) * lam
+               + q * s - self._c(self.kappa_s) * lam)
+        if np.any(self.scatter_b != 0):
+            kb = self._c(self.kappa_s * self.scatter_b)
+            for o in self.g.direction_cartesian():
+                out = out + q * o * np.sum(kb * o * lam, axis=(-2, -1), keepdims=True)
+        return out
 
     def adjoint_step(self, F_n, lam, dt):
         """Discrete adjoint of one RK4 step (plain RK4 scheme, filter off).
@@ -532,6 +579,17 @@ class Problem:
             lam_n = lam_n + Ubar
             Ubar_next = Ubar
         return lam_n, gk, ge
+
+
+def nucleon_scattering(A_n, A_p):
+    """Scattering of neutrinos on neutrons and protons (Eqs. cross, crossnun,
+    crossnup, Sect. 6): sigma^D = A_n (1 - omega.omega'/3) + A_p (1 - omega.omega'/10).
+    Returns (kappa_s, b) of the single kernel (kappa_s/4pi)(1 + b omega.omega'):
+    kappa_s = 4 pi (A_n + A_p), b = -(A_n/3 + A_p/10)/(A_n + A_p)."""
+    A_n = np.asarray(A_n, dtype=np.float64)
+    A_p = np.asarray(A_p, dtype=np.float64)
+    A = A_n + A_p
+    return 4 * np.pi * A, -(A_n / 3.0 + A_p / 10.0) / A
 
 
 def exact_free_streaming(grid, F0_of, t):

@@ -16,7 +16,7 @@ import numpy.polynomial.chebyshev as npcheb
 import pytest
 
 import analytic as A
-from oracle.transport import Grid, Problem, exact_free_streaming
+from oracle.transport import Grid, Problem, exact_free_streaming, nucleon_scattering
 from paper_1104_5330_gb300 import inputs as I
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
@@ -116,7 +116,7 @@ def pin_conservation(grid):
     return abs(NK[0] + J2[0] - J1[0]) / (abs(J1[0]) + abs(J2[0]) + abs(NF[0]))
 
 
-def pin_adjoint_fd(nsteps=4, seed=3):
+def pin_adjoint_fd(nsteps=4, seed=3, scatter_b=None):
     g = Grid(0.2, 1.0, 9, 6, 8, 6, 8, groups=2)
     kap, eta, ks = I.gradient_fields(g.r, g.theta, g.phi, 2, 1104, 0.2, 1.0)
     F0 = np.stack([I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 1104 + k, 0.2, 1.0) for k in range(2)])
@@ -125,10 +125,10 @@ def pin_adjoint_fd(nsteps=4, seed=3):
     w = g.outgoing_flux_weights()
 
     def obj(k, e):
-        p = Problem(g, k, e, ks, gR1, gR2)
+        p = Problem(g, k, e, ks, gR1, gR2, scatter_b=scatter_b)
         return np.sum(w * p.run(F0, dt, nsteps)[:, -1])
 
-    pr = Problem(g, kap, eta, ks, gR1, gR2)
+    pr = Problem(g, kap, eta, ks, gR1, gR2, scatter_b=scatter_b)
     Fs = [F0]
     for _ in range(nsteps):
         Fs.append(pr.rk4_step(Fs[-1], dt))
@@ -153,6 +153,52 @@ def pin_adjoint_fd(nsteps=4, seed=3):
                 fd = (obj(kap, eta + eps * v) - obj(kap, eta - eps * v)) / (2 * eps)
             worst = max(worst, abs(fd - np.sum(G_ * v)) / max(abs(fd), 1e-30))
     return worst
+
+
+def pin_anisotropic(g, seed=11):
+    """The kernel (kappa_s/4pi)(1 + b omega.omega') of Eqs. (sigmadif, crossnun)
+    acts on direction functions of degree l <= 2 by fixed factors: 0 on the
+    isotropic part (number kept, App. A), -kappa_s (1 - b/3) on the first moment
+    (the damping 4 pi (a - b/3) n of Eqs. mom1, optdep) and -kappa_s on l = 2
+    (no second-moment term in the kernel). Checked on the local-frame components
+    of omega, on the Cartesian omega_z of Eq. (omegaz) and on three l = 2
+    functions, with kappa_s and b varying from point to point."""
+    rng = np.random.default_rng(seed)
+    shp = (1, g.Nr, g.Nt, g.Np)
+    ks = rng.uniform(0.5, 2.0, shp)
+    b = rng.uniform(-1.0, 1.0, shp)
+    pr = Problem(g, kappa_s=ks, scatter_b=b, bc="none")
+    Th, Ph = g.Theta[:, None], g.Phi[None, :]
+    oz = I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi)[2]
+    l1 = 1.0 - b / 3.0
+    cases = [(np.ones((g.NT, g.NP)), 0.0),
+             (np.cos(Th) + 0 * Ph, l1), (np.sin(Th) * np.cos(Ph), l1),
+             (np.sin(Th) * np.sin(Ph), l1), (oz, l1),
+             (3 * np.cos(Th) ** 2 - 1 + 0 * Ph, 1.0), (np.sin(Th) ** 2 * np.cos(2 * Ph), 1.0),
+             (np.sin(Th) * np.cos(Th) * np.cos(Ph), 1.0)]
+    worst = 0.0
+    for f, factor in cases:
+        F = np.ascontiguousarray(np.broadcast_to(f, g.shape))
+        expect = -(ks * factor)[..., None, None] * F
+        worst = max(worst, np.abs(pr.collision(F) - expect).max() / np.abs(F).max())
+    return worst
+
+
+def pin_anisotropic_relaxation(nsteps=20, dt=0.01, ks=0.9, b=-1.0 / 3.0):
+    """Homogeneous medium, direction-only data F0 = 1 + c.omega + (omega_z^2 - 1/3)
+    (L F = 0 by Eq. propf): the RK4 solution is 1 + c.omega R(-ks (1 - b/3) dt)^n
+    + (omega_z^2 - 1/3) R(-ks dt)^n, R the RK4 polynomial (Eqs. mom1, optdep)."""
+    g = Grid(0.2, 1.0, 5, 8, 12, 8, 12)
+    ox, oy, oz = I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi)
+    c = (0.4, -0.7, 0.25)
+    F1 = c[0] * ox + c[1] * oy + c[2] * oz
+    F2 = oz ** 2 - 1.0 / 3.0
+    F = np.ascontiguousarray(np.broadcast_to(1.0 + F1 + F2, g.shape))
+    pr = Problem(g, kappa_s=np.full((1, 5, 8, 12), ks), scatter_b=b, bc="none")
+    Fn = pr.run(F, dt, nsteps)
+    R = lambda z: 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    ex = 1.0 + F1 * R(-ks * (1 - b / 3) * dt) ** nsteps + F2 * R(-ks * dt) ** nsteps
+    return np.abs(Fn - ex).max() / np.abs(ex).max()
 
 
 # ---------------------------------------------------------------------- tests
@@ -327,16 +373,68 @@ def test_filter_single_modes():
         assert np.abs(g.filter(F) - sig(k / 8) * F).max() < 1e-14
 
 
-def test_implicit_collision_solves_backward_euler():
+@pytest.mark.parametrize("aniso", [False, True])
+def test_implicit_collision_solves_backward_euler(aniso):
+    """F+ - dt CT(F+) = F* (the definition of the backward-Euler step), with the
+    isotropic and the linearly anisotropic kernel (b varying in [-1, 1])."""
     g = Grid(0.2, 1.0, 7, 6, 8, 6, 8)
     kap, eta, ks = I.absorber_fields(g.r, g.theta, g.phi)
     kap = kap * 40.0
+    b = np.random.default_rng(4).uniform(-1, 1, kap.shape) if aniso else None
     F = I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 3, 0.2, 1.0)[None]
-    pr = Problem(g, kap, eta, ks, scheme="split")
+    pr = Problem(g, kap, eta, ks * 20.0, scheme="split", scatter_b=b)
     dt = 0.05
     Fp = pr.implicit_collision(F, dt)
     res = Fp - F - dt * pr.collision(Fp)
     assert np.abs(res).max() < 1e-14 * np.abs(F).max() * 10
+    if aniso:   # the anisotropic part matters at this size
+        iso = Problem(g, kap, eta, ks * 20.0, scheme="split").implicit_collision(F, dt)
+        assert np.abs(iso - Fp).max() > 1e-3 * np.abs(F).max()
+
+
+def test_anisotropic_kernel_on_low_degree_functions():
+    assert pin_anisotropic(Grid(0.2, 1.0, 5, 6, 8, 8, 8)) < 1e-13
+    assert pin_anisotropic(Grid(0.3, 1.0, 4, 5, 6, 6, 10), seed=2) < 1e-13
+
+
+def test_anisotropic_scattering_balance_and_symmetry():
+    """App. A: the scattering integral conserves particle number, and with the
+    detailed-balance symmetry of the kernel (Eq. DBC) it is self-adjoint in the
+    quadrature's inner product: <G, S F>_q = <S G, F>_q for any F, G."""
+    g = Grid(0.2, 1.0, 4, 5, 6, 8, 10, groups=2)
+    rng = np.random.default_rng(8)
+    shp = (2, g.Nr, g.Nt, g.Np)
+    pr = Problem(g, kappa_s=rng.uniform(0.5, 2, shp), scatter_b=rng.uniform(-1, 1, shp), bc="none")
+    q = g.quadrature_weights_direction()
+    F, G = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    SF, SG = pr.collision(F), pr.collision(G)
+    assert np.abs((q * SF).sum(axis=(-2, -1))).max() < 1e-14 * np.abs(SF).max() * 10
+    lhs, rhs = (q * G * SF).sum(axis=(-2, -1)), (q * SG * F).sum(axis=(-2, -1))
+    assert np.abs(lhs - rhs).max() < 1e-13 * np.abs(lhs).max()
+
+
+def test_anisotropic_relaxation_of_the_first_moment():
+    assert pin_anisotropic_relaxation() < 1e-13
+    assert pin_anisotropic_relaxation(b=-0.1, ks=2.0) < 1e-13
+
+
+def test_nucleon_mixture_kernel():
+    """Eqs. (crossnun, crossnup): b = -1/3 on neutrons, -1/10 on protons; the
+    mixture's first-moment damping kappa_s (1 - b/3) equals the optical depth
+    4 pi (a - b_abs/3) of Eq. (optdep) with a = A_n + A_p, b_abs = -(A_n/3 + A_p/10)."""
+    assert nucleon_scattering(2.0, 0.0)[1] == pytest.approx(-1.0 / 3.0, abs=1e-15)
+    assert nucleon_scattering(0.0, 0.5)[1] == pytest.approx(-0.1, abs=1e-15)
+    An, Ap = np.array([0.3, 1.2, 0.0]), np.array([0.7, 0.1, 2.0])
+    ks, b = nucleon_scattering(An, Ap)
+    a, babs = An + Ap, -(An / 3 + Ap / 10)
+    assert np.allclose(ks, 4 * np.pi * a, rtol=1e-15)
+    assert np.allclose(ks * (1 - b / 3), 4 * np.pi * (a - babs / 3), rtol=1e-14)
+
+
+def test_adjoint_matches_finite_differences_anisotropic():
+    g = Grid(0.2, 1.0, 9, 6, 8, 6, 8, groups=2)
+    b = np.random.default_rng(9).uniform(-1, 1, (2, 9, 6, 8))
+    assert pin_adjoint_fd(nsteps=3, scatter_b=b) < 1e-6
 
 
 def test_adjoint_dot_products():
@@ -349,12 +447,13 @@ def test_adjoint_dot_products():
                      (g.d_Th, g.d_Th_T), (g.d_r, g.d_r_T)):
         assert abs(np.sum(fwd(F) * mu) - np.sum(F * bwd(mu))) < 1e-12 * scale
     kap, eta, ks = I.gradient_fields(g.r, g.theta, g.phi, 2, 5, 0.2, 1.0)
-    pr = Problem(g, kap, eta, ks)
     dt = I.dt_rule(0.2, 1.0, 9)
     d = rng.standard_normal(g.shape)
-    lam_n, _, _ = pr.adjoint_step(F, mu, dt)
-    lhs = np.sum((pr.rk4_step(F + d, dt) - pr.rk4_step(F, dt)) * mu)
-    assert abs(lhs - np.sum(d * lam_n)) < 1e-11 * abs(lhs)
+    for b in (None, rng.uniform(-1, 1, kap.shape)):
+        pr = Problem(g, kap, eta, ks * 30.0, scatter_b=b)
+        lam_n, _, _ = pr.adjoint_step(F, mu, dt)
+        lhs = np.sum((pr.rk4_step(F + d, dt) - pr.rk4_step(F, dt)) * mu)
+        assert abs(lhs - np.sum(d * lam_n)) < 1e-11 * abs(lhs)
 
 
 def test_adjoint_matches_finite_differences():
@@ -465,6 +564,35 @@ def _m10(mp):
     mp.setattr(Grid, "__init__", bad)
 
 
+@mutant("anisotropic term with the wrong sign")
+def _m11(mp):
+    orig = Problem.collision
+    def bad(self, F):
+        H = self.g.first_moment(F)
+        wH = sum(o * h[..., None, None] for o, h in zip(self.g.direction_cartesian(), H))
+        return orig(self, F) - 2 * self._c(self.kappa_s * self.scatter_b) * wH
+    mp.setattr(Problem, "collision", bad)
+
+
+@mutant("first moment without the 1/4pi")
+def _m12(mp):
+    mp.setattr(Grid, "first_moment", lambda self, F: np.stack(
+        [self.sphere_integral(F * o) for o in self.direction_cartesian()]))
+
+
+@mutant("transpose of the anisotropic term without the quadrature weight")
+def _m13(mp):
+    orig = Problem._A_T
+    def bad(self, lam):
+        out = orig(self, lam)
+        kb = self._c(self.kappa_s * self.scatter_b)
+        for o in self.g.direction_cartesian():
+            s = np.sum(kb * o * lam, axis=(-2, -1), keepdims=True)
+            out = out - self._q * o * s + o * s / (self.g.NT * self.g.NP)
+        return out
+    mp.setattr(Problem, "_A_T", bad)
+
+
 def _all_pins_pass():
     small = Grid(0.2, 1.0, 9, 8, 8, 8, 8)
     checks = [
@@ -474,7 +602,8 @@ def _all_pins_pass():
         lambda: pin_tau(Grid(0.2, 1.0, 9, 4, 4, 6, 4)) < 1e-11,
         lambda: pin_free_streaming(17, 8, T=0.05) < 0.05,
         lambda: pin_conservation(Grid(0.2, 1.0, 12, 8, 8, 8, 8)) < 1e-12,
-        lambda: pin_adjoint_fd(nsteps=2) < 1e-6,
+        lambda: pin_adjoint_fd(nsteps=2, scatter_b=-0.5) < 1e-6,
+        lambda: pin_anisotropic(Grid(0.2, 1.0, 4, 5, 6, 6, 8)) < 1e-13,
     ]
     for c in checks:
         try:
