@@ -18,7 +18,8 @@ ts_step_profile; FP64 ALU peak derived from the SM count, the FP64 lanes per SM
 and the clock, with a measured DFMA-loop rate beside it), end-to-end rate
 through ts_step_host (host buffers, copies inside the timed region), the
 reduced-precision variants (FP32, FP32 + FP64 radial rows, tensor-core TF32x3
-and BF16x3) and the adjoint step on the same workload, the 64-problem batch,
+and BF16x3) and the adjoint step on the same workload, the same grid with
+linearly anisotropic neutrino-nucleon scattering, the 64-problem batch,
 the differentiation workload (33 x 16^4, 8 groups, 200 steps with sqrt(N)
 checkpoints), the CPU oracle timed on a bounded sample on this host's cores,
 and SM clocks sampled during the timed region.
@@ -385,6 +386,49 @@ def run_batch(args, stream):
     return out
 
 
+def run_anisotropic(args, dims, stream):
+    """The default grid with neutrino scattering on a neutron / proton mixture:
+    kernel (kappa_s/4pi)(1 + b omega.omega'), kappa_s = 4 pi (A_n + A_p),
+    b = -(A_n/3 + A_p/10)/(A_n + A_p) from seeded smooth amplitude fields, FP64,
+    RK4 + Tau rows. Reports the step rate and the angular pass's per-launch time
+    beside that of the isotropic form on the same grid."""
+    import torch
+    import paper_1104_5330_gb300.ts as ts
+    from paper_1104_5330_gb300 import inputs as I
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=ts.TS_FP64)
+    r, th, ph, Th, Ph = gg.nodes()
+    kap, eta, _ = I.absorber_fields(r, th, ph, groups=G)
+    ks, b = ts.nucleon_scattering(*I.nucleon_densities(r, th, ph, G, 1104, R1, R2))
+    F0 = np.stack([I.seeded_smooth(r, th, ph, Th, Ph, 1104 + g, R1, R2) for g in range(G)])
+    gR1, gR2 = I.inflow_from(F0, NT)
+    gg.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(R1, R2, Nr)
+    F = torch.as_tensor(F0, dtype=torch.float64, device="cuda").contiguous()
+    out = {}
+    for name, bb in (("isotropic", None), ("anisotropic", b)):
+        gg.set_scattering_anisotropy(bb)
+        gg.step(F, dt, args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gg.step(F, dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        pm, pn = ts.ts_step_profile(gg.handle, F, dt, max(2, min(args.steps, 10)))
+        out[name] = (gg.points * args.steps / (ms * 1e-3), ms / args.steps, pm[0] / pn[0])
+    ts.ts_sync_status(gg.handle)
+    v, msps, ang = out["anisotropic"]
+    return {"value": v, "unit": "point-updates/s", "ms_per_step": msps, "dtype": "f64",
+            "workload": f"nucleon mixture on {Nr}x{Nt}x{Np}x{NT}x{NP}, {G} groups",
+            "b_range": [float(b.min()), float(b.max())],
+            "kappa_s_range": [float(ks.min()), float(ks.max())],
+            "angular_ms_per_launch": ang,
+            "isotropic_same_grid": {"value": out["isotropic"][0],
+                                    "angular_ms_per_launch": out["isotropic"][2]}}
+
+
 def run_ours(args, dims, wname):
     import torch
     import torch.distributed as dist
@@ -571,6 +615,8 @@ def run_ours(args, dims, wname):
                            "ms_per_step": msa / na, "dtype": "f64",
                            "includes": "forward recomputation of the stage inputs"}
 
+    if not args.skip_aniso:
+        line["anisotropic_scattering"] = run_anisotropic(args, dims, stream)
     if not args.skip_batch:
         line["batch"] = run_batch(args, stream)
     if not args.skip_diff and args.diff_steps > 0:
@@ -603,6 +649,7 @@ def main():
     ap.add_argument("--skip-variants", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-aniso", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--skip-diff", action="store_true")
     ap.add_argument("--diff-steps", type=int, default=200)

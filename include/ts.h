@@ -127,6 +127,20 @@ ts_status ts_set_coeffs(ts_grid* grid, const double* kappa, const double* eta,
                         const double* kappa_s, const void* inflow_R1,
                         const void* inflow_R2, void* stream);
 
+/* Make the scattering linearly anisotropic (Eqs. sigmadif, crossnun, crossnup,
+ * Sect. 3.1 and 6): the kernel becomes (kappa_s/4pi)(1 + b omega.omega'), so
+ *   CT = eta - kappa F + kappa_s (J + b omega.H - F),  H = (1/4pi) int omega F dOmega.
+ * b: [G][Nr][Ntheta][Nphi] double, DEVICE, copied into the grid on `stream`;
+ * b = -1/3 for neutrino-neutron and -1/10 for neutrino-proton scattering, and
+ * b = -(A_n/3 + A_p/10)/(A_n + A_p) with kappa_s = 4 pi (A_n + A_p) for their
+ * mixture (Eq. cross). The kernel is non-negative for |b| <= 1; values are not
+ * checked. NULL restores isotropic scattering (the default). Applies to every
+ * later ts_step (both schemes), ts_rhs, ts_adjoint_step and batched step of the
+ * grid. TS_ERR_UNSUPPORTED if NTheta < 3 or NPhi < 3 (the split scheme's
+ * closed form relies on the direction quadrature integrating omega_i omega_j
+ * exactly). The first call allocates one coefficient field on the device. */
+ts_status ts_set_scattering_anisotropy(ts_grid* grid, const double* b, void* stream);
+
 /* Set F = inflow data at the inflow nodes (r = R1 with cos Theta > 0, r = R2
  * with cos Theta < 0). Call once on initial data: the Tau rows of ts_step
  * then keep those values fixed. */

@@ -491,6 +491,7 @@ ts::Problem make_problem(const ts_grid* g) {
   p.kap = g->kap;
   p.eta = g->eta;
   p.kaps = g->kaps;
+  p.scb = g->aniso ? g->scb : nullptr;
   p.gR1 = g->gR1;
   p.gR2 = g->gR2;
   p.tc = !ts::tc_supported(g->d.Nr)             ? ts::TC_NONE
@@ -735,7 +736,8 @@ ts_status ts_destroy_grid(ts_grid* g) {
   if (!g) return TS_OK;
   cudaDeviceSynchronize();
   void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
-                  g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err, g->tcb16};
+                  g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err, g->tcb16,
+                  g->scb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : g->adj)
@@ -771,6 +773,31 @@ ts_status ts_set_coeffs(ts_grid* g, const double* kappa, const double* eta,
     if (e != cudaSuccess) return cuda_fail(e, "ts_set_coeffs");
   }
   g->coeffs = true;
+  return TS_OK;
+}
+
+ts_status ts_set_scattering_anisotropy(ts_grid* g, const double* b, void* stream) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  if (!b) {
+    g->aniso = false;
+    ++g->gen;
+    return TS_OK;
+  }
+  if (g->d.NT < 3 || g->d.NP < 3)
+    return fail(TS_ERR_UNSUPPORTED, "anisotropic scattering needs NTheta >= 3 and NPhi >= 3");
+  const size_t nc = (size_t)g->d.nblk * sizeof(double);
+  if (!g->scb) {
+    cudaError_t e = cudaMalloc((void**)&g->scb, nc);
+    if (e != cudaSuccess) {
+      g->scb = nullptr;
+      return cuda_fail(e, "ts_set_scattering_anisotropy");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(g->scb, b, nc, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ts_set_scattering_anisotropy");
+  g->aniso = true;
+  ++g->gen;
   return TS_OK;
 }
 

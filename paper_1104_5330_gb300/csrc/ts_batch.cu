@@ -234,6 +234,7 @@ struct ts_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<void*> lastF;
   std::vector<double> lastdt;
+  std::vector<unsigned> lastgen;   // per-problem ts_grid::gen at the last upload
 };
 
 namespace {
@@ -325,7 +326,8 @@ cudaError_t enqueue_step(ts_batch* b, cudaStream_t st) {
 template <typename T, typename C>
 ts_status batch_step(ts_batch* b, void* const* F, const double* dt, int nsteps, cudaStream_t user) {
   bool changed = b->lastF.empty();
-  for (int q = 0; q < b->n && !changed; ++q) changed = b->lastF[q] != F[q] || b->lastdt[q] != dt[q];
+  for (int q = 0; q < b->n && !changed; ++q)
+    changed = b->lastF[q] != F[q] || b->lastdt[q] != dt[q] || b->lastgen[q] != b->grids[q]->gen;
   cudaError_t e = cudaSuccess;
   if (changed) {
     e = cudaStreamSynchronize(b->st);  // the staging copy may still be read by an earlier upload
@@ -333,6 +335,8 @@ ts_status batch_step(ts_batch* b, void* const* F, const double* dt, int nsteps, 
     fill_items<T, C>(b, F, dt);
     b->lastF.assign(F, F + b->n);
     b->lastdt.assign(dt, dt + b->n);
+    b->lastgen.resize(b->n);
+    for (int q = 0; q < b->n; ++q) b->lastgen[q] = b->grids[q]->gen;
   }
   e = cudaEventRecord(b->ev_in, user);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev_in, 0);

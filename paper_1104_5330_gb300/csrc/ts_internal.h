@@ -82,6 +82,12 @@ constexpr int kRBPlane = 2;
 __host__ __device__ constexpr int rb_ang(int elem_bytes) { return elem_bytes == 4 ? 2 : 1; }
 __host__ __device__ constexpr int rb_rad(int elem_bytes) { return elem_bytes == 4 ? 2 : 2; }
 
+// Per-block scalars of the angular passes. Register-blocked form: J, kappa,
+// eta, kappa_s, 1/r, cot(theta), kappa_s b, H_r, H_theta, H_phi (H: the first
+// angular moment in the local frame e_r, e_theta, e_phi); run-time form: J and H.
+constexpr int kAngScalars = 10;
+constexpr int kAngMoments = 4;
+
 // Which forward passes of a grid can use the register-blocked even/odd form.
 inline int rb_mask(const Dims& d, int elem_bytes, int n64) {
   int m = 0;
@@ -101,6 +107,8 @@ struct Problem {
   const double* kap; // [G][Nr][Nt][Np]
   const double* eta;
   const double* kaps;
+  const double* scb; // anisotropy b of the scattering kernel (kappa_s/4pi)(1 + b omega.omega'),
+                     // [G][Nr][Nt][Np]; NULL: isotropic scattering
   const void* gR1;   // inflow data, element type of the grid
   const void* gR2;
   int tc;            // TcKind: radial pass on the tensor cores (float grids)
@@ -204,6 +212,9 @@ struct ts_grid {
   void* io = nullptr;
   ts::TileParams tp{};   // tile shapes (0 = built-in heuristic); set by ts_autotune
   void* tcb16 = nullptr; // TS_BF16X3: bf16 terms of D_r (tensor-core B operand)
+  double* scb = nullptr; // anisotropy b of the scattering kernel (ts_set_scattering_anisotropy)
+  bool aniso = false;    // scb holds values in use
+  unsigned gen = 0;      // bumped when the launch parameters change (batched steps re-upload)
 };
 
 namespace ts {

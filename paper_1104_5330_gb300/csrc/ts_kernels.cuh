@@ -38,8 +38,10 @@ __device__ __forceinline__ void decode_block(const Dims& d, long long blk, int& 
 // ----------------------------------------------------------------------------
 // Pass 1 (forward): angular blocks. A CTA owns `nb` consecutive blocks, which
 // are contiguous in memory (block b = elements [b*S, (b+1)*S), S = NT*NP).
-// K = sgn * (a_Th dTh U + a_Ph dPh U) + [eta - (kappa+kappa_s) U + kappa_s J]
-// a_Th = -sin(Th)/r, a_Ph = -sin(Th) sin(Ph) cot(th)/r.
+// K = sgn * (a_Th dTh U + a_Ph dPh U) + [eta - (kappa+kappa_s) U + kappa_s (J + b omega.H)]
+// a_Th = -sin(Th)/r, a_Ph = -sin(Th) sin(Ph) cot(th)/r; b: anisotropy of the
+// scattering kernel (p.scb, NULL = 0), H the first angular moment, taken in the
+// local frame: omega = cos(Th) e_r + sin(Th) cos(Ph) e_th + sin(Th) sin(Ph) e_ph.
 template <typename T, typename C>
 __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& t,
                                              const T* __restrict__ U, T* __restrict__ K, C sgn,
@@ -51,8 +53,9 @@ __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& 
   C* sB = sA + NT * NT;                    // BThT [k'][k]
   C* sD = sB + NT * NT;                    // DPhT [m'][m]
   C* su = sD + NP * NP;                    // tile [bb][k][m]
-  C* sJ = su + nb * S;                     // [nb]
+  C* sJ = su + nb * S;                     // [kAngMoments][nb]: J, H_r, H_th, H_ph
   const long long b0 = tile * nb;
+  const bool aniso = collision && p.scb != nullptr;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
     sA[x] = t.AThT[x];
@@ -65,10 +68,32 @@ __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& 
   if (collision) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
-      C acc = 0;
-      for (int x = lane; x < S; x += 32) acc = fmac(t.qdir[x / NP], su[bb * S + x], acc);
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) sJ[bb] = acc;
+      C acc = 0, hr = 0, ht = 0, hp = 0;
+      for (int x = lane; x < S; x += 32) {
+        const int k = x / NP, m = x - k * NP;
+        const C u = su[bb * S + x];
+        acc = fmac(t.qdir[k], u, acc);
+        if (aniso) {
+          const C qu = t.qdir[k] * u, qs = t.sinT[k] * qu;
+          hr = fmac(t.cosT[k], qu, hr);
+          ht = fmac(t.cosP[m], qs, ht);
+          hp = fmac(t.sinP[m], qs, hp);
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (aniso) {
+          hr += __shfl_xor_sync(0xffffffffu, hr, o);
+          ht += __shfl_xor_sync(0xffffffffu, ht, o);
+          hp += __shfl_xor_sync(0xffffffffu, hp, o);
+        }
+      }
+      if (lane == 0) {
+        sJ[bb] = acc;
+        sJ[nb + bb] = hr;
+        sJ[2 * nb + bb] = ht;
+        sJ[3 * nb + bb] = hp;
+      }
     }
     __syncthreads();
   }
@@ -92,6 +117,11 @@ __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& 
       const C u = ub[r];
       const C kap = (C)p.kap[blk], eta = (C)p.eta[blk], ks = (C)p.kaps[blk];
       v += eta - (kap + ks) * u + ks * sJ[bb];
+      if (aniso) {
+        const C kb = (C)(p.kaps[blk] * p.scb[blk]);
+        v += kb * (t.cosT[k] * sJ[nb + bb] +
+                   t.sinT[k] * (t.cosP[m] * sJ[2 * nb + bb] + t.sinP[m] * sJ[3 * nb + bb]));
+      }
     }
     K[blk * S + r] = (T)v;
   }
@@ -543,6 +573,7 @@ k_plane_T_fold(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__
 
 // Adjoint pass 1^T: angular blocks.
 //   Ubar_s = Ubar - D_Th^T(a_Th lt) - D_Ph^T(a_Ph lt) - (kappa+kappa_s) lt + kappa_s q_k sum lt
+//            + q_k omega . G,  G = kappa_s b sum_block omega lt  (anisotropic scattering)
 //   gk -= sum_block lt*Us,  ge += sum_block lt
 //   lam_out = lam_in + Ubar_s;   Kbar_out = wl*lam + wu*Ubar_s (if Kbar_out)
 // The transposed derivatives are folded as in the forward pass: D_Th^T on the
@@ -567,8 +598,9 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
   C* sMd = sMs + hP * hP;
   C* s1 = sMd + hP * hP;                    // a_Th lt folded: [bb][ES | OS | ED | OD][kk][p]
   C* s2 = s1 + nb * S;                      // a_Ph lt pair halves: [bb][sigma | delta][k][p]
-  C* sSum = s2 + nb * S;                    // [nb] kappa_s-weighted sum of lt
+  C* sSum = s2 + nb * S;                    // [kAngMoments][nb] kappa_s sum lt, G_r, G_th, G_ph
   const long long b0 = (long long)blockIdx.x * nb;
+  const bool aniso = p.scb != nullptr;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < hT * hT; x += blockDim.x) {
     sPe[x] = t.PeThA[x];
@@ -608,19 +640,37 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
-      double sl = 0, slu = 0;
+      double sl = 0, slu = 0, gr = 0, gt = 0, gp = 0;
       for (int x = lane; x < S; x += 32) {
         const double v = (double)lt[(b0 + bb) * S + x];
         sl += v;
         slu = fma(v, (double)Us[(b0 + bb) * S + x], slu);
+        if (aniso) {
+          const int k = x / NP, m = x - k * NP;
+          const double vs = (double)t.sinT[k] * v;
+          gr = fma((double)t.cosT[k], v, gr);
+          gt = fma((double)t.cosP[m], vs, gt);
+          gp = fma((double)t.sinP[m], vs, gp);
+        }
       }
       for (int o = 16; o; o >>= 1) {
         sl += __shfl_xor_sync(0xffffffffu, sl, o);
         slu += __shfl_xor_sync(0xffffffffu, slu, o);
+        if (aniso) {
+          gr += __shfl_xor_sync(0xffffffffu, gr, o);
+          gt += __shfl_xor_sync(0xffffffffu, gt, o);
+          gp += __shfl_xor_sync(0xffffffffu, gp, o);
+        }
       }
       if (lane == 0) {
         const long long blk = b0 + bb;
         sSum[bb] = (C)(p.kaps[blk] * sl);
+        if (aniso) {
+          const double kb = p.kaps[blk] * p.scb[blk];
+          sSum[nb + bb] = (C)(kb * gr);
+          sSum[2 * nb + bb] = (C)(kb * gt);
+          sSum[3 * nb + bb] = (C)(kb * gp);
+        }
         ge[blk] += sl;
         gk[blk] -= slu;
       }
@@ -649,6 +699,8 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
     }
     const long long blk = b0 + bb;
     const C kap = (C)p.kap[blk], ks = (C)p.kaps[blk];
+    // omega.G at (k, m) and (k, m + NP/2): cos(Th) G_r +- sin(Th) gc
+    const C gc = aniso ? t.cosP[m] * sSum[2 * nb + bb] + t.sinP[m] * sSum[3 * nb + bb] : (C)0;
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const int kr = side ? km : k;
@@ -656,9 +708,13 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
       const C ps = (C)0.5 * (aO + sg * aE), qd = (C)0.5 * (bO + sg * bE);
       const C f1 = (C)0.5 * (fs[side] + fd[side]), f2 = (C)0.5 * (fs[side] - fd[side]);
       const long long gi = blk * S + kr * NP + m;
-      const C qs = t.qdir[kr] * sSum[bb];
-      const C ub1 = (C)Ubar[gi] - (ps + qd) - f1 - (kap + ks) * (C)lt[gi] + qs;
-      const C ub2 = (C)Ubar[gi + hP] - (ps - qd) - f2 - (kap + ks) * (C)lt[gi + hP] + qs;
+      C qs = t.qdir[kr] * sSum[bb], qa = 0;
+      if (aniso) {
+        qs += t.qdir[kr] * t.cosT[kr] * sSum[nb + bb];
+        qa = t.qdir[kr] * t.sinT[kr] * gc;
+      }
+      const C ub1 = (C)Ubar[gi] - (ps + qd) - f1 - (kap + ks) * (C)lt[gi] + qs + qa;
+      const C ub2 = (C)Ubar[gi + hP] - (ps - qd) - f2 - (kap + ks) * (C)lt[gi + hP] + qs - qa;
       lam_out[gi] = (T)((C)lam_in[gi] + ub1);
       lam_out[gi + hP] = (T)((C)lam_in[gi + hP] + ub2);
       if (Kbar_out) {
@@ -672,7 +728,11 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
 // ----------------------------------------------------------------------------
 // Split scheme: backward-Euler collision step in closed form per angular block,
 //   J+ = (J* + dt eta)/(1 + dt kappa),  F+ = (F* + dt (eta + kappa_s J+))/(1 + dt (kappa+kappa_s)),
-// then F = inflow data at the inflow nodes (if the grid has Tau rows).
+// with anisotropic scattering also H+ = H*/(1 + dt (kappa + kappa_s) - dt kappa_s b/3) and
+// F+ += dt kappa_s b omega.H+ / (1 + dt (kappa+kappa_s)): the quadrature integrates
+// omega_i omega_j exactly (NTheta, NPhi >= 3), (1/4pi) sum q omega_i omega_j = delta_ij/3,
+// and the first moments of 1 vanish by symmetry. Then F = inflow data at the
+// inflow nodes (if the grid has Tau rows).
 template <typename T, typename C>
 __device__ __forceinline__ void implicit_collision_tile(const Problem& p, const Tables<C>& t,
                                                         T* F, double dt, int nb,
@@ -684,21 +744,50 @@ __device__ __forceinline__ void implicit_collision_tile(const Problem& p, const 
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const bool aniso = p.scb != nullptr;
   for (int bb = warp; bb < nbb; bb += nw) {
     const long long blk = b0 + bb;
-    double acc = 0;
-    for (int x = lane; x < S; x += 32) acc = fma((double)t.qdir[x / NP], (double)F[blk * S + x], acc);
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    double acc = 0, hr = 0, ht = 0, hp = 0;
+    for (int x = lane; x < S; x += 32) {
+      const int k = x / NP, m = x - k * NP;
+      const double u = (double)F[blk * S + x];
+      acc = fma((double)t.qdir[k], u, acc);
+      if (aniso) {
+        const double qu = (double)t.qdir[k] * u, qs = (double)t.sinT[k] * qu;
+        hr = fma((double)t.cosT[k], qu, hr);
+        ht = fma((double)t.cosP[m], qs, ht);
+        hp = fma((double)t.sinP[m], qs, hp);
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (aniso) {
+        hr += __shfl_xor_sync(0xffffffffu, hr, o);
+        ht += __shfl_xor_sync(0xffffffffu, ht, o);
+        hp += __shfl_xor_sync(0xffffffffu, hp, o);
+      }
+    }
     const double kap = p.kap[blk], eta = p.eta[blk], ks = p.kaps[blk];
     const double Jp = (acc + dt * eta) / (1.0 + dt * kap);
     const double num = dt * (eta + ks * Jp), den = 1.0 + dt * (kap + ks);
+    double kbr = 0, kbt = 0, kbp = 0;   // dt kappa_s b H+
+    if (aniso) {
+      const double kb = ks * p.scb[blk], f = dt * kb / (den - dt * kb / 3.0);
+      kbr = f * hr;
+      kbt = f * ht;
+      kbp = f * hp;
+    }
     int g, i, j, l;
     decode_block(d, blk, g, i, j, l);
     const T* g1 = reinterpret_cast<const T*>(p.gR1);
     const T* g2 = reinterpret_cast<const T*>(p.gR2);
     for (int x = lane; x < S; x += 32) {
       const int k = x / NP, m = x - k * NP;
-      double v = ((double)F[blk * S + x] + num) / den;
+      double v = (double)F[blk * S + x] + num;
+      if (aniso)
+        v += (double)t.cosT[k] * kbr +
+             (double)t.sinT[k] * ((double)t.cosP[m] * kbt + (double)t.sinP[m] * kbp);
+      v /= den;
       if (p.bc == TS_BC_TAU_INFLOW) {
         const long long pos = (((long long)g * d.Nt + j) * d.Np + l) * hT;
         if (i == 0 && k < hT) v = g1 ? (double)g1[(pos + k) * NP + m] : 0.0;

@@ -154,7 +154,7 @@ __host__ __device__ inline int rad_spec(const Dims& d) {
 //  * Phi through Ms, Md (the circulant Fourier derivative on the halves): half.
 // Shared layout: [PeT | PoT | QeT | QoT (NT/2 x NT/2 each) | MsPhT | MdPhT |
 //                 tile nb*S | folded halves nb*(S+8) | transposed halves
-//                 nb*(NP*UTP+8) | 6 nb per-block scalars]
+//                 nb*(NP*UTP+8) | kAngScalars nb per-block scalars]
 template <typename C>
 __device__ __forceinline__ void angular_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
                                                 C* sD) {
@@ -181,12 +181,13 @@ __device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int n
   for (int x = 4 * threadIdx.x; x < nbb * S; x += 4 * blockDim.x) copy4<ASYNC, T, C>(su + x, src + x);
 }
 
-// Preparation of a staged tile: coefficients, J, the folded halves
+// Preparation of a staged tile: coefficients, J (and, with anisotropic
+// scattering, kappa_s b and the first moment H), the folded halves
 // [se | so | de | do] ([k' < NT/2][p < NP/2] each) for the Theta contraction and
 // the pointwise terms, and the transposed halves uT[p][k] = s, uT[NP/2 + p][k] =
 // d for the Phi contraction. Entry: su complete and visible. Exit (after the
 // caller's barrier): su is no longer read.
-template <int NT_, int NP_, typename T, typename C>
+template <int NT_, int NP_, bool ANISO, typename T, typename C>
 __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C>& t,
                                                 const C* su, C* sSD, C* uT, C* sc, int collision,
                                                 int nb, long long tile) {
@@ -196,10 +197,12 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
   const int Q4 = hT * hP;   // one folded half
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
+  const bool aniso = ANISO && collision;
   for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // once per block
     sc[nb + x] = (C)p.kap[b0 + x];
     sc[2 * nb + x] = (C)p.eta[b0 + x];
     sc[3 * nb + x] = (C)p.kaps[b0 + x];
+    if (aniso) sc[6 * nb + x] = (C)(p.kaps[b0 + x] * p.scb[b0 + x]);
     int g, i, j, l;
     decode_block(d, b0 + x, g, i, j, l);
     sc[4 * nb + x] = t.inv_r[i];
@@ -259,21 +262,76 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
                   : (C)0;
       for (int o = tpb >> 1; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (act && (x % tpb) == 0) sc[bb] = acc;
+      if (aniso) {
+        // First moment in the local frame from the pair halves: cos(Theta) is odd
+        // under k -> NT-1-k, cos(Phi) and sin(Phi) under m -> m + NP/2, so
+        // H_r takes the Theta-odd part of the sums, H_theta and H_phi the
+        // Theta-even part of the differences.
+        C hr = 0, ht = 0, hp = 0;
+        if (act) {
+          C a1 = 0, a2 = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            a1 = fmac(t.cosP[p4 + c], e2[c], a1);
+            a2 = fmac(t.sinP[p4 + c], e2[c], a2);
+          }
+          const C qs = t.qdir[kk] * t.sinT[kk];
+          hr = t.qdir[kk] * t.cosT[kk] * ((o1[0] + o1[1]) + (o1[2] + o1[3]));
+          ht = qs * a1;
+          hp = qs * a2;
+        }
+        for (int o = tpb >> 1; o; o >>= 1) {
+          hr += __shfl_xor_sync(0xffffffffu, hr, o);
+          ht += __shfl_xor_sync(0xffffffffu, ht, o);
+          hp += __shfl_xor_sync(0xffffffffu, hp, o);
+        }
+        if (act && (x % tpb) == 0) {
+          sc[7 * nb + bb] = hr;
+          sc[8 * nb + bb] = ht;
+          sc[9 * nb + bb] = hp;
+        }
+      }
     }
   }
   if (collision && !warp_J) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
-      C acc = 0;
-      for (int x = lane; x < S; x += 32) acc = fmac(t.qdir[x / NP], su[bb * S + x], acc);
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) sc[bb] = acc;
+      C acc = 0, hr = 0, ht = 0, hp = 0;
+      for (int x = lane; x < S; x += 32) {
+        const int k = x / NP, m = x - k * NP;
+        const C u = su[bb * S + x];
+        acc = fmac(t.qdir[k], u, acc);
+        if (aniso) {
+          const C qu = t.qdir[k] * u, qs = t.sinT[k] * qu;
+          hr = fmac(t.cosT[k], qu, hr);
+          ht = fmac(t.cosP[m], qs, ht);
+          hp = fmac(t.sinP[m], qs, hp);
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (aniso) {
+          hr += __shfl_xor_sync(0xffffffffu, hr, o);
+          ht += __shfl_xor_sync(0xffffffffu, ht, o);
+          hp += __shfl_xor_sync(0xffffffffu, hp, o);
+        }
+      }
+      if (lane == 0) {
+        sc[bb] = acc;
+        if (aniso) {
+          sc[7 * nb + bb] = hr;
+          sc[8 * nb + bb] = ht;
+          sc[9 * nb + bb] = hp;
+        }
+      }
     }
   }
 }
 
 // Compute a prepared tile and write K. Reads sSD, uT, sc and the matrices.
-template <int NT_, int NP_, typename T, typename C>
+// ANISO: add the anisotropic scattering term (a separate instantiation keeps
+// the register allocation of the isotropic form unchanged).
+template <int NT_, int NP_, bool ANISO, typename T, typename C>
 __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Tables<C>& t,
                                                    const C* sSD, const C* uT, const C* sc,
                                                    const C* sP, const C* sQ, const C* sD,
@@ -287,6 +345,7 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int KR = hT / RB, PC = hP / CB;
+  constexpr bool aniso = ANISO;
   // unit = (pc, 4 blocks, kr, block group): a 16-byte load phase spans 4 blocks
   const int units = ((nbb + 3) / 4) * 4 * KR * PC;
   const C* sPe = sP;
@@ -357,6 +416,17 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
     const C ir = sc[4 * nb + bb], ct = sc[5 * nb + bb];
     const C J = sc[bb], kap = sc[nb + bb], eta = sc[2 * nb + bb], ks = sc[3 * nb + bb];
     const C src = eta + ks * J, kks = kap + ks;
+    // anisotropic scattering kappa_s b omega.H = cos(Th) hr + sin(Th) hc at m and
+    // cos(Th) hr - sin(Th) hc at m + NP/2
+    C hr = 0, hc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) hc[c] = 0;
+    if (aniso) {
+      const C kb = sc[6 * nb + bb], ht = kb * sc[8 * nb + bb], hp = kb * sc[9 * nb + bb];
+      hr = kb * sc[7 * nb + bb];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) hc[c] = t.cosP[p0 + c] * ht + t.sinP[p0 + c] * hp;
+    }
     C s1[CB], s2[CB];   // a_Phi / a_Theta at m and m + NP/2, with the 1/2 of the halves
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
@@ -405,6 +475,11 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
             v1 += src - kq * (sv[c] + dv[c]);
             v2 += src - kq * (sv[c] - dv[c]);
           }
+          if (aniso) {
+            const C ar = t.cosT[k] * hr, at = t.sinT[k] * hc[c];
+            v1 += ar + at;
+            v2 += ar - at;
+          }
           o1v[c] = (T)v1;
           o2v[c] = (T)v2;
         }
@@ -416,10 +491,10 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
   }
 }
 
-template <int NT_, int NP_, typename T, typename C>
-__device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C>& t,
-                                                const T* __restrict__ U, T* __restrict__ K,
-                                                C sgn, int collision, int nb, long long tile) {
+template <int NT_, int NP_, bool ANISO, typename T, typename C>
+__device__ __forceinline__ void angular_tile_rb_form(const Problem& p, const Tables<C>& t,
+                                                     const T* __restrict__ U, T* __restrict__ K,
+                                                     C sgn, int collision, int nb, long long tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims& d = p.d;
   const int NT = d.NT, NP = d.NP, S = NT * NP;
@@ -433,14 +508,28 @@ __device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C
   angular_rb_mats<C>(t, d, sP, sQ, sD);
   angular_rb_load<false, T, C>(d, U, nb, tile, su);
   __syncthreads();
-  angular_rb_prep<NT_, NP_, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+  angular_rb_prep<NT_, NP_, ANISO, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
   __syncthreads();
-  angular_rb_compute<NT_, NP_, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb, tile);
+  angular_rb_compute<NT_, NP_, ANISO, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb,
+                                            tile);
+}
+
+template <int NT_, int NP_, typename T, typename C>
+__device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C>& t,
+                                                const T* __restrict__ U, T* __restrict__ K,
+                                                C sgn, int collision, int nb, long long tile) {
+  if (collision && p.scb)
+    angular_tile_rb_form<NT_, NP_, true, T, C>(p, t, U, K, sgn, collision, nb, tile);
+  else
+    angular_tile_rb_form<NT_, NP_, false, T, C>(p, t, U, K, sgn, collision, nb, tile);
 }
 
 // Persistent: the next tile is copied into the staging buffer as soon as the
 // current one has been prepared, and lands while the current one is computed.
-template <typename T, typename C, int NT_, int NP_>
+// ANISO: the form with anisotropic scattering (launched when the grid has it
+// and the pass includes the collision term); a separate kernel, so that the
+// isotropic form keeps its own register allocation.
+template <typename T, typename C, int NT_, int NP_, bool ANISO>
 __global__ void __launch_bounds__(kThreads, 2)
 k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
              int collision, int nb, long long ntiles) {
@@ -461,13 +550,13 @@ k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K,
   for (; tile < ntiles; tile += gridDim.x) {
     cp_async_wait0();
     __syncthreads();   // this tile staged; the previous tile's compute is done
-    angular_rb_prep<NT_, NP_, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+    angular_rb_prep<NT_, NP_, ANISO, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
     __syncthreads();   // staging buffer free
     const long long next = tile + gridDim.x;
     if (next < ntiles) angular_rb_load<true, T, C>(d, U, nb, next, su);
     cp_async_commit();
-    angular_rb_compute<NT_, NP_, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb,
-                                       tile);
+    angular_rb_compute<NT_, NP_, ANISO, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision,
+                                              nb, tile);
   }
   cp_async_wait0();
 }

@@ -31,8 +31,9 @@ static inline unsigned grid1(long long n) { return (unsigned)n; }
 template <typename C>
 size_t smem_angular(const Dims& d, int nb, bool rb) {
   const size_t S = (size_t)d.NT * d.NP, mats = 2 * d.NT * d.NT + d.NP * d.NP;
-  if (!rb) return (mats + nb * S + nb) * sizeof(C);
-  return (mats + nb * (S + (size_t)ang_ss(d.NT, d.NP) + ang_us<C>(d.NT, d.NP)) + 6 * nb) *
+  if (!rb) return (mats + nb * S + (size_t)kAngMoments * nb) * sizeof(C);
+  return (mats + nb * (S + (size_t)ang_ss(d.NT, d.NP) + ang_us<C>(d.NT, d.NP)) +
+          (size_t)kAngScalars * nb) *
          sizeof(C);
 }
 template <typename C>
@@ -130,15 +131,23 @@ static int radial_W(const Dims& d, int ntiles, bool rb = false) {
 // plane pass; 17, 33, 65 radial nodes), and the run-time form (template
 // argument 0) for every other size.
 
+template <typename T, typename C, int A, int B, bool ANISO>
+static cudaError_t angular_pp_form(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
+                                   int collision, int nb, long long ntiles, cudaStream_t s) {
+  static const cudaError_t e = allow_smem(k_angular_pp<T, C, A, B, ANISO>);  // once per kernel
+  if (e != cudaSuccess) return e;
+  const size_t smem = smem_angular_pp<C>(p.d, nb);
+  const int ctas = persistent_ctas(k_angular_pp<T, C, A, B, ANISO>, smem, ntiles);
+  k_angular_pp<T, C, A, B, ANISO><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, collision, nb,
+                                                               ntiles);
+  return cudaGetLastError();
+}
 template <typename T, typename C, int A, int B>
 static cudaError_t angular_pp(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                               int collision, int nb, long long ntiles, cudaStream_t s) {
-  static const cudaError_t e = allow_smem(k_angular_pp<T, C, A, B>);  // once per kernel
-  if (e != cudaSuccess) return e;
-  const size_t smem = smem_angular_pp<C>(p.d, nb);
-  const int ctas = persistent_ctas(k_angular_pp<T, C, A, B>, smem, ntiles);
-  k_angular_pp<T, C, A, B><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, collision, nb, ntiles);
-  return cudaGetLastError();
+  if (collision && p.scb)
+    return angular_pp_form<T, C, A, B, true>(p, t, U, K, sgn, collision, nb, ntiles, s);
+  return angular_pp_form<T, C, A, B, false>(p, t, U, K, sgn, collision, nb, ntiles, s);
 }
 
 template <typename T, typename C, int N>
@@ -315,7 +324,7 @@ cudaError_t Launch<T, C>::angular_T(const Problem& p, const Tables<C>& t, const 
   const Dims& d = p.d;
   const int nb = p.tp.nbT > 0 ? p.tp.nbT : angular_nb<T, C>(d, 2);
   const size_t smem =
-      (size_t)(2 * d.NT * d.NT + d.NP * d.NP + nb * (2 * d.NT * d.NP + 1)) * sizeof(C);
+      (size_t)(2 * d.NT * d.NT + d.NP * d.NP + nb * (2 * d.NT * d.NP + kAngMoments)) * sizeof(C);
   k_angular_T<T, C><<<grid1((d.nblk + nb - 1) / nb), kThreads, smem, s>>>(
       p, t, lt, Ubar, Us, gk, ge, lam, lam_in, lam_out, Kbar_out, (C)wl, (C)wu, nb);
   return cudaGetLastError();

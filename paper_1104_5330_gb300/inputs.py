@@ -169,6 +169,31 @@ def gradient_fields(r, theta, phi, groups, seed, R1, R2, kappa_s=0.5):
     return kap, eta, np.full_like(kap, kappa_s)
 
 
+def nucleon_densities(r, theta, phi, groups, seed, R1, R2):
+    """Neutron and proton scattering amplitudes A_n, A_p, each [G][Nr][Nth][Nph]
+    (density times the per-nucleon coefficient of the neutrino-nucleon kernels),
+    scaled so that 4 pi (A_n + A_p) is of order one: A_n = (0.75 + 0.25 s)/(4 pi),
+    A_p = (0.3 + 0.2 s')/(4 pi), with s, s' seeded smooth position-only fields
+    normalised to [-1, 1] (proton fraction between about 0.06 and 0.5)."""
+    An = np.empty((groups, len(r), len(theta), len(phi)))
+    Ap = np.empty_like(An)
+    for g in range(groups):
+        s = _normalised(seeded_smooth(r, theta, phi, None, None, seed + 3000 + g, R1, R2,
+                                      with_direction=False))
+        s2 = _normalised(seeded_smooth(r, theta, phi, None, None, seed + 4000 + g, R1, R2,
+                                       with_direction=False))
+        An[g] = (0.75 + 0.25 * s) / (4 * np.pi)
+        Ap[g] = (0.3 + 0.2 * s2) / (4 * np.pi)
+    return An, Ap
+
+
+def signed_field(r, theta, phi, groups, seed, R1, R2):
+    """A seeded smooth position-only field normalised to [-1, 1] per group,
+    [G][Nr][Nth][Nph] (e.g. a scattering anisotropy covering its whole range)."""
+    return np.stack([_normalised(seeded_smooth(r, theta, phi, None, None, seed + 5000 + g, R1, R2,
+                                               with_direction=False)) for g in range(groups)])
+
+
 def inflow_from(F, NTheta):
     """Static inflow data equal to F's own values at the inflow nodes:
     r = R1 for the directions with cos Theta > 0 (the first NTheta/2 Theta

@@ -16,6 +16,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -58,6 +59,7 @@ def _load():
         "ts_destroy_grid": [P],
         "ts_grid_nodes": [P, P, P, P, P, P],
         "ts_set_coeffs": [P, P, P, P, P, P, P],
+        "ts_set_scattering_anisotropy": [P, P, P],
         "ts_apply_inflow": [P, P, P],
         "ts_step": [P, P, D, I, P],
         "ts_step_host": [P, P, D, I, P],
@@ -155,6 +157,21 @@ def ts_grid_nodes(grid, desc: GridDesc):
 def ts_set_coeffs(grid, kappa, eta, kappa_s, inflow_R1=None, inflow_R2=None, stream=None):
     _check(LIB.ts_set_coeffs(grid, _ptr(kappa), _ptr(eta), _ptr(kappa_s), _ptr(inflow_R1),
                              _ptr(inflow_R2), _stream(stream)), "ts_set_coeffs")
+
+
+def nucleon_scattering(A_n, A_p):
+    """Single kernel (kappa_s/4pi)(1 + b omega.omega') of neutrino scattering on
+    neutrons and protons, sigma = A_n (1 - omega.omega'/3) + A_p (1 - omega.omega'/10)
+    (Eqs. cross, crossnun, crossnup): kappa_s = 4 pi (A_n + A_p) and
+    b = -(A_n/3 + A_p/10)/(A_n + A_p). Host arithmetic on numpy arrays."""
+    A_n = np.asarray(A_n, dtype=np.float64)
+    A_p = np.asarray(A_p, dtype=np.float64)
+    return 4.0 * np.pi * (A_n + A_p), -(A_n / 3.0 + A_p / 10.0) / (A_n + A_p)
+
+
+def ts_set_scattering_anisotropy(grid, b, stream=None):
+    _check(LIB.ts_set_scattering_anisotropy(grid, _ptr(b), _stream(stream)),
+           "ts_set_scattering_anisotropy")
 
 
 def ts_apply_inflow(grid, F, stream=None):
@@ -319,6 +336,16 @@ class Grid:
         self._coeffs = [cv(kappa, torch.float64), cv(eta, torch.float64), cv(kappa_s, torch.float64),
                         cv(inflow_R1, self.dtype), cv(inflow_R2, self.dtype)]
         ts_set_coeffs(self.handle, *self._coeffs)
+
+    def set_scattering_anisotropy(self, b=None):
+        """b: [G][Nr][Ntheta][Nphi] anisotropy of the kernel (kappa_s/4pi)(1 + b omega.omega'),
+        a scalar (broadcast) or None (isotropic)."""
+        if b is None:
+            self._scb = None
+        else:
+            self._scb = torch.broadcast_to(torch.as_tensor(b, dtype=torch.float64, device=self.device),
+                                           self.coef_shape).contiguous()
+        ts_set_scattering_anisotropy(self.handle, self._scb)
 
     def apply_inflow(self, F):
         ts_apply_inflow(self.handle, F)
