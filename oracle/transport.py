@@ -30,7 +30,11 @@ Readings of the paper taken here (the paper is silent or garbled on these):
     dF/dt at the inflow node equals the (static, hence zero) rate of the
     inflow data. Inflow data enter by setting F = g at the inflow nodes once
     (``apply_inflow``).
-  * Time: classical RK4 (the paper's AB2 of Sect. 5.1 is replaced).
+  * Time: classical RK4 by default; the paper's second-order Adams-Bashforth
+    (Sect. 5.1) as scheme "ab2": F_{n+1} = F_n + dt (3/2 K_n - 1/2 K_{n-1}),
+    K = Tau(-L F + CT); the paper does not say how the first step is taken:
+    here K_{-1} = K_0 (one forward-Euler step), and the history restarts when
+    asked (``reset_history``).
   * Quadrature: Fejer's first rule in cos(th), cos(Th) (integral of the
     polynomial interpolant); trapezoid in ph, Ph; Clenshaw-Curtis in r.
   * Split variant: one streaming-only RK4 step, then a backward-Euler
@@ -447,6 +451,7 @@ class Problem:
             np.asarray(scatter_b, dtype=np.float64), z.shape)
         self.g_R1, self.g_R2 = g_R1, g_R2
         self.bc, self.scheme = bc, scheme
+        self._K_prev = None   # AB2 history: K of the previous step
         self.filter_on, self.filter_alpha, self.filter_order = filter_on, filter_alpha, filter_order
 
     def _c(self, a):
@@ -514,9 +519,23 @@ class Problem:
         src = sum(phi[a] * (c[..., a] * L[..., a])[..., None, None] for a in range(4))
         return (rhs_F + dt * self._c(self.kappa_s) * src) / self._c(den)
 
+    def reset_history(self):
+        """Forget the AB2 history: the next step starts with forward Euler."""
+        self._K_prev = None
+
+    def ab2_step(self, F, dt):
+        """Second-order Adams-Bashforth (Sect. 5.1): F + dt (3/2 K_n - 1/2 K_{n-1});
+        the first step after a restart is F + dt K_0."""
+        K = self.rhs(F)
+        Kp = K if self._K_prev is None else self._K_prev
+        self._K_prev = K
+        return F + dt * (1.5 * K - 0.5 * Kp)
+
     def step(self, F, dt):
         if self.scheme == "rk4":
             Fn = self.rk4_step(F, dt)
+        elif self.scheme == "ab2":
+            Fn = self.ab2_step(F, dt)
         elif self.scheme == "split":
             Fs = self.rk4_step(F, dt, streaming_only=True)
             Fn = self.implicit_collision(Fs, dt)

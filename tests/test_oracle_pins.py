@@ -201,6 +201,36 @@ def pin_anisotropic_relaxation(nsteps=20, dt=0.01, ks=0.9, b=-1.0 / 3.0):
     return np.abs(Fn - ex).max() / np.abs(ex).max()
 
 
+def ab2_linear(h, n):
+    """y_n of the AB2 recurrence y_{k+1} = y_k + h (3/2 y_k - 1/2 y_{k-1}) for
+    y' = lambda y, h = lambda dt, started with y_0 = 1, y_1 = 1 + h: written
+    through the roots of z^2 - (1 + 3h/2) z + h/2 = 0."""
+    a = 1 + 1.5 * h
+    disc = math.sqrt(a * a - 2 * h)
+    z1, z2 = (a + disc) / 2, (a - disc) / 2
+    c1 = (1 + h - z2) / (z1 - z2)
+    return c1 * z1 ** n + (1 - c1) * z2 ** n
+
+
+def pin_ab2(nsteps=20, dt=0.01, ks=0.9, b=-1.0 / 3.0, Nr=5):
+    """Sect. 5.1's AB2 on the homogeneous relaxation problem of
+    pin_anisotropic_relaxation: each degree of the direction data follows the
+    scalar AB2 recurrence with its own decay rate (0, ks (1 - b/3), ks). Without
+    Tau rows the streaming operator has large eigenvalues near the imaginary
+    axis, outside AB2's stability region; on the shell 1 <= r <= 2 at these dt
+    its rounding noise stays at the rounding level."""
+    g = Grid(1.0, 2.0, Nr, 6, 8, 6, 8)
+    ox, oy, oz = I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi)
+    F1 = 0.4 * ox - 0.7 * oy + 0.25 * oz
+    F2 = oz ** 2 - 1.0 / 3.0
+    F = np.ascontiguousarray(np.broadcast_to(1.0 + F1 + F2, g.shape))
+    pr = Problem(g, kappa_s=np.full((1, Nr, 6, 8), ks), scatter_b=b, bc="none", scheme="ab2")
+    Fn = pr.run(F, dt, nsteps)
+    ex = (1.0 + F1 * ab2_linear(-ks * (1 - b / 3) * dt, nsteps)
+          + F2 * ab2_linear(-ks * dt, nsteps))
+    return np.abs(Fn - ex).max() / np.abs(ex).max()
+
+
 # ---------------------------------------------------------------------- tests
 def test_chebyshev_transform_round_trip():
     g = Grid(0.2, 1.0, 17, 4, 4, 4, 4)
@@ -418,6 +448,51 @@ def test_anisotropic_relaxation_of_the_first_moment():
     assert pin_anisotropic_relaxation(b=-0.1, ks=2.0) < 1e-13
 
 
+def test_ab2_recurrence_closed_form():
+    assert pin_ab2() < 1e-13
+    assert pin_ab2(nsteps=30, dt=0.02, ks=1.7, b=0.5, Nr=4) < 1e-13
+    # the closed form itself against the recurrence run by hand
+    h, y = -0.3, [1.0, 0.7]
+    for _ in range(10):
+        y.append(y[-1] + h * (1.5 * y[-1] - 0.5 * y[-2]))
+    assert abs(ab2_linear(h, 11) - y[11]) < 1e-15
+
+
+def test_ab2_second_order_in_time():
+    """The error of AB2 against the exact decay exp(-ks t) shrinks by about 4
+    when dt halves (the scheme of Sect. 5.1 is second order), also with the
+    forward-Euler first step."""
+    g = Grid(0.2, 1.0, 4, 4, 6, 6, 8)
+    ox, oy, oz = I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi)
+    F = np.ascontiguousarray(np.broadcast_to(1.0 + oz, g.shape))
+    errs = []
+    for n in (20, 40, 80):
+        pr = Problem(g, kappa_s=np.full((1, 4, 4, 6), 2.0), bc="none", scheme="ab2")
+        Fn = pr.run(F, 0.4 / n, n)
+        ex = 1.0 + oz * math.exp(-2.0 * 0.4)
+        errs.append(np.abs(Fn - ex).max())
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.6 < e1 / e2 < 4.4
+
+
+def test_ab2_history_restart():
+    g = Grid(0.2, 1.0, 5, 4, 6, 6, 8)
+    kap, eta, ks = I.absorber_fields(g.r, g.theta, g.phi)
+    F0 = I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 3, 0.2, 1.0)[None]
+    gR1, gR2 = I.inflow_from(F0, g.NT)
+    pr = Problem(g, kap, eta, ks, gR1, gR2, scheme="ab2")
+    dt = I.dt_rule(0.2, 1.0, 5)
+    a = pr.run(pr.run(F0, dt, 3), dt, 2)            # history carried over
+    pr.reset_history()
+    b = pr.run(F0, dt, 5)
+    assert np.array_equal(a, b)
+    pr.reset_history()
+    c = pr.run(F0, dt, 3)
+    pr.reset_history()
+    d = pr.run(c, dt, 2)                            # restarted: differs
+    assert np.abs(d - a).max() > 1e-10
+
+
 def test_nucleon_mixture_kernel():
     """Eqs. (crossnun, crossnup): b = -1/3 on neutrons, -1/10 on protons; the
     mixture's first-moment damping kappa_s (1 - b/3) equals the optical depth
@@ -564,6 +639,16 @@ def _m10(mp):
     mp.setattr(Grid, "__init__", bad)
 
 
+@mutant("AB2 weights swapped")
+def _m14(mp):
+    def bad(self, F, dt):
+        K = self.rhs(F)
+        Kp = K if self._K_prev is None else self._K_prev
+        self._K_prev = K
+        return F + dt * (0.5 * K + 0.5 * Kp)
+    mp.setattr(Problem, "ab2_step", bad)
+
+
 @mutant("anisotropic term with the wrong sign")
 def _m11(mp):
     orig = Problem.collision
@@ -604,6 +689,7 @@ def _all_pins_pass():
         lambda: pin_conservation(Grid(0.2, 1.0, 12, 8, 8, 8, 8)) < 1e-12,
         lambda: pin_adjoint_fd(nsteps=2, scatter_b=-0.5) < 1e-6,
         lambda: pin_anisotropic(Grid(0.2, 1.0, 4, 5, 6, 6, 8)) < 1e-13,
+        lambda: pin_ab2(nsteps=6) < 1e-13,
     ]
     for c in checks:
         try:
