@@ -19,7 +19,8 @@ and the clock, with a measured DFMA-loop rate beside it), end-to-end rate
 through ts_step_host (host buffers, copies inside the timed region), the
 reduced-precision variants (FP32, FP32 + FP64 radial rows, tensor-core TF32x3
 and BF16x3) and the adjoint step on the same workload, the same grid with
-linearly anisotropic neutrino-nucleon scattering, the 64-problem batch,
+linearly anisotropic neutrino-nucleon scattering and with the paper's AB2 time
+marching, the 64-problem batch,
 the differentiation workload (33 x 16^4, 8 groups, 200 steps with sqrt(N)
 checkpoints), the CPU oracle timed on a bounded sample on this host's cores,
 and SM clocks sampled during the timed region.
@@ -429,6 +430,40 @@ def run_anisotropic(args, dims, stream):
                                     "angular_ms_per_launch": out["isotropic"][2]}}
 
 
+def run_ab2(args, dims, stream, rk4_ms_per_step):
+    """The default workload with the paper's second-order Adams-Bashforth
+    marching (one stage derivative per step) at dt = 0.2 x the smallest radial
+    spacing (its stability limit on these grids; RK4 runs at 0.4). Reports the
+    step rate and the simulated time advanced per second against RK4's."""
+    import torch
+    import paper_1104_5330_gb300.ts as ts
+    from paper_1104_5330_gb300 import inputs as I
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=ts.TS_FP64, scheme=ts.TS_AB2)
+    r, th, ph, Th, Ph = gg.nodes()
+    kap, eta, ks = I.absorber_fields(r, th, ph, groups=G)
+    F0 = np.stack([I.seeded_smooth(r, th, ph, Th, Ph, 1104 + g, R1, R2) for g in range(G)])
+    gR1, gR2 = I.inflow_from(F0, NT)
+    gg.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(R1, R2, Nr, 0.2)
+    F = torch.as_tensor(F0, dtype=torch.float64, device="cuda").contiguous()
+    gg.step(F, dt, args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 4 * args.steps
+    e0.record(stream)
+    gg.step(F, dt, n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ts.ts_sync_status(gg.handle)
+    dt_rk4 = I.dt_rule(R1, R2, Nr)
+    return {"value": gg.points * n / (ms * 1e-3), "unit": "point-updates/s",
+            "ms_per_step": ms / n, "steps": n, "dtype": "f64", "dt": dt,
+            "launches_per_step": 3,
+            "simulated_time_rate_vs_rk4": (dt / (ms / n)) / (dt_rk4 / rk4_ms_per_step)}
+
+
 def run_ours(args, dims, wname):
     import torch
     import torch.distributed as dist
@@ -617,6 +652,7 @@ def run_ours(args, dims, wname):
 
     if not args.skip_aniso:
         line["anisotropic_scattering"] = run_anisotropic(args, dims, stream)
+        line["ab2"] = run_ab2(args, dims, stream, ms / args.steps)
     if not args.skip_batch:
         line["batch"] = run_batch(args, stream)
     if not args.skip_diff and args.diff_steps > 0:

@@ -75,10 +75,18 @@ typedef enum {
 } ts_precision;
 
 typedef enum {
-  TS_RK4 = 0,                /* classical RK4 on -L F + CT */
-  TS_RK4_SPLIT_IMPLICIT = 1  /* RK4 on -L F, then backward-Euler collision step
-                                (closed form), then F = inflow data at inflow nodes
-                                (implicit first-order source step of App. B) */
+  TS_RK4 = 0,                 /* classical RK4 on -L F + CT */
+  TS_RK4_SPLIT_IMPLICIT = 1,  /* RK4 on -L F, then backward-Euler collision step
+                                 (closed form), then F = inflow data at inflow nodes
+                                 (implicit first-order source step of App. B) */
+  TS_AB2 = 2                  /* second-order Adams-Bashforth on -L F + CT (Sect. 5.1):
+                                 F + dt (3/2 K_n - 1/2 K_{n-1}), one stage derivative
+                                 per step. The grid keeps K_{n-1} between calls; the
+                                 first step after a restart is F + dt K_n. Restarts:
+                                 grid creation, ts_set_coeffs,
+                                 ts_set_scattering_anisotropy, ts_apply_inflow,
+                                 ts_reset_history, and a ts_step on a different F
+                                 pointer than the last one. Not in batches, no adjoint. */
 } ts_scheme;
 
 typedef enum {
@@ -145,6 +153,10 @@ ts_status ts_set_scattering_anisotropy(ts_grid* grid, const double* b, void* str
  * with cos Theta < 0). Call once on initial data: the Tau rows of ts_step
  * then keep those values fixed. */
 ts_status ts_apply_inflow(ts_grid* grid, void* F, void* stream);
+
+/* Forget the TS_AB2 history of the grid: its next step is a forward-Euler
+ * starting step. No effect on the other schemes. */
+ts_status ts_reset_history(ts_grid* grid);
 
 /* Advance F (in place) by `nsteps` steps of size dt with the grid's scheme,
  * boundary rows and filter. Requires ts_set_coeffs first (TS_ERR_STATE).

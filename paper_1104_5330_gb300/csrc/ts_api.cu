@@ -567,10 +567,30 @@ cudaError_t run_stage(ts_grid* g, const Tables<C>& t, const T* in, T* F, int s, 
 
 template <typename T, typename C>
 cudaError_t run_steps(ts_grid* g, const Tables<C>& t, T* F, double dt, int nsteps,
-                      cudaStream_t st, Profiler* prof = nullptr) {
+                      cudaStream_t st, Profiler* prof = nullptr, const void* key = nullptr) {
   const bool split = g->desc.scheme == TS_RK4_SPLIT_IMPLICIT;
   const ts::Problem p = make_problem(g);
   cudaError_t e = cudaSuccess;
+  if (g->desc.scheme == TS_AB2) {
+    // one stage derivative per step; the radial pass finishes K and applies the
+    // Adams-Bashforth update in place, keeping K in Acc for the next step
+    if (g->hist_F != (key ? key : F)) g->hist = false;
+    g->hist_F = key ? key : F;
+    T* K = static_cast<T*>(g->K);
+    T* Acc = static_cast<T*>(g->Acc);
+    const bool tau = g->desc.bc == TS_BC_TAU_INFLOW;
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, F, K, (C)-1, true, st)));
+      TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, F, K, (C)-1, st)));
+      TS_TIMED(prof, 2, (Launch<T, C>::radial(p, t, g->t64.Dr, F, K, (C)-1, tau,
+                                              g->hist ? ts::RAD_AB2 : ts::RAD_AB2_START, F, Acc,
+                                              nullptr, nullptr, dt, st)));
+      if (e == cudaSuccess) g->hist = true;
+      if (g->desc.filter_on) TS_TIMED(prof, 3, (Launch<T, C>::filter(p, t, F, K, st)));
+    }
+    if (e != cudaSuccess) g->hist = false;
+    return e;
+  }
   for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
     for (int s = 0; s < 4 && e == cudaSuccess; ++s)
       e = run_stage<T, C>(g, t, s == 0 ? F : static_cast<T*>(g->U), F, s, !split, dt, st, prof);
@@ -675,7 +695,7 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   if (g.precision != TS_FP64 && g.precision != TS_FP32 && g.precision != TS_FP32_R64 &&
       g.precision != TS_TF32X3 && g.precision != TS_BF16X3)
     return fail(TS_ERR_UNSUPPORTED, "unknown precision");
-  if (g.scheme != TS_RK4 && g.scheme != TS_RK4_SPLIT_IMPLICIT)
+  if (g.scheme != TS_RK4 && g.scheme != TS_RK4_SPLIT_IMPLICIT && g.scheme != TS_AB2)
     return fail(TS_ERR_UNSUPPORTED, "unknown scheme");
   if (g.bc != TS_BC_TAU_INFLOW && g.bc != TS_BC_NONE) return fail(TS_ERR_UNSUPPORTED, "unknown bc");
   const size_t es = g.precision == TS_FP64 ? 8 : 4;
@@ -773,11 +793,19 @@ ts_status ts_set_coeffs(ts_grid* g, const double* kappa, const double* eta,
     if (e != cudaSuccess) return cuda_fail(e, "ts_set_coeffs");
   }
   g->coeffs = true;
+  g->hist = false;
+  return TS_OK;
+}
+
+ts_status ts_reset_history(ts_grid* g) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  g->hist = false;
   return TS_OK;
 }
 
 ts_status ts_set_scattering_anisotropy(ts_grid* g, const double* b, void* stream) {
   if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  g->hist = false;
   if (!b) {
     g->aniso = false;
     ++g->gen;
@@ -804,6 +832,7 @@ ts_status ts_set_scattering_anisotropy(ts_grid* g, const double* b, void* stream
 ts_status ts_apply_inflow(ts_grid* g, void* F, void* stream) {
   ts_status s = check_F(g, F);
   if (s != TS_OK) return s;
+  g->hist = false;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const ts::Problem p = make_problem(g);
   cudaError_t e = g->es == 8 ? Launch<double, double>::apply_inflow(p, (double*)F, st)
@@ -811,15 +840,25 @@ ts_status ts_apply_inflow(ts_grid* g, void* F, void* stream) {
   return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_apply_inflow");
 }
 
+namespace {
+// Steps of the device field F; `key` identifies the caller's field for the
+// TS_AB2 history (the device pointer, or the host pointer of ts_step_host).
+ts_status step_device(ts_grid* g, void* F, double dt, int nsteps, cudaStream_t st,
+                      const void* key) {
+  if (!std::isfinite(dt) || nsteps < 0) return fail(TS_ERR_ARG, "need finite dt, nsteps >= 0");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
+  cudaError_t e = g->es == 8 ? run_steps<double, double>(g, g->t64, (double*)F, dt, nsteps, st,
+                                                         nullptr, key)
+                             : run_steps<float, float>(g, g->t32, (float*)F, dt, nsteps, st,
+                                                       nullptr, key);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step");
+}
+}  // namespace
+
 ts_status ts_step(ts_grid* g, void* F, double dt, int nsteps, void* stream) {
   ts_status s = check_F(g, F);
   if (s != TS_OK) return s;
-  if (!std::isfinite(dt) || nsteps < 0) return fail(TS_ERR_ARG, "need finite dt, nsteps >= 0");
-  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = g->es == 8 ? run_steps<double, double>(g, g->t64, (double*)F, dt, nsteps, st)
-                             : run_steps<float, float>(g, g->t32, (float*)F, dt, nsteps, st);
-  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step");
+  return step_device(g, F, dt, nsteps, static_cast<cudaStream_t>(stream), F);
 }
 
 ts_status ts_step_profile(ts_grid* g, void* F, double dt, int nsteps, double* pass_ms,
@@ -854,7 +893,7 @@ ts_status ts_step_host(ts_grid* g, void* F_host, double dt, int nsteps, void* st
   }
   cudaError_t e = cudaMemcpyAsync(g->io, F_host, nb, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "ts_step_host (to device)");
-  s = ts_step(g, g->io, dt, nsteps, stream);
+  s = step_device(g, g->io, dt, nsteps, st, F_host);
   if (s != TS_OK) return s;
   e = cudaMemcpyAsync(F_host, g->io, nb, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -422,6 +422,9 @@ ts_status ts_batch_create(const ts_grid_desc* descs, int n, int autotune, ts_bat
   for (int q = 1; q < n; ++q)
     if (descs[q].precision != descs[0].precision)
       return ts::fail_status(TS_ERR_UNSUPPORTED, "all problems of a batch share one precision");
+  for (int q = 0; q < n; ++q)
+    if (descs[q].scheme == TS_AB2)
+      return ts::fail_status(TS_ERR_UNSUPPORTED, "batches run the RK4 schemes (TS_AB2 is per grid)");
   ts_batch* b = new ts_batch();
   b->n = n;
   for (int q = 0; q < n; ++q) {

@@ -132,7 +132,9 @@ enum RadialMode {
   RAD_STAGE0 = 1,  // Acc = K;        U = F + dt/2 K
   RAD_STAGE1 = 2,  // Acc += 2K;      U = F + dt/2 K
   RAD_STAGE2 = 3,  // Acc += 2K;      U = F + dt K
-  RAD_STAGE3 = 4   // F = F + dt/6 (Acc + K)
+  RAD_STAGE3 = 4,  // F = F + dt/6 (Acc + K)
+  RAD_AB2 = 5,     // F = F + dt (3/2 K - 1/2 Acc);  Acc = K   (Acc: K of the previous step)
+  RAD_AB2_START = 6  // F = F + dt K;  Acc = K
 };
 
 template <typename T, typename C>
@@ -215,6 +217,8 @@ struct ts_grid {
   double* scb = nullptr; // anisotropy b of the scattering kernel (ts_set_scattering_anisotropy)
   bool aniso = false;    // scb holds values in use
   unsigned gen = 0;      // bumped when the launch parameters change (batched steps re-upload)
+  bool hist = false;     // TS_AB2: Acc holds K of the previous step of hist_F
+  const void* hist_F = nullptr;
 };
 
 namespace ts {

@@ -267,8 +267,16 @@ __device__ __forceinline__ void radial_tile(const Problem& p, const Tables<C>& t
         Acc[gi] = (T)((C)Acc[gi] + (C)2 * kv);
         Uout[gi] = (T)((C)F[gi] + dt * kv);
         break;
-      default:  // RAD_STAGE3
+      case RAD_STAGE3:
         F[gi] = (T)((C)F[gi] + dt / (C)6 * ((C)Acc[gi] + kv));
+        break;
+      case RAD_AB2:   // in place: the tile's F lines were staged before the barrier
+        F[gi] = (T)((C)F[gi] + dt * ((C)1.5 * kv - (C)0.5 * (C)Acc[gi]));
+        Acc[gi] = (T)kv;
+        break;
+      default:        // RAD_AB2_START
+        F[gi] = (T)((C)F[gi] + dt * kv);
+        Acc[gi] = (T)kv;
         break;
     }
   }

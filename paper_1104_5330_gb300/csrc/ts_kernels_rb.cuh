@@ -1094,6 +1094,19 @@ __device__ __forceinline__ void radial_store(int mode, long long gi, const C (&k
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) o[cc] = (T)((C)f[cc] + dt / (C)6 * ((C)ac[cc] + kv[cc]));
     st4<T>(F + gi, o);
+  } else if (mode >= RAD_AB2) {
+    // in place: every read of this tile's F lines happened before the tile's barrier
+    T f[4], ac[4];
+    ld4<T>(F + gi, f);
+    if (mode == RAD_AB2) ld4<T>(Acc + gi, ac);
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const C inc = mode == RAD_AB2 ? (C)1.5 * kv[cc] - (C)0.5 * (C)ac[cc] : kv[cc];
+      o[cc] = (T)((C)f[cc] + dt * inc);
+      ac[cc] = (T)kv[cc];
+    }
+    st4<T>(Acc + gi, ac);
+    st4<T>(F + gi, o);
   } else {
     T f[4], ac[4];
     ld4<T>(F + gi, f);
@@ -1195,7 +1208,7 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
         if (mode != RAD_RHS) {
           prefetch_l2(F + g1);
           prefetch_l2(F + g2);
-          if (mode != RAD_STAGE0) {
+          if (mode != RAD_STAGE0 && mode != RAD_AB2_START) {
             prefetch_l2(Acc + g1);
             prefetch_l2(Acc + g2);
           }

@@ -323,7 +323,7 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
           const long long gi = base + (long long)i * d.S_i + w;
           kv[e] = Kin[gi];
           if (mode != RAD_RHS) f[e] = F[gi];
-          if (mode != RAD_RHS && mode != RAD_STAGE0) ac[e] = Acc[gi];
+          if (mode != RAD_RHS && mode != RAD_STAGE0 && mode != RAD_AB2_START) ac[e] = Acc[gi];
         }
       }
 #pragma unroll
@@ -349,8 +349,16 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
             Acc[gi] = ac[e] + 2.f * v;
             Uout[gi] = f[e] + dt * v;
             break;
-          default:
+          case RAD_STAGE3:
             F[gi] = f[e] + dt / 6.f * (ac[e] + v);
+            break;
+          case RAD_AB2:   // in place: the A tile was staged before the MMAs
+            F[gi] = f[e] + dt * (1.5f * v - 0.5f * ac[e]);
+            Acc[gi] = v;
+            break;
+          default:        // RAD_AB2_START
+            F[gi] = f[e] + dt * v;
+            Acc[gi] = v;
             break;
         }
       }

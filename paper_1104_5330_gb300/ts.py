@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ts.h")
 
 TS_OK, TS_ERR_ARG, TS_ERR_UNSUPPORTED, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, TS_ERR_STATE = range(7)
 TS_FP64, TS_FP32, TS_FP32_R64, TS_TF32X3, TS_BF16X3 = 0, 1, 2, 3, 4
-TS_RK4, TS_RK4_SPLIT_IMPLICIT = 0, 1
+TS_RK4, TS_RK4_SPLIT_IMPLICIT, TS_AB2 = 0, 1, 2
 TS_BC_TAU_INFLOW, TS_BC_NONE = 0, 1
 
 STATUS_NAMES = ["TS_OK", "TS_ERR_ARG", "TS_ERR_UNSUPPORTED", "TS_ERR_OOM", "TS_ERR_CUDA",
@@ -60,6 +60,7 @@ def _load():
         "ts_grid_nodes": [P, P, P, P, P, P],
         "ts_set_coeffs": [P, P, P, P, P, P, P],
         "ts_set_scattering_anisotropy": [P, P, P],
+        "ts_reset_history": [P],
         "ts_apply_inflow": [P, P, P],
         "ts_step": [P, P, D, I, P],
         "ts_step_host": [P, P, D, I, P],
@@ -172,6 +173,10 @@ def nucleon_scattering(A_n, A_p):
 def ts_set_scattering_anisotropy(grid, b, stream=None):
     _check(LIB.ts_set_scattering_anisotropy(grid, _ptr(b), _stream(stream)),
            "ts_set_scattering_anisotropy")
+
+
+def ts_reset_history(grid):
+    _check(LIB.ts_reset_history(grid), "ts_reset_history")
 
 
 def ts_apply_inflow(grid, F, stream=None):
@@ -350,6 +355,10 @@ class Grid:
     def apply_inflow(self, F):
         ts_apply_inflow(self.handle, F)
         return F
+
+    def reset_history(self):
+        """TS_AB2: the next step is a forward-Euler starting step."""
+        ts_reset_history(self.handle)
 
     def step(self, F, dt, nsteps=1):
         ts_step(self.handle, F, dt, nsteps)
