@@ -312,6 +312,19 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
     const float db = b == 0 ? dv[0] : dN;
     const float kb = act ? Kin[base + (long long)b * d.S_i + w] + ck * db : 0.f;
     const float tb = t.tsign[b];
+    // every update mode as dst = f + cv (cw v + ca ac), Acc = aa ac + ab v
+    const bool rhs = mode == RAD_RHS;
+    const bool rA = mode == RAD_STAGE1 || mode == RAD_STAGE2 || mode == RAD_STAGE3 ||
+                    mode == RAD_AB2;
+    const bool wA = !rhs && mode != RAD_STAGE3;
+    float cv = dt, cw = 1.f, ca = 0.f, aa = 0.f, ab = 1.f;
+    if (mode == RAD_STAGE0 || mode == RAD_STAGE1) cv = 0.5f * dt;
+    if (mode == RAD_STAGE1 || mode == RAD_STAGE2) { aa = 1.f; ab = 2.f; }
+    if (mode == RAD_STAGE3) { cv = dt / 6.f; ca = 1.f; }
+    if (mode == RAD_AB2) { cw = 1.5f; ca = -0.5f; }
+    // RK4 stages 0-2 write the next stage input; stage 3 and AB2 update F in
+    // place (the A tile was staged before the MMAs)
+    float* dst = rhs ? out : (mode >= RAD_STAGE3 ? F : Uout);
     for (int c = 0; c < Nr; c += 16) {
       if (c > 0) tmem_ld16(lane_base + (uint32_t)c, dv);
       if (!act) continue;
@@ -319,11 +332,12 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
         const int i = c + e;
+        f[e] = ac[e] = 0.f;
         if (i < Nr) {
           const long long gi = base + (long long)i * d.S_i + w;
           kv[e] = Kin[gi];
-          if (mode != RAD_RHS) f[e] = F[gi];
-          if (mode != RAD_RHS && mode != RAD_STAGE0 && mode != RAD_AB2_START) ac[e] = Acc[gi];
+          if (!rhs) f[e] = F[gi];
+          if (rA) ac[e] = Acc[gi];
         }
       }
 #pragma unroll
@@ -333,34 +347,12 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
         const long long gi = base + (long long)i * d.S_i + w;
         float v = kv[e] + ck * dv[e];
         if (tau) v -= kb * tb * t.tsign[i];
-        switch (mode) {
-          case RAD_RHS:
-            out[gi] = v;
-            break;
-          case RAD_STAGE0:
-            Acc[gi] = v;
-            Uout[gi] = f[e] + 0.5f * dt * v;
-            break;
-          case RAD_STAGE1:
-            Acc[gi] = ac[e] + 2.f * v;
-            Uout[gi] = f[e] + 0.5f * dt * v;
-            break;
-          case RAD_STAGE2:
-            Acc[gi] = ac[e] + 2.f * v;
-            Uout[gi] = f[e] + dt * v;
-            break;
-          case RAD_STAGE3:
-            F[gi] = f[e] + dt / 6.f * (ac[e] + v);
-            break;
-          case RAD_AB2:   // in place: the A tile was staged before the MMAs
-            F[gi] = f[e] + dt * (1.5f * v - 0.5f * ac[e]);
-            Acc[gi] = v;
-            break;
-          default:        // RAD_AB2_START
-            F[gi] = f[e] + dt * v;
-            Acc[gi] = v;
-            break;
+        if (rhs) {
+          dst[gi] = v;
+          continue;
         }
+        dst[gi] = f[e] + cv * (cw * v + ca * ac[e]);
+        if (wA) Acc[gi] = aa * ac[e] + ab * v;
       }
     }
   }
