@@ -8,10 +8,12 @@ What it computes (Bonazzola, Vasset & Peres 2011):
   dF/dt = -L_sph F + CT,
   L_sph = cos(Th) d_r + (1/r)[ sin(Th)cos(Ph) d_th + sin(Th)sin(Ph)/sin(th) d_ph
                                - sin(Th) d_Th - sin(Th)sin(Ph) cot(th) d_Ph ]   (Eq. Liouvsph, Sect. 4.1)
-  CT = eta - kappa F + kappa_s (J + b omega.H - F),                         (Eq. Transp, Sect. 2.2)
-  J = (1/4pi) int F dOmega, H = (1/4pi) int omega F dOmega, from the linearly
-  anisotropic kernel A (1 + b omega.omega') with kappa_s = 4 pi A (Eqs. sigmadif,
-  sigmatot, crossnun, crossnup); b = 0 is isotropic scattering
+  CT = eta - kappa F + kappa_s (J + b omega.H + c omega.M~.omega - F),     (Eq. Transp, Sect. 2.2)
+  J = (1/4pi) int F dOmega, H = (1/4pi) int omega F dOmega, M~ = M - J I/3 with
+  M = (1/4pi) int omega omega F dOmega, from the scattering kernel
+  (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)), mu = omega.omega' (Eqs. sigmadif,
+  sigmatot; b: the neutrino-nucleon kernels, Eqs. crossnun, crossnup; c = 3/4,
+  b = 0: Thomson, Eq. sigmaTh); b = c = 0 is isotropic scattering
 on the phase-space grid (r, th, ph, Th, Ph) with energy groups as independent
 slices. Every per-axis derivative follows the paper's coefficient-space route
 (Sect. 5.1): nodal values -> spectral coefficients -> derivative in coefficient
@@ -403,6 +405,12 @@ class Grid:
         """H = (1/4pi) int F omega dOmega, Cartesian components, [3][g][r][th][ph]."""
         return np.stack([self.scattering_mean(F * o) for o in self.direction_cartesian()])
 
+    def second_moment(self, F):
+        """M = (1/4pi) int F omega omega dOmega, Cartesian, [3][3][g][r][th][ph]."""
+        o = self.direction_cartesian()
+        return np.stack([np.stack([self.scattering_mean(F * o[i] * o[j]) for j in range(3)])
+                         for i in range(3)])
+
     def moments(self, F):
         """F0 = J, F1 = (1/4pi) int F omega dOmega (Cartesian components,
         Eqs. omegax-omegaz and Fmom0), particle number N (Eq. Npho, with the
@@ -438,10 +446,12 @@ class Problem:
 
     def __init__(self, grid, kappa=None, eta=None, kappa_s=None, g_R1=None, g_R2=None,
                  bc="tau", scheme="rk4", filter_on=False, filter_alpha=36.0, filter_order=16,
-                 scatter_b=None):
-        """scatter_b: the ratio b = B/A of the linearly anisotropic scattering
-        kernel A (1 + b omega.omega') (Eqs. sigmadif, crossnun, crossnup), a
-        [g][r][th][ph] field or a scalar; None or 0 is isotropic scattering."""
+                 scatter_b=None, scatter_c=None):
+        """scatter_b, scatter_c: the coefficients of the scattering kernel
+        (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)), mu = omega.omega', each a
+        [g][r][th][ph] field or a scalar; None or 0 drops the term. b = B/A of
+        the neutrino-nucleon kernels A (1 + b mu) (Eqs. crossnun, crossnup);
+        c = 3/4 with b = 0 is the Thomson kernel (3/16pi)(1 + mu^2) (Eq. sigmaTh)."""
         self.g = grid
         z = np.zeros((grid.G, grid.Nr, grid.Nt, grid.Np))
         self.kappa = z if kappa is None else np.asarray(kappa, dtype=np.float64)
@@ -449,6 +459,8 @@ class Problem:
         self.kappa_s = z if kappa_s is None else np.asarray(kappa_s, dtype=np.float64)
         self.scatter_b = z if scatter_b is None else np.broadcast_to(
             np.asarray(scatter_b, dtype=np.float64), z.shape)
+        self.scatter_c = z if scatter_c is None else np.broadcast_to(
+            np.asarray(scatter_c, dtype=np.float64), z.shape)
         self.g_R1, self.g_R2 = g_R1, g_R2
         self.bc, self.scheme = bc, scheme
         self._K_prev = None   # AB2 history: K of the previous step
@@ -459,14 +471,21 @@ class Problem:
 
     def collision(self, F):
         """CT = eta - kappa F - sigma_t F + int sigma_d(omega.omega') F(omega') dOmega'
-        with sigma_d = A (1 + b omega.omega') and kappa_s = sigma_t = 4 pi A:
-        CT = eta - kappa F + kappa_s (J + b omega.H - F), H the first moment."""
+        with sigma_d = (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)) and kappa_s = sigma_t
+        (the mu^2 - 1/3 term integrates to zero):
+        CT = eta - kappa F + kappa_s (J + b omega.H + c omega.M~.omega - F), since
+        (1/4pi) int (omega.omega')^2 F' dOmega' = omega.M.omega and omega.I.omega = 1."""
         J = self.g.scattering_mean(F)[..., None, None]
         CT = self._c(self.eta) - self._c(self.kappa) * F + self._c(self.kappa_s) * (J - F)
+        o = self.g.direction_cartesian()
         if np.any(self.scatter_b != 0):
             H = self.g.first_moment(F)
-            wH = sum(o * h[..., None, None] for o, h in zip(self.g.direction_cartesian(), H))
+            wH = sum(oi * h[..., None, None] for oi, h in zip(o, H))
             CT = CT + self._c(self.kappa_s * self.scatter_b) * wH
+        if np.any(self.scatter_c != 0):
+            M = self.g.second_moment(F)
+            wMw = sum(o[i] * o[j] * M[i, j][..., None, None] for i in range(3) for j in range(3))
+            CT = CT + self._c(self.kappa_s * self.scatter_c) * (wMw - J / 3.0)
         return CT
 
     def rhs(self, F, streaming_only=False):
@@ -500,23 +519,28 @@ class Problem:
     def implicit_collision(self, Fs, dt):
         """Backward Euler F+ = F* + dt CT(F+), solved exactly. CT couples the
         directions only through the moments l_a(F) = (1/4pi) int phi_a F dOmega
-        of phi = (1, ox, oy, oz) with weights c = (1, b, b, b):
-          (1 + dt (kappa + kappa_s)) F+ = F* + dt eta + dt kappa_s sum_a c_a phi_a L_a,
-        L_a = l_a(F+). Applying l_b gives, per position, the 4 x 4 system
-          (1 + dt (kappa + kappa_s)) L_b - dt kappa_s sum_a c_a G_ba L_a = l_b(F* + dt eta),
+        of phi = (1, ox, oy, oz, ox^2, oy^2, oz^2, ox oy, ox oz, oy oz): its gain
+        term is kappa_s sum_a w_a phi_a l_a(F) with w = (1 - c/3, b, b, b, c, c, c,
+        2c, 2c, 2c). So
+          (1 + dt (kappa + kappa_s)) F+ = F* + dt eta + dt kappa_s sum_a w_a phi_a L_a,
+        L_a = l_a(F+). Applying l_b gives, per position, the 10 x 10 system
+          (1 + dt (kappa + kappa_s)) L_b - dt kappa_s sum_a w_a G_ba L_a = l_b(F* + dt eta),
         G_ba = l_b(phi_a) (the quadrature's own Gram matrix); then F+ from L.
-        Isotropic case (b = 0): J+ = (J* + dt eta)/(1 + dt kappa)."""
+        Isotropic case (b = c = 0): J+ = (J* + dt eta)/(1 + dt kappa)."""
         g = self.g
-        phi = (np.ones_like(g.direction_cartesian()[0]),) + g.direction_cartesian()
+        o = g.direction_cartesian()
+        phi = ((np.ones_like(o[0]),) + o + tuple(o[i] * o[i] for i in range(3))
+               + (o[0] * o[1], o[0] * o[2], o[1] * o[2]))
         Gm = np.stack([np.stack([g.scattering_mean(pb * pa) for pa in phi], -1) for pb in phi], -2)
         rhs_F = Fs + dt * self._c(self.eta)
-        rhs = np.stack([g.scattering_mean(rhs_F * pb) for pb in phi], -1)      # [g][r][th][ph][4]
+        rhs = np.stack([g.scattering_mean(rhs_F * pb) for pb in phi], -1)      # [g][r][th][ph][10]
         den = 1.0 + dt * (self.kappa + self.kappa_s)
-        c = np.stack([np.ones_like(self.scatter_b)] + [self.scatter_b] * 3, -1)  # [g][r][th][ph][4]
-        M = (den[..., None, None] * np.eye(4)
-             - dt * self.kappa_s[..., None, None] * Gm[None, None] * c[..., None, :])
+        b, c = self.scatter_b, self.scatter_c
+        w = np.stack([1.0 - c / 3.0, b, b, b, c, c, c, 2 * c, 2 * c, 2 * c], -1)
+        M = (den[..., None, None] * np.eye(len(phi))
+             - dt * self.kappa_s[..., None, None] * Gm[None, None] * w[..., None, :])
         L = np.linalg.solve(M, rhs[..., None])[..., 0]
-        src = sum(phi[a] * (c[..., a] * L[..., a])[..., None, None] for a in range(4))
+        src = sum(phi[a] * (w[..., a] * L[..., a])[..., None, None] for a in range(len(phi)))
         return (rhs_F + dt * self._c(self.kappa_s) * src) / self._c(den)
 
     def reset_history(self):
@@ -555,17 +579,27 @@ class Problem:
     # ------------------------------------------------------------- adjoint
     def _A_T(self, lam):
         """Transpose of the linear stage operator
-        U -> -L U - kappa U + kappa_s (J(U) + b omega.H(U) - U), with J(U) = sum q U
-        and H(U) = sum q omega U: the scattering part transposes to
-        q (sum kappa_s lam) + q omega . (sum kappa_s b omega lam)."""
+        U -> -L U - kappa U + kappa_s (J(U) + b omega.H(U) + c omega.M~(U).omega - U),
+        with J(U) = sum q U, H(U) = sum q omega U, M(U) = sum q omega omega U: the
+        scattering part transposes to q (sum kappa_s lam) + q omega.(sum kappa_s b
+        omega lam) + q omega.(sum kappa_s c omega omega lam).omega - q (sum kappa_s c lam)/3."""
         q = self._q
         s = np.sum(self._c(self.kappa_s) * lam, axis=(-2, -1), keepdims=True)
         out = (-self.g.liouville_T(lam) - self._c(self.kappa) * lam
                + q * s - self._c(self.kappa_s) * lam)
+        o = self.g.direction_cartesian()
         if np.any(self.scatter_b != 0):
             kb = self._c(self.kappa_s * self.scatter_b)
-            for o in self.g.direction_cartesian():
-                out = out + q * o * np.sum(kb * o * lam, axis=(-2, -1), keepdims=True)
+            for oi in o:
+                out = out + q * oi * np.sum(kb * oi * lam, axis=(-2, -1), keepdims=True)
+        if np.any(self.scatter_c != 0):
+            # U -> kappa_s c (sum_ij o_i o_j M_ij(U) - J(U)/3), M_ij(U) = sum q o_i o_j U
+            kc = self._c(self.kappa_s * self.scatter_c)
+            for i in range(3):
+                for j in range(3):
+                    out = out + q * o[i] * o[j] * np.sum(kc * o[i] * o[j] * lam, axis=(-2, -1),
+                                                         keepdims=True)
+            out = out - q * np.sum(kc * lam, axis=(-2, -1), keepdims=True) / 3.0
         return out
 
     def adjoint_step(self, F_n, lam, dt):

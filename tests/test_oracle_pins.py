@@ -116,7 +116,7 @@ def pin_conservation(grid):
     return abs(NK[0] + J2[0] - J1[0]) / (abs(J1[0]) + abs(J2[0]) + abs(NF[0]))
 
 
-def pin_adjoint_fd(nsteps=4, seed=3, scatter_b=None):
+def pin_adjoint_fd(nsteps=4, seed=3, scatter_b=None, scatter_c=None):
     g = Grid(0.2, 1.0, 9, 6, 8, 6, 8, groups=2)
     kap, eta, ks = I.gradient_fields(g.r, g.theta, g.phi, 2, 1104, 0.2, 1.0)
     F0 = np.stack([I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 1104 + k, 0.2, 1.0) for k in range(2)])
@@ -125,10 +125,10 @@ def pin_adjoint_fd(nsteps=4, seed=3, scatter_b=None):
     w = g.outgoing_flux_weights()
 
     def obj(k, e):
-        p = Problem(g, k, e, ks, gR1, gR2, scatter_b=scatter_b)
+        p = Problem(g, k, e, ks, gR1, gR2, scatter_b=scatter_b, scatter_c=scatter_c)
         return np.sum(w * p.run(F0, dt, nsteps)[:, -1])
 
-    pr = Problem(g, kap, eta, ks, gR1, gR2, scatter_b=scatter_b)
+    pr = Problem(g, kap, eta, ks, gR1, gR2, scatter_b=scatter_b, scatter_c=scatter_c)
     Fs = [F0]
     for _ in range(nsteps):
         Fs.append(pr.rk4_step(Fs[-1], dt))
@@ -155,27 +155,31 @@ def pin_adjoint_fd(nsteps=4, seed=3, scatter_b=None):
     return worst
 
 
-def pin_anisotropic(g, seed=11):
-    """The kernel (kappa_s/4pi)(1 + b omega.omega') of Eqs. (sigmadif, crossnun)
-    acts on direction functions of degree l <= 2 by fixed factors: 0 on the
-    isotropic part (number kept, App. A), -kappa_s (1 - b/3) on the first moment
-    (the damping 4 pi (a - b/3) n of Eqs. mom1, optdep) and -kappa_s on l = 2
-    (no second-moment term in the kernel). Checked on the local-frame components
-    of omega, on the Cartesian omega_z of Eq. (omegaz) and on three l = 2
-    functions, with kappa_s and b varying from point to point."""
+def pin_anisotropic(g, seed=11, quadrupole=False):
+    """The kernel (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)) of Eqs. (sigmadif,
+    crossnun, sigmaTh) acts on the direction functions of degree l by fixed
+    factors (Funk-Hecke): 0 on the isotropic part (number kept, App. A),
+    -kappa_s (1 - b/3) on the first moment (the damping 4 pi (a - b/3) n of
+    Eqs. mom1, optdep), -kappa_s (1 - 2c/15) on l = 2 and -kappa_s on l = 3.
+    Checked on the local-frame components of omega, on the Cartesian omega_z of
+    Eq. (omegaz), on three l = 2 functions and one l = 3 function, with
+    kappa_s, b (and c) varying from point to point."""
     rng = np.random.default_rng(seed)
     shp = (1, g.Nr, g.Nt, g.Np)
     ks = rng.uniform(0.5, 2.0, shp)
     b = rng.uniform(-1.0, 1.0, shp)
-    pr = Problem(g, kappa_s=ks, scatter_b=b, bc="none")
+    c = rng.uniform(-1.0, 1.5, shp) if quadrupole else np.zeros(shp)
+    pr = Problem(g, kappa_s=ks, scatter_b=b, scatter_c=c if quadrupole else None, bc="none")
     Th, Ph = g.Theta[:, None], g.Phi[None, :]
     oz = I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi)[2]
     l1 = 1.0 - b / 3.0
+    l2 = 1.0 - 2.0 * c / 15.0
     cases = [(np.ones((g.NT, g.NP)), 0.0),
              (np.cos(Th) + 0 * Ph, l1), (np.sin(Th) * np.cos(Ph), l1),
              (np.sin(Th) * np.sin(Ph), l1), (oz, l1),
-             (3 * np.cos(Th) ** 2 - 1 + 0 * Ph, 1.0), (np.sin(Th) ** 2 * np.cos(2 * Ph), 1.0),
-             (np.sin(Th) * np.cos(Th) * np.cos(Ph), 1.0)]
+             (3 * np.cos(Th) ** 2 - 1 + 0 * Ph, l2), (np.sin(Th) ** 2 * np.cos(2 * Ph), l2),
+             (np.sin(Th) * np.cos(Th) * np.cos(Ph), l2), (oz ** 2 - 1.0 / 3.0, l2),
+             (5 * np.cos(Th) ** 3 - 3 * np.cos(Th) + 0 * Ph, 1.0)]
     worst = 0.0
     for f, factor in cases:
         F = np.ascontiguousarray(np.broadcast_to(f, g.shape))
@@ -184,20 +188,22 @@ def pin_anisotropic(g, seed=11):
     return worst
 
 
-def pin_anisotropic_relaxation(nsteps=20, dt=0.01, ks=0.9, b=-1.0 / 3.0):
-    """Homogeneous medium, direction-only data F0 = 1 + c.omega + (omega_z^2 - 1/3)
-    (L F = 0 by Eq. propf): the RK4 solution is 1 + c.omega R(-ks (1 - b/3) dt)^n
-    + (omega_z^2 - 1/3) R(-ks dt)^n, R the RK4 polynomial (Eqs. mom1, optdep)."""
+def pin_anisotropic_relaxation(nsteps=20, dt=0.01, ks=0.9, b=-1.0 / 3.0, c=0.0):
+    """Homogeneous medium, direction-only data F0 = 1 + a.omega + (omega_z^2 - 1/3)
+    (L F = 0 by Eq. propf): the RK4 solution is 1 + a.omega R(-ks (1 - b/3) dt)^n
+    + (omega_z^2 - 1/3) R(-ks (1 - 2c/15) dt)^n, R the RK4 polynomial (Eqs. mom1,
+    optdep; the l = 2 factor of the kernel's mu^2 term)."""
     g = Grid(0.2, 1.0, 5, 8, 12, 8, 12)
     ox, oy, oz = I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi)
-    c = (0.4, -0.7, 0.25)
-    F1 = c[0] * ox + c[1] * oy + c[2] * oz
+    a = (0.4, -0.7, 0.25)
+    F1 = a[0] * ox + a[1] * oy + a[2] * oz
     F2 = oz ** 2 - 1.0 / 3.0
     F = np.ascontiguousarray(np.broadcast_to(1.0 + F1 + F2, g.shape))
-    pr = Problem(g, kappa_s=np.full((1, 5, 8, 12), ks), scatter_b=b, bc="none")
+    pr = Problem(g, kappa_s=np.full((1, 5, 8, 12), ks), scatter_b=b, scatter_c=c, bc="none")
     Fn = pr.run(F, dt, nsteps)
     R = lambda z: 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
-    ex = 1.0 + F1 * R(-ks * (1 - b / 3) * dt) ** nsteps + F2 * R(-ks * dt) ** nsteps
+    ex = (1.0 + F1 * R(-ks * (1 - b / 3) * dt) ** nsteps
+          + F2 * R(-ks * (1 - 2 * c / 15) * dt) ** nsteps)
     return np.abs(Fn - ex).max() / np.abs(ex).max()
 
 
@@ -229,6 +235,33 @@ def pin_ab2(nsteps=20, dt=0.01, ks=0.9, b=-1.0 / 3.0, Nr=5):
     ex = (1.0 + F1 * ab2_linear(-ks * (1 - b / 3) * dt, nsteps)
           + F2 * ab2_linear(-ks * dt, nsteps))
     return np.abs(Fn - ex).max() / np.abs(ex).max()
+
+
+def pin_kernel_brute_force(phase, b=None, c=None, seed=21):
+    """The gain term against the kernel summed pair by pair: for every position
+    and direction omega, kappa_s sum_{omega'} q' 4 pi phase(omega.omega') F(omega'),
+    q' the quadrature weights of (1/4pi) int dOmega' (the plain definition of the
+    scattering integral of Eq. Transp with the kernel sigma_d(omega.omega'))."""
+    g = Grid(0.3, 1.0, 3, 3, 4, 6, 8)
+    rng = np.random.default_rng(seed)
+    shp = (1, 3, 3, 4)
+    ks = rng.uniform(0.5, 2.0, shp)
+    F = rng.standard_normal(g.shape)
+    pr = Problem(g, kappa_s=ks, scatter_b=b, scatter_c=c, bc="none")
+    gain = pr.collision(F) + ks[..., None, None] * F
+    q = g.quadrature_weights_direction().ravel()
+    ox, oy, oz = (np.broadcast_to(o, (g.Nt, g.Np, g.NT, g.NP))
+                  for o in I.direction_cartesian(g.theta, g.phi, g.Theta, g.Phi))
+    worst = 0.0
+    for i in range(3):
+        for j in range(3):
+            for l in range(4):
+                w = np.stack([ox[j, l].ravel(), oy[j, l].ravel(), oz[j, l].ravel()], 1)   # [S][3]
+                mu = w @ w.T
+                K = 4 * np.pi * phase(mu, (0, i, j, l)) * q[None, :]
+                ref = ks[0, i, j, l] * (K @ F[0, i, j, l].ravel())
+                worst = max(worst, np.abs(gain[0, i, j, l].ravel() - ref).max() / np.abs(ref).max())
+    return worst
 
 
 # ---------------------------------------------------------------------- tests
@@ -403,16 +436,18 @@ def test_filter_single_modes():
         assert np.abs(g.filter(F) - sig(k / 8) * F).max() < 1e-14
 
 
-@pytest.mark.parametrize("aniso", [False, True])
+@pytest.mark.parametrize("aniso", [False, True, "quadrupole"])
 def test_implicit_collision_solves_backward_euler(aniso):
     """F+ - dt CT(F+) = F* (the definition of the backward-Euler step), with the
-    isotropic and the linearly anisotropic kernel (b varying in [-1, 1])."""
+    isotropic kernel, the linearly anisotropic one (b varying in [-1, 1]) and
+    the one with the mu^2 term (c varying in [-1, 1.5])."""
     g = Grid(0.2, 1.0, 7, 6, 8, 6, 8)
     kap, eta, ks = I.absorber_fields(g.r, g.theta, g.phi)
     kap = kap * 40.0
     b = np.random.default_rng(4).uniform(-1, 1, kap.shape) if aniso else None
+    c = np.random.default_rng(5).uniform(-1, 1.5, kap.shape) if aniso == "quadrupole" else None
     F = I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 3, 0.2, 1.0)[None]
-    pr = Problem(g, kap, eta, ks * 20.0, scheme="split", scatter_b=b)
+    pr = Problem(g, kap, eta, ks * 20.0, scheme="split", scatter_b=b, scatter_c=c)
     dt = 0.05
     Fp = pr.implicit_collision(F, dt)
     res = Fp - F - dt * pr.collision(Fp)
@@ -425,16 +460,37 @@ def test_implicit_collision_solves_backward_euler(aniso):
 def test_anisotropic_kernel_on_low_degree_functions():
     assert pin_anisotropic(Grid(0.2, 1.0, 5, 6, 8, 8, 8)) < 1e-13
     assert pin_anisotropic(Grid(0.3, 1.0, 4, 5, 6, 6, 10), seed=2) < 1e-13
+    assert pin_anisotropic(Grid(0.2, 1.0, 5, 6, 8, 8, 8), quadrupole=True) < 1e-13
+    assert pin_anisotropic(Grid(0.3, 1.0, 4, 5, 6, 6, 10), seed=2, quadrupole=True) < 1e-13
 
 
-def test_anisotropic_scattering_balance_and_symmetry():
+def test_kernels_against_pairwise_sums():
+    """Thomson (3/16pi)(1 + mu^2) (Eq. sigmaTh, per unit sigma_t), neutrino-neutron
+    A (1 - mu/3) and neutrino-proton A (1 - mu/10) with kappa_s = 4 pi A (Eqs.
+    crossnun, crossnup), and the general (1/4pi)(1 + b mu + c (mu^2 - 1/3)) with
+    point-dependent b, c."""
+    thomson = lambda mu, ix: 3.0 / (16 * np.pi) * (1 + mu ** 2)
+    assert pin_kernel_brute_force(thomson, c=0.75) < 1e-13
+    nun = lambda mu, ix: (1 - mu / 3.0) / (4 * np.pi)
+    assert pin_kernel_brute_force(nun, b=-1.0 / 3.0) < 1e-13
+    nup = lambda mu, ix: (1 - mu / 10.0) / (4 * np.pi)
+    assert pin_kernel_brute_force(nup, b=-0.1) < 1e-13
+    rng = np.random.default_rng(3)
+    b, c = rng.uniform(-1, 1, (1, 3, 3, 4)), rng.uniform(-1, 1, (1, 3, 3, 4))
+    gen = lambda mu, ix: (1 + b[ix] * mu + c[ix] * (mu ** 2 - 1.0 / 3.0)) / (4 * np.pi)
+    assert pin_kernel_brute_force(gen, b=b, c=c) < 1e-13
+
+
+@pytest.mark.parametrize("quadrupole", [False, True])
+def test_anisotropic_scattering_balance_and_symmetry(quadrupole):
     """App. A: the scattering integral conserves particle number, and with the
     detailed-balance symmetry of the kernel (Eq. DBC) it is self-adjoint in the
     quadrature's inner product: <G, S F>_q = <S G, F>_q for any F, G."""
     g = Grid(0.2, 1.0, 4, 5, 6, 8, 10, groups=2)
     rng = np.random.default_rng(8)
     shp = (2, g.Nr, g.Nt, g.Np)
-    pr = Problem(g, kappa_s=rng.uniform(0.5, 2, shp), scatter_b=rng.uniform(-1, 1, shp), bc="none")
+    pr = Problem(g, kappa_s=rng.uniform(0.5, 2, shp), scatter_b=rng.uniform(-1, 1, shp),
+                 scatter_c=rng.uniform(-1, 1, shp) if quadrupole else None, bc="none")
     q = g.quadrature_weights_direction()
     F, G = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
     SF, SG = pr.collision(F), pr.collision(G)
@@ -446,6 +502,8 @@ def test_anisotropic_scattering_balance_and_symmetry():
 def test_anisotropic_relaxation_of_the_first_moment():
     assert pin_anisotropic_relaxation() < 1e-13
     assert pin_anisotropic_relaxation(b=-0.1, ks=2.0) < 1e-13
+    assert pin_anisotropic_relaxation(b=0.0, c=0.75, ks=1.3) < 1e-13     # Thomson
+    assert pin_anisotropic_relaxation(b=0.4, c=-0.8) < 1e-13
 
 
 def test_ab2_recurrence_closed_form():
@@ -510,6 +568,8 @@ def test_adjoint_matches_finite_differences_anisotropic():
     g = Grid(0.2, 1.0, 9, 6, 8, 6, 8, groups=2)
     b = np.random.default_rng(9).uniform(-1, 1, (2, 9, 6, 8))
     assert pin_adjoint_fd(nsteps=3, scatter_b=b) < 1e-6
+    c = np.random.default_rng(10).uniform(-1, 1.5, (2, 9, 6, 8))
+    assert pin_adjoint_fd(nsteps=3, scatter_b=b, scatter_c=c) < 1e-6
 
 
 def test_adjoint_dot_products():
@@ -524,8 +584,9 @@ def test_adjoint_dot_products():
     kap, eta, ks = I.gradient_fields(g.r, g.theta, g.phi, 2, 5, 0.2, 1.0)
     dt = I.dt_rule(0.2, 1.0, 9)
     d = rng.standard_normal(g.shape)
-    for b in (None, rng.uniform(-1, 1, kap.shape)):
-        pr = Problem(g, kap, eta, ks * 30.0, scatter_b=b)
+    for b, c in ((None, None), (rng.uniform(-1, 1, kap.shape), None),
+                 (rng.uniform(-1, 1, kap.shape), rng.uniform(-1, 1.5, kap.shape))):
+        pr = Problem(g, kap, eta, ks * 30.0, scatter_b=b, scatter_c=c)
         lam_n, _, _ = pr.adjoint_step(F, mu, dt)
         lhs = np.sum((pr.rk4_step(F + d, dt) - pr.rk4_step(F, dt)) * mu)
         assert abs(lhs - np.sum(d * lam_n)) < 1e-11 * abs(lhs)
@@ -678,6 +739,24 @@ def _m13(mp):
     mp.setattr(Problem, "_A_T", bad)
 
 
+@mutant("quadrupole term without the trace removal")
+def _m15(mp):
+    orig = Problem.collision
+    def bad(self, F):
+        J = self.g.scattering_mean(F)[..., None, None]
+        return orig(self, F) + self._c(self.kappa_s * self.scatter_c) * J / 3.0
+    mp.setattr(Problem, "collision", bad)
+
+
+@mutant("transposed quadrupole without its trace term")
+def _m16(mp):
+    orig = Problem._A_T
+    def bad(self, lam):
+        kc = self._c(self.kappa_s * self.scatter_c)
+        return orig(self, lam) + self._q * np.sum(kc * lam, axis=(-2, -1), keepdims=True) / 3.0
+    mp.setattr(Problem, "_A_T", bad)
+
+
 def _all_pins_pass():
     small = Grid(0.2, 1.0, 9, 8, 8, 8, 8)
     checks = [
@@ -687,8 +766,9 @@ def _all_pins_pass():
         lambda: pin_tau(Grid(0.2, 1.0, 9, 4, 4, 6, 4)) < 1e-11,
         lambda: pin_free_streaming(17, 8, T=0.05) < 0.05,
         lambda: pin_conservation(Grid(0.2, 1.0, 12, 8, 8, 8, 8)) < 1e-12,
-        lambda: pin_adjoint_fd(nsteps=2, scatter_b=-0.5) < 1e-6,
-        lambda: pin_anisotropic(Grid(0.2, 1.0, 4, 5, 6, 6, 8)) < 1e-13,
+        lambda: pin_adjoint_fd(nsteps=2, scatter_b=-0.5, scatter_c=0.75) < 1e-6,
+        lambda: pin_anisotropic(Grid(0.2, 1.0, 4, 5, 6, 6, 8), quadrupole=True) < 1e-13,
+        lambda: pin_kernel_brute_force(lambda mu, ix: 3.0 / (16 * np.pi) * (1 + mu ** 2), c=0.75) < 1e-13,
         lambda: pin_ab2(nsteps=6) < 1e-13,
     ]
     for c in checks:
