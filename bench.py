@@ -391,8 +391,9 @@ def run_anisotropic(args, dims, stream):
     """The default grid with neutrino scattering on a neutron / proton mixture:
     kernel (kappa_s/4pi)(1 + b omega.omega'), kappa_s = 4 pi (A_n + A_p),
     b = -(A_n/3 + A_p/10)/(A_n + A_p) from seeded smooth amplitude fields, FP64,
-    RK4 + Tau rows. Reports the step rate and the angular pass's per-launch time
-    beside that of the isotropic form on the same grid."""
+    RK4 + Tau rows; and the same grid with Thomson scattering (3/16pi)(1 + mu^2)
+    (c = 3/4) on the mixture's kappa_s. Reports the step rates and the angular
+    pass's per-launch time beside that of the isotropic form on the same grid."""
     import torch
     import paper_1104_5330_gb300.ts as ts
     from paper_1104_5330_gb300 import inputs as I
@@ -407,8 +408,10 @@ def run_anisotropic(args, dims, stream):
     dt = I.dt_rule(R1, R2, Nr)
     F = torch.as_tensor(F0, dtype=torch.float64, device="cuda").contiguous()
     out = {}
-    for name, bb in (("isotropic", None), ("anisotropic", b)):
+    for name, bb, cc in (("isotropic", None, None), ("anisotropic", b, None),
+                         ("thomson", None, 0.75)):
         gg.set_scattering_anisotropy(bb)
+        gg.set_scattering_quadrupole(cc)
         gg.step(F, dt, args.warmup)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -427,7 +430,10 @@ def run_anisotropic(args, dims, stream):
             "kappa_s_range": [float(ks.min()), float(ks.max())],
             "angular_ms_per_launch": ang,
             "isotropic_same_grid": {"value": out["isotropic"][0],
-                                    "angular_ms_per_launch": out["isotropic"][2]}}
+                                    "angular_ms_per_launch": out["isotropic"][2]},
+            "thomson_same_grid": {"value": out["thomson"][0], "ms_per_step": out["thomson"][1],
+                                  "angular_ms_per_launch": out["thomson"][2],
+                                  "kernel": "(3/16pi)(1 + mu^2): b = 0, c = 3/4"}}
 
 
 def run_ab2(args, dims, stream, rk4_ms_per_step):

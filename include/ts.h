@@ -149,6 +149,21 @@ ts_status ts_set_coeffs(ts_grid* grid, const double* kappa, const double* eta,
  * exactly). The first call allocates one coefficient field on the device. */
 ts_status ts_set_scattering_anisotropy(ts_grid* grid, const double* b, void* stream);
 
+/* Add a mu^2 term to the scattering kernel (mu = omega.omega'): with it and
+ * ts_set_scattering_anisotropy the kernel is
+ *   (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)),
+ *   CT = eta - kappa F + kappa_s (J + b omega.H + c omega.M~.omega - F),
+ * M~ = M - J I/3 the traceless second moment, M = (1/4pi) int omega omega F dOmega.
+ * Thomson scattering (3/16pi)(1 + mu^2) per unit sigma_t (Eq. sigmaTh) is c = 3/4,
+ * b = 0. c: [G][Nr][Ntheta][Nphi] double, DEVICE, copied into the grid on
+ * `stream`; NULL removes the term (the default). The kernel is non-negative
+ * when 1 - |b| - c/3 >= 0 and 1 + 2c/3 - |b| >= 0; values are not checked.
+ * Applies like ts_set_scattering_anisotropy. TS_ERR_UNSUPPORTED for the split
+ * scheme with NTheta < 6 or NPhi < 6 (its closed form relies on the direction
+ * quadrature integrating products of four components of omega exactly). The
+ * first call allocates one coefficient field on the device. */
+ts_status ts_set_scattering_quadrupole(ts_grid* grid, const double* c, void* stream);
+
 /* Set F = inflow data at the inflow nodes (r = R1 with cos Theta > 0, r = R2
  * with cos Theta < 0). Call once on initial data: the Tau rows of ts_step
  * then keep those values fixed. */

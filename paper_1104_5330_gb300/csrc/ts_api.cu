@@ -492,6 +492,7 @@ ts::Problem make_problem(const ts_grid* g) {
   p.eta = g->eta;
   p.kaps = g->kaps;
   p.scb = g->aniso ? g->scb : nullptr;
+  p.scc = g->quad ? g->scc : nullptr;
   p.gR1 = g->gR1;
   p.gR2 = g->gR2;
   p.tc = !ts::tc_supported(g->d.Nr)             ? ts::TC_NONE
@@ -757,7 +758,7 @@ ts_status ts_destroy_grid(ts_grid* g) {
   cudaDeviceSynchronize();
   void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
                   g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err, g->tcb16,
-                  g->scb};
+                  g->scb, g->scc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : g->adj)
@@ -825,6 +826,33 @@ ts_status ts_set_scattering_anisotropy(ts_grid* g, const double* b, void* stream
                                   static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "ts_set_scattering_anisotropy");
   g->aniso = true;
+  ++g->gen;
+  return TS_OK;
+}
+
+ts_status ts_set_scattering_quadrupole(ts_grid* g, const double* c, void* stream) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  g->hist = false;
+  if (!c) {
+    g->quad = false;
+    ++g->gen;
+    return TS_OK;
+  }
+  if (g->desc.scheme == TS_RK4_SPLIT_IMPLICIT && (g->d.NT < 6 || g->d.NP < 6))
+    return fail(TS_ERR_UNSUPPORTED,
+                "the split scheme with a mu^2 term needs NTheta >= 6 and NPhi >= 6");
+  const size_t nc = (size_t)g->d.nblk * sizeof(double);
+  if (!g->scc) {
+    cudaError_t e = cudaMalloc((void**)&g->scc, nc);
+    if (e != cudaSuccess) {
+      g->scc = nullptr;
+      return cuda_fail(e, "ts_set_scattering_quadrupole");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(g->scc, c, nc, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ts_set_scattering_quadrupole");
+  g->quad = true;
   ++g->gen;
   return TS_OK;
 }

@@ -83,10 +83,16 @@ __host__ __device__ constexpr int rb_ang(int elem_bytes) { return elem_bytes == 
 __host__ __device__ constexpr int rb_rad(int elem_bytes) { return elem_bytes == 4 ? 2 : 2; }
 
 // Per-block scalars of the angular passes. Register-blocked form: J, kappa,
-// eta, kappa_s, 1/r, cot(theta), kappa_s b, H_r, H_theta, H_phi (H: the first
-// angular moment in the local frame e_r, e_theta, e_phi); run-time form: J and H.
-constexpr int kAngScalars = 10;
-constexpr int kAngMoments = 4;
+// eta, kappa_s, 1/r, cot(theta), kappa_s b, H_r, H_theta, H_phi, kappa_s c,
+// M_rr, M_thth, M_phph, M_thph, M_rth, M_rph (H, M: the first and second
+// angular moments in the local frame e_r, e_theta, e_phi); run-time form: J, H
+// and M; adjoint form: the same sums of lt plus kappa_s c sum lt.
+constexpr int kAngScalars = 17;
+constexpr int kAngMoments = 11;
+
+// Forms of the angular pass by scattering kernel: isotropic, with the mu term,
+// with the mu and mu^2 terms.
+enum KernelForm { KF_ISO = 0, KF_LINEAR = 1, KF_QUADRATIC = 2 };
 
 // Which forward passes of a grid can use the register-blocked even/odd form.
 inline int rb_mask(const Dims& d, int elem_bytes, int n64) {
@@ -107,14 +113,19 @@ struct Problem {
   const double* kap; // [G][Nr][Nt][Np]
   const double* eta;
   const double* kaps;
-  const double* scb; // anisotropy b of the scattering kernel (kappa_s/4pi)(1 + b omega.omega'),
-                     // [G][Nr][Nt][Np]; NULL: isotropic scattering
+  const double* scb; // b and c of the scattering kernel (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)),
+  const double* scc; // mu = omega.omega', [G][Nr][Nt][Np] each; NULL: that term is zero
   const void* gR1;   // inflow data, element type of the grid
   const void* gR2;
   int tc;            // TcKind: radial pass on the tensor cores (float grids)
   const void* tcb16; // BF16x3: the three bf16 terms of D_r in the MMA's B layout
   int* err;          // device flag set by a bounded wait that ran out
 };
+
+__host__ __device__ inline int kernel_form(const Problem& p, int collision) {
+  if (!collision) return KF_ISO;
+  return p.scc ? KF_QUADRATIC : p.scb ? KF_LINEAR : KF_ISO;
+}
 
 // Operand forms of the tensor-core radial pass.
 enum TcKind { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2 };
@@ -214,8 +225,10 @@ struct ts_grid {
   void* io = nullptr;
   ts::TileParams tp{};   // tile shapes (0 = built-in heuristic); set by ts_autotune
   void* tcb16 = nullptr; // TS_BF16X3: bf16 terms of D_r (tensor-core B operand)
-  double* scb = nullptr; // anisotropy b of the scattering kernel (ts_set_scattering_anisotropy)
+  double* scb = nullptr; // b of the scattering kernel (ts_set_scattering_anisotropy)
   bool aniso = false;    // scb holds values in use
+  double* scc = nullptr; // c of the scattering kernel (ts_set_scattering_quadrupole)
+  bool quad = false;     // scc holds values in use
   unsigned gen = 0;      // bumped when the launch parameters change (batched steps re-upload)
   bool hist = false;     // TS_AB2: Acc holds K of the previous step of hist_F
   const void* hist_F = nullptr;

@@ -38,10 +38,12 @@ __device__ __forceinline__ void decode_block(const Dims& d, long long blk, int& 
 // ----------------------------------------------------------------------------
 // Pass 1 (forward): angular blocks. A CTA owns `nb` consecutive blocks, which
 // are contiguous in memory (block b = elements [b*S, (b+1)*S), S = NT*NP).
-// K = sgn * (a_Th dTh U + a_Ph dPh U) + [eta - (kappa+kappa_s) U + kappa_s (J + b omega.H)]
-// a_Th = -sin(Th)/r, a_Ph = -sin(Th) sin(Ph) cot(th)/r; b: anisotropy of the
-// scattering kernel (p.scb, NULL = 0), H the first angular moment, taken in the
-// local frame: omega = cos(Th) e_r + sin(Th) cos(Ph) e_th + sin(Th) sin(Ph) e_ph.
+// K = sgn * (a_Th dTh U + a_Ph dPh U)
+//     + [eta - (kappa+kappa_s) U + kappa_s (J + b omega.H + c omega.M~.omega)]
+// a_Th = -sin(Th)/r, a_Ph = -sin(Th) sin(Ph) cot(th)/r; b, c: the kernel's mu and
+// mu^2 - 1/3 coefficients (p.scb, p.scc, NULL = 0), H and M~ = M - J I/3 the
+// first and traceless second angular moments, taken in the local frame:
+// omega = cos(Th) e_r + sin(Th) cos(Ph) e_th + sin(Th) sin(Ph) e_ph.
 template <typename T, typename C>
 __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& t,
                                              const T* __restrict__ U, T* __restrict__ K, C sgn,
@@ -53,9 +55,10 @@ __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& 
   C* sB = sA + NT * NT;                    // BThT [k'][k]
   C* sD = sB + NT * NT;                    // DPhT [m'][m]
   C* su = sD + NP * NP;                    // tile [bb][k][m]
-  C* sJ = su + nb * S;                     // [kAngMoments][nb]: J, H_r, H_th, H_ph
+  C* sJ = su + nb * S;   // [kAngMoments][nb]: J, H_r, H_th, H_ph, M_rr, M_thth, M_phph, M_thph, M_rth, M_rph
   const long long b0 = tile * nb;
-  const bool aniso = collision && p.scb != nullptr;
+  const int kf = kernel_form(p, collision);
+  const bool aniso = kf >= KF_LINEAR, quad = kf >= KF_QUADRATIC;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
     sA[x] = t.AThT[x];
@@ -68,31 +71,37 @@ __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& 
   if (collision) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
-      C acc = 0, hr = 0, ht = 0, hp = 0;
+      C mo[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // J, H (3), M (6)
       for (int x = lane; x < S; x += 32) {
         const int k = x / NP, m = x - k * NP;
         const C u = su[bb * S + x];
-        acc = fmac(t.qdir[k], u, acc);
+        mo[0] = fmac(t.qdir[k], u, mo[0]);
         if (aniso) {
-          const C qu = t.qdir[k] * u, qs = t.sinT[k] * qu;
-          hr = fmac(t.cosT[k], qu, hr);
-          ht = fmac(t.cosP[m], qs, ht);
-          hp = fmac(t.sinP[m], qs, hp);
+          const C qu = t.qdir[k] * u, qs = t.sinT[k] * qu, ct = t.cosT[k];
+          const C cp = t.cosP[m], sp = t.sinP[m];
+          mo[1] = fmac(ct, qu, mo[1]);
+          mo[2] = fmac(cp, qs, mo[2]);
+          mo[3] = fmac(sp, qs, mo[3]);
+          if (quad) {
+            const C qss = t.sinT[k] * qs;
+            mo[4] = fmac(ct * ct, qu, mo[4]);
+            mo[5] = fmac(cp * cp, qss, mo[5]);
+            mo[6] = fmac(sp * sp, qss, mo[6]);
+            mo[7] = fmac(cp * sp, qss, mo[7]);
+            mo[8] = fmac(ct * cp, qs, mo[8]);
+            mo[9] = fmac(ct * sp, qs, mo[9]);
+          }
         }
       }
-      for (int o = 16; o; o >>= 1) {
-        acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (aniso) {
-          hr += __shfl_xor_sync(0xffffffffu, hr, o);
-          ht += __shfl_xor_sync(0xffffffffu, ht, o);
-          hp += __shfl_xor_sync(0xffffffffu, hp, o);
-        }
-      }
+      const int na = quad ? 10 : aniso ? 4 : 1;   // uniform over the block
+#pragma unroll
+      for (int a = 0; a < 10; ++a)   // constant indices keep mo in registers
+        if (a < na)
+          for (int o = 16; o; o >>= 1) mo[a] += __shfl_xor_sync(0xffffffffu, mo[a], o);
       if (lane == 0) {
-        sJ[bb] = acc;
-        sJ[nb + bb] = hr;
-        sJ[2 * nb + bb] = ht;
-        sJ[3 * nb + bb] = hp;
+#pragma unroll
+        for (int a = 0; a < 10; ++a)
+          if (a < na) sJ[a * nb + bb] = mo[a];
       }
     }
     __syncthreads();
@@ -117,10 +126,18 @@ __device__ __forceinline__ void angular_tile(const Problem& p, const Tables<C>& 
       const C u = ub[r];
       const C kap = (C)p.kap[blk], eta = (C)p.eta[blk], ks = (C)p.kaps[blk];
       v += eta - (kap + ks) * u + ks * sJ[bb];
-      if (aniso) {
+      const C ct = t.cosT[k], st = t.sinT[k], cp = t.cosP[m], sp = t.sinP[m];
+      if (aniso && p.scb) {
         const C kb = (C)(p.kaps[blk] * p.scb[blk]);
-        v += kb * (t.cosT[k] * sJ[nb + bb] +
-                   t.sinT[k] * (t.cosP[m] * sJ[2 * nb + bb] + t.sinP[m] * sJ[3 * nb + bb]));
+        v += kb * (ct * sJ[nb + bb] + st * (cp * sJ[2 * nb + bb] + sp * sJ[3 * nb + bb]));
+      }
+      if (quad) {
+        const C kc = (C)(p.kaps[blk] * p.scc[blk]), j3 = sJ[bb] * ((C)1 / (C)3);
+        const C* M = sJ + 4 * nb + bb;
+        v += kc * (ct * ct * (M[0] - j3) +
+                   st * st * (cp * cp * (M[nb] - j3) + sp * sp * (M[2 * nb] - j3) +
+                              (C)2 * cp * sp * M[3 * nb]) +
+                   (C)2 * ct * st * (cp * M[4 * nb] + sp * M[5 * nb]));
       }
     }
     K[blk * S + r] = (T)v;
@@ -581,7 +598,9 @@ k_plane_T_fold(Problem p, Tables<C> t, const T* __restrict__ lt, T* __restrict__
 
 // Adjoint pass 1^T: angular blocks.
 //   Ubar_s = Ubar - D_Th^T(a_Th lt) - D_Ph^T(a_Ph lt) - (kappa+kappa_s) lt + kappa_s q_k sum lt
-//            + q_k omega . G,  G = kappa_s b sum_block omega lt  (anisotropic scattering)
+//            + q_k omega.G + q_k (omega.G2.omega - g0/3)   (anisotropic kernels)
+//   G = kappa_s b sum_block omega lt, G2 = kappa_s c sum_block omega omega lt,
+//   g0 = kappa_s c sum_block lt
 //   gk -= sum_block lt*Us,  ge += sum_block lt
 //   lam_out = lam_in + Ubar_s;   Kbar_out = wl*lam + wu*Ubar_s (if Kbar_out)
 // The transposed derivatives are folded as in the forward pass: D_Th^T on the
@@ -606,9 +625,10 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
   C* sMd = sMs + hP * hP;
   C* s1 = sMd + hP * hP;                    // a_Th lt folded: [bb][ES | OS | ED | OD][kk][p]
   C* s2 = s1 + nb * S;                      // a_Ph lt pair halves: [bb][sigma | delta][k][p]
-  C* sSum = s2 + nb * S;                    // [kAngMoments][nb] kappa_s sum lt, G_r, G_th, G_ph
+  C* sSum = s2 + nb * S;   // [kAngMoments][nb] kappa_s sum lt, G (3), G2 (6: rr thth phph thph rth rph), g0
   const long long b0 = (long long)blockIdx.x * nb;
-  const bool aniso = p.scb != nullptr;
+  const int kf = kernel_form(p, 1);
+  const bool aniso = kf >= KF_LINEAR, quad = kf >= KF_QUADRATIC;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   for (int x = threadIdx.x; x < hT * hT; x += blockDim.x) {
     sPe[x] = t.PeThA[x];
@@ -648,36 +668,50 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
   {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
-      double sl = 0, slu = 0, gr = 0, gt = 0, gp = 0;
+      double sl = 0, slu = 0, g[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // G (3), G2 (6)
       for (int x = lane; x < S; x += 32) {
         const double v = (double)lt[(b0 + bb) * S + x];
         sl += v;
         slu = fma(v, (double)Us[(b0 + bb) * S + x], slu);
         if (aniso) {
           const int k = x / NP, m = x - k * NP;
-          const double vs = (double)t.sinT[k] * v;
-          gr = fma((double)t.cosT[k], v, gr);
-          gt = fma((double)t.cosP[m], vs, gt);
-          gp = fma((double)t.sinP[m], vs, gp);
+          const double ct = (double)t.cosT[k], st = (double)t.sinT[k];
+          const double cp = (double)t.cosP[m], sp = (double)t.sinP[m], vs = st * v;
+          g[0] = fma(ct, v, g[0]);
+          g[1] = fma(cp, vs, g[1]);
+          g[2] = fma(sp, vs, g[2]);
+          if (quad) {
+            const double vss = st * vs;
+            g[3] = fma(ct * ct, v, g[3]);
+            g[4] = fma(cp * cp, vss, g[4]);
+            g[5] = fma(sp * sp, vss, g[5]);
+            g[6] = fma(cp * sp, vss, g[6]);
+            g[7] = fma(ct * cp, vs, g[7]);
+            g[8] = fma(ct * sp, vs, g[8]);
+          }
         }
       }
+      const int ng = quad ? 9 : aniso ? 3 : 0;   // uniform over the block
       for (int o = 16; o; o >>= 1) {
         sl += __shfl_xor_sync(0xffffffffu, sl, o);
         slu += __shfl_xor_sync(0xffffffffu, slu, o);
-        if (aniso) {
-          gr += __shfl_xor_sync(0xffffffffu, gr, o);
-          gt += __shfl_xor_sync(0xffffffffu, gt, o);
-          gp += __shfl_xor_sync(0xffffffffu, gp, o);
-        }
+#pragma unroll
+        for (int a = 0; a < 9; ++a)   // constant indices keep g in registers
+          if (a < ng) g[a] += __shfl_xor_sync(0xffffffffu, g[a], o);
       }
       if (lane == 0) {
         const long long blk = b0 + bb;
         sSum[bb] = (C)(p.kaps[blk] * sl);
         if (aniso) {
-          const double kb = p.kaps[blk] * p.scb[blk];
-          sSum[nb + bb] = (C)(kb * gr);
-          sSum[2 * nb + bb] = (C)(kb * gt);
-          sSum[3 * nb + bb] = (C)(kb * gp);
+          const double kb = p.scb ? p.kaps[blk] * p.scb[blk] : 0.0;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) sSum[(1 + a) * nb + bb] = (C)(kb * g[a]);
+        }
+        if (quad) {
+          const double kc = p.kaps[blk] * p.scc[blk];
+#pragma unroll
+          for (int a = 3; a < 9; ++a) sSum[(1 + a) * nb + bb] = (C)(kc * g[a]);
+          sSum[10 * nb + bb] = (C)(kc * sl);
         }
         ge[blk] += sl;
         gk[blk] -= slu;
@@ -707,8 +741,16 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
     }
     const long long blk = b0 + bb;
     const C kap = (C)p.kap[blk], ks = (C)p.kaps[blk];
-    // omega.G at (k, m) and (k, m + NP/2): cos(Th) G_r +- sin(Th) gc
-    const C gc = aniso ? t.cosP[m] * sSum[2 * nb + bb] + t.sinP[m] * sSum[3 * nb + bb] : (C)0;
+    // omega.G at (k, m) and (k, m + NP/2): cos(Th) G_r +- sin(Th) gc; omega.G2.omega:
+    // cos^2(Th) G2_rr + sin^2(Th) gq +- 2 cos(Th) sin(Th) gr2
+    const C cpm = t.cosP[m], spm = t.sinP[m];
+    const C gc = aniso ? cpm * sSum[2 * nb + bb] + spm * sSum[3 * nb + bb] : (C)0;
+    C gq = 0, gr2 = 0;
+    if (quad) {
+      gq = cpm * cpm * sSum[5 * nb + bb] + spm * spm * sSum[6 * nb + bb] +
+           (C)2 * cpm * spm * sSum[7 * nb + bb];
+      gr2 = (C)2 * (cpm * sSum[8 * nb + bb] + spm * sSum[9 * nb + bb]);
+    }
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       const int kr = side ? km : k;
@@ -718,8 +760,14 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
       const long long gi = blk * S + kr * NP + m;
       C qs = t.qdir[kr] * sSum[bb], qa = 0;
       if (aniso) {
-        qs += t.qdir[kr] * t.cosT[kr] * sSum[nb + bb];
-        qa = t.qdir[kr] * t.sinT[kr] * gc;
+        const C ct = t.cosT[kr], st = t.sinT[kr];
+        qs += t.qdir[kr] * ct * sSum[nb + bb];
+        qa = t.qdir[kr] * st * gc;
+        if (quad) {
+          qs += t.qdir[kr] * (ct * ct * sSum[4 * nb + bb] + st * st * gq -
+                              sSum[10 * nb + bb] * ((C)1 / (C)3));
+          qa += t.qdir[kr] * ct * st * gr2;
+        }
       }
       const C ub1 = (C)Ubar[gi] - (ps + qd) - f1 - (kap + ks) * (C)lt[gi] + qs + qa;
       const C ub2 = (C)Ubar[gi + hP] - (ps - qd) - f2 - (kap + ks) * (C)lt[gi + hP] + qs - qa;
@@ -736,11 +784,14 @@ k_angular_T(Problem p, Tables<C> t, const T* __restrict__ lt, const T* __restric
 // ----------------------------------------------------------------------------
 // Split scheme: backward-Euler collision step in closed form per angular block,
 //   J+ = (J* + dt eta)/(1 + dt kappa),  F+ = (F* + dt (eta + kappa_s J+))/(1 + dt (kappa+kappa_s)),
-// with anisotropic scattering also H+ = H*/(1 + dt (kappa + kappa_s) - dt kappa_s b/3) and
-// F+ += dt kappa_s b omega.H+ / (1 + dt (kappa+kappa_s)): the quadrature integrates
-// omega_i omega_j exactly (NTheta, NPhi >= 3), (1/4pi) sum q omega_i omega_j = delta_ij/3,
-// and the first moments of 1 vanish by symmetry. Then F = inflow data at the
-// inflow nodes (if the grid has Tau rows).
+// with an anisotropic kernel also H+ = H*/(1 + dt (kappa + kappa_s) - dt kappa_s b/3),
+// M~+ = M~*/(1 + dt (kappa + kappa_s) - dt kappa_s 2c/15) and
+// F+ += dt kappa_s (b omega.H+ + c omega.M~+.omega) / (1 + dt (kappa+kappa_s)): the
+// quadrature integrates the products of up to four components of omega exactly
+// (NTheta, NPhi >= 3 for b, >= 6 for c), so (1/4pi) sum q omega_i omega_j = delta_ij/3
+// and M~ of omega.A.omega is 2A/15 for traceless A, and the odd moments of even
+// functions vanish by symmetry. Then F = inflow data at the inflow nodes (if the
+// grid has Tau rows).
 template <typename T, typename C>
 __device__ __forceinline__ void implicit_collision_tile(const Problem& p, const Tables<C>& t,
                                                         T* F, double dt, int nb,
@@ -752,38 +803,59 @@ __device__ __forceinline__ void implicit_collision_tile(const Problem& p, const 
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const bool aniso = p.scb != nullptr;
+  const int kf = kernel_form(p, 1);
+  const bool aniso = kf >= KF_LINEAR, quad = kf >= KF_QUADRATIC;
   for (int bb = warp; bb < nbb; bb += nw) {
     const long long blk = b0 + bb;
-    double acc = 0, hr = 0, ht = 0, hp = 0;
+    double acc = 0, mo[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};   // H (3), M (6: rr thth phph thph rth rph)
     for (int x = lane; x < S; x += 32) {
       const int k = x / NP, m = x - k * NP;
       const double u = (double)F[blk * S + x];
       acc = fma((double)t.qdir[k], u, acc);
       if (aniso) {
+        const double ct = (double)t.cosT[k], cp = (double)t.cosP[m], sp = (double)t.sinP[m];
         const double qu = (double)t.qdir[k] * u, qs = (double)t.sinT[k] * qu;
-        hr = fma((double)t.cosT[k], qu, hr);
-        ht = fma((double)t.cosP[m], qs, ht);
-        hp = fma((double)t.sinP[m], qs, hp);
+        mo[0] = fma(ct, qu, mo[0]);
+        mo[1] = fma(cp, qs, mo[1]);
+        mo[2] = fma(sp, qs, mo[2]);
+        if (quad) {
+          const double qss = (double)t.sinT[k] * qs;
+          mo[3] = fma(ct * ct, qu, mo[3]);
+          mo[4] = fma(cp * cp, qss, mo[4]);
+          mo[5] = fma(sp * sp, qss, mo[5]);
+          mo[6] = fma(cp * sp, qss, mo[6]);
+          mo[7] = fma(ct * cp, qs, mo[7]);
+          mo[8] = fma(ct * sp, qs, mo[8]);
+        }
       }
     }
+    const int nm = quad ? 9 : aniso ? 3 : 0;   // uniform over the block
     for (int o = 16; o; o >>= 1) {
       acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (aniso) {
-        hr += __shfl_xor_sync(0xffffffffu, hr, o);
-        ht += __shfl_xor_sync(0xffffffffu, ht, o);
-        hp += __shfl_xor_sync(0xffffffffu, hp, o);
-      }
+#pragma unroll
+      for (int a = 0; a < 9; ++a)   // constant indices keep mo in registers
+        if (a < nm) mo[a] += __shfl_xor_sync(0xffffffffu, mo[a], o);
     }
     const double kap = p.kap[blk], eta = p.eta[blk], ks = p.kaps[blk];
     const double Jp = (acc + dt * eta) / (1.0 + dt * kap);
     const double num = dt * (eta + ks * Jp), den = 1.0 + dt * (kap + ks);
     double kbr = 0, kbt = 0, kbp = 0;   // dt kappa_s b H+
-    if (aniso) {
+    double q6[6] = {0, 0, 0, 0, 0, 0};  // dt kappa_s c M~+ (rr thth phph, 2 thph, 2 rth, 2 rph)
+    if (aniso && p.scb) {
       const double kb = ks * p.scb[blk], f = dt * kb / (den - dt * kb / 3.0);
-      kbr = f * hr;
-      kbt = f * ht;
-      kbp = f * hp;
+      kbr = f * mo[0];
+      kbt = f * mo[1];
+      kbp = f * mo[2];
+    }
+    if (quad) {
+      const double kc = ks * p.scc[blk], f = dt * kc / (den - dt * kc * (2.0 / 15.0));
+      const double j3 = acc / 3.0;
+      q6[0] = f * (mo[3] - j3);
+      q6[1] = f * (mo[4] - j3);
+      q6[2] = f * (mo[5] - j3);
+      q6[3] = 2.0 * f * mo[6];
+      q6[4] = 2.0 * f * mo[7];
+      q6[5] = 2.0 * f * mo[8];
     }
     int g, i, j, l;
     decode_block(d, blk, g, i, j, l);
@@ -792,9 +864,14 @@ __device__ __forceinline__ void implicit_collision_tile(const Problem& p, const 
     for (int x = lane; x < S; x += 32) {
       const int k = x / NP, m = x - k * NP;
       double v = (double)F[blk * S + x] + num;
-      if (aniso)
-        v += (double)t.cosT[k] * kbr +
-             (double)t.sinT[k] * ((double)t.cosP[m] * kbt + (double)t.sinP[m] * kbp);
+      if (aniso) {
+        const double ct = (double)t.cosT[k], st = (double)t.sinT[k];
+        const double cp = (double)t.cosP[m], sp = (double)t.sinP[m];
+        v += ct * kbr + st * (cp * kbt + sp * kbp);
+        if (quad)
+          v += ct * ct * q6[0] + st * st * (cp * cp * q6[1] + sp * sp * q6[2] + cp * sp * q6[3]) +
+               ct * st * (cp * q6[4] + sp * q6[5]);
+      }
       v /= den;
       if (p.bc == TS_BC_TAU_INFLOW) {
         const long long pos = (((long long)g * d.Nt + j) * d.Np + l) * hT;

@@ -181,13 +181,14 @@ __device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int n
   for (int x = 4 * threadIdx.x; x < nbb * S; x += 4 * blockDim.x) copy4<ASYNC, T, C>(su + x, src + x);
 }
 
-// Preparation of a staged tile: coefficients, J (and, with anisotropic
-// scattering, kappa_s b and the first moment H), the folded halves
+// Preparation of a staged tile: coefficients, J (and, with an anisotropic
+// kernel, kappa_s b, kappa_s c and the first and second moments H, M), the
+// folded halves
 // [se | so | de | do] ([k' < NT/2][p < NP/2] each) for the Theta contraction and
 // the pointwise terms, and the transposed halves uT[p][k] = s, uT[NP/2 + p][k] =
 // d for the Phi contraction. Entry: su complete and visible. Exit (after the
 // caller's barrier): su is no longer read.
-template <int NT_, int NP_, bool ANISO, typename T, typename C>
+template <int NT_, int NP_, int KF, typename T, typename C>
 __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C>& t,
                                                 const C* su, C* sSD, C* uT, C* sc, int collision,
                                                 int nb, long long tile) {
@@ -197,12 +198,14 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
   const int Q4 = hT * hP;   // one folded half
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
-  const bool aniso = ANISO && collision;
+  const bool aniso = KF >= KF_LINEAR && collision;
+  const bool quad = KF >= KF_QUADRATIC && collision;
   for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // once per block
     sc[nb + x] = (C)p.kap[b0 + x];
     sc[2 * nb + x] = (C)p.eta[b0 + x];
     sc[3 * nb + x] = (C)p.kaps[b0 + x];
-    if (aniso) sc[6 * nb + x] = (C)(p.kaps[b0 + x] * p.scb[b0 + x]);
+    if (aniso) sc[6 * nb + x] = p.scb ? (C)(p.kaps[b0 + x] * p.scb[b0 + x]) : (C)0;
+    if (quad) sc[10 * nb + x] = (C)(p.kaps[b0 + x] * p.scc[b0 + x]);
     int g, i, j, l;
     decode_block(d, b0 + x, g, i, j, l);
     sc[4 * nb + x] = t.inv_r[i];
@@ -291,12 +294,48 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
           sc[9 * nb + bb] = hp;
         }
       }
+      if (quad) {
+        // second moment: cos^2(Th), sin^2(Th) are even under k -> NT-1-k and
+        // cos(Th) sin(Th) odd; cos^2(Ph), sin^2(Ph), cos(Ph) sin(Ph) are even under
+        // m -> m + NP/2 and cos(Ph), sin(Ph) odd. So M_rr, M_thth, M_phph, M_thph
+        // take the Theta-even part of the sums, M_rth, M_rph the Theta-odd part of
+        // the differences.
+        C m6[6] = {0, 0, 0, 0, 0, 0};
+        if (act) {
+          C se = 0, sc2 = 0, ss2 = 0, scs = 0, tc = 0, tsn = 0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const C cp = t.cosP[p4 + c], sp = t.sinP[p4 + c];
+            se += e1[c];
+            sc2 = fmac(cp * cp, e1[c], sc2);
+            ss2 = fmac(sp * sp, e1[c], ss2);
+            scs = fmac(cp * sp, e1[c], scs);
+            tc = fmac(cp, o2[c], tc);
+            tsn = fmac(sp, o2[c], tsn);
+          }
+          const C q = t.qdir[kk], ct = t.cosT[kk], st = t.sinT[kk];
+          const C qss = q * st * st, qcs = q * ct * st;
+          m6[0] = q * ct * ct * se;
+          m6[1] = qss * sc2;
+          m6[2] = qss * ss2;
+          m6[3] = qss * scs;
+          m6[4] = qcs * tc;
+          m6[5] = qcs * tsn;
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+          for (int o = tpb >> 1; o; o >>= 1) m6[a] += __shfl_xor_sync(0xffffffffu, m6[a], o);
+        if (act && (x % tpb) == 0) {
+#pragma unroll
+          for (int a = 0; a < 6; ++a) sc[(11 + a) * nb + bb] = m6[a];
+        }
+      }
     }
   }
   if (collision && !warp_J) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
-      C acc = 0, hr = 0, ht = 0, hp = 0;
+      C acc = 0, hr = 0, ht = 0, hp = 0, m6[6] = {0, 0, 0, 0, 0, 0};
       for (int x = lane; x < S; x += 32) {
         const int k = x / NP, m = x - k * NP;
         const C u = su[bb * S + x];
@@ -306,6 +345,15 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
           hr = fmac(t.cosT[k], qu, hr);
           ht = fmac(t.cosP[m], qs, ht);
           hp = fmac(t.sinP[m], qs, hp);
+          if (quad) {
+            const C ct = t.cosT[k], cp = t.cosP[m], sp = t.sinP[m], qss = t.sinT[k] * qs;
+            m6[0] = fmac(ct * ct, qu, m6[0]);
+            m6[1] = fmac(cp * cp, qss, m6[1]);
+            m6[2] = fmac(sp * sp, qss, m6[2]);
+            m6[3] = fmac(cp * sp, qss, m6[3]);
+            m6[4] = fmac(ct * cp, qs, m6[4]);
+            m6[5] = fmac(ct * sp, qs, m6[5]);
+          }
         }
       }
       for (int o = 16; o; o >>= 1) {
@@ -315,6 +363,10 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
           ht += __shfl_xor_sync(0xffffffffu, ht, o);
           hp += __shfl_xor_sync(0xffffffffu, hp, o);
         }
+        if (quad) {
+#pragma unroll
+          for (int a = 0; a < 6; ++a) m6[a] += __shfl_xor_sync(0xffffffffu, m6[a], o);
+        }
       }
       if (lane == 0) {
         sc[bb] = acc;
@@ -323,15 +375,19 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
           sc[8 * nb + bb] = ht;
           sc[9 * nb + bb] = hp;
         }
+        if (quad) {
+#pragma unroll
+          for (int a = 0; a < 6; ++a) sc[(11 + a) * nb + bb] = m6[a];
+        }
       }
     }
   }
 }
 
 // Compute a prepared tile and write K. Reads sSD, uT, sc and the matrices.
-// ANISO: add the anisotropic scattering term (a separate instantiation keeps
-// the register allocation of the isotropic form unchanged).
-template <int NT_, int NP_, bool ANISO, typename T, typename C>
+// KF: add the kernel's mu (and mu^2) terms (separate instantiations keep the
+// register allocation of the isotropic form unchanged).
+template <int NT_, int NP_, int KF, typename T, typename C>
 __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Tables<C>& t,
                                                    const C* sSD, const C* uT, const C* sc,
                                                    const C* sP, const C* sQ, const C* sD,
@@ -345,7 +401,8 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
   const long long b0 = tile * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int KR = hT / RB, PC = hP / CB;
-  constexpr bool aniso = ANISO;
+  constexpr bool aniso = KF >= KF_LINEAR;
+  constexpr bool quad = KF >= KF_QUADRATIC;
   // unit = (pc, 4 blocks, kr, block group): a 16-byte load phase spans 4 blocks
   const int units = ((nbb + 3) / 4) * 4 * KR * PC;
   const C* sPe = sP;
@@ -427,6 +484,25 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
 #pragma unroll
       for (int c = 0; c < CB; ++c) hc[c] = t.cosP[p0 + c] * ht + t.sinP[p0 + c] * hp;
     }
+    // mu^2 term kappa_s c omega.M~.omega, M~ = M - J I/3: at (k, m)
+    // cos^2(Th) mrr + sin^2(Th) qmc + cos(Th) sin(Th) rmc, at m + NP/2 the last term
+    // changes sign; qmc, rmc per column
+    C mrr = 0, qmc[CB], rmc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) qmc[c] = rmc[c] = 0;
+    if (quad) {
+      const C kc = sc[10 * nb + bb], j3 = J * ((C)1 / (C)3);
+      mrr = kc * (sc[11 * nb + bb] - j3);
+      const C mtt = kc * (sc[12 * nb + bb] - j3), mpp = kc * (sc[13 * nb + bb] - j3);
+      const C mtp = (C)2 * kc * sc[14 * nb + bb];
+      const C mrt = (C)2 * kc * sc[15 * nb + bb], mrp = (C)2 * kc * sc[16 * nb + bb];
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const C cp = t.cosP[p0 + c], sp = t.sinP[p0 + c];
+        qmc[c] = cp * cp * mtt + sp * sp * mpp + cp * sp * mtp;
+        rmc[c] = cp * mrt + sp * mrp;
+      }
+    }
     C s1[CB], s2[CB];   // a_Phi / a_Theta at m and m + NP/2, with the 1/2 of the halves
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
@@ -476,9 +552,14 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
             v2 += src - kq * (sv[c] - dv[c]);
           }
           if (aniso) {
-            const C ar = t.cosT[k] * hr, at = t.sinT[k] * hc[c];
-            v1 += ar + at;
-            v2 += ar - at;
+            const C ct = t.cosT[k], st = t.sinT[k];
+            C ev = ct * hr, od = st * hc[c];
+            if (quad) {
+              ev += ct * ct * mrr + st * st * qmc[c];
+              od += ct * st * rmc[c];
+            }
+            v1 += ev + od;
+            v2 += ev - od;
           }
           o1v[c] = (T)v1;
           o2v[c] = (T)v2;
@@ -491,7 +572,7 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
   }
 }
 
-template <int NT_, int NP_, bool ANISO, typename T, typename C>
+template <int NT_, int NP_, int KF, typename T, typename C>
 __device__ __forceinline__ void angular_tile_rb_form(const Problem& p, const Tables<C>& t,
                                                      const T* __restrict__ U, T* __restrict__ K,
                                                      C sgn, int collision, int nb, long long tile) {
@@ -508,28 +589,34 @@ __device__ __forceinline__ void angular_tile_rb_form(const Problem& p, const Tab
   angular_rb_mats<C>(t, d, sP, sQ, sD);
   angular_rb_load<false, T, C>(d, U, nb, tile, su);
   __syncthreads();
-  angular_rb_prep<NT_, NP_, ANISO, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+  angular_rb_prep<NT_, NP_, KF, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
   __syncthreads();
-  angular_rb_compute<NT_, NP_, ANISO, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb,
-                                            tile);
+  angular_rb_compute<NT_, NP_, KF, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb,
+                                         tile);
 }
 
 template <int NT_, int NP_, typename T, typename C>
 __device__ __forceinline__ void angular_tile_rb(const Problem& p, const Tables<C>& t,
                                                 const T* __restrict__ U, T* __restrict__ K,
                                                 C sgn, int collision, int nb, long long tile) {
-  if (collision && p.scb)
-    angular_tile_rb_form<NT_, NP_, true, T, C>(p, t, U, K, sgn, collision, nb, tile);
-  else
-    angular_tile_rb_form<NT_, NP_, false, T, C>(p, t, U, K, sgn, collision, nb, tile);
+  switch (kernel_form(p, collision)) {
+    case KF_QUADRATIC:
+      angular_tile_rb_form<NT_, NP_, KF_QUADRATIC, T, C>(p, t, U, K, sgn, collision, nb, tile);
+      break;
+    case KF_LINEAR:
+      angular_tile_rb_form<NT_, NP_, KF_LINEAR, T, C>(p, t, U, K, sgn, collision, nb, tile);
+      break;
+    default:
+      angular_tile_rb_form<NT_, NP_, KF_ISO, T, C>(p, t, U, K, sgn, collision, nb, tile);
+  }
 }
 
 // Persistent: the next tile is copied into the staging buffer as soon as the
 // current one has been prepared, and lands while the current one is computed.
-// ANISO: the form with anisotropic scattering (launched when the grid has it
-// and the pass includes the collision term); a separate kernel, so that the
-// isotropic form keeps its own register allocation.
-template <typename T, typename C, int NT_, int NP_, bool ANISO>
+// KF: the kernel form (launched by the grid's scattering kernel when the pass
+// includes the collision term); separate kernels, so that the isotropic form
+// keeps its own register allocation.
+template <typename T, typename C, int NT_, int NP_, int KF>
 __global__ void __launch_bounds__(kThreads, 2)
 k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K, C sgn,
              int collision, int nb, long long ntiles) {
@@ -550,13 +637,13 @@ k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K,
   for (; tile < ntiles; tile += gridDim.x) {
     cp_async_wait0();
     __syncthreads();   // this tile staged; the previous tile's compute is done
-    angular_rb_prep<NT_, NP_, ANISO, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+    angular_rb_prep<NT_, NP_, KF, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
     __syncthreads();   // staging buffer free
     const long long next = tile + gridDim.x;
     if (next < ntiles) angular_rb_load<true, T, C>(d, U, nb, next, su);
     cp_async_commit();
-    angular_rb_compute<NT_, NP_, ANISO, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision,
-                                              nb, tile);
+    angular_rb_compute<NT_, NP_, KF, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision,
+                                           nb, tile);
   }
   cp_async_wait0();
 }

@@ -131,23 +131,29 @@ static int radial_W(const Dims& d, int ntiles, bool rb = false) {
 // plane pass; 17, 33, 65 radial nodes), and the run-time form (template
 // argument 0) for every other size.
 
-template <typename T, typename C, int A, int B, bool ANISO>
+template <typename T, typename C, int A, int B, int KF>
 static cudaError_t angular_pp_form(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                                    int collision, int nb, long long ntiles, cudaStream_t s) {
-  static const cudaError_t e = allow_smem(k_angular_pp<T, C, A, B, ANISO>);  // once per kernel
+  static const cudaError_t e = allow_smem(k_angular_pp<T, C, A, B, KF>);  // once per kernel
   if (e != cudaSuccess) return e;
   const size_t smem = smem_angular_pp<C>(p.d, nb);
-  const int ctas = persistent_ctas(k_angular_pp<T, C, A, B, ANISO>, smem, ntiles);
-  k_angular_pp<T, C, A, B, ANISO><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, collision, nb,
-                                                               ntiles);
+  const int ctas = persistent_ctas(k_angular_pp<T, C, A, B, KF>, smem, ntiles);
+  k_angular_pp<T, C, A, B, KF><<<ctas, kThreads, smem, s>>>(p, t, U, K, sgn, collision, nb,
+                                                            ntiles);
   return cudaGetLastError();
 }
+// The kernel with the mu^2 term runs in the run-time-size form only.
 template <typename T, typename C, int A, int B>
 static cudaError_t angular_pp(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                               int collision, int nb, long long ntiles, cudaStream_t s) {
-  if (collision && p.scb)
-    return angular_pp_form<T, C, A, B, true>(p, t, U, K, sgn, collision, nb, ntiles, s);
-  return angular_pp_form<T, C, A, B, false>(p, t, U, K, sgn, collision, nb, ntiles, s);
+  switch (kernel_form(p, collision)) {
+    case KF_QUADRATIC:
+      return angular_pp_form<T, C, 0, 0, KF_QUADRATIC>(p, t, U, K, sgn, collision, nb, ntiles, s);
+    case KF_LINEAR:
+      return angular_pp_form<T, C, A, B, KF_LINEAR>(p, t, U, K, sgn, collision, nb, ntiles, s);
+    default:
+      return angular_pp_form<T, C, A, B, KF_ISO>(p, t, U, K, sgn, collision, nb, ntiles, s);
+  }
 }
 
 template <typename T, typename C, int N>

@@ -60,6 +60,7 @@ def _load():
         "ts_grid_nodes": [P, P, P, P, P, P],
         "ts_set_coeffs": [P, P, P, P, P, P, P],
         "ts_set_scattering_anisotropy": [P, P, P],
+        "ts_set_scattering_quadrupole": [P, P, P],
         "ts_reset_history": [P],
         "ts_apply_inflow": [P, P, P],
         "ts_step": [P, P, D, I, P],
@@ -173,6 +174,11 @@ def nucleon_scattering(A_n, A_p):
 def ts_set_scattering_anisotropy(grid, b, stream=None):
     _check(LIB.ts_set_scattering_anisotropy(grid, _ptr(b), _stream(stream)),
            "ts_set_scattering_anisotropy")
+
+
+def ts_set_scattering_quadrupole(grid, c, stream=None):
+    _check(LIB.ts_set_scattering_quadrupole(grid, _ptr(c), _stream(stream)),
+           "ts_set_scattering_quadrupole")
 
 
 def ts_reset_history(grid):
@@ -351,6 +357,17 @@ class Grid:
             self._scb = torch.broadcast_to(torch.as_tensor(b, dtype=torch.float64, device=self.device),
                                            self.coef_shape).contiguous()
         ts_set_scattering_anisotropy(self.handle, self._scb)
+
+    def set_scattering_quadrupole(self, c=None):
+        """c: [G][Nr][Ntheta][Nphi] coefficient of mu^2 - 1/3 in the kernel
+        (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)), a scalar (broadcast) or None
+        (no such term); Thomson scattering is c = 3/4 with b = 0."""
+        if c is None:
+            self._scc = None
+        else:
+            self._scc = torch.broadcast_to(torch.as_tensor(c, dtype=torch.float64, device=self.device),
+                                           self.coef_shape).contiguous()
+        ts_set_scattering_quadrupole(self.handle, self._scc)
 
     def apply_inflow(self, F):
         ts_apply_inflow(self.handle, F)
