@@ -473,36 +473,6 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
     const C ir = sc[4 * nb + bb], ct = sc[5 * nb + bb];
     const C J = sc[bb], kap = sc[nb + bb], eta = sc[2 * nb + bb], ks = sc[3 * nb + bb];
     const C src = eta + ks * J, kks = kap + ks;
-    // anisotropic scattering kappa_s b omega.H = cos(Th) hr + sin(Th) hc at m and
-    // cos(Th) hr - sin(Th) hc at m + NP/2
-    C hr = 0, hc[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) hc[c] = 0;
-    if (aniso) {
-      const C kb = sc[6 * nb + bb], ht = kb * sc[8 * nb + bb], hp = kb * sc[9 * nb + bb];
-      hr = kb * sc[7 * nb + bb];
-#pragma unroll
-      for (int c = 0; c < CB; ++c) hc[c] = t.cosP[p0 + c] * ht + t.sinP[p0 + c] * hp;
-    }
-    // mu^2 term kappa_s c omega.M~.omega, M~ = M - J I/3: at (k, m)
-    // cos^2(Th) mrr + sin^2(Th) qmc + cos(Th) sin(Th) rmc, at m + NP/2 the last term
-    // changes sign; qmc, rmc per column
-    C mrr = 0, qmc[CB], rmc[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) qmc[c] = rmc[c] = 0;
-    if (quad) {
-      const C kc = sc[10 * nb + bb], j3 = J * ((C)1 / (C)3);
-      mrr = kc * (sc[11 * nb + bb] - j3);
-      const C mtt = kc * (sc[12 * nb + bb] - j3), mpp = kc * (sc[13 * nb + bb] - j3);
-      const C mtp = (C)2 * kc * sc[14 * nb + bb];
-      const C mrt = (C)2 * kc * sc[15 * nb + bb], mrp = (C)2 * kc * sc[16 * nb + bb];
-#pragma unroll
-      for (int c = 0; c < CB; ++c) {
-        const C cp = t.cosP[p0 + c], sp = t.sinP[p0 + c];
-        qmc[c] = cp * cp * mtt + sp * sp * mpp + cp * sp * mtp;
-        rmc[c] = cp * mrt + sp * mrp;
-      }
-    }
     C s1[CB], s2[CB];   // a_Phi / a_Theta at m and m + NP/2, with the 1/2 of the halves
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
@@ -551,22 +521,66 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
             v1 += src - kq * (sv[c] + dv[c]);
             v2 += src - kq * (sv[c] - dv[c]);
           }
-          if (aniso) {
-            const C ct = t.cosT[k], st = t.sinT[k];
-            C ev = ct * hr, od = st * hc[c];
-            if (quad) {
-              ev += ct * ct * mrr + st * st * qmc[c];
-              od += ct * st * rmc[c];
-            }
-            v1 += ev + od;
-            v2 += ev - od;
-          }
           o1v[c] = (T)v1;
           o2v[c] = (T)v2;
         }
         T* out = K + blk * S + k * NP + p0;
         st4<T>(out, o1v);
         st4<T>(out + hP, o2v);
+      }
+    }
+    if (aniso) {
+      // The kernel's mu (and mu^2) terms, added in a second sweep over this
+      // unit's outputs once its accumulators are dead (volatile reloads of the
+      // values this thread has just stored keep them out of registers):
+      //   kappa_s b omega.H = cos(Th) hr + sin(Th) hc,
+      //   kappa_s c omega.M~.omega = cos^2(Th) mrr + sin^2(Th) qmc + cos(Th) sin(Th) rmc,
+      // M~ = M - J I/3; at m + NP/2 the terms odd in (cos Ph, sin Ph) change sign.
+      C hr, hc[CB], mrr = 0, qmc[CB], rmc[CB];
+      {
+        const C kb = sc[6 * nb + bb], ht = kb * sc[8 * nb + bb], hp = kb * sc[9 * nb + bb];
+        hr = kb * sc[7 * nb + bb];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          hc[c] = t.cosP[p0 + c] * ht + t.sinP[p0 + c] * hp;
+          qmc[c] = rmc[c] = 0;
+        }
+      }
+      if (quad) {
+        const C kc = sc[10 * nb + bb], j3 = J * ((C)1 / (C)3);
+        mrr = kc * (sc[11 * nb + bb] - j3);
+        const C mtt = kc * (sc[12 * nb + bb] - j3), mpp = kc * (sc[13 * nb + bb] - j3);
+        const C mtp = (C)2 * kc * sc[14 * nb + bb];
+        const C mrt = (C)2 * kc * sc[15 * nb + bb], mrp = (C)2 * kc * sc[16 * nb + bb];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          const C cp = t.cosP[p0 + c], sp = t.sinP[p0 + c];
+          qmc[c] = cp * cp * mtt + sp * sp * mpp + cp * sp * mtp;
+          rmc[c] = cp * mrt + sp * mrp;
+        }
+      }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          const int k = side ? NT - 1 - k0 - r : k0 + r;
+          const C ct = t.cosT[k], st = t.sinT[k];
+          T* out = K + blk * S + k * NP + p0;
+          volatile T* vout = out;
+          T o1v[CB], o2v[CB];
+#pragma unroll
+          for (int c = 0; c < CB; ++c) {
+            C ev = ct * hr, od = st * hc[c];
+            if (quad) {
+              ev += ct * ct * mrr + st * st * qmc[c];
+              od += ct * st * rmc[c];
+            }
+            o1v[c] = (T)((C)vout[c] + (ev + od));
+            o2v[c] = (T)((C)vout[hP + c] + (ev - od));
+          }
+          st4<T>(out, o1v);
+          st4<T>(out + hP, o2v);
+        }
       }
     }
   }

@@ -142,13 +142,12 @@ static cudaError_t angular_pp_form(const Problem& p, const Tables<C>& t, const T
                                                             ntiles);
   return cudaGetLastError();
 }
-// The kernel with the mu^2 term runs in the run-time-size form only.
 template <typename T, typename C, int A, int B>
 static cudaError_t angular_pp(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                               int collision, int nb, long long ntiles, cudaStream_t s) {
   switch (kernel_form(p, collision)) {
     case KF_QUADRATIC:
-      return angular_pp_form<T, C, 0, 0, KF_QUADRATIC>(p, t, U, K, sgn, collision, nb, ntiles, s);
+      return angular_pp_form<T, C, A, B, KF_QUADRATIC>(p, t, U, K, sgn, collision, nb, ntiles, s);
     case KF_LINEAR:
       return angular_pp_form<T, C, A, B, KF_LINEAR>(p, t, U, K, sgn, collision, nb, ntiles, s);
     default:
