@@ -1246,19 +1246,38 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
   const int W4 = Wc / 4;
   const int n64 = p.n_fp64_rows;
   const T* Ub = U + base;
-  for (int x = threadIdx.x; x < hh * W4; x += blockDim.x) {   // even/odd parts once per pair
-    const int ii = x / W4, w = (x - ii * W4) * 4;
-    T a[4], b[4];
-    ld4<T>(Ub + ii * Si + w, a);
-    ld4<T>(Ub + (N - ii) * Si + w, b);
-    C e[4], o[4];
+  {
+    // even/odd parts once per pair; UL row pairs per trip, all their loads
+    // issued before the first store
+    constexpr int UL = sizeof(T) == 4 ? 4 : 2;
+    const int n = hh * W4;
+    for (int x0 = threadIdx.x; x0 < n; x0 += UL * (int)blockDim.x) {
+      T a[UL][4], b[UL][4];
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      e[cc] = (C)a[cc] + (C)b[cc];
-      o[cc] = (C)a[cc] - (C)b[cc];
+      for (int u = 0; u < UL; ++u) {
+        const int x = x0 + u * (int)blockDim.x;
+        if (x < n) {
+          const int ii = x / W4, w = (x - ii * W4) * 4;
+          ld4<T>(Ub + ii * Si + w, a[u]);
+          ld4<T>(Ub + (N - ii) * Si + w, b[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UL; ++u) {
+        const int x = x0 + u * (int)blockDim.x;
+        if (x < n) {
+          const int ii = x / W4, w = (x - ii * W4) * 4;
+          C e[4], o[4];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            e[cc] = (C)a[u][cc] + (C)b[u][cc];
+            o[cc] = (C)a[u][cc] - (C)b[u][cc];
+          }
+          st4<C>(sEv + ii * W + w, e);
+          st4<C>(sOd + ii * W + w, o);
+        }
+      }
     }
-    st4<C>(sEv + ii * W + w, e);
-    st4<C>(sOd + ii * W + w, o);
   }
   if (odd) {
     for (int x = threadIdx.x; x < W4; x += blockDim.x) {
