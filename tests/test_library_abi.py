@@ -50,3 +50,17 @@ def test_null_arguments_are_rejected(T):
     assert T.LIB.ts_adjoint_step(None, None, None, None, None, ctypes.c_double(0.1), None) == T.TS_ERR_ARG
     assert T.LIB.ts_destroy_grid(None) == T.TS_OK
     assert T.LIB.ts_field_elems(None) == 0
+
+
+def test_new_entry_points_reject_null_grids(T):
+    assert T.LIB.ts_set_scattering_anisotropy(None, None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_set_scattering_quadrupole(None, None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_reset_history(None) == T.TS_ERR_ARG
+
+
+def test_batches_refuse_ab2_before_touching_the_device(T):
+    descs = (T.GridDesc * 2)(_desc(T), _desc(T, scheme=T.TS_AB2))
+    h = ctypes.c_void_p()
+    assert T.LIB.ts_batch_create(descs, 2, 0, ctypes.byref(h)) == T.TS_ERR_UNSUPPORTED
+    assert h.value is None
+    assert b"AB2" in T.LIB.ts_last_error()
