@@ -10,15 +10,18 @@
  *     L_sph = cos(Th) d_r + (1/r)[ sin(Th)cos(Ph) d_th + sin(Th)sin(Ph)/sin(th) d_ph
  *                                  - sin(Th) d_Th - sin(Th)sin(Ph) cot(th) d_Ph ]
  *                                                            (Eq. Liouvsph, Sect. 4.1)
- *     CT = eta - kappa F + kappa_s (J - F),  J = (1/4 pi) int F dOmega
- *          (Eq. Transp, Sect. 2.2, with the isotropic kernel of Eq. sigman, B = 0,
- *           coherent scattering Eq. sigmadif so that groups decouple)
+ *     CT = eta - kappa F + kappa_s (J + b omega.H + c omega.M~.omega - F)
+ *          (Eq. Transp, Sect. 2.2, coherent scattering Eq. sigmadif so that groups
+ *           decouple, kernel (kappa_s/4pi)(1 + b mu + c (mu^2 - 1/3)), mu =
+ *           omega.omega'; J, H, M~ the zeroth, first and traceless second angular
+ *           moments; b = c = 0 (isotropic, Eq. sigman with B = 0) unless set by
+ *           ts_set_scattering_anisotropy / ts_set_scattering_quadrupole)
  * with spectral derivatives on every axis (Sect. 5.1): Chebyshev in r on
  * Gauss-Lobatto nodes, double-Fourier-sphere parity Fourier series on the
  * pole-free nodes th_j = pi (j+1/2)/N_theta and Th_k = pi (k+1/2)/N_Theta,
  * Fourier in phi and Phi; inflow boundaries by the Tau method (Sect. 5.1;
  * inflow at R1 where cos Theta > 0, at R2 where cos Theta < 0, Sect. 4.2);
- * classical RK4 in time.
+ * classical RK4 or second-order Adams-Bashforth (Sect. 5.1) in time.
  *
  * Conventions shared by every entry point
  *  - Layout of a field F: F[g][i_r][j_theta][l_phi][k_Theta][m_Phi], row-major,
@@ -143,7 +146,7 @@ ts_status ts_set_coeffs(ts_grid* grid, const double* kappa, const double* eta,
  * b = -(A_n/3 + A_p/10)/(A_n + A_p) with kappa_s = 4 pi (A_n + A_p) for their
  * mixture (Eq. cross). The kernel is non-negative for |b| <= 1; values are not
  * checked. NULL restores isotropic scattering (the default). Applies to every
- * later ts_step (both schemes), ts_rhs, ts_adjoint_step and batched step of the
+ * later ts_step (every scheme), ts_rhs, ts_adjoint_step and batched step of the
  * grid. TS_ERR_UNSUPPORTED if NTheta < 3 or NPhi < 3 (the split scheme's
  * closed form relies on the direction quadrature integrating omega_i omega_j
  * exactly). The first call allocates one coefficient field on the device. */
