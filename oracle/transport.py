@@ -370,10 +370,7 @@ class Grid:
     def filter(self, F, alpha=36.0, order=16):
         """Exponential filter sigma(k) = exp(-alpha (k/k_max)^order) applied
         per axis in coefficient space (r, th, ph, Th, Ph)."""
-        N = self.Nr - 1
-        sig_r = np.exp(-alpha * (np.arange(self.Nr) / N) ** order)
-        c = self.cheb_coeffs(F)
-        F = self.cheb_values(c * sig_r.reshape(1, -1, 1, 1, 1, 1))
+        F = self._filter_r(F, alpha, order)
         def circ(f, axis, kmax):
             return self._fourier_filter(f, axis, lambda k: np.exp(-alpha * (k / kmax) ** order))
         ext = self._extend(F, AX_TH, self._partner_th(F))
@@ -383,6 +380,12 @@ class Grid:
         F = np.take(circ(ext, AX_TTH, self.NT), np.arange(self.NT), axis=AX_TTH)
         F = circ(F, AX_TPH, self.NP // 2)
         return F
+
+    def _filter_r(self, F, alpha, order):
+        N = self.Nr - 1
+        sig_r = np.exp(-alpha * (np.arange(self.Nr) / N) ** order)
+        c = self.cheb_coeffs(F)
+        return self.cheb_values(c * sig_r.reshape(1, -1, 1, 1, 1, 1))
 
     # ------------------------------------------------------------- moments
     def direction_cartesian(self):
@@ -439,6 +442,61 @@ class Grid:
              * (qT * np.cos(self.Theta))[None, None, :, None] * (2 * np.pi / NP)
              * np.ones((Nt, Np, NT, NP)))
         return w
+
+
+class GridUpwindR(Grid):
+    """The hybrid grid of Sect. 5.3: spectral in (th, ph, Th, Ph) as in Grid,
+    first-order finite differences in r on N_r uniform nodes r_i = R1 + i dr.
+    Readings: the paper's "simple first order finite-difference scheme" in r is
+    taken upwind along the propagation (cos Th > 0: (F_i - F_{i-1})/dr; cos Th < 0:
+    (F_{i+1} - F_i)/dr), and the inflow node (no upstream neighbour) holds the
+    inflow data: its rate is zero instead of the Tau row. Radial integrals use the
+    trapezoid rule; the radial filter is the identity. No adjoint."""
+
+    def __init__(self, R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups=1):
+        super().__init__(R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups)
+        self.dr = (self.R2 - self.R1) / (Nr - 1)
+        self.r = self.R1 + self.dr * np.arange(Nr)
+
+    def d_r_upwind(self, F):
+        """One-sided differences upstream of each direction; zero at the inflow node."""
+        back = np.zeros_like(F)
+        back[:, 1:] = (F[:, 1:] - F[:, :-1]) / self.dr
+        fwd = np.zeros_like(F)
+        fwd[:, :-1] = (F[:, 1:] - F[:, :-1]) / self.dr
+        out = (np.cos(self.Theta) > 0).reshape(1, 1, 1, 1, -1, 1)
+        return np.where(out, back, fwd)
+
+    def liouville(self, F):
+        a_r, a_th, a_ph, a_Th, a_Ph = self.coefficients()
+        return (a_r * self.d_r_upwind(F) + a_th * self.d_th(F) + a_ph * self.d_ph(F)
+                + a_Th * self.d_Th(F) + a_Ph * self.d_Ph(F))
+
+    def tau(self, K, gdot=0.0):
+        """The inflow nodes hold the static inflow data: their rate is gdot (= 0)."""
+        K = K.copy()
+        b_of_k = self._inflow_node_index()
+        for kk in range(self.NT):
+            K[:, b_of_k[kk], :, :, kk, :] = gdot
+        return K
+
+    def clenshaw_curtis_r(self, h, axis=AX_R):
+        """int_{R1}^{R2} h dr by the trapezoid rule on the uniform nodes."""
+        w = np.full(self.Nr, self.dr)
+        w[0] = w[-1] = 0.5 * self.dr
+        return np.tensordot(h, w, axes=([axis], [0]))
+
+    def _filter_r(self, F, alpha, order):
+        return F
+
+    def d_r(self, F):
+        raise NotImplementedError("the upwind radial derivative depends on the direction")
+
+    def liouville_T(self, mu):
+        raise NotImplementedError("no adjoint on the finite-difference radial grid")
+
+    def tau_T(self, mu):
+        raise NotImplementedError("no adjoint on the finite-difference radial grid")
 
 
 class Problem:

@@ -16,7 +16,7 @@ import numpy.polynomial.chebyshev as npcheb
 import pytest
 
 import analytic as A
-from oracle.transport import Grid, Problem, exact_free_streaming, nucleon_scattering
+from oracle.transport import Grid, GridUpwindR, Problem, exact_free_streaming, nucleon_scattering
 from paper_1104_5330_gb300 import inputs as I
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.txt")
@@ -262,6 +262,39 @@ def pin_kernel_brute_force(phase, b=None, c=None, seed=21):
                 ref = ks[0, i, j, l] * (K @ F[0, i, j, l].ravel())
                 worst = max(worst, np.abs(gain[0, i, j, l].ravel() - ref).max() / np.abs(ref).max())
     return worst
+
+
+def pin_upwind_identities():
+    """First-order upwind differences in r (Sect. 5.3) are exact on linear data and
+    off by -+dr on r^2 (backward: 2r - dr, forward: 2r + dr): with the spectral
+    angular derivatives exact on cos(Th), L_h r^2 = cos(Th)(2r -+ dr) and
+    L_h (r cos Th) = 1 (= omega.grad of x.omega) away from the inflow nodes, where
+    the one-sided difference has no upstream point and is zero."""
+    g = GridUpwindR(0.3, 1.1, 9, 4, 6, 8, 6)
+    r = g.r.reshape(1, -1, 1, 1, 1, 1)
+    c = np.cos(g.Theta).reshape(1, 1, 1, 1, -1, 1)
+    inflow = np.zeros((1, g.Nr, 1, 1, g.NT, 1), dtype=bool)
+    for kk, b in enumerate(g._inflow_node_index()):
+        inflow[0, b, 0, 0, kk, 0] = True
+    F2 = np.broadcast_to(r ** 2, g.shape)
+    ex2 = np.where(inflow, 0.0, c * (2 * r - np.sign(c) * g.dr))
+    F1 = np.broadcast_to(r * c, g.shape)
+    L1 = g.liouville(np.ascontiguousarray(F1))
+    ex1 = np.where(inflow, L1, 1.0)      # at the inflow nodes only the angular part remains
+    return max(np.abs(g.liouville(np.ascontiguousarray(F2)) - ex2).max(), np.abs(L1 - ex1).max())
+
+
+def pin_upwind_free_streaming(Nr, T=0.1):
+    """Vacuum free streaming of the Gaussian shell against the exact solution
+    (Eq. Tra1) on the upwind radial grid, dt = 0.4 dr."""
+    g = GridUpwindR(0.2, 1.0, Nr, 4, 4, 8, 4)
+    F0f = lambda rr, mu: np.exp(-((rr - 0.6) / 0.1) ** 2) * (1 + 0.5 * mu)
+    pr = Problem(g)
+    F = pr.apply_inflow(I.gaussian_shell(g.r, g.theta, g.phi, g.Theta, g.Phi))
+    dt = 0.4 * g.dr
+    n = int(round(T / dt))
+    ex = exact_free_streaming(g, F0f, n * dt)
+    return np.abs(pr.run(F, dt, n)[0, :, 0, 0, :, 0] - ex).max()
 
 
 # ---------------------------------------------------------------------- tests
@@ -551,6 +584,26 @@ def test_ab2_history_restart():
     assert np.abs(d - a).max() > 1e-10
 
 
+def test_upwind_radial_grid_identities_and_hold():
+    assert pin_upwind_identities() < 1e-12
+    g = GridUpwindR(0.2, 1.0, 7, 4, 4, 6, 4)
+    K = np.random.default_rng(2).standard_normal(g.shape)
+    T = g.tau(K)
+    h = g.NT // 2
+    assert np.all(T[:, 0, :, :, :h] == 0) and np.all(T[:, -1, :, :, h:] == 0)
+    assert np.array_equal(T[:, 1:-1], K[:, 1:-1])
+    # trapezoid rule in r: exact on linear integrands
+    assert abs(g.clenshaw_curtis_r(1.0 + 2.0 * g.r, axis=0) - (0.8 + (1.0 - 0.04))) < 1e-14
+
+
+def test_upwind_radial_grid_converges_at_first_order():
+    """Sect. 5.3 uses a first-order radial scheme: halving dr halves the error."""
+    e = [pin_upwind_free_streaming(n) for n in (33, 65, 129)]
+    assert e[2] < 0.1
+    for a, b in zip(e, e[1:]):
+        assert 1.6 < a / b < 2.2, e
+
+
 def test_nucleon_mixture_kernel():
     """Eqs. (crossnun, crossnup): b = -1/3 on neutrons, -1/10 on protons; the
     mixture's first-moment damping kappa_s (1 - b/3) equals the optical depth
@@ -710,6 +763,18 @@ def _m14(mp):
     mp.setattr(Problem, "ab2_step", bad)
 
 
+@mutant("radial differences taken downwind")
+def _m17(mp):
+    def bad(self, F):
+        back = np.zeros_like(F)
+        back[:, 1:] = (F[:, 1:] - F[:, :-1]) / self.dr
+        fwd = np.zeros_like(F)
+        fwd[:, :-1] = (F[:, 1:] - F[:, :-1]) / self.dr
+        out = (np.cos(self.Theta) > 0).reshape(1, 1, 1, 1, -1, 1)
+        return np.where(out, fwd, back)
+    mp.setattr(GridUpwindR, "d_r_upwind", bad)
+
+
 @mutant("anisotropic term with the wrong sign")
 def _m11(mp):
     orig = Problem.collision
@@ -770,6 +835,7 @@ def _all_pins_pass():
         lambda: pin_anisotropic(Grid(0.2, 1.0, 4, 5, 6, 6, 8), quadrupole=True) < 1e-13,
         lambda: pin_kernel_brute_force(lambda mu, ix: 3.0 / (16 * np.pi) * (1 + mu ** 2), c=0.75) < 1e-13,
         lambda: pin_ab2(nsteps=6) < 1e-13,
+        lambda: pin_upwind_identities() < 1e-12,
     ]
     for c in checks:
         try:
