@@ -19,8 +19,9 @@ and the clock, with a measured DFMA-loop rate beside it), end-to-end rate
 through ts_step_host (host buffers, copies inside the timed region), the
 reduced-precision variants (FP32, FP32 + FP64 radial rows, tensor-core TF32x3
 and BF16x3) and the adjoint step on the same workload, the same grid with
-linearly anisotropic neutrino-nucleon scattering and with the paper's AB2 time
-marching, the 64-problem batch,
+linearly anisotropic neutrino-nucleon scattering, with Thomson scattering and with
+the paper's AB2 time marching, the Lambert-shell run of Sect. 5.3 on the hybrid
+grid (upwind finite differences in r), the 64-problem batch,
 the differentiation workload (33 x 16^4, 8 groups, 200 steps with sqrt(N)
 checkpoints), the CPU oracle timed on a bounded sample on this host's cores,
 and SM clocks sampled during the timed region.
@@ -470,6 +471,42 @@ def run_ab2(args, dims, stream, rk4_ms_per_step):
             "simulated_time_rate_vs_rk4": (dt / (ms / n)) / (dt_rk4 / rk4_ms_per_step)}
 
 
+def run_hybrid(args, stream):
+    """The 5-D shell run of Sect. 5.3 on the hybrid grid (first-order upwind
+    differences in r on 129 uniform nodes, spectral angular axes 16 x 16 x 24 x 16,
+    one group, FP64, RK4 at dt = 0.4 dr): empty shell 0.5 <= r <= 1, Lambert
+    emission F0 cos(Theta) at R1, coherent scattering of optical depth 5 from a
+    plasma vanishing at R2. Reports the step rate and the radial pass's time."""
+    import torch
+    import paper_1104_5330_gb300.ts as ts
+    from paper_1104_5330_gb300 import inputs as I
+    R1, R2, Nr, Nt, Np, NT, NP = 0.5, 1.0, 129, 16, 16, 24, 16
+    gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=1, precision=ts.TS_FP64,
+                 radial=ts.TS_RADIAL_UPWIND_FD)
+    r, th, ph, Th, Ph = gg.nodes()
+    ks = I.shell_scattering(r, th, ph, R1, R2, 5.0)
+    gR1, gR2 = I.lambert_inflow(Th, Nt, Np, NP)
+    gg.set_coeffs(None, None, ks, gR1, gR2)
+    dt = 0.4 * (R2 - R1) / (Nr - 1)
+    F = gg.apply_inflow(torch.zeros(gg.shape, dtype=torch.float64, device="cuda"))
+    gg.step(F, dt, args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gg.step(F, dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pm, pn = ts.ts_step_profile(gg.handle, F, dt, max(2, min(args.steps, 10)))
+    ts.ts_sync_status(gg.handle)
+    return {"value": gg.points * args.steps / (ms * 1e-3), "unit": "point-updates/s",
+            "ms_per_step": ms / args.steps, "dtype": "f64",
+            "workload": f"Lambert shell, optical depth 5, {Nr}x{Nt}x{Np}x{NT}x{NP}, 1 group",
+            "radial": "first-order upwind differences on uniform nodes",
+            "pass_ms_per_launch": {n: float(pm[a] / pn[a])
+                                   for a, n in enumerate(("angular", "plane", "radial"))}}
+
+
 def run_ours(args, dims, wname):
     import torch
     import torch.distributed as dist
@@ -659,6 +696,7 @@ def run_ours(args, dims, wname):
     if not args.skip_aniso:
         line["anisotropic_scattering"] = run_anisotropic(args, dims, stream)
         line["ab2"] = run_ab2(args, dims, stream, ms / args.steps)
+        line["hybrid_radial_fd"] = run_hybrid(args, stream)
     if not args.skip_batch:
         line["batch"] = run_batch(args, stream)
     if not args.skip_diff and args.diff_steps > 0:

@@ -97,6 +97,19 @@ typedef enum {
   TS_BC_NONE = 1         /* no boundary rows (operator tests, closed domains) */
 } ts_bc;
 
+typedef enum {
+  TS_RADIAL_CHEBYSHEV = 0,  /* Chebyshev-Gauss-Lobatto nodes, spectral d_r (Sect. 5.1) */
+  TS_RADIAL_UPWIND_FD = 1   /* the hybrid grid of Sect. 5.3: N_r uniform nodes
+                               r_i = R1 + i (R2-R1)/(N_r-1), first-order one-sided
+                               differences upstream of each direction (cos Theta > 0:
+                               (F_i - F_{i-1})/dr, cos Theta < 0: (F_{i+1} - F_i)/dr);
+                               with TS_BC_TAU_INFLOW the inflow nodes hold their data
+                               (zero rate) in place of the Tau rows; radial integrals by
+                               the trapezoid rule; no radial filter. TS_FP64 and
+                               TS_FP32 only; no adjoint, no batches, no
+                               ts_moments_noalloc (TS_ERR_UNSUPPORTED). */
+} ts_radial;
+
 typedef struct {
   double R1, R2;                            /* shell radii, 0 < R1 < R2 */
   int Nr, Ntheta, Nphi, NTheta, NPhi;       /* nodes per axis */
@@ -107,6 +120,7 @@ typedef struct {
   int filter_on;                            /* 1: exponential filter after each step */
   double filter_alpha;                      /* sigma(k) = exp(-alpha (k/kmax)^order) */
   int filter_order;
+  int radial;                               /* ts_radial (0: Chebyshev) */
 } ts_grid_desc;
 
 typedef struct ts_grid ts_grid;             /* opaque, library-owned */

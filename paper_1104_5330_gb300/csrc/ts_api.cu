@@ -412,8 +412,10 @@ HostTables build_tables(const ts_grid_desc& g) {
   HostTables h;
   const int Nr = g.Nr, Nt = g.Ntheta, Np = g.Nphi, NT = g.NTheta, NP = g.NPhi;
   const int N = Nr - 1;
+  const bool fd = g.radial == TS_RADIAL_UPWIND_FD;
   for (int i = 0; i < Nr; ++i)
-    h.r.push_back(0.5 * (g.R1 + g.R2) - 0.5 * (g.R2 - g.R1) * std::cos(M_PI * i / N));
+    h.r.push_back(fd ? g.R1 + (g.R2 - g.R1) * i / N
+                     : 0.5 * (g.R1 + g.R2) - 0.5 * (g.R2 - g.R1) * std::cos(M_PI * i / N));
   for (int j = 0; j < Nt; ++j) h.theta.push_back(M_PI * (j + 0.5) / Nt);
   for (int l = 0; l < Np; ++l) h.phi.push_back(2.0 * M_PI * l / Np);
   for (int k = 0; k < NT; ++k) h.Theta.push_back(M_PI * (k + 0.5) / NT);
@@ -428,6 +430,10 @@ HostTables build_tables(const ts_grid_desc& g) {
   const double fa = g.filter_alpha > 0 ? g.filter_alpha : 36.0;
   const int fo = g.filter_order > 0 ? g.filter_order : 16;
   h.Fr = cheb_filter(Nr, fa, fo);
+  if (fd) {   // no radial filter on the finite-difference grid
+    h.Fr.assign((size_t)Nr * Nr, 0.0);
+    for (int i = 0; i < Nr; ++i) h.Fr[(size_t)i * Nr + i] = 1.0;
+  }
   dfs_split(fourier_filter(2 * Nt, Nt, fa, fo), Nt, h.FthA, h.FthB);
   h.Fph = fourier_filter(Np, Np / 2, fa, fo);
   dfs_split(fourier_filter(2 * NT, NT, fa, fo), NT, h.FThA, h.FThB);
@@ -460,7 +466,12 @@ HostTables build_tables(const ts_grid_desc& g) {
     h.sinP.push_back(std::sin(h.Phi[m]));
   }
   const Vec cc = clenshaw_curtis(Nr);
-  for (int i = 0; i < Nr; ++i) h.wr.push_back(cc[i] * 0.5 * (g.R2 - g.R1) * h.r[i] * h.r[i]);
+  for (int i = 0; i < Nr; ++i) {
+    // int r^2 dr: Clenshaw-Curtis on the Chebyshev nodes, trapezoid on the uniform ones
+    const double w = fd ? (g.R2 - g.R1) / N * ((i == 0 || i == N) ? 0.5 : 1.0)
+                        : cc[i] * 0.5 * (g.R2 - g.R1);
+    h.wr.push_back(w * h.r[i] * h.r[i]);
+  }
   h.wth = fejer(Nt);
   even_odd_tables(h);
   tc_tables(h);
@@ -550,6 +561,18 @@ struct Profiler {
     if (e == cudaSuccess && (prof)) e = (prof)->end(k);      \
   } while (0)
 
+// The radial pass of the grid's radial discretisation: the spectral pass
+// (Chebyshev nodes) or the one-sided differences of the hybrid grid.
+template <typename T, typename C>
+cudaError_t radial_pass(const ts_grid* g, const ts::Problem& p, const Tables<C>& t, const T* U,
+                        const T* K, C sgn, bool tau, int mode, T* F, T* Acc, T* Uout, T* out,
+                        double dt, cudaStream_t st) {
+  if (g->desc.radial == TS_RADIAL_UPWIND_FD)
+    return ts::launch_radial_fd<T, C>(p, t, U, K, sgn, tau, mode, F, Acc, Uout, out, dt,
+                                      (g->desc.R2 - g->desc.R1) / (g->desc.Nr - 1), st);
+  return Launch<T, C>::radial(p, t, g->t64.Dr, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, st);
+}
+
 template <typename T, typename C>
 cudaError_t run_stage(ts_grid* g, const Tables<C>& t, const T* in, T* F, int s, bool collision,
                       double dt, cudaStream_t st, Profiler* prof) {
@@ -560,9 +583,8 @@ cudaError_t run_stage(ts_grid* g, const Tables<C>& t, const T* in, T* F, int s, 
   cudaError_t e = cudaSuccess;
   TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, (C)-1, collision, st)));
   TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, in, K, (C)-1, st)));
-  TS_TIMED(prof, 2, (Launch<T, C>::radial(p, t, g->t64.Dr, in, K, (C)-1,
-                                          g->desc.bc == TS_BC_TAU_INFLOW, ts::RAD_STAGE0 + s, F,
-                                          Acc, U, nullptr, dt, st)));
+  TS_TIMED(prof, 2, (radial_pass<T, C>(g, p, t, in, K, (C)-1, g->desc.bc == TS_BC_TAU_INFLOW,
+                                       ts::RAD_STAGE0 + s, F, Acc, U, nullptr, dt, st)));
   return e;
 }
 
@@ -583,9 +605,9 @@ cudaError_t run_steps(ts_grid* g, const Tables<C>& t, T* F, double dt, int nstep
     for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
       TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, F, K, (C)-1, true, st)));
       TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, F, K, (C)-1, st)));
-      TS_TIMED(prof, 2, (Launch<T, C>::radial(p, t, g->t64.Dr, F, K, (C)-1, tau,
-                                              g->hist ? ts::RAD_AB2 : ts::RAD_AB2_START, F, Acc,
-                                              nullptr, nullptr, dt, st)));
+      TS_TIMED(prof, 2, (radial_pass<T, C>(g, p, t, F, K, (C)-1, tau,
+                                           g->hist ? ts::RAD_AB2 : ts::RAD_AB2_START, F, Acc,
+                                           nullptr, nullptr, dt, st)));
       if (e == cudaSuccess) g->hist = true;
       if (g->desc.filter_on) TS_TIMED(prof, 3, (Launch<T, C>::filter(p, t, F, K, st)));
     }
@@ -609,9 +631,8 @@ cudaError_t run_rhs(ts_grid* g, const Tables<C>& t, const T* F, T* K, bool liouv
   cudaError_t e = Launch<T, C>::angular(p, t, F, K, sgn, !liouville_only, st);
   if (e == cudaSuccess) e = Launch<T, C>::plane(p, t, F, K, sgn, st);
   if (e == cudaSuccess)
-    e = Launch<T, C>::radial(p, t, g->t64.Dr, F, K, sgn,
-                             !liouville_only && g->desc.bc == TS_BC_TAU_INFLOW, ts::RAD_RHS,
-                             nullptr, nullptr, nullptr, K, 0.0, st);
+    e = radial_pass<T, C>(g, p, t, F, K, sgn, !liouville_only && g->desc.bc == TS_BC_TAU_INFLOW,
+                          ts::RAD_RHS, nullptr, nullptr, nullptr, K, 0.0, st);
   return e;
 }
 
@@ -699,6 +720,10 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   if (g.scheme != TS_RK4 && g.scheme != TS_RK4_SPLIT_IMPLICIT && g.scheme != TS_AB2)
     return fail(TS_ERR_UNSUPPORTED, "unknown scheme");
   if (g.bc != TS_BC_TAU_INFLOW && g.bc != TS_BC_NONE) return fail(TS_ERR_UNSUPPORTED, "unknown bc");
+  if (g.radial != TS_RADIAL_CHEBYSHEV && g.radial != TS_RADIAL_UPWIND_FD)
+    return fail(TS_ERR_UNSUPPORTED, "unknown radial discretisation");
+  if (g.radial == TS_RADIAL_UPWIND_FD && g.precision != TS_FP64 && g.precision != TS_FP32)
+    return fail(TS_ERR_UNSUPPORTED, "the finite-difference radial grid runs in TS_FP64 or TS_FP32");
   const size_t es = g.precision == TS_FP64 ? 8 : 4;
   if (!fits(g, es)) return fail(TS_ERR_UNSUPPORTED, "grid too large for one shared-memory tile");
 
@@ -717,6 +742,7 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   {
     const char* gen = std::getenv("TS_GENERIC_PASSES");  // 1: plain passes only (testing)
     G->tp.rb = (gen && gen[0] == '1') ? 0 : ts::rb_mask(d, (int)es, g.precision == TS_FP32_R64 ? 2 : 0);
+    if (g.radial == TS_RADIAL_UPWIND_FD) G->tp.rb &= ~4;   // no even/odd radial form
   }
 
   cudaError_t e = upload_tables<double>(G->h, &G->tab64, &G->t64);
@@ -958,6 +984,8 @@ ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* gra
   if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   if (g->desc.scheme != TS_RK4 || g->desc.filter_on)
     return fail(TS_ERR_UNSUPPORTED, "adjoint covers the TS_RK4 scheme without filter");
+  if (g->desc.radial != TS_RADIAL_CHEBYSHEV)
+    return fail(TS_ERR_UNSUPPORTED, "adjoint covers the Chebyshev radial grid");
   if (!g->adj[0]) {
     for (int a = 0; a < 7; ++a) {
       cudaError_t e = cudaMalloc(&g->adj[a], field_bytes(g));

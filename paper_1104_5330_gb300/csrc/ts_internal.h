@@ -134,6 +134,13 @@ enum TcKind { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2 };
 cudaError_t launch_radial_tc(const Problem& p, const Tables<float>& t, const float* U,
                              const float* K, float sgn, bool tau, int mode, float* F, float* Acc,
                              float* Uout, float* out, double dt, cudaStream_t s);
+// Radial pass of the hybrid grid (uniform r nodes, one-sided upwind differences;
+// `hold`: zero rate at the inflow nodes). Defined in ts_fd.cu.
+template <typename T, typename C>
+cudaError_t launch_radial_fd(const Problem& p, const Tables<C>& t, const T* U, const T* K, C sgn,
+                             bool hold, int mode, T* F, T* Acc, T* Uout, T* out, double dt,
+                             double dr, cudaStream_t s);
+
 // Whether the tensor-core radial pass handles N_r (its tile must fit shared memory).
 inline bool tc_supported(int Nr) { return Nr >= 3 && Nr <= 81; }
 

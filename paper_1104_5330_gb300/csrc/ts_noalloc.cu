@@ -197,6 +197,8 @@ ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0
     return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: unsupported grid sizes");
   if (d.precision != TS_FP64 && d.precision != TS_FP32 && d.precision != TS_FP32_R64)
     return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: unknown precision");
+  if (d.radial != TS_RADIAL_CHEBYSHEV)
+    return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: Chebyshev radial grids only");
   Sizes z{d.groups, d.Nr, d.Ntheta, d.Nphi, d.NTheta, d.NPhi, d.R1, d.R2,
           (long long)d.groups * d.Nr * d.Ntheta * d.Nphi};
   const long long need = z.nblk + 2LL * d.groups * d.Ntheta * d.Nphi;

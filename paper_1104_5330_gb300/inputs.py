@@ -194,6 +194,29 @@ def signed_field(r, theta, phi, groups, seed, R1, R2):
                                                with_direction=False)) for g in range(groups)])
 
 
+def lambert_inflow(Theta, Ntheta, Nphi, NPhi, groups=1, F0=1.0):
+    """Inflow data of a Lambert emitter at the inner sphere: F(R1) = F0 cos(Theta)
+    on the outgoing directions (cos Theta > 0, the first NTheta/2 nodes), nothing
+    entering at R2. Returns (g_R1, g_R2), each [G][Ntheta][Nphi][NTheta/2][NPhi]."""
+    h = len(Theta) // 2
+    c = np.cos(np.asarray(Theta[:h]))[None, None, None, :, None]
+    gR1 = np.ascontiguousarray(np.broadcast_to(F0 * c, (groups, Ntheta, Nphi, h, NPhi)))
+    return gR1, np.zeros_like(gR1)
+
+
+def shell_scattering(r, theta, phi, R1, R2, tau, groups=1):
+    """Scattering coefficient of the shell plasma n0 [1 + 0.1 r sin(th) cos(ph) cos(th)]
+    [1 - (r - R1)/(R2 - R1)]^8 (largest at R1, vanishing at R2), scaled so that
+    the radial optical depth of the unmodulated profile, int kappa_s dr, is tau.
+    Returns [G][Nr][Nth][Nph]."""
+    rr = np.asarray(r)[:, None, None]
+    th = np.asarray(theta)[None, :, None]
+    ph = np.asarray(phi)[None, None, :]
+    k0 = 9.0 * tau / (R2 - R1)
+    ks = k0 * (1.0 + 0.1 * rr * np.sin(th) * np.cos(ph) * np.cos(th)) * (1.0 - (rr - R1) / (R2 - R1)) ** 8
+    return np.ascontiguousarray(np.broadcast_to(ks, (groups,) + ks.shape))
+
+
 def inflow_from(F, NTheta):
     """Static inflow data equal to F's own values at the inflow nodes:
     r = R1 for the directions with cos Theta > 0 (the first NTheta/2 Theta

@@ -34,6 +34,7 @@ def _desc(T, **kw):
     (dict(Nr=2), 2), (dict(Nr=200), 2), (dict(Nphi=7), 2), (dict(NTheta=5), 2),
     (dict(NPhi=3), 2), (dict(NTheta=66), 2), (dict(R1=0.0), 1), (dict(R2=0.1), 1),
     (dict(groups=0), 1), (dict(precision=9), 2), (dict(scheme=4), 2), (dict(bc=3), 2),
+    (dict(radial=2), 2), (dict(radial=1, precision=3), 2), (dict(radial=1, precision=2), 2),
 ])
 def test_create_grid_rejects_bad_descriptors(T, kw, status):
     h = ctypes.c_void_p()
@@ -64,3 +65,8 @@ def test_batches_refuse_ab2_before_touching_the_device(T):
     assert T.LIB.ts_batch_create(descs, 2, 0, ctypes.byref(h)) == T.TS_ERR_UNSUPPORTED
     assert h.value is None
     assert b"AB2" in T.LIB.ts_last_error()
+    descs = (T.GridDesc * 1)(_desc(T, radial=T.TS_RADIAL_UPWIND_FD))
+    assert T.LIB.ts_batch_create(descs, 1, 0, ctypes.byref(h)) == T.TS_ERR_UNSUPPORTED
+    d = _desc(T, radial=T.TS_RADIAL_UPWIND_FD)
+    assert T.LIB.ts_moments_noalloc(ctypes.byref(d), ctypes.c_void_p(1), None, None, None,
+                                    None, None, None) == T.TS_ERR_UNSUPPORTED
