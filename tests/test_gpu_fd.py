@@ -134,3 +134,16 @@ def test_unsupported_combinations():
     d = ts.GridDesc(0.2, 1.0, 9, 4, 4, 4, 4, 1, 0, 0, 0, 0, 36.0, 16, ts.TS_RADIAL_UPWIND_FD)
     with pytest.raises(ts.TSError):
         ts.Batch([d], autotune=False)
+
+
+def test_largest_radial_size_129_nodes():
+    """N_r = 129 (the paper's hybrid run), ragged angular sizes, AB2 with held inflow."""
+    ts = T()
+    og, gg = _pair((0.5, 1.0, 129, 5, 6, 8, 10), G=2, scheme=ts.TS_AB2)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = OProblem(og, kap, eta, ks, gR1, gR2, scheme="ab2")
+    gg.set_coeffs(kap, eta, ks, gR1, gR2)
+    dt = 0.5 * _dt(og)
+    Fg = cuda(F0)
+    gg.step(Fg, dt, 12)
+    assert rel_l2(host(Fg), op.run(F0, dt, 12)) < FP64_TOL
