@@ -51,8 +51,8 @@ class GridDesc(ctypes.Structure):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libts.so not built ({LIB_PATH}); run __graft_entry__.build() "
-                          "or python -m paper_1104_5330_gb300.build")
+        raise ImportError(f"libts.so not built ({LIB_PATH}); run "
+                          "python -m paper_1104_5330_gb300.build")
     lib = ctypes.CDLL(LIB_PATH)
     P, D, I, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
     sig = {
