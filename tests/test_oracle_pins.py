@@ -584,6 +584,19 @@ def test_ab2_history_restart():
     assert np.abs(d - a).max() > 1e-10
 
 
+def test_outgoing_flux_weights_reproduce_the_flux():
+    """The weights of the differentiation objective give the outgoing flux J_R2 of
+    Eq. (Flux) for any field, and the closed form R2^2 4 pi 2 pi a 2/3 for
+    F = 1 + a cos(Theta) (the same integral as in test_moments_two_moment_form)."""
+    g = Grid(0.3, 1.2, 5, 6, 8, 8, 10, groups=2)
+    w = g.outgoing_flux_weights()
+    F = np.random.default_rng(13).standard_normal(g.shape)
+    J2 = g.moments(F)[4]
+    assert np.allclose((w * F[:, -1]).sum(axis=(1, 2, 3, 4)), J2, rtol=1e-13, atol=1e-13)
+    Fc = np.ascontiguousarray(np.broadcast_to(1.0 + 0.6 * np.cos(g.Theta)[:, None], g.shape))
+    assert abs((w * Fc[0, -1]).sum() - 1.2 ** 2 * 4 * math.pi * 2 * math.pi * 0.6 * 2 / 3) < 1e-12
+
+
 def test_upwind_radial_grid_identities_and_hold():
     assert pin_upwind_identities() < 1e-12
     g = GridUpwindR(0.2, 1.0, 7, 4, 4, 6, 4)
