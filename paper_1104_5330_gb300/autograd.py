@@ -13,7 +13,10 @@ recomputed once.
 App. A) with the library's quadrature weights (ts_flux_weights).
 
 All tensors live on the grid's device; kappa, eta, kappa_s are float64
-[G][Nr][Ntheta][Nphi]; F has the grid's element type.
+[G][Nr][Ntheta][Nphi]; F has the grid's element type. The grid's scattering
+kernel (set with set_scattering_anisotropy / set_scattering_quadrupole) applies
+to the forward steps and to their adjoint alike; the grid must use the TS_RK4
+scheme on the Chebyshev radial grid (the adjoint's scope).
 """
 from __future__ import annotations
 
