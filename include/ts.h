@@ -134,8 +134,9 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out);
 /* Free the grid's tables and workspace. Synchronizes the device first. */
 ts_status ts_destroy_grid(ts_grid* grid);
 
-/* Host copies of the nodes: r[Nr] (Chebyshev-Gauss-Lobatto on [R1,R2],
- * ascending), theta[Ntheta], phi[Nphi], Theta[NTheta], Phi[NPhi]. Any pointer
+/* Host copies of the nodes: r[Nr] (Chebyshev-Gauss-Lobatto on [R1,R2], or
+ * uniform for TS_RADIAL_UPWIND_FD; ascending), theta[Ntheta], phi[Nphi],
+ * Theta[NTheta], Phi[NPhi]. Any pointer
  * may be NULL. Synchronous, host memory only. */
 ts_status ts_grid_nodes(const ts_grid* grid, double* r_host, double* theta_host,
                         double* phi_host, double* Theta_host, double* Phi_host);
@@ -191,8 +192,10 @@ ts_status ts_apply_inflow(ts_grid* grid, void* F, void* stream);
 ts_status ts_reset_history(ts_grid* grid);
 
 /* Advance F (in place) by `nsteps` steps of size dt with the grid's scheme,
- * boundary rows and filter. Requires ts_set_coeffs first (TS_ERR_STATE).
- * Uses the grid's workspace: calls on one grid must not overlap. */
+ * boundary rows, scattering kernel and filter. Requires ts_set_coeffs first
+ * (TS_ERR_STATE). Uses the grid's workspace: calls on one grid must not
+ * overlap. Launches per step: 12 for TS_RK4 (three passes per stage), 13 for
+ * TS_RK4_SPLIT_IMPLICIT, 3 for TS_AB2, plus the filter's when it is on. */
 ts_status ts_step(ts_grid* grid, void* F, double dt, int nsteps, void* stream);
 
 /* As ts_step, and also times every kernel launch with CUDA events recorded on
