@@ -210,7 +210,8 @@ ts_status ts_step_profile(ts_grid* grid, void* F, double dt, int nsteps, double*
                           int* launches_host, void* stream);
 
 /* As ts_step, with F in HOST memory: copies F to the device, steps, copies
- * back, and synchronizes `stream` before returning. F_host should be pinned
+ * back, and synchronizes `stream` before returning (for TS_AB2 the history
+ * follows the host pointer: stepping another F_host restarts it). F_host should be pinned
  * for full copy bandwidth. */
 ts_status ts_step_host(ts_grid* grid, void* F_host, double dt, int nsteps, void* stream);
 
