@@ -634,6 +634,34 @@ class Problem:
             F = self.step(F, dt)
         return F
 
+    # ------------------------------------------------------ time-step limit
+    def spectral_radius(self, x0, iters=60):
+        """Power-iteration estimate of the spectral radius of the linear part of
+        the stage operator, A x = rhs(x) - rhs(0) (the stage derivative with
+        eta = 0 and homogeneous inflow rows), from the start field x0: x <- A x,
+        renormalised each iteration; the estimate is the geometric mean of the
+        growth factors ||A x|| / ||x|| over the second half of the iterations
+        (their product over m iterations tends to rho^m: Gelfand's formula; the
+        single factor oscillates when the largest eigenvalues are a complex
+        pair, their geometric mean does not)."""
+        K0 = self.rhs(np.zeros_like(x0))
+        x = x0 / np.linalg.norm(x0)
+        logs = []
+        for _ in range(iters):
+            y = self.rhs(x) - K0
+            ny = np.linalg.norm(y)
+            logs.append(np.log(ny))
+            x = y / ny
+        half = logs[len(logs) // 2:]
+        return float(np.exp(np.mean(half)))
+
+    def stable_dt(self, x0, iters=60, limit=2.6):
+        """Largest dt with dt rho(A) <= limit (RK4: its stability region reaches
+        2 sqrt(2) on the imaginary axis and 2.79 on the negative real axis; 2.6
+        keeps a margin for the estimate) -- the explicit scheme's Courant limit
+        (Sect. 5.4) from the discrete operator itself, every axis included."""
+        return limit / self.spectral_radius(x0, iters)
+
     # ------------------------------------------------------------- adjoint
     def _A_T(self, lam):
         """Transpose of the linear stage operator

@@ -877,3 +877,32 @@ def test_two_summation_orders_agree():
         Kb = Problem(b, kap, eta, ks).rhs(F)
         assert np.linalg.norm(Ka - Kb) / np.linalg.norm(Ka) < 1e-13
     assert pin_liouville(Grid(0.2, 1.0, 9, 8, 8, 8, 8, summation="library")) < 1e-12
+
+
+def test_power_iteration_finds_the_spectral_radius_and_a_stable_step():
+    """On a grid small enough for the dense operator, the power-iteration
+    estimate of rho(A) agrees with the largest eigenvalue modulus of A (numpy's
+    eig) within a few percent; RK4 at the guard's step stays bounded over many
+    steps, at twice the RK4 limit it grows (Sect. 5.4's Courant limits, taken
+    from the discrete operator: every axis included)."""
+    from oracle.transport import Grid, Problem
+    from paper_1104_5330_gb300 import inputs as I
+    g = Grid(0.2, 1.0, 9, 2, 4, 4, 4)
+    kap, eta, ks = I.absorber_fields(g.r, g.theta, g.phi, groups=1)
+    pr = Problem(g, kap, None, ks)
+    n = g.points
+    K0 = pr.rhs(np.zeros(g.shape))
+    A = np.stack([(pr.rhs(np.eye(n)[j].reshape(g.shape)) - K0).ravel() for j in range(n)], 1)
+    rho = np.abs(np.linalg.eigvals(A)).max()
+    x0 = np.random.default_rng(3).standard_normal(g.shape)
+    est = pr.spectral_radius(x0, iters=200)
+    assert abs(est - rho) < 0.05 * rho, (est, rho)
+    dt = pr.stable_dt(x0, iters=200)
+    F = x0.copy()
+    for _ in range(300):
+        F = pr.rk4_step(F, dt)
+    assert np.linalg.norm(F) < 10 * np.linalg.norm(x0)
+    G = x0.copy()
+    for _ in range(30):
+        G = pr.rk4_step(G, 2.2 * dt)
+    assert np.linalg.norm(G) > 1e3 * np.linalg.norm(x0)
