@@ -15,7 +15,10 @@
 // code only ever sees a host-side stand-in under the array's name, so the
 // first call on each device looks up its device address with
 // cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should come before any stream capture. Every call shares the array and
+// call should come before any stream capture. Later calls on a stream that is
+// not capturing look the address up again (it is cheap), so a device reset that
+// reloads the module and moves the array is picked up; during a capture the
+// cached address is used. Every call shares the array and
 // it keeps the last call's contents: every slot a call reads is written by the
 // same call first, so nothing needs clearing, but calls whose kernels overlap
 // on the GPU (different streams, or host threads) race on the array.
@@ -161,15 +164,21 @@ ts_status noalloc_fail(ts_status s, const std::string& m) {
   return s;
 }
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
-ts_status scratch_address(double** out) {
+// Device address of the scratch array on the current device, looked up with
+// that device current: on the first call on the device, and again on every
+// call whose stream is not capturing (a device reset may have moved the array);
+// a capturing stream uses the address cached by an earlier call.
+ts_status scratch_address(cudaStream_t st, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(TS_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(TS_ERR_UNSUPPORTED, "device index too large");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess)
+    return noalloc_fail(TS_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (!g_noalloc_ptr[dev] || cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
@@ -195,7 +204,8 @@ ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0
       d.NTheta < 2 || d.NTheta > 64 || d.NPhi < 2 || d.NPhi > 64 || (d.Nphi % 2) ||
       (d.NTheta % 2) || (d.NPhi % 2))
     return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: unsupported grid sizes");
-  if (d.precision != TS_FP64 && d.precision != TS_FP32 && d.precision != TS_FP32_R64)
+  if (d.precision != TS_FP64 && d.precision != TS_FP32 && d.precision != TS_FP32_R64 &&
+      d.precision != TS_TF32X3 && d.precision != TS_BF16X3)
     return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: unknown precision");
   if (d.radial != TS_RADIAL_CHEBYSHEV)
     return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: Chebyshev radial grids only");
@@ -208,10 +218,10 @@ ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0
                             " doubles of scratch; the static maximum is " +
                             std::to_string(kNoAllocScratch) +
                             " (groups*Nr*Ntheta*Nphi + 2*groups*Ntheta*Nphi)");
-  double* scratch = nullptr;
-  ts_status s = scratch_address(&scratch);
-  if (s != TS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  ts_status s = scratch_address(st, &scratch);
+  if (s != TS_OK) return s;
   const int wpb = kThreads / 32;
   const unsigned blocks = (unsigned)((z.nblk + wpb - 1) / wpb);
   if (d.precision == TS_FP64)

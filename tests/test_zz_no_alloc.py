@@ -29,10 +29,26 @@ def _outputs(shape, G):
     return z(*shape[:4]), z(3, *shape[:4]), z(G), z(G), z(G)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-12)])
-def test_noalloc_moments_match_ts_moments_twice(precision, tol):
-    dims = (0.2, 1.0, 11, 7, 10, 6, 12)
-    G = 3
+CASES = [
+    # (dims, groups, precision): odd N_r (even number of Chebyshev intervals), the float
+    # precisions, an even N_r (the Clenshaw-Curtis weights' odd-N branch), 64 direction
+    # nodes per axis (the kernel's whole direction tables), and a grid whose scratch need
+    # groups*Nr*Nt*Np + 2*groups*Nt*Np is exactly the static maximum 2^21
+    ((0.2, 1.0, 11, 7, 10, 6, 12), 3, 0),
+    ((0.2, 1.0, 11, 7, 10, 6, 12), 3, 1),
+    ((0.2, 1.0, 11, 7, 10, 6, 12), 2, 2),
+    ((0.2, 1.0, 11, 7, 10, 6, 12), 2, 3),
+    ((0.2, 1.0, 12, 5, 6, 8, 8), 2, 0),
+    ((0.2, 1.0, 5, 2, 2, 64, 64), 1, 0),
+    ((0.2, 1.0, 126, 64, 64, 2, 2), 4, 0),
+]
+
+
+@pytest.mark.parametrize("dims,G,precision", CASES)
+def test_noalloc_moments_match_ts_moments_twice(dims, G, precision):
+    tol = 1e-12
+    if dims[2] == 126:
+        assert G * dims[2] * dims[3] * dims[4] + 2 * G * dims[3] * dims[4] == 1 << 21
     og, gg = pair(*dims, G=G, precision=precision)
     dt = torch.float64 if precision == 0 else torch.float32
     for call, seed in enumerate((21, 22)):
