@@ -210,9 +210,16 @@ ts_status ts_step_profile(ts_grid* grid, void* F, double dt, int nsteps, double*
                           int* launches_host, void* stream);
 
 /* As ts_step, with F in HOST memory: copies F to the device, steps, copies
- * back, and synchronizes `stream` before returning (for TS_AB2 the history
- * follows the host pointer: stepping another F_host restarts it). F_host should be pinned
- * for full copy bandwidth. */
+ * back, and synchronizes `stream` before returning. Float grids with more than
+ * one group (and a scheme other than TS_AB2) are pipelined in two chunks of
+ * groups: chunk k is stepped on `stream` while chunk k+1 is copied in and chunk
+ * k-1 copied out on two copy streams of the grid (one cudaMemcpyAsync per chunk
+ * and direction), so only the first chunk's copy in and the last chunk's copy
+ * out add to the step's time; the copies are ordered after earlier work on
+ * `stream`. Double grids (whose step time dwarfs the copies) and TS_AB2 (whose
+ * history covers every group, and follows the host pointer: stepping another
+ * F_host restarts it) copy the whole field each way. Allocates a device field
+ * on first use. F_host should be pinned for full copy bandwidth. */
 ts_status ts_step_host(ts_grid* grid, void* F_host, double dt, int nsteps, void* stream);
 
 /* One stage derivative K = Tau(-L_sph F + CT) (the right-hand side of
@@ -239,6 +246,21 @@ ts_status ts_adjoint_step(ts_grid* grid, const void* F_n, void* lambda,
  * sum w * F[g][Nr-1][...]. */
 ts_status ts_flux_weights(ts_grid* grid, double* w, void* stream);
 
+/* Outgoing radial flux through R2 per group (Eq. Flux, App. A):
+ *   J_R2[g] = sum_{j,l,k,m} w[j][l][k][m] F[g][Nr-1][j][l][k][m]
+ * with the weights of ts_flux_weights (the quadrature of ts_moments restricted
+ * to the r = R2 slab; equal to ts_moments' J_R2 up to summation order).
+ * F: the grid's element type; J_R2: [G] device doubles. Reads only the r = R2
+ * slab. Deterministic (fixed summation order). Uses a small scratch buffer of
+ * the grid: calls on one grid must not overlap. */
+ts_status ts_outgoing_flux(ts_grid* grid, const void* F, double* J_R2, void* stream);
+
+/* Gradient of sum_g gJ[g] J_R2[g] with respect to F (the adjoint seed of the
+ * outgoing-flux objective): writes lambda[g][i][...] = gJ[g] w[...] for
+ * i = Nr-1 and 0 for every other radial node. gJ: [G] device doubles; lambda:
+ * the grid's element type and the layout of F (overwritten entirely). */
+ts_status ts_outgoing_flux_adjoint(ts_grid* grid, const double* gJ, void* lambda, void* stream);
+
 /* Angular moments and balances (App. A and App. C), all double:
  *   F0[G][Nr][Nth][Nph] = (1/4pi) int F dOmega,
  *   F1[3][G][Nr][Nth][Nph] = (1/4pi) int F omega dOmega (Cartesian x,y,z,
@@ -257,7 +279,8 @@ ts_status ts_moments(ts_grid* grid, const void* F, double* F0, double* F1, doubl
  * counterpart; this is a property of the library only.
  *  - Takes the grid description instead of a ts_grid (creating a grid
  *    allocates) and computes its node and quadrature tables in the kernel.
- *    Precision selects the element type of F (double or float).
+ *    Precision selects the element type of F (double for TS_FP64, float for
+ *    every other precision).
  *  - Allocates nothing: its per-block partial sums live in a static device
  *    array of 2^21 doubles (16 MiB) that every GPU loading the library holds
  *    until the process exits. Grids needing more than
@@ -265,7 +288,9 @@ ts_status ts_moments(ts_grid* grid, const void* F, double* F0, double* F1, doubl
  *    rejected with TS_ERR_UNSUPPORTED (text in ts_last_error()).
  *  - The first call on a device (with that device current) looks up the
  *    array's device address and caches it; make that first call before any
- *    stream capture.
+ *    stream capture. Calls on a stream that is not capturing look it up again,
+ *    so a device reset that moves the array is followed; calls during a
+ *    capture use the cached address.
  *  - Every call shares the array and it keeps the last call's contents. Each
  *    call writes every slot it reads, so nothing needs clearing, but calls
  *    whose kernels overlap on the GPU (other streams, other host threads)
@@ -322,6 +347,62 @@ ts_status ts_batch_grid(ts_batch* batch, int problem, ts_grid** grid);
 ts_status ts_batch_step(ts_batch* batch, void* const* F_host_array, const double* dt_host,
                         int nsteps, void* stream);
 
+/* ------------------------------------------------- conservative 2-D variant
+ * The spherically symmetric problem F(r, Theta) of App. B written for the
+ * conservative variable Fhat = r^2 sin(Theta) F (App. B, Eq. flux), with
+ * coherent scattering of kernel (kappa_s/4pi)(1 + c (mu^2 - 1/3)):
+ *   dFhat/dt = - cos Th dFhat/dr + (1/r) (sin Th dFhat/dTh + cos Th P Fhat)
+ *              + kappa_s [ - Fhat + sin Th int_0^pi k_c(Th, Th') Fhat(Th') dTh' ],
+ *   k_c = (1/2)(1 + c (cos^2 Th cos^2 Th' + (1/2) sin^2 Th sin^2 Th' - 1/3))
+ * (Eq. speccons; c = 3/4 is the Thomson form printed there, c = 0 isotropic
+ * scattering). r: Chebyshev-Gauss-Lobatto nodes and differentiation; Theta:
+ * the pole-free nodes pi (k+1/2)/NTheta with Fhat odd on the doubled circle;
+ * P drops the Nyquist sine mode of Fhat so that the Theta term integrates to
+ * zero exactly; Theta' integrals by Fejer's first rule on Fhat / sin Th'. With
+ * N = 8 pi^2 int dr int dTh Fhat and J_R = 8 pi^2 int cos Th Fhat(R, Th) dTh
+ * (Eqs. Npho, Flux with the theta, phi, Phi integrals done), the discrete
+ * operator without boundary rows satisfies dN/dt + J_R2 - J_R1 = 0 (Eq. Cons)
+ * to rounding for every Fhat. Time: classical RK4; boundaries: Tau inflow rows
+ * (TS_BC_TAU_INFLOW: the rate at each direction's inflow node is zero) or none.
+ * FP64. Fields: Fhat[P][Nr][NTheta] (device doubles), P independent problems
+ * stepped together, each by one CTA holding its whole grid in shared memory
+ * (TS_ERR_UNSUPPORTED if a problem's working set exceeds it). The paper's own
+ * 2-D time scheme (implicit radial update, finite-difference edge zones) is not
+ * this one. */
+typedef struct {
+  double R1, R2;        /* shell radii, 0 < R1 < R2 */
+  int Nr, NTheta;       /* 3 <= Nr <= 129; NTheta even, 2..64 */
+  int problems;         /* independent problems */
+  double scatter_c;     /* kernel parameter c */
+  int bc;               /* ts_bc */
+} ts_cons2d_desc;
+
+typedef struct ts_cons2d ts_cons2d;   /* opaque, library-owned */
+
+/* Create: node and differentiation tables (closed forms), uploaded; kappa_s and
+ * inflow data zero until set. Synchronous. */
+ts_status ts_cons2d_create(const ts_cons2d_desc* desc, ts_cons2d** out);
+ts_status ts_cons2d_destroy(ts_cons2d* grid);
+/* Host copies of r[Nr] (ascending) and Theta[NTheta]; either may be NULL. */
+ts_status ts_cons2d_nodes(const ts_cons2d* grid, double* r_host, double* Theta_host);
+/* kappa_s[P][Nr] (device), inflow Fhat data inflow_R1[P][NTheta/2] at R1 for the
+ * directions cos Th > 0 and inflow_R2[P][NTheta/2] at R2 for cos Th < 0
+ * (device); NULL means zero. Copied on `stream`. */
+ts_status ts_cons2d_set_coeffs(ts_cons2d* grid, const double* kappa_s, const double* inflow_R1,
+                               const double* inflow_R2, void* stream);
+/* Fhat = inflow data at the inflow nodes. */
+ts_status ts_cons2d_apply_inflow(ts_cons2d* grid, double* Fhat, void* stream);
+/* K = the right-hand side (with the grid's boundary rows) of Fhat. */
+ts_status ts_cons2d_rhs(ts_cons2d* grid, const double* Fhat, double* K, void* stream);
+/* nsteps classical RK4 steps of size dt, in place, every stage and step in
+ * shared memory (one launch per call). */
+ts_status ts_cons2d_step(ts_cons2d* grid, double* Fhat, double dt, int nsteps, void* stream);
+/* Per problem p: NJ[3p..3p+2] = N, J_R1, J_R2 of Fhat, and residual[p] =
+ * dN/dt + J_R2 - J_R1 of the operator without boundary rows (zero to rounding:
+ * the discrete form of Eq. Cons). Device doubles. */
+ts_status ts_cons2d_balance(ts_cons2d* grid, const double* Fhat, double* NJ, double* residual,
+                            void* stream);
+
 /* Measured fused multiply-add rate of the current device in TFLOP/s (2 flops
  * per FMA), for precision TS_FP64 or TS_FP32 (else TS_ERR_UNSUPPORTED): a loop
  * of 8 independent FMA chains per thread, 8 CTAs of 256 threads per SM, best
@@ -330,6 +411,35 @@ ts_status ts_batch_step(ts_batch* batch, void* const* F_host_array, const double
  * paper has no counterpart: this is the measured denominator of the roofline of
  * the FP64 passes, which are bound by the FP64 arithmetic units. */
 ts_status ts_probe_fma_rate(int precision, double* tflops, void* stream);
+
+/* Time-step limit of the grid's explicit stage operator (the Courant limits of
+ * Sect. 5.4, every axis included, taken from the discrete operator itself):
+ * power iteration on the linear part A x = K(x) - K(0) of the stage derivative
+ * K of ts_rhs (the grid's coefficients, scattering kernel and boundary rows),
+ * from the start field x0 (device; the grid's element type and the layout of
+ * F; any field with a component along the dominant eigenvectors, e.g. seeded
+ * random numbers; not modified): x <- A x / |A x| for `iters` iterations
+ * (2..100000); rho = the geometric mean of the growth factors |A x| / |x| over
+ * the last half of them (Gelfand's formula: it settles even when the largest
+ * eigenvalues are a complex pair). dt_max = 2.6 / rho keeps dt A inside
+ * classical RK4's stability region (which reaches 2 sqrt 2 on the imaginary
+ * axis and 2.79 on the negative real axis). Host outputs, either may be NULL.
+ * Overwrites the grid's workspace and restarts the TS_AB2 history; allocates a
+ * small scratch buffer on first use; synchronizes `stream`. */
+ts_status ts_stable_dt(ts_grid* grid, const void* x0, int iters, double* rho_host,
+                       double* dt_max_host, void* stream);
+
+/* Failure-detection hook: bound the tensor-core radial pass's (TS_TF32X3,
+ * TS_BF16X3) wait for its operand copy to `operand_wait_iterations` spins of
+ * mbarrier.try_wait. 0 restores the default bound (2^24); a negative value
+ * makes that wait give up at once, so that every CTA of the pass takes its
+ * timeout path: it issues no products, latches the grid's error flag
+ * (ts_sync_status then returns TS_ERR_TIMEOUT), waits with the full bound for
+ * its own copy to land, frees its tensor memory and returns; that pass's
+ * outputs are not written. Only this wait changes: the waits that drain work
+ * in flight keep their full bound. Host-side; takes effect at the next
+ * launch. (No counterpart in the paper: a test hook of the bounded waits.) */
+ts_status ts_set_wait_limit(ts_grid* grid, long long operand_wait_iterations);
 
 /* Status of device-side checks latched since the last call (bounded waits).
  * Synchronizes `stream`. */

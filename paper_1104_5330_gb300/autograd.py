@@ -10,7 +10,8 @@ back (ts_adjoint_step), so memory is O(sqrt(n)) fields and the forward is
 recomputed once.
 
 ``outgoing_flux(grid, F)`` is the radial flux through R2 per group (Eq. Flux,
-App. A) with the library's quadrature weights (ts_flux_weights).
+App. A), evaluated by the library (ts_outgoing_flux) with the adjoint seed of
+ts_outgoing_flux_adjoint as its backward.
 
 All tensors live on the grid's device; kappa, eta, kappa_s are float64
 [G][Nr][Ntheta][Nphi]; F has the grid's element type. The grid's scattering
@@ -77,7 +78,26 @@ def transport_steps(grid, F0, kappa, eta, kappa_s=None, dt=None, nsteps=1, inflo
                                 int(nsteps), segment)
 
 
+class OutgoingFlux(torch.autograd.Function):
+    """J_R2 per group through the library (ts_outgoing_flux); its backward is
+    the library's adjoint seed (ts_outgoing_flux_adjoint)."""
+
+    @staticmethod
+    def forward(ctx, F, grid):
+        ctx.grid = grid
+        J = torch.empty(grid.shape[0], dtype=torch.float64, device=F.device)
+        _ts.ts_outgoing_flux(grid.handle, F.detach().contiguous(), J)
+        return J
+
+    @staticmethod
+    def backward(ctx, gJ):
+        grid = ctx.grid
+        lam = torch.empty(grid.shape, dtype=grid.dtype, device=gJ.device)
+        _ts.ts_outgoing_flux_adjoint(grid.handle, gJ.detach().to(torch.float64).contiguous(), lam)
+        return lam, None
+
+
 def outgoing_flux(grid, F):
-    """J_R2 per group: R2^2 int sin(th) dth dph int sin(Th) cos(Th) dTh dPh F(R2) (Eq. Flux)."""
-    w = grid.flux_weights().to(F.dtype)
-    return torch.einsum("gjlkm,jlkm->g", F[:, -1], w)
+    """J_R2 per group, R2^2 int sin(th) dth dph int sin(Th) cos(Th) dTh dPh F(R2)
+    (Eq. Flux), float64 [G], differentiable in F."""
+    return OutgoingFlux.apply(F, grid)

@@ -14,6 +14,7 @@
 //    Gauss-Lobatto nodes from their cosine-sum closed forms.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -488,6 +489,10 @@ HostTables build_tables(const ts_grid_desc& g) {
 }  // namespace
 
 void ts::set_last_error(const std::string& msg) { g_err = msg; }
+ts::Vec ts::cheb_diff_matrix(int Nr, double R1, double R2) { return cheb_diff(Nr, R1, R2); }
+ts::Vec ts::fourier_diff_matrix(int M) { return fourier_diff(M); }
+ts::Vec ts::fejer_weights(int N) { return fejer(N); }
+ts::Vec ts::clenshaw_curtis_weights(int Nr) { return clenshaw_curtis(Nr); }
 ts_status ts::fail_status(ts_status s, const std::string& msg) { return fail(s, msg); }
 ts_status ts::cuda_status(cudaError_t e, const char* where) { return cuda_fail(e, where); }
 
@@ -512,7 +517,30 @@ ts::Problem make_problem(const ts_grid* g) {
                                           : ts::TC_NONE;
   p.tcb16 = g->tcb16;
   p.err = g->err;
+  p.wait_operand = g->wait_operand > 0 ? g->wait_operand : ts::kDefaultWaitIters;
+  if (g->wait_operand < 0) p.wait_operand = 0;
+  p.plane_store = 0;
+  if (g->sn > 0) {   // one slice of groups: every per-group pointer offset to group s0
+    const long long per = g->d.nblk / g->d.G;
+    const long long infl = (long long)g->d.Nt * g->d.Np * (g->d.NT / 2) * g->d.NP;
+    p.d.G = g->sn;
+    p.d.total = (long long)g->sn * g->d.S_g;
+    p.d.nblk = per * g->sn;
+    p.kap += g->s0 * per;
+    p.eta += g->s0 * per;
+    p.kaps += g->s0 * per;
+    if (p.scb) p.scb += g->s0 * per;
+    if (p.scc) p.scc += g->s0 * per;
+    p.gR1 = static_cast<const char*>(p.gR1) + g->s0 * infl * (long long)g->es;
+    p.gR2 = static_cast<const char*>(p.gR2) + g->s0 * infl * (long long)g->es;
+  }
   return p;
+}
+
+// A workspace field of the grid at the current group slice.
+template <typename T>
+T* work(const ts_grid* g, void* base) {
+  return static_cast<T*>(base) + (g->sn > 0 ? g->s0 * g->d.S_g : 0);
 }
 
 size_t field_bytes(const ts_grid* g) { return (size_t)g->d.total * g->es; }
@@ -573,19 +601,40 @@ cudaError_t radial_pass(const ts_grid* g, const ts::Problem& p, const Tables<C>&
   return Launch<T, C>::radial(p, t, g->t64.Dr, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, st);
 }
 
+// One stage derivative of `in` and the radial pass's output `mode`: the angular,
+// plane and radial passes, or -- float grids with a fused plan -- the plane
+// pass writing its terms into the grid's K and the fused angular + radial pass.
+template <typename T, typename C>
+cudaError_t stage_passes(ts_grid* g, const ts::Problem& p, const Tables<C>& t, const T* in, T* K,
+                         C sgn, bool collision, bool tau, int mode, T* F, T* Acc, T* Uout,
+                         T* out, double dt, cudaStream_t st, Profiler* prof) {
+  cudaError_t e = cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    if (p.tp.fnb > 0) {
+      ts::Problem pp = p;
+      pp.plane_store = 1;
+      TS_TIMED(prof, 1, (Launch<T, C>::plane(pp, t, in, K, sgn, st)));
+      TS_TIMED(prof, 2, (ts::launch_fused(p, t, g->t64.Dr, in, K, sgn, collision, tau, mode, F,
+                                          Acc, Uout, out, dt, st)));
+      return e;
+    }
+  }
+  TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, sgn, collision, st)));
+  TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, in, K, sgn, st)));
+  TS_TIMED(prof, 2, (radial_pass<T, C>(g, p, t, in, K, sgn, tau, mode, F, Acc, Uout, out, dt,
+                                       st)));
+  return e;
+}
+
 template <typename T, typename C>
 cudaError_t run_stage(ts_grid* g, const Tables<C>& t, const T* in, T* F, int s, bool collision,
                       double dt, cudaStream_t st, Profiler* prof) {
   const ts::Problem p = make_problem(g);
-  T* K = static_cast<T*>(g->K);
-  T* U = static_cast<T*>(g->U);
-  T* Acc = static_cast<T*>(g->Acc);
-  cudaError_t e = cudaSuccess;
-  TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, (C)-1, collision, st)));
-  TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, in, K, (C)-1, st)));
-  TS_TIMED(prof, 2, (radial_pass<T, C>(g, p, t, in, K, (C)-1, g->desc.bc == TS_BC_TAU_INFLOW,
-                                       ts::RAD_STAGE0 + s, F, Acc, U, nullptr, dt, st)));
-  return e;
+  T* K = work<T>(g, g->K);
+  T* U = work<T>(g, g->U);
+  T* Acc = work<T>(g, g->Acc);
+  return stage_passes<T, C>(g, p, t, in, K, (C)-1, collision, g->desc.bc == TS_BC_TAU_INFLOW,
+                            ts::RAD_STAGE0 + s, F, Acc, U, nullptr, dt, st, prof);
 }
 
 template <typename T, typename C>
@@ -599,15 +648,13 @@ cudaError_t run_steps(ts_grid* g, const Tables<C>& t, T* F, double dt, int nstep
     // Adams-Bashforth update in place, keeping K in Acc for the next step
     if (g->hist_F != (key ? key : F)) g->hist = false;
     g->hist_F = key ? key : F;
-    T* K = static_cast<T*>(g->K);
-    T* Acc = static_cast<T*>(g->Acc);
+    T* K = work<T>(g, g->K);
+    T* Acc = work<T>(g, g->Acc);
     const bool tau = g->desc.bc == TS_BC_TAU_INFLOW;
     for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, F, K, (C)-1, true, st)));
-      TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, F, K, (C)-1, st)));
-      TS_TIMED(prof, 2, (radial_pass<T, C>(g, p, t, F, K, (C)-1, tau,
-                                           g->hist ? ts::RAD_AB2 : ts::RAD_AB2_START, F, Acc,
-                                           nullptr, nullptr, dt, st)));
+      e = stage_passes<T, C>(g, p, t, F, K, (C)-1, true, tau,
+                             g->hist ? ts::RAD_AB2 : ts::RAD_AB2_START, F, Acc, nullptr, nullptr,
+                             dt, st, prof);
       if (e == cudaSuccess) g->hist = true;
       if (g->desc.filter_on) TS_TIMED(prof, 3, (Launch<T, C>::filter(p, t, F, K, st)));
     }
@@ -616,9 +663,9 @@ cudaError_t run_steps(ts_grid* g, const Tables<C>& t, T* F, double dt, int nstep
   }
   for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
     for (int s = 0; s < 4 && e == cudaSuccess; ++s)
-      e = run_stage<T, C>(g, t, s == 0 ? F : static_cast<T*>(g->U), F, s, !split, dt, st, prof);
+      e = run_stage<T, C>(g, t, s == 0 ? F : work<T>(g, g->U), F, s, !split, dt, st, prof);
     if (split) TS_TIMED(prof, 3, (Launch<T, C>::implicit_collision(p, t, F, dt, st)));
-    if (g->desc.filter_on) TS_TIMED(prof, 3, (Launch<T, C>::filter(p, t, F, static_cast<T*>(g->K), st)));
+    if (g->desc.filter_on) TS_TIMED(prof, 3, (Launch<T, C>::filter(p, t, F, work<T>(g, g->K), st)));
   }
   return e;
 }
@@ -628,12 +675,9 @@ cudaError_t run_rhs(ts_grid* g, const Tables<C>& t, const T* F, T* K, bool liouv
                     cudaStream_t st) {
   const ts::Problem p = make_problem(g);
   const C sgn = liouville_only ? (C)1 : (C)-1;
-  cudaError_t e = Launch<T, C>::angular(p, t, F, K, sgn, !liouville_only, st);
-  if (e == cudaSuccess) e = Launch<T, C>::plane(p, t, F, K, sgn, st);
-  if (e == cudaSuccess)
-    e = radial_pass<T, C>(g, p, t, F, K, sgn, !liouville_only && g->desc.bc == TS_BC_TAU_INFLOW,
-                          ts::RAD_RHS, nullptr, nullptr, nullptr, K, 0.0, st);
-  return e;
+  return stage_passes<T, C>(g, p, t, F, K, sgn, !liouville_only,
+                            !liouville_only && g->desc.bc == TS_BC_TAU_INFLOW, ts::RAD_RHS,
+                            nullptr, nullptr, nullptr, K, 0.0, st, nullptr);
 }
 
 template <typename T, typename C>
@@ -693,6 +737,95 @@ ts_status check_F(const ts_grid* g, const void* F) {
 
 }  // namespace
 
+namespace {
+
+// Power iteration of ts_stable_dt. Partial sums of squares of (y - y0) per
+// block (fixed grid, deterministic order), written back into y.
+constexpr int kPiBlocks = 304, kPiThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kPiThreads)
+k_pi_sub_norm(T* y, const T* y0, long long n, double* part) {
+  __shared__ double red[kPiThreads];
+  double a = 0.0;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
+       x += (long long)gridDim.x * blockDim.x) {
+    const double v = y0 ? (double)y[x] - (double)y0[x] : (double)y[x];
+    if (y0) y[x] = (T)v;
+    a = fma(v, v, a);
+  }
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// norm = sqrt(sum of the partials); logs[it] = log(norm) (it >= 0)
+__global__ void k_pi_finish(const double* part, int np, double* norm, double* logs, int it) {
+  __shared__ double red[kPiThreads];
+  double a = 0.0;
+  for (int x = threadIdx.x; x < np; x += blockDim.x) a += part[x];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *norm = sqrt(red[0]);
+    if (it >= 0) logs[it] = log(*norm);
+  }
+}
+
+template <typename T>
+__global__ void k_pi_scale(const T* y, T* x, long long n, const double* norm) {
+  const double s = 1.0 / *norm;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = (T)((double)y[i] * s);
+}
+
+template <typename T, typename C>
+cudaError_t power_iteration(ts_grid* g, const Tables<C>& t, const T* x0, int iters,
+                            std::vector<double>& logs, cudaStream_t st) {
+  const long long n = g->d.total;
+  T* x = static_cast<T*>(g->U);
+  T* y = static_cast<T*>(g->K);
+  T* y0 = static_cast<T*>(g->Acc);
+  double* part = g->piw;
+  double* norm = g->piw + kPiBlocks;
+  double* lg = g->piw + kPiBlocks + 1;
+  // y0 = K(0): the affine part (emissivity, inflow rows)
+  cudaError_t e = cudaMemsetAsync(x, 0, (size_t)n * sizeof(T), st);
+  if (e == cudaSuccess) e = run_rhs<T, C>(g, t, x, y0, false, st);
+  // x = x0 / |x0|
+  if (e == cudaSuccess) {
+    k_pi_sub_norm<T><<<kPiBlocks, kPiThreads, 0, st>>>(const_cast<T*>(x0), nullptr, n, part);
+    k_pi_finish<<<1, kPiThreads, 0, st>>>(part, kPiBlocks, norm, lg, -1);
+    k_pi_scale<T><<<kPiBlocks, kPiThreads, 0, st>>>(x0, x, n, norm);
+    e = cudaGetLastError();
+  }
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    e = run_rhs<T, C>(g, t, x, y, false, st);                // y = K(x)
+    if (e != cudaSuccess) break;
+    k_pi_sub_norm<T><<<kPiBlocks, kPiThreads, 0, st>>>(y, y0, n, part);   // y = K(x) - K(0)
+    k_pi_finish<<<1, kPiThreads, 0, st>>>(part, kPiBlocks, norm, lg, it);
+    k_pi_scale<T><<<kPiBlocks, kPiThreads, 0, st>>>(y, x, n, norm);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    logs.assign(iters, 0.0);
+    e = cudaMemcpyAsync(logs.data(), lg, iters * sizeof(double), cudaMemcpyDeviceToHost, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* ts_last_error(void) { return g_err.c_str(); }
@@ -743,6 +876,15 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
     const char* gen = std::getenv("TS_GENERIC_PASSES");  // 1: plain passes only (testing)
     G->tp.rb = (gen && gen[0] == '1') ? 0 : ts::rb_mask(d, (int)es, g.precision == TS_FP32_R64 ? 2 : 0);
     if (g.radial == TS_RADIAL_UPWIND_FD) G->tp.rb &= ~4;   // no even/odd radial form
+    // fused angular + radial pass: float grids with the even/odd angular and radial
+    // forms (not the tensor-core radial precisions) whose tile fits shared memory
+    // (TS_FUSED=1 selects it; its contractions are not yet faster than the three
+    // passes', so the three-pass form stays the default)
+    const char* fz = std::getenv("TS_FUSED");
+    const bool tc = g.precision == TS_TF32X3 || g.precision == TS_BF16X3;
+    const bool want = es == 4 && !tc && (G->tp.rb & 5) == 5 && fz && fz[0] == '1';
+    if (!want || !ts::fused_plan(d, g.precision == TS_FP32_R64 ? 2 : 0, &G->tp.fnb, &G->tp.fnbuf))
+      G->tp.fnb = G->tp.fnbuf = 0;
   }
 
   cudaError_t e = upload_tables<double>(G->h, &G->tab64, &G->t64);
@@ -762,9 +904,15 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   const size_t sizes[] = {ncoef, ncoef, ncoef, ninfl, ninfl, nf, nf, nf,
                           (size_t)g.Nr * 8, (size_t)g.Ntheta * 8, ncoef,
                           (size_t)g.groups * 2 * g.Ntheta * g.Nphi * 8, sizeof(int)};
+  // TS_POISON_WORKSPACE=1 (testing): the workspace fields U, K, Acc start as
+  // NaN (all bits set) instead of zero, so that a read of a workspace element
+  // no pass has written shows up as NaN in the result
+  const char* poison = std::getenv("TS_POISON_WORKSPACE");
+  const bool nan_ws = poison && poison[0] == '1';
   for (int b = 0; b < 13 && e == cudaSuccess; ++b) {
     e = cudaMalloc(bufs[b], sizes[b]);
-    if (e == cudaSuccess) e = cudaMemset(*bufs[b], 0, sizes[b]);
+    const bool ws = b >= 5 && b <= 7;
+    if (e == cudaSuccess) e = cudaMemset(*bufs[b], ws && nan_ws ? 0xFF : 0, sizes[b]);
   }
   if (e == cudaSuccess) e = cudaMemcpy(G->wr, G->h.wr.data(), g.Nr * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
@@ -789,6 +937,10 @@ ts_status ts_destroy_grid(ts_grid* g) {
     if (p) cudaFree(p);
   for (void* p : g->adj)
     if (p) cudaFree(p);
+  if (g->piw) cudaFree(g->piw);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  if (g->cs_in) cudaStreamDestroy(g->cs_in);
+  if (g->cs_out) cudaStreamDestroy(g->cs_out);
   delete g;
   return TS_OK;
 }
@@ -935,6 +1087,8 @@ ts_status ts_step_profile(ts_grid* g, void* F, double dt, int nsteps, double* pa
 ts_status ts_step_host(ts_grid* g, void* F_host, double dt, int nsteps, void* stream) {
   ts_status s = check_F(g, F_host);
   if (s != TS_OK) return s;
+  if (!std::isfinite(dt) || nsteps < 0) return fail(TS_ERR_ARG, "need finite dt, nsteps >= 0");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nb = field_bytes(g);
   if (!g->io) {
@@ -945,13 +1099,74 @@ ts_status ts_step_host(ts_grid* g, void* F_host, double dt, int nsteps, void* st
       return fail(TS_ERR_OOM, "ts_step_host: device buffer allocation failed");
     }
   }
-  cudaError_t e = cudaMemcpyAsync(g->io, F_host, nb, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "ts_step_host (to device)");
-  s = step_device(g, g->io, dt, nsteps, st, F_host);
-  if (s != TS_OK) return s;
-  e = cudaMemcpyAsync(F_host, g->io, nb, cudaMemcpyDeviceToHost, st);
+  const int G = g->d.G;
+  // Groups per pipelined chunk. Each chunk's step is a separate set of launches,
+  // so a chunk costs launch gaps and partial waves; on a GB300 (pinned copies at
+  // about 200 GB/s each way) two chunks paid off for the short float steps and
+  // none for the double ones, whose step time dwarfs the copies.
+  const int cg = g->es == 8 ? G : (G + 1) / 2;
+  const int nch = (G + cg - 1) / cg;
+  if (g->desc.scheme == TS_AB2 || nch == 1) {
+    // one copy each way around the whole step (the AB2 history covers all groups)
+    cudaError_t e = cudaMemcpyAsync(g->io, F_host, nb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ts_step_host (to device)");
+    s = step_device(g, g->io, dt, nsteps, st, F_host);
+    if (s != TS_OK) return s;
+    e = cudaMemcpyAsync(F_host, g->io, nb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step_host (to host)");
+  }
+  // Groups are independent: group k's steps run on `stream` while group k+1 is
+  // copied in on one copy stream and group k-1 copied out on another, so only
+  // the first group's copy in and the last group's copy out are exposed.
+  cudaError_t e = cudaSuccess;
+  if (!g->cs_in) e = cudaStreamCreateWithFlags(&g->cs_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !g->cs_out) e = cudaStreamCreateWithFlags(&g->cs_out, cudaStreamNonBlocking);
+  while (e == cudaSuccess && (int)g->ev.size() < 2 * nch + 2) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) g->ev.push_back(ev);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "ts_step_host (streams)");
+  cudaEvent_t* in_done = g->ev.data();            // [nch]: chunk k is on the device
+  cudaEvent_t* step_done = g->ev.data() + nch;    // [nch]: chunk k's steps are done
+  cudaEvent_t start = g->ev[2 * nch], out_done = g->ev[2 * nch + 1];
+  const size_t gb = (size_t)g->d.S_g * g->es;     // bytes of one group
+  char* dev = static_cast<char*>(g->io);
+  char* host = static_cast<char*>(F_host);
+  // the copies follow the caller's earlier work on `stream`
+  e = cudaEventRecord(start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cs_in, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cs_out, start, 0);
+  for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+    const int n = std::min(cg, G - k * cg);
+    const size_t off = (size_t)k * cg * gb;
+    e = cudaMemcpyAsync(dev + off, host + off, n * gb, cudaMemcpyHostToDevice, g->cs_in);
+    if (e == cudaSuccess) e = cudaEventRecord(in_done[k], g->cs_in);
+  }
+  g->hist = false;
+  for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+    const int n = std::min(cg, G - k * cg);
+    const size_t off = (size_t)k * cg * gb;
+    e = cudaStreamWaitEvent(st, in_done[k], 0);
+    if (e != cudaSuccess) break;
+    g->s0 = k * cg;
+    g->sn = n;
+    e = g->es == 8 ? run_steps<double, double>(g, g->t64, reinterpret_cast<double*>(dev + off),
+                                               dt, nsteps, st)
+                   : run_steps<float, float>(g, g->t32, reinterpret_cast<float*>(dev + off), dt,
+                                             nsteps, st);
+    g->s0 = g->sn = 0;
+    if (e == cudaSuccess) e = cudaEventRecord(step_done[k], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cs_out, step_done[k], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(host + off, dev + off, n * gb, cudaMemcpyDeviceToHost, g->cs_out);
+  }
+  g->s0 = g->sn = 0;
+  if (e == cudaSuccess) e = cudaEventRecord(out_done, g->cs_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, out_done, 0);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step_host (to host)");
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_step_host");
 }
 
 ts_status ts_rhs(ts_grid* g, const void* F, void* K, void* stream) {
@@ -987,8 +1202,11 @@ ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* gra
   if (g->desc.radial != TS_RADIAL_CHEBYSHEV)
     return fail(TS_ERR_UNSUPPORTED, "adjoint covers the Chebyshev radial grid");
   if (!g->adj[0]) {
+    const char* poison = std::getenv("TS_POISON_WORKSPACE");   // see ts_create_grid
     for (int a = 0; a < 7; ++a) {
       cudaError_t e = cudaMalloc(&g->adj[a], field_bytes(g));
+      if (e == cudaSuccess && poison && poison[0] == '1')
+        e = cudaMemset(g->adj[a], 0xFF, field_bytes(g));
       if (e != cudaSuccess) {
         for (int b = 0; b <= a; ++b) {
           if (g->adj[b]) cudaFree(g->adj[b]);
@@ -1026,6 +1244,50 @@ ts_status ts_moments(ts_grid* g, const void* F, double* F0, double* F1, double* 
       : Launch<float, float>::moments(p, g->t64, g->wr, g->wth, (const float*)F, F0, F1,
                                       g->partN, g->partJ, N, JR1, JR2, g->desc.R1, g->desc.R2, st);
   return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_moments");
+}
+
+ts_status ts_set_wait_limit(ts_grid* g, long long operand_wait_iterations) {
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  // 0 restores the default; a negative value makes the wait give up at once
+  g->wait_operand = operand_wait_iterations == 0 ? 0
+                    : operand_wait_iterations < 0 ? -1 : operand_wait_iterations;
+  ++g->gen;
+  return TS_OK;
+}
+
+ts_status ts_stable_dt(ts_grid* g, const void* x0, int iters, double* rho_host,
+                       double* dt_max_host, void* stream) {
+  ts_status s = check_F(g, x0);
+  if (s != TS_OK) return s;
+  if (iters < 2 || iters > 100000) return fail(TS_ERR_ARG, "ts_stable_dt: need 2 <= iters <= 100000");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
+  if (!g->piw || g->piw_n < iters) {
+    if (g->piw) cudaFree(g->piw);
+    g->piw = nullptr;
+    g->piw_n = 0;
+    cudaError_t e = cudaMalloc(&g->piw, (kPiBlocks + 1 + (size_t)iters) * sizeof(double));
+    if (e != cudaSuccess) {
+      g->piw = nullptr;
+      cudaGetLastError();
+      return fail(TS_ERR_OOM, "ts_stable_dt: scratch allocation failed");
+    }
+    g->piw_n = iters;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<double> logs;
+  cudaError_t e = g->es == 8
+      ? power_iteration<double, double>(g, g->t64, (const double*)x0, iters, logs, st)
+      : power_iteration<float, float>(g, g->t32, (const float*)x0, iters, logs, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ts_stable_dt");
+  double m = 0.0;
+  const int h = iters / 2;
+  for (int it = h; it < iters; ++it) m += logs[it];
+  const double rho = std::exp(m / (iters - h));
+  if (!std::isfinite(rho)) return fail(TS_ERR_ARG, "ts_stable_dt: start field gave no finite estimate");
+  if (rho_host) *rho_host = rho;
+  if (dt_max_host) *dt_max_host = rho > 0.0 ? 2.6 / rho : INFINITY;
+  g->hist = false;
+  return TS_OK;
 }
 
 ts_status ts_sync_status(ts_grid* g, void* stream) {

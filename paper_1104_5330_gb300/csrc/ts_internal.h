@@ -74,6 +74,9 @@ struct TileParams {
   // Bit mask of forward passes that use the register-blocked even/odd form
   // (1 angular, 2 plane, 4 radial); set from the grid's sizes.
   int rb = 0;
+  // Fused angular + radial pass (float grids whose tile fits shared memory):
+  // angular blocks per chunk and U staging buffers; fnb = 0: three passes.
+  int fnb = 0, fnbuf = 0;
 };
 
 // Output rows per thread of the register-blocked passes: angular 2 in float and
@@ -120,12 +123,18 @@ struct Problem {
   int tc;            // TcKind: radial pass on the tensor cores (float grids)
   const void* tcb16; // BF16x3: the three bf16 terms of D_r in the MMA's B layout
   int* err;          // device flag set by a bounded wait that ran out
+  long long wait_operand;  // bound (iterations) of the tensor-core pass's operand wait
+  int plane_store;         // 1: the plane pass writes K = its terms (fused stages), 0: adds
 };
 
 __host__ __device__ inline int kernel_form(const Problem& p, int collision) {
   if (!collision) return KF_ISO;
   return p.scc ? KF_QUADRATIC : p.scb ? KF_LINEAR : KF_ISO;
 }
+
+// Default bound (spin iterations) of the device-side waits of the tensor-core
+// radial pass.
+constexpr long long kDefaultWaitIters = 1LL << 24;
 
 // Operand forms of the tensor-core radial pass.
 enum TcKind { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2 };
@@ -134,6 +143,15 @@ enum TcKind { TC_NONE = 0, TC_TF32X3 = 1, TC_BF16X3 = 2 };
 cudaError_t launch_radial_tc(const Problem& p, const Tables<float>& t, const float* U,
                              const float* K, float sgn, bool tau, int mode, float* F, float* Acc,
                              float* Uout, float* out, double dt, cudaStream_t s);
+// Fused angular + radial pass of a stage (float grids; defined with the float
+// kernels in ts_f32.cu). fused_plan picks the chunk and staging-buffer counts
+// that fit shared memory (returns false if none does); launch_fused runs the
+// pass on the plane terms the plane pass wrote into Kp.
+bool fused_plan(const Dims& d, int n64, int* nb, int* nbuf);
+cudaError_t launch_fused(const Problem& p, const Tables<float>& t, const double* Dr64,
+                         const float* U, const float* Kp, float sgn, bool collision, bool tau,
+                         int mode, float* F, float* Acc, float* Uout, float* out, double dt,
+                         cudaStream_t s);
 // Radial pass of the hybrid grid (uniform r nodes, one-sided upwind differences;
 // `hold`: zero rate at the inflow nodes). Defined in ts_fd.cu.
 template <typename T, typename C>
@@ -208,6 +226,16 @@ struct HostTables {
 };
 
 ts_status fail_status(ts_status s, const std::string& msg);
+
+// Host tables shared by the grid types (closed forms, see ts_api.cu):
+// Chebyshev-Gauss-Lobatto differentiation matrix on [R1, R2] ([out][in]); the
+// periodic Fourier derivative on M equispaced nodes of a 2 pi circle (Nyquist
+// zeroed); Fejer's first rule for int_0^pi g(t) sin t dt on pi (k+1/2)/N;
+// Clenshaw-Curtis weights for int_{-1}^{1} on the Nr Gauss-Lobatto nodes.
+Vec cheb_diff_matrix(int Nr, double R1, double R2);
+Vec fourier_diff_matrix(int M);
+Vec fejer_weights(int N);
+Vec clenshaw_curtis_weights(int Nr);
 ts_status cuda_status(cudaError_t e, const char* where);
 
 }  // namespace ts
@@ -228,6 +256,8 @@ struct ts_grid {
   void *U = nullptr, *K = nullptr, *Acc = nullptr;
   void* adj[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double *wr = nullptr, *wth = nullptr, *partN = nullptr, *partJ = nullptr;
+  double* piw = nullptr;  // power iteration: partial sums, norms and their logs (ts_stable_dt)
+  int piw_n = 0;
   int* err = nullptr;    // device flag: a bounded device-side wait ran out
   void* io = nullptr;
   ts::TileParams tp{};   // tile shapes (0 = built-in heuristic); set by ts_autotune
@@ -239,6 +269,14 @@ struct ts_grid {
   unsigned gen = 0;      // bumped when the launch parameters change (batched steps re-upload)
   bool hist = false;     // TS_AB2: Acc holds K of the previous step of hist_F
   const void* hist_F = nullptr;
+  long long wait_operand = 0;  // 0: the default bound (ts_set_wait_limit)
+  // Group slice the launches cover (ts_step_host's per-group pipeline): groups
+  // s0 .. s0+sn-1, every pointer of the problem and the workspace offset to
+  // group s0; sn = 0: all groups.
+  int s0 = 0, sn = 0;
+  // Copy streams and per-group events of the pipelined ts_step_host.
+  cudaStream_t cs_in = nullptr, cs_out = nullptr;
+  std::vector<cudaEvent_t> ev;
 };
 
 namespace ts {

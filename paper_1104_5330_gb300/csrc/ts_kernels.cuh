@@ -199,7 +199,7 @@ __device__ __forceinline__ void plane_tile(const Problem& p, const Tables<C>& t,
     const C ath = sTk * t.cosP[m] * ir;
     const C aph = sTk * t.sinP[m] * ir * t.inv_sinth[j];
     const long long idx = base + (long long)j * d.S_j + (long long)l * d.S_l + m;
-    K[idx] = (T)((C)K[idx] + sgn * (ath * dth + aph * dph));
+    K[idx] = (T)((p.plane_store ? (C)0 : (C)K[idx]) + sgn * (ath * dth + aph * dph));
   }
 }
 

@@ -155,6 +155,21 @@ __host__ __device__ inline int rad_spec(const Dims& d) {
 // Shared layout: [PeT | PoT | QeT | QoT (NT/2 x NT/2 each) | MsPhT | MdPhT |
 //                 tile nb*S | folded halves nb*(S+8) | transposed halves
 //                 nb*(NP*UTP+8) | kAngScalars nb per-block scalars]
+// The angular blocks of one tile: block bb (< nbb) of the tile is the global
+// block b0 + bb * bs (consecutive blocks in the angular pass; the N_r blocks of
+// one (g, theta, phi) position, stride N_theta N_phi, in the fused pass).
+struct AngBlocks {
+  long long b0, bs;
+  int nbb;
+};
+__device__ __forceinline__ AngBlocks ang_blocks(const Dims& d, int nb, long long tile) {
+  AngBlocks a;
+  a.b0 = tile * nb;
+  a.bs = 1;
+  a.nbb = (int)min((long long)nb, d.nblk - a.b0);
+  return a;
+}
+
 template <typename C>
 __device__ __forceinline__ void angular_rb_mats(const Tables<C>& t, const Dims& d, C* sP, C* sQ,
                                                 C* sD) {
@@ -191,23 +206,23 @@ __device__ __forceinline__ void angular_rb_load(const Dims& d, const T* U, int n
 template <int NT_, int NP_, int KF, typename T, typename C>
 __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C>& t,
                                                 const C* su, C* sSD, C* uT, C* sc, int collision,
-                                                int nb, long long tile) {
+                                                int nb, AngBlocks ab) {
   const Dims& d = p.d;
   const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2, hT = NT / 2;
   const int UTP = ang_utp<C>(NT), H4 = hP / 4, SS = ang_ss(NT, NP), US = ang_us<C>(NT, NP);
   const int Q4 = hT * hP;   // one folded half
-  const long long b0 = tile * nb;
-  const int nbb = (int)min((long long)nb, d.nblk - b0);
+  const int nbb = ab.nbb;
   const bool aniso = KF >= KF_LINEAR && collision;
   const bool quad = KF >= KF_QUADRATIC && collision;
   for (int x = threadIdx.x; x < nbb; x += blockDim.x) {  // once per block
-    sc[nb + x] = (C)p.kap[b0 + x];
-    sc[2 * nb + x] = (C)p.eta[b0 + x];
-    sc[3 * nb + x] = (C)p.kaps[b0 + x];
-    if (aniso) sc[6 * nb + x] = p.scb ? (C)(p.kaps[b0 + x] * p.scb[b0 + x]) : (C)0;
-    if (quad) sc[10 * nb + x] = (C)(p.kaps[b0 + x] * p.scc[b0 + x]);
+    const long long bx = ab.b0 + x * ab.bs;
+    sc[nb + x] = (C)p.kap[bx];
+    sc[2 * nb + x] = (C)p.eta[bx];
+    sc[3 * nb + x] = (C)p.kaps[bx];
+    if (aniso) sc[6 * nb + x] = p.scb ? (C)(p.kaps[bx] * p.scb[bx]) : (C)0;
+    if (quad) sc[10 * nb + x] = (C)(p.kaps[bx] * p.scc[bx]);
     int g, i, j, l;
-    decode_block(d, b0 + x, g, i, j, l);
+    decode_block(d, bx, g, i, j, l);
     sc[4 * nb + x] = t.inv_r[i];
     sc[5 * nb + x] = t.cot_th[j];
   }
@@ -387,19 +402,20 @@ __device__ __forceinline__ void angular_rb_prep(const Problem& p, const Tables<C
 // Compute a prepared tile and write K. Reads sSD, uT, sc and the matrices.
 // KF: add the kernel's mu (and mu^2) terms (separate instantiations keep the
 // register allocation of the isotropic form unchanged).
+// Kt: the output of the tile's block 0 (block bb at Kt + bb S, global memory or
+// a shared-memory tile).
 template <int NT_, int NP_, int KF, typename T, typename C>
 __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Tables<C>& t,
                                                    const C* sSD, const C* uT, const C* sc,
                                                    const C* sP, const C* sQ, const C* sD,
-                                                   T* __restrict__ K, C sgn, int collision,
-                                                   int nb, long long tile) {
+                                                   T* __restrict__ Kt, C sgn, int collision,
+                                                   int nb, AngBlocks ab) {
   constexpr int RB = RBAng<C>::v, CB = 4;
   const Dims& d = p.d;
   const int NT = ctsz<NT_>(d.NT), NP = ctsz<NP_>(d.NP), S = NT * NP, hP = NP / 2, hT = NT / 2;
   const int UTP = ang_utp<C>(NT), SS = ang_ss(NT, NP), US = ang_us<C>(NT, NP);
   const int Q4 = hT * hP;
-  const long long b0 = tile * nb;
-  const int nbb = (int)min((long long)nb, d.nblk - b0);
+  const int nbb = ab.nbb;
   const int KR = hT / RB, PC = hP / CB;
   constexpr bool aniso = KF >= KF_LINEAR;
   constexpr bool quad = KF >= KF_QUADRATIC;
@@ -469,7 +485,6 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
         }
       }
     }
-    const long long blk = b0 + bb;
     const C ir = sc[4 * nb + bb], ct = sc[5 * nb + bb];
     const C J = sc[bb], kap = sc[nb + bb], eta = sc[2 * nb + bb], ks = sc[3 * nb + bb];
     const C src = eta + ks * J, kks = kap + ks;
@@ -524,7 +539,7 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
           o1v[c] = (T)v1;
           o2v[c] = (T)v2;
         }
-        T* out = K + blk * S + k * NP + p0;
+        T* out = Kt + (long long)bb * S + k * NP + p0;
         st4<T>(out, o1v);
         st4<T>(out + hP, o2v);
       }
@@ -565,7 +580,7 @@ __device__ __forceinline__ void angular_rb_compute(const Problem& p, const Table
         for (int r = 0; r < RB; ++r) {
           const int k = side ? NT - 1 - k0 - r : k0 + r;
           const C ct = t.cosT[k], st = t.sinT[k];
-          T* out = K + blk * S + k * NP + p0;
+          T* out = Kt + (long long)bb * S + k * NP + p0;
           volatile T* vout = out;
           T o1v[CB], o2v[CB];
 #pragma unroll
@@ -603,10 +618,11 @@ __device__ __forceinline__ void angular_tile_rb_form(const Problem& p, const Tab
   angular_rb_mats<C>(t, d, sP, sQ, sD);
   angular_rb_load<false, T, C>(d, U, nb, tile, su);
   __syncthreads();
-  angular_rb_prep<NT_, NP_, KF, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+  const AngBlocks ab = ang_blocks(d, nb, tile);
+  angular_rb_prep<NT_, NP_, KF, T, C>(p, t, su, sSD, uT, sc, collision, nb, ab);
   __syncthreads();
-  angular_rb_compute<NT_, NP_, KF, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision, nb,
-                                         tile);
+  angular_rb_compute<NT_, NP_, KF, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K + ab.b0 * S, sgn,
+                                         collision, nb, ab);
 }
 
 template <int NT_, int NP_, typename T, typename C>
@@ -651,13 +667,14 @@ k_angular_pp(Problem p, Tables<C> t, const T* __restrict__ U, T* __restrict__ K,
   for (; tile < ntiles; tile += gridDim.x) {
     cp_async_wait0();
     __syncthreads();   // this tile staged; the previous tile's compute is done
-    angular_rb_prep<NT_, NP_, KF, T, C>(p, t, su, sSD, uT, sc, collision, nb, tile);
+    const AngBlocks ab = ang_blocks(d, nb, tile);
+    angular_rb_prep<NT_, NP_, KF, T, C>(p, t, su, sSD, uT, sc, collision, nb, ab);
     __syncthreads();   // staging buffer free
     const long long next = tile + gridDim.x;
     if (next < ntiles) angular_rb_load<true, T, C>(d, U, nb, next, su);
     cp_async_commit();
-    angular_rb_compute<NT_, NP_, KF, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K, sgn, collision,
-                                           nb, tile);
+    angular_rb_compute<NT_, NP_, KF, T, C>(p, t, sSD, uT, sc, sP, sQ, sD, K + ab.b0 * S, sgn,
+                                           collision, nb, ab);
   }
   cp_async_wait0();
 }
@@ -793,9 +810,11 @@ __device__ __forceinline__ void plane_rb_body(const Problem& p, const Tables<C>&
       const C isn = t.inv_sinth[j];
       T* pa = K + base + (long long)j * d.S_j + (long long)l * d.S_l + mA;
       T* pb = K + base + (long long)j * d.S_j + (long long)lh * d.S_l + mB;
-      T ka[CB], kb[CB];
-      ld4<T>(pa, ka);
-      ld4<T>(pb, kb);
+      T ka[CB] = {0, 0, 0, 0}, kb[CB] = {0, 0, 0, 0};
+      if (!p.plane_store) {
+        ld4<T>(pa, ka);
+        ld4<T>(pb, kb);
+      }
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
         ka[cc] = (T)((C)ka[cc] + cA[cc] * (ps[r][cc] + qd[r][cc]) + sA[cc] * isn * da[r][cc]);
@@ -1085,10 +1104,15 @@ __device__ __forceinline__ void plane_sq_body(const Problem& p, const Tables<C>&
       T* p0 = K + base + (long long)j * d.S_j + (long long)l * d.S_l + kl * N + m0;
       T* p1 = p0 + (long long)hp * d.S_l;      // phi partner row l + N/2
       T k0a[CB], k0b[CB], k1a[CB], k1b[CB];
-      ldv<T, CB>(p0, k0a);
-      ldv<T, CB>(p0 + hp, k0b);
-      ldv<T, CB>(p1, k1a);
-      ldv<T, CB>(p1 + hp, k1b);
+      if (p.plane_store) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c) k0a[c] = k0b[c] = k1a[c] = k1b[c] = (T)0;
+      } else {
+        ldv<T, CB>(p0, k0a);
+        ldv<T, CB>(p0 + hp, k0b);
+        ldv<T, CB>(p1, k1a);
+        ldv<T, CB>(p1 + hp, k1b);
+      }
 #pragma unroll
       for (int c = 0; c < CB; ++c) {
         const C psA = aOA[c] + sg * aEA[c], qdA = bOA[c] + sg * bEA[c];   // x 2

@@ -31,7 +31,7 @@
 
 namespace ts {
 
-constexpr long long kWaitIters = 1LL << 24;
+constexpr long long kWaitIters = kDefaultWaitIters;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -52,8 +52,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  for (long long it = 0; it < kWaitIters; ++it)
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity,
+                                          long long iters = kWaitIters) {
+  for (long long it = 0; it < iters; ++it)
     if (mbar_try(addr, parity)) return true;
   return false;
 }
@@ -255,7 +256,9 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
   const uint32_t tmem = *tslot;
   bool ok = true;
   if (tid == 0) {
-    ok = mbar_wait(bar0, 0);
+    // the operand wait's bound is p.wait_operand (the default, or a shorter one
+    // set with ts_set_wait_limit to exercise the timeout path)
+    ok = mbar_wait(bar0, 0, p.wait_operand);
     if (ok) {
       const uint32_t idesc = KIND == TC_TF32X3 ? umma_idesc_tf32(128, sh.Npad)
                                                : umma_idesc_bf16(128, sh.Npad);
@@ -286,14 +289,17 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
           :: "r"(bar1) : "memory");
     }
   }
-  // every thread waits for the products (bounded)
-  const bool done = __syncthreads_and(ok ? 1 : 0) && mbar_wait(bar1, 0);
+  // every thread waits for the products (bounded); `issued` is CTA-wide: the
+  // MMAs and their commit were issued only if thread 0's operand wait succeeded
+  const bool issued = __syncthreads_and(ok ? 1 : 0);
+  const bool done = issued && mbar_wait(bar1, 0);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const bool all_done = __syncthreads_and(done ? 1 : 0);
   if (!all_done) {
     if (tid == 0 && p.err) atomicExch(p.err, 1);
-    mbar_wait(bar0, 0);  // let our own copies land before the CTA exits
-    if (ok) mbar_wait(bar1, 0);
+    // let our own bulk copy and MMAs finish before the CTA exits (full bound)
+    mbar_wait(bar0, 0);
+    if (issued) mbar_wait(bar1, 0);
   } else {
     // epilogue on this thread's r-line (column w = TMEM lane): r term, Tau rows,
     // stage update, reading the products from TMEM 16 rows at a time (the

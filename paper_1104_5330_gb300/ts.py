@@ -49,6 +49,12 @@ class GridDesc(ctypes.Structure):
                 ("filter_order", ctypes.c_int), ("radial", ctypes.c_int)]
 
 
+class Cons2DDesc(ctypes.Structure):
+    _fields_ = [("R1", ctypes.c_double), ("R2", ctypes.c_double), ("Nr", ctypes.c_int),
+                ("NTheta", ctypes.c_int), ("problems", ctypes.c_int),
+                ("scatter_c", ctypes.c_double), ("bc", ctypes.c_int)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libts.so not built ({LIB_PATH}); run "
@@ -71,6 +77,8 @@ def _load():
         "ts_liouville": [P, P, P, P],
         "ts_adjoint_step": [P, P, P, P, P, D, P],
         "ts_flux_weights": [P, P, P],
+        "ts_outgoing_flux": [P, P, P, P],
+        "ts_outgoing_flux_adjoint": [P, P, P, P],
         "ts_moments": [P, P, P, P, P, P, P, P],
         "ts_moments_noalloc": [ctypes.POINTER(GridDesc), P, P, P, P, P, P, P],
         "ts_autotune": [P, P],
@@ -80,7 +88,17 @@ def _load():
         "ts_batch_grid": [P, I, ctypes.POINTER(P)],
         "ts_batch_step": [P, P, P, I, P],
         "ts_sync_status": [P, P],
+        "ts_set_wait_limit": [P, ctypes.c_longlong],
+        "ts_stable_dt": [P, P, I, ctypes.POINTER(D), ctypes.POINTER(D), P],
         "ts_probe_fma_rate": [I, ctypes.POINTER(D), P],
+        "ts_cons2d_create": [ctypes.POINTER(Cons2DDesc), ctypes.POINTER(P)],
+        "ts_cons2d_destroy": [P],
+        "ts_cons2d_nodes": [P, P, P],
+        "ts_cons2d_set_coeffs": [P, P, P, P, P],
+        "ts_cons2d_apply_inflow": [P, P, P],
+        "ts_cons2d_rhs": [P, P, P, P],
+        "ts_cons2d_step": [P, P, D, I, P],
+        "ts_cons2d_balance": [P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -231,6 +249,15 @@ def ts_flux_weights(grid, w, stream=None):
     _check(LIB.ts_flux_weights(grid, _ptr(w), _stream(stream)), "ts_flux_weights")
 
 
+def ts_outgoing_flux(grid, F, J_R2, stream=None):
+    _check(LIB.ts_outgoing_flux(grid, _ptr(F), _ptr(J_R2), _stream(stream)), "ts_outgoing_flux")
+
+
+def ts_outgoing_flux_adjoint(grid, gJ, lam, stream=None):
+    _check(LIB.ts_outgoing_flux_adjoint(grid, _ptr(gJ), _ptr(lam), _stream(stream)),
+           "ts_outgoing_flux_adjoint")
+
+
 def ts_moments(grid, F, F0=None, F1=None, N=None, J_R1=None, J_R2=None, stream=None):
     _check(LIB.ts_moments(grid, _ptr(F), _ptr(F0), _ptr(F1), _ptr(N), _ptr(J_R1), _ptr(J_R2),
                           _stream(stream)), "ts_moments")
@@ -276,6 +303,19 @@ def ts_batch_step(batch, fields, dts, nsteps=1, stream=None):
     ptrs = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
     dt = (ctypes.c_double * n)(*[float(x) for x in dts])
     _check(LIB.ts_batch_step(batch, ptrs, dt, int(nsteps), _stream(stream)), "ts_batch_step")
+
+
+def ts_stable_dt(grid, x0, iters=60, stream=None):
+    """(rho, dt_max): power-iteration spectral radius of the stage operator's
+    linear part from the start field x0, and the RK4 step 2.6 / rho."""
+    rho, dtm = ctypes.c_double(), ctypes.c_double()
+    _check(LIB.ts_stable_dt(grid, _ptr(x0), int(iters), ctypes.byref(rho), ctypes.byref(dtm),
+                            _stream(stream)), "ts_stable_dt")
+    return rho.value, dtm.value
+
+
+def ts_set_wait_limit(grid, operand_wait_iterations):
+    _check(LIB.ts_set_wait_limit(grid, int(operand_wait_iterations)), "ts_set_wait_limit")
 
 
 def ts_sync_status(grid, stream=None):
@@ -401,6 +441,12 @@ class Grid:
         ts_flux_weights(self.handle, w)
         return w
 
+    def outgoing_flux(self, F):
+        """J_R2 per group (Eq. Flux), float64 [G]."""
+        J = torch.empty(self.shape[0], dtype=torch.float64, device=self.device)
+        ts_outgoing_flux(self.handle, F, J)
+        return J
+
     def moments(self, F):
         G = self.shape[0]
         F0 = torch.empty(self.coef_shape, dtype=torch.float64, device=self.device)
@@ -442,3 +488,64 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Cons2D:
+    """Owning handle of the conservative 2-D (r, Theta) variant (ts_cons2d_*):
+    Fhat[P][Nr][NTheta] float64 tensors on the device."""
+
+    def __init__(self, R1, R2, Nr, NTheta, problems=1, scatter_c=0.75, bc=TS_BC_TAU_INFLOW):
+        self.desc = Cons2DDesc(R1, R2, Nr, NTheta, problems, scatter_c, bc)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _check(LIB.ts_cons2d_create(ctypes.byref(self.desc), ctypes.byref(h)), "ts_cons2d_create")
+        self.handle = h
+        self.shape = (problems, Nr, NTheta)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            _check(LIB.ts_cons2d_destroy(self.handle), "ts_cons2d_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nodes(self):
+        r, th = np.zeros(self.desc.Nr), np.zeros(self.desc.NTheta)
+        _check(LIB.ts_cons2d_nodes(self.handle, r.ctypes.data_as(ctypes.c_void_p),
+                                   th.ctypes.data_as(ctypes.c_void_p)), "ts_cons2d_nodes")
+        return r, th
+
+    def set_coeffs(self, kappa_s=None, inflow_R1=None, inflow_R2=None):
+        cv = lambda a: None if a is None else torch.as_tensor(
+            a, dtype=torch.float64, device=self.device).contiguous()
+        self._c = [cv(kappa_s), cv(inflow_R1), cv(inflow_R2)]
+        _check(LIB.ts_cons2d_set_coeffs(self.handle, *[_ptr(x) for x in self._c],
+                                        _stream(None)), "ts_cons2d_set_coeffs")
+
+    def apply_inflow(self, Fh):
+        _check(LIB.ts_cons2d_apply_inflow(self.handle, _ptr(Fh), _stream(None)),
+               "ts_cons2d_apply_inflow")
+        return Fh
+
+    def rhs(self, Fh):
+        K = torch.empty_like(Fh)
+        _check(LIB.ts_cons2d_rhs(self.handle, _ptr(Fh), _ptr(K), _stream(None)), "ts_cons2d_rhs")
+        return K
+
+    def step(self, Fh, dt, nsteps=1):
+        _check(LIB.ts_cons2d_step(self.handle, _ptr(Fh), float(dt), int(nsteps), _stream(None)),
+               "ts_cons2d_step")
+        return Fh
+
+    def balance(self, Fh):
+        """(N, J_R1, J_R2) [P][3] and the residual dN/dt + J_R2 - J_R1 [P]."""
+        P = self.shape[0]
+        NJ = torch.empty((P, 3), dtype=torch.float64, device=self.device)
+        res = torch.empty(P, dtype=torch.float64, device=self.device)
+        _check(LIB.ts_cons2d_balance(self.handle, _ptr(Fh), _ptr(NJ), _ptr(res), _stream(None)),
+               "ts_cons2d_balance")
+        return NJ, res

@@ -106,3 +106,37 @@ def test_gradients_match_central_differences(dims, G, n):
                 fd = (J(kap, eta + eps * v) - J(kap, eta - eps * v)) / (2 * eps)
             ad = float(np.sum(grad * v))
             assert abs(fd - ad) <= 1e-6 * abs(fd), (which, fd, ad)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-6)])
+def test_outgoing_flux_matches_oracle_and_its_seed_is_the_weights(precision, tol):
+    """ts_outgoing_flux against the oracle's J_R2 (Eq. Flux, App. A), and
+    ts_outgoing_flux_adjoint against the oracle's weights at r = R2 scaled by a
+    per-group cotangent, zero at every other radial node."""
+    og, gg = pair(0.2, 1.0, 11, 7, 10, 6, 12, G=3, precision=precision)
+    F = np.random.default_rng(31).standard_normal(og.shape) + 2.0
+    dt = torch.float64 if precision == 0 else torch.float32
+    Fd = cuda(F, dt)
+    J = host(gg.outgoing_flux(Fd))
+    Fo = host(Fd)                                    # the values the GPU saw
+    JR2 = og.moments(Fo)[4]
+    assert rel_l2(J, JR2) < tol
+    _, _, _, _, J2 = gg.moments(Fd)
+    assert rel_l2(J, host(J2)) < 1e-13
+    gJ = np.array([0.5, -1.25, 2.0])
+    lam = torch.full(og.shape, float("nan"), dtype=dt, device="cuda")
+    T().ts_outgoing_flux_adjoint(gg.handle, cuda(gJ), lam)
+    expect = np.zeros(og.shape)
+    expect[:, -1] = gJ[:, None, None, None, None] * og.outgoing_flux_weights()[None]
+    assert rel_l2(host(lam), expect) < (1e-15 if precision == 0 else 1e-7)
+    assert np.all(host(lam)[:, :-1] == 0.0)
+
+
+def test_outgoing_flux_backward_is_the_library_seed():
+    from paper_1104_5330_gb300.autograd import outgoing_flux
+    og, gg = pair(0.2, 1.0, 9, 6, 8, 6, 8, G=2)
+    F = cuda(np.random.default_rng(5).standard_normal(og.shape)).requires_grad_()
+    (outgoing_flux(gg, F) * torch.tensor([3.0, -1.0], dtype=torch.float64, device="cuda")).sum().backward()
+    expect = np.zeros(og.shape)
+    expect[:, -1] = np.array([3.0, -1.0])[:, None, None, None, None] * og.outgoing_flux_weights()[None]
+    assert rel_l2(host(F.grad), expect) < 1e-15

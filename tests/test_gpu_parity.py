@@ -340,9 +340,12 @@ def test_extreme_sizes_rhs_and_steps(dims):
     floor = rel_l2(OProblem(og2, kap, eta, ks, gR1, gR2).rhs(F0), Ko)
     tol = max(FP64_TOL, 2.0 * floor)
     assert rel_l2(host(gg.rhs(cuda(F0))), Ko) < tol
-    # the radial step-size rule ignores the angular terms, which at 64 nodes near
-    # the poles need a far smaller step for a stable RK4 run: take 1e-5
-    dt = 1e-5
+    # the step from the discrete operator's spectral radius (every axis, the
+    # angular terms at 64 nodes near the poles included), half of the RK4 limit
+    x0 = cuda(np.random.default_rng(77).standard_normal(og.shape))
+    rho, dt = T().ts_stable_dt(gg.handle, x0, 80)
+    assert rho > 0 and np.isfinite(dt)
+    dt *= 0.5
     Fg = cuda(F0)
     gg.step(Fg, dt, 3)
     Fo = op.run(F0, dt, 3)
@@ -352,3 +355,21 @@ def test_extreme_sizes_rhs_and_steps(dims):
     F32 = cuda(F0, torch.float32)
     g32.step(F32, dt, 3)
     assert rel_l2(host(F32), Fo) < FP32_TOL
+
+
+@pytest.mark.parametrize("dims", [RAGGED, (0.2, 1.0, 9, 8, 8, 8, 8)])
+def test_stable_dt_is_the_oracle_power_iteration(dims):
+    """ts_stable_dt runs the oracle's power iteration (same start field, same
+    iterations) on the device: the estimates agree to rounding, and a run at
+    the step it returns stays bounded."""
+    og, gg = pair(*dims, G=2)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    x0 = np.random.default_rng(5).standard_normal(og.shape)
+    rho, dt = T().ts_stable_dt(gg.handle, cuda(x0), 40)
+    rho_o = op.spectral_radius(x0, 40)
+    assert abs(rho - rho_o) < 1e-10 * rho_o
+    assert abs(dt - 2.6 / rho_o) < 1e-10 * dt
+    Fg = cuda(F0)
+    gg.step(Fg, dt, 200)
+    assert np.isfinite(host(Fg)).all() and np.abs(host(Fg)).max() < 10 * np.abs(F0).max()

@@ -72,3 +72,31 @@ def test_tensor_core_agrees_with_simt_fp32(prec):
     simt.step(b, dt, 10)
     T().ts_sync_status(tc.handle)
     assert rel_l2(host(a), host(b)) < 2e-6
+
+
+@pytest.mark.parametrize("prec", TC)
+def test_operand_wait_timeout_is_reported_and_the_grid_recovers(prec):
+    """Failure detection without a fault: the tensor-core pass's operand wait is
+    made to give up at once (ts_set_wait_limit < 0). Every CTA then issues no
+    products, latches the grid's error flag, drains its own bulk copy with the
+    full bound and frees its tensor memory; ts_sync_status reports
+    TS_ERR_TIMEOUT once and clears the flag. With the default bound back, the
+    next steps return TS_OK and match the oracle."""
+    ts = T()
+    dims = GRIDS[1]
+    og, gg = pair(*dims, G=2, precision=prec)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    dt = I.dt_rule(dims[0], dims[1], dims[2])
+    ts.ts_set_wait_limit(gg.handle, -1)
+    Fg = cuda(F0, torch.float32)
+    gg.step(Fg, dt, 1)
+    with pytest.raises(ts.TSError) as e:
+        ts.ts_sync_status(gg.handle)
+    assert e.value.status == ts.TS_ERR_TIMEOUT
+    ts.ts_sync_status(gg.handle)          # reported once, then cleared
+    ts.ts_set_wait_limit(gg.handle, 0)
+    Fg = cuda(F0, torch.float32)
+    gg.step(Fg, dt, 5)
+    ts.ts_sync_status(gg.handle)
+    assert rel_l2(host(Fg), op.run(F0, dt, 5)) < 1e-5

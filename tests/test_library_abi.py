@@ -57,6 +57,12 @@ def test_new_entry_points_reject_null_grids(T):
     assert T.LIB.ts_set_scattering_anisotropy(None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_set_scattering_quadrupole(None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_reset_history(None) == T.TS_ERR_ARG
+    assert T.LIB.ts_outgoing_flux(None, None, None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_outgoing_flux_adjoint(None, None, None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_set_wait_limit(None, 0) == T.TS_ERR_ARG
+    assert T.LIB.ts_stable_dt(None, None, 10, None, None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_cons2d_create(None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_cons2d_step(None, None, ctypes.c_double(0.1), 1, None) == T.TS_ERR_ARG
 
 
 def test_batches_refuse_ab2_before_touching_the_device(T):
