@@ -224,7 +224,30 @@ def pass_work(dims, es):
         "plane": pts * es * 3,          # read U, read+write K
         "radial": pts * es * 5,         # read U, K, F, Acc; write U (or F) and Acc: 4-6 fields
     }
+    # fused stages (float grids): the plane pass writes its terms (read U, write K),
+    # the fused pass reads U, K and the stage update's fields: RK4 stages 1..4 move
+    # 4, 6, 6, 5 fields (F and K / U, K, F, Acc and U, Acc / ... / U, K, F, Acc and F)
+    flops["fused"] = flops["angular"] + flops["radial"]
+    byts["plane_store"] = pts * es * 2
+    byts["fused"] = pts * es * (4 + 6 + 6 + 5) / 4.0
     return pts, flops, byts
+
+
+def pass_names(pn):
+    """Names of the profiled pass buckets: (angular, plane, radial) for the
+    three-pass form, (plane, fused) when the angular bucket is empty (the fused
+    angular + radial pass runs in the radial bucket)."""
+    if pn[0] == 0 and pn[2] > 0:
+        return {1: "plane_store", 2: "fused"}
+    return {0: "angular", 1: "plane", 2: "radial"}
+
+
+KERNEL_OF = {"plane_store": None, "fused": "k_fused"}
+
+
+def path_bytes_per_update(es):
+    """Compulsory bytes per RK4 point-update (F, U, Acc: 17 field accesses)."""
+    return 17 * es
 
 
 # ------------------------------------------------------------- oracle side
@@ -369,8 +392,12 @@ def run_batch(args, stream):
         Fs.append(F)
         dts.append(I.dt_rule(s.R1, s.R2, s.Nr))
     pts = b.points
-    b.step(Fs, dts, 2)              # graph capture + warm-up
+    b.step(Fs, dts, 3)              # graph capture + warm-up
     torch.cuda.synchronize()
+    # check: the two smallest problems stepped alone on their own grids from the
+    # same state must agree with the batch to FP32 rounding
+    small = sorted(range(len(specs)), key=lambda q: b.grids[q].points)[:2]
+    ref = {q: Fs[q].clone() for q in small}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     b.step(Fs, dts, args.batch_steps)
@@ -378,11 +405,18 @@ def run_batch(args, stream):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     finite = all(bool(torch.isfinite(F).all()) for F in Fs)
+    agree = {}
+    for q in small:
+        b.grids[q].step(ref[q], dts[q], args.batch_steps)
+        torch.cuda.synchronize()
+        agree[f"problem_{q}"] = float(torch.linalg.vector_norm((Fs[q] - ref[q]).double()) /
+                                      torch.linalg.vector_norm(ref[q].double()))
     out = {"value": pts * args.batch_steps / (ms * 1e-3), "unit": "point-updates/s",
            "ms_per_step": ms / args.batch_steps, "steps": args.batch_steps,
            "problems": len(specs), "points_per_step": pts, "dtype": "f32 (+f64 radial end rows, f64 collision)",
            "scheme": "RK4 streaming + implicit collision", "setup_s_incl_autotune": t_setup,
-           "launches_per_step": 14, "finite": finite}
+           "launches_per_step": 14, "finite": finite,
+           "rel_l2_vs_single_problem_steps": agree}
     del Fs
     b.close()
     return out
@@ -507,6 +541,141 @@ def run_hybrid(args, stream):
                                    for a, n in enumerate(("angular", "plane", "radial"))}}
 
 
+def variant_line(ts, dims, wname, vname, vprec, pts, steps, ms, err, nv, pm, pn, peaks, sms,
+                 smax):
+    """Rate, error and per-pass roofline of one float variant: the dominant
+    kernel's algorithmic bytes over its average launch time (CUDA events on the
+    launching stream), and the path fraction 17 s x rate / HBM peak."""
+    names = pass_names(pn)
+    _, fl, by = pass_work(dims, 4)
+    per = {n: pm[a] / pn[a] for a, n in names.items() if pn[a] > 0}
+    tot = sum(pm[a] for a in names)
+    dom = max(per, key=lambda n: pm[[a for a, m in names.items() if m == n][0]])
+    avg = per[dom]
+    hbm = by[dom] / (avg * 1e-3) / 1e9
+    if dom == "fused":
+        kn = "k_fused<float>"
+    elif dom == "plane_store":
+        kn = "plane pass (store form)"
+    else:
+        kf = eo_kernel(dom, dims) if even_odd_passes(dims, 4)[dom] else f"k_{dom}"
+        kn = ("k_radial_tc" if dom == "radial" and vprec in (ts.TS_TF32X3, ts.TS_BF16X3)
+              else kf) + "<float>"
+    rate = pts * steps / (ms * 1e-3)
+    return {"value": rate, "unit": "point-updates/s", "ms_per_step": ms / steps, "dtype": "f32",
+            "rel_l2_vs_gpu_fp64": err, "after_steps": nv,
+            "path_fraction_of_hbm": path_bytes_per_update(4) * rate / 1e9 / peaks["hbm_gbs"],
+            "roofline": {"bound": "hbm", "kernel": kn, "achieved": hbm, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
+                         "traffic": _traffic(dom, wname, vname),
+                         "fp32_alu_tflops": fl.get(dom if dom != "plane_store" else "plane", 0) /
+                         (avg * 1e-3) / 1e12,
+                         "fp32_alu_peak_tflops": sms * 2 * FP32_FMA_PER_SM_CLK * smax * 1e6 / 1e12,
+                         "pass_share": {n: float(pm[a] / tot) for a, n in names.items()},
+                         "pass_ms_per_launch": {n: float(v) for n, v in per.items()},
+                         "algorithmic_bytes_per_launch": by[dom]}}
+
+
+def run_cons2d(args, stream):
+    """The conservative 2-D variant of App. B (Fhat = r^2 sin Th F, Eq. speccons)
+    on its shell problem: 0.5 <= r <= 1, empty at t = 0, Fhat(R1, Th) =
+    cos Th sin Th on the outgoing directions, Thomson scattering (c = 3/4) from
+    a plasma vanishing at R2, kappa_s = 9 tau/(R2 - R1) (1 - (r - R1)/(R2 - R1))^8;
+    2048 independent problems with optical depths tau log-spaced over [0.1, 10],
+    65 x 24 nodes each (the paper: 65 spectral radial points and 25 in Theta),
+    RK4 at dt = 0.4 h_min, every step of a call in one launch. Reports the rate
+    and the operator's discrete number balance |dN/dt + J_R2 - J_R1| relative to
+    the fluxes after the run (zero to rounding: Eq. Cons)."""
+    import torch
+    import paper_1104_5330_gb300.ts as ts
+    P, Nr, NT, R1, R2 = 2048, 65, 24, 0.5, 1.0
+    tau = np.logspace(-1, 1, P)
+    g = ts.Cons2D(R1, R2, Nr, NT, problems=P, scatter_c=0.75)
+    r, th = g.nodes()
+    ks = 9 * tau[:, None] / (R2 - R1) * (1 - (r[None, :] - R1) / (R2 - R1)) ** 8
+    g1 = np.tile(np.cos(th[:NT // 2]) * np.sin(th[:NT // 2]), (P, 1))
+    g.set_coeffs(ks, g1, None)
+    X = g.apply_inflow(torch.zeros((P, Nr, NT), dtype=torch.float64, device="cuda"))
+    dt = 0.4 * 0.5 * (R2 - R1) * (1 - math.cos(math.pi / (Nr - 1)))
+    g.step(X, dt, args.warmup)
+    torch.cuda.synchronize()
+    n = 10 * args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(X, dt, n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    gb = ts.Cons2D(R1, R2, Nr, NT, problems=P, scatter_c=0.75, bc=ts.TS_BC_NONE)
+    gb.set_coeffs(ks, g1, None)
+    NJ, res = gb.balance(X)
+    NJ, res = NJ.cpu().numpy(), res.cpu().numpy()
+    scale = np.abs(NJ[:, 1:]).max(axis=1) + np.abs(NJ[:, 0]).max() * 1e-300
+    pts = P * Nr * NT
+    out = {"value": pts * n / (ms * 1e-3), "unit": "point-updates/s", "ms_per_step": ms / n,
+           "steps": n, "problems": P, "grid": [Nr, NT], "dtype": "f64", "launches_per_call": 1,
+           "workload": "App. B shell: Lambert inflow at R1, Thomson scattering, tau in [0.1, 10]",
+           "balance_residual_rel_max": float(np.max(np.abs(res) / scale)),
+           "N_range": [float(NJ[:, 0].min()), float(NJ[:, 0].max())]}
+    g.close()
+    gb.close()
+    return out
+
+
+def run_workload_precisions(args, wname, stream, precisions, nv):
+    """Rates of `precisions` on another workload of the same family (absorber,
+    seeded smooth F0, static inflow, RK4 at dt = 0.4 h_min), and each float
+    variant's relative L2 distance to the GPU FP64 result after nv steps."""
+    import torch
+    import paper_1104_5330_gb300.ts as ts
+    from paper_1104_5330_gb300 import inputs as I
+    dims = WORKLOADS[wname]
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    dt = I.dt_rule(R1, R2, Nr)
+    peaks, _ = _peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    smax = peaks.get("sm_max_mhz", 2070.0)
+    out = {"workload": wname, "grid": [Nr, Nt, Np, NT, NP], "groups": G, "dt": dt,
+           "steps": args.steps}
+    ref = None
+    for name in precisions:
+        prec = getattr(ts, PRECISIONS[name])
+        gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=prec)
+        r, th, ph, Th, Ph = gg.nodes()
+        kap, eta, ks = I.absorber_fields(r, th, ph, groups=G)
+        F0 = np.stack([I.seeded_smooth(r, th, ph, Th, Ph, 1104 + g, R1, R2) for g in range(G)])
+        gR1, gR2 = I.inflow_from(F0, NT)
+        gg.set_coeffs(kap, eta, ks, gR1, gR2)
+        F = torch.as_tensor(F0, dtype=gg.dtype, device="cuda").contiguous()
+        gg.step(F, dt, nv)
+        if prec == ts.TS_FP64:
+            ref = F.clone()
+            err = None
+        else:
+            err = float(torch.linalg.vector_norm(F.double() - ref) / torch.linalg.vector_norm(ref))
+        gg.step(F, dt, args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gg.step(F, dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ts.ts_sync_status(gg.handle)
+        pm, pn = ts.ts_step_profile(gg.handle, F, dt, 2)
+        if prec == ts.TS_FP64:
+            out[name] = {"value": gg.points * args.steps / (ms * 1e-3), "unit": "point-updates/s",
+                         "ms_per_step": ms / args.steps, "dtype": "f64",
+                         "pass_ms_per_launch": {n: float(pm[a] / pn[a])
+                                                for a, n in pass_names(pn).items()}}
+        else:
+            out[name] = variant_line(ts, dims, wname, name, prec, gg.points, args.steps, ms, err,
+                                     nv, pm, pn, peaks, sms, smax)
+        del gg, F
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, dims, wname):
     import torch
     import torch.distributed as dist
@@ -559,19 +728,25 @@ def run_ours(args, dims, wname):
         sync_all()
     ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     value = job_rate(pts * args.steps, world, ms)
-    launches = 12 * args.steps
 
     # per-pass device time (CUDA events on the launching stream)
     nprof = max(2, min(args.steps, 10))
     pass_ms, pass_n = ts.ts_step_profile(gg.handle, F, dt, nprof)
-    names = ["angular", "plane", "radial"]
+    bucket = pass_names(pass_n)
+    names = [bucket[a] for a in sorted(bucket)]
+    launches = int(sum(pass_n)) * args.steps // nprof   # every kernel of a step
     _, flops, byts = pass_work(dims, es)
-    shares = pass_ms[:3] / pass_ms[:3].sum()
-    dom = int(np.argmax(pass_ms[:3]))
-    dname = names[dom]
+    flops["plane_store"] = flops["plane"]
+    tot = sum(pass_ms[a] for a in bucket)
+    shares = [pass_ms[a] / tot for a in sorted(bucket)]
+    dom = max(bucket, key=lambda a: pass_ms[a])
+    dname = bucket[dom]
     avg_ms = pass_ms[dom] / pass_n[dom]
     peaks, peak_src = _peaks()
-    kfam = eo_kernel(dname, dims) if even_odd_passes(dims, es)[dname] else f"k_{dname}"
+    if dname in KERNEL_OF:
+        kfam = KERNEL_OF[dname] or "k_plane_sq"
+    else:
+        kfam = eo_kernel(dname, dims) if even_odd_passes(dims, es)[dname] else f"k_{dname}"
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     smax = peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = sms * 2 * FP64_FMA_PER_SM_CLK * smax * 1e6 / 1e12
@@ -656,26 +831,9 @@ def run_ours(args, dims, wname):
             ts.ts_sync_status(g32.handle)
             ms32 = e0.elapsed_time(e1)
             pm, pn = ts.ts_step_profile(g32.handle, F32b, dt, nv)
-            _, fl32, by32 = pass_work(dims, 4)
-            d32 = int(np.argmax(pm[:3]))
-            hbm32 = by32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e9
-            alu32 = fl32[names[d32]] / (pm[d32] / pn[d32] * 1e-3) / 1e12
-            kf = (eo_kernel(names[d32], dims) if even_odd_passes(dims, 4)[names[d32]]
-                  else f"k_{names[d32]}")
-            kn = (kname.get(names[d32], kf) if vprec in (ts.TS_TF32X3, ts.TS_BF16X3) else kf)
-            kn += "<float>"
-            line["variants"][vname] = {
-                "value": pts * args.steps / (ms32 * 1e-3), "unit": "point-updates/s",
-                "ms_per_step": ms32 / args.steps, "dtype": "f32",
-                "rel_l2_vs_gpu_fp64": err32, "after_steps": nv,
-                "roofline": {"bound": "hbm", "kernel": kn,
-                             "achieved": hbm32, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                             "frac": hbm32 / peaks["hbm_gbs"],
-                             "traffic": _traffic(names[d32], wname, vname),
-                             "fp32_alu_tflops": alu32,
-                             "fp32_alu_peak_tflops": sms * 2 * FP32_FMA_PER_SM_CLK * smax * 1e6 / 1e12,
-                             "pass_share": {n: float(s) for n, s in zip(names, pm[:3] / pm[:3].sum())},
-                             "pass_ms_per_launch": {n: float(pm[a] / pn[a]) for a, n in enumerate(names)}}}
+            line["variants"][vname] = variant_line(ts, dims, wname, vname, vprec, pts,
+                                                   args.steps, ms32, err32, nv, pm, pn, peaks,
+                                                   sms, smax)
             del g32, F32, F32b
         lam = torch.randn_like(F)
         gk = torch.zeros(gg.coef_shape, dtype=torch.float64, device="cuda")
@@ -693,6 +851,16 @@ def run_ours(args, dims, wname):
                            "ms_per_step": msa / na, "dtype": "f64",
                            "includes": "forward recomputation of the stage inputs"}
 
+    if not args.skip_workloads:
+        # the vacuum-free grid of the free-streaming check (17 x 8^4, 1 group) and the
+        # precision grid (65 x 32^4, 1 group: 68M points) with every precision
+        line["workload_17x8^4_g1"] = run_workload_precisions(
+            args, "absorber_17x8^4_g1", stream, ["fp64", "fp32"], 10)
+        line["precision_65x32^4_g1"] = run_workload_precisions(
+            args, "absorber_65x32^4_g1", stream, ["fp64", "fp32", "fp32_r64", "tf32x3", "bf16x3"],
+            10)
+    if not args.skip_workloads:
+        line["conservative_2d"] = run_cons2d(args, stream)
     if not args.skip_aniso:
         line["anisotropic_scattering"] = run_anisotropic(args, dims, stream)
         line["ab2"] = run_ab2(args, dims, stream, ms / args.steps)
@@ -730,7 +898,8 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-aniso", action="store_true")
-    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--skip-workloads", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--skip-diff", action="store_true")
     ap.add_argument("--diff-steps", type=int, default=200)
     args = ap.parse_args()
