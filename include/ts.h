@@ -70,7 +70,10 @@ typedef enum {
   TS_TF32X3 = 3,   /* float storage; the radial derivative on the tensor cores
                       (tcgen05, operands split into TF32 hi + lo, three products
                       hi*hi + hi*lo + lo*hi accumulated in FP32) for N_r <= 81,
-                      angular passes as TS_FP32 */
+                      angular passes as TS_FP32 (with the environment variable
+                      TS_TC_ANGULAR=1 at grid creation, 16 x 16 direction blocks
+                      and the isotropic kernel, the Theta and Phi contractions of
+                      the angular pass also run on the tensor cores, same split) */
   TS_BF16X3 = 4    /* float storage; the radial derivative on the tensor cores
                       with operands split into three bf16 terms b0 + b1 + b2 and
                       the six products of total order <= 2 accumulated in FP32,

@@ -265,6 +265,32 @@ std::vector<uint16_t> tc_tables_bf16(const HostTables& h) {
   return out;
 }
 
+// The angular pass's tensor-core B operands (16 x 16 direction blocks), each split
+// into TF32 hi + lo in the K-major core layout (8-row x 4-column core matrices,
+// core (n/8, k/4) at float offset ((n/8) KC + k/4) 32):
+//   W1[n = k][kk] = A[k][kk] (kk < 16), B[k][kk - 16] (kk >= 16): the DFS pair of the
+//   doubled Theta circle, K = 32;  W2[n = m][kk = m'] = D_Phi[m][m'], K = 16.
+// Order: W1 hi, W1 lo, W2 hi, W2 lo.
+std::vector<float> tc_angular_tables(const HostTables& h) {
+  const int N = 16;
+  std::vector<float> out((size_t)2 * N * 32 + 2 * N * 16, 0.f);
+  auto put = [&](size_t base, int KC, int n, int k, double v, size_t term) {
+    const float hi = tf32_round((float)v);
+    const float lo = tf32_round((float)(v - (double)hi));
+    const size_t o = (size_t)((n / 8) * KC + k / 4) * 32 + (n % 8) * 4 + (k % 4);
+    out[base + o] = hi;
+    out[base + term + o] = lo;
+  };
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < 2 * N; ++k)
+      put(0, 8, n, k, k < N ? h.ATh[(size_t)n * N + k] : h.BTh[(size_t)n * N + (k - N)],
+          (size_t)N * 32);
+  const size_t b2 = (size_t)2 * N * 32;
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < N; ++k) put(b2, 4, n, k, h.DPh[(size_t)n * N + k], (size_t)N * 16);
+  return out;
+}
+
 void even_odd_tables(HostTables& h) {
   auto pq = [](const Vec& A, const Vec& B, int N, Vec& PT, Vec& QT) {
     PT.assign((size_t)N * N, 0.0);
@@ -520,6 +546,10 @@ ts::Problem make_problem(const ts_grid* g) {
   p.wait_operand = g->wait_operand > 0 ? g->wait_operand : ts::kDefaultWaitIters;
   if (g->wait_operand < 0) p.wait_operand = 0;
   p.plane_store = 0;
+  p.ep64 = g->t64.EpT;
+  p.op64 = g->t64.OpT;
+  p.mc64 = g->t64.DrMc;
+  p.tcang = g->tcang;
   if (g->sn > 0) {   // one slice of groups: every per-group pointer offset to group s0
     const long long per = g->d.nblk / g->d.G;
     const long long infl = (long long)g->d.Nt * g->d.Np * (g->d.NT / 2) * g->d.NP;
@@ -889,6 +919,19 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
 
   cudaError_t e = upload_tables<double>(G->h, &G->tab64, &G->t64);
   if (e == cudaSuccess && g.precision != TS_FP64) e = upload_tables<float>(G->h, &G->tab32, &G->t32);
+  if (e == cudaSuccess && g.precision == TS_TF32X3 && g.NTheta == 16 && g.NPhi == 16 &&
+      g.radial == TS_RADIAL_CHEBYSHEV) {
+    // TS_TC_ANGULAR=1 puts the angular pass on the tensor cores too; it is correct
+    // but slower than the SIMT pass (each CTA's split -> MMA -> epilogue runs in
+    // series on K = 16..32 contractions), so the SIMT pass stays the default
+    const char* on = std::getenv("TS_TC_ANGULAR");
+    if (on && on[0] == '1') {
+      const std::vector<float> w = tc_angular_tables(G->h);
+      e = cudaMalloc((void**)&G->tcang, w.size() * sizeof(float));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(G->tcang, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+  }
   if (e == cudaSuccess && g.precision == TS_BF16X3) {
     const std::vector<uint16_t> b16 = tc_tables_bf16(G->h);
     e = cudaMalloc(&G->tcb16, b16.size() * sizeof(uint16_t));
@@ -932,7 +975,7 @@ ts_status ts_destroy_grid(ts_grid* g) {
   cudaDeviceSynchronize();
   void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
                   g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err, g->tcb16,
-                  g->scb, g->scc};
+                  g->scb, g->scc, g->tcang};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : g->adj)

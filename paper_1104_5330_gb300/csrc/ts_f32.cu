@@ -4,6 +4,7 @@
 #include "ts_fused.cuh"
 #include "ts_launch.cuh"
 #include "ts_tc.cuh"
+#include "ts_tc_angular.cuh"
 
 namespace ts {
 
@@ -34,6 +35,27 @@ cudaError_t launch_radial_tc(const Problem& p, const Tables<float>& t, const flo
   return radial_tc<TC_TF32X3>(p, t.TcBhi, t, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, s);
 }
 
+
+cudaError_t launch_angular_tc(const Problem& p, const Tables<float>& t, const float* U, float* K,
+                              float sgn, bool collision, cudaStream_t s) {
+  static const cudaError_t e = allow_smem(k_angular_tc);  // once
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (p.d.nblk + TcAng::BPT - 1) / TcAng::BPT;
+  static int per_sm = 0, nsm = 0;
+  if (!per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_angular_tc, 128, TcAng::bytes) !=
+            cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    if (nsm < 1) nsm = 1;
+  }
+  const int ctas = (int)std::min<long long>(ntiles, (long long)per_sm * nsm);
+  k_angular_tc<<<ctas, 128, TcAng::bytes, s>>>(p, t, p.tcang, U, K, sgn, collision ? 1 : 0,
+                                               ntiles);
+  return cudaGetLastError();
+}
 
 bool fused_plan(const Dims& d, int n64, int* nb, int* nbuf) {
   // one chunk of all N_r blocks and two staging buffers if they fit; else one

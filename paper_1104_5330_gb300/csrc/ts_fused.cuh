@@ -148,9 +148,8 @@ k_fused(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* __rest
         C a[4], b[4];
         ld4<C>(su + (size_t)ii * S + w0, a);
         ld4<C>(su + (size_t)(N - ii) * S + w0, b);
-        // D_r entries in double: D[i][ii] and D[i][N-ii]
-        const double dA = Dr64[i * Nr + ii], dB = Dr64[i * Nr + (N - ii)];
-        const double Ep = dA + dB, Op = dA - dB;
+        // the folded D_r in double: D[i][ii] + D[i][N-ii] and D[i][ii] - D[i][N-ii]
+        const double Ep = p.ep64[ii * hh + i], Op = p.op64[ii * hh + i];
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
           ae[cc] = fma(Ep, (double)a[cc] + (double)b[cc], ae[cc]);
@@ -159,7 +158,7 @@ k_fused(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* __rest
       }
       C m4[4] = {0, 0, 0, 0};
       if (odd) ld4<C>(su + (size_t)(N / 2) * S + w0, m4);
-      const double dm = odd ? Dr64[i * Nr + N / 2] : 0.0;
+      const double dm = odd ? p.mc64[i] : 0.0;
       C lo[4], hi[4];
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {

@@ -125,6 +125,13 @@ struct Problem {
   int* err;          // device flag set by a bounded wait that ran out
   long long wait_operand;  // bound (iterations) of the tensor-core pass's operand wait
   int plane_store;         // 1: the plane pass writes K = its terms (fused stages), 0: adds
+  // D_r folded onto the row pairs (i, N-i) in double ([ii][i], see Tables::EpT) and
+  // its middle column: the double-precision end rows of float grids
+  const double *ep64, *op64, *mc64;
+  // TS_TF32X3 with 16 x 16 direction blocks: the Theta (DFS pair, K = 32) and Phi
+  // (K = 16) derivative matrices split into TF32 hi + lo in the tensor-core B
+  // layout (W1 hi, W1 lo, W2 hi, W2 lo); NULL: the angular pass runs on the SIMT units
+  const float* tcang;
 };
 
 __host__ __device__ inline int kernel_form(const Problem& p, int collision) {
@@ -152,6 +159,10 @@ cudaError_t launch_fused(const Problem& p, const Tables<float>& t, const double*
                          const float* U, const float* Kp, float sgn, bool collision, bool tau,
                          int mode, float* F, float* Acc, float* Uout, float* out, double dt,
                          cudaStream_t s);
+// Angular pass on the tensor cores (TS_TF32X3, 16 x 16 direction blocks, isotropic
+// kernel; defined with the float kernels).
+cudaError_t launch_angular_tc(const Problem& p, const Tables<float>& t, const float* U, float* K,
+                              float sgn, bool collision, cudaStream_t s);
 // Radial pass of the hybrid grid (uniform r nodes, one-sided upwind differences;
 // `hold`: zero rate at the inflow nodes). Defined in ts_fd.cu.
 template <typename T, typename C>
@@ -270,6 +281,7 @@ struct ts_grid {
   bool hist = false;     // TS_AB2: Acc holds K of the previous step of hist_F
   const void* hist_F = nullptr;
   long long wait_operand = 0;  // 0: the default bound (ts_set_wait_limit)
+  float* tcang = nullptr;      // angular tensor-core operand terms (Problem::tcang)
   // Group slice the launches cover (ts_step_host's per-group pipeline): groups
   // s0 .. s0+sn-1, every pointer of the problem and the workspace offset to
   // group s0; sn = 0: all groups.

@@ -1311,23 +1311,37 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
       st4<C>(sMid + 4 * x, m);
     }
   }
-  for (int v = threadIdx.x; v < 2 * n64 * W4; v += blockDim.x) {  // rows nearest the ends
-    const int w0 = (v % W4) * 4, rr = v / W4;
-    const int i = rr < n64 ? rr : N - (rr - n64);
-    double a[4] = {0, 0, 0, 0}, a2[4] = {0, 0, 0, 0};   // even / odd ii: 8 chains
-#pragma unroll 8
-    for (int ii = 0; ii < Nr; ++ii) {
-      const double dv = Dr64[i * Nr + ii];
-      T u[4];
-      ld4<T>(Ub + ii * Si + w0, u);
+  // rows nearest the ends in double: the row pair (i, N-i) from the even / odd
+  // parts of the line, folded like the float rows (half the multiply-adds of two
+  // dense rows): row i = (Op O + Ep E)/2 + D[i][M] u_M, row N-i = (Op O - Ep E)/2 -
+  // D[i][M] u_M (the sums and differences of two floats are exact in double)
+  for (int v = threadIdx.x; v < n64 * W4; v += blockDim.x) {
+    const int w0 = (v % W4) * 4, i = v / W4;
+    double ae[4] = {0, 0, 0, 0}, ao[4] = {0, 0, 0, 0};
+#pragma unroll 4
+    for (int ii = 0; ii < hh; ++ii) {
+      const double ep = p.ep64[ii * hh + i], op = p.op64[ii * hh + i];
+      T a[4], b[4];
+      ld4<T>(Ub + ii * Si + w0, a);
+      ld4<T>(Ub + (N - ii) * Si + w0, b);
 #pragma unroll
       for (int cc = 0; cc < 4; ++cc) {
-        if (ii & 1) a2[cc] = fma(dv, (double)u[cc], a2[cc]);
-        else a[cc] = fma(dv, (double)u[cc], a[cc]);
+        ae[cc] = fma(ep, (double)a[cc] + (double)b[cc], ae[cc]);
+        ao[cc] = fma(op, (double)a[cc] - (double)b[cc], ao[cc]);
       }
     }
-    C r4[4] = {(C)(a[0] + a2[0]), (C)(a[1] + a2[1]), (C)(a[2] + a2[2]), (C)(a[3] + a2[3])};
-    st4<C>(sR + rr * W + w0, r4);
+    T um[4] = {0, 0, 0, 0};
+    if (odd) ld4<T>(Ub + (N / 2) * Si + w0, um);
+    const double dm = odd ? p.mc64[i] : 0.0;
+    C lo[4], hi[4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const double mid = dm * (double)um[cc];
+      lo[cc] = (C)(0.5 * (ao[cc] + ae[cc]) + mid);
+      hi[cc] = (C)(0.5 * (ao[cc] - ae[cc]) - mid);
+    }
+    st4<C>(sR + i * W + w0, lo);
+    st4<C>(sR + (n64 + i) * W + w0, hi);
   }
   __syncthreads();
   const int IR = hh / RB, units = IR * W4;

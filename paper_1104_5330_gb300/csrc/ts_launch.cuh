@@ -194,6 +194,10 @@ template <typename T, typename C>
 cudaError_t Launch<T, C>::angular(const Problem& p, const Tables<C>& t, const T* U, T* K, C sgn,
                                   bool collision, cudaStream_t s) {
   const Dims& d = p.d;
+  if constexpr (sizeof(T) == 4) {
+    if (p.tcang && d.NT == 16 && d.NP == 16 && kernel_form(p, collision ? 1 : 0) == KF_ISO)
+      return launch_angular_tc(p, t, U, K, sgn, collision, s);
+  }
   const bool rb = p.tp.rb & 1;
   const int nb = p.tp.nb > 0 ? p.tp.nb : angular_nb<T, C>(d, 1, rb);
   const long long ntiles = (d.nblk + nb - 1) / nb;

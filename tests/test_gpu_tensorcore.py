@@ -100,3 +100,45 @@ def test_operand_wait_timeout_is_reported_and_the_grid_recovers(prec):
     gg.step(Fg, dt, 5)
     ts.ts_sync_status(gg.handle)
     assert rel_l2(host(Fg), op.run(F0, dt, 5)) < 1e-5
+
+
+# 16 x 16 direction blocks: the angular pass also runs on the tensor cores for
+# TS_TF32X3 (8 blocks per tile; the last tile of these grids is ragged)
+ANG16 = [(0.2, 1.0, 9, 3, 2, 16, 16), (0.2, 1.0, 17, 4, 6, 16, 16), (0.2, 1.0, 33, 16, 16, 16, 16)]
+
+
+def _grid_tc_angular(dims, G, on):
+    import os
+    old = os.environ.get("TS_TC_ANGULAR")
+    os.environ["TS_TC_ANGULAR"] = "1" if on else "0"
+    try:
+        return pair(*dims, G=G, precision=3)
+    finally:
+        if old is None:
+            del os.environ["TS_TC_ANGULAR"]
+        else:
+            os.environ["TS_TC_ANGULAR"] = old
+
+
+@pytest.mark.parametrize("dims", ANG16)
+def test_tensor_core_angular_pass_against_oracle_and_simt(dims):
+    G = 3 if dims[2] < 33 else 4
+    og, tc = _grid_tc_angular(dims, G, True)
+    _, simt = _grid_tc_angular(dims, G, False)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, tc, kap, eta, ks, gR1, gR2)
+    simt.set_coeffs(kap, eta, ks, gR1, gR2)
+    F = F0 + 0.1 * np.random.default_rng(8).standard_normal(og.shape)
+    Kt = host(tc.rhs(cuda(F, torch.float32)))
+    T().ts_sync_status(tc.handle)
+    assert rel_l2(Kt, op.rhs(F)) < 1e-5
+    assert rel_l2(Kt, host(simt.rhs(cuda(F, torch.float32)))) < 2e-6
+    LF = host(tc.liouville(cuda(F, torch.float32)))
+    assert rel_l2(LF, og.liouville(F)) < 1e-5
+    dt = I.dt_rule(dims[0], dims[1], dims[2])
+    a, b = cuda(F0, torch.float32), cuda(F0, torch.float32)
+    tc.step(a, dt, 10)
+    simt.step(b, dt, 10)
+    T().ts_sync_status(tc.handle)
+    assert rel_l2(host(a), op.run(F0, dt, 10)) < 1e-5
+    assert rel_l2(host(a), host(b)) < 2e-6
