@@ -92,7 +92,8 @@ typedef enum {
                                  grid creation, ts_set_coeffs,
                                  ts_set_scattering_anisotropy, ts_apply_inflow,
                                  ts_reset_history, and a ts_step on a different F
-                                 pointer than the last one. Not in batches, no adjoint. */
+                                 pointer than the last one. Not in batches; its
+                                 adjoint is ts_adjoint_step_ab2. */
 } ts_scheme;
 
 typedef enum {
@@ -243,6 +244,29 @@ ts_status ts_liouville(ts_grid* grid, const void* F, void* LF, void* stream);
  * of the discrete step. Uses the grid's workspace. */
 ts_status ts_adjoint_step(ts_grid* grid, const void* F_n, void* lambda,
                           double* grad_kappa, double* grad_eta, double dt, void* stream);
+
+/* Discrete adjoint of one TS_AB2 step (filter off). The marching F_{n+1} =
+ * F_n + dt (3/2 K_n - 1/2 K_{n-1}) (Sect. 5.1), started by F_1 = F_0 + dt K_0,
+ * uses K_n = K(F_n) in step n (weight 3/2 dt; dt in the starting step) and in
+ * step n+1 (weight -1/2 dt). Given F_n, lambda = dObj/dF_{n+1} and lambda_prev =
+ * dObj/dF_{n+2} (zeros for the last step), with mu = dt (w lambda -
+ * lambda_prev/2), w = 1 if `first` (n = 0) else 3/2: overwrites lambda_prev with
+ * lambda and lambda with dObj/dF_n = lambda + A^T Tau^T mu (A the linear part of
+ * the stage derivative), and ADDS to grad_kappa and grad_eta ([G][Nr][Ntheta][Nphi])
+ * -sum_(Theta,Phi) (Tau^T mu) F_n and sum_(Theta,Phi) Tau^T mu. Walking n = N-1
+ * .. 0 with the recomputed states gives the gradients of an objective of F_N.
+ * The paper has no adjoint: this is the exact transpose of the discrete AB2
+ * step. Uses the grid's adjoint workspace. */
+ts_status ts_adjoint_step_ab2(ts_grid* grid, const void* F_n, void* lambda, void* lambda_prev,
+                              double* grad_kappa, double* grad_eta, double dt, int first,
+                              void* stream);
+
+/* Set the TS_AB2 history: the grid's next ts_step on the field F (the same device
+ * pointer) takes K_prev (device, the grid's element type and the layout of F) as
+ * K_{n-1} instead of starting with a forward-Euler step. Lets a caller resume
+ * AB2 from a saved state F_n and K_{n-1} = K(F_{n-1}) (ts_rhs), e.g. to
+ * recompute a checkpointed segment. TS_ERR_UNSUPPORTED for other schemes. */
+ts_status ts_set_history(ts_grid* grid, const void* F, const void* K_prev, void* stream);
 
 /* Weights w[Ntheta][Nphi][NTheta][NPhi] (device, double) such that the
  * outgoing radial flux J_R2 of Eq. (Flux), App. A, for group g is

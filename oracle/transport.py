@@ -720,6 +720,27 @@ class Problem:
         return lam_n, gk, ge
 
 
+    def adjoint_step_ab2(self, F_n, lam, lam_prev, dt, first):
+        """Discrete adjoint of one AB2 step (filter off). The forward marching
+        F_{n+1} = F_n + dt (3/2 K_n - 1/2 K_{n-1}) (n >= 1) and F_1 = F_0 + dt K_0
+        uses K_n = K(F_n) in step n (weight 3/2 dt, or dt in the starting step) and
+        in step n+1 (weight -1/2 dt). So with lam = dObj/dF_{n+1} and lam_prev =
+        dObj/dF_{n+2} (zero for the last step), the stage-derivative adjoint is
+        mu_n = dt (w lam - lam_prev/2), w = 1 if `first` (n = 0) else 3/2, and
+          dObj/dF_n = lam + A^T Tau^T mu_n,
+          g_kappa = -sum_(Th,Ph) (Tau^T mu_n) F_n,   g_eta = sum_(Th,Ph) Tau^T mu_n.
+        Returns (dObj/dF_n, g_kappa, g_eta); the caller then passes (dObj/dF_n,
+        lam) as (lam, lam_prev) of the step before."""
+        if self.filter_on:
+            raise NotImplementedError("adjoint covers steps without the filter")
+        self._q = self.g.quadrature_weights_direction()
+        mu = dt * ((1.0 if first else 1.5) * lam - 0.5 * lam_prev)
+        lt = self.g.tau_T(mu) if self.bc == "tau" else mu
+        ge = lt.sum(axis=(-2, -1))
+        gk = -(lt * F_n).sum(axis=(-2, -1))
+        return lam + self._A_T(lt), gk, ge
+
+
 def nucleon_scattering(A_n, A_p):
     """Scattering of neutrinos on neutrons and protons (Eqs. cross, crossnun,
     crossnup, Sect. 6): sigma^D = A_n (1 - omega.omega'/3) + A_p (1 - omega.omega'/10).

@@ -16,8 +16,8 @@ ts_outgoing_flux_adjoint as its backward.
 All tensors live on the grid's device; kappa, eta, kappa_s are float64
 [G][Nr][Ntheta][Nphi]; F has the grid's element type. The grid's scattering
 kernel (set with set_scattering_anisotropy / set_scattering_quadrupole) applies
-to the forward steps and to their adjoint alike; the grid must use the TS_RK4
-scheme on the Chebyshev radial grid (the adjoint's scope).
+to the forward steps and to their adjoint alike; the grid must use the TS_RK4 or
+TS_AB2 scheme on the Chebyshev radial grid, filter off (the adjoint's scope).
 """
 from __future__ import annotations
 
@@ -29,17 +29,31 @@ from . import ts as _ts
 
 
 class TransportSteps(torch.autograd.Function):
+    """RK4 grids checkpoint F at segment starts. AB2 grids (the paper's scheme)
+    checkpoint the pair (F_s, K_{s-1}) -- K of the state before, from ts_rhs -- so
+    that a segment's recomputation resumes the two-level marching through
+    ts_set_history; their backward walks ts_adjoint_step_ab2 with the two adjoint
+    levels (dObj/dF_{n+1}, dObj/dF_{n+2})."""
+
     @staticmethod
     def forward(ctx, F0, kappa, eta, grid, kappa_s, inflow_R1, inflow_R2, dt, nsteps, segment):
         grid.set_coeffs(kappa, eta, kappa_s, inflow_R1, inflow_R2)
+        ab2 = grid.desc.scheme == _ts.TS_AB2
         seg = segment or max(1, math.ceil(math.sqrt(nsteps)))
         F = F0.detach().clone().contiguous()
-        checkpoints = [F.clone()]
+        checkpoints = [(F.clone(), None)]
+        if ab2:
+            grid.reset_history()
         for n in range(nsteps):
+            Kh = None
+            if ab2 and (n + 1) % seg == 0 and n + 1 < nsteps:
+                Kh = torch.empty_like(F)
+                _ts.ts_rhs(grid.handle, F, Kh)          # K_n: the history of step n + 1
             _ts.ts_step(grid.handle, F, dt, 1)
             if (n + 1) % seg == 0 and n + 1 < nsteps:
-                checkpoints.append(F.clone())
+                checkpoints.append((F.clone(), Kh))
         ctx.grid = grid
+        ctx.ab2 = ab2
         ctx.dt, ctx.nsteps, ctx.seg = dt, nsteps, seg
         ctx.coeffs = (kappa.detach(), eta.detach(), kappa_s, inflow_R1, inflow_R2)
         ctx.checkpoints = checkpoints
@@ -47,23 +61,34 @@ class TransportSteps(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gF):
-        grid, dt, nsteps, seg = ctx.grid, ctx.dt, ctx.nsteps, ctx.seg
+        grid, dt, nsteps, seg, ab2 = ctx.grid, ctx.dt, ctx.nsteps, ctx.seg, ctx.ab2
         kappa, eta, kappa_s, g1, g2 = ctx.coeffs
         grid.set_coeffs(kappa, eta, kappa_s, g1, g2)       # the adjoint uses the forward's fields
         lam = gF.detach().to(grid.dtype).clone().contiguous()
+        lam_prev = torch.zeros_like(lam)
         gk = torch.zeros(grid.coef_shape, dtype=torch.float64, device=lam.device)
         ge = torch.zeros_like(gk)
         nseg = len(ctx.checkpoints)
         for s in range(nseg - 1, -1, -1):
             start = s * seg
             stop = min(nsteps, start + seg)
-            states = [ctx.checkpoints[s]]
-            F = ctx.checkpoints[s].clone()
+            F0s, Kh = ctx.checkpoints[s]
+            states = [F0s]
+            F = F0s.clone()
+            if ab2:
+                if Kh is None:
+                    grid.reset_history()
+                else:
+                    _ts.ts_set_history(grid.handle, F, Kh)
             for _ in range(start, stop - 1):
                 _ts.ts_step(grid.handle, F, dt, 1)
                 states.append(F.clone())
             for n in range(stop - 1, start - 1, -1):
-                _ts.ts_adjoint_step(grid.handle, states[n - start], lam, gk, ge, dt)
+                if ab2:
+                    _ts.ts_adjoint_step_ab2(grid.handle, states[n - start], lam, lam_prev, gk, ge,
+                                            dt, n == 0)
+                else:
+                    _ts.ts_adjoint_step(grid.handle, states[n - start], lam, gk, ge, dt)
             del states
         ctx.checkpoints = None
         return lam, gk, ge, None, None, None, None, None, None, None

@@ -751,6 +751,57 @@ cudaError_t run_adjoint(ts_grid* g, const Tables<C>& t, const T* Fn, T* lam, dou
   return e;
 }
 
+// mu = a lam + b lam_prev, then lam_prev = lam (the AB2 adjoint's stage weights and
+// the shift of its two time levels)
+template <typename T>
+__global__ void k_ab2_mu(const T* lam, T* lam_prev, T* mu, double a, double b, long long n) {
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < n;
+       x += (long long)gridDim.x * blockDim.x) {
+    const double l = (double)lam[x];
+    mu[x] = (T)(a * l + b * (double)lam_prev[x]);
+    lam_prev[x] = (T)l;
+  }
+}
+
+template <typename T, typename C>
+cudaError_t run_adjoint_ab2(ts_grid* g, const Tables<C>& t, const T* Fn, T* lam, T* lam_prev,
+                            double* gk, double* ge, double dt, bool first, cudaStream_t st) {
+  const ts::Problem p = make_problem(g);
+  const bool tau = g->desc.bc == TS_BC_TAU_INFLOW;
+  T* mu = static_cast<T*>(g->adj[3]);
+  T* lt = static_cast<T*>(g->adj[4]);
+  T* Ub = static_cast<T*>(g->adj[5]);
+  const long long n = g->d.total;
+  const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_ab2_mu<T><<<blocks, 256, 0, st>>>(lam, lam_prev, mu, dt * (first ? 1.0 : 1.5), -0.5 * dt, n);
+  cudaError_t e = cudaGetLastError();
+  // lam <- lam + A^T Tau^T mu; the gradients from Tau^T mu and F_n
+  if (e == cudaSuccess) e = Launch<T, C>::radial_T(p, t, mu, 1.0, tau, lt, Ub, st);
+  if (e == cudaSuccess) e = Launch<T, C>::plane_T(p, t, lt, Ub, st);
+  if (e == cudaSuccess)
+    e = Launch<T, C>::angular_T(p, t, lt, Ub, Fn, gk, ge, lam, lam, lam, nullptr, 0.0, 0.0, st);
+  return e;
+}
+
+ts_status adjoint_workspace(ts_grid* g) {
+  if (g->adj[0]) return TS_OK;
+  const char* poison = std::getenv("TS_POISON_WORKSPACE");   // see ts_create_grid
+  for (int a = 0; a < 7; ++a) {
+    cudaError_t e = cudaMalloc(&g->adj[a], field_bytes(g));
+    if (e == cudaSuccess && poison && poison[0] == '1')
+      e = cudaMemset(g->adj[a], 0xFF, field_bytes(g));
+    if (e != cudaSuccess) {
+      for (int b = 0; b <= a; ++b) {
+        if (g->adj[b]) cudaFree(g->adj[b]);
+        g->adj[b] = nullptr;
+      }
+      cudaGetLastError();
+      return fail(TS_ERR_OOM, "adjoint workspace allocation failed");
+    }
+  }
+  return TS_OK;
+}
+
 bool fits(const ts_grid_desc& g, size_t es) {
   const size_t mx = 227 * 1024;
   const size_t a = (size_t)(2 * g.NTheta * g.NTheta + g.NPhi * g.NPhi + 2 * g.NTheta * g.NPhi + 1) * es;
@@ -1233,6 +1284,43 @@ ts_status ts_liouville(ts_grid* g, const void* F, void* LF, void* stream) {
   return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_liouville");
 }
 
+ts_status ts_adjoint_step_ab2(ts_grid* g, const void* F_n, void* lambda, void* lambda_prev,
+                              double* grad_kappa, double* grad_eta, double dt, int first,
+                              void* stream) {
+  ts_status s = check_F(g, F_n);
+  if (s != TS_OK) return s;
+  if (!lambda || !lambda_prev || !grad_kappa || !grad_eta)
+    return fail(TS_ERR_ARG, "NULL adjoint argument");
+  if (!std::isfinite(dt)) return fail(TS_ERR_ARG, "dt must be finite");
+  if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
+  if (g->desc.scheme != TS_AB2 || g->desc.filter_on)
+    return fail(TS_ERR_UNSUPPORTED, "ts_adjoint_step_ab2 covers the TS_AB2 scheme without filter");
+  if (g->desc.radial != TS_RADIAL_CHEBYSHEV)
+    return fail(TS_ERR_UNSUPPORTED, "adjoint covers the Chebyshev radial grid");
+  s = adjoint_workspace(g);
+  if (s != TS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = g->es == 8
+      ? run_adjoint_ab2<double, double>(g, g->t64, (const double*)F_n, (double*)lambda,
+                                        (double*)lambda_prev, grad_kappa, grad_eta, dt, first != 0, st)
+      : run_adjoint_ab2<float, float>(g, g->t32, (const float*)F_n, (float*)lambda,
+                                      (float*)lambda_prev, grad_kappa, grad_eta, dt, first != 0, st);
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_adjoint_step_ab2");
+}
+
+ts_status ts_set_history(ts_grid* g, const void* F, const void* K_prev, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  if (!K_prev) return fail(TS_ERR_ARG, "K_prev is NULL");
+  if (g->desc.scheme != TS_AB2) return fail(TS_ERR_UNSUPPORTED, "the history belongs to TS_AB2");
+  cudaError_t e = cudaMemcpyAsync(g->Acc, K_prev, field_bytes(g), cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ts_set_history");
+  g->hist = true;
+  g->hist_F = F;
+  return TS_OK;
+}
+
 ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* grad_kappa,
                           double* grad_eta, double dt, void* stream) {
   ts_status s = check_F(g, F_n);
@@ -1244,22 +1332,8 @@ ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* gra
     return fail(TS_ERR_UNSUPPORTED, "adjoint covers the TS_RK4 scheme without filter");
   if (g->desc.radial != TS_RADIAL_CHEBYSHEV)
     return fail(TS_ERR_UNSUPPORTED, "adjoint covers the Chebyshev radial grid");
-  if (!g->adj[0]) {
-    const char* poison = std::getenv("TS_POISON_WORKSPACE");   // see ts_create_grid
-    for (int a = 0; a < 7; ++a) {
-      cudaError_t e = cudaMalloc(&g->adj[a], field_bytes(g));
-      if (e == cudaSuccess && poison && poison[0] == '1')
-        e = cudaMemset(g->adj[a], 0xFF, field_bytes(g));
-      if (e != cudaSuccess) {
-        for (int b = 0; b <= a; ++b) {
-          if (g->adj[b]) cudaFree(g->adj[b]);
-          g->adj[b] = nullptr;
-        }
-        cudaGetLastError();
-        return fail(TS_ERR_OOM, "adjoint workspace allocation failed");
-      }
-    }
-  }
+  s = adjoint_workspace(g);
+  if (s != TS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = g->es == 8
       ? run_adjoint<double, double>(g, g->t64, (const double*)F_n, (double*)lambda, grad_kappa, grad_eta, dt, st)

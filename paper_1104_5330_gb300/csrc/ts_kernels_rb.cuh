@@ -130,7 +130,10 @@ __host__ __device__ constexpr int ang_us(int NT, int NP) { return NP * ang_utp<C
 // Line lengths with compiled-in forms of the single-problem kernels (0: the
 // run-time form, which the batched kernel always uses). The two forms perform
 // the same operations; results agree to rounding, not bit for bit.
+// Square direction blocks (16, 24, 32) return N; the 24 x 16 blocks of the hybrid-grid
+// shell workload return 2416.
 __host__ __device__ inline int ang_spec(const Dims& d) {
+  if (d.NT == 24 && d.NP == 16) return 2416;
   if (d.NT != d.NP) return 0;
   return (d.NT == 16 || d.NT == 24 || d.NT == 32) ? d.NT : 0;
 }

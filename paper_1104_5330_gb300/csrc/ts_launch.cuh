@@ -207,6 +207,7 @@ cudaError_t Launch<T, C>::angular(const Problem& p, const Tables<C>& t, const T*
       case 16: return angular_pp<T, C, 16, 16>(p, t, U, K, sgn, col, nb, ntiles, s);
       case 24: return angular_pp<T, C, 24, 24>(p, t, U, K, sgn, col, nb, ntiles, s);
       case 32: return angular_pp<T, C, 32, 32>(p, t, U, K, sgn, col, nb, ntiles, s);
+      case 2416: return angular_pp<T, C, 24, 16>(p, t, U, K, sgn, col, nb, ntiles, s);
       default: return angular_pp<T, C, 0, 0>(p, t, U, K, sgn, col, nb, ntiles, s);
     }
   }

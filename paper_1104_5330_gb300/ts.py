@@ -76,6 +76,8 @@ def _load():
         "ts_rhs": [P, P, P, P],
         "ts_liouville": [P, P, P, P],
         "ts_adjoint_step": [P, P, P, P, P, D, P],
+        "ts_adjoint_step_ab2": [P, P, P, P, P, P, D, I, P],
+        "ts_set_history": [P, P, P, P],
         "ts_flux_weights": [P, P, P],
         "ts_outgoing_flux": [P, P, P, P],
         "ts_outgoing_flux_adjoint": [P, P, P, P],
@@ -243,6 +245,16 @@ def ts_liouville(grid, F, LF, stream=None):
 def ts_adjoint_step(grid, F_n, lam, grad_kappa, grad_eta, dt, stream=None):
     _check(LIB.ts_adjoint_step(grid, _ptr(F_n), _ptr(lam), _ptr(grad_kappa), _ptr(grad_eta),
                                float(dt), _stream(stream)), "ts_adjoint_step")
+
+
+def ts_adjoint_step_ab2(grid, F_n, lam, lam_prev, grad_kappa, grad_eta, dt, first, stream=None):
+    _check(LIB.ts_adjoint_step_ab2(grid, _ptr(F_n), _ptr(lam), _ptr(lam_prev), _ptr(grad_kappa),
+                                   _ptr(grad_eta), float(dt), int(bool(first)), _stream(stream)),
+           "ts_adjoint_step_ab2")
+
+
+def ts_set_history(grid, F, K_prev, stream=None):
+    _check(LIB.ts_set_history(grid, _ptr(F), _ptr(K_prev), _stream(stream)), "ts_set_history")
 
 
 def ts_flux_weights(grid, w, stream=None):

@@ -140,3 +140,69 @@ def test_outgoing_flux_backward_is_the_library_seed():
     expect = np.zeros(og.shape)
     expect[:, -1] = np.array([3.0, -1.0])[:, None, None, None, None] * og.outgoing_flux_weights()[None]
     assert rel_l2(host(F.grad), expect) < 1e-15
+
+
+@pytest.mark.parametrize("first", [False, True])
+def test_ab2_adjoint_step_matches_oracle(first):
+    """ts_adjoint_step_ab2 against the oracle's AB2 adjoint step (same F_n, lam,
+    lam_prev): dObj/dF_n, the shifted level and both gradients."""
+    og, gg = pair(0.2, 1.0, 11, 7, 10, 6, 12, G=2, scheme=2)
+    kap, eta, ks, F0, gR1, gR2 = _workload(og)
+    gg.set_coeffs(kap, eta, ks, gR1, gR2)
+    op = OProblem(og, kap, eta, ks, gR1, gR2, scheme="ab2")
+    rng = np.random.default_rng(41)
+    lam, lp = rng.standard_normal(og.shape), rng.standard_normal(og.shape)
+    dt = I.dt_rule(0.2, 1.0, og.Nr, 0.2)
+    L, LP = cuda(lam), cuda(lp)
+    gk = torch.zeros(gg.coef_shape, dtype=torch.float64, device="cuda")
+    ge = torch.zeros_like(gk)
+    T().ts_adjoint_step_ab2(gg.handle, cuda(F0), L, LP, gk, ge, dt, first)
+    lam_n, a, b = op.adjoint_step_ab2(F0, lam, lp, dt, first)
+    assert rel_l2(host(L), lam_n) < 1e-12
+    assert np.array_equal(host(LP), lam)
+    assert rel_l2(host(gk), a) < 1e-12 and rel_l2(host(ge), b) < 1e-12
+
+
+def test_ab2_gradients_match_oracle_adjoint_and_central_differences():
+    """Gradients of the outgoing flux after 9 AB2 steps (checkpoint segments of 3:
+    each recomputation resumes from (F_s, K_{s-1})) against the oracle's AB2
+    adjoint chain (1e-12) and central finite differences of the GPU forward (1e-6)."""
+    from paper_1104_5330_gb300.autograd import outgoing_flux
+    og, gg = pair(0.2, 1.0, 11, 7, 10, 6, 12, G=2, scheme=2)
+    kap, eta, ks, F0, gR1, gR2 = _workload(og)
+    dt = I.dt_rule(0.2, 1.0, og.Nr, 0.2)
+    n = 9
+    J1, gk, ge, _ = _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, n, segment=3)
+    J2, gk2, ge2, _ = _grads(gg, F0, kap, eta, ks, gR1, gR2, dt, n, segment=n)
+    assert rel_l2(host(gk), host(gk2)) < 1e-14 and rel_l2(host(ge), host(ge2)) < 1e-14
+    op = OProblem(og, kap, eta, ks, gR1, gR2, scheme="ab2")
+    Fs = [F0]
+    for _ in range(n):
+        Fs.append(op.step(Fs[-1], dt))
+    lam = np.zeros(og.shape)
+    lam[:, -1] = og.outgoing_flux_weights()
+    lp = np.zeros_like(lam)
+    GK, GE = np.zeros_like(kap), np.zeros_like(eta)
+    for m in range(n - 1, -1, -1):
+        ln, a, b = op.adjoint_step_ab2(Fs[m], lam, lp, dt, m == 0)
+        lp, lam = lam, ln
+        GK += a
+        GE += b
+    assert rel_l2(host(gk), GK) < 1e-12
+    assert rel_l2(host(ge), GE) < 1e-12
+
+    def J(k, e):
+        gg.set_coeffs(k, e, ks, gR1, gR2)
+        F = cuda(F0)
+        gg.step(F, dt, n)
+        return float(outgoing_flux(gg, F).sum())
+
+    v = np.broadcast_to(I.seeded_smooth(og.r, og.theta, og.phi, None, None, 99, og.R1, og.R2,
+                                        with_direction=False), kap.shape)
+    for base, grad, which in ((kap, host(gk), "kappa"), (eta, host(ge), "eta")):
+        eps = 1e-5 * np.linalg.norm(base) / np.linalg.norm(v)
+        if which == "kappa":
+            fd = (J(kap + eps * v, eta) - J(kap - eps * v, eta)) / (2 * eps)
+        else:
+            fd = (J(kap, eta + eps * v) - J(kap, eta - eps * v)) / (2 * eps)
+        assert abs(fd - float(np.sum(grad * v))) <= 1e-6 * abs(fd), which

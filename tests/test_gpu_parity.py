@@ -373,3 +373,18 @@ def test_stable_dt_is_the_oracle_power_iteration(dims):
     Fg = cuda(F0)
     gg.step(Fg, dt, 200)
     assert np.isfinite(host(Fg)).all() and np.abs(host(Fg)).max() < 10 * np.abs(F0).max()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_compiled_24x16_direction_blocks(precision, tol):
+    """N_Theta = 24, N_Phi = 16 (the hybrid-grid shell workload's direction grid) runs
+    an angular pass compiled for those line lengths: stage derivative and steps."""
+    og, gg = pair(0.2, 1.0, 17, 4, 6, 24, 16, G=2, precision=precision)
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    op = setup_both(og, gg, kap, eta, ks, gR1, gR2)
+    dt_ = torch.float64 if precision == 0 else torch.float32
+    assert rel_l2(host(gg.rhs(cuda(F0, dt_))), op.rhs(F0)) < tol
+    dt = I.dt_rule(0.2, 1.0, 17)
+    Fg = cuda(F0, dt_)
+    gg.step(Fg, dt, 10)
+    assert rel_l2(host(Fg), op.run(F0, dt, 10)) < tol

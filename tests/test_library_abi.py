@@ -61,6 +61,9 @@ def test_new_entry_points_reject_null_grids(T):
     assert T.LIB.ts_outgoing_flux_adjoint(None, None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_set_wait_limit(None, 0) == T.TS_ERR_ARG
     assert T.LIB.ts_stable_dt(None, None, 10, None, None, None) == T.TS_ERR_ARG
+    assert T.LIB.ts_adjoint_step_ab2(None, None, None, None, None, None, ctypes.c_double(0.1), 0,
+                                     None) == T.TS_ERR_ARG
+    assert T.LIB.ts_set_history(None, None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_cons2d_create(None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_cons2d_step(None, None, ctypes.c_double(0.1), 1, None) == T.TS_ERR_ARG
 

@@ -906,3 +906,49 @@ def test_power_iteration_finds_the_spectral_radius_and_a_stable_step():
     for _ in range(30):
         G = pr.rk4_step(G, 2.2 * dt)
     assert np.linalg.norm(G) > 1e3 * np.linalg.norm(x0)
+
+
+def test_ab2_adjoint_dot_product_and_finite_differences():
+    """The AB2 adjoint (from the AB2 recurrence, Sect. 5.1) against the forward:
+    for n steps from F_0, <dObj/dF_0, v> equals the directional derivative of
+    Obj = <w, F_n> along v (exact: the step is affine in F), and the kappa and
+    eta gradients equal central finite differences (eta: exact; kappa: 1e-6)."""
+    from oracle.transport import Grid, Problem
+    from paper_1104_5330_gb300 import inputs as I
+    g = Grid(0.2, 1.0, 9, 4, 4, 6, 6)
+    kap, eta, ks = I.absorber_fields(g.r, g.theta, g.phi, groups=1)
+    F0 = I.seeded_smooth(g.r, g.theta, g.phi, g.Theta, g.Phi, 7, 0.2, 1.0)[None]
+    gR1, gR2 = I.inflow_from(F0, g.NT)
+    rng = np.random.default_rng(12)
+    w = rng.standard_normal(g.shape)
+    dt, n = 0.5 * I.dt_rule(0.2, 1.0, 9, 0.2), 6
+
+    def run(k, e, F):
+        pr = Problem(g, k, e, ks, gR1, gR2, scheme="ab2")
+        Fs = [F]
+        for _ in range(n):
+            Fs.append(pr.step(Fs[-1], dt))
+        return pr, Fs
+
+    pr, Fs = run(kap, eta, F0)
+    lam, lam_prev = w.copy(), np.zeros_like(w)
+    GK, GE = np.zeros_like(kap), np.zeros_like(eta)
+    for m in range(n - 1, -1, -1):
+        lam_n, a, b = pr.adjoint_step_ab2(Fs[m], lam, lam_prev, dt, first=(m == 0))
+        lam_prev, lam = lam, lam_n
+        GK += a
+        GE += b
+    v = rng.standard_normal(g.shape)
+    J = lambda F: float(np.sum(w * F))
+    eps = 1e-3
+    fd = (J(run(kap, eta, F0 + eps * v)[1][-1]) - J(run(kap, eta, F0 - eps * v)[1][-1])) / (2 * eps)
+    assert abs(fd - np.sum(lam * v)) < 1e-11 * max(1.0, abs(fd))
+    vk = np.abs(rng.standard_normal(kap.shape))
+    for which, grad in (("kappa", GK), ("eta", GE)):
+        base = kap if which == "kappa" else eta
+        ep = 1e-5 * np.linalg.norm(base) / np.linalg.norm(vk)
+        if which == "kappa":
+            fd = (J(run(kap + ep * vk, eta, F0)[1][-1]) - J(run(kap - ep * vk, eta, F0)[1][-1])) / (2 * ep)
+        else:
+            fd = (J(run(kap, eta + ep * vk, F0)[1][-1]) - J(run(kap, eta - ep * vk, F0)[1][-1])) / (2 * ep)
+        assert abs(fd - np.sum(grad * vk)) < 1e-6 * abs(fd), (which, fd, np.sum(grad * vk))
