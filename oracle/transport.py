@@ -499,6 +499,121 @@ class GridUpwindR(Grid):
         raise NotImplementedError("no adjoint on the finite-difference radial grid")
 
 
+class GridZonedR(Grid):
+    """The three-zone radial grid of App. B: first-order upwind finite differences
+    on n_fd uniform nodes in each edge zone of width w = zone_width (R2 - R1), and
+    Chebyshev-Gauss-Lobatto differentiation on the n_sp = Nr - 2 (n_fd - 1) nodes
+    of the central zone [R1 + w, R2 - w]; neighbouring zones share their interface
+    node. Readings (the paper solves the central zone with its implicit radial
+    update; here every zone is explicit, RK4 as elsewhere):
+      * the rate at an interface node is the upstream zone's (the zone the
+        direction comes from), so the value stays continuous;
+      * the central zone takes that rate at its inflow interface by the Tau
+        method: its top Chebyshev coefficient is replaced so that its rate there
+        equals the upstream one. The non-radial parts of the rate are the same at
+        the node, so this is a correction of the radial derivative alone:
+          d(i) = dB(i) + (dFD(b) - dB(b)) T_N(x_i) / T_N(x_b)   (i in the central zone),
+        b the inflow interface, dB the Chebyshev derivative, dFD the upstream
+        zone's one-sided difference at b;
+      * the outer inflow nodes hold their data (zero rate), as on the hybrid grid;
+      * radial integrals: trapezoid in the edge zones, Clenshaw-Curtis in the
+        central one. No adjoint, no radial filter."""
+
+    def __init__(self, R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups=1, zone_nodes=30,
+                 zone_width=0.1):
+        super().__init__(R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups)
+        nA = zone_nodes
+        nB = Nr - 2 * (nA - 1)
+        if nA < 2 or nB < 3 or not (0.0 < zone_width < 0.5):
+            raise ValueError("need zone_nodes >= 2, Nr - 2 (zone_nodes - 1) >= 3, 0 < width < 1/2")
+        w = zone_width * (self.R2 - self.R1)
+        self.nA, self.nB, self.w = nA, nB, w
+        self.iB0, self.iB1 = nA - 1, nA - 1 + nB - 1          # interface nodes (global)
+        self.hA = w / (nA - 1)
+        self._gB = Grid(self.R1 + w, self.R2 - w, nB, 2, 2, NTheta, 2)
+        self.r = np.concatenate([self.R1 + self.hA * np.arange(nA), self._gB.r[1:-1],
+                                 self.R2 - w + self.hA * np.arange(nA)])
+
+    def _dB(self, F):
+        """Chebyshev derivative of the central zone (coefficient space, its own nodes)."""
+        FB = F[:, self.iB0:self.iB1 + 1]
+        gB = self._gB
+        c = _along(gB.cheb_S, FB, AX_R)
+        c = _along(gB.cheb_C, c, AX_R)
+        return _along(gB.cheb_V, c, AX_R)
+
+    def d_r_zoned(self, F):
+        """The radial derivative of every direction (see the class notes)."""
+        h = self.hA
+        nA, iB0, iB1, N = self.nA, self.iB0, self.iB1, self.Nr - 1
+        back = np.zeros_like(F)
+        back[:, 1:] = (F[:, 1:] - F[:, :-1]) / h       # valid inside the edge zones
+        fwd = np.zeros_like(F)
+        fwd[:, :-1] = (F[:, 1:] - F[:, :-1]) / h
+        dB = self._dB(F)
+        nB = self.nB
+        tN = np.cos(np.pi * (nB - 1 - np.arange(nB)))    # T_N on the central nodes (ascending)
+        out = np.zeros_like(F)
+        outward = np.cos(self.Theta) > 0
+        for kk in range(self.NT):
+            sl = (slice(None), slice(None), slice(None), slice(None), kk)
+            if outward[kk]:   # from R1: zone A backward, inflow interface iB0
+                out[sl][:, :iB0 + 1] = back[sl][:, :iB0 + 1]
+                b, dfd = 0, back[sl][:, iB0]
+                dz = dB[sl] + (dfd - dB[sl][:, b])[:, None] * (tN / tN[b])[None, :, None, None, None]
+                out[sl][:, iB0:iB1 + 1] = dz
+                out[sl][:, iB0] = dfd
+                out[sl][:, iB1 + 1:] = back[sl][:, iB1 + 1:]
+            else:             # from R2: zone C forward, inflow interface iB1
+                out[sl][:, iB1:] = fwd[sl][:, iB1:]
+                b, dfd = nB - 1, fwd[sl][:, iB1]
+                dz = dB[sl] + (dfd - dB[sl][:, b])[:, None] * (tN / tN[b])[None, :, None, None, None]
+                out[sl][:, iB0:iB1 + 1] = dz
+                out[sl][:, iB1] = dfd
+                out[sl][:, :iB0] = fwd[sl][:, :iB0]
+        return out
+
+    def liouville(self, F):
+        a_r, a_th, a_ph, a_Th, a_Ph = self.coefficients()
+        return (a_r * self.d_r_zoned(F) + a_th * self.d_th(F) + a_ph * self.d_ph(F)
+                + a_Th * self.d_Th(F) + a_Ph * self.d_Ph(F))
+
+    def tau(self, K, gdot=0.0):
+        """The outer inflow nodes hold the static inflow data: their rate is gdot."""
+        K = K.copy()
+        b_of_k = self._inflow_node_index()
+        for kk in range(self.NT):
+            K[:, b_of_k[kk], :, :, kk, :] = gdot
+        return K
+
+    def clenshaw_curtis_r(self, h, axis=AX_R):
+        """Trapezoid in the edge zones, Clenshaw-Curtis in the central one."""
+        wts = np.zeros(self.Nr)
+        tr = np.full(self.nA, self.hA)
+        tr[0] = tr[-1] = 0.5 * self.hA
+        wts[:self.nA] += tr
+        wts[self.iB1:] += tr
+        gB = self._gB
+        k = np.arange(self.nB)
+        ints = np.zeros(self.nB)
+        ev = k % 2 == 0
+        ints[ev] = 2.0 / (1.0 - k[ev].astype(float) ** 2)
+        wts[self.iB0:self.iB1 + 1] += (ints @ gB.cheb_S) * 0.5 * (gB.R2 - gB.R1)
+        return np.tensordot(h, wts, axes=([axis], [0]))
+
+    def _filter_r(self, F, alpha, order):
+        return F
+
+    def d_r(self, F):
+        raise NotImplementedError("the zoned radial derivative depends on the direction")
+
+    def liouville_T(self, mu):
+        raise NotImplementedError("no adjoint on the zoned radial grid")
+
+    def tau_T(self, mu):
+        raise NotImplementedError("no adjoint on the zoned radial grid")
+
+
 class Problem:
     """Grid + coefficient fields + boundary data + scheme options."""
 

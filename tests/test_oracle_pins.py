@@ -952,3 +952,48 @@ def test_ab2_adjoint_dot_product_and_finite_differences():
         else:
             fd = (J(run(kap, eta + ep * vk, F0)[1][-1]) - J(run(kap, eta - ep * vk, F0)[1][-1])) / (2 * ep)
         assert abs(fd - np.sum(grad * vk)) < 1e-6 * abs(fd), (which, fd, np.sum(grad * vk))
+
+
+def test_zoned_radial_grid_exact_identities():
+    """Three-zone radial grid (App. B): linear radial data have derivative 1 at
+    every node but the outer inflow node of each direction (upwind differences and
+    the Chebyshev derivative are exact, so the interface correction vanishes);
+    quadratic data give r_i + r_{i-1} (outward) or r_i + r_{i+1} (inward) in the
+    edge zones and, in the central zone, 2 r_i plus the upstream difference's
+    error carried by T_N (the Tau correction in closed form); the rate at each
+    interface is the upstream zone's; the radial rule integrates 1 and r exactly."""
+    from oracle.transport import GridZonedR
+    g = GridZonedR(0.5, 1.0, 2 * (6 - 1) + 13, 2, 2, 4, 2, zone_nodes=6, zone_width=0.1)
+    r = g.r
+    shape = g.shape
+    F1 = np.ascontiguousarray(np.broadcast_to(r[None, :, None, None, None, None], shape))
+    d1 = g.d_r_zoned(F1)
+    outward = np.cos(g.Theta) > 0
+    for kk in range(g.NT):
+        col = d1[0, :, 0, 0, kk, 0]
+        keep = np.arange(g.Nr) != (0 if outward[kk] else g.Nr - 1)
+        assert np.abs(col[keep] - 1.0).max() < 1e-12
+    F2 = F1 ** 2
+    d2 = g.d_r_zoned(F2)
+    nB = g.nB
+    tN = np.cos(np.pi * (nB - 1 - np.arange(nB)))
+    for kk in range(g.NT):
+        col = d2[0, :, 0, 0, kk, 0]
+        if outward[kk]:
+            i = np.arange(1, g.iB0 + 1)
+            assert np.abs(col[i] - (r[i] + r[i - 1])).max() < 1e-12
+            j = np.arange(g.iB1 + 1, g.Nr)
+            assert np.abs(col[j] - (r[j] + r[j - 1])).max() < 1e-12
+            b, dfd = 0, r[g.iB0] + r[g.iB0 - 1]
+        else:
+            i = np.arange(0, g.iB0)
+            assert np.abs(col[i] - (r[i] + r[i + 1])).max() < 1e-12
+            j = np.arange(g.iB1, g.Nr - 1)
+            assert np.abs(col[j] - (r[j] + r[j + 1])).max() < 1e-12
+            b, dfd = nB - 1, r[g.iB1] + r[g.iB1 + 1]
+        rB = r[g.iB0:g.iB1 + 1]
+        expect = 2 * rB + (dfd - 2 * rB[b]) * tN / tN[b]
+        assert np.abs(col[g.iB0:g.iB1 + 1] - expect).max() < 1e-11
+    one = np.ones((1, g.Nr))
+    assert abs(g.clenshaw_curtis_r(one, axis=1)[0] - 0.5) < 1e-14
+    assert abs(g.clenshaw_curtis_r(r[None], axis=1)[0] - 0.5 * (1.0 - 0.25)) < 1e-14
