@@ -505,23 +505,30 @@ def run_ab2(args, dims, stream, rk4_ms_per_step):
             "simulated_time_rate_vs_rk4": (dt / (ms / n)) / (dt_rk4 / rk4_ms_per_step)}
 
 
-def run_hybrid(args, stream):
+def run_hybrid(args, stream, zoned=False):
     """The 5-D shell run of Sect. 5.3 on the hybrid grid (first-order upwind
     differences in r on 129 uniform nodes, spectral angular axes 16 x 16 x 24 x 16,
     one group, FP64, RK4 at dt = 0.4 dr): empty shell 0.5 <= r <= 1, Lambert
     emission F0 cos(Theta) at R1, coherent scattering of optical depth 5 from a
-    plasma vanishing at R2. Reports the step rate and the radial pass's time."""
+    plasma vanishing at R2. Reports the step rate and the radial pass's time.
+    zoned: the same shell on the three-zone grid of App. B (30 + 65 + 30 radial
+    nodes, edge zones of width 0.1 (R2 - R1)), dt = 0.4 x the smallest spacing."""
+    import numpy as np
     import torch
     import paper_1104_5330_gb300.ts as ts
     from paper_1104_5330_gb300 import inputs as I
-    R1, R2, Nr, Nt, Np, NT, NP = 0.5, 1.0, 129, 16, 16, 24, 16
-    gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=1, precision=ts.TS_FP64,
-                 radial=ts.TS_RADIAL_UPWIND_FD)
+    R1, R2, Nr, Nt, Np, NT, NP = 0.5, 1.0, 123 if zoned else 129, 16, 16, 24, 16
+    if zoned:
+        gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=1, precision=ts.TS_FP64,
+                     radial=ts.TS_RADIAL_ZONED, zone_nodes=30, zone_width=0.1)
+    else:
+        gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=1, precision=ts.TS_FP64,
+                     radial=ts.TS_RADIAL_UPWIND_FD)
     r, th, ph, Th, Ph = gg.nodes()
     ks = I.shell_scattering(r, th, ph, R1, R2, 5.0)
     gR1, gR2 = I.lambert_inflow(Th, Nt, Np, NP)
     gg.set_coeffs(None, None, ks, gR1, gR2)
-    dt = 0.4 * (R2 - R1) / (Nr - 1)
+    dt = 0.4 * float(np.diff(r).min())
     F = gg.apply_inflow(torch.zeros(gg.shape, dtype=torch.float64, device="cuda"))
     gg.step(F, dt, args.warmup)
     torch.cuda.synchronize()
@@ -536,7 +543,10 @@ def run_hybrid(args, stream):
     return {"value": gg.points * args.steps / (ms * 1e-3), "unit": "point-updates/s",
             "ms_per_step": ms / args.steps, "dtype": "f64",
             "workload": f"Lambert shell, optical depth 5, {Nr}x{Nt}x{Np}x{NT}x{NP}, 1 group",
-            "radial": "first-order upwind differences on uniform nodes",
+            "radial": ("30 + 65 + 30 nodes: upwind differences in edge zones of width "
+                       "0.1 (R2 - R1), Chebyshev in the central zone" if zoned else
+                       "first-order upwind differences on uniform nodes"),
+            "dt": dt,
             "pass_ms_per_launch": {n: float(pm[a] / pn[a])
                                    for a, n in enumerate(("angular", "plane", "radial"))}}
 
@@ -865,6 +875,7 @@ def run_ours(args, dims, wname):
         line["anisotropic_scattering"] = run_anisotropic(args, dims, stream)
         line["ab2"] = run_ab2(args, dims, stream, ms / args.steps)
         line["hybrid_radial_fd"] = run_hybrid(args, stream)
+        line["zoned_radial"] = run_hybrid(args, stream, zoned=True)
     if not args.skip_batch:
         line["batch"] = run_batch(args, stream)
     if not args.skip_diff and args.diff_steps > 0:

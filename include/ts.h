@@ -103,7 +103,7 @@ typedef enum {
 
 typedef enum {
   TS_RADIAL_CHEBYSHEV = 0,  /* Chebyshev-Gauss-Lobatto nodes, spectral d_r (Sect. 5.1) */
-  TS_RADIAL_UPWIND_FD = 1   /* the hybrid grid of Sect. 5.3: N_r uniform nodes
+  TS_RADIAL_UPWIND_FD = 1,  /* the hybrid grid of Sect. 5.3: N_r uniform nodes
                                r_i = R1 + i (R2-R1)/(N_r-1), first-order one-sided
                                differences upstream of each direction (cos Theta > 0:
                                (F_i - F_{i-1})/dr, cos Theta < 0: (F_{i+1} - F_i)/dr);
@@ -112,6 +112,23 @@ typedef enum {
                                the trapezoid rule; no radial filter. TS_FP64 and
                                TS_FP32 only; no adjoint, no batches, no
                                ts_moments_noalloc (TS_ERR_UNSUPPORTED). */
+  TS_RADIAL_ZONED = 2       /* the three radial zones of App. B: zone_nodes uniform
+                               nodes with first-order upwind differences in each edge
+                               zone of width zone_width (R2-R1), and Chebyshev-Gauss-
+                               Lobatto differentiation on the Nr - 2 (zone_nodes - 1)
+                               nodes of the central zone [R1 + w, R2 - w] (the zones
+                               share their interface node; Nr counts every node). The
+                               rate at an interface node is the upstream zone's (the
+                               zone the direction comes from); the central zone takes
+                               it at its inflow interface by the Tau method (its top
+                               Chebyshev coefficient replaced so that its rate there
+                               equals the upstream one). The outer inflow nodes hold
+                               their data (zero rate). Radial integrals: trapezoid in
+                               the edge zones, Clenshaw-Curtis in the central one. The
+                               paper advances the central zone with an implicit
+                               radial update; here every zone is explicit (the grid's
+                               scheme). TS_FP64 and TS_FP32; no adjoint, no batches,
+                               no ts_moments_noalloc (TS_ERR_UNSUPPORTED). */
 } ts_radial;
 
 typedef struct {
@@ -125,6 +142,9 @@ typedef struct {
   double filter_alpha;                      /* sigma(k) = exp(-alpha (k/kmax)^order) */
   int filter_order;
   int radial;                               /* ts_radial (0: Chebyshev) */
+  int zone_nodes;                           /* TS_RADIAL_ZONED: nodes per edge zone (>= 2) */
+  double zone_width;                        /* TS_RADIAL_ZONED: edge-zone width / (R2-R1),
+                                               in (0, 1/2) */
 } ts_grid_desc;
 
 typedef struct ts_grid ts_grid;             /* opaque, library-owned */

@@ -440,9 +440,22 @@ HostTables build_tables(const ts_grid_desc& g) {
   const int Nr = g.Nr, Nt = g.Ntheta, Np = g.Nphi, NT = g.NTheta, NP = g.NPhi;
   const int N = Nr - 1;
   const bool fd = g.radial == TS_RADIAL_UPWIND_FD;
-  for (int i = 0; i < Nr; ++i)
-    h.r.push_back(fd ? g.R1 + (g.R2 - g.R1) * i / N
-                     : 0.5 * (g.R1 + g.R2) - 0.5 * (g.R2 - g.R1) * std::cos(M_PI * i / N));
+  const bool zoned = g.radial == TS_RADIAL_ZONED;
+  // zoned: edge zones of zone_nodes uniform nodes, width w; central Chebyshev zone
+  const int zA = g.zone_nodes, zB = Nr - 2 * (g.zone_nodes - 1);
+  const double zw = g.zone_width * (g.R2 - g.R1), zh = zoned ? zw / (zA - 1) : 0.0;
+  for (int i = 0; i < Nr; ++i) {
+    if (zoned) {
+      const double a = g.R1 + zw, b = g.R2 - zw;
+      if (i < zA) h.r.push_back(g.R1 + zh * i);
+      else if (i < zA - 1 + zB - 1) h.r.push_back(0.5 * (a + b) - 0.5 * (b - a) *
+                                                  std::cos(M_PI * (i - (zA - 1)) / (zB - 1)));
+      else h.r.push_back(b + zh * (i - (zA - 1 + zB - 1)));
+    } else {
+      h.r.push_back(fd ? g.R1 + (g.R2 - g.R1) * i / N
+                       : 0.5 * (g.R1 + g.R2) - 0.5 * (g.R2 - g.R1) * std::cos(M_PI * i / N));
+    }
+  }
   for (int j = 0; j < Nt; ++j) h.theta.push_back(M_PI * (j + 0.5) / Nt);
   for (int l = 0; l < Np; ++l) h.phi.push_back(2.0 * M_PI * l / Np);
   for (int k = 0; k < NT; ++k) h.Theta.push_back(M_PI * (k + 0.5) / NT);
@@ -457,7 +470,7 @@ HostTables build_tables(const ts_grid_desc& g) {
   const double fa = g.filter_alpha > 0 ? g.filter_alpha : 36.0;
   const int fo = g.filter_order > 0 ? g.filter_order : 16;
   h.Fr = cheb_filter(Nr, fa, fo);
-  if (fd) {   // no radial filter on the finite-difference grid
+  if (fd || zoned) {   // no radial filter on the finite-difference and zoned grids
     h.Fr.assign((size_t)Nr * Nr, 0.0);
     for (int i = 0; i < Nr; ++i) h.Fr[(size_t)i * Nr + i] = 1.0;
   }
@@ -498,6 +511,18 @@ HostTables build_tables(const ts_grid_desc& g) {
     const double w = fd ? (g.R2 - g.R1) / N * ((i == 0 || i == N) ? 0.5 : 1.0)
                         : cc[i] * 0.5 * (g.R2 - g.R1);
     h.wr.push_back(w * h.r[i] * h.r[i]);
+  }
+  if (zoned) {   // trapezoid in the edge zones, Clenshaw-Curtis in the central one
+    const Vec ccB = clenshaw_curtis(zB);
+    Vec w(Nr, 0.0);
+    const int iB0 = zA - 1, iB1 = zA - 1 + zB - 1;
+    for (int i = 0; i < zA; ++i) {
+      const double t = zh * ((i == 0 || i == zA - 1) ? 0.5 : 1.0);
+      w[i] += t;
+      w[iB1 + i] += t;
+    }
+    for (int j = 0; j < zB; ++j) w[iB0 + j] += ccB[j] * 0.5 * (g.R2 - g.R1 - 2 * zw);
+    for (int i = 0; i < Nr; ++i) h.wr[i] = w[i] * h.r[i] * h.r[i];
   }
   h.wth = fejer(Nt);
   even_odd_tables(h);
@@ -628,6 +653,11 @@ cudaError_t radial_pass(const ts_grid* g, const ts::Problem& p, const Tables<C>&
   if (g->desc.radial == TS_RADIAL_UPWIND_FD)
     return ts::launch_radial_fd<T, C>(p, t, U, K, sgn, tau, mode, F, Acc, Uout, out, dt,
                                       (g->desc.R2 - g->desc.R1) / (g->desc.Nr - 1), st);
+  if (g->desc.radial == TS_RADIAL_ZONED) {
+    const C* zt = static_cast<const C*>(sizeof(C) == 8 ? g->zt64 : g->zt32);
+    return ts::launch_radial_zoned<T, C>(p, t, zt, zt + (size_t)g->zB * g->zB, g->zA, g->zB,
+                                         g->zh, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, st);
+  }
   return Launch<T, C>::radial(p, t, g->t64.Dr, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, st);
 }
 
@@ -934,10 +964,18 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   if (g.scheme != TS_RK4 && g.scheme != TS_RK4_SPLIT_IMPLICIT && g.scheme != TS_AB2)
     return fail(TS_ERR_UNSUPPORTED, "unknown scheme");
   if (g.bc != TS_BC_TAU_INFLOW && g.bc != TS_BC_NONE) return fail(TS_ERR_UNSUPPORTED, "unknown bc");
-  if (g.radial != TS_RADIAL_CHEBYSHEV && g.radial != TS_RADIAL_UPWIND_FD)
+  if (g.radial != TS_RADIAL_CHEBYSHEV && g.radial != TS_RADIAL_UPWIND_FD &&
+      g.radial != TS_RADIAL_ZONED)
     return fail(TS_ERR_UNSUPPORTED, "unknown radial discretisation");
-  if (g.radial == TS_RADIAL_UPWIND_FD && g.precision != TS_FP64 && g.precision != TS_FP32)
-    return fail(TS_ERR_UNSUPPORTED, "the finite-difference radial grid runs in TS_FP64 or TS_FP32");
+  if (g.radial != TS_RADIAL_CHEBYSHEV && g.precision != TS_FP64 && g.precision != TS_FP32)
+    return fail(TS_ERR_UNSUPPORTED,
+                "the finite-difference and zoned radial grids run in TS_FP64 or TS_FP32");
+  if (g.radial == TS_RADIAL_ZONED &&
+      (g.zone_nodes < 2 || g.Nr - 2 * (g.zone_nodes - 1) < 3 || !(g.zone_width > 0.0) ||
+       !(g.zone_width < 0.5)))
+    return fail(TS_ERR_UNSUPPORTED,
+                "zoned radial grid: need zone_nodes >= 2, Nr - 2 (zone_nodes - 1) >= 3, "
+                "0 < zone_width < 1/2");
   const size_t es = g.precision == TS_FP64 ? 8 : 4;
   if (!fits(g, es)) return fail(TS_ERR_UNSUPPORTED, "grid too large for one shared-memory tile");
 
@@ -956,7 +994,7 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   {
     const char* gen = std::getenv("TS_GENERIC_PASSES");  // 1: plain passes only (testing)
     G->tp.rb = (gen && gen[0] == '1') ? 0 : ts::rb_mask(d, (int)es, g.precision == TS_FP32_R64 ? 2 : 0);
-    if (g.radial == TS_RADIAL_UPWIND_FD) G->tp.rb &= ~4;   // no even/odd radial form
+    if (g.radial != TS_RADIAL_CHEBYSHEV) G->tp.rb &= ~4;   // no even/odd radial form
     // fused angular + radial pass: float grids with the even/odd angular and radial
     // forms (not the tensor-core radial precisions) whose tile fits shared memory
     // (TS_FUSED=1 selects it; its contractions are not yet faster than the three
@@ -981,6 +1019,23 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
       e = cudaMalloc((void**)&G->tcang, w.size() * sizeof(float));
       if (e == cudaSuccess)
         e = cudaMemcpy(G->tcang, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+  }
+  if (e == cudaSuccess && g.radial == TS_RADIAL_ZONED) {
+    G->zA = g.zone_nodes;
+    G->zB = g.Nr - 2 * (g.zone_nodes - 1);
+    const double w = g.zone_width * (g.R2 - g.R1);
+    G->zh = w / (G->zA - 1);
+    Vec zt = cheb_diff(G->zB, g.R1 + w, g.R2 - w);
+    for (int j = 0; j < G->zB; ++j) zt.push_back(((G->zB - 1 - j) % 2) ? -1.0 : 1.0);
+    e = cudaMalloc(&G->zt64, zt.size() * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(G->zt64, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && g.precision != TS_FP64) {
+      std::vector<float> zf(zt.begin(), zt.end());
+      e = cudaMalloc(&G->zt32, zf.size() * sizeof(float));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(G->zt32, zf.data(), zf.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
   }
   if (e == cudaSuccess && g.precision == TS_BF16X3) {
@@ -1026,7 +1081,7 @@ ts_status ts_destroy_grid(ts_grid* g) {
   cudaDeviceSynchronize();
   void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
                   g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err, g->tcb16,
-                  g->scb, g->scc, g->tcang};
+                  g->scb, g->scc, g->tcang, g->zt64, g->zt32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : g->adj)

@@ -27,7 +27,7 @@ TS_OK, TS_ERR_ARG, TS_ERR_UNSUPPORTED, TS_ERR_OOM, TS_ERR_CUDA, TS_ERR_TIMEOUT, 
 TS_FP64, TS_FP32, TS_FP32_R64, TS_TF32X3, TS_BF16X3 = 0, 1, 2, 3, 4
 TS_RK4, TS_RK4_SPLIT_IMPLICIT, TS_AB2 = 0, 1, 2
 TS_BC_TAU_INFLOW, TS_BC_NONE = 0, 1
-TS_RADIAL_CHEBYSHEV, TS_RADIAL_UPWIND_FD = 0, 1
+TS_RADIAL_CHEBYSHEV, TS_RADIAL_UPWIND_FD, TS_RADIAL_ZONED = 0, 1, 2
 
 STATUS_NAMES = ["TS_OK", "TS_ERR_ARG", "TS_ERR_UNSUPPORTED", "TS_ERR_OOM", "TS_ERR_CUDA",
                 "TS_ERR_TIMEOUT", "TS_ERR_STATE"]
@@ -46,7 +46,8 @@ class GridDesc(ctypes.Structure):
                 ("NTheta", ctypes.c_int), ("NPhi", ctypes.c_int), ("groups", ctypes.c_int),
                 ("precision", ctypes.c_int), ("scheme", ctypes.c_int), ("bc", ctypes.c_int),
                 ("filter_on", ctypes.c_int), ("filter_alpha", ctypes.c_double),
-                ("filter_order", ctypes.c_int), ("radial", ctypes.c_int)]
+                ("filter_order", ctypes.c_int), ("radial", ctypes.c_int),
+                ("zone_nodes", ctypes.c_int), ("zone_width", ctypes.c_double)]
 
 
 class Cons2DDesc(ctypes.Structure):
@@ -339,9 +340,11 @@ class Grid:
 
     def __init__(self, R1=0.2, R2=1.0, Nr=17, Ntheta=8, Nphi=8, NTheta=8, NPhi=8, groups=1,
                  precision=TS_FP64, scheme=TS_RK4, bc=TS_BC_TAU_INFLOW, filter_on=False,
-                 filter_alpha=36.0, filter_order=16, device=None, radial=TS_RADIAL_CHEBYSHEV):
+                 filter_alpha=36.0, filter_order=16, device=None, radial=TS_RADIAL_CHEBYSHEV,
+                 zone_nodes=0, zone_width=0.0):
         self.desc = GridDesc(R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups, precision, scheme,
-                             bc, int(filter_on), filter_alpha, filter_order, radial)
+                             bc, int(filter_on), filter_alpha, filter_order, radial, zone_nodes,
+                             zone_width)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             self.handle = ts_create_grid(self.desc)

@@ -34,7 +34,12 @@ def _desc(T, **kw):
     (dict(Nr=2), 2), (dict(Nr=200), 2), (dict(Nphi=7), 2), (dict(NTheta=5), 2),
     (dict(NPhi=3), 2), (dict(NTheta=66), 2), (dict(R1=0.0), 1), (dict(R2=0.1), 1),
     (dict(groups=0), 1), (dict(precision=9), 2), (dict(scheme=4), 2), (dict(bc=3), 2),
-    (dict(radial=2), 2), (dict(radial=1, precision=3), 2), (dict(radial=1, precision=2), 2),
+    (dict(radial=3), 2), (dict(radial=1, precision=3), 2), (dict(radial=1, precision=2), 2),
+    (dict(radial=2), 2), (dict(radial=2, zone_nodes=1, zone_width=0.1), 2),
+    (dict(radial=2, zone_nodes=5, zone_width=0.1), 2),
+    (dict(radial=2, zone_nodes=3, zone_width=0.5), 2),
+    (dict(radial=2, zone_nodes=3, zone_width=float("nan")), 2),
+    (dict(radial=2, zone_nodes=3, zone_width=0.1, precision=4), 2),
 ])
 def test_create_grid_rejects_bad_descriptors(T, kw, status):
     h = ctypes.c_void_p()
