@@ -366,12 +366,16 @@ ts_status ts_tile_shape(const ts_grid* grid, int* angular_blocks, int* plane_pai
 /* ---------------------------------------------------------------- batches
  * Many independent problems of uneven sizes (each with its own grid
  * description, energy groups, scheme and coefficients; one precision for the
- * whole batch) stepped together. Each pass of a stage is one persistent
- * launch whose CTAs take tiles of every problem from an atomic work queue; a
- * step is captured once into a CUDA graph and replayed. Results equal those
- * of ts_step on each problem's grid to rounding (the same operations; the
- * batched kernel runs the run-time-size form of each pass), and replaying the
- * graph reproduces them bit for bit. (The paper steps one problem at a time;
+ * whole batch) stepped together. Problems of fewer than 2^22 points share one
+ * persistent launch per pass of a stage, whose CTAs take tiles of every such
+ * problem from an atomic work queue (the run-time-size form of each pass);
+ * larger problems, which fill the GPU on their own, are stepped by their
+ * grid's own passes (the compiled line-length forms where the sizes have them).
+ * A step is captured into a CUDA graph and replayed (captured again when a
+ * field pointer, a dt or a problem's coefficients change). Results equal those
+ * of ts_step on each problem's grid to rounding (bit for bit for the large
+ * problems: the same launches), and replaying the graph reproduces them bit for
+ * bit. (The paper steps one problem at a time;
  * batching is a property of this library.) */
 typedef struct ts_batch ts_batch;
 

@@ -937,6 +937,11 @@ cudaError_t power_iteration(ts_grid* g, const Tables<C>& t, const T* x0, int ite
 
 }  // namespace
 
+cudaError_t ts::step_grid(ts_grid* g, void* F, double dt, int nsteps, cudaStream_t st) {
+  return g->es == 8 ? run_steps<double, double>(g, g->t64, (double*)F, dt, nsteps, st)
+                    : run_steps<float, float>(g, g->t32, (float*)F, dt, nsteps, st);
+}
+
 extern "C" {
 
 const char* ts_last_error(void) { return g_err.c_str(); }

@@ -217,10 +217,18 @@ cudaError_t set_batch_attrs() {
 
 }  // namespace ts
 
+// Problems with at least this many points fill the GPU on their own: the batch
+// steps them with their grid's single-problem passes (the compiled line-length
+// forms where the sizes have them), recorded into the batch's graph; the
+// smaller ones share the persistent work-queue launches.
+constexpr long long kBatchOwnPassesPoints = 1LL << 22;
+
 struct ts_batch {
   int n = 0;
   size_t es = 8;
   std::vector<ts_grid*> grids;
+  std::vector<int> queued;   // problems stepped by the work-queue launches (the rest: own passes)
+  std::vector<char> own;     // own[q]: problem q is stepped by its grid's passes
   void* items_dev = nullptr;
   void* items_host = nullptr;  // pinned staging copy of the item table
   size_t items_bytes = 0;
@@ -252,9 +260,10 @@ template <typename T, typename C>
 void fill_items(ts_batch* b, void* const* F, const double* dt) {
   BatchItem<T, C>* it = static_cast<BatchItem<T, C>*>(b->items_host);
   long long off[4] = {0, 0, 0, 0};
-  for (int q = 0; q < b->n; ++q) {
+  for (size_t k = 0; k < b->queued.size(); ++k) {
+    const int q = b->queued[k];
     ts_grid* g = b->grids[q];
-    BatchItem<T, C>& x = it[q];
+    BatchItem<T, C>& x = it[k];
     x.p = ts::problem_of(g);
     x.p.tp = ts::resolve<T, C>(g->d, g->tp);
     x.t = tables_of<T, C>(g);
@@ -282,7 +291,8 @@ cudaError_t layout_batch(ts_batch* b) {
   cudaError_t ea = ts::set_batch_attrs<T, C>();
   if (ea != cudaSuccess) return ea;
   size_t sm[3] = {0, 0, 0};
-  for (ts_grid* g : b->grids) {
+  for (int q : b->queued) {
+    ts_grid* g = b->grids[q];
     const ts::TileParams tp = ts::resolve<T, C>(g->d, g->tp);
     sm[0] = std::max(sm[0], ts::smem_angular<C>(g->d, tp.nb, tp.rb & 1));
     sm[1] = std::max(sm[1], ts::smem_plane<C>(g->d, tp.c, tp.rb & 2));
@@ -309,17 +319,24 @@ cudaError_t layout_batch(ts_batch* b) {
 template <typename T, typename C>
 cudaError_t enqueue_step(ts_batch* b, cudaStream_t st) {
   const BatchItem<T, C>* items = static_cast<const BatchItem<T, C>*>(b->items_dev);
-  cudaError_t e = cudaMemsetAsync(b->counters, 0, 13 * sizeof(unsigned long long), st);
-  for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
-    ts::k_batch_pass<T, C, 0><<<b->ctas[0], ts::kThreads, b->smem[0], st>>>(items, b->n, b->total[0], b->counters + 3 * s + 0, s);
-    ts::k_batch_pass<T, C, 1><<<b->ctas[1], ts::kThreads, b->smem[1], st>>>(items, b->n, b->total[1], b->counters + 3 * s + 1, s);
-    ts::k_batch_pass<T, C, 2><<<b->ctas[2], ts::kThreads, b->smem[2], st>>>(items, b->n, b->total[2], b->counters + 3 * s + 2, s);
-    e = cudaGetLastError();
+  const int ni = (int)b->queued.size();
+  cudaError_t e = cudaSuccess;
+  if (ni > 0) {
+    e = cudaMemsetAsync(b->counters, 0, 13 * sizeof(unsigned long long), st);
+    for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+      ts::k_batch_pass<T, C, 0><<<b->ctas[0], ts::kThreads, b->smem[0], st>>>(items, ni, b->total[0], b->counters + 3 * s + 0, s);
+      ts::k_batch_pass<T, C, 1><<<b->ctas[1], ts::kThreads, b->smem[1], st>>>(items, ni, b->total[1], b->counters + 3 * s + 1, s);
+      ts::k_batch_pass<T, C, 2><<<b->ctas[2], ts::kThreads, b->smem[2], st>>>(items, ni, b->total[2], b->counters + 3 * s + 2, s);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && b->any_split) {
+      ts::k_batch_pass<T, C, 3><<<b->ctas[3], ts::kThreads, 0, st>>>(items, ni, b->total[3], b->counters + 12, 0);
+      e = cudaGetLastError();
+    }
   }
-  if (e == cudaSuccess && b->any_split) {
-    ts::k_batch_pass<T, C, 3><<<b->ctas[3], ts::kThreads, 0, st>>>(items, b->n, b->total[3], b->counters + 12, 0);
-    e = cudaGetLastError();
-  }
+  // the large problems: one step of each by its grid's own passes
+  for (int q = 0; q < b->n && e == cudaSuccess; ++q)
+    if (b->own[q]) e = ts::step_grid(b->grids[q], b->lastF[q], b->lastdt[q], 1, st);
   return e;
 }
 
@@ -337,6 +354,12 @@ ts_status batch_step(ts_batch* b, void* const* F, const double* dt, int nsteps, 
     b->lastdt.assign(dt, dt + b->n);
     b->lastgen.resize(b->n);
     for (int q = 0; q < b->n; ++q) b->lastgen[q] = b->grids[q]->gen;
+    // the large problems' launches carry their fields and steps in their
+    // arguments: record the graph again
+    if (b->exec && b->queued.size() < (size_t)b->n) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
   }
   e = cudaEventRecord(b->ev_in, user);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev_in, 0);
@@ -447,6 +470,11 @@ ts_status ts_batch_create(const ts_grid_desc* descs, int n, int autotune, ts_bat
     }
   }
   b->es = b->grids[0]->es;
+  b->own.assign(n, 0);
+  for (int q = 0; q < n; ++q) {
+    if ((long long)b->grids[q]->d.total >= kBatchOwnPassesPoints) b->own[q] = 1;
+    else b->queued.push_back(q);
+  }
   b->items_bytes = (size_t)n * (b->es == 8 ? sizeof(BatchItem<double, double>) : sizeof(BatchItem<float, float>));
   cudaError_t e = cudaMalloc(&b->items_dev, b->items_bytes);
   if (e == cudaSuccess) e = cudaMallocHost(&b->items_host, b->items_bytes);

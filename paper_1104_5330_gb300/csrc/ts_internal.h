@@ -306,4 +306,8 @@ struct ts_grid {
 
 namespace ts {
 Problem problem_of(const ts_grid* g);
+// nsteps steps of the device field F on `st` by the grid's own single-problem
+// passes (the compiled line-length forms where the sizes have them); kernel
+// launches only, so a stream capture can record them.
+cudaError_t step_grid(ts_grid* g, void* F, double dt, int nsteps, cudaStream_t st);
 }  // namespace ts

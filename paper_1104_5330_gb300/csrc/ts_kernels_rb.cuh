@@ -1314,37 +1314,39 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
       st4<C>(sMid + 4 * x, m);
     }
   }
-  // rows nearest the ends in double: the row pair (i, N-i) from the even / odd
-  // parts of the line, folded like the float rows (half the multiply-adds of two
-  // dense rows): row i = (Op O + Ep E)/2 + D[i][M] u_M, row N-i = (Op O - Ep E)/2 -
-  // D[i][M] u_M (the sums and differences of two floats are exact in double)
-  for (int v = threadIdx.x; v < n64 * W4; v += blockDim.x) {
-    const int w0 = (v % W4) * 4, i = v / W4;
-    double ae[4] = {0, 0, 0, 0}, ao[4] = {0, 0, 0, 0};
+  // rows nearest the ends in double: the row pairs (i, N-i), i < n64, from the
+  // even / odd parts of the line, folded like the float rows (half the
+  // multiply-adds of two dense rows): row i = (Op O + Ep E)/2 + D[i][M] u_M,
+  // row N-i = (Op O - Ep E)/2 - D[i][M] u_M. One thread per column forms each
+  // even / odd value once, in double (the sum and difference of two floats are
+  // exact there), and feeds it to every pair: two conversions, two additions and
+  // 2 n64 multiply-adds per line point pair.
+  if (n64 > 0) {
+    constexpr int M64 = 2;   // at most two pairs (TS_FP32_R64)
+    for (int w = threadIdx.x; w < Wc; w += blockDim.x) {
+      double ae[M64] = {0, 0}, ao[M64] = {0, 0};
 #pragma unroll 4
-    for (int ii = 0; ii < hh; ++ii) {
-      const double ep = p.ep64[ii * hh + i], op = p.op64[ii * hh + i];
-      T a[4], b[4];
-      ld4<T>(Ub + ii * Si + w0, a);
-      ld4<T>(Ub + (N - ii) * Si + w0, b);
+      for (int ii = 0; ii < hh; ++ii) {
+        const double a = (double)Ub[ii * Si + w], b = (double)Ub[(N - ii) * Si + w];
+        const double e = a + b, o = a - b;
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        ae[cc] = fma(ep, (double)a[cc] + (double)b[cc], ae[cc]);
-        ao[cc] = fma(op, (double)a[cc] - (double)b[cc], ao[cc]);
+        for (int q = 0; q < M64; ++q) {
+          if (q < n64) {
+            ae[q] = fma(p.ep64[ii * hh + q], e, ae[q]);
+            ao[q] = fma(p.op64[ii * hh + q], o, ao[q]);
+          }
+        }
+      }
+      const double um = odd ? (double)Ub[(N / 2) * Si + w] : 0.0;
+#pragma unroll
+      for (int q = 0; q < M64; ++q) {
+        if (q < n64) {
+          const double mid = odd ? p.mc64[q] * um : 0.0;
+          sR[q * W + w] = (C)(0.5 * (ao[q] + ae[q]) + mid);
+          sR[(n64 + q) * W + w] = (C)(0.5 * (ao[q] - ae[q]) - mid);
+        }
       }
     }
-    T um[4] = {0, 0, 0, 0};
-    if (odd) ld4<T>(Ub + (N / 2) * Si + w0, um);
-    const double dm = odd ? p.mc64[i] : 0.0;
-    C lo[4], hi[4];
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const double mid = dm * (double)um[cc];
-      lo[cc] = (C)(0.5 * (ao[cc] + ae[cc]) + mid);
-      hi[cc] = (C)(0.5 * (ao[cc] - ae[cc]) - mid);
-    }
-    st4<C>(sR + i * W + w0, lo);
-    st4<C>(sR + (n64 + i) * W + w0, hi);
   }
   __syncthreads();
   const int IR = hh / RB, units = IR * W4;

@@ -1,5 +1,6 @@
-"""Batched steps of uneven problems (one persistent launch per pass over every
-problem's tiles, graph-captured) and the tile-shape autotuner.
+"""Batched steps of uneven problems (one persistent launch per pass over the
+tiles of every problem below 2^22 points, the larger ones by their grid's own
+passes; graph-captured) and the tile-shape autotuner.
 
 Bars: the batched step performs the single-problem step's operations on each
 problem's grid (the batched kernel runs the run-time-size form of each pass,
@@ -127,6 +128,52 @@ def test_batch_reuses_its_graph_with_new_fields_and_steps():
     for q in range(3):
         assert torch.equal(Fs[q], F2[q])
         assert rel_l2(host(Fs[q]), host(ref[q])) <= 2e-6
+    b.close()
+
+
+# a problem of at least 2^22 points: the batch steps it with its grid's own passes
+LARGE = (33, 16, 16, 16, 16, 2, 3.0)
+
+
+@pytest.mark.parametrize("precision,scheme", [(0, 0), (2, 1)])
+def test_batch_steps_large_problems_with_their_own_passes(precision, scheme):
+    """A batch of small problems (work queue) and one of 4.3M points (its grid's
+    own compiled passes, recorded into the batch's graph): the large problem is
+    bit-identical to the single-problem step, the small ones agree to rounding,
+    new fields and steps record the graph again, and in FP64 the large problem
+    matches the oracle."""
+    ts = T()
+    specs = [SPECS[0], LARGE, SPECS[3]]
+    b = ts.Batch(_descs(precision, scheme, specs), autotune=False)
+    assert b.grids[1].points >= 1 << 22 and b.grids[0].points < 1 << 22
+    dtype = torch.float64 if precision == 0 else torch.float32
+    ogs, data, Fs, dts = _setup(b, specs, dtype)
+    ref = [F.clone() for F in Fs]
+    b.step(Fs, dts, 3)
+    torch.cuda.synchronize()
+    for q, g in enumerate(b.grids):
+        g.step(ref[q], dts[q], 3)
+    torch.cuda.synchronize()
+    tol = 1e-13 if precision == 0 else 2e-6
+    assert torch.equal(Fs[1], ref[1])
+    for q in (0, 2):
+        assert rel_l2(host(Fs[q]), host(ref[q])) <= tol, q
+    if precision == 0:
+        kap, eta, ks, F0, gR1, gR2 = data[1]
+        oref = OProblem(ogs[1], kap, eta, ks, gR1, gR2).run(F0, dts[1], 3)
+        assert rel_l2(host(Fs[1]), oref) < 1e-12
+    # new field pointers and steps
+    F2 = [cuda(d[3], dtype) for d in data]
+    dt2 = [0.5 * d for d in dts]
+    ref2 = [F.clone() for F in F2]
+    b.step(F2, dt2, 2)
+    torch.cuda.synchronize()
+    for q, g in enumerate(b.grids):
+        g.step(ref2[q], dt2[q], 2)
+    torch.cuda.synchronize()
+    assert torch.equal(F2[1], ref2[1])
+    for q in (0, 2):
+        assert rel_l2(host(F2[q]), host(ref2[q])) <= tol, q
     b.close()
 
 
