@@ -32,7 +32,10 @@
  *    Coefficient fields, gradients and moments are always double.
  *  - Pointers are DEVICE pointers unless the name ends in _host. The caller
  *    owns every pointer it passes; the library owns the grid (tables and
- *    workspace) from ts_create_grid to ts_destroy_grid.
+ *    workspace) from ts_create_grid to ts_destroy_grid. Device fields (F, K,
+ *    LF, lambda, lambda_prev, x0) must be 16-byte aligned (every cudaMalloc
+ *    and PyTorch allocation is; the passes use 16-byte vector accesses);
+ *    otherwise TS_ERR_ARG.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *    stream). Calls are asynchronous on that stream unless stated otherwise.
  *  - Argument errors are returned synchronously and leave the device state

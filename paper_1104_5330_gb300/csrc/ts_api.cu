@@ -843,6 +843,14 @@ bool fits(const ts_grid_desc& g, size_t es) {
 ts_status check_F(const ts_grid* g, const void* F) {
   if (!g) return fail(TS_ERR_ARG, "grid is NULL");
   if (!F) return fail(TS_ERR_ARG, "field pointer is NULL");
+  if (!ts::aligned16(F)) return fail(TS_ERR_ARG, "field pointer is not 16-byte aligned");
+  return TS_OK;
+}
+
+// A device output or adjoint field: non-NULL and 16-byte aligned.
+ts_status check_out(const void* p, const char* what) {
+  if (!p) return fail(TS_ERR_ARG, std::string(what) + " is NULL");
+  if (!ts::aligned16(p)) return fail(TS_ERR_ARG, std::string(what) + " is not 16-byte aligned");
   return TS_OK;
 }
 
@@ -1239,8 +1247,9 @@ ts_status ts_step_profile(ts_grid* g, void* F, double dt, int nsteps, double* pa
 }
 
 ts_status ts_step_host(ts_grid* g, void* F_host, double dt, int nsteps, void* stream) {
-  ts_status s = check_F(g, F_host);
-  if (s != TS_OK) return s;
+  if (!g) return fail(TS_ERR_ARG, "grid is NULL");
+  if (!F_host) return fail(TS_ERR_ARG, "field pointer is NULL");
+  ts_status s = TS_OK;
   if (!std::isfinite(dt) || nsteps < 0) return fail(TS_ERR_ARG, "need finite dt, nsteps >= 0");
   if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1326,7 +1335,8 @@ ts_status ts_step_host(ts_grid* g, void* F_host, double dt, int nsteps, void* st
 ts_status ts_rhs(ts_grid* g, const void* F, void* K, void* stream) {
   ts_status s = check_F(g, F);
   if (s != TS_OK) return s;
-  if (!K) return fail(TS_ERR_ARG, "K is NULL");
+  s = check_out(K, "K");
+  if (s != TS_OK) return s;
   if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = g->es == 8 ? run_rhs<double, double>(g, g->t64, (const double*)F, (double*)K, false, st)
@@ -1337,7 +1347,8 @@ ts_status ts_rhs(ts_grid* g, const void* F, void* K, void* stream) {
 ts_status ts_liouville(ts_grid* g, const void* F, void* LF, void* stream) {
   ts_status s = check_F(g, F);
   if (s != TS_OK) return s;
-  if (!LF) return fail(TS_ERR_ARG, "LF is NULL");
+  s = check_out(LF, "LF");
+  if (s != TS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = g->es == 8 ? run_rhs<double, double>(g, g->t64, (const double*)F, (double*)LF, true, st)
                              : run_rhs<float, float>(g, g->t32, (const float*)F, (float*)LF, true, st);
@@ -1351,6 +1362,8 @@ ts_status ts_adjoint_step_ab2(ts_grid* g, const void* F_n, void* lambda, void* l
   if (s != TS_OK) return s;
   if (!lambda || !lambda_prev || !grad_kappa || !grad_eta)
     return fail(TS_ERR_ARG, "NULL adjoint argument");
+  if (!ts::aligned16(lambda) || !ts::aligned16(lambda_prev))
+    return fail(TS_ERR_ARG, "lambda and lambda_prev must be 16-byte aligned");
   if (!std::isfinite(dt)) return fail(TS_ERR_ARG, "dt must be finite");
   if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   if (g->desc.scheme != TS_AB2 || g->desc.filter_on)
@@ -1386,6 +1399,7 @@ ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* gra
   ts_status s = check_F(g, F_n);
   if (s != TS_OK) return s;
   if (!lambda || !grad_kappa || !grad_eta) return fail(TS_ERR_ARG, "NULL adjoint argument");
+  if (!ts::aligned16(lambda)) return fail(TS_ERR_ARG, "lambda must be 16-byte aligned");
   if (!std::isfinite(dt)) return fail(TS_ERR_ARG, "dt must be finite");
   if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   if (g->desc.scheme != TS_RK4 || g->desc.filter_on)

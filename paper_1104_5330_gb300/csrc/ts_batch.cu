@@ -503,6 +503,7 @@ ts_status ts_batch_step(ts_batch* b, void* const* F, const double* dt, int nstep
   if (!b || !F || !dt || nsteps < 0) return ts::fail_status(TS_ERR_ARG, "bad batch step arguments");
   for (int q = 0; q < b->n; ++q) {
     if (!F[q]) return ts::fail_status(TS_ERR_ARG, "a field pointer is NULL");
+    if (!ts::aligned16(F[q])) return ts::fail_status(TS_ERR_ARG, "a field pointer is not 16-byte aligned");
     if (!std::isfinite(dt[q])) return ts::fail_status(TS_ERR_ARG, "dt must be finite");
     if (!b->grids[q]->coeffs) return ts::fail_status(TS_ERR_STATE, "ts_set_coeffs missing for a problem");
   }

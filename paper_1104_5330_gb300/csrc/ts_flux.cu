@@ -83,6 +83,7 @@ extern "C" {
 ts_status ts_outgoing_flux(ts_grid* g, const void* F, double* J_R2, void* stream) {
   if (!g) return ts::fail_status(TS_ERR_ARG, "grid is NULL");
   if (!F || !J_R2) return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux: NULL argument");
+  if (!ts::aligned16(F)) return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux: F is not 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const ts::Dims& d = g->d;
   const long long nq = (long long)d.G * d.Nt * d.Np;
@@ -103,6 +104,8 @@ ts_status ts_outgoing_flux(ts_grid* g, const void* F, double* J_R2, void* stream
 ts_status ts_outgoing_flux_adjoint(ts_grid* g, const double* gJ, void* lambda, void* stream) {
   if (!g) return ts::fail_status(TS_ERR_ARG, "grid is NULL");
   if (!gJ || !lambda) return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux_adjoint: NULL argument");
+  if (!ts::aligned16(lambda))
+    return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux_adjoint: lambda is not 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const ts::Dims& d = g->d;
   const long long blocks = std::min<long long>((d.total + kFluxThreads - 1) / kFluxThreads, 152LL * 16);

@@ -11,6 +11,11 @@
 
 namespace ts {
 
+// Device fields are read and written with 16-byte vector accesses and
+// 16-byte asynchronous copies: the entry points require 16-byte alignment.
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+
 // Sets the text that ts_last_error() returns on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -197,6 +197,7 @@ ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0
                              double* N, double* J_R1, double* J_R2, void* stream) {
   if (!desc) return noalloc_fail(TS_ERR_ARG, "ts_moments_noalloc: desc is NULL");
   if (!F) return noalloc_fail(TS_ERR_ARG, "ts_moments_noalloc: F is NULL");
+  if (!ts::aligned16(F)) return noalloc_fail(TS_ERR_ARG, "ts_moments_noalloc: F is not 16-byte aligned");
   const ts_grid_desc& d = *desc;
   if (!(d.R1 > 0.0) || !(d.R2 > d.R1) || !std::isfinite(d.R2) || d.groups < 1)
     return noalloc_fail(TS_ERR_ARG, "ts_moments_noalloc: need 0 < R1 < R2 and groups >= 1");

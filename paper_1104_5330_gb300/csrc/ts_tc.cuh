@@ -108,7 +108,7 @@ struct TcForm {
 
 struct TcShape {
   int Kpad, Npad, KC, tmem_cols;
-  size_t offA, offB, offBar, bytes, a_bytes, b_bytes;
+  size_t offA, offB, offBar, offU, bytes, a_bytes, b_bytes;
 };
 
 template <int KIND>
@@ -127,7 +127,8 @@ __host__ __device__ inline TcShape tc_shape(int Nr) {
   s.offB = Fm::NTERM * s.a_bytes;                             // NTERM matrix terms
   s.offBar = s.offB + Fm::NTERM * s.b_bytes;
   s.offBar = (s.offBar + 15) / 16 * 16;
-  s.bytes = s.offBar + 32;                                    // 2 mbarriers + TMEM slot
+  s.offU = s.offBar + 32;                                     // 2 mbarriers + TMEM slot
+  s.bytes = s.offU + (size_t)Nr * 128 * sizeof(float);        // the tile's lines, raw
   return s;
 }
 
@@ -236,16 +237,44 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
                  :: "r"(smem_u32(tslot)), "r"(sh.tmem_cols) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // the tile's N_r lines into shared memory as raw floats, every 16-byte copy in
+  // flight at once (cp.async; columns beyond the tile are zero), and the lines
+  // of K, F and Acc that the epilogue reads requested into L2 meanwhile
+  float* sU = reinterpret_cast<float*>(smem_raw + sh.offU);
+  for (int x = tid; x < Nr * 32; x += 128) {
+    const int i = x >> 5, c4 = (x & 31) * 4;
+    if (c4 < Wc) {
+      copy4<true, float, float>(sU + i * 128 + c4, U + base + (long long)i * d.S_i + c4);
+    } else {
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};
+      st4<float>(sU + i * 128 + c4, z);
+    }
+  }
+  cp_async_commit();
+  {
+    const int lane = tid & 31;
+    const int cw = warp * 32;   // this warp's 32 columns: one 128-byte line per row
+    if (cw < Wc) {
+      for (int i = lane; i < Nr; i += 32) {
+        const long long gi = base + (long long)i * d.S_i + cw;
+        prefetch_l2(Kin + gi);
+        if (mode != RAD_RHS) prefetch_l2(F + gi);
+        if (mode == RAD_STAGE1 || mode == RAD_STAGE2 || mode == RAD_STAGE3 || mode == RAD_AB2)
+          prefetch_l2(Acc + gi);
+      }
+    }
+  }
+  cp_async_wait0();
+  __syncthreads();
   // data tile -> A operand terms (rows = columns w, K = radial node), one core
-  // row (KE nodes of one column) per thread and step; columns beyond the tile
-  // and nodes beyond N_r are zero
+  // row (KE nodes of one column) per thread and step; nodes beyond N_r are zero
   for (int x = tid; x < sh.KC * 128; x += 128) {
     const int kq = x >> 7, w = x & 127;
     float v[Fm::KE];
 #pragma unroll
     for (int e = 0; e < Fm::KE; ++e) {
       const int kk = kq * Fm::KE + e;
-      v[e] = (kk < Nr && w < Wc) ? U[base + (long long)kk * d.S_i + w] : 0.f;
+      v[e] = kk < Nr ? sU[kk * 128 + w] : 0.f;
     }
     split_store_row<KIND>(v, sA, core_off<Fm::KE, Fm::EB>(w, kq * Fm::KE, sh.KC), sh.a_bytes);
   }

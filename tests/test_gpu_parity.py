@@ -197,6 +197,27 @@ def test_adjoint_parity_with_oracle(dims):
     assert rel_l2(host(ge), geo) < FP64_TOL
 
 
+def test_misaligned_fields_are_rejected():
+    """Fields are accessed with 16-byte vectors: a view 8 bytes past a 16-byte
+    boundary is refused (TS_ERR_ARG) and nothing runs; the aligned field steps."""
+    og, gg = pair(0.2, 1.0, 9, 4, 4, 4, 4)
+    ts = T()
+    kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)
+    gg.set_coeffs(kap, eta, ks, gR1, gR2)
+    n = F0.size
+    buf = torch.zeros(n + 2, dtype=torch.float64, device="cuda")
+    bad = buf[1:n + 1].view(F0.shape)
+    bad.copy_(torch.as_tensor(F0, device="cuda"))
+    with pytest.raises(ts.TSError, match="aligned"):
+        gg.step(bad, 1e-3, 1)
+    with pytest.raises(ts.TSError, match="aligned"):
+        gg.rhs(cuda(F0), buf[1:n + 1].view(F0.shape))
+    assert torch.equal(bad, torch.as_tensor(F0, device="cuda"))   # untouched
+    good = cuda(F0)
+    gg.step(good, 1e-3, 1)
+    assert torch.isfinite(good).all()
+
+
 def test_fp32_variant_against_oracle():
     og, gg = pair(*RAGGED, G=2, precision=1)
     kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)

@@ -58,6 +58,17 @@ def test_null_arguments_are_rejected(T):
     assert T.LIB.ts_field_elems(None) == 0
 
 
+def test_misaligned_fields_are_rejected_before_any_device_work(T):
+    """Device fields must be 16-byte aligned (the passes use 16-byte vector
+    accesses): an address 4 bytes past a boundary is refused with TS_ERR_ARG,
+    which ts_moments_noalloc checks before touching the device."""
+    d = _desc(T)
+    st = T.LIB.ts_moments_noalloc(ctypes.byref(d), ctypes.c_void_p(0x10004), None, None, None,
+                                  None, None, None)
+    assert st == T.TS_ERR_ARG
+    assert "aligned" in T.LIB.ts_last_error().decode()
+
+
 def test_new_entry_points_reject_null_grids(T):
     assert T.LIB.ts_set_scattering_anisotropy(None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_set_scattering_quadrupole(None, None, None) == T.TS_ERR_ARG
@@ -82,5 +93,5 @@ def test_batches_refuse_ab2_before_touching_the_device(T):
     descs = (T.GridDesc * 1)(_desc(T, radial=T.TS_RADIAL_UPWIND_FD))
     assert T.LIB.ts_batch_create(descs, 1, 0, ctypes.byref(h)) == T.TS_ERR_UNSUPPORTED
     d = _desc(T, radial=T.TS_RADIAL_UPWIND_FD)
-    assert T.LIB.ts_moments_noalloc(ctypes.byref(d), ctypes.c_void_p(1), None, None, None,
+    assert T.LIB.ts_moments_noalloc(ctypes.byref(d), ctypes.c_void_p(0x10000), None, None, None,
                                     None, None, None) == T.TS_ERR_UNSUPPORTED
