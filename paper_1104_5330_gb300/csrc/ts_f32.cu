@@ -21,7 +21,7 @@ static cudaError_t radial_tc(const Problem& p, const void* Bterms, const Tables<
   const Dims& d = p.d;
   const int S = d.NT * d.NP;
   const long long nct = (long long)d.G * d.Nt * d.Np * ((S + 127) / 128);
-  k_radial_tc<KIND><<<grid1(nct), 128, sh.bytes, s>>>(p, t, Bterms, U, K, sgn, tau ? 1 : 0, mode,
+  k_radial_tc<KIND><<<grid1(nct), kTcThreads, sh.bytes, s>>>(p, t, Bterms, U, K, sgn, tau ? 1 : 0, mode,
                                                       F, Acc, Uout, out, (float)dt);
   return cudaGetLastError();
 }

@@ -1,7 +1,8 @@
 // Radial pass on the 5th-generation tensor cores (tcgen05), split operands.
 //
-// One CTA (4 warps) owns 128 consecutive (Theta, Phi) columns of one (g,
-// theta, phi) position and all N_r radial nodes. The radial derivative of
+// One CTA (8 warps, two threads per column) owns 128 consecutive (Theta, Phi)
+// columns of one (g, theta, phi) position and all N_r radial nodes. The radial
+// derivative of
 // those 128 r-lines is one matrix product
 //     D[w][i] = sum_i' u[i'][w] Dr[i][i']        (M = 128 columns, N = N_r padded
 //                                                 to 16, K = N_r padded to the
@@ -15,11 +16,12 @@
 //    order <= 2 (b0c0, b0c1, b1c0, b0c2, b1c1, b2c0), smallest first.
 // The matrix terms are prepared on the host in the canonical no-swizzle
 // K-major layout (8-row x 16-byte core matrices) and copied into shared
-// memory by the bulk-copy (TMA) engine; the data tile is split and laid out
-// by the threads. After the MMAs complete, every thread reads its column's N_r
-// results from TMEM (tcgen05.ld) and applies the r term, the Tau rows and the
-// RK4 stage update for its own r-line, loading each group of rows it updates
-// before storing any of them. Every wait is bounded: if it runs out, the kernel
+// memory by the bulk-copy (TMA) engine; the data tile's lines are staged
+// raw by cp.async (with the epilogue's lines requested into L2 meanwhile), then
+// split and laid out by the threads. After the MMAs complete, the two threads
+// of each column read its N_r results from TMEM (tcgen05.ld, alternate 8-row
+// groups) and apply the r term, the Tau rows and the RK4 stage update to their
+// rows of the r-line, loading each group of rows before storing any of them. Every wait is bounded: if it runs out, the kernel
 // sets the grid's error flag (ts_sync_status reports TS_ERR_TIMEOUT), waits a
 // bounded time for its own operations in flight, frees its TMEM and returns.
 #pragma once
@@ -189,8 +191,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&v)[16]) {
   for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
+// 8 consecutive TMEM columns of this warp's 32 lanes (one per thread).
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(addr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+// Threads per CTA: two per column of the 128-column tile (warps w and w + 4
+// read the same TMEM lanes, each finishing alternate 8-row groups).
+constexpr int kTcThreads = 256;
+
 template <int KIND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 3)
 k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const float* U,
             const float* Kin, float sgn, int tau, int mode, float* F, float* Acc, float* Uout,
             float* out, float dt) {
@@ -241,7 +260,7 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
   // flight at once (cp.async; columns beyond the tile are zero), and the lines
   // of K, F and Acc that the epilogue reads requested into L2 meanwhile
   float* sU = reinterpret_cast<float*>(smem_raw + sh.offU);
-  for (int x = tid; x < Nr * 32; x += 128) {
+  for (int x = tid; x < Nr * 32; x += kTcThreads) {
     const int i = x >> 5, c4 = (x & 31) * 4;
     if (c4 < Wc) {
       copy4<true, float, float>(sU + i * 128 + c4, U + base + (long long)i * d.S_i + c4);
@@ -253,9 +272,9 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
   cp_async_commit();
   {
     const int lane = tid & 31;
-    const int cw = warp * 32;   // this warp's 32 columns: one 128-byte line per row
+    const int cw = (warp & 3) * 32;   // this warp's 32 columns: one 128-byte line per row
     if (cw < Wc) {
-      for (int i = lane; i < Nr; i += 32) {
+      for (int i = lane + 32 * (warp >> 2); i < Nr; i += 64) {
         const long long gi = base + (long long)i * d.S_i + cw;
         prefetch_l2(Kin + gi);
         if (mode != RAD_RHS) prefetch_l2(F + gi);
@@ -268,7 +287,7 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
   __syncthreads();
   // data tile -> A operand terms (rows = columns w, K = radial node), one core
   // row (KE nodes of one column) per thread and step; nodes beyond N_r are zero
-  for (int x = tid; x < sh.KC * 128; x += 128) {
+  for (int x = tid; x < sh.KC * 128; x += kTcThreads) {
     const int kq = x >> 7, w = x & 127;
     float v[Fm::KE];
 #pragma unroll
@@ -330,22 +349,27 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
     mbar_wait(bar0, 0);
     if (issued) mbar_wait(bar1, 0);
   } else {
-    // epilogue on this thread's r-line (column w = TMEM lane): r term, Tau rows,
-    // stage update, reading the products from TMEM 16 rows at a time (the
-    // loads of a warp are issued by all its lanes); the loads of each 16-row
-    // group are all issued before any of its stores
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    const int w = tid;
+    // epilogue on this thread's r-line (column w = TMEM lane; the two threads of
+    // a column take alternate 8-row groups): r term, Tau rows, stage update,
+    // reading the products from TMEM 8 rows at a time (the loads of a warp are
+    // issued by all its lanes); the loads of each group are all issued before
+    // any of its stores
+    const int w = tid & 127, half = tid >> 7;
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     const bool act = w < Wc;
     const int k = act ? (c0 + w) / NP : 0;
     const float ck = sgn * t.cosT[k];
     const int b = t.cosT[k] > 0.f ? 0 : Nr - 1;
-    float dv[16];
-    tmem_ld16(lane_base + (uint32_t)((Nr - 1) / 16 * 16), dv);   // group holding row N
-    const float dN = dv[(Nr - 1) % 16];
-    tmem_ld16(lane_base, dv);                                    // group holding row 0
+    float dv[8];
+    tmem_ld8(lane_base + (uint32_t)((Nr - 1) / 8 * 8), dv);   // group holding row N
+    const float dN = dv[(Nr - 1) % 8];
+    tmem_ld8(lane_base, dv);                                  // group holding row 0
     const float db = b == 0 ? dv[0] : dN;
-    const float kb = act ? Kin[base + (long long)b * d.S_i + w] + ck * db : 0.f;
+    const long long Si = d.S_i;
+    const float* Kc = Kin + base + w;   // this column's lines
+    const float* Fc = F + base + w;
+    const float* Ac = Acc + base + w;
+    const float kb = act ? Kc[(long long)b * Si] + ck * db : 0.f;
     const float tb = t.tsign[b];
     // every update mode as dst = f + cv (cw v + ca ac), Acc = aa ac + ab v
     const bool rhs = mode == RAD_RHS;
@@ -359,35 +383,36 @@ k_radial_tc(Problem p, Tables<float> t, const void* __restrict__ Bterms, const f
     if (mode == RAD_AB2) { cw = 1.5f; ca = -0.5f; }
     // RK4 stages 0-2 write the next stage input; stage 3 and AB2 update F in
     // place (the A tile was staged before the MMAs)
-    float* dst = rhs ? out : (mode >= RAD_STAGE3 ? F : Uout);
-    for (int c = 0; c < Nr; c += 16) {
-      if (c > 0) tmem_ld16(lane_base + (uint32_t)c, dv);
+    float* dst = (rhs ? out : (mode >= RAD_STAGE3 ? F : Uout)) + base + w;
+    float* Aw = Acc + base + w;
+    for (int c = 8 * half; c < Nr; c += 16) {
+      tmem_ld8(lane_base + (uint32_t)c, dv);
       if (!act) continue;
-      float kv[16], f[16], ac[16];
+      const long long r0 = (long long)c * Si;
+      float kv[8], f[8], ac[8];
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
-        const int i = c + e;
-        f[e] = ac[e] = 0.f;
-        if (i < Nr) {
-          const long long gi = base + (long long)i * d.S_i + w;
-          kv[e] = Kin[gi];
-          if (!rhs) f[e] = F[gi];
-          if (rA) ac[e] = Acc[gi];
+      for (int e = 0; e < 8; ++e) {
+        f[e] = ac[e] = kv[e] = 0.f;
+        if (c + e < Nr) {
+          const long long o = r0 + e * Si;
+          kv[e] = Kc[o];
+          if (!rhs) f[e] = Fc[o];
+          if (rA) ac[e] = Ac[o];
         }
       }
 #pragma unroll
-      for (int e = 0; e < 16; ++e) {
+      for (int e = 0; e < 8; ++e) {
         const int i = c + e;
         if (i >= Nr) break;
-        const long long gi = base + (long long)i * d.S_i + w;
+        const long long o = r0 + e * Si;
         float v = kv[e] + ck * dv[e];
         if (tau) v -= kb * tb * t.tsign[i];
         if (rhs) {
-          dst[gi] = v;
+          dst[o] = v;
           continue;
         }
-        dst[gi] = f[e] + cv * (cw * v + ca * ac[e]);
-        if (wA) Acc[gi] = aa * ac[e] + ab * v;
+        dst[o] = f[e] + cv * (cw * v + ca * ac[e]);
+        if (wA) Aw[o] = aa * ac[e] + ab * v;
       }
     }
   }
