@@ -655,8 +655,8 @@ cudaError_t radial_pass(const ts_grid* g, const ts::Problem& p, const Tables<C>&
                                       (g->desc.R2 - g->desc.R1) / (g->desc.Nr - 1), st);
   if (g->desc.radial == TS_RADIAL_ZONED) {
     const C* zt = static_cast<const C*>(sizeof(C) == 8 ? g->zt64 : g->zt32);
-    return ts::launch_radial_zoned<T, C>(p, t, zt, zt + (size_t)g->zB * g->zB, g->zA, g->zB,
-                                         g->zh, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, st);
+    return ts::launch_radial_zoned<T, C>(p, t, zt, g->zA, g->zB, g->zh, U, K, sgn, tau, mode,
+                                         F, Acc, Uout, out, dt, st);
   }
   return Launch<T, C>::radial(p, t, g->t64.Dr, U, K, sgn, tau, mode, F, Acc, Uout, out, dt, st);
 }
@@ -1039,8 +1039,19 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
     G->zB = g.Nr - 2 * (g.zone_nodes - 1);
     const double w = g.zone_width * (g.R2 - g.R1);
     G->zh = w / (G->zA - 1);
-    Vec zt = cheb_diff(G->zB, g.R1 + w, g.R2 - w);
-    for (int j = 0; j < G->zB; ++j) zt.push_back(((G->zB - 1 - j) % 2) ? -1.0 : 1.0);
+    // the central zone's Gauss-Lobatto matrix D ([out][in]) folded over its
+    // centro-antisymmetry: Ep, Op = (D[i][j] +- D[i][M-j]) / 2 (i, j < H),
+    // Dm[i] = D[i][M/2], Mr[j] = D[M/2][j] (odd nB), then T_N on its nodes
+    const int nB = G->zB, M = nB - 1, Hh = nB / 2;
+    const Vec D = cheb_diff(nB, g.R1 + w, g.R2 - w);
+    Vec zt;
+    for (int i = 0; i < Hh; ++i)
+      for (int j = 0; j < Hh; ++j) zt.push_back(0.5 * (D[i * nB + j] + D[i * nB + M - j]));
+    for (int i = 0; i < Hh; ++i)
+      for (int j = 0; j < Hh; ++j) zt.push_back(0.5 * (D[i * nB + j] - D[i * nB + M - j]));
+    for (int i = 0; i < Hh; ++i) zt.push_back((nB & 1) ? D[i * nB + Hh] : 0.0);
+    for (int j = 0; j < Hh; ++j) zt.push_back((nB & 1) ? D[Hh * nB + j] : 0.0);
+    for (int j = 0; j < nB; ++j) zt.push_back(((nB - 1 - j) % 2) ? -1.0 : 1.0);
     e = cudaMalloc(&G->zt64, zt.size() * sizeof(double));
     if (e == cudaSuccess)
       e = cudaMemcpy(G->zt64, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice);

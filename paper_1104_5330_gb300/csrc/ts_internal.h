@@ -175,13 +175,14 @@ cudaError_t launch_radial_fd(const Problem& p, const Tables<C>& t, const T* U, c
                              bool hold, int mode, T* F, T* Acc, T* Uout, T* out, double dt,
                              double dr, cudaStream_t s);
 
-// Radial pass of the three-zone grid (App. B; defined in ts_zoned.cu): DB, tNB
-// the central zone's differentiation matrix and T_N on its nodes, nA nodes per
-// edge zone, nB central nodes, h the edge-zone spacing.
+// Radial pass of the three-zone grid (App. B; defined in ts_zoned.cu): ZT the
+// central zone's folded differentiation tables [Ep H*H | Op H*H | Dm H | Mr H |
+// T_N on its nB nodes] (H = nB/2), nA nodes per edge zone, h the edge-zone
+// spacing.
 template <typename T, typename C>
-cudaError_t launch_radial_zoned(const Problem& p, const Tables<C>& t, const C* DB, const C* tNB,
-                                int nA, int nB, double h, const T* U, const T* K, C sgn, bool hold,
-                                int mode, T* F, T* Acc, T* Uout, T* out, double dt, cudaStream_t s);
+cudaError_t launch_radial_zoned(const Problem& p, const Tables<C>& t, const C* ZT, int nA, int nB,
+                                double h, const T* U, const T* K, C sgn, bool hold, int mode,
+                                T* F, T* Acc, T* Uout, T* out, double dt, cudaStream_t s);
 
 // Whether the tensor-core radial pass handles N_r (its tile must fit shared memory).
 inline bool tc_supported(int Nr) { return Nr >= 3 && Nr <= 81; }
@@ -295,7 +296,7 @@ struct ts_grid {
   const void* hist_F = nullptr;
   long long wait_operand = 0;  // 0: the default bound (ts_set_wait_limit)
   float* tcang = nullptr;      // angular tensor-core operand terms (Problem::tcang)
-  // TS_RADIAL_ZONED: the central zone's differentiation matrix [out][in] and T_N on
+  // TS_RADIAL_ZONED: the central zone's folded differentiation tables and T_N on
   // its nodes, in double (zt64) and, for float grids, in float (zt32)
   void *zt64 = nullptr, *zt32 = nullptr;
   int zA = 0, zB = 0;          // nodes per edge zone, nodes of the central zone
