@@ -640,7 +640,10 @@ def run_cons2d(args, stream):
 def run_workload_precisions(args, wname, stream, precisions, nv):
     """Rates of `precisions` on another workload of the same family (absorber,
     seeded smooth F0, static inflow, RK4 at dt = 0.4 h_min), and each float
-    variant's relative L2 distance to the GPU FP64 result after nv steps."""
+    variant's relative L2 distance to the GPU FP64 result after nv steps.
+    "fp64+filter": FP64 with the exponential filter on every axis after each
+    step (alpha 36, order 16), its change against the unfiltered FP64 result and
+    the filter's own time per launch."""
     import torch
     import paper_1104_5330_gb300.ts as ts
     from paper_1104_5330_gb300 import inputs as I
@@ -654,8 +657,10 @@ def run_workload_precisions(args, wname, stream, precisions, nv):
            "steps": args.steps}
     ref = None
     for name in precisions:
-        prec = getattr(ts, PRECISIONS[name])
-        gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=prec)
+        base, _, opt = name.partition("+")
+        filt = opt == "filter"
+        prec = getattr(ts, PRECISIONS[base])
+        gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=prec, filter_on=filt)
         r, th, ph, Th, Ph = gg.nodes()
         kap, eta, ks = I.absorber_fields(r, th, ph, groups=G)
         F0 = np.stack([I.seeded_smooth(r, th, ph, Th, Ph, 1104 + g, R1, R2) for g in range(G)])
@@ -663,7 +668,7 @@ def run_workload_precisions(args, wname, stream, precisions, nv):
         gg.set_coeffs(kap, eta, ks, gR1, gR2)
         F = torch.as_tensor(F0, dtype=gg.dtype, device="cuda").contiguous()
         gg.step(F, dt, nv)
-        if prec == ts.TS_FP64:
+        if prec == ts.TS_FP64 and not filt:
             ref = F.clone()
             err = None
         else:
@@ -683,6 +688,10 @@ def run_workload_precisions(args, wname, stream, precisions, nv):
                          "ms_per_step": ms / args.steps, "dtype": "f64",
                          "pass_ms_per_launch": {n: float(pm[a] / pn[a])
                                                 for a, n in pass_names(pn).items()}}
+            if filt:
+                out[name]["filter"] = "exponential, alpha 36, order 16, every axis, after each step"
+                out[name]["filter_ms_per_step"] = float(pm[3] / 2)   # two profiled steps
+                out[name]["rel_l2_change_vs_unfiltered_fp64"] = err
         else:
             out[name] = variant_line(ts, dims, wname, name, prec, gg.points, args.steps, ms, err,
                                      nv, pm, pn, peaks, sms, smax)
@@ -872,8 +881,8 @@ def run_ours(args, dims, wname):
         line["workload_17x8^4_g1"] = run_workload_precisions(
             args, "absorber_17x8^4_g1", stream, ["fp64", "fp32"], 10)
         line["precision_65x32^4_g1"] = run_workload_precisions(
-            args, "absorber_65x32^4_g1", stream, ["fp64", "fp32", "fp32_r64", "tf32x3", "bf16x3"],
-            10)
+            args, "absorber_65x32^4_g1", stream,
+            ["fp64", "fp32", "fp32_r64", "tf32x3", "bf16x3", "fp64+filter"], 10)
     if not args.skip_workloads:
         line["conservative_2d"] = run_cons2d(args, stream)
     if not args.skip_aniso:
