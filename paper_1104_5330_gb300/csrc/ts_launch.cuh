@@ -89,7 +89,24 @@ static int angular_nb(const Dims& d, int ntiles, bool rb = false) {
     const int per = (d.NT / 2 / rb_ang((int)sizeof(C))) * (d.NP / 8);
     int nb = std::max(1, (kThreads + per - 1) / per);
     while (nb > 1 && smem_angular<C>(d, nb, true) > kSmemHalf) --nb;
-    return nb;
+    // The persistent CTAs (two per SM) take tiles in turn: the busiest one runs
+    // ceil(tiles / CTAs) rounds. Down to 3/4 of the largest tile, take the
+    // smallest block count that needs no more rounds (the same number of rounds
+    // with less staging and preparation each, the last round fuller).
+    static int nsm = 0;
+    if (!nsm) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (nsm < 1) nsm = 1;
+    }
+    const long long ctas = 2LL * nsm;
+    auto rounds = [&](int b) { return ((d.nblk + b - 1) / b + ctas - 1) / ctas; };
+    const long long r0 = rounds(nb);
+    int best = nb;
+    for (int b = nb - 1; b >= std::max(1, 3 * nb / 4); --b)
+      if (rounds(b) == r0) best = b;
+    return best;
   }
   int nb = std::max(1, 2048 / S);
   const size_t mats = (size_t)(2 * d.NT * d.NT + d.NP * d.NP) * sizeof(C);

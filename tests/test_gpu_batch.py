@@ -177,6 +177,24 @@ def test_batch_steps_large_problems_with_their_own_passes(precision, scheme):
     b.close()
 
 
+def test_batch_of_large_problems_only():
+    """Every problem on its grid's own passes (no work-queue launch): the batch
+    equals the single-problem steps bit for bit."""
+    ts = T()
+    specs = [LARGE, LARGE]
+    b = ts.Batch(_descs(1, 0, specs), autotune=False)
+    _, _, Fs, dts = _setup(b, specs, torch.float32)
+    ref = [F.clone() for F in Fs]
+    b.step(Fs, dts, 2)
+    torch.cuda.synchronize()
+    for q, g in enumerate(b.grids):
+        g.step(ref[q], dts[q], 2)
+    torch.cuda.synchronize()
+    for q in range(2):
+        assert torch.equal(Fs[q], ref[q])
+    b.close()
+
+
 def test_autotune_changes_no_result_bits():
     ts = T()
     g = ts.Grid(0.2, 1.0, 17, 8, 16, 16, 8, groups=2, precision=1)
