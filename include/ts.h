@@ -95,8 +95,9 @@ typedef enum {
                                  grid creation, ts_set_coeffs,
                                  ts_set_scattering_anisotropy, ts_apply_inflow,
                                  ts_reset_history, and a ts_step on a different F
-                                 pointer than the last one. Not in batches; its
-                                 adjoint is ts_adjoint_step_ab2. */
+                                 pointer than the last one. In batches whose
+                                 problems are all TS_AB2; its adjoint is
+                                 ts_adjoint_step_ab2. */
 } ts_scheme;
 
 typedef enum {
@@ -375,7 +376,11 @@ ts_status ts_tile_shape(const ts_grid* grid, int* angular_blocks, int* plane_pai
  * larger problems, which fill the GPU on their own, are stepped by their
  * grid's own passes (the compiled line-length forms where the sizes have them).
  * A step is captured into a CUDA graph and replayed (captured again when a
- * field pointer, a dt or a problem's coefficients change). Results equal those
+ * field pointer, a dt or a problem's coefficients change). A batch runs the
+ * RK4 schemes (TS_RK4, TS_RK4_SPLIT_IMPLICIT, mixed freely) or TS_AB2 on every
+ * problem; an AB2 batch keeps its history between calls like a grid does (a
+ * restart -- new fields, steps or coefficients, or a grid's own history reset
+ * -- makes the next step forward Euler for every problem). Results equal those
  * of ts_step on each problem's grid to rounding (bit for bit for the large
  * problems: the same launches), and replaying the graph reproduces them bit for
  * bit. (The paper steps one problem at a time;

@@ -950,6 +950,31 @@ cudaError_t ts::step_grid(ts_grid* g, void* F, double dt, int nsteps, cudaStream
                     : run_steps<float, float>(g, g->t32, (float*)F, dt, nsteps, st);
 }
 
+namespace {
+template <typename T, typename C>
+cudaError_t ab2_step(ts_grid* g, const Tables<C>& t, T* F, double dt, bool first,
+                     cudaStream_t st) {
+  const ts::Problem p = make_problem(g);
+  T* K = work<T>(g, g->K);
+  T* Acc = work<T>(g, g->Acc);
+  cudaError_t e = stage_passes<T, C>(g, p, t, F, K, (C)-1, true, g->desc.bc == TS_BC_TAU_INFLOW,
+                                     first ? ts::RAD_AB2_START : ts::RAD_AB2, F, Acc, nullptr,
+                                     nullptr, dt, st, nullptr);
+  if (e == cudaSuccess && g->desc.filter_on) e = Launch<T, C>::filter(p, t, F, K, st);
+  return e;
+}
+}  // namespace
+
+cudaError_t ts::step_grid_ab2(ts_grid* g, void* F, double dt, bool first, cudaStream_t st) {
+  return g->es == 8 ? ab2_step<double, double>(g, g->t64, (double*)F, dt, first, st)
+                    : ab2_step<float, float>(g, g->t32, (float*)F, dt, first, st);
+}
+
+void ts::set_ab2_history(ts_grid* g, const void* F) {
+  g->hist = true;
+  g->hist_F = F;
+}
+
 extern "C" {
 
 const char* ts_last_error(void) { return g_err.c_str(); }

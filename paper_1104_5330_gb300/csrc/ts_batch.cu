@@ -43,7 +43,7 @@ struct BatchItem {
 template <typename T, typename C, int PASS>
 __global__ void __launch_bounds__(kThreads)
 k_batch_pass(const BatchItem<T, C>* __restrict__ items, int nitems, long long total,
-             unsigned long long* counter, int stage) {
+             unsigned long long* counter, int stage, int rmode) {
   __shared__ long long s_tile;
   __shared__ int s_item;
   for (;;) {
@@ -72,7 +72,7 @@ k_batch_pass(const BatchItem<T, C>* __restrict__ items, int nitems, long long to
     else if (PASS == 1)
       plane_tile_any<T, C>(it.p, it.t, in, it.K, (C)-1, it.p.tp.c, lt);
     else if (PASS == 2)
-      radial_tile_any<T, C>(it.p, it.t, it.Dr64, in, it.K, (C)-1, it.tau, RAD_STAGE0 + stage, it.F,
+      radial_tile_any<T, C>(it.p, it.t, it.Dr64, in, it.K, (C)-1, it.tau, rmode, it.F,
                         it.Acc, it.U, nullptr, (C)it.dt, it.p.tp.W, lt);
     else
       implicit_collision_tile<T, C>(it.p, it.t, it.F, it.dt, kThreads / 32, lt);
@@ -240,6 +240,11 @@ struct ts_batch {
   cudaStream_t st = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // TS_AB2 batches: every problem takes one stage derivative per step; the first
+  // step after a restart is forward Euler (its own graph, exec_start), and the
+  // batch's history is valid once a step has run on the current fields
+  bool ab2 = false, hist = false;
+  cudaGraphExec_t exec_start = nullptr;
   std::vector<void*> lastF;
   std::vector<double> lastdt;
   std::vector<unsigned> lastgen;   // per-problem ts_grid::gen at the last upload
@@ -316,27 +321,49 @@ cudaError_t layout_batch(ts_batch* b) {
   return e;
 }
 
+// One step of every problem. RK4 batches: four stages; TS_AB2 batches: one
+// stage derivative, forward Euler when `first` (the step after a restart).
 template <typename T, typename C>
-cudaError_t enqueue_step(ts_batch* b, cudaStream_t st) {
+cudaError_t enqueue_step(ts_batch* b, cudaStream_t st, bool first) {
   const BatchItem<T, C>* items = static_cast<const BatchItem<T, C>*>(b->items_dev);
   const int ni = (int)b->queued.size();
+  const int nstage = b->ab2 ? 1 : 4;
   cudaError_t e = cudaSuccess;
   if (ni > 0) {
     e = cudaMemsetAsync(b->counters, 0, 13 * sizeof(unsigned long long), st);
-    for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
-      ts::k_batch_pass<T, C, 0><<<b->ctas[0], ts::kThreads, b->smem[0], st>>>(items, ni, b->total[0], b->counters + 3 * s + 0, s);
-      ts::k_batch_pass<T, C, 1><<<b->ctas[1], ts::kThreads, b->smem[1], st>>>(items, ni, b->total[1], b->counters + 3 * s + 1, s);
-      ts::k_batch_pass<T, C, 2><<<b->ctas[2], ts::kThreads, b->smem[2], st>>>(items, ni, b->total[2], b->counters + 3 * s + 2, s);
+    for (int s = 0; s < nstage && e == cudaSuccess; ++s) {
+      const int rm = b->ab2 ? (first ? ts::RAD_AB2_START : ts::RAD_AB2) : ts::RAD_STAGE0 + s;
+      ts::k_batch_pass<T, C, 0><<<b->ctas[0], ts::kThreads, b->smem[0], st>>>(items, ni, b->total[0], b->counters + 3 * s + 0, s, rm);
+      ts::k_batch_pass<T, C, 1><<<b->ctas[1], ts::kThreads, b->smem[1], st>>>(items, ni, b->total[1], b->counters + 3 * s + 1, s, rm);
+      ts::k_batch_pass<T, C, 2><<<b->ctas[2], ts::kThreads, b->smem[2], st>>>(items, ni, b->total[2], b->counters + 3 * s + 2, s, rm);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess && b->any_split) {
-      ts::k_batch_pass<T, C, 3><<<b->ctas[3], ts::kThreads, 0, st>>>(items, ni, b->total[3], b->counters + 12, 0);
+      ts::k_batch_pass<T, C, 3><<<b->ctas[3], ts::kThreads, 0, st>>>(items, ni, b->total[3], b->counters + 12, 0, 0);
       e = cudaGetLastError();
     }
   }
   // the large problems: one step of each by its grid's own passes
-  for (int q = 0; q < b->n && e == cudaSuccess; ++q)
-    if (b->own[q]) e = ts::step_grid(b->grids[q], b->lastF[q], b->lastdt[q], 1, st);
+  for (int q = 0; q < b->n && e == cudaSuccess; ++q) {
+    if (!b->own[q]) continue;
+    e = b->ab2 ? ts::step_grid_ab2(b->grids[q], b->lastF[q], b->lastdt[q], first, st)
+               : ts::step_grid(b->grids[q], b->lastF[q], b->lastdt[q], 1, st);
+  }
+  return e;
+}
+
+// Record one step into a graph (the batch's stream is idle).
+template <typename T, typename C>
+cudaError_t record_step(ts_batch* b, bool first, cudaGraphExec_t* exec) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = enqueue_step<T, C>(b, b->st, first);
+    e = cudaStreamEndCapture(b->st, &graph);
+    if (e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
   return e;
 }
 
@@ -355,28 +382,38 @@ ts_status batch_step(ts_batch* b, void* const* F, const double* dt, int nsteps, 
     b->lastgen.resize(b->n);
     for (int q = 0; q < b->n; ++q) b->lastgen[q] = b->grids[q]->gen;
     // the large problems' launches carry their fields and steps in their
-    // arguments: record the graph again
+    // arguments: record the graphs again
     if (b->exec && b->queued.size() < (size_t)b->n) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
     }
+    if (b->exec_start && b->queued.size() < (size_t)b->n) {
+      cudaGraphExecDestroy(b->exec_start);
+      b->exec_start = nullptr;
+    }
+    b->hist = false;   // new fields, steps or coefficients: AB2 restarts
   }
+  // a grid stepped or restarted on its own since the last batch step keeps the
+  // batch's history only if its Acc still holds the history of this field
+  if (b->ab2)
+    for (int q = 0; q < b->n; ++q)
+      if (!b->grids[q]->hist || b->grids[q]->hist_F != F[q]) b->hist = false;
   e = cudaEventRecord(b->ev_in, user);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev_in, 0);
   if (e == cudaSuccess && changed)
     e = cudaMemcpyAsync(b->items_dev, b->items_host, b->items_bytes, cudaMemcpyHostToDevice, b->st);
-  if (e == cudaSuccess && !b->exec) {
-    cudaGraph_t graph = nullptr;
-    e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      cudaError_t e2 = enqueue_step<T, C>(b, b->st);
-      e = cudaStreamEndCapture(b->st, &graph);
-      if (e2 != cudaSuccess) e = e2;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
+  if (e == cudaSuccess && !b->exec) e = record_step<T, C>(b, false, &b->exec);
+  if (e == cudaSuccess && b->ab2 && !b->exec_start)
+    e = record_step<T, C>(b, true, &b->exec_start);
+  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    const bool start = b->ab2 && !b->hist;
+    e = cudaGraphLaunch(start ? b->exec_start : b->exec, b->st);
+    if (e == cudaSuccess && b->ab2) b->hist = true;
   }
-  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) e = cudaGraphLaunch(b->exec, b->st);
+  if (e != cudaSuccess) b->hist = false;
+  // the grids' own AB2 state: their Acc holds K_{n-1} of these fields
+  if (e == cudaSuccess && b->ab2)
+    for (int q = 0; q < b->n; ++q) ts::set_ab2_history(b->grids[q], F[q]);
   if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(user, b->ev_out, 0);
   return e == cudaSuccess ? TS_OK : ts::cuda_status(e, "ts_batch_step");
@@ -427,6 +464,7 @@ ts_status ts_batch_destroy(ts_batch* b) {
   if (!b) return TS_OK;
   cudaDeviceSynchronize();
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->exec_start) cudaGraphExecDestroy(b->exec_start);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->st) cudaStreamDestroy(b->st);
@@ -449,8 +487,9 @@ ts_status ts_batch_create(const ts_grid_desc* descs, int n, int autotune, ts_bat
     if (descs[q].radial != TS_RADIAL_CHEBYSHEV)
       return ts::fail_status(TS_ERR_UNSUPPORTED, "batches run the Chebyshev radial grid");
   for (int q = 0; q < n; ++q)
-    if (descs[q].scheme == TS_AB2)
-      return ts::fail_status(TS_ERR_UNSUPPORTED, "batches run the RK4 schemes (TS_AB2 is per grid)");
+    if ((descs[q].scheme == TS_AB2) != (descs[0].scheme == TS_AB2))
+      return ts::fail_status(TS_ERR_UNSUPPORTED,
+                             "a batch runs TS_AB2 on all its problems or on none");
   ts_batch* b = new ts_batch();
   b->n = n;
   for (int q = 0; q < n; ++q) {
@@ -470,6 +509,7 @@ ts_status ts_batch_create(const ts_grid_desc* descs, int n, int autotune, ts_bat
     }
   }
   b->es = b->grids[0]->es;
+  b->ab2 = descs[0].scheme == TS_AB2;
   b->own.assign(n, 0);
   for (int q = 0; q < n; ++q) {
     if ((long long)b->grids[q]->d.total >= kBatchOwnPassesPoints) b->own[q] = 1;

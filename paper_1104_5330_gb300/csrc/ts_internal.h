@@ -316,4 +316,10 @@ Problem problem_of(const ts_grid* g);
 // passes (the compiled line-length forms where the sizes have them); kernel
 // launches only, so a stream capture can record them.
 cudaError_t step_grid(ts_grid* g, void* F, double dt, int nsteps, cudaStream_t st);
+// One TS_AB2 step of F by the grid's own passes with the history taken as given:
+// forward Euler when `first`, else F + dt (3/2 K_n - 1/2 K_{n-1}) with K_{n-1} in
+// the grid's Acc (kernel launches only, for a stream capture); and the record
+// that the grid's Acc now holds the history of F.
+cudaError_t step_grid_ab2(ts_grid* g, void* F, double dt, bool first, cudaStream_t st);
+void set_ab2_history(ts_grid* g, const void* F);
 }  // namespace ts

@@ -106,11 +106,12 @@ def test_ab2_host_entry_point_keeps_its_own_history():
     assert rel_l2(Fh.numpy(), op.run(F0, dt, 5)) < FP64_TOL
 
 
-def test_ab2_is_not_batched_and_has_no_adjoint():
+def test_ab2_batches_are_not_mixed_and_the_rk4_adjoint_refuses_ab2():
     ts = T()
     d = ts.GridDesc(0.2, 1.0, 9, 4, 4, 4, 4, 1, 0, ts.TS_AB2, 0, 0, 36.0, 16)
+    d4 = ts.GridDesc(0.2, 1.0, 9, 4, 4, 4, 4, 1, 0, ts.TS_RK4, 0, 0, 36.0, 16)
     with pytest.raises(RuntimeError):
-        ts.Batch([d], autotune=False)
+        ts.Batch([d, d4], autotune=False)
     og, gg, op, F0, dt = _both(RAGGED, 1)
     lam = cuda(np.ones(og.shape))
     gk = torch.zeros(gg.coef_shape, dtype=torch.float64, device="cuda")

@@ -195,6 +195,47 @@ def test_batch_of_large_problems_only():
     b.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ab2_batch_matches_single_problem_steps_and_the_oracle(precision):
+    """TS_AB2 on every problem (small ones on the work queue, one of 4.3M points on
+    its own passes): the batch keeps its history across calls (2 + 3 steps equal
+    5 steps of separate grids: forward Euler, then Adams-Bashforth), the large
+    problem bit for bit, the small ones to rounding, and in FP64 the small ones
+    match the oracle's AB2 run."""
+    ts = T()
+    specs = [SPECS[0], LARGE, SPECS[4]]
+    b = ts.Batch(_descs(precision, ts.TS_AB2, specs), autotune=False)
+    dtype = torch.float64 if precision == 0 else torch.float32
+    ogs, data, Fs, dts = _setup(b, specs, dtype)
+    dts = [0.5 * d for d in dts]   # AB2's stability limit is below RK4's
+    sep = []
+    for q, spec in enumerate(specs):
+        g = ts.Grid(0.2, 1.0, *spec[:5], groups=spec[5], precision=precision, scheme=ts.TS_AB2)
+        kap, eta, ks, F0, gR1, gR2 = data[q]
+        g.set_coeffs(kap, eta, ks, gR1, gR2)
+        F = cuda(F0, dtype)
+        g.step(F, dts[q], 5)
+        sep.append(F)
+    b.step(Fs, dts, 2)
+    b.step(Fs, dts, 3)
+    torch.cuda.synchronize()
+    tol = 1e-13 if precision == 0 else 2e-6
+    assert torch.equal(Fs[1], sep[1])
+    for q in (0, 2):
+        assert rel_l2(host(Fs[q]), host(sep[q])) <= tol, q
+    if precision == 0:
+        for q in (0, 2):
+            kap, eta, ks, F0, gR1, gR2 = data[q]
+            ref = OProblem(ogs[q], kap, eta, ks, gR1, gR2, scheme="ab2").run(F0, dts[q], 5)
+            assert rel_l2(host(Fs[q]), ref) < 1e-12, q
+    # a restart (new fields) begins with forward Euler again
+    F2 = [cuda(d[3], dtype) for d in data]
+    b.step(F2, dts, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(F2[1], sep[1])
+    b.close()
+
+
 def test_autotune_changes_no_result_bits():
     ts = T()
     g = ts.Grid(0.2, 1.0, 17, 8, 16, 16, 8, groups=2, precision=1)
