@@ -1250,6 +1250,19 @@ __device__ __forceinline__ void radial_store(int mode, long long gi, const C (&k
   }
 }
 
+// Exact widening of a float to a double by the IEEE-754 binary32 and binary64
+// layouts (sign kept, exponent rebiased by 1023 - 127 = 896, significand shifted
+// up by 52 - 23 = 29 bits), on the integer units; zero maps to zero, and the rare
+// subnormal, infinite or NaN inputs take the conversion instruction. Used where
+// the FP64 pipe, not the integer units, bounds a pass.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (e == 0xFFu || (e == 0u && m != 0u)) return (double)f;
+  const uint64_t mag = e ? ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29) : 0ull;
+  return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | mag));
+}
+
 template <int Nr_, typename T, typename C>
 __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>& t,
                                                const double* __restrict__ Dr64,
@@ -1322,28 +1335,52 @@ __device__ __forceinline__ void radial_rb_body(const Problem& p, const Tables<C>
   // exact there), and feeds it to every pair: two conversions, two additions and
   // 2 n64 multiply-adds per line point pair.
   if (n64 > 0) {
+    // tpc threads per column (adjacent lanes), each over every tpc-th point pair,
+    // summed by shuffles: long lines keep every thread of the tile busy
     constexpr int M64 = 2;   // at most two pairs (TS_FP32_R64)
-    for (int w = threadIdx.x; w < Wc; w += blockDim.x) {
+    int tpc = 1;
+    while (tpc < 8 && 2 * tpc * Wc <= (int)blockDim.x) tpc *= 2;
+    for (int v0 = 0; v0 < Wc * tpc; v0 += blockDim.x) {   // uniform trip count
+      const int v = v0 + (int)threadIdx.x;
+      const bool act = v < Wc * tpc;
+      const int w = act ? v / tpc : 0, part = v % tpc;
       double ae[M64] = {0, 0}, ao[M64] = {0, 0};
+      // point pairs ii = part, part + stride, ... of column w
+      auto sum = [&](int first, int stride) {
 #pragma unroll 4
-      for (int ii = 0; ii < hh; ++ii) {
-        const double a = (double)Ub[ii * Si + w], b = (double)Ub[(N - ii) * Si + w];
-        const double e = a + b, o = a - b;
+        for (int ii = first; ii < hh; ii += stride) {
+          const double a = widen_f32((float)Ub[ii * Si + w]);
+          const double b = widen_f32((float)Ub[(N - ii) * Si + w]);
+          const double e = a + b, o = a - b;
+#pragma unroll
+          for (int q = 0; q < M64; ++q) {
+            if (q < n64) {
+              ae[q] = fma(p.ep64[ii * hh + q], e, ae[q]);
+              ao[q] = fma(p.op64[ii * hh + q], o, ao[q]);
+            }
+          }
+        }
+      };
+      if (act) {
+        if (tpc == 1) sum(0, 1);   // the whole line (a compile-time trip count)
+        else sum(part, tpc);
+      }
+      for (int o = tpc >> 1; o; o >>= 1) {   // the tpc lanes of a column (whole warps take part)
+#pragma unroll
+        for (int q = 0; q < M64; ++q) {
+          ae[q] += __shfl_xor_sync(0xffffffffu, ae[q], o);
+          ao[q] += __shfl_xor_sync(0xffffffffu, ao[q], o);
+        }
+      }
+      if (act && part == 0) {
+        const double um = odd ? widen_f32((float)Ub[(N / 2) * Si + w]) : 0.0;
 #pragma unroll
         for (int q = 0; q < M64; ++q) {
           if (q < n64) {
-            ae[q] = fma(p.ep64[ii * hh + q], e, ae[q]);
-            ao[q] = fma(p.op64[ii * hh + q], o, ao[q]);
+            const double mid = odd ? p.mc64[q] * um : 0.0;
+            sR[q * W + w] = (C)(0.5 * (ao[q] + ae[q]) + mid);
+            sR[(n64 + q) * W + w] = (C)(0.5 * (ao[q] - ae[q]) - mid);
           }
-        }
-      }
-      const double um = odd ? (double)Ub[(N / 2) * Si + w] : 0.0;
-#pragma unroll
-      for (int q = 0; q < M64; ++q) {
-        if (q < n64) {
-          const double mid = odd ? p.mc64[q] * um : 0.0;
-          sR[q * W + w] = (C)(0.5 * (ao[q] + ae[q]) + mid);
-          sR[(n64 + q) * W + w] = (C)(0.5 * (ao[q] - ae[q]) - mid);
         }
       }
     }
