@@ -471,6 +471,13 @@ ts_status ts_cons2d_balance(ts_cons2d* grid, const double* Fhat, double* NJ, dou
  * the FP64 passes, which are bound by the FP64 arithmetic units. */
 ts_status ts_probe_fma_rate(int precision, double* tflops, void* stream);
 
+/* out[i] = in[i] widened from float to double (device arrays of n elements)
+ * by the integer-unit widening the TS_FP32_R64 end rows use (exact: the IEEE-754
+ * binary32 fields moved into binary64 ones; subnormals, infinities and NaNs by
+ * the conversion instruction), so that tests can compare it bit for bit with the
+ * hardware conversion. Asynchronous on `stream`. No counterpart in the paper. */
+ts_status ts_probe_widen(const float* in, double* out, size_t n, void* stream);
+
 /* Time-step limit of the grid's explicit stage operator (the Courant limits of
  * Sect. 5.4, every axis included, taken from the discrete operator itself):
  * power iteration on the linear part A x = K(x) - K(0) of the stage derivative

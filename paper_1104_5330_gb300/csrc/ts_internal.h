@@ -11,6 +11,19 @@
 
 namespace ts {
 
+// Exact widening of a float to a double by the IEEE-754 binary32 and binary64
+// layouts (sign kept, exponent rebiased by 1023 - 127 = 896, significand shifted
+// up by 52 - 23 = 29 bits), on the integer units; zero maps to zero, and the rare
+// subnormal, infinite or NaN inputs take the conversion instruction. Used where
+// the FP64 pipe, not the integer units, bounds a pass.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (e == 0xFFu || (e == 0u && m != 0u)) return (double)f;
+  const uint64_t mag = e ? ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29) : 0ull;
+  return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | mag));
+}
+
 // Device fields are read and written with 16-byte vector accesses and
 // 16-byte asynchronous copies: the entry points require 16-byte alignment.
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -3,6 +3,8 @@
 // transport passes in FP64 are bound by this rate (their arithmetic intensity
 // is far above the FP64 ridge), so the probe gives their roofline denominator
 // a measured counterpart to the one derived from unit counts and clocks.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "ts_internal.h"
@@ -64,7 +66,22 @@ ts_status probe(double* tflops, cudaStream_t st) {
   return TS_OK;
 }
 
+__global__ void k_widen_probe(const float* __restrict__ in, double* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = ts::widen_f32(in[i]);
+}
+
 }  // namespace
+
+extern "C" ts_status ts_probe_widen(const float* in, double* out, size_t n, void* stream) {
+  if ((!in || !out) && n) return ts::fail_status(TS_ERR_ARG, "ts_probe_widen: null pointer");
+  if (n == 0) return TS_OK;
+  const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_widen_probe<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(in, out, n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TS_OK : ts::cuda_status(e, "ts_probe_widen");
+}
 
 extern "C" ts_status ts_probe_fma_rate(int precision, double* tflops, void* stream) {
   if (!tflops) return ts::fail_status(TS_ERR_ARG, "ts_probe_fma_rate: null output");

@@ -94,6 +94,7 @@ def _load():
         "ts_set_wait_limit": [P, ctypes.c_longlong],
         "ts_stable_dt": [P, P, I, ctypes.POINTER(D), ctypes.POINTER(D), P],
         "ts_probe_fma_rate": [I, ctypes.POINTER(D), P],
+        "ts_probe_widen": [P, P, ctypes.c_size_t, P],
         "ts_cons2d_create": [ctypes.POINTER(Cons2DDesc), ctypes.POINTER(P)],
         "ts_cons2d_destroy": [P],
         "ts_cons2d_nodes": [P, P, P],
@@ -147,6 +148,13 @@ def _stream(stream):
 
 def ts_version() -> str:
     return LIB.ts_version().decode()
+
+
+def ts_probe_widen(x, out=None, stream=None):
+    """float32 device tensor -> float64 by the library's integer-unit widening."""
+    out = torch.empty(x.shape, dtype=torch.float64, device=x.device) if out is None else out
+    _check(LIB.ts_probe_widen(_ptr(x), _ptr(out), x.numel(), _stream(stream)), "ts_probe_widen")
+    return out
 
 
 def ts_probe_fma_rate(precision: int, stream=None) -> float:

@@ -218,6 +218,23 @@ def test_misaligned_fields_are_rejected():
     assert torch.isfinite(good).all()
 
 
+def test_fp64_row_widening_is_exact():
+    """The integer-unit float -> double widening of the FP32_R64 end rows equals
+    the conversion instruction bit for bit: a stride-4099 sweep of all 2^32 bit
+    patterns (every exponent and sign) and the special values."""
+    ts = T()
+    pats = np.arange(0, 2**32, 4099, dtype=np.uint64).astype(np.uint32)
+    specials = np.array([0.0, -0.0, np.inf, -np.inf, 1e-45, -1e-45, 1.17549435e-38,
+                         3.4028235e38, 1.0, -1.0], dtype=np.float32).view(np.uint32)
+    bits = np.concatenate([pats, specials])
+    x = torch.as_tensor(bits.view(np.float32).copy(), device="cuda")
+    got = ts.ts_probe_widen(x)
+    ref = x.double()
+    nan = torch.isnan(ref)
+    assert torch.equal(torch.isnan(got), nan)
+    assert torch.equal(got[~nan].view(torch.int64), ref[~nan].view(torch.int64))
+
+
 def test_fp32_variant_against_oracle():
     og, gg = pair(*RAGGED, G=2, precision=1)
     kap, eta, ks, F0, gR1, gR2 = absorber_workload(og)

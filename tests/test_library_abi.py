@@ -69,6 +69,11 @@ def test_misaligned_fields_are_rejected_before_any_device_work(T):
     assert "aligned" in T.LIB.ts_last_error().decode()
 
 
+def test_probe_widen_arguments(T):
+    assert T.LIB.ts_probe_widen(None, None, 0, None) == T.TS_OK
+    assert T.LIB.ts_probe_widen(None, None, 5, None) == T.TS_ERR_ARG
+
+
 def test_new_entry_points_reject_null_grids(T):
     assert T.LIB.ts_set_scattering_anisotropy(None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_set_scattering_quadrupole(None, None, None) == T.TS_ERR_ARG
