@@ -1522,9 +1522,10 @@ __device__ __forceinline__ void radial_tile_rb(const Problem& p, const Tables<C>
 }
 
 // One tile per CTA with the radial line length fixed at compile time.
-// Three CTAs per SM in float (its RB = 2 blocks fit 85 registers), two in double.
+// Four CTAs per SM in float (64 registers: a few bytes of spills, more warps to
+// hide the latency of the line loads), two in double.
 template <typename T, typename C, int Nr_>
-__global__ void __launch_bounds__(kThreads, sizeof(C) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, sizeof(C) == 4 ? 4 : 2)
 k_radial_eo(Problem p, Tables<C> t, const double* __restrict__ Dr64, const T* U, const T* Kin,
             C sgn, int tau, int mode, T* F, T* Acc, T* Uout, T* out, C dt, int W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
