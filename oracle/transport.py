@@ -542,6 +542,17 @@ class GridZonedR(Grid):
         c = _along(gB.cheb_C, c, AX_R)
         return _along(gB.cheb_V, c, AX_R)
 
+    def _outward(self):
+        """Directions whose inflow is at R1 (cos Theta > 0)."""
+        return np.cos(self.Theta) > 0
+
+    def _tau_profile(self, b):
+        """T_N(x_i) / T_N(x_b) on the central nodes: the shape of the Tau
+        correction (the top Chebyshev mode, normalised at the interface b)."""
+        nB = self.nB
+        tN = np.cos(np.pi * (nB - 1 - np.arange(nB)))    # T_N on the central nodes (ascending)
+        return tN / tN[b]
+
     def d_r_zoned(self, F):
         """The radial derivative of every direction (see the class notes)."""
         h = self.hA
@@ -552,22 +563,21 @@ class GridZonedR(Grid):
         fwd[:, :-1] = (F[:, 1:] - F[:, :-1]) / h
         dB = self._dB(F)
         nB = self.nB
-        tN = np.cos(np.pi * (nB - 1 - np.arange(nB)))    # T_N on the central nodes (ascending)
         out = np.zeros_like(F)
-        outward = np.cos(self.Theta) > 0
+        outward = self._outward()
         for kk in range(self.NT):
             sl = (slice(None), slice(None), slice(None), slice(None), kk)
             if outward[kk]:   # from R1: zone A backward, inflow interface iB0
                 out[sl][:, :iB0 + 1] = back[sl][:, :iB0 + 1]
                 b, dfd = 0, back[sl][:, iB0]
-                dz = dB[sl] + (dfd - dB[sl][:, b])[:, None] * (tN / tN[b])[None, :, None, None, None]
+                dz = dB[sl] + (dfd - dB[sl][:, b])[:, None] * self._tau_profile(b)[None, :, None, None, None]
                 out[sl][:, iB0:iB1 + 1] = dz
                 out[sl][:, iB0] = dfd
                 out[sl][:, iB1 + 1:] = back[sl][:, iB1 + 1:]
             else:             # from R2: zone C forward, inflow interface iB1
                 out[sl][:, iB1:] = fwd[sl][:, iB1:]
                 b, dfd = nB - 1, fwd[sl][:, iB1]
-                dz = dB[sl] + (dfd - dB[sl][:, b])[:, None] * (tN / tN[b])[None, :, None, None, None]
+                dz = dB[sl] + (dfd - dB[sl][:, b])[:, None] * self._tau_profile(b)[None, :, None, None, None]
                 out[sl][:, iB0:iB1 + 1] = dz
                 out[sl][:, iB1] = dfd
                 out[sl][:, :iB0] = fwd[sl][:, :iB0]
