@@ -845,6 +845,12 @@ class Problem:
         return lam_n, gk, ge
 
 
+    def _ab2_adjoint_weights(self, first):
+        """Weights of dObj/dF_{n+1} and dObj/dF_{n+2} in the stage-derivative
+        adjoint mu_n: K_n enters step n with dt (the start) or 3/2 dt, and step
+        n+1 with -1/2 dt."""
+        return (1.0 if first else 1.5), -0.5
+
     def adjoint_step_ab2(self, F_n, lam, lam_prev, dt, first):
         """Discrete adjoint of one AB2 step (filter off). The forward marching
         F_{n+1} = F_n + dt (3/2 K_n - 1/2 K_{n-1}) (n >= 1) and F_1 = F_0 + dt K_0
@@ -859,7 +865,8 @@ class Problem:
         if self.filter_on:
             raise NotImplementedError("adjoint covers steps without the filter")
         self._q = self.g.quadrature_weights_direction()
-        mu = dt * ((1.0 if first else 1.5) * lam - 0.5 * lam_prev)
+        w, w_prev = self._ab2_adjoint_weights(first)
+        mu = dt * (w * lam + w_prev * lam_prev)
         lt = self.g.tau_T(mu) if self.bc == "tau" else mu
         ge = lt.sum(axis=(-2, -1))
         gk = -(lt * F_n).sum(axis=(-2, -1))
