@@ -44,15 +44,21 @@ Readings (the same as the 5-D oracle where they overlap):
   * Boundaries: Tau inflow rows on every stage derivative (inflow at R1 where
     cos Th > 0, at R2 where cos Th < 0) or none (operator and balance tests).
   * Time: classical RK4.
+  * Three-zone radial grid (App. B, optional): the r derivative and radial
+    integrals of the 5-D oracle's three-zone grid (first-order upwind edge
+    zones, a Chebyshev central zone joined by the interface Tau correction,
+    trapezoid + Clenshaw-Curtis); the outer inflow nodes hold their data (zero
+    rate) in place of the Tau rows. The number balance is then exact only up to
+    the edge zones' first-order differences.
 The paper's own 2-D solver advances the radial term implicitly with a per-angle
-optimal step and finite-difference edge zones; that time scheme is out of
-scope here (the conservative variable and its discrete balance are built).
+optimal step; that time scheme is out of scope here (the conservative variable
+and its discrete balance are built).
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .transport import Grid as _Grid5
+from .transport import Grid as _Grid5, GridZonedR as _GridZ5
 
 
 def _fejer(N):
@@ -66,13 +72,17 @@ def _fejer(N):
 class Grid2D:
     """Nodes, derivatives and quadratures of the (r, Theta) grid."""
 
-    def __init__(self, R1, R2, Nr, NTheta):
+    def __init__(self, R1, R2, Nr, NTheta, zone_nodes=0, zone_width=0.0):
         if Nr < 3 or NTheta % 2 or NTheta < 2:
             raise ValueError("need Nr >= 3 and an even NTheta")
         # the radial machinery of the 5-D oracle (coefficient-space Chebyshev)
         self._g5 = _Grid5(R1, R2, Nr, 2, 2, NTheta, 2)
         self.R1, self.R2, self.Nr, self.NT = float(R1), float(R2), Nr, NTheta
         self.r = self._g5.r
+        # three-zone radial grid: the 5-D oracle's zoned grid on the same Theta nodes
+        self.zoned = zone_nodes > 0
+        self._gz = (_GridZ5(R1, R2, Nr, 2, 2, NTheta, 2, zone_nodes=zone_nodes,
+                            zone_width=zone_width) if self.zoned else None)
         self.Theta = np.pi * (np.arange(NTheta) + 0.5) / NTheta
         self.wF = _fejer(NTheta)                      # int g sin Th dTh
         # Clenshaw-Curtis weights on the Gauss-Lobatto nodes (int dr): the
@@ -82,10 +92,18 @@ class Grid2D:
         ev = k % 2 == 0
         ints[ev] = 2.0 / (1.0 - k[ev].astype(float) ** 2)   # int_{-1}^{1} T_k dx
         self.wr = (ints @ self._g5.cheb_S) * 0.5 * (R2 - R1)
+        if self.zoned:
+            self.r = self._gz.r
+            self.wr = self._gz.clenshaw_curtis_r(np.eye(Nr), axis=1)
 
     # -------------------------------------------------------------- derivatives
     def d_r(self, F):
-        """d/dr along axis 1 of [P][Nr][NT]."""
+        """d/dr along axis 1 of [P][Nr][NT] (on the three-zone grid: per
+        direction, each zone's rate taken from the direction's upstream side)."""
+        if self.zoned:
+            F6 = np.ascontiguousarray(np.broadcast_to(F[:, :, None, None, :, None],
+                                                      (F.shape[0], self.Nr, 2, 2, self.NT, 2)))
+            return self._gz.d_r_zoned(F6)[:, :, 0, 0, :, 0]
         c = np.tensordot(self._g5.cheb_S, F, axes=([1], [1]))
         c = np.tensordot(self._g5.cheb_C, c, axes=([1], [0]))
         return np.moveaxis(np.tensordot(self._g5.cheb_V, c, axes=([1], [0])), 0, 1)
@@ -172,6 +190,12 @@ class Problem2D:
         g = self.g
         if self.bc == "none":
             return K
+        if g.zoned:   # three-zone grid: the outer inflow nodes hold their data
+            out = K.copy()
+            b = g.inflow_node()
+            for k in range(g.NT):
+                out[:, b[k], k] = gdot
+            return out
         N = g.Nr - 1
         tN = np.cos(np.pi * (N - np.arange(g.Nr)))     # T_N(x_i) on the Gauss-Lobatto nodes
         b = g.inflow_node()

@@ -59,6 +59,42 @@ def test_plain_form_is_the_5d_oracle_on_spherically_symmetric_data(bc, c):
     assert np.abs(K5[:, :, 0, 0, :, 0] - K2).max() < 1e-12 * np.abs(K2).max()
 
 
+@pytest.mark.parametrize("bc", ["none", "tau"])
+@pytest.mark.parametrize("form", ["plain", "hat"])
+def test_three_zone_2d_is_the_5d_three_zone_oracle_on_spherically_symmetric_data(bc, form):
+    """On the three-zone radial grid of App. B, the plain 2-D form equals the 5-D
+    oracle's three-zone grid (itself pinned) on spherically symmetric data, held
+    inflow nodes included; the conservative form's radial term is the same zoned
+    derivative of Fhat (its Theta and scattering terms are the Chebyshev grid's)."""
+    from oracle.transport import GridZonedR
+    nA, nB = 5, 9
+    Nr = 2 * (nA - 1) + nB
+    g = Grid2D(R1, R2, Nr, 8, zone_nodes=nA, zone_width=0.1)
+    gc = Grid2D(R1, R2, Nr, 8)
+    P = 2
+    F = _smooth(g, P, 1, 6, 5)
+    ks = _ks(g, P)
+    if form == "plain":
+        K2 = Problem2D(g, ks, c=0.75, form="plain", bc=bc).rhs(F)
+        g5 = GridZonedR(R1, R2, Nr, 4, 4, 8, 6, groups=P, zone_nodes=nA, zone_width=0.1)
+        F5 = np.ascontiguousarray(np.broadcast_to(F[:, :, None, None, :, None], g5.shape))
+        ks5 = np.ascontiguousarray(np.broadcast_to(ks[:, :, None, None], (P, Nr, 4, 4)))
+        pr5 = Problem5(g5, None, None, ks5, F5[:, 0, :, :, :4], F5[:, -1, :, :, 4:], bc=bc,
+                       scatter_c=0.75)
+        K5 = pr5.rhs(F5)
+        assert np.abs(K5[:, :, 0, 0, :, 0] - K2).max() < 1e-12 * np.abs(K2).max()
+    else:
+        # the zoned conservative operator minus the Chebyshev one on the same nodes is
+        # -cos(Th) times the difference of their r derivatives (Tau/hold rows aside)
+        Kz = Problem2D(g, ks, form="hat", bc="none").rhs(F)
+        gc.r = g.r   # the same nodes for the non-radial terms
+        pc = Problem2D(gc, ks, form="hat", bc="none")
+        diff = Kz - pc.rhs(F)
+        ct = np.cos(g.Theta)[None, None, :]
+        expect = -ct * (g.d_r(F) - gc.d_r(F))
+        assert np.abs(diff - expect).max() < 1e-12 * np.abs(Kz).max()
+
+
 @pytest.mark.parametrize("c", [0.0, 0.75])
 def test_conservative_form_is_the_plain_form_times_the_jacobian(c):
     g = Grid2D(R1, R2, 11, 12)
