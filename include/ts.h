@@ -425,15 +425,24 @@ ts_status ts_batch_step(ts_batch* batch, void* const* F_host_array, const double
  * (TS_BC_TAU_INFLOW: the rate at each direction's inflow node is zero) or none.
  * FP64. Fields: Fhat[P][Nr][NTheta] (device doubles), P independent problems
  * stepped together, each by one CTA holding its whole grid in shared memory
- * (TS_ERR_UNSUPPORTED if a problem's working set exceeds it). The paper's own
- * 2-D time scheme (implicit radial update, finite-difference edge zones) is not
- * this one. */
+ * (TS_ERR_UNSUPPORTED if a problem's working set exceeds it). radial =
+ * TS_RADIAL_ZONED puts the problem on the three-zone radial grid of App. B (as
+ * for ts_grid_desc: zone_nodes uniform nodes with upwind differences in each edge
+ * zone of width zone_width (R2-R1), Chebyshev in the central zone, the interface
+ * Tau correction; the outer inflow nodes hold their data in place of the Tau
+ * rows; radial integrals trapezoid + Clenshaw-Curtis), the configuration the
+ * paper runs this problem on; the balance is then exact only up to the edge
+ * zones' first-order differences. The paper's own 2-D time scheme (an implicit
+ * radial update) is not this one. */
 typedef struct {
   double R1, R2;        /* shell radii, 0 < R1 < R2 */
   int Nr, NTheta;       /* 3 <= Nr <= 129; NTheta even, 2..64 */
   int problems;         /* independent problems */
   double scatter_c;     /* kernel parameter c */
   int bc;               /* ts_bc */
+  int radial;           /* TS_RADIAL_CHEBYSHEV (0) or TS_RADIAL_ZONED */
+  int zone_nodes;       /* TS_RADIAL_ZONED: nodes per edge zone (>= 2) */
+  double zone_width;    /* TS_RADIAL_ZONED: edge-zone width / (R2-R1), in (0, 1/2) */
 } ts_cons2d_desc;
 
 typedef struct ts_cons2d ts_cons2d;   /* opaque, library-owned */

@@ -32,7 +32,8 @@ namespace {
 constexpr int kC2Threads = 256;
 
 struct C2Tables {
-  const double* Dr;    // [Nr][Nr] d/dr, [out][in]
+  const double* Dr;    // [Nr][Nr] d/dr, [out][in] (three-zone grid: directions with cos Th > 0)
+  const double* Dr2;   // three-zone grid: d/dr of the directions with cos Th < 0
   const double* Dt;    // [NT][NT] d/dTh of odd functions on the doubled circle, [out][in]
   const double* cT;    // cos Th_k
   const double* sT;    // sin Th_k
@@ -45,24 +46,27 @@ struct C2Tables {
 struct C2Problem {
   int Nr, NT, P;
   double c;            // kernel parameter
-  int tau;             // Tau inflow rows
+  int tau;             // Tau inflow rows (three-zone grid: held outer inflow nodes)
+  int zoned;           // three-zone radial grid: Dr / Dr2 by direction
   const double* ks;    // [P][Nr] kappa_s
   const double* g1;    // [P][NT/2] inflow Fhat at R1 (cos Th > 0)
   const double* g2;    // [P][NT/2] inflow Fhat at R2 (cos Th < 0)
 };
 
 // Shared layout (doubles): Dr | Dt | cT sT q ir ts wr | ks | F U K Acc | row sums 4 Nr | kb NT
-__host__ __device__ inline size_t c2_smem(int Nr, int NT) {
+// | Dr2 (three-zone grid)
+__host__ __device__ inline size_t c2_smem(int Nr, int NT, bool zoned = false) {
   const size_t n = (size_t)Nr * NT;
   return ((size_t)Nr * Nr + (size_t)NT * NT + 3 * (size_t)NT + 4 * (size_t)Nr + 4 * n +
-          4 * (size_t)Nr + 2 * (size_t)NT + 4) * sizeof(double);
+          4 * (size_t)Nr + 2 * (size_t)NT + 4 + (zoned ? (size_t)Nr * Nr : 0)) *
+         sizeof(double);
 }
 
 // K = rhs(U) for one problem, all in shared memory; tau: Tau rows.
-__device__ void c2_rhs(const C2Problem& z, const double* Dr, const double* Dt, const double* cT,
-                       const double* sT, const double* q, const double* ir, const double* ts,
-                       const double* ks, const double* U, double* K, double* rows, double* kb,
-                       bool tau) {
+__device__ void c2_rhs(const C2Problem& z, const double* Dr, const double* Dr2, const double* Dt,
+                       const double* cT, const double* sT, const double* q, const double* ir,
+                       const double* ts, const double* ks, const double* U, double* K,
+                       double* rows, double* kb, bool tau) {
   const int Nr = z.Nr, NT = z.NT, n = Nr * NT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double* nyq = rows;            // Nyquist coefficient of each row
@@ -96,7 +100,8 @@ __device__ void c2_rhs(const C2Problem& z, const double* Dr, const double* Dt, c
   for (int x = threadIdx.x; x < n; x += blockDim.x) {
     const int i = x / NT, k = x - i * NT;
     double dr = 0, dt = 0;
-    for (int ii = 0; ii < Nr; ++ii) dr = fma(Dr[i * Nr + ii], U[ii * NT + k], dr);
+    const double* D = (z.zoned && !(cT[k] > 0)) ? Dr2 : Dr;   // three-zone grid: by direction
+    for (int ii = 0; ii < Nr; ++ii) dr = fma(D[i * Nr + ii], U[ii * NT + k], dr);
     for (int kk = 0; kk < NT; ++kk) dt = fma(Dt[k * NT + kk], U[i * NT + kk], dt);
     const double u = U[x];
     const double pu = u - ((k & 1) ? -nyq[i] : nyq[i]);
@@ -107,7 +112,10 @@ __device__ void c2_rhs(const C2Problem& z, const double* Dr, const double* Dt, c
     K[x] = stream + ks[i] * (gain - u);
   }
   __syncthreads();
-  if (tau) {
+  if (tau && z.zoned) {   // three-zone grid: each direction's outer inflow node holds its data
+    for (int k = threadIdx.x; k < NT; k += blockDim.x) K[(cT[k] > 0 ? 0 : Nr - 1) * NT + k] = 0.0;
+    __syncthreads();
+  } else if (tau) {
     for (int k = threadIdx.x; k < NT; k += blockDim.x) {
       const int b = cT[k] > 0 ? 0 : Nr - 1;
       kb[k] = -K[b * NT + k] * ts[b];   // alpha = (0 - K(r_b)) / T_N(x_b), T_N(x_b) = +-1
@@ -145,7 +153,10 @@ k_cons2d(C2Problem z, C2Tables t, double* Fh, double* Kout, double* out, double*
   double* Acc = K + n;
   double* rows = Acc + n;
   double* kb = rows + 4 * Nr;
+  double* Dr2 = kb + NT + 4;
   for (int x = threadIdx.x; x < Nr * Nr; x += blockDim.x) Dr[x] = t.Dr[x];
+  if (z.zoned)
+    for (int x = threadIdx.x; x < Nr * Nr; x += blockDim.x) Dr2[x] = t.Dr2[x];
   for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) Dt[x] = t.Dt[x];
   for (int x = threadIdx.x; x < NT; x += blockDim.x) {
     cT[x] = t.cT[x];
@@ -163,12 +174,12 @@ k_cons2d(C2Problem z, C2Tables t, double* Fh, double* Kout, double* out, double*
   __syncthreads();
   const bool tau = z.tau != 0;
   if (mode == 1) {
-    c2_rhs(z, Dr, Dt, cT, sT, q, ir, ts, ks, F, K, rows, kb, tau);
+    c2_rhs(z, Dr, Dr2, Dt, cT, sT, q, ir, ts, ks, F, K, rows, kb, tau);
     for (int x = threadIdx.x; x < n; x += blockDim.x) Kout[(long long)p * n + x] = K[x];
     return;
   }
   if (mode == 2) {
-    c2_rhs(z, Dr, Dt, cT, sT, q, ir, ts, ks, F, K, rows, kb, false);
+    c2_rhs(z, Dr, Dr2, Dt, cT, sT, q, ir, ts, ks, F, K, rows, kb, false);
     // per row: int dTh of K and of Fhat (warp sums), then fixed-order sums over r
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = warp; i < Nr; i += nw) {
@@ -207,7 +218,7 @@ k_cons2d(C2Problem z, C2Tables t, double* Fh, double* Kout, double* out, double*
   }
   for (int step = 0; step < nsteps; ++step) {
     for (int s = 0; s < 4; ++s) {
-      c2_rhs(z, Dr, Dt, cT, sT, q, ir, ts, ks, s == 0 ? F : U, K, rows, kb, tau);
+      c2_rhs(z, Dr, Dr2, Dt, cT, sT, q, ir, ts, ks, s == 0 ? F : U, K, rows, kb, tau);
       for (int x = threadIdx.x; x < n; x += blockDim.x) {
         const double k = K[x];
         if (s == 0) {
@@ -264,18 +275,80 @@ ts_status ts_cons2d_create(const ts_cons2d_desc* desc, ts_cons2d** out) {
     return ts::fail_status(TS_ERR_UNSUPPORTED, "sizes: need 3 <= Nr <= 129, even 2 <= NTheta <= 64");
   if (d.bc != TS_BC_TAU_INFLOW && d.bc != TS_BC_NONE)
     return ts::fail_status(TS_ERR_UNSUPPORTED, "unknown bc");
-  if (c2_smem(d.Nr, d.NTheta) > 227 * 1024)
+  if (d.radial != TS_RADIAL_CHEBYSHEV && d.radial != TS_RADIAL_ZONED)
+    return ts::fail_status(TS_ERR_UNSUPPORTED, "radial: TS_RADIAL_CHEBYSHEV or TS_RADIAL_ZONED");
+  const bool zoned = d.radial == TS_RADIAL_ZONED;
+  if (zoned && (d.zone_nodes < 2 || d.Nr - 2 * (d.zone_nodes - 1) < 3 || !(d.zone_width > 0.0) ||
+                !(d.zone_width < 0.5)))
+    return ts::fail_status(TS_ERR_UNSUPPORTED,
+                           "zoned radial grid: need zone_nodes >= 2, Nr - 2 (zone_nodes - 1) >= 3, "
+                           "0 < zone_width < 1/2");
+  if (c2_smem(d.Nr, d.NTheta, zoned) > 227 * 1024)
     return ts::fail_status(TS_ERR_UNSUPPORTED, "tile too large for one CTA's shared memory");
   const int Nr = d.Nr, NT = d.NTheta, N = Nr - 1;
   ts_cons2d* G = new ts_cons2d();
   G->desc = d;
-  for (int i = 0; i < Nr; ++i)
-    G->r.push_back(0.5 * (d.R1 + d.R2) - 0.5 * (d.R2 - d.R1) * std::cos(M_PI * i / N));
+  // three-zone grid (App. B): nA uniform nodes per edge zone of width w, the nB
+  // Gauss-Lobatto nodes of [R1 + w, R2 - w] between them (shared interfaces)
+  const int nA = zoned ? d.zone_nodes : 0, nB = zoned ? Nr - 2 * (nA - 1) : 0;
+  const double zw = zoned ? d.zone_width * (d.R2 - d.R1) : 0.0, zh = zoned ? zw / (nA - 1) : 0.0;
+  const int iB0 = nA - 1, iB1 = nA - 1 + nB - 1;
+  for (int i = 0; i < Nr; ++i) {
+    if (!zoned) {
+      G->r.push_back(0.5 * (d.R1 + d.R2) - 0.5 * (d.R2 - d.R1) * std::cos(M_PI * i / N));
+    } else {
+      const double a = d.R1 + zw, b = d.R2 - zw;
+      if (i < nA) G->r.push_back(d.R1 + zh * i);
+      else if (i < iB1) G->r.push_back(0.5 * (a + b) - 0.5 * (b - a) * std::cos(M_PI * (i - iB0) / (nB - 1)));
+      else G->r.push_back(b + zh * (i - iB1));
+    }
+  }
   for (int k = 0; k < NT; ++k) G->Theta.push_back(M_PI * (k + 0.5) / NT);
   // tables: d/dr; d/dTh of odd functions on the doubled circle (A - B of its
   // Fourier derivative, node 2NT-1-k' carrying -Fhat(k')); Fejer / sin Th;
   // 1/r; T_N(x_i); Clenshaw-Curtis x (R2-R1)/2
-  std::vector<double> Dr = ts::cheb_diff_matrix(Nr, d.R1, d.R2);
+  std::vector<double> Dr = zoned ? std::vector<double>((size_t)Nr * Nr, 0.0)
+                                 : ts::cheb_diff_matrix(Nr, d.R1, d.R2);
+  std::vector<double> Dr2 = Dr;
+  if (zoned) {
+    // the zoned derivative of each direction class as a matrix ([out][in]):
+    // upwind differences in the edge zones (none at the outer inflow node), the
+    // central Chebyshev rows plus the interface Tau correction
+    //   d(i) += T_N(x_i)/T_N(x_b) (dFD(b) - dB(b)),  b the inflow interface,
+    // every row linear in the line's values
+    const std::vector<double> DB = ts::cheb_diff_matrix(nB, d.R1 + zw, d.R2 - zw);
+    auto tN = [&](int j) { return ((nB - 1 - j) % 2) ? -1.0 : 1.0; };
+    for (int dir = 0; dir < 2; ++dir) {   // 0: cos Th > 0 (inflow at R1), 1: cos Th < 0
+      std::vector<double>& Z = dir == 0 ? Dr : Dr2;
+      const int b = dir == 0 ? 0 : nB - 1;          // central inflow interface
+      // dFD(b) - dB(b) as a row over the line
+      std::vector<double> c((size_t)Nr, 0.0);
+      if (dir == 0) {
+        c[iB0] += 1.0 / zh;
+        c[iB0 - 1] -= 1.0 / zh;
+      } else {
+        c[iB1 + 1] += 1.0 / zh;
+        c[iB1] -= 1.0 / zh;
+      }
+      for (int j = 0; j < nB; ++j) c[iB0 + j] -= DB[(size_t)b * nB + j];
+      for (int i = 0; i < Nr; ++i) {
+        double* row = &Z[(size_t)i * Nr];
+        const bool central = dir == 0 ? (i > iB0 && i <= iB1) : (i >= iB0 && i < iB1);
+        if (central) {
+          const int ib = i - iB0;
+          for (int j = 0; j < nB; ++j) row[iB0 + j] += DB[(size_t)ib * nB + j];
+          const double s = tN(ib) / tN(b);
+          for (int j = 0; j < Nr; ++j) row[j] += s * c[j];
+        } else if (dir == 0 && i > 0) {
+          row[i] += 1.0 / zh;
+          row[i - 1] -= 1.0 / zh;
+        } else if (dir == 1 && i < N) {
+          row[i + 1] += 1.0 / zh;
+          row[i] -= 1.0 / zh;
+        }
+      }
+    }
+  }
   const std::vector<double> Dc = ts::fourier_diff_matrix(2 * NT);
   std::vector<double> Dt((size_t)NT * NT);
   for (int k = 0; k < NT; ++k)
@@ -294,7 +367,17 @@ ts_status ts_cons2d_create(const ts_cons2d_desc* desc, ts_cons2d** out) {
     tsg[i] = ((N - i) % 2) ? -1.0 : 1.0;
     wr[i] = cc[i] * 0.5 * (d.R2 - d.R1);
   }
-  std::vector<const std::vector<double>*> parts = {&Dr, &Dt, &cT, &sT, &q, &ir, &tsg, &wr};
+  if (zoned) {   // trapezoid in the edge zones, Clenshaw-Curtis in the central one
+    const std::vector<double> ccB = ts::clenshaw_curtis_weights(nB);
+    std::fill(wr.begin(), wr.end(), 0.0);
+    for (int i = 0; i < nA; ++i) {
+      const double t = zh * ((i == 0 || i == nA - 1) ? 0.5 : 1.0);
+      wr[i] += t;
+      wr[iB1 + i] += t;
+    }
+    for (int j = 0; j < nB; ++j) wr[iB0 + j] += ccB[j] * 0.5 * (d.R2 - d.R1 - 2 * zw);
+  }
+  std::vector<const std::vector<double>*> parts = {&Dr, &Dr2, &Dt, &cT, &sT, &q, &ir, &tsg, &wr};
   size_t tot = 0;
   for (auto* v : parts) tot += v->size();
   std::vector<double> host;
@@ -303,7 +386,8 @@ ts_status ts_cons2d_create(const ts_cons2d_desc* desc, ts_cons2d** out) {
   cudaError_t e = cudaMalloc(&G->tab, tot * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpy(G->tab, host.data(), tot * sizeof(double), cudaMemcpyHostToDevice);
   const double* ptr = G->tab;
-  const double** slots[] = {&G->t.Dr, &G->t.Dt, &G->t.cT, &G->t.sT, &G->t.q, &G->t.ir, &G->t.ts, &G->t.wr};
+  const double** slots[] = {&G->t.Dr, &G->t.Dr2, &G->t.Dt, &G->t.cT, &G->t.sT,
+                            &G->t.q,  &G->t.ir,  &G->t.ts, &G->t.wr};
   for (size_t a = 0; a < parts.size(); ++a) {
     *slots[a] = ptr;
     ptr += parts[a]->size();
@@ -368,6 +452,7 @@ static C2Problem c2_problem(const ts_cons2d* g) {
   z.P = g->desc.problems;
   z.c = g->desc.scatter_c;
   z.tau = g->desc.bc == TS_BC_TAU_INFLOW ? 1 : 0;
+  z.zoned = g->desc.radial == TS_RADIAL_ZONED ? 1 : 0;
   z.ks = g->ks;
   z.g1 = g->g1;
   z.g2 = g->g2;
@@ -383,7 +468,7 @@ static ts_status c2_launch(ts_cons2d* g, double* Fh, double* K, double* out, dou
     if (e != cudaSuccess) return ts::cuda_status(e, where);
     init = true;
   }
-  const size_t smem = c2_smem(g->desc.Nr, g->desc.NTheta);
+  const size_t smem = c2_smem(g->desc.Nr, g->desc.NTheta, g->desc.radial == TS_RADIAL_ZONED);
   k_cons2d<<<g->desc.problems, kC2Threads, smem, static_cast<cudaStream_t>(stream)>>>(
       c2_problem(g), g->t, Fh, K, out, out2, dt, nsteps, mode);
   cudaError_t e = cudaGetLastError();

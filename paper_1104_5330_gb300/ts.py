@@ -53,7 +53,9 @@ class GridDesc(ctypes.Structure):
 class Cons2DDesc(ctypes.Structure):
     _fields_ = [("R1", ctypes.c_double), ("R2", ctypes.c_double), ("Nr", ctypes.c_int),
                 ("NTheta", ctypes.c_int), ("problems", ctypes.c_int),
-                ("scatter_c", ctypes.c_double), ("bc", ctypes.c_int)]
+                ("scatter_c", ctypes.c_double), ("bc", ctypes.c_int),
+                ("radial", ctypes.c_int), ("zone_nodes", ctypes.c_int),
+                ("zone_width", ctypes.c_double)]
 
 
 def _load():
@@ -517,8 +519,10 @@ class Cons2D:
     """Owning handle of the conservative 2-D (r, Theta) variant (ts_cons2d_*):
     Fhat[P][Nr][NTheta] float64 tensors on the device."""
 
-    def __init__(self, R1, R2, Nr, NTheta, problems=1, scatter_c=0.75, bc=TS_BC_TAU_INFLOW):
-        self.desc = Cons2DDesc(R1, R2, Nr, NTheta, problems, scatter_c, bc)
+    def __init__(self, R1, R2, Nr, NTheta, problems=1, scatter_c=0.75, bc=TS_BC_TAU_INFLOW,
+                 radial=TS_RADIAL_CHEBYSHEV, zone_nodes=0, zone_width=0.0):
+        self.desc = Cons2DDesc(R1, R2, Nr, NTheta, problems, scatter_c, bc, radial, zone_nodes,
+                               zone_width)
         self.device = torch.device("cuda", torch.cuda.current_device())
         h = ctypes.c_void_p()
         _check(LIB.ts_cons2d_create(ctypes.byref(self.desc), ctypes.byref(h)), "ts_cons2d_create")
