@@ -622,7 +622,7 @@ def variant_line(ts, dims, wname, vname, vprec, pts, steps, ms, err, nv, pm, pn,
                          "algorithmic_bytes_per_launch": by[dom]}}
 
 
-def run_cons2d(args, stream):
+def run_cons2d(args, stream, zoned=False):
     """The conservative 2-D variant of App. B (Fhat = r^2 sin Th F, Eq. speccons)
     on its shell problem: 0.5 <= r <= 1, empty at t = 0, Fhat(R1, Th) =
     cos Th sin Th on the outgoing directions, Thomson scattering (c = 3/4) from
@@ -631,18 +631,22 @@ def run_cons2d(args, stream):
     65 x 24 nodes each (the paper: 65 spectral radial points and 25 in Theta),
     RK4 at dt = 0.4 h_min, every step of a call in one launch. Reports the rate
     and the operator's discrete number balance |dN/dt + J_R2 - J_R1| relative to
-    the fluxes after the run (zero to rounding: Eq. Cons)."""
+    the fluxes after the run (zero to rounding: Eq. Cons). zoned: the paper's
+    three-zone radial grid of App. B, 30 + 25 + 30 nodes (edge zones of width
+    0.1 (R2 - R1); N_r = 83), dt = 0.4 x the smallest spacing; its balance holds
+    up to the edge zones' first-order differences."""
     import torch
     import paper_1104_5330_gb300.ts as ts
-    P, Nr, NT, R1, R2 = 2048, 65, 24, 0.5, 1.0
+    P, Nr, NT, R1, R2 = 2048, (83 if zoned else 65), 24, 0.5, 1.0
     tau = np.logspace(-1, 1, P)
-    g = ts.Cons2D(R1, R2, Nr, NT, problems=P, scatter_c=0.75)
+    zk = dict(radial=ts.TS_RADIAL_ZONED, zone_nodes=30, zone_width=0.1) if zoned else {}
+    g = ts.Cons2D(R1, R2, Nr, NT, problems=P, scatter_c=0.75, **zk)
     r, th = g.nodes()
     ks = 9 * tau[:, None] / (R2 - R1) * (1 - (r[None, :] - R1) / (R2 - R1)) ** 8
     g1 = np.tile(np.cos(th[:NT // 2]) * np.sin(th[:NT // 2]), (P, 1))
     g.set_coeffs(ks, g1, None)
     X = g.apply_inflow(torch.zeros((P, Nr, NT), dtype=torch.float64, device="cuda"))
-    dt = 0.4 * 0.5 * (R2 - R1) * (1 - math.cos(math.pi / (Nr - 1)))
+    dt = 0.4 * float(np.diff(r).min())   # the smallest spacing (Gauss-Lobatto or zoned)
     g.step(X, dt, args.warmup)
     torch.cuda.synchronize()
     n = 10 * args.steps
@@ -652,17 +656,20 @@ def run_cons2d(args, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    gb = ts.Cons2D(R1, R2, Nr, NT, problems=P, scatter_c=0.75, bc=ts.TS_BC_NONE)
+    gb = ts.Cons2D(R1, R2, Nr, NT, problems=P, scatter_c=0.75, bc=ts.TS_BC_NONE, **zk)
     gb.set_coeffs(ks, g1, None)
     NJ, res = gb.balance(X)
     NJ, res = NJ.cpu().numpy(), res.cpu().numpy()
     scale = np.abs(NJ[:, 1:]).max(axis=1) + np.abs(NJ[:, 0]).max() * 1e-300
     pts = P * Nr * NT
     out = {"value": pts * n / (ms * 1e-3), "unit": "point-updates/s", "ms_per_step": ms / n,
-           "steps": n, "problems": P, "grid": [Nr, NT], "dtype": "f64", "launches_per_call": 1,
-           "workload": "App. B shell: Lambert inflow at R1, Thomson scattering, tau in [0.1, 10]",
+           "steps": n, "dt": dt, "problems": P, "grid": [Nr, NT], "dtype": "f64",
+           "launches_per_call": 1, "workload": "App. B shell: Lambert inflow at R1, Thomson scattering, tau in [0.1, 10]",
            "balance_residual_rel_max": float(np.max(np.abs(res) / scale)),
            "N_range": [float(NJ[:, 0].min()), float(NJ[:, 0].max())]}
+    if zoned:
+        out["radial"] = ("30 + 25 + 30 nodes: upwind differences in edge zones of width 0.1 "
+                         "(R2 - R1), Chebyshev in the central zone")
     g.close()
     gb.close()
     return out
@@ -916,6 +923,7 @@ def run_ours(args, dims, wname):
             ["fp64", "fp32", "fp32_r64", "tf32x3", "bf16x3", "fp64+filter"], 10)
     if not args.skip_workloads:
         line["conservative_2d"] = run_cons2d(args, stream)
+        line["conservative_2d_zoned"] = run_cons2d(args, stream, zoned=True)
     if not args.skip_aniso:
         line["anisotropic_scattering"] = run_anisotropic(args, dims, stream)
         line["ab2"] = run_ab2(args, dims, stream, ms / args.steps)
