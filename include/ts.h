@@ -135,6 +135,29 @@ typedef enum {
                                no ts_moments_noalloc (TS_ERR_UNSUPPORTED). */
 } ts_radial;
 
+typedef enum {
+  TS_FORM_ADVECTIVE = 0,    /* the state is F; the streaming operator is Eq. Liouvsph
+                               (coefficient x derivative on every axis) */
+  TS_FORM_CONSERVATIVE = 1  /* App. A, Eq. Cohercons: the state is Fhat = r^2 sin(theta)
+                               sin(Theta) F (inflow data and ts_apply_inflow too) and
+                               the streaming operator its flux divergence:
+                                 d_r(cos Th Fhat) + d_th(sin Th cos Ph Fhat / r)
+                                 + d_ph(sin Th sin Ph Fhat / (r sin th))
+                                 - d_Th(sin Th Fhat / r) - d_Ph(sin Th sin Ph cot th Fhat / r).
+                               Fhat is odd under the double-Fourier-sphere reflections
+                               (its theta and Theta derivatives continue it with a minus
+                               sign at the partner node); the Theta flux is taken as
+                               sin Th d_Th Fhat + cos Th Fhat with the Nyquist bin of the
+                               doubled Theta circle removed from the second product, the
+                               Phi flux as the derivative of sin Ph Fhat; the collision
+                               term is r^2 sin th sin Th CT(F) at F = Fhat / (r^2 sin th
+                               sin Th). Every flux but the theta one then integrates
+                               exactly to its boundary value (ts_number_balance), the
+                               theta one to spectral accuracy. TS_FP64, TS_RADIAL_CHEBYSHEV,
+                               TS_RK4 or TS_AB2, no filter; no adjoint, moments, flux
+                               weights, batches (TS_ERR_UNSUPPORTED). */
+} ts_form;
+
 typedef struct {
   double R1, R2;                            /* shell radii, 0 < R1 < R2 */
   int Nr, Ntheta, Nphi, NTheta, NPhi;       /* nodes per axis */
@@ -149,6 +172,7 @@ typedef struct {
   int zone_nodes;                           /* TS_RADIAL_ZONED: nodes per edge zone (>= 2) */
   double zone_width;                        /* TS_RADIAL_ZONED: edge-zone width / (R2-R1),
                                                in (0, 1/2) */
+  int form;                                 /* ts_form (0: advective, the state is F) */
 } ts_grid_desc;
 
 typedef struct ts_grid ts_grid;             /* opaque, library-owned */
@@ -291,6 +315,26 @@ ts_status ts_adjoint_step_ab2(ts_grid* grid, const void* F_n, void* lambda, void
  * AB2 from a saved state F_n and K_{n-1} = K(F_{n-1}) (ts_rhs), e.g. to
  * recompute a checkpointed segment. TS_ERR_UNSUPPORTED for other schemes. */
 ts_status ts_set_history(ts_grid* grid, const void* F, const void* K_prev, void* stream);
+
+/* The number balance of App. A (Eqs. Cons, Npho, Flux) of the grid's operator at
+ * the state F, per group g: out[5 g + 0..4] = (N, J_R1, J_R2, dN/dt, S) with
+ *   N     = int F dV (TS_FORM_ADVECTIVE: int r^2 dr sin th dth dph sin Th dTh dPh F;
+ *           TS_FORM_CONSERVATIVE: int dr dth dph dTh dPh Fhat),
+ *   J_R   = the radial flux through R (Eq. Flux; int cos Th Fhat(R) for Fhat),
+ *   dN/dt = N of the stage derivative WITHOUT Tau rows (the operator itself, with
+ *           the grid's collision term),
+ *   S     = N of the absorption and emission part, eta - kappa F (times r^2 sin th
+ *           sin Th for Fhat), zero for pure scattering,
+ * so that dN/dt + J_R2 - J_R1 - S is the operator's balance error: zero to rounding
+ * for TS_FORM_CONSERVATIVE up to the theta flux's integral, and for the advective
+ * form zero only to spectral accuracy. Quadrature: Clenshaw-Curtis in r, Fejer's
+ * first rule in cos theta, cos Theta (on Fhat / sin: int h dth of h = sin th g is
+ * Fejer on g), trapezoid in phi, Phi, and the grid's radial rule (Clenshaw-Curtis
+ * on Chebyshev nodes, trapezoid on the uniform ones, both on the zoned grid); the
+ * sums run in a fixed order. Any precision. out: HOST array of 5 G doubles; the call returns
+ * after the result is copied (it synchronises the stream). Allocates and frees one
+ * field-sized scratch buffer. */
+ts_status ts_number_balance(ts_grid* grid, const void* F, double* out, void* stream);
 
 /* Weights w[Ntheta][Nphi][NTheta][NPhi] (device, double) such that the
  * outgoing radial flux J_R2 of Eq. (Flux), App. A, for group g is

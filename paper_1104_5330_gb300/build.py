@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libts.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = ["ts_api.cu", "ts_f64.cu", "ts_f32.cu", "ts_noalloc.cu", "ts_batch.cu", "ts_probe.cu",
-         "ts_fd.cu", "ts_flux.cu", "ts_cons2d.cu", "ts_zoned.cu"]
+         "ts_fd.cu", "ts_flux.cu", "ts_cons2d.cu", "ts_zoned.cu", "ts_cons5d.cu"]
 
 
 def nvcc() -> str:

@@ -466,6 +466,12 @@ HostTables build_tables(const ts_grid_desc& g) {
   h.Dph = fourier_diff(Np);
   dfs_split(fourier_diff(2 * NT), NT, h.ATh, h.BTh);
   h.DPh = fourier_diff(NP);
+  if (g.form == TS_FORM_CONSERVATIVE) {
+    // Fhat carries sin(theta) sin(Theta): its continuation to a reflected node of
+    // either doubled circle is minus its value at the partner
+    for (double& x : h.Bth) x = -x;
+    for (double& x : h.BTh) x = -x;
+  }
 
   const double fa = g.filter_alpha > 0 ? g.filter_alpha : 36.0;
   const int fo = g.filter_order > 0 ? g.filter_order : 16;
@@ -679,7 +685,15 @@ cudaError_t stage_passes(ts_grid* g, const ts::Problem& p, const Tables<C>& t, c
       return e;
     }
   }
-  TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, sgn, collision, st)));
+  if constexpr (sizeof(T) == 8 && sizeof(C) == 8) {
+    if (g->desc.form == TS_FORM_CONSERVATIVE) {
+      TS_TIMED(prof, 0, (ts::launch_angular_cons(p, g->t64, in, K, sgn, collision, st)));
+    } else {
+      TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, sgn, collision, st)));
+    }
+  } else {
+    TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, sgn, collision, st)));
+  }
   TS_TIMED(prof, 1, (Launch<T, C>::plane(p, t, in, K, sgn, st)));
   TS_TIMED(prof, 2, (radial_pass<T, C>(g, p, t, in, K, sgn, tau, mode, F, Acc, Uout, out, dt,
                                        st)));
@@ -1014,6 +1028,14 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
     return fail(TS_ERR_UNSUPPORTED,
                 "zoned radial grid: need zone_nodes >= 2, Nr - 2 (zone_nodes - 1) >= 3, "
                 "0 < zone_width < 1/2");
+  if (g.form != TS_FORM_ADVECTIVE && g.form != TS_FORM_CONSERVATIVE)
+    return fail(TS_ERR_UNSUPPORTED, "unknown form");
+  if (g.form == TS_FORM_CONSERVATIVE &&
+      (g.precision != TS_FP64 || g.radial != TS_RADIAL_CHEBYSHEV ||
+       g.scheme == TS_RK4_SPLIT_IMPLICIT || g.filter_on))
+    return fail(TS_ERR_UNSUPPORTED,
+                "the conservative form runs in TS_FP64 on the Chebyshev radial grid with "
+                "TS_RK4 or TS_AB2, unfiltered");
   const size_t es = g.precision == TS_FP64 ? 8 : 4;
   if (!fits(g, es)) return fail(TS_ERR_UNSUPPORTED, "grid too large for one shared-memory tile");
 
@@ -1112,6 +1134,19 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
     const bool ws = b >= 5 && b <= 7;
     if (e == cudaSuccess) e = cudaMemset(*bufs[b], ws && nan_ws ? 0xFF : 0, sizes[b]);
   }
+  if (e == cudaSuccess) {
+    // the number integral's weights: int r^2 dr, Fejer in cos theta and cos Theta
+    // (F); int dr and Fejer on Fhat / sin in theta and Theta (Fhat)
+    const bool cons = g.form == TS_FORM_CONSERVATIVE;
+    const Vec fT = fejer(g.NTheta);
+    Vec w;
+    for (int i = 0; i < g.Nr; ++i) w.push_back(cons ? G->h.wr[i] / (G->h.r[i] * G->h.r[i]) : G->h.wr[i]);
+    for (int j = 0; j < g.Ntheta; ++j) w.push_back(cons ? G->h.wth[j] / G->h.sin_th[j] : G->h.wth[j]);
+    for (int k = 0; k < g.NTheta; ++k) w.push_back(cons ? fT[k] / G->h.sinT[k] : fT[k]);
+    e = cudaMalloc((void**)&G->balw, w.size() * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(G->balw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemcpy(G->wr, G->h.wr.data(), g.Nr * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(G->wth, G->h.wth.data(), g.Ntheta * 8, cudaMemcpyHostToDevice);
@@ -1130,7 +1165,7 @@ ts_status ts_destroy_grid(ts_grid* g) {
   cudaDeviceSynchronize();
   void* ptrs[] = {g->tab64, g->tab32, g->kap, g->eta, g->kaps, g->gR1, g->gR2, g->U, g->K,
                   g->Acc, g->wr, g->wth, g->partN, g->partJ, g->io, g->err, g->tcb16,
-                  g->scb, g->scc, g->tcang, g->zt64, g->zt32};
+                  g->scb, g->scc, g->tcang, g->zt64, g->zt32, g->balw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (void* p : g->adj)
@@ -1404,8 +1439,8 @@ ts_status ts_adjoint_step_ab2(ts_grid* g, const void* F_n, void* lambda, void* l
   if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   if (g->desc.scheme != TS_AB2 || g->desc.filter_on)
     return fail(TS_ERR_UNSUPPORTED, "ts_adjoint_step_ab2 covers the TS_AB2 scheme without filter");
-  if (g->desc.radial != TS_RADIAL_CHEBYSHEV)
-    return fail(TS_ERR_UNSUPPORTED, "adjoint covers the Chebyshev radial grid");
+  if (g->desc.radial != TS_RADIAL_CHEBYSHEV || g->desc.form != TS_FORM_ADVECTIVE)
+    return fail(TS_ERR_UNSUPPORTED, "adjoint covers the advective form on the Chebyshev radial grid");
   s = adjoint_workspace(g);
   if (s != TS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1440,8 +1475,8 @@ ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* gra
   if (!g->coeffs) return fail(TS_ERR_STATE, "ts_set_coeffs has not been called");
   if (g->desc.scheme != TS_RK4 || g->desc.filter_on)
     return fail(TS_ERR_UNSUPPORTED, "adjoint covers the TS_RK4 scheme without filter");
-  if (g->desc.radial != TS_RADIAL_CHEBYSHEV)
-    return fail(TS_ERR_UNSUPPORTED, "adjoint covers the Chebyshev radial grid");
+  if (g->desc.radial != TS_RADIAL_CHEBYSHEV || g->desc.form != TS_FORM_ADVECTIVE)
+    return fail(TS_ERR_UNSUPPORTED, "adjoint covers the advective form on the Chebyshev radial grid");
   s = adjoint_workspace(g);
   if (s != TS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1453,6 +1488,8 @@ ts_status ts_adjoint_step(ts_grid* g, const void* F_n, void* lambda, double* gra
 
 ts_status ts_flux_weights(ts_grid* g, double* w, void* stream) {
   if (!g || !w) return fail(TS_ERR_ARG, "NULL argument");
+  if (g->desc.form != TS_FORM_ADVECTIVE)
+    return fail(TS_ERR_UNSUPPORTED, "ts_flux_weights: advective form only (ts_number_balance)");
   cudaError_t e = cudaMemcpyAsync(w, g->h.fluxw.data(), g->h.fluxw.size() * 8,
                                   cudaMemcpyHostToDevice, static_cast<cudaStream_t>(stream));
   if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
@@ -1463,6 +1500,8 @@ ts_status ts_moments(ts_grid* g, const void* F, double* F0, double* F1, double* 
                      double* JR2, void* stream) {
   ts_status s = check_F(g, F);
   if (s != TS_OK) return s;
+  if (g->desc.form != TS_FORM_ADVECTIVE)
+    return fail(TS_ERR_UNSUPPORTED, "ts_moments: advective form only (ts_number_balance)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const ts::Problem p = make_problem(g);
   cudaError_t e = g->es == 8
@@ -1471,6 +1510,53 @@ ts_status ts_moments(ts_grid* g, const void* F, double* F0, double* F1, double* 
       : Launch<float, float>::moments(p, g->t64, g->wr, g->wth, (const float*)F, F0, F1,
                                       g->partN, g->partJ, N, JR1, JR2, g->desc.R1, g->desc.R2, st);
   return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_moments");
+}
+
+ts_status ts_number_balance(ts_grid* g, const void* F, double* out, void* stream) {
+  ts_status s = check_F(g, F);
+  if (s != TS_OK) return s;
+  if (!out) return fail(TS_ERR_ARG, "ts_number_balance: out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ts::Problem p = make_problem(g);
+  const bool cons = g->desc.form == TS_FORM_CONSERVATIVE;
+  const double rho1 = cons ? 1.0 : g->desc.R1 * g->desc.R1;
+  const double rho2 = cons ? 1.0 : g->desc.R2 * g->desc.R2;
+  void* K = nullptr;
+  double* part = nullptr;   // [nblk][5] block shares, then [G][5] results
+  cudaError_t e = cudaMalloc(&K, field_bytes(g));
+  if (e == cudaSuccess)
+    e = cudaMalloc((void**)&part, ((size_t)g->d.nblk + (size_t)g->d.G) * 5 * sizeof(double));
+  if (e == cudaSuccess) {
+    double* res = part + (size_t)g->d.nblk * 5;
+    if (g->es == 8) {
+      double* Kd = static_cast<double*>(K);
+      e = stage_passes<double, double>(g, p, g->t64, static_cast<const double*>(F), Kd, -1.0,
+                                       true, false, ts::RAD_RHS, nullptr, nullptr, nullptr, Kd,
+                                       0.0, st, nullptr);
+      if (e == cudaSuccess)
+        e = ts::launch_number_balance<double>(p, g->t64, g->balw, cons ? 1 : 0, rho1, rho2,
+                                              static_cast<const double*>(F), Kd, part, res, st);
+    } else {
+      float* Kf = static_cast<float*>(K);
+      e = stage_passes<float, float>(g, p, g->t32, static_cast<const float*>(F), Kf, -1.0f, true,
+                                     false, ts::RAD_RHS, nullptr, nullptr, nullptr, Kf, 0.0, st,
+                                     nullptr);
+      if (e == cudaSuccess)
+        e = ts::launch_number_balance<float>(p, g->t64, g->balw, 0, rho1, rho2,
+                                             static_cast<const float*>(F), Kf, part, res, st);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, res, (size_t)g->d.G * 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                          st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (K) cudaFree(K);
+  if (part) cudaFree(part);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(TS_ERR_OOM, "ts_number_balance: device allocation failed");
+  }
+  return e == cudaSuccess ? TS_OK : cuda_fail(e, "ts_number_balance");
 }
 
 ts_status ts_set_wait_limit(ts_grid* g, long long operand_wait_iterations) {

@@ -484,8 +484,9 @@ ts_status ts_batch_create(const ts_grid_desc* descs, int n, int autotune, ts_bat
     if (descs[q].precision != descs[0].precision)
       return ts::fail_status(TS_ERR_UNSUPPORTED, "all problems of a batch share one precision");
   for (int q = 0; q < n; ++q)
-    if (descs[q].radial != TS_RADIAL_CHEBYSHEV)
-      return ts::fail_status(TS_ERR_UNSUPPORTED, "batches run the Chebyshev radial grid");
+    if (descs[q].radial != TS_RADIAL_CHEBYSHEV || descs[q].form != TS_FORM_ADVECTIVE)
+      return ts::fail_status(TS_ERR_UNSUPPORTED,
+                             "batches run the advective form on the Chebyshev radial grid");
   for (int q = 0; q < n; ++q)
     if ((descs[q].scheme == TS_AB2) != (descs[0].scheme == TS_AB2))
       return ts::fail_status(TS_ERR_UNSUPPORTED,

@@ -83,6 +83,8 @@ extern "C" {
 ts_status ts_outgoing_flux(ts_grid* g, const void* F, double* J_R2, void* stream) {
   if (!g) return ts::fail_status(TS_ERR_ARG, "grid is NULL");
   if (!F || !J_R2) return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux: NULL argument");
+  if (g->desc.form != TS_FORM_ADVECTIVE)
+    return ts::fail_status(TS_ERR_UNSUPPORTED, "ts_outgoing_flux: advective form only");
   if (!ts::aligned16(F)) return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux: F is not 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const ts::Dims& d = g->d;
@@ -104,6 +106,8 @@ ts_status ts_outgoing_flux(ts_grid* g, const void* F, double* J_R2, void* stream
 ts_status ts_outgoing_flux_adjoint(ts_grid* g, const double* gJ, void* lambda, void* stream) {
   if (!g) return ts::fail_status(TS_ERR_ARG, "grid is NULL");
   if (!gJ || !lambda) return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux_adjoint: NULL argument");
+  if (g->desc.form != TS_FORM_ADVECTIVE)
+    return ts::fail_status(TS_ERR_UNSUPPORTED, "ts_outgoing_flux_adjoint: advective form only");
   if (!ts::aligned16(lambda))
     return ts::fail_status(TS_ERR_ARG, "ts_outgoing_flux_adjoint: lambda is not 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

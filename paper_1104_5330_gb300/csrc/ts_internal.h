@@ -197,6 +197,20 @@ cudaError_t launch_radial_zoned(const Problem& p, const Tables<C>& t, const C* Z
                                 double h, const T* U, const T* K, C sgn, bool hold, int mode,
                                 T* F, T* Acc, T* Uout, T* out, double dt, cudaStream_t s);
 
+// The conservative form of App. A (defined in ts_cons5d.cu): the angular pass on
+// Fhat = r^2 sin th sin Th F (the grid's Theta tables are those of the odd
+// continuation) and its dynamic shared memory; the number balance of a grid's
+// operator, w = [radial | theta | Theta] weights of the state's number integral,
+// cons: the source term carries the volume element, part: nblk x 5 doubles, out:
+// G x 5 doubles (N, J_R1, J_R2, dN/dt, S).
+size_t angular_cons_smem(const Dims& d);
+cudaError_t launch_angular_cons(const Problem& p, const Tables<double>& t, const double* U,
+                                double* K, double sgn, bool collision, cudaStream_t s);
+template <typename T>
+cudaError_t launch_number_balance(const Problem& p, const Tables<double>& t, const double* w,
+                                  int cons, double rho1, double rho2, const T* F, const T* K,
+                                  double* part, double* out, cudaStream_t s);
+
 // Whether the tensor-core radial pass handles N_r (its tile must fit shared memory).
 inline bool tc_supported(int Nr) { return Nr >= 3 && Nr <= 81; }
 
@@ -313,6 +327,9 @@ struct ts_grid {
   // its nodes, in double (zt64) and, for float grids, in float (zt32)
   void *zt64 = nullptr, *zt32 = nullptr;
   int zA = 0, zB = 0;          // nodes per edge zone, nodes of the central zone
+  // weights of the state's number integral (ts_number_balance): radial [Nr] |
+  // theta [Ntheta] | Theta [NTheta], device doubles
+  double* balw = nullptr;
   double zh = 0.0;             // edge-zone node spacing
   // Group slice the launches cover (ts_step_host's per-group pipeline): groups
   // s0 .. s0+sn-1, every pointer of the problem and the workspace offset to

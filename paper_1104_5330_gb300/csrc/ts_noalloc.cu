@@ -208,8 +208,9 @@ ts_status ts_moments_noalloc(const ts_grid_desc* desc, const void* F, double* F0
   if (d.precision != TS_FP64 && d.precision != TS_FP32 && d.precision != TS_FP32_R64 &&
       d.precision != TS_TF32X3 && d.precision != TS_BF16X3)
     return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: unknown precision");
-  if (d.radial != TS_RADIAL_CHEBYSHEV)
-    return noalloc_fail(TS_ERR_UNSUPPORTED, "ts_moments_noalloc: Chebyshev radial grids only");
+  if (d.radial != TS_RADIAL_CHEBYSHEV || d.form != TS_FORM_ADVECTIVE)
+    return noalloc_fail(TS_ERR_UNSUPPORTED,
+                        "ts_moments_noalloc: the advective form on Chebyshev radial grids only");
   Sizes z{d.groups, d.Nr, d.Ntheta, d.Nphi, d.NTheta, d.NPhi, d.R1, d.R2,
           (long long)d.groups * d.Nr * d.Ntheta * d.Nphi};
   const long long need = z.nblk + 2LL * d.groups * d.Ntheta * d.Nphi;

@@ -28,6 +28,7 @@ TS_FP64, TS_FP32, TS_FP32_R64, TS_TF32X3, TS_BF16X3 = 0, 1, 2, 3, 4
 TS_RK4, TS_RK4_SPLIT_IMPLICIT, TS_AB2 = 0, 1, 2
 TS_BC_TAU_INFLOW, TS_BC_NONE = 0, 1
 TS_RADIAL_CHEBYSHEV, TS_RADIAL_UPWIND_FD, TS_RADIAL_ZONED = 0, 1, 2
+TS_FORM_ADVECTIVE, TS_FORM_CONSERVATIVE = 0, 1
 
 STATUS_NAMES = ["TS_OK", "TS_ERR_ARG", "TS_ERR_UNSUPPORTED", "TS_ERR_OOM", "TS_ERR_CUDA",
                 "TS_ERR_TIMEOUT", "TS_ERR_STATE"]
@@ -47,7 +48,8 @@ class GridDesc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("scheme", ctypes.c_int), ("bc", ctypes.c_int),
                 ("filter_on", ctypes.c_int), ("filter_alpha", ctypes.c_double),
                 ("filter_order", ctypes.c_int), ("radial", ctypes.c_int),
-                ("zone_nodes", ctypes.c_int), ("zone_width", ctypes.c_double)]
+                ("zone_nodes", ctypes.c_int), ("zone_width", ctypes.c_double),
+                ("form", ctypes.c_int)]
 
 
 class Cons2DDesc(ctypes.Structure):
@@ -85,6 +87,7 @@ def _load():
         "ts_outgoing_flux": [P, P, P, P],
         "ts_outgoing_flux_adjoint": [P, P, P, P],
         "ts_moments": [P, P, P, P, P, P, P, P],
+        "ts_number_balance": [P, P, P, P],
         "ts_moments_noalloc": [ctypes.POINTER(GridDesc), P, P, P, P, P, P, P],
         "ts_autotune": [P, P],
         "ts_tile_shape": [P, P, P, P],
@@ -286,6 +289,12 @@ def ts_moments(grid, F, F0=None, F1=None, N=None, J_R1=None, J_R2=None, stream=N
                           _stream(stream)), "ts_moments")
 
 
+def ts_number_balance(grid, F, out, stream=None):
+    """out: a host float64 numpy array of 5 G values (N, J_R1, J_R2, dN/dt, S)."""
+    _check(LIB.ts_number_balance(grid, _ptr(F), out.ctypes.data_as(ctypes.c_void_p),
+                                 _stream(stream)), "ts_number_balance")
+
+
 def ts_moments_noalloc(desc: GridDesc, F, F0=None, F1=None, N=None, J_R1=None, J_R2=None,
                        stream=None):
     """ts_moments without a grid and without device allocation (static scratch)."""
@@ -351,10 +360,10 @@ class Grid:
     def __init__(self, R1=0.2, R2=1.0, Nr=17, Ntheta=8, Nphi=8, NTheta=8, NPhi=8, groups=1,
                  precision=TS_FP64, scheme=TS_RK4, bc=TS_BC_TAU_INFLOW, filter_on=False,
                  filter_alpha=36.0, filter_order=16, device=None, radial=TS_RADIAL_CHEBYSHEV,
-                 zone_nodes=0, zone_width=0.0):
+                 zone_nodes=0, zone_width=0.0, form=TS_FORM_ADVECTIVE):
         self.desc = GridDesc(R1, R2, Nr, Ntheta, Nphi, NTheta, NPhi, groups, precision, scheme,
                              bc, int(filter_on), filter_alpha, filter_order, radial, zone_nodes,
-                             zone_width)
+                             zone_width, form)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         with torch.cuda.device(self.device):
             self.handle = ts_create_grid(self.desc)
@@ -481,6 +490,13 @@ class Grid:
         J2 = torch.empty(G, dtype=torch.float64, device=self.device)
         ts_moments(self.handle, F, F0, F1, N, J1, J2)
         return F0, F1, N, J1, J2
+
+    def number_balance(self, F):
+        """[G][5] float64 numpy: N, J_R1, J_R2, dN/dt (operator without Tau rows)
+        and the absorption/emission integral S per group (ts_number_balance)."""
+        out = np.zeros((self.shape[0], 5), dtype=np.float64)
+        ts_number_balance(self.handle, F, out)
+        return out
 
 
 class Batch:

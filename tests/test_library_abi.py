@@ -40,6 +40,8 @@ def _desc(T, **kw):
     (dict(radial=2, zone_nodes=3, zone_width=0.5), 2),
     (dict(radial=2, zone_nodes=3, zone_width=float("nan")), 2),
     (dict(radial=2, zone_nodes=3, zone_width=0.1, precision=4), 2),
+    (dict(form=2), 2), (dict(form=1, precision=1), 2), (dict(form=1, scheme=1), 2),
+    (dict(form=1, filter_on=1), 2), (dict(form=1, radial=1), 2),
 ])
 def test_create_grid_rejects_bad_descriptors(T, kw, status):
     h = ctypes.c_void_p()
@@ -54,6 +56,7 @@ def test_null_arguments_are_rejected(T):
     assert T.LIB.ts_step(None, None, ctypes.c_double(0.1), 1, None) == T.TS_ERR_ARG
     assert T.LIB.ts_moments(None, None, None, None, None, None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_adjoint_step(None, None, None, None, None, ctypes.c_double(0.1), None) == T.TS_ERR_ARG
+    assert T.LIB.ts_number_balance(None, None, None, None) == T.TS_ERR_ARG
     assert T.LIB.ts_destroy_grid(None) == T.TS_OK
     assert T.LIB.ts_field_elems(None) == 0
 
@@ -98,5 +101,11 @@ def test_batches_refuse_ab2_before_touching_the_device(T):
     descs = (T.GridDesc * 1)(_desc(T, radial=T.TS_RADIAL_UPWIND_FD))
     assert T.LIB.ts_batch_create(descs, 1, 0, ctypes.byref(h)) == T.TS_ERR_UNSUPPORTED
     d = _desc(T, radial=T.TS_RADIAL_UPWIND_FD)
+    assert T.LIB.ts_moments_noalloc(ctypes.byref(d), ctypes.c_void_p(0x10000), None, None, None,
+                                    None, None, None) == T.TS_ERR_UNSUPPORTED
+    # the conservative form: no batches, no allocation-free moments
+    descs = (T.GridDesc * 1)(_desc(T, form=T.TS_FORM_CONSERVATIVE))
+    assert T.LIB.ts_batch_create(descs, 1, 0, ctypes.byref(h)) == T.TS_ERR_UNSUPPORTED
+    d = _desc(T, form=T.TS_FORM_CONSERVATIVE)
     assert T.LIB.ts_moments_noalloc(ctypes.byref(d), ctypes.c_void_p(0x10000), None, None, None,
                                     None, None, None) == T.TS_ERR_UNSUPPORTED
