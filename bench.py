@@ -587,6 +587,74 @@ def run_hybrid(args, stream, zoned=False):
                                    for a, n in enumerate(("angular", "plane", "radial"))}}
 
 
+def run_cons5d(args, dims, stream, adv_ms_per_step):
+    """The conservative form of App. A (Eq. Cohercons) on the default grid: the
+    absorber workload carried as Fhat = r^2 sin(th) sin(Th) F (inflow J g), FP64
+    RK4 at dt = 0.4 h_min; the step rate, each pass's time and the rate against
+    the advective form's. Then the number balance of both forms on the Lambert
+    shell of Sect. 5.3 on the same grid (empty shell 0.2 <= r <= 1, emission
+    F0 cos Th at R1, a spherically symmetric scattering plasma vanishing at R2,
+    optical depths 0.5, 2, 5, 10 over the four groups), 100 RK4 steps each:
+    |dN/dt + J_R2 - J_R1| of the operator relative to the fluxes."""
+    import torch
+    import paper_1104_5330_gb300.ts as ts
+    from paper_1104_5330_gb300 import inputs as I
+    R1, R2, Nr, Nt, Np, NT, NP, G = dims
+    gg = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=ts.TS_FP64,
+                 form=ts.TS_FORM_CONSERVATIVE)
+    r, th, ph, Th, Ph = gg.nodes()
+    J = (r[:, None, None, None, None] ** 2 * np.sin(th)[None, :, None, None, None]
+         * np.sin(Th)[None, None, None, :, None])
+    kap, eta, ks = I.absorber_fields(r, th, ph, groups=G)
+    F0 = np.stack([I.seeded_smooth(r, th, ph, Th, Ph, 1104 + g, R1, R2) for g in range(G)])
+    gR1, gR2 = I.inflow_from(F0, NT)
+    h = NT // 2
+    gg.set_coeffs(kap, eta, ks, gR1 * J[None, 0, :, :, :h], gR2 * J[None, -1, :, :, h:])
+    dt = I.dt_rule(R1, R2, Nr)
+    X = torch.as_tensor(J[None] * F0, dtype=torch.float64, device="cuda").contiguous()
+    gg.step(X, dt, args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    gg.step(X, dt, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    pm, pn = ts.ts_step_profile(gg.handle, X, dt, max(2, min(args.steps, 10)))
+    ts.ts_sync_status(gg.handle)
+    gg.close()
+    # number balance of both forms on the Lambert shell
+    prof = 9.0 / (R2 - R1) * (1.0 - (r - R1) / (R2 - R1)) ** 8
+    taus = np.array([0.5, 2.0, 5.0, 10.0][:G] + [5.0] * max(0, G - 4))
+    ksh = np.ascontiguousarray(np.broadcast_to(
+        (taus[:, None] * prof[None, :])[:, :, None, None], (G, Nr, Nt, Np)))
+    lR1, lR2 = I.lambert_inflow(Th, Nt, Np, NP, groups=G)
+    res = {}
+    for name, form in (("conservative", ts.TS_FORM_CONSERVATIVE),
+                       ("advective", ts.TS_FORM_ADVECTIVE)):
+        gs = ts.Grid(R1, R2, Nr, Nt, Np, NT, NP, groups=G, precision=ts.TS_FP64, form=form)
+        w1, w2 = (J[None, 0, :, :, :h], J[None, -1, :, :, h:]) if name == "conservative" else (1, 1)
+        gs.set_coeffs(None, None, ksh, lR1 * w1, lR2 * w2)
+        Y = gs.apply_inflow(torch.zeros(gs.shape, dtype=torch.float64, device="cuda"))
+        gs.step(Y, dt, 100)
+        N, J1, J2, dN, S = gs.number_balance(Y).T
+        res[name] = float(np.max(np.abs(dN + J2 - J1 - S) / (np.abs(J1) + np.abs(J2))))
+        res[name + "_N"] = [float(v) for v in N]
+        gs.close()
+    return {"value": gg.points * args.steps / (ms * 1e-3), "unit": "point-updates/s",
+            "ms_per_step": ms / args.steps, "steps": args.steps, "dtype": "f64", "dt": dt,
+            "workload": "absorber, Fhat = r^2 sin th sin Th F, " + "x".join(map(str, dims[2:7]))
+                        + f", {G} groups",
+            "rate_vs_advective": adv_ms_per_step / (ms / args.steps),
+            "pass_ms_per_launch": {n: float(pm[a] / pn[a])
+                                   for a, n in enumerate(("angular", "plane", "radial"))},
+            "balance": {"workload": "Lambert shell, optical depths 0.5, 2, 5, 10, 100 RK4 steps",
+                        "residual_rel_max": {"conservative": res["conservative"],
+                                             "advective": res["advective"]},
+                        "N": {"conservative": res["conservative_N"],
+                              "advective": res["advective_N"]}}}
+
+
 def variant_line(ts, dims, wname, vname, vprec, pts, steps, ms, err, nv, pm, pn, peaks, sms,
                  smax):
     """Rate, error and per-pass roofline of one float variant: the dominant
@@ -924,6 +992,7 @@ def run_ours(args, dims, wname):
     if not args.skip_workloads:
         line["conservative_2d"] = run_cons2d(args, stream)
         line["conservative_2d_zoned"] = run_cons2d(args, stream, zoned=True)
+        line["conservative_5d"] = run_cons5d(args, dims, stream, ms / args.steps)
     if not args.skip_aniso:
         line["anisotropic_scattering"] = run_anisotropic(args, dims, stream)
         line["ab2"] = run_ab2(args, dims, stream, ms / args.steps)

@@ -44,16 +44,20 @@ struct ConsTile {
   size_t bytes;  // dynamic shared memory
 };
 
-// Shared layout (doubles): P, Q [NT][NT] | Ms, Md [hP][hP] | per block: the
-// field [S], the pair sums and differences s, d [NT][hP] each, sig, del
-// [NT][hP] each, the Nyquist bins [hP] and the ten moments.
+// Shared layout (doubles): the Theta halves folded over k -> NT-1-k, Pe, Po,
+// Qe, Qo [h][h] (h = NT/2, each with its 1/2) | the Phi pair-half tables times
+// sin(Phi_q)/2, Ms, Md [hP][hP] | q_k / sin Th_k [NT] | per block: the field
+// [S], the pair sums and differences s, d [NT][hP] each, their Theta-even and
+// -odd parts es, os, ed, od [h][hP] each, the Nyquist bins [hP], the ten
+// moments and eight scalars.
+constexpr int kConsScalars = 8;
 size_t cons_table_doubles(const Dims& d) {
   const size_t hP = d.NP / 2;
-  return 2 * (size_t)d.NT * d.NT + 2 * hP * hP;
+  return (size_t)d.NT * d.NT + 2 * hP * hP + d.NT;
 }
 size_t cons_block_doubles(const Dims& d) {
   const size_t S = (size_t)d.NT * d.NP;
-  return 3 * S + d.NP / 2 + 10;
+  return 3 * S + d.NP / 2 + 10 + kConsScalars;
 }
 
 ConsTile cons_tile(const Dims& d) {
@@ -71,62 +75,66 @@ ConsTile cons_tile(const Dims& d) {
   return t;
 }
 
+// One thread per output quadruple (k, NT-1-k) x (c, c + hP), k < NT/2, c < hP:
+//   Theta: P s at rows k, NT-1-k from the Theta-even/odd parts of s (P is
+//   centro-antisymmetric): A1 = sum Pe e, A2 = sum Po o give P s (k) = A1 + A2,
+//   P s (NT-1-k) = A2 - A1; Q d alike; D_Th Fhat (k, c) = P s + Q d,
+//   (k, c + hP) = P s - Q d.
+//   Phi: v = sin Ph Fhat has pair sums sin(Ph_q) d_q and differences sin(Ph_q) s_q
+//   (sin(Ph_{q+hP}) = -sin(Ph_q)), so the tables carry sin(Ph_q)/2 and act on d, s.
 __global__ void __launch_bounds__(kConsThreads)
 k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
                double* __restrict__ K, double sgn, int collision, int nb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
-  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2, H = NT * hP;
-  double* sP = reinterpret_cast<double*>(smem_raw);   // [k'][k]
-  double* sQ = sP + NT * NT;
-  double* sMs = sQ + NT * NT;                         // [q][p]
+  const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2, H = NT * hP, h = NT / 2,
+            Hh = h * hP;
+  double* sPe = reinterpret_cast<double*>(smem_raw);   // [kk][k], k, kk < h
+  double* sPo = sPe + h * h;
+  double* sQe = sPo + h * h;
+  double* sQo = sQe + h * h;
+  double* sMs = sQo + h * h;                           // [q][c] x sin(Ph_q)/2
   double* sMd = sMs + hP * hP;
-  double* su = sMd + hP * hP;                         // [nb][S]
-  double* ss = su + (size_t)nb * S;                   // [nb][NT][hP]
+  double* sq = sMd + hP * hP;                          // q_k / sin Th_k
+  double* su = sq + NT;                                // [nb][S]
+  double* ss = su + (size_t)nb * S;                    // [nb][NT][hP]
   double* sd = ss + (size_t)nb * H;
-  double* sg = sd + (size_t)nb * H;                   // sig [nb][NT][hP]
-  double* sl = sg + (size_t)nb * H;                   // del
-  double* sc = sl + (size_t)nb * H;                   // Nyquist bins [nb][hP]
-  double* sJ = sc + (size_t)nb * hP;                  // moments [10][nb]
+  double* ses = sd + (size_t)nb * H;                   // [nb][h][hP]
+  double* sos = ses + (size_t)nb * Hh;
+  double* sed = sos + (size_t)nb * Hh;
+  double* sod = sed + (size_t)nb * Hh;
+  double* sc = sod + (size_t)nb * Hh;                  // Nyquist bins [nb][hP]
+  double* sJ = sc + (size_t)nb * hP;                   // moments [10][nb]
+  double* sB = sJ + (size_t)10 * nb;                   // scalars [nb][kConsScalars]
   const long long b0 = (long long)blockIdx.x * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int kf = kernel_form(p, collision);
   const bool aniso = kf >= KF_LINEAR, quad = kf >= KF_QUADRATIC;
 
-  for (int x = threadIdx.x; x < NT * NT; x += blockDim.x) {
-    sP[x] = t.PThT[x];
-    sQ[x] = t.QThT[x];
+  for (int x = threadIdx.x; x < h * h; x += blockDim.x) {
+    sPe[x] = t.PeThT[x];
+    sPo[x] = t.PoThT[x];
+    sQe[x] = t.QeThT[x];
+    sQo[x] = t.QoThT[x];
   }
   for (int x = threadIdx.x; x < hP * hP; x += blockDim.x) {
-    sMs[x] = t.MsPhT[x];
-    sMd[x] = t.MdPhT[x];
+    const double w = 0.5 * t.sinP[x / hP];
+    sMs[x] = w * t.MsPhT[x];
+    sMd[x] = w * t.MdPhT[x];
   }
+  for (int x = threadIdx.x; x < NT; x += blockDim.x) sq[x] = t.qdir[x] / t.sinT[x];
   {
     const double2* src = reinterpret_cast<const double2*>(U + b0 * S);
     double2* dst = reinterpret_cast<double2*>(su);
     for (int x = threadIdx.x; x < nbb * S / 2; x += blockDim.x) dst[x] = src[x];
   }
   __syncthreads();
-  // pair sums and differences of Fhat and of sin Ph Fhat
+  // DFS pair sums and differences
   for (int x = threadIdx.x; x < nbb * H; x += blockDim.x) {
     const int bb = x / H, r = x - bb * H, k = r / hP, q = r - k * hP;
     const double a = su[bb * S + k * NP + q], b = su[bb * S + k * NP + q + hP];
     ss[x] = a + b;
     sd[x] = a - b;
-    const double va = t.sinP[q] * a, vb = t.sinP[q + hP] * b;
-    sg[x] = va + vb;
-    sl[x] = va - vb;
-  }
-  __syncthreads();
-  // Nyquist bins of the doubled Theta circle
-  for (int x = threadIdx.x; x < nbb * hP; x += blockDim.x) {
-    const int bb = x / hP, q = x - bb * hP;
-    double c = 0.0;
-    for (int j = 0; j < NT; ++j) {
-      const double v = ss[(size_t)bb * H + j * hP + q];
-      c += (j & 1) ? -v : v;
-    }
-    sc[x] = c / (2.0 * NT);
   }
   if (collision) {
     // moments of G = Fhat / sin Th, one warp per block
@@ -135,10 +143,10 @@ k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
       double mo[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // J, H (3), M (6)
       for (int x = lane; x < S; x += 32) {
         const int k = x / NP, m = x - k * NP;
-        const double qu = t.qdir[k] * su[bb * S + x] / t.sinT[k];
-        mo[0] += qu;
+        const double u = su[bb * S + x];
+        mo[0] = fma(sq[k], u, mo[0]);
         if (aniso) {
-          const double qs = t.sinT[k] * qu, ct = t.cosT[k];
+          const double qu = sq[k] * u, qs = t.qdir[k] * u, ct = t.cosT[k];
           const double cp = t.cosP[m], sp = t.sinP[m];
           mo[1] = fma(ct, qu, mo[1]);
           mo[2] = fma(cp, qs, mo[2]);
@@ -167,69 +175,113 @@ k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
     }
   }
   __syncthreads();
-  // one thread per output pair (k, c), (k, c + hP)
-  for (int x = threadIdx.x; x < nbb * H; x += blockDim.x) {
-    const int bb = x / H, r = x - bb * H, k = r / hP, c = r - k * hP;
+  // Theta-even/odd parts of s and d; Nyquist bins; per-block scalars
+  for (int x = threadIdx.x; x < nbb * Hh; x += blockDim.x) {
+    const int bb = x / Hh, r = x - bb * Hh, kk = r / hP, q = r - kk * hP;
     const double* bs = ss + (size_t)bb * H;
     const double* bd = sd + (size_t)bb * H;
-    double Ps = 0.0, Qd = 0.0;
-    for (int kk = 0; kk < NT; ++kk) {
-      Ps = fma(sP[kk * NT + k], bs[kk * hP + c], Ps);
-      Qd = fma(sQ[kk * NT + k], bd[kk * hP + c], Qd);
+    const double s1 = bs[kk * hP + q], s2 = bs[(NT - 1 - kk) * hP + q];
+    const double d1 = bd[kk * hP + q], d2 = bd[(NT - 1 - kk) * hP + q];
+    ses[x] = s1 + s2;
+    sos[x] = s1 - s2;
+    sed[x] = d1 + d2;
+    sod[x] = d1 - d2;
+  }
+  for (int x = threadIdx.x; x < nbb * hP; x += blockDim.x) {
+    const int bb = x / hP, q = x - bb * hP;
+    double c = 0.0;
+    for (int j = 0; j < NT; ++j) {
+      const double v = ss[(size_t)bb * H + j * hP + q];
+      c += (j & 1) ? -v : v;
     }
-    const double* bg = sg + (size_t)bb * H + k * hP;
-    const double* bl = sl + (size_t)bb * H + k * hP;
-    double Ms = 0.0, Md = 0.0;
-    for (int q = 0; q < hP; ++q) {
-      Ms = fma(sMs[q * hP + c], bg[q], Ms);
-      Md = fma(sMd[q * hP + c], bl[q], Md);
-    }
+    sc[x] = c / (2.0 * NT);
+  }
+  for (int bb = threadIdx.x; bb < nbb; bb += blockDim.x) {
     const long long blk = b0 + bb;
-    int g, i, j, l;
-    {
-      l = (int)(blk % d.Np);
-      long long qq = blk / d.Np;
-      j = (int)(qq % d.Nt);
-      qq /= d.Nt;
-      i = (int)(qq % d.Nr);
-      g = (int)(qq / d.Nr);
-      (void)g;
-      (void)l;
-    }
-    const double ir = t.inv_r[i], sT = t.sinT[k], cT = t.cosT[k];
-    const double ny = (k & 1) ? -sc[bb * hP + c] : sc[bb * hP + c];
-    const double aP = -sT * t.cot_th[j] * ir;
-    double kap = 0.0, eta = 0.0, ks = 0.0, kb = 0.0, kc = 0.0, jac = 0.0;
+    const int j = (int)((blk / d.Np) % d.Nt);
+    const int i = (int)((blk / ((long long)d.Np * d.Nt)) % d.Nr);
+    const double ir = t.inv_r[i];
+    double* B = sB + bb * kConsScalars;
+    B[0] = -sgn * ir;                 // factor of the streaming terms
+    B[1] = t.cot_th[j];
     if (collision) {
-      kap = p.kap[blk];
-      eta = p.eta[blk];
-      ks = p.kaps[blk];
-      if (aniso && p.scb) kb = ks * p.scb[blk];
-      if (quad) kc = ks * p.scc[blk];
-      jac = sT * t.sin_th[j] / (ir * ir);
+      const double ks = p.kaps[blk];
+      B[2] = p.kap[blk] + ks;                               // loss rate
+      B[3] = p.eta[blk] * t.sin_th[j] / (ir * ir) + ks * sJ[bb];   // eta r^2 sin th + ks J
+      B[4] = (aniso && p.scb) ? ks * p.scb[blk] : 0.0;
+      B[5] = quad ? ks * p.scc[blk] : 0.0;
+    } else {
+      B[2] = B[3] = B[4] = B[5] = 0.0;
     }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < nbb * Hh; x += blockDim.x) {
+    const int bb = x / Hh, r = x - bb * Hh, k = r / hP, c = r - k * hP;
+    const int k2 = NT - 1 - k;
+    const double* es = ses + (size_t)bb * Hh;
+    const double* os = sos + (size_t)bb * Hh;
+    const double* ed = sed + (size_t)bb * Hh;
+    const double* od = sod + (size_t)bb * Hh;
+    double A1 = 0.0, A2 = 0.0, B1 = 0.0, B2 = 0.0;
+    for (int kk = 0; kk < h; ++kk) {
+      const int w = kk * hP + c, e = kk * h + k;
+      A1 = fma(sPe[e], es[w], A1);
+      A2 = fma(sPo[e], os[w], A2);
+      B1 = fma(sQe[e], ed[w], B1);
+      B2 = fma(sQo[e], od[w], B2);
+    }
+    const double* s1 = ss + (size_t)bb * H + k * hP;
+    const double* d1 = sd + (size_t)bb * H + k * hP;
+    const double* s2 = ss + (size_t)bb * H + k2 * hP;
+    const double* d2 = sd + (size_t)bb * H + k2 * hP;
+    double M1 = 0.0, N1 = 0.0, M2 = 0.0, N2 = 0.0;
+    for (int q = 0; q < hP; ++q) {
+      const double ms = sMs[q * hP + c], md = sMd[q * hP + c];
+      M1 = fma(ms, d1[q], M1);
+      N1 = fma(md, s1[q], N1);
+      M2 = fma(ms, d2[q], M2);
+      N2 = fma(md, s2[q], N2);
+    }
+    const double* B = sB + bb * kConsScalars;
+    const double A = B[0], cot = B[1], kl = B[2], eg0 = B[3], kb = B[4], kc = B[5];
+    const double ny = sc[bb * hP + c];
+    const long long blk = b0 + bb;
+    double* Kb = K + blk * S;
+    const double* ub = su + (size_t)bb * S;
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int m = c + half * hP;
-      const double dT = half ? Ps - Qd : Ps + Qd;
-      const double dP = 0.5 * (half ? Ms - Md : Ms + Md);
-      const double u = su[bb * S + k * NP + m];
-      double v = sgn * (-ir * (sT * dT + cT * (u - ny)) + aP * dP);
-      if (collision) {
-        const double* M = sJ + bb;
-        double gain = ks * M[0];
-        const double cp = t.cosP[m], sp = t.sinP[m];
-        if (aniso && p.scb) gain += kb * (cT * M[nb] + sT * (cp * M[2 * nb] + sp * M[3 * nb]));
-        if (quad) {
-          const double j3 = M[0] / 3.0;
-          gain += kc * (cT * cT * (M[4 * nb] - j3) +
-                        sT * sT * (cp * cp * (M[5 * nb] - j3) + sp * sp * (M[6 * nb] - j3) +
-                                   2.0 * cp * sp * M[7 * nb]) +
-                        2.0 * cT * sT * (cp * M[8 * nb] + sp * M[9 * nb]));
+    for (int row = 0; row < 2; ++row) {
+      const int kr = row ? k2 : k;
+      const double Ps = row ? A2 - A1 : A1 + A2, Qd = row ? B2 - B1 : B1 + B2;
+      const double Ms = row ? M2 : M1, Md = row ? N2 : N1;
+      const double sT = t.sinT[kr], cT = t.cosT[kr];
+      const double nyk = (kr & 1) ? -ny : ny;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int m = c + half * hP;
+        const double dT = half ? Ps - Qd : Ps + Qd;
+        const double dP = half ? Ms - Md : Ms + Md;
+        const double u = ub[kr * NP + m];
+        double tt = fma(cot, dP, dT);
+        tt = fma(cT, u - nyk, sT * tt);
+        double v = A * tt;
+        if (collision) {
+          double eg = eg0;
+          if (aniso) {
+            const double* M = sJ + bb;
+            const double cp = t.cosP[m], sp = t.sinP[m];
+            eg += kb * (cT * M[nb] + sT * (cp * M[2 * nb] + sp * M[3 * nb]));
+            if (quad) {
+              const double j3 = M[0] * (1.0 / 3.0);
+              eg += kc * (cT * cT * (M[4 * nb] - j3) +
+                          sT * sT * (cp * cp * (M[5 * nb] - j3) + sp * sp * (M[6 * nb] - j3) +
+                                     2.0 * cp * sp * M[7 * nb]) +
+                          2.0 * cT * sT * (cp * M[8 * nb] + sp * M[9 * nb]));
+            }
+          }
+          v = fma(sT, eg, fma(-kl, u, v));
         }
-        v += jac * eta - (kap + ks) * u + sT * gain;
+        Kb[kr * NP + m] = v;
       }
-      K[blk * S + k * NP + m] = v;
     }
   }
 }
