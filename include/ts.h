@@ -153,9 +153,10 @@ typedef enum {
                                term is r^2 sin th sin Th CT(F) at F = Fhat / (r^2 sin th
                                sin Th). Every flux but the theta one then integrates
                                exactly to its boundary value (ts_number_balance), the
-                               theta one to spectral accuracy. TS_FP64, TS_RADIAL_CHEBYSHEV,
-                               TS_RK4 or TS_AB2, no filter; no adjoint, moments, flux
-                               weights, batches (TS_ERR_UNSUPPORTED). */
+                               theta one to spectral accuracy. Every precision (the float
+                               ones compute the angular pass in float);
+                               TS_RADIAL_CHEBYSHEV, TS_RK4 or TS_AB2, no filter; no adjoint,
+                               moments, flux weights, batches (TS_ERR_UNSUPPORTED). */
 } ts_form;
 
 typedef struct {

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "ts_internal.h"
@@ -685,9 +686,9 @@ cudaError_t stage_passes(ts_grid* g, const ts::Problem& p, const Tables<C>& t, c
       return e;
     }
   }
-  if constexpr (sizeof(T) == 8 && sizeof(C) == 8) {
+  if constexpr (std::is_same<T, C>::value) {
     if (g->desc.form == TS_FORM_CONSERVATIVE) {
-      TS_TIMED(prof, 0, (ts::launch_angular_cons(p, g->t64, in, K, sgn, collision, st)));
+      TS_TIMED(prof, 0, (ts::launch_angular_cons<T>(p, t, in, K, sgn, collision, st)));
     } else {
       TS_TIMED(prof, 0, (Launch<T, C>::angular(p, t, in, K, sgn, collision, st)));
     }
@@ -1031,11 +1032,10 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
   if (g.form != TS_FORM_ADVECTIVE && g.form != TS_FORM_CONSERVATIVE)
     return fail(TS_ERR_UNSUPPORTED, "unknown form");
   if (g.form == TS_FORM_CONSERVATIVE &&
-      (g.precision != TS_FP64 || g.radial != TS_RADIAL_CHEBYSHEV ||
-       g.scheme == TS_RK4_SPLIT_IMPLICIT || g.filter_on))
+      (g.radial != TS_RADIAL_CHEBYSHEV || g.scheme == TS_RK4_SPLIT_IMPLICIT || g.filter_on))
     return fail(TS_ERR_UNSUPPORTED,
-                "the conservative form runs in TS_FP64 on the Chebyshev radial grid with "
-                "TS_RK4 or TS_AB2, unfiltered");
+                "the conservative form runs on the Chebyshev radial grid with TS_RK4 or "
+                "TS_AB2, unfiltered");
   const size_t es = g.precision == TS_FP64 ? 8 : 4;
   if (!fits(g, es)) return fail(TS_ERR_UNSUPPORTED, "grid too large for one shared-memory tile");
 
@@ -1061,7 +1061,8 @@ ts_status ts_create_grid(const ts_grid_desc* desc, ts_grid** out) {
     // passes', so the three-pass form stays the default)
     const char* fz = std::getenv("TS_FUSED");
     const bool tc = g.precision == TS_TF32X3 || g.precision == TS_BF16X3;
-    const bool want = es == 4 && !tc && (G->tp.rb & 5) == 5 && fz && fz[0] == '1';
+    const bool want = es == 4 && !tc && (G->tp.rb & 5) == 5 && fz && fz[0] == '1' &&
+                      g.form == TS_FORM_ADVECTIVE;   // the fused pass is the advective one
     if (!want || !ts::fused_plan(d, g.precision == TS_FP32_R64 ? 2 : 0, &G->tp.fnb, &G->tp.fnbuf))
       G->tp.fnb = G->tp.fnbuf = 0;
   }
@@ -1542,7 +1543,7 @@ ts_status ts_number_balance(ts_grid* g, const void* F, double* out, void* stream
                                      false, ts::RAD_RHS, nullptr, nullptr, nullptr, Kf, 0.0, st,
                                      nullptr);
       if (e == cudaSuccess)
-        e = ts::launch_number_balance<float>(p, g->t64, g->balw, 0, rho1, rho2,
+        e = ts::launch_number_balance<float>(p, g->t64, g->balw, cons ? 1 : 0, rho1, rho2,
                                              static_cast<const float*>(F), Kf, part, res, st);
     }
     if (e == cudaSuccess)

@@ -44,24 +44,24 @@ struct ConsTile {
   size_t bytes;  // dynamic shared memory
 };
 
-// Shared layout (doubles): the Theta halves folded over k -> NT-1-k, Pe, Po,
-// Qe, Qo [h][h] (h = NT/2, each with its 1/2) | the Phi pair-half tables times
-// sin(Phi_q)/2, Ms, Md [hP][hP] | q_k / sin Th_k [NT] | per block: the field
-// [S], the pair sums and differences s, d [NT][hP] each, their Theta-even and
-// -odd parts es, os, ed, od [h][hP] each, the Nyquist bins [hP], the ten
-// moments and eight scalars.
+// Shared layout (elements of T): the Theta halves folded over k -> NT-1-k, Pe,
+// Po, Qe, Qo [h][h] (h = NT/2, each with its 1/2) | the Phi pair-half tables
+// times sin(Phi_q)/2, Ms, Md [hP][hP] | q_k / sin Th_k [NT], padded to 16 bytes |
+// per block: the field [S], the pair sums and differences s, d [NT][hP] each,
+// their Theta-even and -odd parts es, os, ed, od [h][hP] each, the Nyquist bins
+// [hP], the ten moments and eight scalars.
 constexpr int kConsScalars = 8;
-size_t cons_table_doubles(const Dims& d) {
-  const size_t hP = d.NP / 2;
-  return (size_t)d.NT * d.NT + 2 * hP * hP + d.NT;
+size_t cons_table_elems(const Dims& d, size_t es) {
+  const size_t hP = d.NP / 2, v = 16 / es;
+  return ((size_t)d.NT * d.NT + 2 * hP * hP + d.NT + v - 1) / v * v;
 }
-size_t cons_block_doubles(const Dims& d) {
+size_t cons_block_elems(const Dims& d) {
   const size_t S = (size_t)d.NT * d.NP;
   return 3 * S + d.NP / 2 + 10 + kConsScalars;
 }
 
-ConsTile cons_tile(const Dims& d) {
-  const size_t tab = cons_table_doubles(d) * 8, blk = cons_block_doubles(d) * 8;
+ConsTile cons_tile(const Dims& d, size_t es) {
+  const size_t tab = cons_table_elems(d, es) * es, blk = cons_block_elems(d) * es;
   // two CTAs per SM when a few blocks fit in half the shared memory, else one
   const size_t half = 110 * 1024, full = 220 * 1024;
   const size_t budget = tab + 2 * blk <= half ? half : full;
@@ -82,30 +82,35 @@ ConsTile cons_tile(const Dims& d) {
 //   (k, c + hP) = P s - Q d.
 //   Phi: v = sin Ph Fhat has pair sums sin(Ph_q) d_q and differences sin(Ph_q) s_q
 //   (sin(Ph_{q+hP}) = -sin(Ph_q)), so the tables carry sin(Ph_q)/2 and act on d, s.
+// T: the element type of the field, of the tables and of the arithmetic (double
+// for TS_FP64, float for the float precisions).
+template <typename T>
 __global__ void __launch_bounds__(kConsThreads)
-k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
-               double* __restrict__ K, double sgn, int collision, int nb) {
+k_angular_cons(Problem p, Tables<T> t, const T* __restrict__ U, T* __restrict__ K, T sgn,
+               int collision, int nb) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Dims d = p.d;
   const int NT = d.NT, NP = d.NP, S = NT * NP, hP = NP / 2, H = NT * hP, h = NT / 2,
             Hh = h * hP;
-  double* sPe = reinterpret_cast<double*>(smem_raw);   // [kk][k], k, kk < h
-  double* sPo = sPe + h * h;
-  double* sQe = sPo + h * h;
-  double* sQo = sQe + h * h;
-  double* sMs = sQo + h * h;                           // [q][c] x sin(Ph_q)/2
-  double* sMd = sMs + hP * hP;
-  double* sq = sMd + hP * hP;                          // q_k / sin Th_k
-  double* su = sq + NT;                                // [nb][S]
-  double* ss = su + (size_t)nb * S;                    // [nb][NT][hP]
-  double* sd = ss + (size_t)nb * H;
-  double* ses = sd + (size_t)nb * H;                   // [nb][h][hP]
-  double* sos = ses + (size_t)nb * Hh;
-  double* sed = sos + (size_t)nb * Hh;
-  double* sod = sed + (size_t)nb * Hh;
-  double* sc = sod + (size_t)nb * Hh;                  // Nyquist bins [nb][hP]
-  double* sJ = sc + (size_t)nb * hP;                   // moments [10][nb]
-  double* sB = sJ + (size_t)10 * nb;                   // scalars [nb][kConsScalars]
+  constexpr int kVec = 16 / sizeof(T);
+  const int tabn = (NT * NT + 2 * hP * hP + NT + kVec - 1) / kVec * kVec;
+  T* sPe = reinterpret_cast<T*>(smem_raw);   // [kk][k], k, kk < h
+  T* sPo = sPe + h * h;
+  T* sQe = sPo + h * h;
+  T* sQo = sQe + h * h;
+  T* sMs = sQo + h * h;                      // [q][c] x sin(Ph_q)/2
+  T* sMd = sMs + hP * hP;
+  T* sq = sMd + hP * hP;                     // q_k / sin Th_k
+  T* su = reinterpret_cast<T*>(smem_raw) + tabn;   // [nb][S], 16-byte aligned
+  T* ss = su + (size_t)nb * S;               // [nb][NT][hP]
+  T* sd = ss + (size_t)nb * H;
+  T* ses = sd + (size_t)nb * H;              // [nb][h][hP]
+  T* sos = ses + (size_t)nb * Hh;
+  T* sed = sos + (size_t)nb * Hh;
+  T* sod = sed + (size_t)nb * Hh;
+  T* sc = sod + (size_t)nb * Hh;             // Nyquist bins [nb][hP]
+  T* sJ = sc + (size_t)nb * hP;              // moments [10][nb]
+  T* sB = sJ + (size_t)10 * nb;              // scalars [nb][kConsScalars]
   const long long b0 = (long long)blockIdx.x * nb;
   const int nbb = (int)min((long long)nb, d.nblk - b0);
   const int kf = kernel_form(p, collision);
@@ -118,21 +123,23 @@ k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
     sQo[x] = t.QoThT[x];
   }
   for (int x = threadIdx.x; x < hP * hP; x += blockDim.x) {
-    const double w = 0.5 * t.sinP[x / hP];
+    const T w = (T)0.5 * t.sinP[x / hP];
     sMs[x] = w * t.MsPhT[x];
     sMd[x] = w * t.MdPhT[x];
   }
   for (int x = threadIdx.x; x < NT; x += blockDim.x) sq[x] = t.qdir[x] / t.sinT[x];
   {
-    const double2* src = reinterpret_cast<const double2*>(U + b0 * S);
-    double2* dst = reinterpret_cast<double2*>(su);
-    for (int x = threadIdx.x; x < nbb * S / 2; x += blockDim.x) dst[x] = src[x];
+    // S is a multiple of 4 (even NT, NP): the blocks are whole 16-byte vectors
+    const uint4* src = reinterpret_cast<const uint4*>(U + b0 * S);
+    uint4* dst = reinterpret_cast<uint4*>(su);
+    const int nv = (int)((size_t)nbb * S * sizeof(T) / 16);
+    for (int x = threadIdx.x; x < nv; x += blockDim.x) dst[x] = src[x];
   }
   __syncthreads();
   // DFS pair sums and differences
   for (int x = threadIdx.x; x < nbb * H; x += blockDim.x) {
     const int bb = x / H, r = x - bb * H, k = r / hP, q = r - k * hP;
-    const double a = su[bb * S + k * NP + q], b = su[bb * S + k * NP + q + hP];
+    const T a = su[bb * S + k * NP + q], b = su[bb * S + k * NP + q + hP];
     ss[x] = a + b;
     sd[x] = a - b;
   }
@@ -140,19 +147,19 @@ k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
     // moments of G = Fhat / sin Th, one warp per block
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int bb = warp; bb < nbb; bb += blockDim.x >> 5) {
-      double mo[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // J, H (3), M (6)
+      T mo[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};   // J, H (3), M (6)
       for (int x = lane; x < S; x += 32) {
         const int k = x / NP, m = x - k * NP;
-        const double u = su[bb * S + x];
+        const T u = su[bb * S + x];
         mo[0] = fma(sq[k], u, mo[0]);
         if (aniso) {
-          const double qu = sq[k] * u, qs = t.qdir[k] * u, ct = t.cosT[k];
-          const double cp = t.cosP[m], sp = t.sinP[m];
+          const T qu = sq[k] * u, qs = t.qdir[k] * u, ct = t.cosT[k];
+          const T cp = t.cosP[m], sp = t.sinP[m];
           mo[1] = fma(ct, qu, mo[1]);
           mo[2] = fma(cp, qs, mo[2]);
           mo[3] = fma(sp, qs, mo[3]);
           if (quad) {
-            const double qss = t.sinT[k] * qs;
+            const T qss = t.sinT[k] * qs;
             mo[4] = fma(ct * ct, qu, mo[4]);
             mo[5] = fma(cp * cp, qss, mo[5]);
             mo[6] = fma(sp * sp, qss, mo[6]);
@@ -178,10 +185,10 @@ k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
   // Theta-even/odd parts of s and d; Nyquist bins; per-block scalars
   for (int x = threadIdx.x; x < nbb * Hh; x += blockDim.x) {
     const int bb = x / Hh, r = x - bb * Hh, kk = r / hP, q = r - kk * hP;
-    const double* bs = ss + (size_t)bb * H;
-    const double* bd = sd + (size_t)bb * H;
-    const double s1 = bs[kk * hP + q], s2 = bs[(NT - 1 - kk) * hP + q];
-    const double d1 = bd[kk * hP + q], d2 = bd[(NT - 1 - kk) * hP + q];
+    const T* bs = ss + (size_t)bb * H;
+    const T* bd = sd + (size_t)bb * H;
+    const T s1 = bs[kk * hP + q], s2 = bs[(NT - 1 - kk) * hP + q];
+    const T d1 = bd[kk * hP + q], d2 = bd[(NT - 1 - kk) * hP + q];
     ses[x] = s1 + s2;
     sos[x] = s1 - s2;
     sed[x] = d1 + d2;
@@ -189,40 +196,40 @@ k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
   }
   for (int x = threadIdx.x; x < nbb * hP; x += blockDim.x) {
     const int bb = x / hP, q = x - bb * hP;
-    double c = 0.0;
+    T c = 0;
     for (int j = 0; j < NT; ++j) {
-      const double v = ss[(size_t)bb * H + j * hP + q];
+      const T v = ss[(size_t)bb * H + j * hP + q];
       c += (j & 1) ? -v : v;
     }
-    sc[x] = c / (2.0 * NT);
+    sc[x] = c / (T)(2 * NT);
   }
   for (int bb = threadIdx.x; bb < nbb; bb += blockDim.x) {
     const long long blk = b0 + bb;
     const int j = (int)((blk / d.Np) % d.Nt);
     const int i = (int)((blk / ((long long)d.Np * d.Nt)) % d.Nr);
-    const double ir = t.inv_r[i];
-    double* B = sB + bb * kConsScalars;
+    const T ir = t.inv_r[i];
+    T* B = sB + bb * kConsScalars;
     B[0] = -sgn * ir;                 // factor of the streaming terms
     B[1] = t.cot_th[j];
     if (collision) {
-      const double ks = p.kaps[blk];
-      B[2] = p.kap[blk] + ks;                               // loss rate
-      B[3] = p.eta[blk] * t.sin_th[j] / (ir * ir) + ks * sJ[bb];   // eta r^2 sin th + ks J
-      B[4] = (aniso && p.scb) ? ks * p.scb[blk] : 0.0;
-      B[5] = quad ? ks * p.scc[blk] : 0.0;
+      const T ks = (T)p.kaps[blk];
+      B[2] = (T)p.kap[blk] + ks;                                    // loss rate
+      B[3] = (T)p.eta[blk] * t.sin_th[j] / (ir * ir) + ks * sJ[bb];  // eta r^2 sin th + ks J
+      B[4] = (aniso && p.scb) ? ks * (T)p.scb[blk] : (T)0;
+      B[5] = quad ? ks * (T)p.scc[blk] : (T)0;
     } else {
-      B[2] = B[3] = B[4] = B[5] = 0.0;
+      B[2] = B[3] = B[4] = B[5] = 0;
     }
   }
   __syncthreads();
   for (int x = threadIdx.x; x < nbb * Hh; x += blockDim.x) {
     const int bb = x / Hh, r = x - bb * Hh, k = r / hP, c = r - k * hP;
     const int k2 = NT - 1 - k;
-    const double* es = ses + (size_t)bb * Hh;
-    const double* os = sos + (size_t)bb * Hh;
-    const double* ed = sed + (size_t)bb * Hh;
-    const double* od = sod + (size_t)bb * Hh;
-    double A1 = 0.0, A2 = 0.0, B1 = 0.0, B2 = 0.0;
+    const T* es = ses + (size_t)bb * Hh;
+    const T* os = sos + (size_t)bb * Hh;
+    const T* ed = sed + (size_t)bb * Hh;
+    const T* od = sod + (size_t)bb * Hh;
+    T A1 = 0, A2 = 0, B1 = 0, B2 = 0;
     for (int kk = 0; kk < h; ++kk) {
       const int w = kk * hP + c, e = kk * h + k;
       A1 = fma(sPe[e], es[w], A1);
@@ -230,52 +237,52 @@ k_angular_cons(Problem p, Tables<double> t, const double* __restrict__ U,
       B1 = fma(sQe[e], ed[w], B1);
       B2 = fma(sQo[e], od[w], B2);
     }
-    const double* s1 = ss + (size_t)bb * H + k * hP;
-    const double* d1 = sd + (size_t)bb * H + k * hP;
-    const double* s2 = ss + (size_t)bb * H + k2 * hP;
-    const double* d2 = sd + (size_t)bb * H + k2 * hP;
-    double M1 = 0.0, N1 = 0.0, M2 = 0.0, N2 = 0.0;
+    const T* s1 = ss + (size_t)bb * H + k * hP;
+    const T* d1 = sd + (size_t)bb * H + k * hP;
+    const T* s2 = ss + (size_t)bb * H + k2 * hP;
+    const T* d2 = sd + (size_t)bb * H + k2 * hP;
+    T M1 = 0, N1 = 0, M2 = 0, N2 = 0;
     for (int q = 0; q < hP; ++q) {
-      const double ms = sMs[q * hP + c], md = sMd[q * hP + c];
+      const T ms = sMs[q * hP + c], md = sMd[q * hP + c];
       M1 = fma(ms, d1[q], M1);
       N1 = fma(md, s1[q], N1);
       M2 = fma(ms, d2[q], M2);
       N2 = fma(md, s2[q], N2);
     }
-    const double* B = sB + bb * kConsScalars;
-    const double A = B[0], cot = B[1], kl = B[2], eg0 = B[3], kb = B[4], kc = B[5];
-    const double ny = sc[bb * hP + c];
+    const T* B = sB + bb * kConsScalars;
+    const T A = B[0], cot = B[1], kl = B[2], eg0 = B[3], kb = B[4], kc = B[5];
+    const T ny = sc[bb * hP + c];
     const long long blk = b0 + bb;
-    double* Kb = K + blk * S;
-    const double* ub = su + (size_t)bb * S;
+    T* Kb = K + blk * S;
+    const T* ub = su + (size_t)bb * S;
 #pragma unroll
     for (int row = 0; row < 2; ++row) {
       const int kr = row ? k2 : k;
-      const double Ps = row ? A2 - A1 : A1 + A2, Qd = row ? B2 - B1 : B1 + B2;
-      const double Ms = row ? M2 : M1, Md = row ? N2 : N1;
-      const double sT = t.sinT[kr], cT = t.cosT[kr];
-      const double nyk = (kr & 1) ? -ny : ny;
+      const T Ps = row ? A2 - A1 : A1 + A2, Qd = row ? B2 - B1 : B1 + B2;
+      const T Ms = row ? M2 : M1, Md = row ? N2 : N1;
+      const T sT = t.sinT[kr], cT = t.cosT[kr];
+      const T nyk = (kr & 1) ? -ny : ny;
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int m = c + half * hP;
-        const double dT = half ? Ps - Qd : Ps + Qd;
-        const double dP = half ? Ms - Md : Ms + Md;
-        const double u = ub[kr * NP + m];
-        double tt = fma(cot, dP, dT);
+        const T dT = half ? Ps - Qd : Ps + Qd;
+        const T dP = half ? Ms - Md : Ms + Md;
+        const T u = ub[kr * NP + m];
+        T tt = fma(cot, dP, dT);
         tt = fma(cT, u - nyk, sT * tt);
-        double v = A * tt;
+        T v = A * tt;
         if (collision) {
-          double eg = eg0;
+          T eg = eg0;
           if (aniso) {
-            const double* M = sJ + bb;
-            const double cp = t.cosP[m], sp = t.sinP[m];
+            const T* M = sJ + bb;
+            const T cp = t.cosP[m], sp = t.sinP[m];
             eg += kb * (cT * M[nb] + sT * (cp * M[2 * nb] + sp * M[3 * nb]));
             if (quad) {
-              const double j3 = M[0] * (1.0 / 3.0);
+              const T j3 = M[0] * (T)(1.0 / 3.0);
               eg += kc * (cT * cT * (M[4 * nb] - j3) +
                           sT * sT * (cp * cp * (M[5 * nb] - j3) + sp * sp * (M[6 * nb] - j3) +
-                                     2.0 * cp * sp * M[7 * nb]) +
-                          2.0 * cT * sT * (cp * M[8 * nb] + sp * M[9 * nb]));
+                                     (T)2 * cp * sp * M[7 * nb]) +
+                          (T)2 * cT * sT * (cp * M[8 * nb] + sp * M[9 * nb]));
             }
           }
           v = fma(sT, eg, fma(-kl, u, v));
@@ -354,19 +361,24 @@ k_balance_groups(const double* __restrict__ part, long long per, double* __restr
 
 }  // namespace
 
-size_t angular_cons_smem(const Dims& d) { return cons_tile(d).bytes; }
-
-cudaError_t launch_angular_cons(const Problem& p, const Tables<double>& t, const double* U,
-                                double* K, double sgn, bool collision, cudaStream_t s) {
-  const ConsTile c = cons_tile(p.d);
-  cudaError_t e = cudaFuncSetAttribute(k_angular_cons, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)c.bytes);
+template <typename T>
+cudaError_t launch_angular_cons(const Problem& p, const Tables<T>& t, const T* U, T* K, T sgn,
+                                bool collision, cudaStream_t s) {
+  const ConsTile c = cons_tile(p.d, sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute(k_angular_cons<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.bytes);
   if (e != cudaSuccess) return e;
   const long long nct = (p.d.nblk + c.nb - 1) / c.nb;
-  k_angular_cons<<<(unsigned)nct, kConsThreads, c.bytes, s>>>(p, t, U, K, sgn, collision ? 1 : 0,
-                                                              c.nb);
+  k_angular_cons<T><<<(unsigned)nct, kConsThreads, c.bytes, s>>>(p, t, U, K, sgn,
+                                                                 collision ? 1 : 0, c.nb);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_angular_cons<double>(const Problem&, const Tables<double>&,
+                                                 const double*, double*, double, bool,
+                                                 cudaStream_t);
+template cudaError_t launch_angular_cons<float>(const Problem&, const Tables<float>&,
+                                                const float*, float*, float, bool, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_number_balance(const Problem& p, const Tables<double>& t, const double* w,

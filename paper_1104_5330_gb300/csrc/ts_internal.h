@@ -199,13 +199,13 @@ cudaError_t launch_radial_zoned(const Problem& p, const Tables<C>& t, const C* Z
 
 // The conservative form of App. A (defined in ts_cons5d.cu): the angular pass on
 // Fhat = r^2 sin th sin Th F (the grid's Theta tables are those of the odd
-// continuation) and its dynamic shared memory; the number balance of a grid's
+// continuation), in the grid's element type; the number balance of a grid's
 // operator, w = [radial | theta | Theta] weights of the state's number integral,
 // cons: the source term carries the volume element, part: nblk x 5 doubles, out:
 // G x 5 doubles (N, J_R1, J_R2, dN/dt, S).
-size_t angular_cons_smem(const Dims& d);
-cudaError_t launch_angular_cons(const Problem& p, const Tables<double>& t, const double* U,
-                                double* K, double sgn, bool collision, cudaStream_t s);
+template <typename T>
+cudaError_t launch_angular_cons(const Problem& p, const Tables<T>& t, const T* U, T* K, T sgn,
+                                bool collision, cudaStream_t s);
 template <typename T>
 cudaError_t launch_number_balance(const Problem& p, const Tables<double>& t, const double* w,
                                   int cons, double rho1, double rho2, const T* F, const T* K,

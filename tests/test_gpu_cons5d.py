@@ -143,6 +143,35 @@ def test_conservative_balance_is_exact_and_the_advective_one_is_not():
     assert np.abs(Np_ - N).max() < 1e-12 * scale     # the same number, both forms
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp32_r64", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("dims", [RAGGED, EVEN])
+def test_float_precisions(prec, dims):
+    """The float forms (angular pass in float, plane and radial passes of the
+    precision: FP64 end rows, tcgen05 radial) against the FP64 oracle: stage
+    derivative, 20 RK4 steps, AB2 steps and the number balance, <= 1e-5."""
+    ts = T()
+    P = {"fp32": ts.TS_FP32, "fp32_r64": ts.TS_FP32_R64, "tf32x3": ts.TS_TF32X3,
+         "bf16x3": ts.TS_BF16X3}[prec]
+    og = OGrid(*dims, groups=2)
+    kap, eta, ks, X0, g1, g2 = _workload(og)
+    for scheme, name in ((ts.TS_RK4, "rk4"), (ts.TS_AB2, "ab2")):
+        gg = ts.Grid(*dims, groups=2, precision=P, scheme=scheme, form=ts.TS_FORM_CONSERVATIVE)
+        gg.set_coeffs(kap, eta, ks, g1, g2)
+        b, c = _kernel(og, gg, "quadratic")
+        op = C.ConservativeProblem(og, kap, eta, ks, g1, g2, scheme=name, scatter_b=b,
+                                   scatter_c=c)
+        if name == "rk4":
+            assert rel_l2(host(gg.rhs(cuda(X0, torch.float32))), op.rhs(X0)) < 1e-5
+            ref = np.stack(op.balance(X0), axis=1)
+            got = gg.number_balance(cuda(X0, torch.float32))
+            assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+        dt = 0.4 * np.diff(og.r).min() * (0.5 if name == "ab2" else 1.0)
+        Xg = cuda(X0, torch.float32)
+        gg.step(Xg, dt, 20)
+        assert rel_l2(host(Xg), op.run(X0, dt, 20)) < 1e-5, name
+        gg.close()
+
+
 def test_full_size_grid():
     """33 x 16^4, 4 groups (the headline grid): stage derivative and two RK4 steps."""
     og, gg = _pair((0.2, 1.0, 33, 16, 16, 16, 16), G=4)
@@ -199,7 +228,7 @@ def test_unsupported_calls_on_the_conservative_form():
         gg.adjoint_step(Xg, torch.zeros_like(Xg), gk, torch.zeros_like(gk), 1e-3)
     with pytest.raises(ts.TSError):
         gg.outgoing_flux(Xg)
-    for kw in (dict(precision=ts.TS_FP32), dict(scheme=ts.TS_RK4_SPLIT_IMPLICIT),
-               dict(filter_on=True), dict(radial=ts.TS_RADIAL_UPWIND_FD)):
+    for kw in (dict(scheme=ts.TS_RK4_SPLIT_IMPLICIT), dict(filter_on=True),
+               dict(radial=ts.TS_RADIAL_UPWIND_FD)):
         with pytest.raises(ts.TSError):
             ts.Grid(*RAGGED, form=ts.TS_FORM_CONSERVATIVE, **kw)

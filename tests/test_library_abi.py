@@ -40,7 +40,7 @@ def _desc(T, **kw):
     (dict(radial=2, zone_nodes=3, zone_width=0.5), 2),
     (dict(radial=2, zone_nodes=3, zone_width=float("nan")), 2),
     (dict(radial=2, zone_nodes=3, zone_width=0.1, precision=4), 2),
-    (dict(form=2), 2), (dict(form=1, precision=1), 2), (dict(form=1, scheme=1), 2),
+    (dict(form=2), 2), (dict(form=1, precision=9), 2), (dict(form=1, scheme=1), 2),
     (dict(form=1, filter_on=1), 2), (dict(form=1, radial=1), 2),
 ])
 def test_create_grid_rejects_bad_descriptors(T, kw, status):
