@@ -21,10 +21,17 @@
 // circulant Phi derivative on the pair halves of v = sin Ph Fhat:
 //   sig = v(q) + v(q+h), del = v(q) - v(q+h):
 //   D v (p) = (Ms sig + Md del)/2,  D v (p+h) = (Ms sig - Md del)/2,
-// half the multiply-adds of the dense products. The Nyquist bin of the doubled
-// circle (2 NT nodes, the reflected node 2NT-1-j carrying -Fhat(j, m+h)) is
+// half the multiply-adds of the dense products. P and Q are centro-antisymmetric
+// (the Theta nodes are symmetric about pi/2), so rows k and NT-1-k come from the
+// Theta-even and -odd parts of s and d through half-size tables: a quarter of the
+// dense Theta multiply-adds in all. Since sin(Ph_{q+h}) = -sin(Ph_q), sig and del
+// are sin(Ph_q) d(q) and sin(Ph_q) s(q): the kernel folds sin(Ph_q)/2 into Ms, Md
+// and needs no array of v. The Nyquist bin of the doubled circle (2 NT nodes, the
+// reflected node 2NT-1-j carrying -Fhat(j, m+h)) is
 //   c(m) = (1/2NT) sum_j (-1)^j (Fhat(j, m) + Fhat(j, m+h)),
 //   P Fhat (k, m) = Fhat(k, m) - (-1)^k c(m),   c(m + h) = c(m).
+// The pass runs in the grid's element type: double for TS_FP64, float (tables and
+// arithmetic) for the float precisions.
 //
 // Number balance: one warp per angular block sums the block's Theta-Phi
 // quadrature of F, K, cos Th F and the source; a second kernel reduces each
